@@ -1,0 +1,397 @@
+/*
+ * FP64 CPU oracle for the echelle frame renderer -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Only the tests, the smoke check and the benchmark's CPU-baseline leg may load it;
+ * the product path never does.  It is deliberately plain: direct monomial sums, libm
+ * erfc, one stamp at a time, loops in the order the definition is written.
+ *
+ * Method (paper Sec. 2 and Sec. 2.2): the frame is the sum, over the wavelength grid
+ * of every order and fiber, of the fiber image projected on the detector; each fiber
+ * image is the pixel-integrated convolution of the fiber profile with the PSF.  The
+ * fiber profile is a set of slit points s_k with normalised weights u_k (Sec. 2.1:
+ * a normalised illumination profile multiplied at the end by the photons of the
+ * sample).  Readings where the paper is silent (polynomial spectral format, sample
+ * placement, window rule, truncation without renormalisation) are the ones listed in
+ * the design notes and repeated at each function below.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_PI 3.14159265358979323846
+
+/* Index of monomial lt^a s^b: ordered by total degree t = a+b, then a descending. */
+static int coeff_index(int a, int b) {
+  int t = a + b;
+  return t * (t + 1) / 2 + b;
+}
+
+/* Plain definition of the spectral-format polynomial: sum over a+b <= d of c_ab lt^a s^b. */
+static double poly2(const double* c, int degree, double lt, double s) {
+  double sum = 0.0;
+  for (int a = 0; a <= degree; ++a)
+    for (int b = 0; a + b <= degree; ++b) sum += c[coeff_index(a, b)] * pow(lt, a) * pow(s, b);
+  return sum;
+}
+
+static double quad(const double* c, double lt) { return c[0] + c[1] * lt + c[2] * lt * lt; }
+
+/* Standard normal CDF written with erfc so that the lower tail keeps relative precision. */
+static double Phi(double t) { return 0.5 * erfc(-t / sqrt(2.0)); }
+
+double oracle_normal_interval(double a, double b) {
+  /* P(a < Z < b).  When both ends are on the same side of the mean, take the
+   * difference of the two (small) tail probabilities on that side. */
+  if (a >= 0.0) return Phi(-a) - Phi(-b);
+  if (b <= 0.0) return Phi(b) - Phi(a);
+  return 1.0 - Phi(a) - Phi(-b);
+}
+
+static double phi(double t) { return exp(-0.5 * t * t) / sqrt(2.0 * ORACLE_PI); }
+
+/* ---------------------------------------------------------------- Gauss-Legendre */
+
+void oracle_gauss_legendre(int n, double* x, double* w) {
+  /* Roots of the Legendre polynomial P_n by Newton's method from the usual cosine
+   * guesses; P_n and P_{n-1} from the three-term recurrence
+   * k P_k = (2k-1) z P_{k-1} - (k-1) P_{k-2}, and P_n' = n (z P_n - P_{n-1}) / (z^2 - 1). */
+  for (int i = 0; i < n; ++i) {
+    double z = cos(ORACLE_PI * (i + 0.75) / (n + 0.5));
+    double pn = 0.0, dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      pn = p1;
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = pn / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-15) {
+        /* one more evaluation at the converged root for the weight */
+        p0 = 1.0;
+        p1 = z;
+        for (int k = 2; k <= n; ++k) {
+          double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+          p0 = p1;
+          p1 = p2;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        break;
+      }
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+/* ---------------------------------------------------------------- bivariate normal */
+
+/* P(X < h, Y < k) for unit-variance (X, Y) with correlation rho, by Plackett's identity
+ * dF/drho = bivariate density, integrated from rho = 0 with the substitution
+ * rho = sin(t) (the form Drezner & Wesolowsky and Genz use):
+ *   F = Phi(h) Phi(k) + 1/(2 pi) * int_0^{asin rho} exp(-(h^2 + k^2 - 2 h k sin t) / (2 cos^2 t)) dt
+ * The integral is taken with 20-point Gauss-Legendre quadrature. */
+double oracle_bvn_cdf(double h, double k, double rho) {
+  static double gx[20], gw[20];
+  static int init = 0;
+  if (!init) {
+#ifdef _OPENMP
+#pragma omp critical(oracle_gl_init)
+#endif
+    {
+      if (!init) {
+        oracle_gauss_legendre(20, gx, gw);
+        init = 1;
+      }
+    }
+  }
+  double base = Phi(h) * Phi(k);
+  if (rho == 0.0) return base;
+  double top = asin(rho);
+  double half = 0.5 * top, sum = 0.0;
+  for (int i = 0; i < 20; ++i) {
+    double t = half * (gx[i] + 1.0);
+    double st = sin(t), ct = cos(t);
+    sum += gw[i] * exp(-(h * h + k * k - 2.0 * h * k * st) / (2.0 * ct * ct));
+  }
+  return base + sum * half / (2.0 * ORACLE_PI);
+}
+
+double oracle_bvn_rect(double h0, double h1, double k0, double k1, double rho) {
+  /* Reflect an interval that lies wholly above the mean (X -> -X flips the sign of rho),
+   * so that the four corner probabilities are small tail values and the
+   * inclusion-exclusion keeps relative precision. */
+  if (h0 >= 0.0) {
+    double t = -h1;
+    h1 = -h0;
+    h0 = t;
+    rho = -rho;
+  }
+  if (k0 >= 0.0) {
+    double t = -k1;
+    k1 = -k0;
+    k0 = t;
+    rho = -rho;
+  }
+  return oracle_bvn_cdf(h1, k1, rho) - oracle_bvn_cdf(h0, k1, rho) - oracle_bvn_cdf(h1, k0, rho) +
+         oracle_bvn_cdf(h0, k0, rho);
+}
+
+/* ---------------------------------------------------------------- mapping */
+
+/* Sample j of n_lambda sits at the centre of the j-th equal bin of [lambda_lo, lambda_hi]
+ * (the wavelength grid of Sec. 2); the polynomial variable is that wavelength normalised
+ * to [-1, 1].  Slit point k of n_slit sits at the centre of the k-th equal bin of [-1, 1].
+ * The weight is flux density x bin width x slit weight (Sec. 2.1: normalised profile times
+ * the photons in the sample's wavelength range). */
+void oracle_map(const oracle_slice* s, int j, int k, double* x_c, double* y_c, double* sig_x,
+                double* sig_y, double* weight) {
+  double dl = (s->lambda_hi - s->lambda_lo) / s->n_lambda;
+  double lam = s->lambda_lo + (j + 0.5) * dl;
+  double lt = 2.0 * (lam - s->lambda_lo) / (s->lambda_hi - s->lambda_lo) - 1.0;
+  double sk = -1.0 + (2.0 * k + 1.0) / s->n_slit;
+  *x_c = poly2(s->cx, s->degree, lt, sk);
+  *y_c = poly2(s->cy, s->degree, lt, sk);
+  *sig_x = quad(s->sx, lt);
+  *sig_y = quad(s->sy, lt);
+  *weight = s->flux[j] * dl * s->u[k];
+}
+
+/* Window rule: the K x K window is centred on the pixel containing the mapped point;
+ * pixel i spans [i - 1/2, i + 1/2), so that pixel is floor(x_c + 1/2). */
+static int window_origin(double c, int K) { return (int)floor(c + 0.5) - K / 2; }
+
+/* Covariance of the elliptical PSF: widths sa, sb along axes rotated by theta. */
+static void ellipse_cov(double sa, double sb, double theta, double* vx, double* vy, double* cxy) {
+  double c = cos(theta), s = sin(theta);
+  *vx = sa * sa * c * c + sb * sb * s * s;
+  *vy = sa * sa * s * s + sb * sb * c * c;
+  *cxy = (sa * sa - sb * sb) * s * c;
+}
+
+void oracle_stamp(const oracle_slice* s, int psf, int j, int k, double* out, int* i0p, int* r0p) {
+  double xc, yc, sx, sy, w;
+  oracle_map(s, j, k, &xc, &yc, &sx, &sy, &w);
+  int K = s->K;
+  int i0 = window_origin(xc, K), r0 = window_origin(yc, K);
+  *i0p = i0;
+  *r0p = r0;
+  if (psf == ORACLE_PSF_SEPARABLE) {
+    for (int n = 0; n < K; ++n) {
+      double ay = oracle_normal_interval((r0 + n - 0.5 - yc) / sy, (r0 + n + 0.5 - yc) / sy);
+      for (int m = 0; m < K; ++m) {
+        double ax = oracle_normal_interval((i0 + m - 0.5 - xc) / sx, (i0 + m + 0.5 - xc) / sx);
+        out[n * K + m] = w * ax * ay;
+      }
+    }
+  } else {
+    double vx, vy, cxy;
+    ellipse_cov(sx, sy, s->theta, &vx, &vy, &cxy);
+    double gx = sqrt(vx), gy = sqrt(vy), rho = cxy / (gx * gy);
+    for (int n = 0; n < K; ++n)
+      for (int m = 0; m < K; ++m) {
+        double h0 = (i0 + m - 0.5 - xc) / gx, h1 = (i0 + m + 0.5 - xc) / gx;
+        double k0 = (r0 + n - 0.5 - yc) / gy, k1 = (r0 + n + 0.5 - yc) / gy;
+        out[n * K + m] = w * oracle_bvn_rect(h0, h1, k0, k1, rho);
+      }
+  }
+}
+
+double oracle_subpixel_sample(double xc, double yc, double sigx, double sigy, int i, int r, int nsub) {
+  double h = 1.0 / nsub, sum = 0.0;
+  for (int q = 0; q < nsub; ++q)
+    for (int p = 0; p < nsub; ++p) {
+      double x = i - 0.5 + (p + 0.5) * h, y = r - 0.5 + (q + 0.5) * h;
+      sum += phi((x - xc) / sigx) / sigx * phi((y - yc) / sigy) / sigy;
+    }
+  return sum * h * h;
+}
+
+/* ---------------------------------------------------------------- render */
+
+typedef struct {
+  int x0, y0, w, h; /* clipped band of the detector touched by the slice */
+  double* buf;
+} band_t;
+
+static int n_coeffs(int d) { return (d + 1) * (d + 2) / 2; }
+
+static int valid_slice(const oracle_slice* s, int n_det) {
+  if (s->detector < 0 || s->detector >= n_det) return 0;
+  if (s->K < 1 || s->K % 2 == 0 || s->n_lambda < 0 || s->n_slit < 0 || s->degree < 0) return 0;
+  if (!(s->lambda_hi > s->lambda_lo)) return 0;
+  return 1;
+}
+
+/* Render one slice into a private band of its detector (rows/cols it can touch). */
+static void render_slice(const oracle_slice* s, int psf, int H, int W, band_t* band) {
+  int K = s->K;
+  int xmin = W, xmax = -1, ymin = H, ymax = -1;
+  for (int j = 0; j < s->n_lambda; ++j)
+    for (int k = 0; k < s->n_slit; ++k) {
+      double xc, yc, sx, sy, w;
+      oracle_map(s, j, k, &xc, &yc, &sx, &sy, &w);
+      int i0 = window_origin(xc, K), r0 = window_origin(yc, K);
+      if (i0 < xmin) xmin = i0;
+      if (i0 + K - 1 > xmax) xmax = i0 + K - 1;
+      if (r0 < ymin) ymin = r0;
+      if (r0 + K - 1 > ymax) ymax = r0 + K - 1;
+    }
+  if (xmin < 0) xmin = 0;
+  if (ymin < 0) ymin = 0;
+  if (xmax > W - 1) xmax = W - 1;
+  if (ymax > H - 1) ymax = H - 1;
+  band->buf = NULL;
+  band->w = band->h = 0;
+  if (xmax < xmin || ymax < ymin) return;
+  band->x0 = xmin;
+  band->y0 = ymin;
+  band->w = xmax - xmin + 1;
+  band->h = ymax - ymin + 1;
+  band->buf = (double*)calloc((size_t)band->w * band->h, sizeof(double));
+  double* st = (double*)malloc(sizeof(double) * K * K);
+  for (int j = 0; j < s->n_lambda; ++j)
+    for (int k = 0; k < s->n_slit; ++k) {
+      int i0, r0;
+      oracle_stamp(s, psf, j, k, st, &i0, &r0);
+      for (int n = 0; n < K; ++n) {
+        int r = r0 + n;
+        if (r < band->y0 || r >= band->y0 + band->h) continue; /* outside the frame: dropped */
+        for (int m = 0; m < K; ++m) {
+          int i = i0 + m;
+          if (i < band->x0 || i >= band->x0 + band->w) continue;
+          band->buf[(size_t)(r - band->y0) * band->w + (i - band->x0)] += st[n * K + m];
+        }
+      }
+    }
+  free(st);
+}
+
+int oracle_render(int n_det, const int* H, const int* W, int n_slices, const oracle_slice* s, int psf,
+                  double** frames, int n_threads) {
+  if (n_det <= 0 || n_slices < 0) return -1;
+  for (int i = 0; i < n_slices; ++i)
+    if (!valid_slice(&s[i], n_det)) return -1;
+  for (int d = 0; d < n_det; ++d) memset(frames[d], 0, sizeof(double) * (size_t)H[d] * W[d]);
+  band_t* bands = (band_t*)calloc(n_slices > 0 ? n_slices : 1, sizeof(band_t));
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int i = 0; i < n_slices; ++i) render_slice(&s[i], psf, H[s[i].detector], W[s[i].detector], &bands[i]);
+  /* merge the private bands in slice order so the result does not depend on threads */
+  for (int i = 0; i < n_slices; ++i) {
+    band_t* b = &bands[i];
+    if (!b->buf) continue;
+    double* f = frames[s[i].detector];
+    int w = W[s[i].detector];
+    for (int r = 0; r < b->h; ++r)
+      for (int c = 0; c < b->w; ++c) f[(size_t)(b->y0 + r) * w + b->x0 + c] += b->buf[(size_t)r * b->w + c];
+    free(b->buf);
+  }
+  free(bands);
+  return 0;
+}
+
+/* ---------------------------------------------------------------- gradient */
+
+/* d/dx_c of P(e0 < X < e1), X ~ N(x_c, sig^2): -(phi(u1) - phi(u0)) / sig, u = (e - x_c)/sig.
+ * d/dsig of the same:                         -(u1 phi(u1) - u0 phi(u0)) / sig. */
+static void slice_grad(const oracle_slice* s, int H, int W, const double* R, double* gcx, double* gcy,
+                       double* gsx, double* gsy) {
+  int K = s->K, nc = n_coeffs(s->degree);
+  double* ax = (double*)malloc(sizeof(double) * K);
+  double* ay = (double*)malloc(sizeof(double) * K);
+  double* dax = (double*)malloc(sizeof(double) * K);
+  double* day = (double*)malloc(sizeof(double) * K);
+  double* sax = (double*)malloc(sizeof(double) * K);
+  double* say = (double*)malloc(sizeof(double) * K);
+  for (int c = 0; c < nc; ++c) gcx[c] = gcy[c] = 0.0;
+  for (int p = 0; p < 3; ++p) gsx[p] = gsy[p] = 0.0;
+  for (int j = 0; j < s->n_lambda; ++j)
+    for (int k = 0; k < s->n_slit; ++k) {
+      double xc, yc, sx, sy, w;
+      oracle_map(s, j, k, &xc, &yc, &sx, &sy, &w);
+      int i0 = window_origin(xc, K), r0 = window_origin(yc, K);
+      for (int m = 0; m < K; ++m) {
+        double u0 = (i0 + m - 0.5 - xc) / sx, u1 = (i0 + m + 0.5 - xc) / sx;
+        ax[m] = oracle_normal_interval(u0, u1);
+        dax[m] = -(phi(u1) - phi(u0)) / sx;
+        sax[m] = -(u1 * phi(u1) - u0 * phi(u0)) / sx;
+        double v0 = (r0 + m - 0.5 - yc) / sy, v1 = (r0 + m + 0.5 - yc) / sy;
+        ay[m] = oracle_normal_interval(v0, v1);
+        day[m] = -(phi(v1) - phi(v0)) / sy;
+        say[m] = -(v1 * phi(v1) - v0 * phi(v0)) / sy;
+      }
+      double gx = 0, gy = 0, gsig_x = 0, gsig_y = 0;
+      for (int n = 0; n < K; ++n) {
+        int r = r0 + n;
+        if (r < 0 || r >= H) continue;
+        for (int m = 0; m < K; ++m) {
+          int i = i0 + m;
+          if (i < 0 || i >= W) continue;
+          double res = R[(size_t)r * W + i];
+          gx += res * w * dax[m] * ay[n];
+          gy += res * w * ax[m] * day[n];
+          gsig_x += res * w * sax[m] * ay[n];
+          gsig_y += res * w * ax[m] * say[n];
+        }
+      }
+      double dl = (s->lambda_hi - s->lambda_lo) / s->n_lambda;
+      double lam = s->lambda_lo + (j + 0.5) * dl;
+      double lt = 2.0 * (lam - s->lambda_lo) / (s->lambda_hi - s->lambda_lo) - 1.0;
+      double sk = -1.0 + (2.0 * k + 1.0) / s->n_slit;
+      for (int a = 0; a <= s->degree; ++a)
+        for (int b = 0; a + b <= s->degree; ++b) {
+          double mono = pow(lt, a) * pow(sk, b);
+          gcx[coeff_index(a, b)] += gx * mono;
+          gcy[coeff_index(a, b)] += gy * mono;
+        }
+      for (int p = 0; p < 3; ++p) {
+        gsx[p] += gsig_x * pow(lt, p);
+        gsy[p] += gsig_y * pow(lt, p);
+      }
+    }
+  free(ax); free(ay); free(dax); free(day); free(sax); free(say);
+}
+
+double oracle_loss_grad(int n_det, const int* H, const int* W, int n_slices, const oracle_slice* s,
+                        const double* const* target, double* g_cx, double* g_cy, double* g_sx, double* g_sy,
+                        int n_threads) {
+  double** frames = (double**)malloc(sizeof(double*) * n_det);
+  for (int d = 0; d < n_det; ++d) frames[d] = (double*)malloc(sizeof(double) * (size_t)H[d] * W[d]);
+  if (oracle_render(n_det, H, W, n_slices, s, ORACLE_PSF_SEPARABLE, frames, n_threads) != 0) {
+    for (int d = 0; d < n_det; ++d) free(frames[d]);
+    free(frames);
+    return NAN;
+  }
+  double loss = 0.0;
+  for (int d = 0; d < n_det; ++d)
+    for (size_t p = 0; p < (size_t)H[d] * W[d]; ++p) {
+      double r = frames[d][p] - target[d][p];
+      loss += r * r;
+      frames[d][p] = 2.0 * r; /* dL/dI */
+    }
+  int* off = (int*)malloc(sizeof(int) * (n_slices + 1));
+  off[0] = 0;
+  for (int i = 0; i < n_slices; ++i) off[i + 1] = off[i] + n_coeffs(s[i].degree);
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int i = 0; i < n_slices; ++i)
+    slice_grad(&s[i], H[s[i].detector], W[s[i].detector], frames[s[i].detector], g_cx + off[i], g_cy + off[i],
+               g_sx + 3 * i, g_sy + 3 * i);
+  free(off);
+  for (int d = 0; d < n_det; ++d) free(frames[d]);
+  free(frames);
+  return loss;
+}

@@ -1,0 +1,84 @@
+/*
+ * FP64 CPU oracle for the echelle frame renderer -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Only the test-suite, the smoke check and the benchmark's CPU-baseline leg may
+ * load this library.  The product renderer never calls it and shares no code,
+ * header, table or constant with it.
+ *
+ * What it computes (paper Sec. 2, Sec. 2.2): the synthetic echellogram is the
+ * superposition, over a wavelength grid, of the images of the fiber (a normalised
+ * illumination profile scaled by the photons of the sample), each image being the
+ * PSF integrated over the detector pixels.  Written out for one order-slice o:
+ *
+ *   I[r][i] += sum_j sum_k  w_ojk * integral over pixel (i, r) of PSF_ojk(x - x_c, y - y_c)
+ *
+ * restricted to the K x K pixel window centred on the pixel that contains the
+ * mapped position (x_c, y_c), in FP64 with libm erfc.
+ */
+#ifndef E2E_ORACLE_H
+#define E2E_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORACLE_PSF_SEPARABLE = 0, ORACLE_PSF_ELLIPTICAL = 1 };
+
+typedef struct {
+  int detector;
+  int degree;       /* total degree of the (lt, s) -> (x, y) polynomials */
+  int K;            /* odd window size in pixels */
+  int n_lambda;     /* wavelength samples of the order */
+  int n_slit;       /* slit points */
+  double lambda_lo, lambda_hi;
+  const double* cx; /* (degree+1)(degree+2)/2 coefficients, ordered by total degree, then a descending */
+  const double* cy;
+  double sx[3];     /* PSF width polynomial (quadratic in lt), pixels */
+  double sy[3];
+  double theta;     /* rotation of the elliptical PSF axes, radians */
+  const double* u;  /* n_slit slit weights */
+  const double* flux; /* n_lambda flux samples (photons / Angstrom) at the bin centres */
+} oracle_slice;
+
+/* Render every order-slice into its detector frame.  frames[d] points to H[d]*W[d]
+ * doubles (row-major, row = y); they are overwritten.  n_threads <= 0 uses all cores.
+ * Returns 0, or -1 on an invalid argument. */
+int oracle_render(int n_det, const int* H, const int* W, int n_slices, const oracle_slice* s,
+                  int psf, double** frames, int n_threads);
+
+/* Mapped position and PSF widths of stamp (j, k) of one order-slice. */
+void oracle_map(const oracle_slice* s, int j, int k, double* x_c, double* y_c, double* sig_x,
+                double* sig_y, double* weight);
+
+/* The K*K pixel values of one stamp (row-major n*K+m, pixel (i0+m, r0+n)), and its window origin. */
+void oracle_stamp(const oracle_slice* s, int psf, int j, int k, double* out, int* i0, int* r0);
+
+/* P(a < Z < b) for a standard normal Z, a <= b. */
+double oracle_normal_interval(double a, double b);
+
+/* Bivariate standard normal CDF P(X < h, Y < k) with correlation rho (|rho| <= 0.95). */
+double oracle_bvn_cdf(double h, double k, double rho);
+
+/* P(h0 < X < h1, k0 < Y < k1) for the standard bivariate normal with correlation rho. */
+double oracle_bvn_rect(double h0, double h1, double k0, double k1, double rho);
+
+/* n-point Gauss-Legendre nodes and weights on [-1, 1]. */
+void oracle_gauss_legendre(int n, double* x, double* w);
+
+/* Pixel integral of a separable Gaussian by the paper's sub-pixel sampling (Sec. 2.2):
+ * density evaluated at the centres of an nsub x nsub grid of sub-pixels, times the
+ * sub-pixel area.  Pixel (i, r) relative to a centre at (xc, yc). */
+double oracle_subpixel_sample(double xc, double yc, double sigx, double sigy, int i, int r, int nsub);
+
+/* Gradient of L = sum over pixels of (I - T)^2 with respect to every order-slice's
+ * cx, cy (n_c each), sx, sy (3 each), holding each stamp's window origin fixed at
+ * the one the forward render picks.  T has the frames' layout.  Outputs are
+ * concatenated per order-slice in the order they are given.  Returns L. */
+double oracle_loss_grad(int n_det, const int* H, const int* W, int n_slices, const oracle_slice* s,
+                        const double* const* target, double* g_cx, double* g_cy, double* g_sx,
+                        double* g_sy, int n_threads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
