@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark: PSF stamps rendered per second on the full single-detector frame workload.
+
+Workload: 9216 x 9216 FP32 frame, 85 orders x 2 fibers x 2 slices, 6000 wavelength samples x
+64 slit points per order-slice, degree-5 polynomials, field-varying Gaussian PSF (sigma
+1.2-2.0 px), 11 x 11 stamps; science fiber = continuum + 20000 lines, reference fiber =
+Fabry-Perot comb (seeded synthetic stand-ins for an ESPRESSO/HIRES-class echellogram).
+
+One step = one render of the whole frame (mapping, PSF stamps, on-chip accumulation, tile
+merge, frame write) through the C ABI.  ``value`` is stamps/s with the model and spectra
+resident in HBM, timed with CUDA events on the render stream; L2 is flushed between steps
+(a 256 MiB memset outside the timed events).  ``e2e`` is the same metric through the public
+API from pinned host memory: per step the spectra are uploaded (e2e_load_spectrum), the
+frame rendered into a library-owned buffer and fetched to pinned host memory.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (bounded sample of
+the same workload per step).  Under torchrun each rank renders its own detector frame
+(independent frames, no collective: weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2008_05858_gb300 import workloads as W  # noqa: E402
+
+METRIC = "PSF stamps/s at <1e-5 px photocenter err, mixed vs FP64; p99 render latency"
+UNIT = "stamps/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# FP32 lane operations of one separable stamp of window K, counted algorithmically:
+# 2(K+1) Gaussian-tail (erf) evaluations at 16 FP32 operations each (an exponential on the
+# SFU plus a ~12-term rational), 2K edge differences, K^2 products and K^2 sums.
+def fp32_ops_per_stamp(K: int) -> float:
+    return 2 * (K + 1) * 16 + 2 * K + 2 * K * K
+
+
+# FP64 FMAs of one stamp: Horner in s of both coordinates (2 d), plus the per-sample
+# Horner in lambda (2 n_c) spread over the n_slit stamps of the sample.
+def fp64_fma_per_stamp(d: int, n_slit: int) -> float:
+    nc = (d + 1) * (d + 2) / 2
+    return 2 * d + 2 * nc / n_slit
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons), samples=len(sm))
+        try:
+            os.unlink(self.path)
+        except Exception:
+            pass
+        return out
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_sample_rate(w: W.Workload, seconds: float = 12.0, max_slices: int = 64):
+    """Stamps/s of the FP64 oracle on a bounded sample (the first order-slices of w)."""
+    import oracle
+
+    cores = os.cpu_count() or 1
+    per = w.model.slices[0].n_lambda * w.model.slices[0].n_slit
+    n = min(len(w.model.slices), max_slices, max(cores, 1))
+    sub = W.OpticalModel(w.model.det_shape, w.model.slices[:n], w.model.psf)
+    t0 = time.perf_counter()
+    oracle.render(sub, w.flux_for, n_threads=cores)
+    dt = time.perf_counter() - t0
+    # scale the sample to ~`seconds` of work if the first pass was short
+    if dt < seconds / 4 and n < len(w.model.slices):
+        n2 = min(len(w.model.slices), max_slices, int(n * min(8.0, seconds / max(dt, 1e-3))))
+        sub = W.OpticalModel(w.model.det_shape, w.model.slices[:n2], w.model.psf)
+        t0 = time.perf_counter()
+        oracle.render(sub, w.flux_for, n_threads=cores)
+        dt = time.perf_counter() - t0
+        n = n2
+    stamps = n * per
+    return stamps / dt, cores, f"first {n} of {len(w.model.slices)} order-slices ({stamps} stamps), FP64, {dt:.1f} s"
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = W.config2()
+    steps = []
+    for i in range(args.warmup + args.steps):
+        rate, cores, sample = oracle_sample_rate(w, seconds=4.0, max_slices=16)
+        if i >= args.warmup:
+            steps.append(rate)
+    value = statistics.median(steps)
+    stamps = w.model.n_stamps
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": stamps / value * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "stamps_per_frame": stamps, "frame": "9216x9216", "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_2008_05858_gb300 import binding as B
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = local if torch.cuda.is_available() else 0
+    torch.cuda.set_device(dev)
+    w = W.config2(seed=W.SEED_BASE + 2 + rank * 1000 if rank else None)
+    K = w.model.slices[0].K
+    stamps = w.model.n_stamps
+    r = B.Renderer(dev, kernel_timing=1)
+    mid = r.load_model(w.model)
+    sids = r.load_spectra(w)
+    plan = r.plan(mid)
+    frame = r.empty_frames(mid, "f32")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(prec="mixed"):
+        r.render(mid, sids, prec, "f32", out=frame, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kern = {}
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+            for name, ms in B.e2e_kernel_times(r.ctx):
+                kern.setdefault(name, []).append(ms)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = stamps * world / (ms_per_step * 1e-3)
+    clocks = clk.summary()
+
+    # plain FP64 renderer on the same frame (side by side, fewer steps: it is slow)
+    fp64_ms = []
+    step("fp64")
+    torch.cuda.synchronize()
+    for _ in range(max(1, min(3, args.steps))):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step("fp64")
+        b.record(stream)
+        torch.cuda.synchronize()
+        fp64_ms.append(a.elapsed_time(b))
+    fp64_value = stamps / (statistics.median(fp64_ms) * 1e-3)
+
+    # end to end through the public API from pinned host memory
+    pinned = {}
+    for f, sp in w.spectra.items():
+        orders = sorted(sp.flux)
+        cat = torch.from_numpy(np.concatenate([np.asarray(sp.flux[o], dtype=np.float64) for o in orders]))
+        pinned[f] = (orders, [len(sp.flux[o]) for o in orders], cat.pin_memory())
+    h, wd = w.model.det_shape[0]
+    host_frame = torch.empty((h, wd), dtype=torch.float32).pin_memory()
+    h2d = sum(t.numel() * 8 for _, _, t in pinned.values())
+    d2h = host_frame.numel() * 4
+
+    def e2e_step():
+        ids = []
+        for f, (orders, lens, flux) in pinned.items():
+            ids.append(_load_spectrum_ptr(B, r.ctx, f, orders, lens, flux))
+        fid = B.e2e_render_alloc(r.ctx, mid, ids, B.E2E_PREC_MIXED, B.E2E_F32, stream)
+        B.e2e_fetch_frame(r.ctx, fid, 0, host_frame.data_ptr(), False, d2h, stream)
+        stream.synchronize()
+        B.e2e_release_frame(r.ctx, fid)
+        for i in ids:
+            B.e2e_unload_spectrum(r.ctx, i)
+
+    e2e_step()
+    e2e_ms = []
+    for _ in range(max(1, min(5, args.steps))):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_value = stamps * world / (statistics.median(e2e_ms) * 1e-3)
+
+    peaks, peak_kind = _peaks()
+    mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    kr = statistics.median(kern.get("render_mixed", [float("nan")]))
+    km = statistics.median(kern.get("merge", [float("nan")]))
+    d = w.model.slices[0].degree
+    ns = w.model.slices[0].n_slit
+    fp32_peak = n_sm * 128 * 2 * mhz * 1e6  # FLOP/s, FMA = 2
+    fp64_peak = n_sm * 2 * 2 * mhz * 1e6  # 2 DFMA/clk/SM measured (FMA = 2 FLOP)
+    a32 = fp32_ops_per_stamp(K) * 2 * stamps / (kr * 1e-3)  # ops counted as FMA-slots -> FLOP
+    a64 = fp64_fma_per_stamp(d, ns) * 2 * stamps / (kr * 1e-3)
+    traffic = _load_traffic()
+    roof32 = {"bound": "alu", "achieved": a32 / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+              "frac": a32 / fp32_peak, "traffic": traffic,
+              "kernel": "render_mixed", "pipe": "fp32", "kernel_ms": kr,
+              "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (median SM clock under load)"}
+    roof64 = {"bound": "alu", "achieved": a64 / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+              "frac": a64 / fp64_peak, "kernel": "render_mixed", "pipe": "fp64",
+              "peak_basis": f"{n_sm} SMs x 2 DFMA/clk (probe) x 2 x {mhz:.0f} MHz"}
+    roof = roof32 if roof32["frac"] >= roof64["frac"] else roof64
+    other = roof64 if roof is roof32 else roof32
+    launches_per_step = sum(1 for _ in kern)  # distinct kernels per render
+    n_launch = sum(len(v) for v in kern.values())
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "frame": "9216x9216 f32", "orders": 85, "fibers": 2, "slices": 2,
+                   "n_lambda": 6000, "n_slit": 64, "degree": 5, "K": K, "stamps_per_frame": stamps,
+                   "precision": "mixed (FP64 mapping, FP32 stamps, FP64 tile accumulation)",
+                   "l2": "flushed between steps (256 MiB memset outside the timed events)",
+                   "parallelism": f"independent frame per GPU x{world}", "plan": plan},
+        "roofline": roof, "roofline_other_pipe": other,
+        "fp64_renderer": {"value": fp64_value, "unit": UNIT, "ms_per_step": statistics.median(fp64_ms),
+                          "speedup_mixed_over_fp64": value / world / fp64_value},
+        "kernel_ms": {"render_mixed": kr, "merge": km},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": statistics.median(e2e_ms)},
+        "gpu_launches": n_launch,
+        "launches_per_step": launches_per_step,
+        "clocks": clocks, "peak_source": peak_kind, "wall_s_timed": t_wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, sample = oracle_sample_rate(w)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    r.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _load_spectrum_ptr(B, ctx, fiber, orders, lens, flux_tensor):
+    import ctypes as C
+
+    n = len(orders)
+    oid = (C.c_int32 * n)(*orders)
+    nl = (C.c_int32 * n)(*lens)
+    sid = C.c_uint64()
+    B._check(B.load_library().e2e_load_spectrum(C.c_void_p(ctx), fiber, n, oid, nl,
+                                                C.cast(C.c_void_p(flux_tensor.data_ptr()), C.POINTER(C.c_double)),
+                                                C.byref(sid)))
+    return sid.value
+
+
+def _load_traffic():
+    """DRAM bytes per launch of the render kernel from the committed ncu summary, if current."""
+    p = os.path.join(ROOT, "profiles", "render_mixed_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("traffic_bytes_per_launch")
+    except Exception:
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

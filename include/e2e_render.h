@@ -1,0 +1,180 @@
+/*
+ * e2e_render.h -- C ABI of the GB300 echelle frame renderer.
+ *
+ * The library renders the raw detector frame of a fiber-fed echelle spectrograph
+ * from a source spectrum, as the image simulator of arXiv:2008.05858 does (Sec. 2.2):
+ * the frame is the superposition, over a wavelength grid, of the images of the fiber
+ * projected on the detector, each image being the PSF integrated over the pixels.
+ *
+ * Model of one order-slice o (one trace: detector, diffraction order, fiber, slice):
+ *   - wavelength samples j = 0..n_lambda-1 at the centres of n_lambda equal bins of
+ *     [lambda_lo, lambda_hi]; lt_j = that wavelength normalised to [-1, 1];
+ *   - slit points k = 0..n_slit-1 at the centres of n_slit equal bins of s in [-1, 1];
+ *   - a stamp (o, j, k) has weight  w = flux_o[j] * (lambda_hi - lambda_lo)/n_lambda * u_k
+ *     (Sec. 2.1: normalised illumination profile u times the photons of the sample);
+ *   - its centre is (x_c, y_c) = (P_x(lt_j, s_k), P_y(lt_j, s_k)), with P the total-degree
+ *     polynomials given by cx/cy (the spectral format of Sec. 2.1, here in polynomial form);
+ *   - its PSF is a Gaussian with widths sigma_x(lt), sigma_y(lt) (quadratics in lt; Sec. 2.1
+ *     models the PSF analytically as an asymmetric Gaussian), axis-aligned
+ *     (E2E_PSF_SEPARABLE) or with axes rotated by theta (E2E_PSF_ELLIPTICAL);
+ *   - it deposits into the K x K pixel window centred on pixel (floor(x_c+1/2),
+ *     floor(y_c+1/2)) the exact integral of the PSF over each pixel (pixel i spans
+ *     [i-1/2, i+1/2)); flux outside the window is not deposited (no renormalisation),
+ *     pixels outside the detector are dropped.
+ *
+ * Conventions: every function returns 0 (E2E_OK) or a negative E2E_E* code; the text of
+ * the last error of the calling thread is in e2e_last_error().  No C++ exception crosses
+ * the ABI.  Ids are opaque 64-bit handles.  The caller keeps ownership of every array it
+ * passes; the library copies what it keeps.  All work is asynchronous on the CUDA stream
+ * given (a cudaStream_t; NULL = legacy default stream) unless stated otherwise.
+ */
+#ifndef E2E_RENDER_H
+#define E2E_RENDER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ error codes */
+#define E2E_OK 0
+#define E2E_EINVAL -1    /* invalid argument or model */
+#define E2E_ENOMEM -2    /* device memory exhausted */
+#define E2E_ECUDA -3     /* a CUDA call failed; see e2e_last_error() */
+#define E2E_ENOTFOUND -4 /* unknown id */
+#define E2E_EBUSY -5     /* serving: job queued, not admitted yet */
+#define E2E_ETOOBIG -6   /* serving: job can never fit the memory pool */
+#define E2E_ETIMEOUT -7  /* serving: wait timed out */
+#define E2E_ECANCELLED -8
+#define E2E_EDEVICE -9   /* a kernel reported an error status (bounds check) */
+
+/* ------------------------------------------------------------------ enums */
+enum { E2E_PSF_SEPARABLE = 0, E2E_PSF_ELLIPTICAL = 1 };
+/* E2E_PREC_MIXED: FP64 mapping, FP32 PSF stamps in on-chip tiles, FP64 tile accumulation,
+ *                 compensated merge (the fast path).
+ * E2E_PREC_FP64:  everything in FP64, one thread per stamp, FP64 global atomics (baseline). */
+enum { E2E_PREC_MIXED = 0, E2E_PREC_FP64 = 1 };
+enum { E2E_F32 = 0, E2E_F64 = 1 };
+
+/* ------------------------------------------------------------------ limits */
+#define E2E_MAX_DEGREE 8  /* polynomial total degree */
+#define E2E_MAX_K 15      /* window size (odd) */
+
+typedef struct e2e_ctx e2e_ctx;
+
+typedef struct {
+  size_t pool_bytes; /* cap on the device scratch the context may hold (0 = no cap) */
+  int32_t max_inflight; /* serving: jobs on the device at once (0 = default 4) */
+  int32_t debug_checks; /* 1 = kernels bounds-check every deposit and report E2E_EDEVICE */
+  int32_t kernel_timing; /* 1 = record CUDA events around each kernel of a render (see e2e_kernel_times) */
+} e2e_opts;
+
+/* One order-slice (trace).  Arrays are read during e2e_load_model only. */
+typedef struct {
+  int32_t detector;    /* index into the model's detectors */
+  int32_t order;       /* diffraction order number (matches spectra) */
+  int32_t fiber;       /* fiber id (matches spectra) */
+  int32_t slice;       /* pupil slice id (informational) */
+  int32_t degree;      /* total degree d of the (lt, s) polynomials, 0..E2E_MAX_DEGREE */
+  int32_t K;           /* window size, odd, 1..E2E_MAX_K */
+  int32_t n_lambda;    /* wavelength samples, >= 1 */
+  int32_t n_slit;      /* slit points, >= 1 */
+  double lambda_lo, lambda_hi; /* wavelength range (lambda_hi > lambda_lo) */
+  const double* cx;    /* (d+1)(d+2)/2 coefficients of x, index(a,b) = t(t+1)/2 + b, t = a+b,
+                          multiplying lt^a s^b (ordered by total degree, then a descending) */
+  const double* cy;    /* same for y */
+  double sigma_x[3];   /* PSF width (px) = c0 + c1 lt + c2 lt^2; must stay > 0 on [-1, 1] */
+  double sigma_y[3];
+  double theta;        /* E2E_PSF_ELLIPTICAL: rotation of the PSF axes (radians), |rho| <= 0.9 */
+  const double* slit_weights; /* n_slit weights u_k (finite, >= 0) */
+} e2e_order_slice;
+
+typedef struct {
+  int32_t n_detectors;
+  const int32_t* height; /* rows per detector (y) */
+  const int32_t* width;  /* columns per detector (x) */
+  int32_t n_slices;
+  const e2e_order_slice* slices;
+  int32_t psf;           /* E2E_PSF_SEPARABLE or E2E_PSF_ELLIPTICAL */
+} e2e_model_desc;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`.  opts may be NULL (defaults).
+ * Errors: E2E_EINVAL (bad device), E2E_ECUDA. */
+int e2e_create(e2e_ctx** out, int32_t device, const e2e_opts* opts);
+
+/* Destroy a context and free everything it owns (models, spectra, frames, scratch).
+ * Synchronises the device first.  NULL is a no-op. */
+void e2e_destroy(e2e_ctx* ctx);
+
+/* Text of the last error reported to the calling thread ("" if none).  Valid until the
+ * thread's next failing call. */
+const char* e2e_last_error(void);
+
+/* ------------------------------------------------------------------ resident data */
+
+/* Load an optical model (the spectral-format database of Sec. 2.1, which the paper
+ * computes once and reuses across simulations): validates it (degree, K odd, widths > 0 on
+ * [-1, 1], finite coefficients, |rho| <= 0.9 for the elliptical PSF), copies it to the
+ * device and plans the tiled render (synchronous; uses the context's device).
+ * Errors: E2E_EINVAL, E2E_ENOMEM, E2E_ECUDA. */
+int e2e_load_model(e2e_ctx* ctx, const e2e_model_desc* desc, uint64_t* model_id);
+int e2e_unload_model(e2e_ctx* ctx, uint64_t model_id);
+
+/* Load the spectrum of one fiber: n_orders orders (order_ids), order i holding n_lambda[i]
+ * flux samples (photons per Angstrom at the bin centres of that order's order-slices),
+ * packed consecutively in `flux`.  Copied to the device (synchronous).
+ * Errors: E2E_EINVAL (non-finite flux, duplicate order), E2E_ENOMEM, E2E_ECUDA. */
+int e2e_load_spectrum(e2e_ctx* ctx, int32_t fiber, int32_t n_orders, const int32_t* order_ids,
+                      const int32_t* n_lambda, const double* flux, uint64_t* spec_id);
+int e2e_unload_spectrum(e2e_ctx* ctx, uint64_t spec_id);
+
+/* ------------------------------------------------------------------ render */
+
+/* Render every detector of `model` lit by the spectra `spec_ids` (one per fiber used by
+ * the model; each order-slice takes the row of its fiber's spectrum for its order, whose
+ * length must equal its n_lambda).
+ *   dst[d]: device pointer to detector d's frame, row-major, dtype E2E_F32 or E2E_F64,
+ *           pitch_elems[d] elements between rows (pitch_elems may be NULL = width).
+ *           Every pixel of the frame is written.
+ *   precision: E2E_PREC_MIXED or E2E_PREC_FP64.
+ * Asynchronous on `stream`; scratch comes from the context and is released in stream
+ * order.  Errors: E2E_EINVAL, E2E_ENOTFOUND, E2E_ENOMEM, E2E_ECUDA. */
+int e2e_render(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids, int32_t precision,
+               int32_t dtype, void* const* dst, const int64_t* pitch_elems, void* stream);
+
+/* As e2e_render, into frames the library allocates and owns until e2e_release_frame. */
+int e2e_render_alloc(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids,
+                     int32_t precision, int32_t dtype, void* stream, uint64_t* frame_id);
+
+/* Copy detector `detector` of a library-owned frame (height*width elements of its dtype,
+ * row-major) to dst (device or host memory, `bytes` must equal the frame's size).
+ * Stream-ordered; a host destination is complete when the stream is. */
+int e2e_fetch_frame(e2e_ctx* ctx, uint64_t frame_id, int32_t detector, void* dst, int32_t dst_is_device,
+                    size_t bytes, void* stream);
+int e2e_release_frame(e2e_ctx* ctx, uint64_t frame_id);
+
+/* Shape of the mixed-precision plan chosen for a model (for reports/tests): chunk of
+ * wavelength samples per work item, slit points per register run, tile slack, number of
+ * work items, tile size of the merge, and bytes of scratch one render needs. */
+typedef struct {
+  int32_t chunk_lambda, run_slit, slack_x, slack_y;
+  int64_t n_items, n_tiles, scratch_bytes;
+  int32_t tile_w, tile_h, boxes_per_cta, max_box_area;
+} e2e_plan_info;
+int e2e_model_plan(e2e_ctx* ctx, uint64_t model_id, e2e_plan_info* info);
+
+/* Kernel timing (contexts created with kernel_timing = 1): durations in milliseconds of the
+ * kernels of the context's most recent render, measured with CUDA events recorded on the
+ * render's stream around each launch.  Blocks until those events complete.  Writes up to
+ * `cap` entries: names[i] points to a static string naming the kernel; *n receives the
+ * number of kernels.  Errors: E2E_EINVAL (timing not enabled), E2E_ECUDA. */
+int e2e_kernel_times(e2e_ctx* ctx, const char** names, float* ms, int32_t cap, int32_t* n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

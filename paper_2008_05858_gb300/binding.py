@@ -1,0 +1,330 @@
+"""Thin ctypes binding of the renderer's C ABI (``include/e2e_render.h``).
+
+Functions named ``e2e_*`` marshal arguments to the C entry points of the same name and
+nothing else: every step of the render runs in the library's CUDA kernels.  PyTorch only
+supplies device memory and streams.  The :class:`Renderer` class is a convenience layer
+over those calls for optical models and spectra built by :mod:`.workloads`.
+
+There is no CPU fallback: if the library cannot be loaded, or no GPU is present, calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+from . import workloads as W
+
+E2E_OK = 0
+E2E_EINVAL = -1
+E2E_ENOMEM = -2
+E2E_ECUDA = -3
+E2E_ENOTFOUND = -4
+E2E_EBUSY = -5
+E2E_ETOOBIG = -6
+E2E_ETIMEOUT = -7
+E2E_ECANCELLED = -8
+E2E_EDEVICE = -9
+
+E2E_PSF_SEPARABLE = 0
+E2E_PSF_ELLIPTICAL = 1
+E2E_PREC_MIXED = 0
+E2E_PREC_FP64 = 1
+E2E_F32 = 0
+E2E_F64 = 1
+
+PRECISION = {"mixed": E2E_PREC_MIXED, "fp64": E2E_PREC_FP64}
+DTYPE = {"f32": E2E_F32, "f64": E2E_F64}
+
+
+class E2EError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"e2e error {code}: {msg}")
+        self.code = code
+
+
+class e2e_opts(C.Structure):
+    _fields_ = [("pool_bytes", C.c_size_t), ("max_inflight", C.c_int32), ("debug_checks", C.c_int32),
+                ("kernel_timing", C.c_int32)]
+
+
+class e2e_order_slice(C.Structure):
+    _fields_ = [
+        ("detector", C.c_int32), ("order", C.c_int32), ("fiber", C.c_int32), ("slice", C.c_int32),
+        ("degree", C.c_int32), ("K", C.c_int32), ("n_lambda", C.c_int32), ("n_slit", C.c_int32),
+        ("lambda_lo", C.c_double), ("lambda_hi", C.c_double),
+        ("cx", C.POINTER(C.c_double)), ("cy", C.POINTER(C.c_double)),
+        ("sigma_x", C.c_double * 3), ("sigma_y", C.c_double * 3), ("theta", C.c_double),
+        ("slit_weights", C.POINTER(C.c_double)),
+    ]
+
+
+class e2e_model_desc(C.Structure):
+    _fields_ = [
+        ("n_detectors", C.c_int32), ("height", C.POINTER(C.c_int32)), ("width", C.POINTER(C.c_int32)),
+        ("n_slices", C.c_int32), ("slices", C.POINTER(e2e_order_slice)), ("psf", C.c_int32),
+    ]
+
+
+class e2e_plan_info(C.Structure):
+    _fields_ = [
+        ("chunk_lambda", C.c_int32), ("run_slit", C.c_int32), ("slack_x", C.c_int32), ("slack_y", C.c_int32),
+        ("n_items", C.c_int64), ("n_tiles", C.c_int64), ("scratch_bytes", C.c_int64),
+        ("tile_w", C.c_int32), ("tile_h", C.c_int32), ("boxes_per_cta", C.c_int32), ("max_box_area", C.c_int32),
+    ]
+
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_lib = None
+_lock = threading.Lock()
+
+_SIGS = {
+    "e2e_last_error": ([], C.c_char_p),
+    "e2e_create": ([C.POINTER(C.c_void_p), C.c_int32, C.POINTER(e2e_opts)], C.c_int),
+    "e2e_destroy": ([C.c_void_p], None),
+    "e2e_load_model": ([C.c_void_p, C.POINTER(e2e_model_desc), C.POINTER(C.c_uint64)], C.c_int),
+    "e2e_unload_model": ([C.c_void_p, C.c_uint64], C.c_int),
+    "e2e_load_spectrum": ([C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                           C.POINTER(C.c_double), C.POINTER(C.c_uint64)], C.c_int),
+    "e2e_unload_spectrum": ([C.c_void_p, C.c_uint64], C.c_int),
+    "e2e_render": ([C.c_void_p, C.c_uint64, C.c_int32, C.POINTER(C.c_uint64), C.c_int32, C.c_int32,
+                    C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.c_void_p], C.c_int),
+    "e2e_render_alloc": ([C.c_void_p, C.c_uint64, C.c_int32, C.POINTER(C.c_uint64), C.c_int32, C.c_int32,
+                          C.c_void_p, C.POINTER(C.c_uint64)], C.c_int),
+    "e2e_fetch_frame": ([C.c_void_p, C.c_uint64, C.c_int32, C.c_void_p, C.c_int32, C.c_size_t, C.c_void_p], C.c_int),
+    "e2e_release_frame": ([C.c_void_p, C.c_uint64], C.c_int),
+    "e2e_model_plan": ([C.c_void_p, C.c_uint64, C.POINTER(e2e_plan_info)], C.c_int),
+    "e2e_kernel_times": ([C.c_void_p, C.POINTER(C.c_char_p), C.POINTER(C.c_float), C.c_int32,
+                          C.POINTER(C.c_int32)], C.c_int),
+}
+
+
+def lib_path() -> str:
+    return os.path.join(HERE, "_build", "libe2e_render.so")
+
+
+def load_library(build_if_missing: bool = True):
+    """Load (building first if needed) the C-ABI library.  Raises if it cannot."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = lib_path()
+            if build_if_missing:
+                from . import build as _build
+
+                path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"renderer library not built: {path}")
+            L = C.CDLL(path)
+            for name, (args, res) in _SIGS.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def exported_symbols() -> List[str]:
+    return list(_SIGS)
+
+
+def _check(rc: int):
+    if rc != E2E_OK:
+        raise E2EError(rc, load_library().e2e_last_error().decode())
+
+
+# ------------------------------------------------------------------ raw C ABI (same names)
+
+
+def e2e_create(device: int = 0, pool_bytes: int = 0, max_inflight: int = 0, debug_checks: int = 0,
+               kernel_timing: int = 0) -> int:
+    L = load_library()
+    h = C.c_void_p()
+    o = e2e_opts(pool_bytes, max_inflight, debug_checks, kernel_timing)
+    _check(L.e2e_create(C.byref(h), device, C.byref(o)))
+    return h.value
+
+
+def e2e_destroy(ctx: int) -> None:
+    load_library().e2e_destroy(C.c_void_p(ctx))
+
+
+class _ModelDesc:
+    """C view of an OpticalModel; keeps the numpy arrays alive."""
+
+    def __init__(self, model: W.OpticalModel):
+        self.keep = []
+        n = len(model.slices)
+        self.sl = (e2e_order_slice * max(n, 1))()
+        dp = C.POINTER(C.c_double)
+        for i, s in enumerate(model.slices):
+            cx = np.ascontiguousarray(s.cx, dtype=np.float64)
+            cy = np.ascontiguousarray(s.cy, dtype=np.float64)
+            u = np.ascontiguousarray(s.slit_weights, dtype=np.float64)
+            self.keep += [cx, cy, u]
+            o = self.sl[i]
+            o.detector, o.order, o.fiber, o.slice = s.detector, s.order, s.fiber, s.slice
+            o.degree, o.K, o.n_lambda, o.n_slit = s.degree, s.K, s.n_lambda, s.n_slit
+            o.lambda_lo, o.lambda_hi = s.lambda_lo, s.lambda_hi
+            o.cx, o.cy, o.slit_weights = cx.ctypes.data_as(dp), cy.ctypes.data_as(dp), u.ctypes.data_as(dp)
+            for p in range(3):
+                o.sigma_x[p] = float(s.sigma_x[p])
+                o.sigma_y[p] = float(s.sigma_y[p])
+            o.theta = float(s.theta)
+        nd = len(model.det_shape)
+        self.h = (C.c_int32 * nd)(*[h for h, w in model.det_shape])
+        self.w = (C.c_int32 * nd)(*[w for h, w in model.det_shape])
+        self.desc = e2e_model_desc(nd, self.h, self.w, n, self.sl, int(model.psf))
+
+
+def e2e_load_model(ctx: int, model: W.OpticalModel) -> int:
+    d = _ModelDesc(model)
+    mid = C.c_uint64()
+    _check(load_library().e2e_load_model(C.c_void_p(ctx), C.byref(d.desc), C.byref(mid)))
+    return mid.value
+
+
+def e2e_unload_model(ctx: int, model_id: int) -> None:
+    _check(load_library().e2e_unload_model(C.c_void_p(ctx), model_id))
+
+
+def e2e_load_spectrum(ctx: int, fiber: int, orders: Sequence[int], fluxes: Sequence[np.ndarray]) -> int:
+    flux = np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.float64) for f in fluxes])
+                                if len(fluxes) else np.zeros(0))
+    n = len(orders)
+    oid = (C.c_int32 * max(n, 1))(*orders)
+    nl = (C.c_int32 * max(n, 1))(*[len(f) for f in fluxes])
+    sid = C.c_uint64()
+    _check(load_library().e2e_load_spectrum(C.c_void_p(ctx), fiber, n, oid, nl,
+                                            flux.ctypes.data_as(C.POINTER(C.c_double)), C.byref(sid)))
+    return sid.value
+
+
+def e2e_unload_spectrum(ctx: int, spec_id: int) -> None:
+    _check(load_library().e2e_unload_spectrum(C.c_void_p(ctx), spec_id))
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def e2e_render(ctx: int, model_id: int, spec_ids: Sequence[int], precision: int, dtype: int,
+               dst_ptrs: Sequence[int], pitch_elems: Optional[Sequence[int]] = None, stream=None) -> None:
+    n = len(spec_ids)
+    sids = (C.c_uint64 * max(n, 1))(*spec_ids)
+    dst = (C.c_void_p * len(dst_ptrs))(*dst_ptrs)
+    pit = None if pitch_elems is None else (C.c_int64 * len(pitch_elems))(*pitch_elems)
+    _check(load_library().e2e_render(C.c_void_p(ctx), model_id, n, sids, precision, dtype, dst, pit,
+                                     C.c_void_p(_stream_handle(stream))))
+
+
+def e2e_render_alloc(ctx: int, model_id: int, spec_ids: Sequence[int], precision: int, dtype: int, stream=None) -> int:
+    n = len(spec_ids)
+    sids = (C.c_uint64 * max(n, 1))(*spec_ids)
+    fid = C.c_uint64()
+    _check(load_library().e2e_render_alloc(C.c_void_p(ctx), model_id, n, sids, precision, dtype,
+                                           C.c_void_p(_stream_handle(stream)), C.byref(fid)))
+    return fid.value
+
+
+def e2e_fetch_frame(ctx: int, frame_id: int, detector: int, dst_ptr: int, dst_is_device: bool, nbytes: int,
+                    stream=None) -> None:
+    _check(load_library().e2e_fetch_frame(C.c_void_p(ctx), frame_id, detector, C.c_void_p(dst_ptr),
+                                          1 if dst_is_device else 0, nbytes, C.c_void_p(_stream_handle(stream))))
+
+
+def e2e_release_frame(ctx: int, frame_id: int) -> None:
+    _check(load_library().e2e_release_frame(C.c_void_p(ctx), frame_id))
+
+
+def e2e_kernel_times(ctx: int, cap: int = 64):
+    """[(kernel name, ms)] of the context's most recent render (needs kernel_timing=1)."""
+    names = (C.c_char_p * cap)()
+    ms = (C.c_float * cap)()
+    n = C.c_int32()
+    _check(load_library().e2e_kernel_times(C.c_void_p(ctx), names, ms, cap, C.byref(n)))
+    return [(names[i].decode(), float(ms[i])) for i in range(min(n.value, cap))]
+
+
+def e2e_model_plan(ctx: int, model_id: int) -> Dict[str, int]:
+    info = e2e_plan_info()
+    _check(load_library().e2e_model_plan(C.c_void_p(ctx), model_id, C.byref(info)))
+    return {name: getattr(info, name) for name, _ in e2e_plan_info._fields_}
+
+
+# ------------------------------------------------------------------ convenience layer
+
+
+class Renderer:
+    """A context on one GPU holding resident models and spectra.
+
+    >>> r = Renderer()
+    >>> mid = r.load_model(workload.model)
+    >>> sids = r.load_spectra(workload)
+    >>> frames = r.render(mid, sids, "mixed", "f32")   # list of torch tensors, one per detector
+    """
+
+    def __init__(self, device: int = 0, pool_bytes: int = 0, max_inflight: int = 0, debug_checks: int = 0,
+                 kernel_timing: int = 0):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("the renderer needs a CUDA GPU; there is no CPU fallback")
+        self.device = device
+        self.ctx = e2e_create(device, pool_bytes, max_inflight, debug_checks, kernel_timing)
+        self.models: Dict[int, W.OpticalModel] = {}
+
+    def close(self):
+        if self.ctx:
+            e2e_destroy(self.ctx)
+            self.ctx = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_model(self, model: W.OpticalModel) -> int:
+        mid = e2e_load_model(self.ctx, model)
+        self.models[mid] = model
+        return mid
+
+    def unload_model(self, mid: int):
+        e2e_unload_model(self.ctx, mid)
+        self.models.pop(mid, None)
+
+    def load_spectrum(self, spectrum: W.Spectrum) -> int:
+        orders = sorted(spectrum.flux)
+        return e2e_load_spectrum(self.ctx, spectrum.fiber, orders, [spectrum.flux[o] for o in orders])
+
+    def load_spectra(self, workload: W.Workload) -> List[int]:
+        return [self.load_spectrum(workload.spectra[f]) for f in sorted(workload.spectra)]
+
+    def plan(self, mid: int) -> Dict[str, int]:
+        return e2e_model_plan(self.ctx, mid)
+
+    def empty_frames(self, mid: int, dtype: str = "f32"):
+        import torch
+
+        td = torch.float32 if dtype == "f32" else torch.float64
+        return [torch.empty((h, w), dtype=td, device=f"cuda:{self.device}") for h, w in self.models[mid].det_shape]
+
+    def render(self, mid: int, spec_ids: Sequence[int], precision: str = "mixed", dtype: str = "f32",
+               out=None, stream=None):
+        if out is None:
+            out = self.empty_frames(mid, dtype)
+        pitches = [int(t.stride(0)) for t in out]
+        e2e_render(self.ctx, mid, spec_ids, PRECISION[precision], DTYPE[dtype], [int(t.data_ptr()) for t in out],
+                   pitches, stream)
+        return out

@@ -1,0 +1,806 @@
+// C ABI and host runtime of the echelle frame renderer: contexts, resident optical models
+// (with their tiled-render plan) and spectra, render jobs, library-owned frames.
+//
+// The spectral-format "database" of the paper (Sec. 2.1) is computed once and reused across
+// simulations; here an optical model is validated, copied to the device and planned once
+// (e2e_load_model), spectra are resident too, and a render only launches kernels.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/e2e_render.h"
+#include "e2e_device.cuh"
+#include "e2e_kernels.h"
+
+using namespace e2e;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? E2E_ENOMEM : E2E_ECUDA;
+}
+
+#define E2E_CK(call)                                       \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
+  } while (0)
+
+struct SliceHost {
+  e2e_order_slice d;
+  std::vector<double> cx, cy, u;
+};
+
+struct Plan {
+  bool ok = false;
+  int B = 1, DX = 0, DY = 0, JB = 1, NB = 8, max_area = 0, max_deg = 0;
+  std::vector<Item> items;  // host copy
+  int64_t store_elems = 0;
+  size_t smem = 0;
+  // device
+  Item* d_items = nullptr;
+  Tile* d_tiles = nullptr;
+  int32_t* d_lists = nullptr;
+  int n_tiles = 0;
+  // items grouped by K (one kernel launch per group)
+  struct Group {
+    int K, first, count;
+  };
+  std::vector<Group> groups;
+};
+
+struct Model {
+  int n_det = 0, psf = 0;
+  std::vector<int> H, W;
+  std::vector<SliceHost> slices;
+  DevSlice* d_slices = nullptr;
+  double* d_u = nullptr;
+  int* d_dims = nullptr;  // [det][2] = (H, W)
+  int64_t max_stamps = 0;
+  std::vector<int> Ks;    // distinct K values
+  Plan plan;
+};
+
+struct Spectrum {
+  int fiber = 0;
+  std::map<int, std::pair<int64_t, int>> rows;  // order -> (offset, n_lambda)
+  double* d_flux = nullptr;
+};
+
+struct Frame {
+  int dtype = 0;
+  std::vector<int> H, W;
+  std::vector<void*> ptrs;
+};
+
+}  // namespace
+
+struct e2e_ctx {
+  int device = 0;
+  e2e_opts opts{};
+  std::mutex mu;
+  uint64_t next_id = 1;
+  std::map<uint64_t, std::unique_ptr<Model>> models;
+  std::map<uint64_t, std::unique_ptr<Spectrum>> spectra;
+  std::map<uint64_t, std::unique_ptr<Frame>> frames;
+  cudaMemPool_t pool = nullptr;
+  // kernel timing of the most recent render (opts.kernel_timing)
+  struct Timed {
+    const char* name;
+    cudaEvent_t a, b;
+  };
+  std::vector<Timed> timed;
+  std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int n_coeffs(int d) { return (d + 1) * (d + 2) / 2; }
+
+bool finite_all(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+// Minimum of c0 + c1 t + c2 t^2 over t in [-1, 1].
+double quad_min(const double* c) {
+  double m = std::min(c[0] - c[1] + c[2], c[0] + c[1] + c[2]);
+  if (c[2] > 0) {
+    double t = -c[1] / (2 * c[2]);
+    if (t > -1 && t < 1) m = std::min(m, c[0] + c[1] * t + c[2] * t * t);
+  }
+  return m;
+}
+
+int validate_slice(const e2e_order_slice& s, int n_det, int psf, int idx) {
+  char buf[256];
+  auto bad = [&](const char* why) {
+    snprintf(buf, sizeof buf, "order-slice %d: %s", idx, why);
+    return fail(E2E_EINVAL, buf);
+  };
+  if (s.detector < 0 || s.detector >= n_det) return bad("detector index out of range");
+  if (s.degree < 0 || s.degree > E2E_MAX_DEGREE) return bad("degree out of range 0..8");
+  if (s.K < 1 || s.K > E2E_MAX_K || s.K % 2 == 0) return bad("K must be odd and in 1..15");
+  if (s.n_lambda < 1 || s.n_slit < 1) return bad("n_lambda and n_slit must be >= 1");
+  if (s.n_slit > 65536 || s.n_lambda > (1 << 28)) return bad("n_lambda or n_slit too large");
+  if (!std::isfinite(s.lambda_lo) || !std::isfinite(s.lambda_hi) || !(s.lambda_hi > s.lambda_lo))
+    return bad("lambda range must be finite with lambda_hi > lambda_lo");
+  if (!s.cx || !s.cy || !s.slit_weights) return bad("null coefficient or weight array");
+  const int nc = n_coeffs(s.degree);
+  if (!finite_all(s.cx, nc) || !finite_all(s.cy, nc)) return bad("non-finite mapping coefficient");
+  if (!finite_all(s.sigma_x, 3) || !finite_all(s.sigma_y, 3)) return bad("non-finite PSF width coefficient");
+  if (quad_min(s.sigma_x) <= 0 || quad_min(s.sigma_y) <= 0) return bad("PSF width must stay > 0 on [-1, 1]");
+  if (!finite_all(s.slit_weights, s.n_slit)) return bad("non-finite slit weight");
+  if (psf == E2E_PSF_ELLIPTICAL && !std::isfinite(s.theta)) return bad("non-finite theta");
+  return E2E_OK;
+}
+
+Model* find_model(e2e_ctx* ctx, uint64_t id) {
+  auto it = ctx->models.find(id);
+  return it == ctx->models.end() ? nullptr : it->second.get();
+}
+
+void free_plan(Plan& p) {
+  cudaFree(p.d_items);
+  cudaFree(p.d_tiles);
+  cudaFree(p.d_lists);
+  p = Plan{};
+}
+
+void free_model(Model* m) {
+  cudaFree(m->d_slices);
+  cudaFree(m->d_u);
+  cudaFree(m->d_dims);
+  free_plan(m->plan);
+}
+
+template <typename T>
+int upload(T** dptr, const T* src, size_t n) {
+  *dptr = nullptr;
+  if (n == 0) return E2E_OK;
+  E2E_CK(cudaMalloc((void**)dptr, n * sizeof(T)));
+  E2E_CK(cudaMemcpy(*dptr, src, n * sizeof(T), cudaMemcpyHostToDevice));
+  return E2E_OK;
+}
+
+// ------------------------------------------------------------------ planning
+
+// Cost (arbitrary units) of a tile variant per stamp: PSF edge evaluations dominate, then
+// the register outer product, then the shared-memory flush amortised over the run.
+double variant_cost(int K, int DX, int DY, int B) {
+  const double edges = (K + DX + 1) + (K + DY + 1);
+  const double tile = (double)(K + DX) * (K + DY);
+  return edges * 50.0 + tile * 1.0 + tile * 15.0 / B;
+}
+
+int plan_model(Model* m) {
+  Plan& P = m->plan;
+  const int ns = (int)m->slices.size();
+  if (m->psf != E2E_PSF_SEPARABLE || ns == 0) {
+    P.ok = (ns == 0);
+    return E2E_OK;
+  }
+  // ---- device pass: exact window origins of every stamp
+  std::vector<int64_t> task_off(ns + 1, 0), jb_off(ns + 1, 0);
+  for (int i = 0; i < ns; ++i) {
+    const auto& s = m->slices[i].d;
+    task_off[i + 1] = task_off[i] + (int64_t)s.n_lambda * ((s.n_slit + 15) / 16);
+    jb_off[i + 1] = jb_off[i] + (s.n_lambda + 31) / 32;
+  }
+  int64_t *d_task_off = nullptr, *d_jb_off = nullptr;
+  int4* d_bbox = nullptr;
+  int* d_spans = nullptr;
+  std::vector<int4> bbox(jb_off[ns], make_int4(1 << 30, -(1 << 30), 1 << 30, -(1 << 30)));
+  std::vector<int> spans(ns * 10, 0);
+  int rc = upload(&d_task_off, task_off.data(), task_off.size());
+  if (rc == E2E_OK) rc = upload(&d_jb_off, jb_off.data(), jb_off.size());
+  if (rc == E2E_OK) rc = upload(&d_bbox, bbox.data(), bbox.size());
+  if (rc == E2E_OK) rc = upload(&d_spans, spans.data(), spans.size());
+  if (rc == E2E_OK) {
+    cudaError_t e = launch_plan(m->d_slices, ns, d_task_off, task_off[ns], d_bbox, d_jb_off, d_spans, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(bbox.data(), d_bbox, bbox.size() * sizeof(int4), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(spans.data(), d_spans, spans.size() * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) rc = cuda_fail(e, "plan kernel");
+  }
+  cudaFree(d_task_off);
+  cudaFree(d_jb_off);
+  cudaFree(d_bbox);
+  cudaFree(d_spans);
+  if (rc != E2E_OK) return rc;
+
+  // ---- tile variant and run length (one for the whole model; per-K kernels)
+  int K = 0;
+  for (auto& s : m->slices) K = std::max(K, s.d.K);
+  double best = 1e300;
+  int bB = 1, bDX = 0, bDY = 0;
+  const int variants[3][2] = {{0, 0}, {1, 1}, {2, 2}};
+  for (int q = 0; q <= 3; ++q) {  // B = 1..8
+    const int B = 1 << q;
+    int sx = 0, sy = 0;
+    for (int i = 0; i < ns; ++i) {
+      sx = std::max(sx, spans[(i * 5 + q) * 2 + 0]);
+      sy = std::max(sy, spans[(i * 5 + q) * 2 + 1]);
+    }
+    for (auto& v : variants) {
+      bool ok = true;
+      for (int k : m->Ks) ok = ok && mixed_variant_supported(k, v[0], v[1]);
+      if (!ok || sx > v[0] || sy > v[1]) continue;
+      const double c = variant_cost(K, v[0], v[1], B);
+      if (c < best) {
+        best = c;
+        bB = B;
+        bDX = v[0];
+        bDY = v[1];
+      }
+    }
+  }
+  P.B = bB;
+  P.DX = bDX;
+  P.DY = bDY;
+  // items: JB 32-sample blocks so that a CTA has >= 8 warp tasks
+  int min_nkb = 1 << 30;
+  for (auto& s : m->slices) min_nkb = std::min(min_nkb, (s.d.n_slit + P.B - 1) / P.B);
+  P.JB = std::max(1, std::min(8, (8 + min_nkb - 1) / min_nkb));
+  P.max_deg = 0;
+  for (auto& s : m->slices) P.max_deg = std::max(P.max_deg, s.d.degree);
+
+  // ---- items grouped by K, boxes clipped to the detector
+  int64_t store = 0;
+  P.items.clear();
+  P.groups.clear();
+  std::vector<int> Ks = m->Ks;
+  for (int Kg : Ks) {
+    Plan::Group g{Kg, (int)P.items.size(), 0};
+    for (int i = 0; i < ns; ++i) {
+      const auto& s = m->slices[i].d;
+      if (s.K != Kg) continue;
+      const int nblk = (s.n_lambda + 31) / 32;
+      for (int b0 = 0; b0 < nblk; b0 += P.JB) {
+        int4 u = make_int4(1 << 30, -(1 << 30), 1 << 30, -(1 << 30));
+        for (int b = b0; b < std::min(nblk, b0 + P.JB); ++b) {
+          const int4 v = bbox[jb_off[i] + b];
+          u.x = std::min(u.x, v.x);
+          u.y = std::max(u.y, v.y);
+          u.z = std::min(u.z, v.z);
+          u.w = std::max(u.w, v.w);
+        }
+        const int Wd = m->W[s.detector], Hd = m->H[s.detector];
+        const int x0 = std::max(u.x, 0), x1 = std::min(u.y, Wd - 1);
+        const int y0 = std::max(u.z, 0), y1 = std::min(u.w, Hd - 1);
+        if (x1 < x0 || y1 < y0) continue;  // every window of the item is off the detector
+        Item it{};
+        it.slice = i;
+        it.j0 = b0 * 32;
+        it.nj = std::min(s.n_lambda, (b0 + P.JB) * 32) - it.j0;
+        it.bx0 = x0;
+        it.by0 = y0;
+        it.bw = x1 - x0 + 1;
+        it.bh = y1 - y0 + 1;
+        it.store_off = store;
+        store += (int64_t)it.bw * it.bh;
+        P.items.push_back(it);
+        g.count++;
+      }
+    }
+    P.groups.push_back(g);
+  }
+  P.store_elems = store;
+  P.max_area = 0;
+  for (auto& it : P.items) P.max_area = std::max(P.max_area, it.bw * it.bh);
+
+  // ---- shared memory: as many per-warp boxes as fit
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  P.NB = 8;
+  while (P.NB >= 1) {
+    P.smem = mixed_smem_bytes(P.max_area, P.NB, P.JB, P.B, P.max_deg + 1);
+    if ((int)P.smem <= optin) break;
+    P.NB /= 2;
+  }
+  if (P.NB < 1)
+    return fail(E2E_EINVAL, "trace footprint of a 32-sample chunk exceeds on-chip memory (area " +
+                                std::to_string(P.max_area) + " px)");
+
+  // ---- merge tiles: every tile of every detector, with the items overlapping it
+  std::vector<Tile> tiles;
+  std::vector<std::vector<int32_t>> lists;
+  std::vector<int> tile_base(m->n_det + 1, 0);
+  std::vector<int> ntx(m->n_det), nty(m->n_det);
+  for (int d = 0; d < m->n_det; ++d) {
+    ntx[d] = (m->W[d] + kTileW - 1) / kTileW;
+    nty[d] = (m->H[d] + kTileH - 1) / kTileH;
+    tile_base[d + 1] = tile_base[d] + ntx[d] * nty[d];
+  }
+  lists.resize(tile_base[m->n_det]);
+  for (size_t n = 0; n < P.items.size(); ++n) {
+    const Item& it = P.items[n];
+    const int d = m->slices[it.slice].d.detector;
+    for (int ty = it.by0 / kTileH; ty <= (it.by0 + it.bh - 1) / kTileH; ++ty)
+      for (int tx = it.bx0 / kTileW; tx <= (it.bx0 + it.bw - 1) / kTileW; ++tx)
+        lists[tile_base[d] + ty * ntx[d] + tx].push_back((int32_t)n);
+  }
+  std::vector<int32_t> flat;
+  for (int d = 0; d < m->n_det; ++d)
+    for (int ty = 0; ty < nty[d]; ++ty)
+      for (int tx = 0; tx < ntx[d]; ++tx) {
+        const auto& l = lists[tile_base[d] + ty * ntx[d] + tx];
+        Tile t{d, tx * kTileW, ty * kTileH, (int)l.size(), (int64_t)flat.size()};
+        flat.insert(flat.end(), l.begin(), l.end());
+        tiles.push_back(t);
+      }
+  P.n_tiles = (int)tiles.size();
+  rc = upload(&P.d_items, P.items.data(), P.items.size());
+  if (rc == E2E_OK) rc = upload(&P.d_tiles, tiles.data(), tiles.size());
+  if (rc == E2E_OK) rc = upload(&P.d_lists, flat.data(), flat.size());
+  if (rc != E2E_OK) return rc;
+  P.ok = true;
+  return E2E_OK;
+}
+
+// ------------------------------------------------------------------ render
+
+// Bracket one kernel launch with events when the context records kernel timings.
+struct KernelTimer {
+  e2e_ctx* ctx;
+  cudaStream_t st;
+  size_t idx = (size_t)-1;
+  KernelTimer(e2e_ctx* c, cudaStream_t s, const char* name) : ctx(c), st(s) {
+    if (!ctx->opts.kernel_timing) return;
+    e2e_ctx::Timed t{name, nullptr, nullptr};
+    for (cudaEvent_t* e : {&t.a, &t.b}) {
+      if (!ctx->event_pool.empty()) {
+        *e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+      } else if (cudaEventCreate(e) != cudaSuccess) {
+        return;
+      }
+    }
+    cudaEventRecord(t.a, st);
+    idx = ctx->timed.size();
+    ctx->timed.push_back(t);
+  }
+  ~KernelTimer() {
+    if (idx != (size_t)-1) cudaEventRecord(ctx->timed[idx].b, st);
+  }
+};
+
+void reset_timing(e2e_ctx* ctx) {
+  for (auto& t : ctx->timed) {
+    ctx->event_pool.push_back(t.a);
+    ctx->event_pool.push_back(t.b);
+  }
+  ctx->timed.clear();
+}
+
+struct Scratch {
+  std::vector<void*> blocks;
+  cudaStream_t st;
+  ~Scratch() {
+    for (void* p : blocks) cudaFreeAsync(p, st);
+  }
+  cudaError_t get(void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return cudaSuccess;
+    cudaError_t e = cudaMallocAsync(p, bytes, st);
+    if (e == cudaSuccess) blocks.push_back(*p);
+    return e;
+  }
+};
+
+int resolve_flux(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, std::vector<const double*>& table) {
+  std::map<int, Spectrum*> byfiber;
+  if (n_spec < 0 || (n_spec > 0 && !spec_ids)) return fail(E2E_EINVAL, "bad spectrum list");
+  for (int i = 0; i < n_spec; ++i) {
+    auto it = ctx->spectra.find(spec_ids[i]);
+    if (it == ctx->spectra.end()) return fail(E2E_ENOTFOUND, "unknown spectrum id");
+    if (byfiber.count(it->second->fiber)) return fail(E2E_EINVAL, "two spectra for one fiber");
+    byfiber[it->second->fiber] = it->second.get();
+  }
+  table.resize(m->slices.size());
+  for (size_t i = 0; i < m->slices.size(); ++i) {
+    const auto& s = m->slices[i].d;
+    auto f = byfiber.find(s.fiber);
+    if (f == byfiber.end()) return fail(E2E_EINVAL, "no spectrum for fiber " + std::to_string(s.fiber));
+    auto r = f->second->rows.find(s.order);
+    if (r == f->second->rows.end())
+      return fail(E2E_EINVAL, "spectrum of fiber " + std::to_string(s.fiber) + " lacks order " + std::to_string(s.order));
+    if (r->second.second != s.n_lambda)
+      return fail(E2E_EINVAL, "spectrum length differs from n_lambda for order " + std::to_string(s.order));
+    table[i] = f->second->d_flux + r->second.first;
+  }
+  return E2E_OK;
+}
+
+int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, int precision, int dtype,
+                void* const* dst, const int64_t* pitch_in, cudaStream_t st) {
+  if (dtype != E2E_F32 && dtype != E2E_F64) return fail(E2E_EINVAL, "dtype must be E2E_F32 or E2E_F64");
+  if (precision != E2E_PREC_MIXED && precision != E2E_PREC_FP64) return fail(E2E_EINVAL, "bad precision");
+  if (!dst) return fail(E2E_EINVAL, "null destination list");
+  std::vector<int64_t> pitch(m->n_det);
+  for (int d = 0; d < m->n_det; ++d) {
+    if (!dst[d]) return fail(E2E_EINVAL, "null destination frame");
+    pitch[d] = pitch_in ? pitch_in[d] : m->W[d];
+    if (pitch[d] < m->W[d]) return fail(E2E_EINVAL, "pitch smaller than width");
+  }
+  std::vector<const double*> table;
+  int rc = resolve_flux(ctx, m, n_spec, spec_ids, table);
+  if (rc != E2E_OK) return rc;
+  if (m->psf != E2E_PSF_SEPARABLE) return fail(E2E_EINVAL, "elliptical PSF render not available in this build");
+
+  if (ctx->opts.kernel_timing) reset_timing(ctx);
+  Scratch sc{{}, st};
+  const double** d_table = nullptr;
+  int64_t* d_pitch = nullptr;
+  void** d_dst = nullptr;
+  E2E_CK(sc.get((void**)&d_table, table.size() * sizeof(double*)));
+  E2E_CK(sc.get((void**)&d_pitch, pitch.size() * sizeof(int64_t)));
+  E2E_CK(sc.get((void**)&d_dst, m->n_det * sizeof(void*)));
+  E2E_CK(cudaMemcpyAsync(d_table, table.data(), table.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
+  E2E_CK(cudaMemcpyAsync(d_pitch, pitch.data(), pitch.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  E2E_CK(cudaMemcpyAsync(d_dst, dst, m->n_det * sizeof(void*), cudaMemcpyHostToDevice, st));
+
+  if (precision == E2E_PREC_FP64) {
+    // accumulate in FP64: straight into an FP64 destination, else into scratch + convert
+    std::vector<double*> acc(m->n_det);
+    std::vector<int64_t> apitch(m->n_det);
+    for (int d = 0; d < m->n_det; ++d) {
+      if (dtype == E2E_F64) {
+        acc[d] = (double*)dst[d];
+        apitch[d] = pitch[d];
+        E2E_CK(cudaMemset2DAsync(acc[d], pitch[d] * 8, 0, (size_t)m->W[d] * 8, m->H[d], st));
+      } else {
+        E2E_CK(sc.get((void**)&acc[d], (size_t)m->H[d] * m->W[d] * 8));
+        apitch[d] = m->W[d];
+        E2E_CK(cudaMemsetAsync(acc[d], 0, (size_t)m->H[d] * m->W[d] * 8, st));
+      }
+    }
+    double** d_acc = nullptr;
+    int64_t* d_apitch = nullptr;
+    E2E_CK(sc.get((void**)&d_acc, acc.size() * sizeof(double*)));
+    E2E_CK(sc.get((void**)&d_apitch, apitch.size() * sizeof(int64_t)));
+    E2E_CK(cudaMemcpyAsync(d_acc, acc.data(), acc.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
+    E2E_CK(cudaMemcpyAsync(d_apitch, apitch.data(), apitch.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    for (int K : m->Ks) {
+      // one launch per K over all slices; slices of another K exit at once
+      KernelTimer kt(ctx, st, "render_fp64");
+      E2E_CK(launch_render_fp64(K, (int)m->slices.size(), m->max_stamps, m->d_slices, d_table, m->d_u, d_acc,
+                                d_apitch, st));
+    }
+    if (dtype == E2E_F32)
+      for (int d = 0; d < m->n_det; ++d) {
+        KernelTimer kt(ctx, st, "convert");
+        E2E_CK(launch_convert(acc[d], apitch[d], dst[d], dtype, pitch[d], m->H[d], m->W[d], st));
+      }
+    return E2E_OK;
+  }
+
+  // mixed precision
+  Plan& P = m->plan;
+  if (!P.ok) return fail(E2E_EINVAL, "model has no mixed-precision plan");
+  double* store = nullptr;
+  E2E_CK(sc.get((void**)&store, (size_t)P.store_elems * 8));
+  for (auto& g : P.groups) {
+    KernelTimer kt(ctx, st, "render_mixed");
+    E2E_CK(launch_render_mixed(g.K, P.DX, P.DY, m->d_slices, d_table, m->d_u, P.d_items + g.first, g.count, store,
+                               P.B, P.JB, P.NB, P.max_deg, P.smem, st));
+  }
+  {
+    KernelTimer kt(ctx, st, "merge");
+    E2E_CK(launch_merge(P.d_tiles, P.n_tiles, P.d_lists, P.d_items, store, d_dst, dtype, d_pitch, m->d_dims, st));
+  }
+  return E2E_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+const char* e2e_last_error(void) { return g_err.c_str(); }
+
+int e2e_create(e2e_ctx** out, int32_t device, const e2e_opts* opts) {
+  if (!out) return fail(E2E_EINVAL, "null output pointer");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= n) return fail(E2E_EINVAL, "no such CUDA device");
+  DeviceGuard g(device);
+  auto* c = new (std::nothrow) e2e_ctx;
+  if (!c) return fail(E2E_ENOMEM, "host allocation failed");
+  c->device = device;
+  if (opts) c->opts = *opts;
+  if (c->opts.max_inflight <= 0) c->opts.max_inflight = 4;
+  // keep freed scratch in the stream-ordered pool instead of returning it to the driver
+  if (cudaDeviceGetDefaultMemPool(&c->pool, device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  *out = c;
+  return E2E_OK;
+}
+
+void e2e_destroy(e2e_ctx* ctx) {
+  if (!ctx) return;
+  {
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    for (auto& kv : ctx->models) free_model(kv.second.get());
+    for (auto& kv : ctx->spectra) cudaFree(kv.second->d_flux);
+    for (auto& kv : ctx->frames)
+      for (void* p : kv.second->ptrs) cudaFree(p);
+    reset_timing(ctx);
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+  }
+  delete ctx;
+}
+
+int e2e_load_model(e2e_ctx* ctx, const e2e_model_desc* desc, uint64_t* model_id) {
+  if (!ctx || !desc || !model_id) return fail(E2E_EINVAL, "null argument");
+  if (desc->n_detectors < 1 || !desc->height || !desc->width) return fail(E2E_EINVAL, "need >= 1 detector");
+  if (desc->n_slices < 0 || (desc->n_slices > 0 && !desc->slices)) return fail(E2E_EINVAL, "bad slice list");
+  if (desc->psf != E2E_PSF_SEPARABLE && desc->psf != E2E_PSF_ELLIPTICAL) return fail(E2E_EINVAL, "bad psf kind");
+  for (int d = 0; d < desc->n_detectors; ++d)
+    if (desc->height[d] < 1 || desc->width[d] < 1 || desc->height[d] > 16000 || desc->width[d] > 16000)
+      return fail(E2E_EINVAL, "detector size must be 1..16000 px");
+  for (int i = 0; i < desc->n_slices; ++i) {
+    int rc = validate_slice(desc->slices[i], desc->n_detectors, desc->psf, i);
+    if (rc != E2E_OK) return rc;
+  }
+  DeviceGuard g(ctx->device);
+  auto m = std::make_unique<Model>();
+  m->n_det = desc->n_detectors;
+  m->psf = desc->psf;
+  m->H.assign(desc->height, desc->height + m->n_det);
+  m->W.assign(desc->width, desc->width + m->n_det);
+  std::vector<DevSlice> ds(desc->n_slices);
+  std::vector<double> u_all;
+  for (int i = 0; i < desc->n_slices; ++i) {
+    const auto& s = desc->slices[i];
+    SliceHost h;
+    h.d = s;
+    const int nc = n_coeffs(s.degree);
+    h.cx.assign(s.cx, s.cx + nc);
+    h.cy.assign(s.cy, s.cy + nc);
+    h.u.assign(s.slit_weights, s.slit_weights + s.n_slit);
+    h.d.cx = h.cx.data();
+    h.d.cy = h.cy.data();
+    h.d.slit_weights = h.u.data();
+    DevSlice& v = ds[i];
+    memset(&v, 0, sizeof v);
+    for (int c = 0; c < nc; ++c) {
+      v.cx[c] = s.cx[c];
+      v.cy[c] = s.cy[c];
+    }
+    for (int c = 0; c < 3; ++c) {
+      v.sx[c] = s.sigma_x[c];
+      v.sy[c] = s.sigma_y[c];
+    }
+    v.dlam = (s.lambda_hi - s.lambda_lo) / s.n_lambda;
+    v.cos_t = std::cos(s.theta);
+    v.sin_t = std::sin(s.theta);
+    v.degree = s.degree;
+    v.K = s.K;
+    v.n_lambda = s.n_lambda;
+    v.n_slit = s.n_slit;
+    v.det = s.detector;
+    v.H = m->H[s.detector];
+    v.W = m->W[s.detector];
+    v.flux_slot = i;
+    v.u_off = (int64_t)u_all.size();
+    u_all.insert(u_all.end(), s.slit_weights, s.slit_weights + s.n_slit);
+    m->max_stamps = std::max(m->max_stamps, (int64_t)s.n_lambda * s.n_slit);
+    if (std::find(m->Ks.begin(), m->Ks.end(), s.K) == m->Ks.end()) m->Ks.push_back(s.K);
+    m->slices.push_back(std::move(h));
+  }
+  std::sort(m->Ks.begin(), m->Ks.end());
+  std::vector<int> dims(2 * m->n_det);
+  for (int d = 0; d < m->n_det; ++d) {
+    dims[2 * d] = m->H[d];
+    dims[2 * d + 1] = m->W[d];
+  }
+  int rc = upload(&m->d_slices, ds.data(), ds.size());
+  if (rc == E2E_OK) rc = upload(&m->d_u, u_all.data(), u_all.size());
+  if (rc == E2E_OK) rc = upload(&m->d_dims, dims.data(), dims.size());
+  if (rc == E2E_OK) rc = plan_model(m.get());
+  if (rc != E2E_OK) {
+    std::string keep = g_err;
+    free_model(m.get());
+    g_err = keep;
+    return rc;
+  }
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  *model_id = ctx->next_id++;
+  ctx->models[*model_id] = std::move(m);
+  return E2E_OK;
+}
+
+int e2e_unload_model(e2e_ctx* ctx, uint64_t model_id) {
+  if (!ctx) return fail(E2E_EINVAL, "null context");
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->models.find(model_id);
+  if (it == ctx->models.end()) return fail(E2E_ENOTFOUND, "unknown model id");
+  cudaDeviceSynchronize();
+  free_model(it->second.get());
+  ctx->models.erase(it);
+  return E2E_OK;
+}
+
+int e2e_load_spectrum(e2e_ctx* ctx, int32_t fiber, int32_t n_orders, const int32_t* order_ids,
+                      const int32_t* n_lambda, const double* flux, uint64_t* spec_id) {
+  if (!ctx || !spec_id || n_orders < 0 || (n_orders > 0 && (!order_ids || !n_lambda || !flux)))
+    return fail(E2E_EINVAL, "null or negative argument");
+  auto sp = std::make_unique<Spectrum>();
+  sp->fiber = fiber;
+  int64_t total = 0;
+  for (int i = 0; i < n_orders; ++i) {
+    if (n_lambda[i] < 1) return fail(E2E_EINVAL, "n_lambda must be >= 1");
+    if (sp->rows.count(order_ids[i])) return fail(E2E_EINVAL, "duplicate order in spectrum");
+    sp->rows[order_ids[i]] = {total, n_lambda[i]};
+    total += n_lambda[i];
+  }
+  if (!finite_all(flux, (size_t)total)) return fail(E2E_EINVAL, "non-finite flux");
+  DeviceGuard g(ctx->device);
+  int rc = upload(&sp->d_flux, flux, (size_t)total);
+  if (rc != E2E_OK) return rc;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  *spec_id = ctx->next_id++;
+  ctx->spectra[*spec_id] = std::move(sp);
+  return E2E_OK;
+}
+
+int e2e_unload_spectrum(e2e_ctx* ctx, uint64_t spec_id) {
+  if (!ctx) return fail(E2E_EINVAL, "null context");
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->spectra.find(spec_id);
+  if (it == ctx->spectra.end()) return fail(E2E_ENOTFOUND, "unknown spectrum id");
+  cudaDeviceSynchronize();
+  cudaFree(it->second->d_flux);
+  ctx->spectra.erase(it);
+  return E2E_OK;
+}
+
+int e2e_render(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids, int32_t precision,
+               int32_t dtype, void* const* dst, const int64_t* pitch_elems, void* stream) {
+  if (!ctx) return fail(E2E_EINVAL, "null context");
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Model* m = find_model(ctx, model_id);
+  if (!m) return fail(E2E_ENOTFOUND, "unknown model id");
+  return render_impl(ctx, m, n_spec, spec_ids, precision, dtype, dst, pitch_elems, (cudaStream_t)stream);
+}
+
+int e2e_render_alloc(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids, int32_t precision,
+                     int32_t dtype, void* stream, uint64_t* frame_id) {
+  if (!ctx || !frame_id) return fail(E2E_EINVAL, "null argument");
+  if (dtype != E2E_F32 && dtype != E2E_F64) return fail(E2E_EINVAL, "dtype must be E2E_F32 or E2E_F64");
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Model* m = find_model(ctx, model_id);
+  if (!m) return fail(E2E_ENOTFOUND, "unknown model id");
+  auto f = std::make_unique<Frame>();
+  f->dtype = dtype;
+  f->H = m->H;
+  f->W = m->W;
+  const size_t es = dtype == E2E_F32 ? 4 : 8;
+  for (int d = 0; d < m->n_det; ++d) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, (size_t)m->H[d] * m->W[d] * es);
+    if (e != cudaSuccess) {
+      for (void* q : f->ptrs) cudaFree(q);
+      return cuda_fail(e, "frame allocation");
+    }
+    f->ptrs.push_back(p);
+  }
+  int rc = render_impl(ctx, m, n_spec, spec_ids, precision, dtype, f->ptrs.data(), nullptr, (cudaStream_t)stream);
+  if (rc != E2E_OK) {
+    cudaStreamSynchronize((cudaStream_t)stream);
+    for (void* q : f->ptrs) cudaFree(q);
+    return rc;
+  }
+  *frame_id = ctx->next_id++;
+  ctx->frames[*frame_id] = std::move(f);
+  return E2E_OK;
+}
+
+int e2e_fetch_frame(e2e_ctx* ctx, uint64_t frame_id, int32_t detector, void* dst, int32_t dst_is_device, size_t bytes,
+                    void* stream) {
+  if (!ctx || !dst) return fail(E2E_EINVAL, "null argument");
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->frames.find(frame_id);
+  if (it == ctx->frames.end()) return fail(E2E_ENOTFOUND, "unknown frame id");
+  Frame* f = it->second.get();
+  if (detector < 0 || detector >= (int)f->ptrs.size()) return fail(E2E_EINVAL, "detector out of range");
+  const size_t need = (size_t)f->H[detector] * f->W[detector] * (f->dtype == E2E_F32 ? 4 : 8);
+  if (bytes != need) return fail(E2E_EINVAL, "byte count differs from the frame size");
+  E2E_CK(cudaMemcpyAsync(dst, f->ptrs[detector], bytes, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                         (cudaStream_t)stream));
+  return E2E_OK;
+}
+
+int e2e_release_frame(e2e_ctx* ctx, uint64_t frame_id) {
+  if (!ctx) return fail(E2E_EINVAL, "null context");
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->frames.find(frame_id);
+  if (it == ctx->frames.end()) return fail(E2E_ENOTFOUND, "unknown frame id");
+  cudaDeviceSynchronize();
+  for (void* p : it->second->ptrs) cudaFree(p);
+  ctx->frames.erase(it);
+  return E2E_OK;
+}
+
+int e2e_model_plan(e2e_ctx* ctx, uint64_t model_id, e2e_plan_info* info) {
+  if (!ctx || !info) return fail(E2E_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Model* m = find_model(ctx, model_id);
+  if (!m) return fail(E2E_ENOTFOUND, "unknown model id");
+  const Plan& P = m->plan;
+  memset(info, 0, sizeof *info);
+  info->chunk_lambda = 32 * P.JB;
+  info->run_slit = P.B;
+  info->slack_x = P.DX;
+  info->slack_y = P.DY;
+  info->n_items = (int64_t)P.items.size();
+  info->n_tiles = P.n_tiles;
+  info->scratch_bytes = P.store_elems * 8;
+  info->tile_w = kTileW;
+  info->tile_h = kTileH;
+  info->boxes_per_cta = P.NB;
+  info->max_box_area = P.max_area;
+  return E2E_OK;
+}
+
+int e2e_kernel_times(e2e_ctx* ctx, const char** names, float* ms, int32_t cap, int32_t* n) {
+  if (!ctx || !n) return fail(E2E_EINVAL, "null argument");
+  if (!ctx->opts.kernel_timing) return fail(E2E_EINVAL, "context was created without kernel_timing");
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  *n = (int32_t)ctx->timed.size();
+  for (int32_t i = 0; i < *n && i < cap; ++i) {
+    E2E_CK(cudaEventSynchronize(ctx->timed[i].b));
+    float t = 0.f;
+    E2E_CK(cudaEventElapsedTime(&t, ctx->timed[i].a, ctx->timed[i].b));
+    if (names) names[i] = ctx->timed[i].name;
+    if (ms) ms[i] = t;
+  }
+  return E2E_OK;
+}
+
+}  // extern "C"

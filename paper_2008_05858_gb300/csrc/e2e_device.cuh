@@ -1,0 +1,82 @@
+// Device-side data layout and inline math shared by the renderer's kernels.
+//
+// The model of the paper's image simulator (Sec. 2.2): the frame is the superposition,
+// over a wavelength grid, of pixel-integrated fiber images; the fiber image of one
+// wavelength sample is a set of slit points, each a PSF "stamp" centred where the
+// spectral-format polynomial maps (lambda, s), weighted by flux x bin width x the
+// normalised slit illumination (Sec. 2.1).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define E2E_MAXC 45  // (8+1)(8+2)/2 coefficients for total degree 8
+
+namespace e2e {
+
+// One order-slice as the kernels read it (copied once per model; __ldg'd).
+struct DevSlice {
+  double cx[E2E_MAXC];  // x(lt, s) coefficients, index(a,b) = t(t+1)/2 + b
+  double cy[E2E_MAXC];
+  double sx[3], sy[3];  // PSF width quadratics in lt (px)
+  double dlam;          // wavelength bin width (lambda_hi - lambda_lo) / n_lambda
+  double cos_t, sin_t;  // elliptical PSF axis rotation
+  int32_t degree, K, n_lambda, n_slit;
+  int32_t det, H, W, flux_slot;  // detector, its size, index into the per-render flux table
+  int64_t u_off;                 // offset of this slice's slit weights in the model's weight array
+  int64_t stamp_off;             // first global stamp index of this slice (FP64 path)
+};
+
+// A mixed-path work item: wavelength samples [j0, j0+nj) of one slice, every slit point;
+// its stamps' windows are clipped to the detector and bounded by box (bx0, by0, bw, bh).
+struct Item {
+  int32_t slice, j0, nj, pad;
+  int32_t bx0, by0, bw, bh;
+  int64_t store_off;  // offset (elements) of this item's box in the render's box store
+};
+
+// Output tile of the merge: tile (tx, ty) of detector det lists items[list_off .. list_off+n).
+struct Tile {
+  int32_t det, x0, y0, n;
+  int64_t list_off;
+};
+
+__host__ __device__ inline int coeff_index(int a, int b) {
+  int t = a + b;
+  return t * (t + 1) / 2 + b;
+}
+
+// Normalised wavelength of bin-centred sample j of n: lt = (2j + 1 - n) / n in [-1, 1].
+// Numerator and denominator are exact in FP64, so this is correctly rounded.
+__device__ __forceinline__ double norm_sample(int j, int n) { return (double)(2 * j + 1 - n) / (double)n; }
+
+// Per-wavelength-sample coefficients of the polynomial in s: P_b(lt) = sum_a c_ab lt^a
+// (Horner in lt), b = 0..d.  x(lt, s) is then sum_b P_b s^b.
+__device__ __forceinline__ double poly_lt_for_b(const double* c, int degree, int b, double lt) {
+  double p = 0.0;
+  for (int a = degree - b; a >= 0; --a) p = fma(p, lt, c[coeff_index(a, b)]);
+  return p;
+}
+
+// Split an FP64 pixel coordinate into the window-centre pixel floor(v + 1/2) and the
+// offset v - that pixel in [-1/2, 1/2) as FP32, using integer operations on the bits of
+// v + 1.5*2^16 (one FP64 add): the sum has a fixed exponent, so its low 52 mantissa bits
+// are (v + 2^15) in fixed point with 36 fractional bits.  Valid for |v| < 2^15 (callers
+// clamp); the offset keeps 32 fractional bits before rounding to FP32.
+__device__ __forceinline__ void split_coord(double v, int& c, float& f) {
+  const double magic = 98304.0;  // 1.5 * 2^16
+  double t = v + magic;
+  unsigned long long bits = (unsigned long long)__double_as_longlong(t);
+  unsigned long long m = bits & 0xFFFFFFFFFFFFFull;  // (v + 2^15) * 2^36
+  m += (1ull << 35);                                   // + 1/2 pixel
+  c = (int)(m >> 36) - 32768;
+  long long frac = (long long)(m & 0xFFFFFFFFFull) - (1ll << 35);  // in [-2^35, 2^35)
+  f = (float)(int)(frac >> 4) * 2.3283064365386963e-10f;           // * 2^-32
+}
+
+// Clamp a mapped coordinate into the range split_coord handles (far off-frame stamps
+// are dropped anyway; the clamp keeps their windows off-frame).
+__device__ __forceinline__ double clamp_coord(double v) {
+  return fmin(fmax(v, -16000.0), 16000.0);
+}
+
+}  // namespace e2e

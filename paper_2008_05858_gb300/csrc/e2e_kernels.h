@@ -1,0 +1,30 @@
+// Host-callable launchers of the renderer's kernels (internal to the library).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "e2e_device.cuh"
+
+namespace e2e {
+
+constexpr int kTileW = 64;  // merge tile (pixels); 256 threads x 8 pixels
+constexpr int kTileH = 32;
+
+cudaError_t launch_render_fp64(int K, int n_slices, int64_t max_stamps, const DevSlice* slices,
+                               const double* const* flux_tab, const double* u_all, double* const* acc,
+                               const int64_t* pitch, cudaStream_t st);
+cudaError_t launch_convert(const double* src, int64_t src_pitch, void* dst, int dtype, int64_t dst_pitch, int H,
+                           int W, cudaStream_t st);
+
+cudaError_t launch_plan(const DevSlice* slices, int n_slices, const int64_t* task_off, int64_t n_tasks,
+                        int4* jblock_bbox, const int64_t* jblock_off, int* spans, cudaStream_t st);
+bool mixed_variant_supported(int K, int DX, int DY);
+size_t mixed_smem_bytes(int area, int NB, int JB, int B, int nd);
+cudaError_t launch_render_mixed(int K, int DX, int DY, const DevSlice* slices, const double* const* flux_tab,
+                                const double* u_all, const Item* items, int n_items, double* store, int B, int JB,
+                                int NB, int max_deg, size_t smem, cudaStream_t st);
+cudaError_t launch_merge(const Tile* tiles, int n_tiles, const int32_t* lists, const Item* items, const double* store,
+                         void* const* dst, int dtype, const int64_t* pitch, const int* dims, cudaStream_t st);
+
+}  // namespace e2e

@@ -1,0 +1,223 @@
+"""GPU renderer vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerance (spec fidelity target): relative per-pixel error below 1e-6 (with an
+absolute floor of 1e-10 of the frame peak, see framecompare) and photocenter shifts of
+16x16 px windows below 1e-5 px.  The plain FP64 renderer must agree to 1e-12.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2008_05858_gb300 import workloads as W
+from tests.framecompare import compare
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+_ORACLE = {}
+
+
+def oracle_frames(w):
+    key = id(w)
+    if key not in _ORACLE:
+        _ORACLE[key] = oracle.render_workload(w)
+    return _ORACLE[key]
+
+
+@pytest.fixture(scope="module")
+def renderer():
+    from paper_2008_05858_gb300.binding import Renderer
+
+    r = Renderer(0)
+    yield r
+    r.close()
+
+
+def gpu_frames(r, w, precision, dtype):
+    mid = r.load_model(w.model)
+    sids = r.load_spectra(w)
+    out = r.render(mid, sids, precision, dtype)
+    torch.cuda.synchronize()
+    res = [t.double().cpu().numpy() for t in out]
+    for s in sids:
+        from paper_2008_05858_gb300.binding import e2e_unload_spectrum
+
+        e2e_unload_spectrum(r.ctx, s)
+    r.unload_model(mid)
+    return res
+
+
+SMALL = [
+    dict(seed=7),
+    dict(seed=8, K=7, degree=3, n_lambda=257, n_slit=16),
+    dict(seed=9, K=9, degree=4, n_lambda=100, n_slit=33, width=180, height=120),
+    dict(seed=10, K=5, degree=2, n_lambda=1000, n_slit=3, orders=3),
+    dict(seed=11, K=13, degree=5, n_lambda=77, n_slit=64),
+    dict(seed=12, K=3, degree=1, n_lambda=64, n_slit=5),
+    dict(seed=13, K=1, degree=0, n_lambda=31, n_slit=2),
+    dict(seed=14, K=15, degree=5, n_lambda=60, n_slit=7, width=400, height=200),
+    dict(seed=15, K=11, degree=5, n_lambda=2000, n_slit=128, orders=1, fibers=1, slices=1, width=512, height=64),
+]
+
+
+@pytest.mark.parametrize("kw", SMALL, ids=[f"s{k['seed']}" for k in SMALL])
+def test_mixed_matches_oracle_small(renderer, kw):
+    w = W.small_config(**kw)
+    ref = oracle_frames(w)
+    got = gpu_frames(renderer, w, "mixed", "f32")
+    for g, o in zip(got, ref):
+        rep = compare(g, o)
+        assert rep.ok, str(rep)
+
+
+@pytest.mark.parametrize("kw", SMALL[:4], ids=[f"s{k['seed']}" for k in SMALL[:4]])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_fp64_matches_oracle_small(renderer, kw, dtype):
+    w = W.small_config(**kw)
+    ref = oracle_frames(w)
+    got = gpu_frames(renderer, w, "fp64", dtype)
+    for g, o in zip(got, ref):
+        if dtype == "f64":
+            peak = np.abs(o).max()
+            assert np.all(np.abs(g - o) <= 1e-12 * np.abs(o) + 1e-15 * peak)
+        else:
+            assert compare(g, o, rel=1.2e-7, floor=1e-12).ok
+
+
+def test_mixed_f64_output_matches_oracle(renderer):
+    w = W.small_config(seed=21)
+    ref = oracle_frames(w)
+    got = gpu_frames(renderer, w, "mixed", "f64")
+    assert compare(got[0], ref[0]).ok
+
+
+def test_config1_fp64_full(renderer):
+    w = W.config1()
+    ref = oracle_frames(w)
+    got = gpu_frames(renderer, w, "fp64", "f64")
+    peak = np.abs(ref[0]).max()
+    assert np.all(np.abs(got[0] - ref[0]) <= 1e-12 * np.abs(ref[0]) + 1e-15 * peak)
+    assert compare(gpu_frames(renderer, w, "mixed", "f64")[0], ref[0]).ok
+
+
+def test_config5_mixed_full(renderer):
+    w = W.config5()
+    ref = oracle_frames(w)
+    got = gpu_frames(renderer, w, "mixed", "f32")
+    rep = compare(got[0], ref[0])
+    assert rep.ok, str(rep)
+
+
+def test_config2_reduced_orders(renderer):
+    w = W.config2(n_orders=6, size=9216)
+    ref = oracle_frames(w)
+    got = gpu_frames(renderer, w, "mixed", "f32")
+    rep = compare(got[0], ref[0])
+    assert rep.ok, str(rep)
+
+
+def test_multi_detector_and_empty_detector(renderer):
+    w = W.small_config(seed=31, n_detectors=3)
+    # detector 2 gets no slices at all: must come back all zeros
+    w.model.slices = [s for s in w.model.slices if s.detector != 2]
+    ref = oracle_frames(w)
+    got = gpu_frames(renderer, w, "mixed", "f32")
+    for g, o in zip(got, ref):
+        assert compare(g, o).ok
+    assert not got[2].any()
+
+
+def test_model_without_slices_renders_zeros(renderer):
+    m = W.OpticalModel([(40, 50)], [])
+    mid = renderer.load_model(m)
+    out = renderer.render(mid, [], "mixed", "f32")
+    torch.cuda.synchronize()
+    assert not out[0].any().item()
+    renderer.unload_model(mid)
+
+
+def test_trace_entirely_off_frame(renderer):
+    w = W.small_config(seed=41)
+    for s in w.model.slices:
+        s.cy[0] += 10000.0
+    got = gpu_frames(renderer, w, "mixed", "f32")
+    assert not np.any(got[0])
+
+
+def test_pitched_destination(renderer):
+    w = W.small_config(seed=51)
+    ref = oracle_frames(w)[0]
+    mid = renderer.load_model(w.model)
+    sids = renderer.load_spectra(w)
+    h, wd = w.model.det_shape[0]
+    big = torch.full((h, wd + 37), -1.0, dtype=torch.float32, device="cuda")
+    view = big[:, :wd]
+    renderer.render(mid, sids, "mixed", "f32", out=[view])
+    torch.cuda.synchronize()
+    assert compare(view.double().cpu().numpy(), ref).ok
+    assert torch.all(big[:, wd:] == -1.0).item()
+
+
+def test_render_is_deterministic(renderer):
+    w = W.small_config(seed=61, n_lambda=500, n_slit=32)
+    a = gpu_frames(renderer, w, "mixed", "f32")[0]
+    b = gpu_frames(renderer, w, "mixed", "f32")[0]
+    assert np.array_equal(a, b)
+
+
+def test_linearity_in_the_spectrum(renderer):
+    w = W.small_config(seed=71)
+    w2 = W.small_config(seed=71)
+    for f in w2.spectra:
+        for o in w2.spectra[f].flux:
+            w2.spectra[f].flux[o] = w2.spectra[f].flux[o] * 2.5
+    a = gpu_frames(renderer, w, "mixed", "f64")[0]
+    b = gpu_frames(renderer, w2, "mixed", "f64")[0]
+    assert np.allclose(b, 2.5 * a, rtol=2e-6, atol=1e-10 * np.abs(b).max())
+
+
+@pytest.mark.parametrize("mutate,msg", [
+    (lambda s: setattr(s, "K", 8), "odd"),
+    (lambda s: s.cx.__setitem__(1, float("nan")), "non-finite"),
+    (lambda s: setattr(s, "sigma_x", np.array([-0.5, 0.0, 0.0])), "width"),
+    (lambda s: setattr(s, "degree", 9), "degree"),
+])
+def test_invalid_models_are_rejected(renderer, mutate, msg):
+    from paper_2008_05858_gb300.binding import E2EError, E2E_EINVAL
+
+    w = W.small_config(seed=81)
+    mutate(w.model.slices[0])
+    with pytest.raises(E2EError) as e:
+        renderer.load_model(w.model)
+    assert e.value.code == E2E_EINVAL and msg in str(e.value)
+
+
+def test_spectrum_length_mismatch_is_rejected(renderer):
+    from paper_2008_05858_gb300.binding import E2EError, E2E_EINVAL
+
+    w = W.small_config(seed=82)
+    mid = renderer.load_model(w.model)
+    bad = W.Spectrum(0, {o: f[:-1] for o, f in w.spectra[0].flux.items()})
+    sids = [renderer.load_spectrum(bad), renderer.load_spectrum(w.spectra[1])]
+    with pytest.raises(E2EError) as e:
+        renderer.render(mid, sids, "mixed", "f32")
+    assert e.value.code == E2E_EINVAL
+    renderer.unload_model(mid)
+
+
+def test_render_alloc_and_fetch(renderer):
+    from paper_2008_05858_gb300 import binding as B
+
+    w = W.small_config(seed=91)
+    ref = oracle_frames(w)[0]
+    mid = renderer.load_model(w.model)
+    sids = renderer.load_spectra(w)
+    fid = B.e2e_render_alloc(renderer.ctx, mid, sids, B.E2E_PREC_MIXED, B.E2E_F32)
+    h, wd = w.model.det_shape[0]
+    host = np.zeros((h, wd), dtype=np.float32)
+    B.e2e_fetch_frame(renderer.ctx, fid, 0, host.ctypes.data, False, host.nbytes)
+    torch.cuda.synchronize()
+    B.e2e_release_frame(renderer.ctx, fid)
+    assert compare(host.astype(np.float64), ref).ok
+    with pytest.raises(B.E2EError):
+        B.e2e_release_frame(renderer.ctx, fid)
