@@ -174,6 +174,13 @@ int e2e_model_plan(e2e_ctx* ctx, uint64_t model_id, e2e_plan_info* info);
  * number of kernels.  Errors: E2E_EINVAL (timing not enabled), E2E_ECUDA. */
 int e2e_kernel_times(e2e_ctx* ctx, const char** names, float* ms, int32_t cap, int32_t* n);
 
+/* Diagnostic: out[i] = the FP32 Gaussian tail erfc(|u[i]|) the renderer's mixed-precision
+ * kernels use (the pixel integral of Sec. 2.2 is a difference of two such tails), with u[i]
+ * taken as a double-float (hi = (float)u, lo = (float)(u - hi)).  u_dev (n doubles) and
+ * out_dev (n floats) are device pointers; asynchronous on `stream`.  Errors: E2E_EINVAL,
+ * E2E_ECUDA. */
+int e2e_eval_tail(const double* u_dev, int64_t n, float* out_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

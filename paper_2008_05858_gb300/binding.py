@@ -100,6 +100,7 @@ _SIGS = {
     "e2e_model_plan": ([C.c_void_p, C.c_uint64, C.POINTER(e2e_plan_info)], C.c_int),
     "e2e_kernel_times": ([C.c_void_p, C.POINTER(C.c_char_p), C.POINTER(C.c_float), C.c_int32,
                           C.POINTER(C.c_int32)], C.c_int),
+    "e2e_eval_tail": ([C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
 }
 
 
@@ -254,6 +255,14 @@ def e2e_kernel_times(ctx: int, cap: int = 64):
     n = C.c_int32()
     _check(load_library().e2e_kernel_times(C.c_void_p(ctx), names, ms, cap, C.byref(n)))
     return [(names[i].decode(), float(ms[i])) for i in range(min(n.value, cap))]
+
+
+def e2e_eval_tail(u_dev_ptr: int, n: int, out_dev_ptr: int, stream=None) -> None:
+    """out[i] = the renderer's FP32 erfc(|u[i]|) (device pointers to n doubles / n floats)."""
+    rc = load_library().e2e_eval_tail(C.c_void_p(u_dev_ptr), n, C.c_void_p(out_dev_ptr),
+                                      C.c_void_p(_stream_handle(stream)))
+    if rc != E2E_OK:
+        raise E2EError(rc, "e2e_eval_tail failed")
 
 
 def e2e_model_plan(ctx: int, model_id: int) -> Dict[str, int]:

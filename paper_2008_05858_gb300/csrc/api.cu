@@ -210,30 +210,33 @@ int plan_model(Model* m) {
     return E2E_OK;
   }
   // ---- device pass: exact window origins of every stamp
-  std::vector<int64_t> task_off(ns + 1, 0), jb_off(ns + 1, 0);
+  std::vector<int64_t> task_off(ns + 1, 0), bb_off(ns + 1, 0);
+  std::vector<int> n_jb(ns), n_k16(ns);
   for (int i = 0; i < ns; ++i) {
     const auto& s = m->slices[i].d;
-    task_off[i + 1] = task_off[i] + (int64_t)s.n_lambda * ((s.n_slit + 15) / 16);
-    jb_off[i + 1] = jb_off[i] + (s.n_lambda + 31) / 32;
+    n_jb[i] = (s.n_lambda + 31) / 32;
+    n_k16[i] = (s.n_slit + 15) / 16;
+    task_off[i + 1] = task_off[i] + (int64_t)s.n_lambda * n_k16[i];
+    bb_off[i + 1] = bb_off[i] + (int64_t)n_jb[i] * n_k16[i];
   }
-  int64_t *d_task_off = nullptr, *d_jb_off = nullptr;
+  int64_t *d_task_off = nullptr, *d_bb_off = nullptr;
   int4* d_bbox = nullptr;
   int* d_spans = nullptr;
-  std::vector<int4> bbox(jb_off[ns], make_int4(1 << 30, -(1 << 30), 1 << 30, -(1 << 30)));
+  std::vector<int4> bbox(bb_off[ns], make_int4(1 << 30, -(1 << 30), 1 << 30, -(1 << 30)));
   std::vector<int> spans(ns * 10, 0);
   int rc = upload(&d_task_off, task_off.data(), task_off.size());
-  if (rc == E2E_OK) rc = upload(&d_jb_off, jb_off.data(), jb_off.size());
+  if (rc == E2E_OK) rc = upload(&d_bb_off, bb_off.data(), bb_off.size());
   if (rc == E2E_OK) rc = upload(&d_bbox, bbox.data(), bbox.size());
   if (rc == E2E_OK) rc = upload(&d_spans, spans.data(), spans.size());
   if (rc == E2E_OK) {
-    cudaError_t e = launch_plan(m->d_slices, ns, d_task_off, task_off[ns], d_bbox, d_jb_off, d_spans, 0);
+    cudaError_t e = launch_plan(m->d_slices, ns, d_task_off, task_off[ns], d_bbox, d_bb_off, d_spans, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMemcpy(bbox.data(), d_bbox, bbox.size() * sizeof(int4), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(spans.data(), d_spans, spans.size() * sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) rc = cuda_fail(e, "plan kernel");
   }
   cudaFree(d_task_off);
-  cudaFree(d_jb_off);
+  cudaFree(d_bb_off);
   cudaFree(d_bbox);
   cudaFree(d_spans);
   if (rc != E2E_OK) return rc;
@@ -267,70 +270,73 @@ int plan_model(Model* m) {
   P.B = bB;
   P.DX = bDX;
   P.DY = bDY;
-  // items: JB 32-sample blocks so that a CTA has >= 8 warp tasks
-  int min_nkb = 1 << 30;
-  for (auto& s : m->slices) min_nkb = std::min(min_nkb, (s.d.n_slit + P.B - 1) / P.B);
-  P.JB = std::max(1, std::min(8, (8 + min_nkb - 1) / min_nkb));
   P.max_deg = 0;
   for (auto& s : m->slices) P.max_deg = std::max(P.max_deg, s.d.degree);
 
-  // ---- items grouped by K, boxes clipped to the detector
-  int64_t store = 0;
-  P.items.clear();
-  P.groups.clear();
-  std::vector<int> Ks = m->Ks;
-  for (int Kg : Ks) {
-    Plan::Group g{Kg, (int)P.items.size(), 0};
-    for (int i = 0; i < ns; ++i) {
-      const auto& s = m->slices[i].d;
-      if (s.K != Kg) continue;
-      const int nblk = (s.n_lambda + 31) / 32;
-      for (int b0 = 0; b0 < nblk; b0 += P.JB) {
-        int4 u = make_int4(1 << 30, -(1 << 30), 1 << 30, -(1 << 30));
-        for (int b = b0; b < std::min(nblk, b0 + P.JB); ++b) {
-          const int4 v = bbox[jb_off[i] + b];
-          u.x = std::min(u.x, v.x);
-          u.y = std::max(u.y, v.y);
-          u.z = std::min(u.z, v.z);
-          u.w = std::max(u.w, v.w);
-        }
-        const int Wd = m->W[s.detector], Hd = m->H[s.detector];
-        const int x0 = std::max(u.x, 0), x1 = std::min(u.y, Wd - 1);
-        const int y0 = std::max(u.z, 0), y1 = std::min(u.w, Hd - 1);
-        if (x1 < x0 || y1 < y0) continue;  // every window of the item is off the detector
-        Item it{};
-        it.slice = i;
-        it.j0 = b0 * 32;
-        it.nj = std::min(s.n_lambda, (b0 + P.JB) * 32) - it.j0;
-        it.bx0 = x0;
-        it.by0 = y0;
-        it.bw = x1 - x0 + 1;
-        it.bh = y1 - y0 + 1;
-        it.store_off = store;
-        store += (int64_t)it.bw * it.bh;
-        P.items.push_back(it);
-        g.count++;
-      }
-    }
-    P.groups.push_back(g);
-  }
-  P.store_elems = store;
-  P.max_area = 0;
-  for (auto& it : P.items) P.max_area = std::max(P.max_area, it.bw * it.bh);
-
-  // ---- shared memory: as many per-warp boxes as fit
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  P.NB = 8;
-  while (P.NB >= 1) {
-    P.smem = mixed_smem_bytes(P.max_area, P.NB, P.JB, P.B, P.max_deg + 1);
+
+  // ---- items: (32-sample blocks) x (16-point blocks); at most 16 warp tasks (<= 512 runs,
+  // which keeps the fixed-point low words of a box below 2^31) and a box that fits on chip
+  for (int jb_cap = 8; jb_cap >= 1; jb_cap /= 2) {
+    int64_t store = 0;
+    P.items.clear();
+    P.groups.clear();
+    P.JB = 1;
+    for (int Kg : m->Ks) {
+      Plan::Group g{Kg, (int)P.items.size(), 0};
+      for (int i = 0; i < ns; ++i) {
+        const auto& s = m->slices[i].d;
+        if (s.K != Kg) continue;
+        const int nrc_full = (s.n_slit + P.B - 1) / P.B;
+        const int KC = nrc_full <= 16 ? n_k16[i] : P.B;  // 16-point blocks per item
+        const int nrc = std::min(nrc_full, (KC * 16 + P.B - 1) / P.B);
+        const int JB = std::max(1, std::min(jb_cap, std::min((8 + nrc - 1) / nrc, 16 / nrc)));
+        P.JB = std::max(P.JB, JB);
+        for (int b0 = 0; b0 < n_jb[i]; b0 += JB)
+          for (int c0 = 0; c0 < n_k16[i]; c0 += KC) {
+            int4 u = make_int4(1 << 30, -(1 << 30), 1 << 30, -(1 << 30));
+            for (int b = b0; b < std::min(n_jb[i], b0 + JB); ++b)
+              for (int c = c0; c < std::min(n_k16[i], c0 + KC); ++c) {
+                const int4 v = bbox[bb_off[i] + (int64_t)b * n_k16[i] + c];
+                u.x = std::min(u.x, v.x);
+                u.y = std::max(u.y, v.y);
+                u.z = std::min(u.z, v.z);
+                u.w = std::max(u.w, v.w);
+              }
+            const int Wd = m->W[s.detector], Hd = m->H[s.detector];
+            const int x0 = std::max(u.x, 0), x1 = std::min(u.y, Wd - 1);
+            const int y0 = std::max(u.z, 0), y1 = std::min(u.w, Hd - 1);
+            if (x1 < x0 || y1 < y0) continue;  // every window of the item is off the detector
+            Item it{};
+            it.slice = i;
+            it.j0 = b0 * 32;
+            it.nj = std::min(s.n_lambda, (b0 + JB) * 32) - it.j0;
+            it.k0 = c0 * 16;
+            it.nk = std::min(s.n_slit, (c0 + KC) * 16) - it.k0;
+            it.bx0 = x0;
+            it.by0 = y0;
+            it.bw = x1 - x0 + 1;
+            it.bh = y1 - y0 + 1;
+            it.store_off = store;
+            store += (int64_t)it.bw * it.bh;
+            P.items.push_back(it);
+            g.count++;
+          }
+      }
+      P.groups.push_back(g);
+    }
+    P.store_elems = store;
+    P.max_area = 0;
+    for (auto& it : P.items) P.max_area = std::max(P.max_area, it.bw * it.bh);
+    P.smem = mixed_smem_bytes(P.max_area, P.JB, P.B, P.max_deg + 1);
     if ((int)P.smem <= optin) break;
-    P.NB /= 2;
+    if (jb_cap == 1)
+      return fail(E2E_EINVAL, "trace footprint of a work item exceeds on-chip memory (area " +
+                                  std::to_string(P.max_area) + " px)");
   }
-  if (P.NB < 1)
-    return fail(E2E_EINVAL, "trace footprint of a 32-sample chunk exceeds on-chip memory (area " +
-                                std::to_string(P.max_area) + " px)");
+  P.NB = 1;
 
   // ---- merge tiles: every tile of every detector, with the items overlapping it
   std::vector<Tile> tiles;
@@ -513,7 +519,7 @@ int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, in
   for (auto& g : P.groups) {
     KernelTimer kt(ctx, st, "render_mixed");
     E2E_CK(launch_render_mixed(g.K, P.DX, P.DY, m->d_slices, d_table, m->d_u, P.d_items + g.first, g.count, store,
-                               P.B, P.JB, P.NB, P.max_deg, P.smem, st));
+                               P.B, P.JB, P.max_deg, P.smem, st));
   }
   {
     KernelTimer kt(ctx, st, "merge");

@@ -26,11 +26,12 @@ struct DevSlice {
   int64_t stamp_off;             // first global stamp index of this slice (FP64 path)
 };
 
-// A mixed-path work item: wavelength samples [j0, j0+nj) of one slice, every slit point;
-// its stamps' windows are clipped to the detector and bounded by box (bx0, by0, bw, bh).
+// A mixed-path work item: a block of wavelength samples x a block of slit points of one
+// slice; its stamps' windows, clipped to the detector, lie in box (bx0, by0, bw, bh).
 struct Item {
-  int32_t slice, j0, nj, pad;
+  int32_t slice, j0, nj, k0, nk;  // wavelength samples [j0, j0+nj), slit points [k0, k0+nk)
   int32_t bx0, by0, bw, bh;
+  int32_t pad;
   int64_t store_off;  // offset (elements) of this item's box in the render's box store
 };
 

@@ -1,22 +1,24 @@
 // Mixed-precision tiled renderer (separable Gaussian PSF) and the halo merge.
 //
-// Work item = one order-slice x a chunk of wavelength samples x every slit point.  Inside
-// the item, each lane owns a *run* of B consecutive slit points of one wavelength sample:
-// the run's stamps land within a (K+DX) x (K+DY) pixel tile (the plan checks this for every
-// run of the model), so the lane accumulates their outer products w * A_x (x) A_y in
-// registers and flushes the tile once per run into its warp's FP32 box in shared memory.
-// After each round the warps' boxes are folded (pairwise, FP32) into the item's FP64 box,
-// and at the end the FP64 box goes to a scratch "box store".  The merge kernel then owns
-// every output pixel: it adds, with compensated summation, the boxes of all items that
-// overlap its tile, in item order, and writes the frame once.  No global atomics; the
-// result is independent of scheduling.
+// Work item = one order-slice x a block of wavelength samples x a block of slit points.
+// Inside the item, each lane owns a *run* of B consecutive slit points of one wavelength
+// sample: the run's stamps land within a (K+DX) x (K+DY) pixel tile (the plan checks this for
+// every run of the model), so the lane accumulates their outer products w * A_x (x) A_y in
+// FP32 registers and flushes the tile once per run into the item's box in shared memory.
+// The box holds 52-bit fixed-point sums (two 32-bit words per pixel, scaled by a power of
+// two above the item's total flux) updated with integer atomics: the accumulation is exact
+// and independent of the order of the flushes.  At the end the box is written, in FP64, to a
+// scratch "box store".  The merge kernel then owns every output pixel: it adds, with
+// compensated summation, the boxes of all items overlapping its tile, in item order, and
+// writes the frame once.  No global atomics; the frame does not depend on scheduling.
 //
 // Precision (the paper's fidelity target, Sec. 2.2, is a photocenter shift below ~1e-5 px):
-// mapping in FP64 (centre split into integer pixel + FP32 offset exactly), PSF pixel
-// integrals in FP32, per-tile accumulation FP32 over <= one run and one round, FP64 across
-// rounds and items.
+// mapping in FP64, the centre split exactly into an integer pixel and an FP32 offset, PSF
+// pixel integrals in FP32 with double-float edge arguments (phi32.cuh), FP32 sums over one
+// run (<= B stamps) in registers, exact fixed-point sums per item, FP64 across items.
 #include "e2e_device.cuh"
 #include "e2e_kernels.h"
+#include "phi32.cuh"
 
 namespace e2e {
 
@@ -36,11 +38,11 @@ __device__ __forceinline__ double horner_s(const double* P, int d, double s) {
 // ------------------------------------------------------------------------------ plan
 
 // One thread per (slice, wavelength sample j, block of 16 slit points): map the stamps
-// exactly as the render will, and record (a) per 32-sample block of each slice the bounding
-// box of the stamps' windows, (b) per slice the largest spread of window origins over any
-// aligned run of B = 1, 2, 4, 8, 16 consecutive slit points.
+// exactly as the render will, and record (a) per (32-sample block, 16-point block) of each
+// slice the bounding box of the stamps' windows, (b) per slice the largest spread of window
+// origins over any aligned run of B = 1, 2, 4, 8, 16 consecutive slit points.
 __global__ void k_plan(const DevSlice* __restrict__ slices, int n_slices, const int64_t* __restrict__ task_off,
-                       int4* __restrict__ jblock_bbox, const int64_t* __restrict__ jblock_off,
+                       int4* __restrict__ bbox, const int64_t* __restrict__ bbox_off,
                        int* __restrict__ spans /* [n_slices][5][2] */) {
   const int64_t n_tasks = task_off[n_slices];
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tasks; t += (int64_t)gridDim.x * blockDim.x) {
@@ -85,7 +87,7 @@ __global__ void k_plan(const DevSlice* __restrict__ slices, int n_slices, const 
       }
     }
     const int h = S.K / 2;
-    int4* bb = jblock_bbox + jblock_off[lo] + j / 32;
+    int4* bb = bbox + bbox_off[lo] + (int64_t)(j / 32) * nkb + kb;
     atomicMin(&bb->x, xmn - h);
     atomicMax(&bb->y, xmx + h);
     atomicMin(&bb->z, ymn - h);
@@ -108,15 +110,10 @@ struct MixedArgs {
   double* store;
   int B;        // slit points per run
   int JB;       // 32-sample blocks per item
-  int NB;       // FP32 boxes per CTA (warps share when < 8)
   int max_deg;  // largest degree among the launched slices
 };
 
-// P(a < Z < b) * 2 from the edge values E = erfc(|t|), t = edge offset / (sqrt2 sigma):
-// same-side differences of the tails, or 2 minus both tails across the mean.
-__device__ __forceinline__ float twice_interval(float ta, float tb, float ea, float eb) {
-  return ta >= 0.f ? ea - eb : (tb <= 0.f ? eb - ea : 2.f - ea - eb);
-}
+constexpr int kSplit = 22;  // fixed point: value * 2^P = hi * 2^22 + lo, lo in [0, 2^22)
 
 template <int K, int DX, int DY>
 __global__ void __launch_bounds__(kThreads) k_render_mixed(const MixedArgs a) {
@@ -127,142 +124,161 @@ __global__ void __launch_bounds__(kThreads) k_render_mixed(const MixedArgs a) {
   const int area = it.bw * it.bh;
   const int J = 32 * a.JB;
   const int nd = S.degree + 1;
-  // shared layout: FP64 box | NB FP32 boxes | per-sample table | run staging
-  double* box64 = reinterpret_cast<double*>(smem);
-  float* box32 = reinterpret_cast<float*>(box64 + area);
-  double* tabP = reinterpret_cast<double*>(box32 + ((a.NB * area + 1) & ~1));  // [J][2][nd]
-  double* tabW = tabP + (size_t)J * 2 * nd;                                     // [J]
-  float2* tabG = reinterpret_cast<float2*>(tabW + J);                           // [J]
-  int4* stage = reinterpret_cast<int4*>((reinterpret_cast<uintptr_t>(tabG + J) + 15) & ~(uintptr_t)15);  // [B][kThreads]
+  // shared layout: per-sample tables | run staging | box hi words | box lo words
+  double* tabP = reinterpret_cast<double*>(smem);  // [J][2][nd]
+  double* tabW = tabP + (size_t)J * 2 * nd;         // [J] flux x bin width / 4
+  float4* tabG = reinterpret_cast<float4*>(tabW + J);  // [J] (gx hi, gx lo, gy hi, gy lo), g = 1/(sqrt2 sigma)
+  int4* stage = reinterpret_cast<int4*>(tabG + J);  // [B][kThreads]
+  int* boxh = reinterpret_cast<int*>(stage + (size_t)a.B * kThreads);
+  unsigned* boxl = reinterpret_cast<unsigned*>(boxh + area);
+  __shared__ double s_red[kWarps];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int p = tid; p < area; p += kThreads) box64[p] = 0.0;
-  for (int p = tid; p < a.NB * area; p += kThreads) box32[p] = 0.f;
+  for (int p = tid; p < area; p += kThreads) {
+    boxh[p] = 0;
+    boxl[p] = 0u;
+  }
   const double* flux = a.flux_tab[S.flux_slot];
+  const double* u = a.u_all + S.u_off;
   for (int q = tid; q < it.nj * 2 * nd; q += kThreads) {
     const int jj = q / (2 * nd), r = q - jj * 2 * nd, axis = r / nd, b = r - axis * nd;
     const double lt = norm_sample(it.j0 + jj, S.n_lambda);
     tabP[q] = poly_lt_for_b(axis ? S.cy : S.cx, S.degree, b, lt);
   }
+  // flux bound of the item: sum over its stamps of |w| (bounds every pixel of its box)
+  double usum = 0.0;
+  for (int k = lane; k < it.nk; k += 32) usum += fabs(u[it.k0 + k]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) usum += __shfl_xor_sync(0xffffffffu, usum, o);
+  double wsum = 0.0;
   for (int jj = tid; jj < it.nj; jj += kThreads) {
     const double lt = norm_sample(it.j0 + jj, S.n_lambda);
     const double sgx = fma(fma(S.sx[2], lt, S.sx[1]), lt, S.sx[0]);
     const double sgy = fma(fma(S.sy[2], lt, S.sy[1]), lt, S.sy[0]);
-    tabG[jj] = make_float2((float)(0.70710678118654752440 / sgx), (float)(0.70710678118654752440 / sgy));
-    tabW[jj] = flux[it.j0 + jj] * S.dlam * 0.25;  // 0.25: the profiles below are 2x the pixel integrals
+    const double gx = 0.70710678118654752440 / sgx, gy = 0.70710678118654752440 / sgy;
+    const float gxh = (float)gx, gyh = (float)gy;
+    tabG[jj] = make_float4(gxh, (float)(gx - (double)gxh), gyh, (float)(gy - (double)gyh));
+    const double wj = flux[it.j0 + jj] * S.dlam;
+    tabW[jj] = wj * 0.25;  // 0.25: the profiles below are 2x the pixel integrals
+    wsum += fabs(wj);
   }
-  __syncthreads();
-
-  const double* u = a.u_all + S.u_off;
-  const int nkb = (S.n_slit + a.B - 1) / a.B;
-  const int ntask = a.JB * nkb;
-  float* mybox = box32 + (warp % a.NB) * area;
-  for (int round0 = 0; round0 < ntask; round0 += kWarps) {
-    const int task = round0 + warp;
-    const int jj = (task % a.JB) * 32 + lane;
-    const int kb = task / a.JB;
-    if (task < ntask && jj < it.nj) {
-      const int k0 = kb * a.B;
-      const int nb = min(a.B, S.n_slit - k0);
-      double px[9], py[9];
 #pragma unroll
-      for (int b = 0; b <= 8; ++b) {
-        px[b] = b < nd ? tabP[(jj * 2 + 0) * nd + b] : 0.0;
-        py[b] = b < nd ? tabP[(jj * 2 + 1) * nd + b] : 0.0;
+  for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+  if (lane == 0) s_red[warp] = wsum;
+  __syncthreads();
+  double total = 0.0;
+#pragma unroll
+  for (int q = 0; q < kWarps; ++q) total += s_red[q];
+  total *= usum;
+  // scale 2^P with |box sums| <= total < 2^(52-P); clamp so 2^P stays a normal FP32
+  int ex = 0;
+  frexp(total, &ex);
+  const int P = total > 0.0 ? max(-100, min(100, 52 - ex)) : 0;
+  const float sc = ldexpf(1.f, P), sc_hi = ldexpf(1.f, P - kSplit);
+
+  const int nrc = (it.nk + a.B - 1) / a.B;
+  const int jbs = (it.nj + 31) / 32;  // 32-sample blocks of this item (<= a.JB)
+  const int ntask = jbs * nrc;
+  for (int task = warp; task < ntask && total > 0.0; task += kWarps) {
+    const int jj = (task % jbs) * 32 + lane;
+    if (jj >= it.nj) continue;
+    const int k0 = it.k0 + (task / jbs) * a.B;
+    const int nb = min(a.B, it.k0 + it.nk - k0);
+    double px[9], py[9];
+#pragma unroll
+    for (int b = 0; b <= 8; ++b) {
+      px[b] = b < nd ? tabP[(jj * 2 + 0) * nd + b] : 0.0;
+      py[b] = b < nd ? tabP[(jj * 2 + 1) * nd + b] : 0.0;
+    }
+    int xmn = 1 << 30, ymn = 1 << 30;
+    for (int b = 0; b < nb; ++b) {
+      const double s = norm_sample(k0 + b, S.n_slit);
+      int ci, ri;
+      float fx, fy;
+      split_coord(clamp_coord(horner_s(px, S.degree, s)), ci, fx);
+      split_coord(clamp_coord(horner_s(py, S.degree, s)), ri, fy);
+      xmn = min(xmn, ci);
+      ymn = min(ymn, ri);
+      stage[b * kThreads + tid] = make_int4(ci, ri, __float_as_int(fx), __float_as_int(fy));
+    }
+    const float4 g = tabG[jj];
+    const double wj = tabW[jj];
+    float acc[RY][RX];
+#pragma unroll
+    for (int r = 0; r < RY; ++r)
+#pragma unroll
+      for (int c = 0; c < RX; ++c) acc[r][c] = 0.f;
+    for (int b = 0; b < nb; ++b) {
+      const int4 st = stage[b * kThreads + tid];
+      const int ox = st.x - xmn, oy = st.y - ymn;  // 0..DX, 0..DY
+      const float fx = __int_as_float(st.z), fy = __int_as_float(st.w);
+      const float w = (float)(wj * u[k0 + b]);
+      float wax[RX], ay[RY];
+      {
+        float th, tl;
+        edge_arg((float)(-ox - H) - 0.5f, fx, g.x, g.y, th, tl);
+        float ep = erfc_df(th, tl), tp = th;
+#pragma unroll
+        for (int c = 0; c < RX; ++c) {
+          edge_arg((float)(c + 1 - ox - H) - 0.5f, fx, g.x, g.y, th, tl);
+          const float en = erfc_df(th, tl);
+          const float v = twice_interval(tp, th, ep, en);
+          wax[c] = (c >= ox && c < ox + K) ? w * v : 0.f;
+          tp = th;
+          ep = en;
+        }
       }
-      int xmn = 1 << 30, ymn = 1 << 30;
-      for (int b = 0; b < nb; ++b) {
-        const double s = norm_sample(k0 + b, S.n_slit);
-        int ci, ri;
-        float fx, fy;
-        split_coord(clamp_coord(horner_s(px, S.degree, s)), ci, fx);
-        split_coord(clamp_coord(horner_s(py, S.degree, s)), ri, fy);
-        xmn = min(xmn, ci);
-        ymn = min(ymn, ri);
-        stage[b * kThreads + tid] = make_int4(ci, ri, __float_as_int(fx), __float_as_int(fy));
+      {
+        float th, tl;
+        edge_arg((float)(-oy - H) - 0.5f, fy, g.z, g.w, th, tl);
+        float ep = erfc_df(th, tl), tp = th;
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+          edge_arg((float)(r + 1 - oy - H) - 0.5f, fy, g.z, g.w, th, tl);
+          const float en = erfc_df(th, tl);
+          const float v = twice_interval(tp, th, ep, en);
+          ay[r] = (r >= oy && r < oy + K) ? v : 0.f;
+          tp = th;
+          ep = en;
+        }
       }
-      const float2 g = tabG[jj];
-      const double wj = tabW[jj];
-      float acc[RY][RX];
 #pragma unroll
       for (int r = 0; r < RY; ++r)
 #pragma unroll
-        for (int c = 0; c < RX; ++c) acc[r][c] = 0.f;
-      for (int b = 0; b < nb; ++b) {
-        const int4 st = stage[b * kThreads + tid];
-        const int ox = st.x - xmn, oy = st.y - ymn;  // 0..DX, 0..DY
-        const float fx = __int_as_float(st.z), fy = __int_as_float(st.w);
-        const float w = (float)(wj * u[k0 + b]);
-        float wax[RX], ay[RY];
-        {
-          float tp = ((float)(-ox - H) - 0.5f - fx) * g.x;
-          float ep = erfcf(fabsf(tp));
+        for (int c = 0; c < RX; ++c) acc[r][c] = fmaf(ay[r], wax[c], acc[r][c]);
+    }
+    // flush the run tile into the box as exact fixed-point increments
+    const int gx0 = xmn - H - it.bx0, gy0 = ymn - H - it.by0;
 #pragma unroll
-          for (int c = 0; c < RX; ++c) {
-            const float tn = ((float)(c + 1 - ox - H) - 0.5f - fx) * g.x;
-            const float en = erfcf(fabsf(tn));
-            const float v = twice_interval(tp, tn, ep, en);
-            wax[c] = (c >= ox && c < ox + K) ? w * v : 0.f;
-            tp = tn;
-            ep = en;
-          }
-        }
-        {
-          float tp = ((float)(-oy - H) - 0.5f - fy) * g.y;
-          float ep = erfcf(fabsf(tp));
+    for (int r = 0; r < RY; ++r) {
+      const int gy = gy0 + r;
+      if (gy < 0 || gy >= it.bh) continue;
 #pragma unroll
-          for (int r = 0; r < RY; ++r) {
-            const float tn = ((float)(r + 1 - oy - H) - 0.5f - fy) * g.y;
-            const float en = erfcf(fabsf(tn));
-            const float v = twice_interval(tp, tn, ep, en);
-            ay[r] = (r >= oy && r < oy + K) ? v : 0.f;
-            tp = tn;
-            ep = en;
-          }
-        }
-#pragma unroll
-        for (int r = 0; r < RY; ++r)
-#pragma unroll
-          for (int c = 0; c < RX; ++c) acc[r][c] = fmaf(ay[r], wax[c], acc[r][c]);
-      }
-      // flush the run tile into this warp's FP32 box
-      const int gx0 = xmn - H - it.bx0, gy0 = ymn - H - it.by0;
-#pragma unroll
-      for (int r = 0; r < RY; ++r) {
-        const int gy = gy0 + r;
-        if (gy < 0 || gy >= it.bh) continue;
-#pragma unroll
-        for (int c = 0; c < RX; ++c) {
-          const int gx = gx0 + c;
-          if (gx >= 0 && gx < it.bw) atomicAdd(mybox + gy * it.bw + gx, acc[r][c]);
+      for (int c = 0; c < RX; ++c) {
+        const int gxp = gx0 + c;
+        const float v = acc[r][c];
+        if (gxp >= 0 && gxp < it.bw && v != 0.f) {
+          const float hf = floorf(v * sc_hi);
+          const float lf = fmaf(-hf, 4194304.f, v * sc);
+          atomicAdd(boxh + gy * it.bw + gxp, __float2int_rz(hf));
+          atomicAdd(boxl + gy * it.bw + gxp, __float2uint_rn(lf));
         }
       }
     }
-    __syncthreads();
-    // fold the warps' FP32 boxes (pairwise) into the FP64 box and clear them
-    for (int p = tid; p < area; p += kThreads) {
-      float v[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = q < a.NB ? box32[q * area + p] : 0.f;
-      const float s = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
-      box64[p] += (double)s;
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (q < a.NB) box32[q * area + p] = 0.f;
-    }
-    __syncthreads();
   }
+  __syncthreads();
   double* out = a.store + it.store_off;
-  for (int p = tid; p < area; p += kThreads) out[p] = box64[p];
+  const double inv = ldexp(1.0, -P);
+  for (int p = tid; p < area; p += kThreads)
+    out[p] = fma((double)boxh[p], 4194304.0, (double)boxl[p]) * inv;
 }
 
-size_t mixed_smem_bytes(int area, int NB, int JB, int B, int nd) {
-  size_t bytes = (size_t)area * 8;
-  bytes += (size_t)((NB * area + 1) & ~1) * 4;
+size_t mixed_smem_bytes(int area, int JB, int B, int nd) {
   const int J = 32 * JB;
-  bytes += (size_t)J * 2 * nd * 8 + (size_t)J * 8 + (size_t)J * 8;
+  size_t bytes = (size_t)J * 2 * nd * 8 + (size_t)J * 8 + (size_t)J * 16;
   bytes = (bytes + 15) & ~(size_t)15;
   bytes += (size_t)B * kThreads * 16;
+  bytes += (size_t)area * 8;
   return bytes;
 }
 
@@ -311,11 +327,11 @@ __global__ void __launch_bounds__(256) k_merge(const Tile* __restrict__ tiles, c
 // ------------------------------------------------------------------------------ launchers
 
 cudaError_t launch_plan(const DevSlice* slices, int n_slices, const int64_t* task_off, int64_t n_tasks,
-                        int4* jblock_bbox, const int64_t* jblock_off, int* spans, cudaStream_t st) {
+                        int4* bbox, const int64_t* bbox_off, int* spans, cudaStream_t st) {
   if (n_tasks == 0) return cudaSuccess;
   int64_t blocks = (n_tasks + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_plan<<<(unsigned)blocks, 256, 0, st>>>(slices, n_slices, task_off, jblock_bbox, jblock_off, spans);
+  k_plan<<<(unsigned)blocks, 256, 0, st>>>(slices, n_slices, task_off, bbox, bbox_off, spans);
   return cudaGetLastError();
 }
 
@@ -338,9 +354,9 @@ bool mixed_variant_supported(int K, int DX, int DY) {
 
 cudaError_t launch_render_mixed(int K, int DX, int DY, const DevSlice* slices, const double* const* flux_tab,
                                 const double* u_all, const Item* items, int n_items, double* store, int B, int JB,
-                                int NB, int max_deg, size_t smem, cudaStream_t st) {
+                                int max_deg, size_t smem, cudaStream_t st) {
   if (n_items == 0) return cudaSuccess;
-  MixedArgs a{slices, flux_tab, u_all, items, store, B, JB, NB, max_deg};
+  MixedArgs a{slices, flux_tab, u_all, items, store, B, JB, max_deg};
 #define E2E_V(KK, X, Y) \
   if (K == KK && DX == X && DY == Y) return launch_one<KK, X, Y>(a, n_items, smem, st);
   E2E_V(1, 0, 0) E2E_V(3, 0, 0) E2E_V(5, 0, 0) E2E_V(7, 0, 0) E2E_V(9, 0, 0) E2E_V(11, 0, 0) E2E_V(13, 0, 0)

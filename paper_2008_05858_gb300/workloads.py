@@ -211,11 +211,12 @@ def _make_slice(
             cx[coeff_index(a, b)] = rng.uniform(-1.0, 1.0) * 2.0 ** (-t)
             cy[coeff_index(a, b)] = rng.uniform(-1.0, 1.0) * 2.0 ** (-t)
     cx[coeff_index(0, 0)] = width / 2.0
-    cx[coeff_index(1, 0)] = 0.45 * width
-    cx[coeff_index(0, 1)] = rng.uniform(-1.0, 1.0)  # slit tilt
     cy[coeff_index(0, 0)] = y_centre
-    cy[coeff_index(1, 0)] = rng.uniform(-1.0, 1.0) * 0.5
-    cy[coeff_index(0, 1)] = slit_half_height
+    if degree >= 1:
+        cx[coeff_index(1, 0)] = 0.45 * width
+        cx[coeff_index(0, 1)] = rng.uniform(-1.0, 1.0)  # slit tilt
+        cy[coeff_index(1, 0)] = rng.uniform(-1.0, 1.0) * 0.5
+        cy[coeff_index(0, 1)] = slit_half_height
     if degree >= 2:
         cy[coeff_index(2, 0)] = rng.uniform(5.0, 20.0)  # order curvature
     if sigma is not None:

