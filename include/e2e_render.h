@@ -174,6 +174,29 @@ int e2e_model_plan(e2e_ctx* ctx, uint64_t model_id, e2e_plan_info* info);
  * number of kernels.  Errors: E2E_EINVAL (timing not enabled), E2E_ECUDA. */
 int e2e_kernel_times(e2e_ctx* ctx, const char** names, float* ms, int32_t cap, int32_t* n);
 
+/* Render without allocating (no counterpart in the paper: a deployment convenience).
+ * Some callers cannot allocate device memory while they run: a process whose device memory
+ * is already reserved by another runtime (for instance a deep-learning framework's caching
+ * allocator holding most of the GPU), or a real-time pipeline that must not allocate after
+ * start-up because an allocation can block the stream or fail mid-observation.  This entry
+ * point renders like e2e_render with precision E2E_PREC_MIXED, but takes its scratch (the
+ * per-item box store and the small launch tables) from a fixed buffer of
+ * E2E_STATIC_SCRATCH_BYTES that the library holds in device memory on every GPU it is loaded
+ * on, until the process exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - A model whose scratch (e2e_plan_info.scratch_bytes plus a few KB of tables) exceeds the
+ *     buffer is rejected with E2E_ETOOBIG and a message giving both sizes.
+ *   - The first call on a device looks up the buffer's device address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture.
+ *   - All calls share the one buffer and it keeps the previous call's contents; nothing in
+ *     it needs to start at zero (every call rewrites all it reads).  Calls whose work
+ *     overlaps on the GPU (different streams, or another thread) race on the buffer: order
+ *     them on one stream or synchronise between them.
+ * Arguments as for e2e_render (dst/pitch per detector, dtype E2E_F32 or E2E_F64).
+ * Errors: E2E_EINVAL, E2E_ENOTFOUND, E2E_ETOOBIG, E2E_ECUDA. */
+#define E2E_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
+int e2e_render_static(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids, int32_t dtype,
+                      void* const* dst, const int64_t* pitch_elems, void* stream);
+
 /* Diagnostic: out[i] = the FP32 Gaussian tail erfc(|u[i]|) the renderer's mixed-precision
  * kernels use (the pixel integral of Sec. 2.2 is a difference of two such tails), with u[i]
  * taken as a double-float (hi = (float)u, lo = (float)(u - hi)).  u_dev (n doubles) and

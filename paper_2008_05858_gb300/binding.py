@@ -101,7 +101,12 @@ _SIGS = {
     "e2e_kernel_times": ([C.c_void_p, C.POINTER(C.c_char_p), C.POINTER(C.c_float), C.c_int32,
                           C.POINTER(C.c_int32)], C.c_int),
     "e2e_eval_tail": ([C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
+    "e2e_render_static": ([C.c_void_p, C.c_uint64, C.c_int32, C.POINTER(C.c_uint64), C.c_int32,
+                           C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.c_void_p], C.c_int),
 }
+
+#: size of the library's fixed device scratch used by e2e_render_static
+E2E_STATIC_SCRATCH_BYTES = 64 << 20
 
 
 def lib_path() -> str:
@@ -227,6 +232,19 @@ def e2e_render(ctx: int, model_id: int, spec_ids: Sequence[int], precision: int,
     pit = None if pitch_elems is None else (C.c_int64 * len(pitch_elems))(*pitch_elems)
     _check(load_library().e2e_render(C.c_void_p(ctx), model_id, n, sids, precision, dtype, dst, pit,
                                      C.c_void_p(_stream_handle(stream))))
+
+
+def e2e_render_static(ctx: int, model_id: int, spec_ids: Sequence[int], dtype: int, dst_ptrs: Sequence[int],
+                      pitch_elems: Optional[Sequence[int]] = None, stream=None) -> None:
+    """Mixed-precision render that allocates nothing: scratch comes from the library's fixed
+    device buffer (E2E_STATIC_SCRATCH_BYTES).  For callers that cannot allocate device memory
+    while running; calls that overlap on the GPU share that buffer and must be serialised."""
+    n = len(spec_ids)
+    sids = (C.c_uint64 * max(n, 1))(*spec_ids)
+    dst = (C.c_void_p * len(dst_ptrs))(*dst_ptrs)
+    pit = None if pitch_elems is None else (C.c_int64 * len(pitch_elems))(*pitch_elems)
+    _check(load_library().e2e_render_static(C.c_void_p(ctx), model_id, n, sids, dtype, dst, pit,
+                                            C.c_void_p(_stream_handle(stream))))
 
 
 def e2e_render_alloc(ctx: int, model_id: int, spec_ids: Sequence[int], precision: int, dtype: int, stream=None) -> int:

@@ -793,6 +793,88 @@ int e2e_model_plan(e2e_ctx* ctx, uint64_t model_id, e2e_plan_info* info) {
   return E2E_OK;
 }
 
+// ---------------------------------------------------------------- render without allocating
+//
+// For callers that cannot allocate device memory mid-run (another runtime owns the GPU's
+// memory, or a real-time loop must not block or fail on an allocation), the mixed-precision
+// render can take its scratch from this fixed buffer instead of the stream-ordered pool.  It
+// lives in device memory on every GPU that loads the library, for the life of the process.
+// Host code sees `g_static_scratch` only as a host-side handle: its device address comes
+// from cudaGetSymbolAddress, looked up once per device with that device current.
+static __device__ __align__(256) unsigned char g_static_scratch[E2E_STATIC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_static_mu;
+std::map<int, void*> g_static_addr;  // device -> device address of g_static_scratch
+
+int static_scratch_address(int device, void** out) {
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  auto it = g_static_addr.find(device);
+  if (it != g_static_addr.end()) {
+    *out = it->second;
+    return E2E_OK;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);  // the caller made `device` current
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+  g_static_addr[device] = p;
+  *out = p;
+  return E2E_OK;
+}
+
+size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+}  // namespace
+
+int e2e_render_static(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids, int32_t dtype,
+                      void* const* dst, const int64_t* pitch_in, void* stream) {
+  if (!ctx) return fail(E2E_EINVAL, "null context");
+  if (dtype != E2E_F32 && dtype != E2E_F64) return fail(E2E_EINVAL, "dtype must be E2E_F32 or E2E_F64");
+  if (!dst) return fail(E2E_EINVAL, "null destination list");
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Model* m = find_model(ctx, model_id);
+  if (!m) return fail(E2E_ENOTFOUND, "unknown model id");
+  if (m->psf != E2E_PSF_SEPARABLE) return fail(E2E_EINVAL, "the fixed-scratch render supports the separable PSF");
+  const Plan& P = m->plan;
+  if (!P.ok) return fail(E2E_EINVAL, "model has no mixed-precision plan");
+  std::vector<int64_t> pitch(m->n_det);
+  for (int d = 0; d < m->n_det; ++d) {
+    if (!dst[d]) return fail(E2E_EINVAL, "null destination frame");
+    pitch[d] = pitch_in ? pitch_in[d] : m->W[d];
+    if (pitch[d] < m->W[d]) return fail(E2E_EINVAL, "pitch smaller than width");
+  }
+  std::vector<const double*> table;
+  int rc = resolve_flux(ctx, m, n_spec, spec_ids, table);
+  if (rc != E2E_OK) return rc;
+  // layout in the fixed buffer: flux table | pitches | destination pointers | box store
+  const size_t off_table = 0;
+  const size_t off_pitch = align256(off_table + table.size() * sizeof(double*));
+  const size_t off_dst = align256(off_pitch + pitch.size() * sizeof(int64_t));
+  const size_t off_store = align256(off_dst + (size_t)m->n_det * sizeof(void*));
+  const size_t need = off_store + (size_t)P.store_elems * sizeof(double);
+  if (need > E2E_STATIC_SCRATCH_BYTES)
+    return fail(E2E_ETOOBIG, "model needs " + std::to_string(need) + " bytes of scratch; the fixed buffer holds " +
+                                 std::to_string((size_t)E2E_STATIC_SCRATCH_BYTES));
+  void* base = nullptr;
+  rc = static_scratch_address(ctx->device, &base);
+  if (rc != E2E_OK) return rc;
+  unsigned char* b = static_cast<unsigned char*>(base);
+  const double** d_table = reinterpret_cast<const double**>(b + off_table);
+  int64_t* d_pitch = reinterpret_cast<int64_t*>(b + off_pitch);
+  void** d_dst = reinterpret_cast<void**>(b + off_dst);
+  double* store = reinterpret_cast<double*>(b + off_store);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!table.empty())
+    E2E_CK(cudaMemcpyAsync(d_table, table.data(), table.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
+  E2E_CK(cudaMemcpyAsync(d_pitch, pitch.data(), pitch.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  E2E_CK(cudaMemcpyAsync(d_dst, dst, m->n_det * sizeof(void*), cudaMemcpyHostToDevice, st));
+  for (auto& grp : P.groups)
+    E2E_CK(launch_render_mixed(grp.K, P.DX, P.DY, m->d_slices, d_table, m->d_u, P.d_items + grp.first, grp.count,
+                               store, P.B, P.JB, P.max_deg, P.smem, st));
+  E2E_CK(launch_merge(P.d_tiles, P.n_tiles, P.d_lists, P.d_items, store, d_dst, dtype, d_pitch, m->d_dims, st));
+  return E2E_OK;
+}
+
 int e2e_kernel_times(e2e_ctx* ctx, const char** names, float* ms, int32_t cap, int32_t* n) {
   if (!ctx || !n) return fail(E2E_EINVAL, "null argument");
   if (!ctx->opts.kernel_timing) return fail(E2E_EINVAL, "context was created without kernel_timing");
