@@ -48,7 +48,7 @@ struct SliceHost {
 
 struct Plan {
   bool ok = false;
-  int B = 1, DX = 0, DY = 0, JB = 1, NB = 8, max_area = 0, max_deg = 0;
+  int B = 1, DX = 0, DY = 0, JB = 1, NB = 8, max_area = 0, max_deg = 0, nk_max = 1;
   std::vector<Item> items;  // host copy
   int64_t store_elems = 0;
   size_t smem = 0;
@@ -194,12 +194,17 @@ int upload(T** dptr, const T* src, size_t n) {
 
 // ------------------------------------------------------------------ planning
 
-// Cost (arbitrary units) of a tile variant per stamp: PSF edge evaluations dominate, then
-// the register outer product, then the shared-memory flush amortised over the run.
+// Relative cost per stamp of a tile variant of the lane-pair kernel: each lane evaluates a
+// profile of K + max(DX, DY) pixels (~30 FP32 operations and 2 SFU operations per edge),
+// accumulates half the (K+DX) x (K+DY) tile, and flushes its half once per run of B stamps
+// (~10 operations per pixel); tiles above 84 accumulators per lane halve the occupancy.
 double variant_cost(int K, int DX, int DY, int B) {
-  const double edges = (K + DX + 1) + (K + DY + 1);
+  const int D = std::max(DX, DY);
+  const double edges = 2.0 * (K + D + 1);
   const double tile = (double)(K + DX) * (K + DY);
-  return edges * 50.0 + tile * 1.0 + tile * 15.0 / B;
+  double c = edges * 30.0 + tile + tile * 10.0 / B;
+  if ((K + DX) * ((K + DY + 1) / 2) > 84) c *= 1.6;
+  return c;
 }
 
 int plan_model(Model* m) {
@@ -246,7 +251,7 @@ int plan_model(Model* m) {
   for (auto& s : m->slices) K = std::max(K, s.d.K);
   double best = 1e300;
   int bB = 1, bDX = 0, bDY = 0;
-  const int variants[3][2] = {{0, 0}, {1, 1}, {2, 2}};
+  const int variants[4][2] = {{0, 0}, {1, 1}, {1, 2}, {2, 2}};
   for (int q = 0; q <= 3; ++q) {  // B = 1..8
     const int B = 1 << q;
     int sx = 0, sy = 0;
@@ -329,8 +334,12 @@ int plan_model(Model* m) {
     }
     P.store_elems = store;
     P.max_area = 0;
-    for (auto& it : P.items) P.max_area = std::max(P.max_area, it.bw * it.bh);
-    P.smem = mixed_smem_bytes(P.max_area, P.JB, P.B, P.max_deg + 1);
+    P.nk_max = 1;
+    for (auto& it : P.items) {
+      P.max_area = std::max(P.max_area, it.bw * it.bh);
+      P.nk_max = std::max(P.nk_max, it.nk);
+    }
+    P.smem = mixed_smem_bytes(P.max_area, P.JB, P.nk_max, P.B, P.max_deg + 1);
     if ((int)P.smem <= optin) break;
     if (jb_cap == 1)
       return fail(E2E_EINVAL, "trace footprint of a work item exceeds on-chip memory (area " +
@@ -519,7 +528,7 @@ int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, in
   for (auto& g : P.groups) {
     KernelTimer kt(ctx, st, "render_mixed");
     E2E_CK(launch_render_mixed(g.K, P.DX, P.DY, m->d_slices, d_table, m->d_u, P.d_items + g.first, g.count, store,
-                               P.B, P.JB, P.max_deg, P.smem, st));
+                               P.B, P.JB, P.nk_max, P.max_deg, P.smem, st));
   }
   {
     KernelTimer kt(ctx, st, "merge");
@@ -870,7 +879,7 @@ int e2e_render_static(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uin
   E2E_CK(cudaMemcpyAsync(d_dst, dst, m->n_det * sizeof(void*), cudaMemcpyHostToDevice, st));
   for (auto& grp : P.groups)
     E2E_CK(launch_render_mixed(grp.K, P.DX, P.DY, m->d_slices, d_table, m->d_u, P.d_items + grp.first, grp.count,
-                               store, P.B, P.JB, P.max_deg, P.smem, st));
+                               store, P.B, P.JB, P.nk_max, P.max_deg, P.smem, st));
   E2E_CK(launch_merge(P.d_tiles, P.n_tiles, P.d_lists, P.d_items, store, d_dst, dtype, d_pitch, m->d_dims, st));
   return E2E_OK;
 }

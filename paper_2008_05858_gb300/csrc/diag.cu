@@ -7,10 +7,10 @@ namespace {
 
 __global__ void k_eval_tail(const double* __restrict__ u, int64_t n, float* __restrict__ out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = u[i];
+    const double v = u[i] * e2e::kSqrtLog2eD;  // the kernels' argument is in log2 units
     const float h = (float)v;
     const float l = (float)(v - (double)h);
-    out[i] = e2e::erfc_df(h, l);
+    out[i] = e2e::tail2(h, l);
   }
 }
 

@@ -58,26 +58,54 @@ __device__ __forceinline__ double poly_lt_for_b(const double* c, int degree, int
   return p;
 }
 
+// Window-centre marker for a mapped coordinate outside |v| < 2^15 px (or not finite): the
+// stamp lies off every detector and deposits nothing.
+constexpr int kOffFrame = -(1 << 28);
+
 // Split an FP64 pixel coordinate into the window-centre pixel floor(v + 1/2) and the
-// offset v - that pixel in [-1/2, 1/2) as FP32, using integer operations on the bits of
-// v + 1.5*2^16 (one FP64 add): the sum has a fixed exponent, so its low 52 mantissa bits
-// are (v + 2^15) in fixed point with 36 fractional bits.  Valid for |v| < 2^15 (callers
-// clamp); the offset keeps 32 fractional bits before rounding to FP32.
+// offset v - that pixel in [-1/2, 1/2] as FP32, using integer operations on the bits of
+// v + 1.5*2^16 (one FP64 add): for |v| < 2^15 the sum has the fixed exponent 16, so its low
+// 52 mantissa bits are (v + 2^15) in fixed point with 36 fractional bits.  Anything else
+// (including NaN) returns kOffFrame.  The offset keeps 32 fractional bits before rounding
+// to FP32.
 __device__ __forceinline__ void split_coord(double v, int& c, float& f) {
   const double magic = 98304.0;  // 1.5 * 2^16
-  double t = v + magic;
-  unsigned long long bits = (unsigned long long)__double_as_longlong(t);
+  const double t = v + magic;
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(t);
+  if ((bits >> 52) != 1039ull) {  // sign 0, biased exponent 1023 + 16
+    c = kOffFrame;
+    f = 0.f;
+    return;
+  }
   unsigned long long m = bits & 0xFFFFFFFFFFFFFull;  // (v + 2^15) * 2^36
   m += (1ull << 35);                                   // + 1/2 pixel
   c = (int)(m >> 36) - 32768;
-  long long frac = (long long)(m & 0xFFFFFFFFFull) - (1ll << 35);  // in [-2^35, 2^35)
-  f = (float)(int)(frac >> 4) * 2.3283064365386963e-10f;           // * 2^-32
+  const long long frac = (long long)(m & 0xFFFFFFFFFull) - (1ll << 35);  // in [-2^35, 2^35)
+  f = (float)(int)(frac >> 4) * 2.3283064365386963e-10f;                 // * 2^-32
 }
 
-// Clamp a mapped coordinate into the range split_coord handles (far off-frame stamps
-// are dropped anyway; the clamp keeps their windows off-frame).
+// Clamp a mapped coordinate for the plain FP64 renderer (far off-frame stamps are dropped).
 __device__ __forceinline__ double clamp_coord(double v) {
   return fmin(fmax(v, -16000.0), 16000.0);
+}
+
+// x(s) = sum_b P_b s^b by Horner in s, for the (uniform) degree d: straight-line FMAs.
+__device__ __forceinline__ double horner_s(const double* P, int d, double s) {
+  switch (d) {
+    case 0: return P[0];
+    case 1: return fma(P[1], s, P[0]);
+    case 2: return fma(fma(P[2], s, P[1]), s, P[0]);
+    case 3: return fma(fma(fma(P[3], s, P[2]), s, P[1]), s, P[0]);
+    case 4: return fma(fma(fma(fma(P[4], s, P[3]), s, P[2]), s, P[1]), s, P[0]);
+    case 5: return fma(fma(fma(fma(fma(P[5], s, P[4]), s, P[3]), s, P[2]), s, P[1]), s, P[0]);
+    case 6: return fma(fma(fma(fma(fma(fma(P[6], s, P[5]), s, P[4]), s, P[3]), s, P[2]), s, P[1]), s, P[0]);
+    case 7:
+      return fma(fma(fma(fma(fma(fma(fma(P[7], s, P[6]), s, P[5]), s, P[4]), s, P[3]), s, P[2]), s, P[1]), s, P[0]);
+    default:
+      return fma(fma(fma(fma(fma(fma(fma(fma(P[8], s, P[7]), s, P[6]), s, P[5]), s, P[4]), s, P[3]), s, P[2]), s,
+                     P[1]),
+                 s, P[0]);
+  }
 }
 
 }  // namespace e2e

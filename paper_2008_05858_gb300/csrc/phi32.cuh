@@ -1,14 +1,15 @@
-// FP32 Gaussian tail erfc(|u|) for a double-float argument u = uh + ul.
+// FP32 Gaussian tail for a double-float argument, in log2 units.
 //
 // A stamp's pixel integrals are differences of the normal CDF at the pixel edges (the
-// pixel-integrated PSF of Sec. 2.2).  In FP32 the edge argument u = (edge - centre)/(sqrt2
-// sigma) carries a relative error of ~1e-7, which the factor exp(-u^2) amplifies by 2u^2
-// (1e-6 at u = 2).  So u is kept as a double-float and the exponent is formed exactly:
+// pixel-integrated PSF of Sec. 2.2).  In FP32 an edge argument carries a relative error of
+// ~1e-7, which the factor exp(-a^2) amplifies by 2a^2 (1e-6 at a = 2), so the kernels keep
+// the argument as a double-float and form the exponent exactly.  The argument is scaled by
+// sqrt(log2 e): with w = a sqrt(log2 e),
 //
-//   erfc(a) = exp(-a^2) * erfcx(a),        a = |u|
-//   exp(-a^2) = 2^(zh + zl),  zh + zl = -(a^2) log2(e) to ~2^-48 (FMA error terms),
-//   2^zh by the SFU (ex2.approx, 2.4 ulp measured), 2^zl ~= 1 + zl ln2 (|zl| < 1e-5),
-//   erfcx(a) by the rational P4/Q5 of tail_coeffs.h (fit error 2e-9; rcp.approx on the SFU).
+//   erfc(a) = 2^(-w^2) * erfcx(w / sqrt(log2 e)),
+//   w^2 = p + e exactly to ~2^-48 (FMA error terms), 2^(-p) on the SFU (ex2.approx,
+//   2.4 ulp measured), 2^(-e) ~= 1 - e ln2 (|e| < 1e-5),
+//   erfcx by the rational P4/Q5 of tail_coeffs.h (fit error 2e-9; rcp.approx on the SFU).
 //
 // Worst-case relative error is a few FP32 ulp for every a, independent of a (no 2a^2
 // amplification); the test-suite checks it against CUDA's FP64 erfc on the GPU.
@@ -29,21 +30,13 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
-// erfc(|uh + ul|), |ul| <= ulp(uh).
-__device__ __forceinline__ float erfc_df(float uh, float ul) {
-  const float a = fabsf(uh);
-  const float al = uh < 0.f ? -ul : ul;  // a + al = |u|
-  const float p = a * a;
-  float e = fmaf(a, a, -p);             // exact error of p
-  e = fmaf(a + a, al, e);               // + 2 a al  (al^2 negligible)
-  const float L = -1.44269502163f;      // -log2(e), FP32 part
-  const float Llo = -1.925963e-08f;     // -log2(e) - L
-  const float zh = p * L;
-  float zl = fmaf(p, L, -zh);
-  zl = fmaf(p, Llo, zl);
-  zl = fmaf(e, L, zl);
-  const float ex = ex2_approx(zh) * fmaf(zl, 0.693147181f, 1.f);
-  const float x = fminf(a, 30.f);
+// erfc(|w| / sqrt(log2 e)) for w = wh + wl, |wl| <= a few ulp(wh).
+__device__ __forceinline__ float tail2(float wh, float wl) {
+  const float p = wh * wh;
+  float e = fmaf(wh, wh, -p);      // exact error of p
+  e = fmaf(wh + wh, wl, e);        // + 2 wh wl  (wl^2 negligible)
+  const float ex = ex2_approx(-p) * fmaf(e, -0.693147181f, 1.f);
+  const float x = fminf(fabsf(wh), 40.f);
   float P = kTailP4;
   P = fmaf(P, x, kTailP3);
   P = fmaf(P, x, kTailP2);
@@ -58,21 +51,28 @@ __device__ __forceinline__ float erfc_df(float uh, float ul) {
   return (ex * P) * rcp_approx(Q);
 }
 
-// Twice the probability that a standard normal lies between two edges, from the edges'
-// signed arguments ta <= tb and their tails Ea = erfc(|ta|), Eb = erfc(|tb|): on one side
-// of the mean a difference of the (small) tails, across the mean 2 minus both tails.
-__device__ __forceinline__ float twice_interval(float ta, float tb, float ea, float eb) {
-  return ta >= 0.f ? ea - eb : (tb <= 0.f ? eb - ea : 2.f - ea - eb);
+// erf(|w| / sqrt(log2 e)) for |w| <= kErfMaxArg (odd polynomial, ~1.7 ulp): near the window
+// centre the pixel integrals are sums and differences of erf, which do not cancel there the
+// way differences of erfc values close to 1 do.
+__device__ __forceinline__ float erf_small(float w) {
+  const float a = fabsf(w);
+  const float z = a * a;
+  float S = kErfS4;
+  S = fmaf(S, z, kErfS3);
+  S = fmaf(S, z, kErfS2);
+  S = fmaf(S, z, kErfS1);
+  S = fmaf(S, z, kErfS0);
+  return a * S;
 }
 
-// Edge argument as a double-float: u = (e - f) * g with e a half-integer (exact), f the
-// FP32 sub-pixel offset, g = gh + gl = 1/(sqrt2 sigma).  e - f is split exactly
-// (|e| >= 1/2 >= |f|, so Fast2Sum applies); the product keeps its FMA error term.
-__device__ __forceinline__ void edge_arg(float e, float f, float gh, float gl, float& uh, float& ul) {
+// Edge argument as a double-float: w = (e - f) * g with e a half-integer (exact), f the
+// FP32 sub-pixel offset, g = gh + gl.  e - f is split exactly (|e| >= 1/2 >= |f|, so
+// Fast2Sum applies); the product keeps its FMA error term.
+__device__ __forceinline__ void edge_arg(float e, float f, float gh, float gl, float& wh, float& wl) {
   const float dh = e - f;
   const float dl = (e - dh) - f;
-  uh = dh * gh;
-  ul = fmaf(dh, gh, -uh) + fmaf(dh, gl, dl * gh);
+  wh = dh * gh;
+  wl = fmaf(dh, gh, -wh) + fmaf(dh, gl, dl * gh);
 }
 
 }  // namespace e2e

@@ -24,23 +24,19 @@ namespace e2e {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+constexpr int kPairs = kThreads / 2;
 
-// Horner in s over the per-sample coefficients P_b(lt), b = 0..d (same sequence of FMAs
-// in the plan and the render, so both see identical window origins).
-__device__ __forceinline__ double horner_s(const double* P, int d, double s) {
-  double x = 0.0;
-#pragma unroll
-  for (int b = 8; b >= 0; --b)
-    if (b <= d) x = fma(x, s, P[b]);
-  return x;
-}
+// Normalised coordinate of bin-centred sample j of n, (2j + 1 - n) / n, as a product with the
+// correctly rounded reciprocal (the plan and the render compute it identically).
+__device__ __forceinline__ double norm_sample_r(int j, int n, double inv_n) { return (double)(2 * j + 1 - n) * inv_n; }
 
 // ------------------------------------------------------------------------------ plan
 
 // One thread per (slice, wavelength sample j, block of 16 slit points): map the stamps
 // exactly as the render will, and record (a) per (32-sample block, 16-point block) of each
 // slice the bounding box of the stamps' windows, (b) per slice the largest spread of window
-// origins over any aligned run of B = 1, 2, 4, 8, 16 consecutive slit points.
+// origins over any aligned run of B = 1, 2, 4, 8, 16 consecutive slit points.  Stamps that
+// map off every detector (kOffFrame) are ignored.
 __global__ void k_plan(const DevSlice* __restrict__ slices, int n_slices, const int64_t* __restrict__ task_off,
                        int4* __restrict__ bbox, const int64_t* __restrict__ bbox_off,
                        int* __restrict__ spans /* [n_slices][5][2] */) {
@@ -55,7 +51,8 @@ __global__ void k_plan(const DevSlice* __restrict__ slices, int n_slices, const 
     const int nkb = (S.n_slit + 15) / 16;
     const int64_t local = t - task_off[lo];
     const int j = (int)(local / nkb), kb = (int)(local - (int64_t)j * nkb);
-    const double lt = norm_sample(j, S.n_lambda);
+    const double lt = norm_sample_r(j, S.n_lambda, 1.0 / (double)S.n_lambda);
+    const double inv_ns = 1.0 / (double)S.n_slit;
     double px[9], py[9];
 #pragma unroll
     for (int b = 0; b <= 8; ++b) {
@@ -68,30 +65,39 @@ __global__ void k_plan(const DevSlice* __restrict__ slices, int n_slices, const 
     for (int q = 0; q < 5; ++q) { rxmn[q] = rymn[q] = 1 << 30; rxmx[q] = rymx[q] = -(1 << 30); spx[q] = spy[q] = 0; }
     const int k0 = kb * 16, k1 = min(k0 + 16, S.n_slit);
     for (int k = k0; k < k1; ++k) {
-      const double s = norm_sample(k, S.n_slit);
+      const double s = norm_sample_r(k, S.n_slit, inv_ns);
       int ci, ri;
       float fx, fy;
-      split_coord(clamp_coord(horner_s(px, S.degree, s)), ci, fx);
-      split_coord(clamp_coord(horner_s(py, S.degree, s)), ri, fy);
-      xmn = min(xmn, ci); xmx = max(xmx, ci); ymn = min(ymn, ri); ymx = max(ymx, ri);
+      split_coord(horner_s(px, S.degree, s), ci, fx);
+      split_coord(horner_s(py, S.degree, s), ri, fy);
+      const bool on = ci != kOffFrame && ri != kOffFrame;
+      if (on) {
+        xmn = min(xmn, ci); xmx = max(xmx, ci); ymn = min(ymn, ri); ymx = max(ymx, ri);
+      }
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
         const int B = 1 << q;
-        rxmn[q] = min(rxmn[q], ci); rxmx[q] = max(rxmx[q], ci);
-        rymn[q] = min(rymn[q], ri); rymx[q] = max(rymx[q], ri);
+        if (on) {
+          rxmn[q] = min(rxmn[q], ci); rxmx[q] = max(rxmx[q], ci);
+          rymn[q] = min(rymn[q], ri); rymx[q] = max(rymx[q], ri);
+        }
         if (((k + 1) % B) == 0 || k + 1 == k1) {  // end of an aligned run
-          spx[q] = max(spx[q], rxmx[q] - rxmn[q]);
-          spy[q] = max(spy[q], rymx[q] - rymn[q]);
+          if (rxmx[q] >= rxmn[q]) {
+            spx[q] = max(spx[q], rxmx[q] - rxmn[q]);
+            spy[q] = max(spy[q], rymx[q] - rymn[q]);
+          }
           rxmn[q] = rymn[q] = 1 << 30; rxmx[q] = rymx[q] = -(1 << 30);
         }
       }
     }
-    const int h = S.K / 2;
-    int4* bb = bbox + bbox_off[lo] + (int64_t)(j / 32) * nkb + kb;
-    atomicMin(&bb->x, xmn - h);
-    atomicMax(&bb->y, xmx + h);
-    atomicMin(&bb->z, ymn - h);
-    atomicMax(&bb->w, ymx + h);
+    if (xmx >= xmn) {
+      const int h = S.K / 2;
+      int4* bb = bbox + bbox_off[lo] + (int64_t)(j / 32) * nkb + kb;
+      atomicMin(&bb->x, xmn - h);
+      atomicMax(&bb->y, xmx + h);
+      atomicMin(&bb->z, ymn - h);
+      atomicMax(&bb->w, ymx + h);
+    }
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
       atomicMax(&spans[(lo * 5 + q) * 2 + 0], spx[q]);
@@ -109,29 +115,61 @@ struct MixedArgs {
   const Item* items;
   double* store;
   int B;        // slit points per run
-  int JB;       // 32-sample blocks per item
+  int JB;       // largest number of 32-sample blocks in an item
+  int nk_max;   // largest number of slit points in an item
   int max_deg;  // largest degree among the launched slices
 };
 
-constexpr int kSplit = 22;  // fixed point: value * 2^P = hi * 2^22 + lo, lo in [0, 2^22)
+// Shared-memory layout of one CTA (offsets in bytes), identical on host and device.
+struct MixedLayout {
+  size_t tabP, tabS, tabW, tabU, tabG, stage, boxh, boxl, total;
+  __host__ __device__ MixedLayout(int J, int NK, int nd, int B, int area) {
+    size_t o = 0;
+    tabP = o; o += (size_t)J * 2 * nd * 8;   // P_b(lt) of x and y per sample
+    tabS = o; o += (size_t)NK * 8;            // s of each slit point
+    tabW = o; o += (size_t)J * 8;             // flux x bin width / 4 per sample, (hi, lo) floats
+    tabU = o; o += (size_t)NK * 8;            // slit weights, (hi, lo) floats
+    o = (o + 15) & ~(size_t)15;
+    tabG = o; o += (size_t)J * 16;            // 1/(sqrt2 sigma) of x and y, (hi, lo) each
+    stage = o; o += (size_t)B * kPairs * 16;  // mapped stamps of the runs in flight
+    boxh = o; o += (size_t)area * 4;          // fixed-point box, high words
+    boxl = o; o += (size_t)area * 4;          // low words
+    total = o;
+  }
+};
+
+__device__ __forceinline__ float2 split_df(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
+// Two CTAs per SM (128 registers) when a lane's accumulator tile is small enough, else one.
+template <int K, int DX, int DY>
+constexpr int mixed_min_blocks() {
+  return (K + DX) * ((K + DY + 1) / 2) <= 84 ? 2 : 1;
+}
 
 template <int K, int DX, int DY>
-__global__ void __launch_bounds__(kThreads) k_render_mixed(const MixedArgs a) {
+__global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_render_mixed(const MixedArgs a) {
   constexpr int RX = K + DX, RY = K + DY, H = K / 2;
+  constexpr int D = DX > DY ? DX : DY;  // slack of the profile a lane evaluates
+  constexpr int R = K + D;              // pixels of that profile
+  constexpr int RYH = (RY + 1) / 2;     // tile rows accumulated per lane of a pair
   extern __shared__ __align__(16) unsigned char smem[];
   const Item it = a.items[blockIdx.x];
   const DevSlice& S = a.slices[it.slice];
   const int area = it.bw * it.bh;
-  const int J = 32 * a.JB;
   const int nd = S.degree + 1;
-  // shared layout: per-sample tables | run staging | box hi words | box lo words
-  double* tabP = reinterpret_cast<double*>(smem);  // [J][2][nd]
-  double* tabW = tabP + (size_t)J * 2 * nd;         // [J] flux x bin width / 4
-  float4* tabG = reinterpret_cast<float4*>(tabW + J);  // [J] (gx hi, gx lo, gy hi, gy lo), g = 1/(sqrt2 sigma)
-  int4* stage = reinterpret_cast<int4*>(tabG + J);  // [B][kThreads]
-  int* boxh = reinterpret_cast<int*>(stage + (size_t)a.B * kThreads);
-  unsigned* boxl = reinterpret_cast<unsigned*>(boxh + area);
-  __shared__ double s_red[kWarps];
+  const MixedLayout L(32 * a.JB, a.nk_max, a.max_deg + 1, a.B, area);
+  double* tabP = reinterpret_cast<double*>(smem + L.tabP);
+  double* tabS = reinterpret_cast<double*>(smem + L.tabS);
+  float2* tabW = reinterpret_cast<float2*>(smem + L.tabW);
+  float2* tabU = reinterpret_cast<float2*>(smem + L.tabU);
+  float4* tabG = reinterpret_cast<float4*>(smem + L.tabG);
+  int4* stage = reinterpret_cast<int4*>(smem + L.stage);
+  int* boxh = reinterpret_cast<int*>(smem + L.boxh);
+  unsigned* boxl = reinterpret_cast<unsigned*>(smem + L.boxl);
+  __shared__ double s_w[kWarps], s_u[kWarps];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int p = tid; p < area; p += kThreads) {
@@ -140,146 +178,193 @@ __global__ void __launch_bounds__(kThreads) k_render_mixed(const MixedArgs a) {
   }
   const double* flux = a.flux_tab[S.flux_slot];
   const double* u = a.u_all + S.u_off;
-  for (int q = tid; q < it.nj * 2 * nd; q += kThreads) {
-    const int jj = q / (2 * nd), r = q - jj * 2 * nd, axis = r / nd, b = r - axis * nd;
-    const double lt = norm_sample(it.j0 + jj, S.n_lambda);
-    tabP[q] = poly_lt_for_b(axis ? S.cy : S.cx, S.degree, b, lt);
-  }
-  // flux bound of the item: sum over its stamps of |w| (bounds every pixel of its box)
+  const double inv_nl = 1.0 / (double)S.n_lambda, inv_ns = 1.0 / (double)S.n_slit;
   double usum = 0.0;
-  for (int k = lane; k < it.nk; k += 32) usum += fabs(u[it.k0 + k]);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) usum += __shfl_xor_sync(0xffffffffu, usum, o);
+  for (int kk = tid; kk < it.nk; kk += kThreads) {
+    const double uk = u[it.k0 + kk];
+    tabS[kk] = norm_sample_r(it.k0 + kk, S.n_slit, inv_ns);
+    tabU[kk] = split_df(uk);
+    usum += fabs(uk);
+  }
   double wsum = 0.0;
   for (int jj = tid; jj < it.nj; jj += kThreads) {
-    const double lt = norm_sample(it.j0 + jj, S.n_lambda);
+    const double lt = norm_sample_r(it.j0 + jj, S.n_lambda, inv_nl);
+    for (int b = 0; b < nd; ++b) {
+      tabP[(jj * 2 + 0) * nd + b] = poly_lt_for_b(S.cx, S.degree, b, lt);
+      tabP[(jj * 2 + 1) * nd + b] = poly_lt_for_b(S.cy, S.degree, b, lt);
+    }
+    // edge arguments are carried in log2 units: w = (edge - centre) sqrt(log2 e) / (sqrt2 sigma)
     const double sgx = fma(fma(S.sx[2], lt, S.sx[1]), lt, S.sx[0]);
     const double sgy = fma(fma(S.sy[2], lt, S.sy[1]), lt, S.sy[0]);
-    const double gx = 0.70710678118654752440 / sgx, gy = 0.70710678118654752440 / sgy;
-    const float gxh = (float)gx, gyh = (float)gy;
-    tabG[jj] = make_float4(gxh, (float)(gx - (double)gxh), gyh, (float)(gy - (double)gyh));
+    const double kq = kSqrtLog2eD * 0.70710678118654752440;
+    const float2 gx = split_df(kq / sgx), gy = split_df(kq / sgy);
+    tabG[jj] = make_float4(gx.x, gx.y, gy.x, gy.y);
     const double wj = flux[it.j0 + jj] * S.dlam;
-    tabW[jj] = wj * 0.25;  // 0.25: the profiles below are 2x the pixel integrals
+    tabW[jj] = split_df(wj * 0.25);  // 0.25: the profiles below are 2x the pixel integrals
     wsum += fabs(wj);
   }
+  // flux bound of the item: sum over its stamps of |w| (bounds every pixel of its box)
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
-  if (lane == 0) s_red[warp] = wsum;
+  for (int o = 16; o > 0; o >>= 1) {
+    wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+    usum += __shfl_xor_sync(0xffffffffu, usum, o);
+  }
+  if (lane == 0) {
+    s_w[warp] = wsum;
+    s_u[warp] = usum;
+  }
   __syncthreads();
-  double total = 0.0;
+  double wtot = 0.0, utot = 0.0;
 #pragma unroll
-  for (int q = 0; q < kWarps; ++q) total += s_red[q];
-  total *= usum;
+  for (int q = 0; q < kWarps; ++q) {
+    wtot += s_w[q];
+    utot += s_u[q];
+  }
+  const double total = wtot * utot;
   // scale 2^P with |box sums| <= total < 2^(52-P); clamp so 2^P stays a normal FP32
   int ex = 0;
   frexp(total, &ex);
-  const int P = total > 0.0 ? max(-100, min(100, 52 - ex)) : 0;
-  const float sc = ldexpf(1.f, P), sc_hi = ldexpf(1.f, P - kSplit);
+  const int Psh = total > 0.0 ? max(-100, min(100, 52 - ex)) : 0;
+  const float sc = ldexpf(1.f, Psh), sc_hi = ldexpf(1.f, Psh - 22);
 
+  // A lane pair owns one run: lane 0 evaluates the x profile, lane 1 the y profile (same
+  // code, different inputs), they swap profiles by shuffle, and each accumulates half of
+  // the tile's rows.
+  const int q = lane >> 1, par = lane & 1;
   const int nrc = (it.nk + a.B - 1) / a.B;
-  const int jbs = (it.nj + 31) / 32;  // 32-sample blocks of this item (<= a.JB)
-  const int ntask = jbs * nrc;
+  const int njh = (it.nj + 15) / 16;
+  const int ntask = njh * nrc;
+  int4* mystage = stage + warp * 16 + q;
   for (int task = warp; task < ntask && total > 0.0; task += kWarps) {
-    const int jj = (task % jbs) * 32 + lane;
-    if (jj >= it.nj) continue;
-    const int k0 = it.k0 + (task / jbs) * a.B;
-    const int nb = min(a.B, it.k0 + it.nk - k0);
-    double px[9], py[9];
+    const int jj = (task % njh) * 16 + q;
+    const bool jvalid = jj < it.nj;      // uniform over the pair
+    const int kk0 = (task / njh) * a.B;  // first slit point of the run, relative to the item
+    const int nb = min(a.B, it.nk - kk0);
+    // map the run's stamps (FP64), half each, into the staging area
+    {
+      double px[9], py[9];
 #pragma unroll
-    for (int b = 0; b <= 8; ++b) {
-      px[b] = b < nd ? tabP[(jj * 2 + 0) * nd + b] : 0.0;
-      py[b] = b < nd ? tabP[(jj * 2 + 1) * nd + b] : 0.0;
+      for (int b = 0; b <= 8; ++b) {
+        px[b] = (jvalid && b < nd) ? tabP[(jj * 2 + 0) * nd + b] : 0.0;
+        py[b] = (jvalid && b < nd) ? tabP[(jj * 2 + 1) * nd + b] : 0.0;
+      }
+      for (int b = par; b < nb; b += 2) {
+        int ci = kOffFrame, ri = kOffFrame;
+        float fx = 0.f, fy = 0.f;
+        if (jvalid) {
+          const double s = tabS[kk0 + b];
+          split_coord(horner_s(px, S.degree, s), ci, fx);
+          split_coord(horner_s(py, S.degree, s), ri, fy);
+        }
+        mystage[b * kPairs] = make_int4(ci, ri, __float_as_int(fx), __float_as_int(fy));
+      }
     }
+    __syncwarp();
     int xmn = 1 << 30, ymn = 1 << 30;
     for (int b = 0; b < nb; ++b) {
-      const double s = norm_sample(k0 + b, S.n_slit);
-      int ci, ri;
-      float fx, fy;
-      split_coord(clamp_coord(horner_s(px, S.degree, s)), ci, fx);
-      split_coord(clamp_coord(horner_s(py, S.degree, s)), ri, fy);
-      xmn = min(xmn, ci);
-      ymn = min(ymn, ri);
-      stage[b * kThreads + tid] = make_int4(ci, ri, __float_as_int(fx), __float_as_int(fy));
+      const int4 st = mystage[b * kPairs];
+      if (st.x != kOffFrame && st.y != kOffFrame) {
+        xmn = min(xmn, st.x);
+        ymn = min(ymn, st.y);
+      }
     }
-    const float4 g = tabG[jj];
-    const double wj = tabW[jj];
-    float acc[RY][RX];
+    const float4 g4 = jvalid ? tabG[jj] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float gh = par ? g4.z : g4.x, gl = par ? g4.w : g4.y;
+    const float2 wj = jvalid ? tabW[jj] : make_float2(0.f, 0.f);
+    float acc[RYH][RX];
 #pragma unroll
-    for (int r = 0; r < RY; ++r)
+    for (int r = 0; r < RYH; ++r)
 #pragma unroll
       for (int c = 0; c < RX; ++c) acc[r][c] = 0.f;
     for (int b = 0; b < nb; ++b) {
-      const int4 st = stage[b * kThreads + tid];
-      const int ox = st.x - xmn, oy = st.y - ymn;  // 0..DX, 0..DY
-      const float fx = __int_as_float(st.z), fy = __int_as_float(st.w);
-      const float w = (float)(wj * u[k0 + b]);
-      float wax[RX], ay[RY];
-      {
-        float th, tl;
-        edge_arg((float)(-ox - H) - 0.5f, fx, g.x, g.y, th, tl);
-        float ep = erfc_df(th, tl), tp = th;
+      const int4 st = mystage[b * kPairs];
+      const bool on = st.x != kOffFrame && st.y != kOffFrame;
+      const int o = on ? (par ? st.y - ymn : st.x - xmn) : 0;  // window offset in the tile, 0..D
+      const float f = __int_as_float(par ? st.w : st.z);
+      const float2 uk = tabU[kk0 + b];
+      const float w = on ? fmaf(wj.x, uk.x, fmaf(wj.x, uk.y, wj.y * uk.x)) : 0.f;
+      const float mult = par ? (on ? 1.f : 0.f) : w;  // the weight rides on the x profile
+      const float of = (float)o;
+      // edge tails E = erfc(|w|), and near the centre also F = erf(|w|)
+      constexpr int F0 = H >= 1 ? H - 1 : 0, F1 = (H + D + 2 < R) ? H + D + 2 : R;
+      float E[R + 1], F[R + 1];
+#pragma unroll
+      for (int c = 0; c <= R; ++c) {
+        float wh, wl;
+        edge_arg((float)(c - H) - 0.5f - of, f, gh, gl, wh, wl);
+        E[c] = tail2(wh, wl);
+        if (c >= F0 && c <= F1) F[c] = fabsf(wh) < kErfMaxArg ? erf_small(wh) : 1.f - E[c];
+      }
+      // twice the pixel integrals: away from the window centre the difference of the two
+      // edges' tails; for the centre pixel (cs) and its neighbours sums and differences of
+      // erf; pixels outside the stamp's window (tile slack) are zero
+      const int cs = o + H;
+      float prof[R];
+#pragma unroll
+      for (int c = 0; c < R; ++c) {
+        float v;
+        if (c < H - 1) {
+          v = E[c + 1] - E[c];
+        } else if (c > H + D + 1) {
+          v = E[c] - E[c + 1];
+        } else {
+          const float tl = E[c + 1] - E[c], tr = E[c] - E[c + 1];
+          const float fl = F[c] - F[c + 1], fc = F[c] + F[c + 1], fr = F[c + 1] - F[c];
+          v = c < cs - 1 ? tl : (c == cs - 1 ? fl : (c == cs ? fc : (c == cs + 1 ? fr : tr)));
+        }
+        bool valid = true;
+        if (c < D) valid = c >= o;
+        if (c >= K) valid = valid && (c - K < o);
+        prof[c] = valid ? mult * v : 0.f;
+      }
+      float ax[RX], ay[RYH];
+#pragma unroll
+      for (int c = 0; c < R; ++c) {
+        const float other = __shfl_xor_sync(0xffffffffu, prof[c], 1);
+        if (c < RX) ax[c] = par ? other : prof[c];
+        if (c < RYH) ay[c] = par ? 0.f : other;  // lane 0: rows 0..RYH-1 of lane 1's y profile
+      }
+#pragma unroll
+      for (int i = 0; i < RYH; ++i)
+        if (RYH + i < RY) ay[i] = par ? prof[RYH + i] : ay[i];  // lane 1: its own rows RYH..RY-1
+#pragma unroll
+      for (int r = 0; r < RYH; ++r)
+#pragma unroll
+        for (int c = 0; c < RX; ++c) acc[r][c] = fmaf(ay[r], ax[c], acc[r][c]);
+    }
+    __syncwarp();  // the staging is reused by the next task
+    // flush this lane's rows of the run tile as exact fixed-point increments
+    if (xmn != (1 << 30)) {
+      const int gx0 = xmn - H - it.bx0, gy0 = ymn - H - it.by0 + par * RYH;
+      const int nrow = min(RYH, RY - par * RYH);
+      const bool inside = gx0 >= 0 && gx0 + RX <= it.bw && gy0 >= 0 && gy0 + nrow <= it.bh;
+#pragma unroll
+      for (int r = 0; r < RYH; ++r) {
+        const int gy = gy0 + r;
+        if (r >= nrow || (!inside && (gy < 0 || gy >= it.bh))) continue;
+        int* rowh = boxh + gy * it.bw + gx0;
+        unsigned* rowl = boxl + gy * it.bw + gx0;
 #pragma unroll
         for (int c = 0; c < RX; ++c) {
-          edge_arg((float)(c + 1 - ox - H) - 0.5f, fx, g.x, g.y, th, tl);
-          const float en = erfc_df(th, tl);
-          const float v = twice_interval(tp, th, ep, en);
-          wax[c] = (c >= ox && c < ox + K) ? w * v : 0.f;
-          tp = th;
-          ep = en;
-        }
-      }
-      {
-        float th, tl;
-        edge_arg((float)(-oy - H) - 0.5f, fy, g.z, g.w, th, tl);
-        float ep = erfc_df(th, tl), tp = th;
-#pragma unroll
-        for (int r = 0; r < RY; ++r) {
-          edge_arg((float)(r + 1 - oy - H) - 0.5f, fy, g.z, g.w, th, tl);
-          const float en = erfc_df(th, tl);
-          const float v = twice_interval(tp, th, ep, en);
-          ay[r] = (r >= oy && r < oy + K) ? v : 0.f;
-          tp = th;
-          ep = en;
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < RY; ++r)
-#pragma unroll
-        for (int c = 0; c < RX; ++c) acc[r][c] = fmaf(ay[r], wax[c], acc[r][c]);
-    }
-    // flush the run tile into the box as exact fixed-point increments
-    const int gx0 = xmn - H - it.bx0, gy0 = ymn - H - it.by0;
-#pragma unroll
-    for (int r = 0; r < RY; ++r) {
-      const int gy = gy0 + r;
-      if (gy < 0 || gy >= it.bh) continue;
-#pragma unroll
-      for (int c = 0; c < RX; ++c) {
-        const int gxp = gx0 + c;
-        const float v = acc[r][c];
-        if (gxp >= 0 && gxp < it.bw && v != 0.f) {
-          const float hf = floorf(v * sc_hi);
-          const float lf = fmaf(-hf, 4194304.f, v * sc);
-          atomicAdd(boxh + gy * it.bw + gxp, __float2int_rz(hf));
-          atomicAdd(boxl + gy * it.bw + gxp, __float2uint_rn(lf));
+          if (!inside && (gx0 + c < 0 || gx0 + c >= it.bw)) continue;
+          const float val = acc[r][c];
+          const float hf = floorf(val * sc_hi);
+          const float lf = fmaf(-hf, 4194304.f, val * sc);
+          atomicAdd(rowh + c, __float2int_rz(hf));
+          atomicAdd(rowl + c, __float2uint_rn(lf));
         }
       }
     }
   }
   __syncthreads();
   double* out = a.store + it.store_off;
-  const double inv = ldexp(1.0, -P);
+  const double inv = ldexp(1.0, -Psh);
   for (int p = tid; p < area; p += kThreads)
-    out[p] = fma((double)boxh[p], 4194304.0, (double)boxl[p]) * inv;
+    out[p] = __ll2double_rn(((long long)boxh[p] << 22) + (long long)boxl[p]) * inv;
 }
 
-size_t mixed_smem_bytes(int area, int JB, int B, int nd) {
-  const int J = 32 * JB;
-  size_t bytes = (size_t)J * 2 * nd * 8 + (size_t)J * 8 + (size_t)J * 16;
-  bytes = (bytes + 15) & ~(size_t)15;
-  bytes += (size_t)B * kThreads * 16;
-  bytes += (size_t)area * 8;
-  return bytes;
+size_t mixed_smem_bytes(int area, int JB, int nk_max, int B, int nd) {
+  return MixedLayout(32 * JB, nk_max, nd, B, area).total;
 }
 
 // ------------------------------------------------------------------------------ merge
@@ -348,21 +433,23 @@ bool mixed_variant_supported(int K, int DX, int DY) {
   if (K < 1 || K > 15 || (K % 2) == 0) return false;
   if (DX == 0 && DY == 0) return true;
   if (DX == 1 && DY == 1) return K <= 13;
-  if (DX == 2 && DY == 2) return K <= 11;
+  if (DX == 1 && DY == 2) return K <= 13;
+  if (DX == 2 && DY == 2) return K <= 9;
   return false;
 }
 
 cudaError_t launch_render_mixed(int K, int DX, int DY, const DevSlice* slices, const double* const* flux_tab,
                                 const double* u_all, const Item* items, int n_items, double* store, int B, int JB,
-                                int max_deg, size_t smem, cudaStream_t st) {
+                                int nk_max, int max_deg, size_t smem, cudaStream_t st) {
   if (n_items == 0) return cudaSuccess;
-  MixedArgs a{slices, flux_tab, u_all, items, store, B, JB, max_deg};
+  MixedArgs a{slices, flux_tab, u_all, items, store, B, JB, nk_max, max_deg};
 #define E2E_V(KK, X, Y) \
   if (K == KK && DX == X && DY == Y) return launch_one<KK, X, Y>(a, n_items, smem, st);
   E2E_V(1, 0, 0) E2E_V(3, 0, 0) E2E_V(5, 0, 0) E2E_V(7, 0, 0) E2E_V(9, 0, 0) E2E_V(11, 0, 0) E2E_V(13, 0, 0)
   E2E_V(15, 0, 0)
   E2E_V(1, 1, 1) E2E_V(3, 1, 1) E2E_V(5, 1, 1) E2E_V(7, 1, 1) E2E_V(9, 1, 1) E2E_V(11, 1, 1) E2E_V(13, 1, 1)
-  E2E_V(1, 2, 2) E2E_V(3, 2, 2) E2E_V(5, 2, 2) E2E_V(7, 2, 2) E2E_V(9, 2, 2) E2E_V(11, 2, 2)
+  E2E_V(1, 1, 2) E2E_V(3, 1, 2) E2E_V(5, 1, 2) E2E_V(7, 1, 2) E2E_V(9, 1, 2) E2E_V(11, 1, 2) E2E_V(13, 1, 2)
+  E2E_V(1, 2, 2) E2E_V(3, 2, 2) E2E_V(5, 2, 2) E2E_V(7, 2, 2) E2E_V(9, 2, 2)
 #undef E2E_V
   return cudaErrorInvalidValue;
 }

@@ -1,17 +1,26 @@
 // Generated by gen_tail_coeffs.py -- do not edit.
-// erfcx(a) ~= P(a)/Q(a) on [0, 6.5], degrees (4, 5), max relative fit error 2.01e-09
+// erfcx(w / sqrt(log2 e)) ~= P(w)/Q(w) on w in [0, 6.5 sqrt(log2 e)], degrees (4, 5), max relative fit error 2.01e-09
 #pragma once
 namespace e2e {
 constexpr float kTailP0 = 1.000000002e+00f;
-constexpr float kTailP1 = 1.196801051e+00f;
-constexpr float kTailP2 = 6.888182247e-01f;
-constexpr float kTailP3 = 2.091055320e-01f;
-constexpr float kTailP4 = 2.866942590e-02f;
+constexpr float kTailP1 = 9.964022297e-01f;
+constexpr float kTailP2 = 4.774524070e-01f;
+constexpr float kTailP3 = 1.206712217e-01f;
+constexpr float kTailP4 = 1.377431187e-02f;
 constexpr float kTailQ0 = 1.000000000e+00f;
-constexpr float kTailQ1 = 2.325180436e+00f;
-constexpr float kTailQ2 = 2.312499560e+00f;
-constexpr float kTailQ3 = 1.245580569e+00f;
-constexpr float kTailQ4 = 3.706832211e-01f;
-constexpr float kTailQ5 = 5.081347772e-02f;
-constexpr float kTailMaxArg = 6.5f;
+constexpr float kTailQ1 = 1.935839690e+00f;
+constexpr float kTailQ2 = 1.602902543e+00f;
+constexpr float kTailQ3 = 7.188032186e-01f;
+constexpr float kTailQ4 = 1.780958689e-01f;
+constexpr float kTailQ5 = 2.032556214e-02f;
+constexpr float kTailMaxArg = 7.8073f;  // largest w the fit covers
+constexpr float kSqrtLog2e = 1.201122409f;
+constexpr double kSqrtLog2eD = 1.2011224087864498;
+// erf(w / sqrt(log2 e)) ~= w * S(w^2) for |w| <= 0.70, 5 terms, max relative fit error 6.12e-09
+constexpr float kErfS0 = 9.394372730e-01f;
+constexpr float kErfS1 = -2.170555199e-01f;
+constexpr float kErfS2 = 4.512608812e-02f;
+constexpr float kErfS3 = -7.394556502e-03f;
+constexpr float kErfS4 = 8.743762265e-04f;
+constexpr float kErfMaxArg = 0.70f;
 }  // namespace e2e
