@@ -194,15 +194,16 @@ int upload(T** dptr, const T* src, size_t n) {
 
 // ------------------------------------------------------------------ planning
 
-// Relative cost per stamp of a tile variant of the lane-pair kernel: each lane evaluates a
-// profile of K + max(DX, DY) pixels (~30 FP32 operations and 2 SFU operations per edge),
-// accumulates half the (K+DX) x (K+DY) tile, and flushes its half once per run of B stamps
-// (~10 operations per pixel); tiles above 84 accumulators per lane halve the occupancy.
+// Relative cost per stamp of a tile variant of the lane-pair kernel: each lane evaluates
+// the K+1 edges of one axis of the stamp's window (~30 FP32 operations and 2 SFU operations
+// per edge), shifts it into the tile (D selects per pixel), accumulates half of the
+// (K+DX) x (K+DY) tile, and flushes its half once per run of B stamps (~10 operations per
+// pixel); tiles above 84 accumulators per lane halve the occupancy.
 double variant_cost(int K, int DX, int DY, int B) {
   const int D = std::max(DX, DY);
-  const double edges = 2.0 * (K + D + 1);
+  const double edges = 2.0 * (K + 1);
   const double tile = (double)(K + DX) * (K + DY);
-  double c = edges * 30.0 + tile + tile * 10.0 / B;
+  double c = edges * 30.0 + 2.0 * (K + D) * D + tile + tile * 10.0 / B;
   if ((K + DX) * ((K + DY + 1) / 2) > 84) c *= 1.6;
   return c;
 }
@@ -251,8 +252,8 @@ int plan_model(Model* m) {
   for (auto& s : m->slices) K = std::max(K, s.d.K);
   double best = 1e300;
   int bB = 1, bDX = 0, bDY = 0;
-  const int variants[4][2] = {{0, 0}, {1, 1}, {1, 2}, {2, 2}};
-  for (int q = 0; q <= 3; ++q) {  // B = 1..8
+  const int variants[5][2] = {{0, 0}, {1, 1}, {1, 2}, {1, 3}, {2, 2}};
+  for (int q = 0; q <= 4; ++q) {  // B = 1..16
     const int B = 1 << q;
     int sx = 0, sy = 0;
     for (int i = 0; i < ns; ++i) {
@@ -523,8 +524,8 @@ int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, in
   // mixed precision
   Plan& P = m->plan;
   if (!P.ok) return fail(E2E_EINVAL, "model has no mixed-precision plan");
-  double* store = nullptr;
-  E2E_CK(sc.get((void**)&store, (size_t)P.store_elems * 8));
+  float2* store = nullptr;
+  E2E_CK(sc.get((void**)&store, (size_t)P.store_elems * sizeof(float2)));
   for (auto& g : P.groups) {
     KernelTimer kt(ctx, st, "render_mixed");
     E2E_CK(launch_render_mixed(g.K, P.DX, P.DY, m->d_slices, d_table, m->d_u, P.d_items + g.first, g.count, store,
@@ -860,7 +861,7 @@ int e2e_render_static(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uin
   const size_t off_pitch = align256(off_table + table.size() * sizeof(double*));
   const size_t off_dst = align256(off_pitch + pitch.size() * sizeof(int64_t));
   const size_t off_store = align256(off_dst + (size_t)m->n_det * sizeof(void*));
-  const size_t need = off_store + (size_t)P.store_elems * sizeof(double);
+  const size_t need = off_store + (size_t)P.store_elems * sizeof(float2);
   if (need > E2E_STATIC_SCRATCH_BYTES)
     return fail(E2E_ETOOBIG, "model needs " + std::to_string(need) + " bytes of scratch; the fixed buffer holds " +
                                  std::to_string((size_t)E2E_STATIC_SCRATCH_BYTES));
@@ -871,7 +872,7 @@ int e2e_render_static(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uin
   const double** d_table = reinterpret_cast<const double**>(b + off_table);
   int64_t* d_pitch = reinterpret_cast<int64_t*>(b + off_pitch);
   void** d_dst = reinterpret_cast<void**>(b + off_dst);
-  double* store = reinterpret_cast<double*>(b + off_store);
+  float2* store = reinterpret_cast<float2*>(b + off_store);
   cudaStream_t st = (cudaStream_t)stream;
   if (!table.empty())
     E2E_CK(cudaMemcpyAsync(d_table, table.data(), table.size() * sizeof(double*), cudaMemcpyHostToDevice, st));

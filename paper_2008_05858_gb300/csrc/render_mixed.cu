@@ -22,7 +22,10 @@
 
 namespace e2e {
 
-constexpr int kThreads = 256;
+#ifndef E2E_MIXED_THREADS
+#define E2E_MIXED_THREADS 128
+#endif
+constexpr int kThreads = E2E_MIXED_THREADS;  // threads per render CTA
 constexpr int kWarps = kThreads / 32;
 constexpr int kPairs = kThreads / 2;
 
@@ -113,7 +116,7 @@ struct MixedArgs {
   const double* const* flux_tab;
   const double* u_all;
   const Item* items;
-  double* store;
+  float2* store;
   int B;        // slit points per run
   int JB;       // largest number of 32-sample blocks in an item
   int nk_max;   // largest number of slit points in an item
@@ -143,10 +146,39 @@ __device__ __forceinline__ float2 split_df(double v) {
   return make_float2(h, (float)(v - (double)h));
 }
 
+// a + b as an unevaluated pair (s, e), s = fl(a + b), a + b = s + e exactly (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (hi * 2^22 + lo) * scale as an FP32 pair (h, l) with h + l exact to ~2^-48: the 54-bit
+// integer is cut into four 16-bit pieces (each exact in FP32) and summed with TwoSum.
+__device__ __forceinline__ float2 fixed_to_pair(int hi, unsigned lo, float scale) {
+  const float t1 = (float)(hi >> 16) * 274877906944.f;  // 2^38
+  const float t2 = (float)(hi & 0xFFFF) * 4194304.f;    // 2^22
+  const float t3 = (float)(lo >> 16) * 65536.f;         // 2^16
+  const float t4 = (float)(lo & 0xFFFFu);
+  float s, e, e2;
+  two_sum(t1, t2, s, e);
+  two_sum(s, t3, s, e2);
+  e += e2;
+  two_sum(s, t4, s, e2);
+  e += e2;
+  return make_float2(s * scale, e * scale);
+}
+
 // Two CTAs per SM (128 registers) when a lane's accumulator tile is small enough, else one.
+#ifndef E2E_MID_TILE_BLOCKS
+#define E2E_MID_TILE_BLOCKS 4
+#endif
+// CTAs per SM the register budget is set for (128-thread CTAs): 4 (128 registers) for lane
+// tiles up to 72 accumulators, E2E_MID_TILE_BLOCKS up to 84, else 2.
 template <int K, int DX, int DY>
 constexpr int mixed_min_blocks() {
-  return (K + DX) * ((K + DY + 1) / 2) <= 84 ? 2 : 1;
+  return ((K + DX) * ((K + DY + 1) / 2) <= 72 ? 4 : ((K + DX) * ((K + DY + 1) / 2) <= 84 ? E2E_MID_TILE_BLOCKS : 2)) *
+         128 / kThreads;
 }
 
 template <int K, int DX, int DY>
@@ -284,38 +316,39 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
       const float2 uk = tabU[kk0 + b];
       const float w = on ? fmaf(wj.x, uk.x, fmaf(wj.x, uk.y, wj.y * uk.x)) : 0.f;
       const float mult = par ? (on ? 1.f : 0.f) : w;  // the weight rides on the x profile
-      const float of = (float)o;
-      // edge tails E = erfc(|w|), and near the centre also F = erf(|w|)
-      constexpr int F0 = H >= 1 ? H - 1 : 0, F1 = (H + D + 2 < R) ? H + D + 2 : R;
-      float E[R + 1], F[R + 1];
+      // Profile of the stamp's own K-pixel window, window pixel m spanning edges m and m+1
+      // at offsets (m - H -+ 1/2) - f from the stamp centre: tails E = erfc(|w|) at every
+      // edge, and erf F = erf(|w|) at the four edges around the centre pixel H.  Twice the
+      // pixel integrals are differences of left tails (m < H-1), of right tails (m > H+1),
+      // and sums / differences of erf for the centre pixel and its two neighbours.
+      float E[K + 1], F[K + 1];
 #pragma unroll
-      for (int c = 0; c <= R; ++c) {
+      for (int m = 0; m <= K; ++m) {
         float wh, wl;
-        edge_arg((float)(c - H) - 0.5f - of, f, gh, gl, wh, wl);
-        E[c] = tail2(wh, wl);
-        if (c >= F0 && c <= F1) F[c] = fabsf(wh) < kErfMaxArg ? erf_small(wh) : 1.f - E[c];
+        edge_arg((float)(m - H) - 0.5f, f, gh, gl, wh, wl);
+        E[m] = tail2(wh, wl);
+        if (m >= H - 1 && m <= H + 2) F[m] = fabsf(wh) < kErfMaxArg ? erf_small(wh) : 1.f - E[m];
       }
-      // twice the pixel integrals: away from the window centre the difference of the two
-      // edges' tails; for the centre pixel (cs) and its neighbours sums and differences of
-      // erf; pixels outside the stamp's window (tile slack) are zero
-      const int cs = o + H;
+      float win[K];
+#pragma unroll
+      for (int m = 0; m < K; ++m) {
+        float v;
+        if (m < H - 1) v = E[m + 1] - E[m];
+        else if (m == H - 1) v = F[m] - F[m + 1];
+        else if (m == H) v = F[m] + F[m + 1];
+        else if (m == H + 1) v = F[m + 1] - F[m];
+        else v = E[m] - E[m + 1];
+        win[m] = mult * v;
+      }
+      // place the window at its offset o (0..D) in the tile: prof[c] = win[c - o]
       float prof[R];
 #pragma unroll
       for (int c = 0; c < R; ++c) {
-        float v;
-        if (c < H - 1) {
-          v = E[c + 1] - E[c];
-        } else if (c > H + D + 1) {
-          v = E[c] - E[c + 1];
-        } else {
-          const float tl = E[c + 1] - E[c], tr = E[c] - E[c + 1];
-          const float fl = F[c] - F[c + 1], fc = F[c] + F[c + 1], fr = F[c + 1] - F[c];
-          v = c < cs - 1 ? tl : (c == cs - 1 ? fl : (c == cs ? fc : (c == cs + 1 ? fr : tr)));
-        }
-        bool valid = true;
-        if (c < D) valid = c >= o;
-        if (c >= K) valid = valid && (c - K < o);
-        prof[c] = valid ? mult * v : 0.f;
+        float v = 0.f;
+#pragma unroll
+        for (int d = 0; d <= D; ++d)
+          if (c - d >= 0 && c - d < K) v = (o == d) ? win[c - d] : v;
+        prof[c] = v;
       }
       float ax[RX], ay[RYH];
 #pragma unroll
@@ -357,10 +390,10 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
     }
   }
   __syncthreads();
-  double* out = a.store + it.store_off;
-  const double inv = ldexp(1.0, -Psh);
-  for (int p = tid; p < area; p += kThreads)
-    out[p] = __ll2double_rn(((long long)boxh[p] << 22) + (long long)boxl[p]) * inv;
+  // box value = (hi word * 2^22 + lo word) * 2^-P, written as an unevaluated FP32 pair
+  float2* out = a.store + it.store_off;
+  const float inv = ldexpf(1.f, -Psh);
+  for (int p = tid; p < area; p += kThreads) out[p] = fixed_to_pair(boxh[p], boxl[p], inv);
 }
 
 size_t mixed_smem_bytes(int area, int JB, int nk_max, int B, int nd) {
@@ -369,43 +402,56 @@ size_t mixed_smem_bytes(int area, int JB, int nk_max, int B, int nd) {
 
 // ------------------------------------------------------------------------------ merge
 
-// One CTA per output tile: sum, in item order and with Neumaier compensation, the FP64
-// boxes of the items overlapping the tile, convert and write every pixel once.
+// One CTA per output tile: sum, in item order, the boxes of the items overlapping the tile
+// with compensated summation (TwoSum on the FP32 pairs: Neumaier's correction carried in a
+// second word), convert and write every pixel once.  Tiles that no item touches are zeros.
 template <typename T>
 __global__ void __launch_bounds__(256) k_merge(const Tile* __restrict__ tiles, const int32_t* __restrict__ lists,
-                                               const Item* __restrict__ items, const double* __restrict__ store,
+                                               const Item* __restrict__ items, const float2* __restrict__ store,
                                                T* const* dst, const int64_t* __restrict__ pitch, const int* __restrict__ dims) {
   const Tile t = tiles[blockIdx.x];
   const int H = dims[2 * t.det], W = dims[2 * t.det + 1];
   const int tx = threadIdx.x & (kTileW - 1), ty0 = threadIdx.x / kTileW;
   constexpr int kRows = kTileW * kTileH / 256;  // pixels per thread
-  double sum[kRows], comp[kRows];
-#pragma unroll
-  for (int q = 0; q < kRows; ++q) sum[q] = comp[q] = 0.0;
+  constexpr int kStep = 256 / kTileW;
   const int x = t.x0 + tx;
+  T* frame = dst[t.det];
+  const int64_t P = pitch[t.det];
+  if (t.n == 0) {
+    if (x < W) {
+#pragma unroll
+      for (int q = 0; q < kRows; ++q) {
+        const int y = t.y0 + ty0 + q * kStep;
+        if (y < H) frame[(int64_t)y * P + x] = (T)0;
+      }
+    }
+    return;
+  }
+  float sum[kRows], comp[kRows];
+#pragma unroll
+  for (int q = 0; q < kRows; ++q) sum[q] = comp[q] = 0.f;
   for (int n = 0; n < t.n; ++n) {
     const Item it = items[lists[t.list_off + n]];
     const int gx = x - it.bx0;
     if (gx < 0 || gx >= it.bw) continue;
-    const double* box = store + it.store_off;
+    const float2* box = store + it.store_off;
 #pragma unroll
     for (int q = 0; q < kRows; ++q) {
-      const int gy = t.y0 + ty0 + q * (256 / kTileW) - it.by0;
+      const int gy = t.y0 + ty0 + q * kStep - it.by0;
       if (gy >= 0 && gy < it.bh) {
-        const double v = box[(int64_t)gy * it.bw + gx];
-        const double s = sum[q] + v;
-        comp[q] += fabs(sum[q]) >= fabs(v) ? (sum[q] - s) + v : (v - s) + sum[q];
+        const float2 v = box[(int64_t)gy * it.bw + gx];
+        float s, e;
+        two_sum(sum[q], v.x, s, e);
         sum[q] = s;
+        comp[q] += e + v.y;
       }
     }
   }
   if (x >= W) return;
-  T* frame = dst[t.det];
-  const int64_t P = pitch[t.det];
 #pragma unroll
   for (int q = 0; q < kRows; ++q) {
-    const int y = t.y0 + ty0 + q * (256 / kTileW);
-    if (y < H) frame[(int64_t)y * P + x] = (T)(sum[q] + comp[q]);
+    const int y = t.y0 + ty0 + q * kStep;
+    if (y < H) frame[(int64_t)y * P + x] = sizeof(T) == 8 ? (T)((double)sum[q] + (double)comp[q]) : (T)(sum[q] + comp[q]);
   }
 }
 
@@ -434,12 +480,13 @@ bool mixed_variant_supported(int K, int DX, int DY) {
   if (DX == 0 && DY == 0) return true;
   if (DX == 1 && DY == 1) return K <= 13;
   if (DX == 1 && DY == 2) return K <= 13;
+  if (DX == 1 && DY == 3) return K <= 11;
   if (DX == 2 && DY == 2) return K <= 9;
   return false;
 }
 
 cudaError_t launch_render_mixed(int K, int DX, int DY, const DevSlice* slices, const double* const* flux_tab,
-                                const double* u_all, const Item* items, int n_items, double* store, int B, int JB,
+                                const double* u_all, const Item* items, int n_items, float2* store, int B, int JB,
                                 int nk_max, int max_deg, size_t smem, cudaStream_t st) {
   if (n_items == 0) return cudaSuccess;
   MixedArgs a{slices, flux_tab, u_all, items, store, B, JB, nk_max, max_deg};
@@ -449,12 +496,13 @@ cudaError_t launch_render_mixed(int K, int DX, int DY, const DevSlice* slices, c
   E2E_V(15, 0, 0)
   E2E_V(1, 1, 1) E2E_V(3, 1, 1) E2E_V(5, 1, 1) E2E_V(7, 1, 1) E2E_V(9, 1, 1) E2E_V(11, 1, 1) E2E_V(13, 1, 1)
   E2E_V(1, 1, 2) E2E_V(3, 1, 2) E2E_V(5, 1, 2) E2E_V(7, 1, 2) E2E_V(9, 1, 2) E2E_V(11, 1, 2) E2E_V(13, 1, 2)
+  E2E_V(1, 1, 3) E2E_V(3, 1, 3) E2E_V(5, 1, 3) E2E_V(7, 1, 3) E2E_V(9, 1, 3) E2E_V(11, 1, 3)
   E2E_V(1, 2, 2) E2E_V(3, 2, 2) E2E_V(5, 2, 2) E2E_V(7, 2, 2) E2E_V(9, 2, 2)
 #undef E2E_V
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_merge(const Tile* tiles, int n_tiles, const int32_t* lists, const Item* items, const double* store,
+cudaError_t launch_merge(const Tile* tiles, int n_tiles, const int32_t* lists, const Item* items, const float2* store,
                          void* const* dst, int dtype, const int64_t* pitch, const int* dims, cudaStream_t st) {
   if (n_tiles == 0) return cudaSuccess;
   if (dtype == 0)
