@@ -79,7 +79,8 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.5)  # let the sampler start before the timed region
         except Exception:
             self.proc = None
         return self
@@ -297,7 +298,7 @@ def run_gpu(args):
               "kernel": "render_mixed", "pipe": "fp32", "kernel_ms": kr,
               "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (median SM clock under load)"}
     roof64 = {"bound": "alu", "achieved": a64 / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
-              "frac": a64 / fp64_peak, "kernel": "render_mixed", "pipe": "fp64",
+              "frac": a64 / fp64_peak, "traffic": traffic, "kernel": "render_mixed", "pipe": "fp64", "kernel_ms": kr,
               "peak_basis": f"{n_sm} SMs x 2 DFMA/clk (probe) x 2 x {mhz:.0f} MHz"}
     roof = roof32 if roof32["frac"] >= roof64["frac"] else roof64
     other = roof64 if roof is roof32 else roof32
@@ -347,13 +348,33 @@ def _load_spectrum_ptr(B, ctx, fiber, orders, lens, flux_tensor):
     return sid.value
 
 
+KERNEL_SOURCES = ["paper_2008_05858_gb300/csrc/render_mixed.cu", "paper_2008_05858_gb300/csrc/phi32.cuh",
+                  "paper_2008_05858_gb300/csrc/e2e_device.cuh", "paper_2008_05858_gb300/csrc/tail_coeffs.h"]
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def _load_traffic():
-    """DRAM bytes per launch of the render kernel from the committed ncu summary, if current."""
-    p = os.path.join(ROOT, "profiles", "render_mixed_traffic.json")
+    """DRAM bytes per launch of the render kernel from the committed ncu summary, or None if
+    the kernel's sources changed since those counters were taken."""
+    p = os.path.join(ROOT, "profiles", "render_mixed_traffic.txt")
     try:
-        with open(p) as f:
-            d = json.load(f)
-        return d.get("traffic_bytes_per_launch")
+        kv = {}
+        for line in open(p):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha256_16") != kernel_source_hash():
+            return None
+        return float(kv["traffic_bytes_per_launch_full_frame"])
     except Exception:
         return None
 
@@ -361,7 +382,7 @@ def _load_traffic():
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

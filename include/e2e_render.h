@@ -157,6 +157,34 @@ int e2e_fetch_frame(e2e_ctx* ctx, uint64_t frame_id, int32_t detector, void* dst
                     size_t bytes, void* stream);
 int e2e_release_frame(e2e_ctx* ctx, uint64_t frame_id);
 
+/* ------------------------------------------------------------------ differentiation */
+
+/* Gradient of a frame loss L with respect to the optical model, for calibration fitting:
+ * the vector-Jacobian product  g = sum over pixels of dL/dI * dI/dtheta  of the render of a
+ * separable-PSF model lit by spec_ids, for theta = every order-slice's mapping coefficients
+ * (cx, cy) and PSF-width coefficients (sigma_x, sigma_y).  Each stamp's window is held at the
+ * origin the forward render picks (the frame is piecewise smooth in the coefficients; its
+ * jumps where a centre crosses a pixel edge are excluded).  The pixel-integral derivatives
+ * follow from the PSF model of Sec. 2.1/2.2: dA/dx_c = -(phi(u1) - phi(u0))/sigma and
+ * dA/dsigma = -(u1 phi(u1) - u0 phi(u0))/sigma for a pixel between edges u0 < u1.
+ *   dldi[d]: device pointer to detector d's dL/dI (dtype E2E_F32 / E2E_F64, pitch_elems[d]
+ *            elements per row; pitch_elems may be NULL = width).
+ *   g_cx, g_cy: device FP64 arrays of sum over slices of (d+1)(d+2)/2 entries, the slices'
+ *            coefficient vectors concatenated in model order; g_sx, g_sy: 3 per slice.  They
+ *            are overwritten.
+ * Asynchronous on `stream`.  Errors: E2E_EINVAL (elliptical PSF, bad arguments),
+ * E2E_ENOTFOUND, E2E_ENOMEM, E2E_ECUDA. */
+int e2e_render_adjoint(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids, int32_t dtype,
+                       const void* const* dldi, const int64_t* pitch_elems, double* g_cx, double* g_cy,
+                       double* g_sx, double* g_sy, void* stream);
+
+/* Replace the mapping and PSF-width coefficients of a resident model (host arrays laid out
+ * as the gradients of e2e_render_adjoint), validate them as e2e_load_model does, and re-plan.
+ * Synchronous: waits for the device before replacing what in-flight work may read.
+ * Errors: E2E_EINVAL (the model keeps its old coefficients), E2E_ENOTFOUND, E2E_ECUDA. */
+int e2e_update_model(e2e_ctx* ctx, uint64_t model_id, const double* cx, const double* cy, const double* sx,
+                     const double* sy);
+
 /* Shape of the mixed-precision plan chosen for a model (for reports/tests): chunk of
  * wavelength samples per work item, slit points per register run, tile slack, number of
  * work items, tile size of the merge, and bytes of scratch one render needs. */

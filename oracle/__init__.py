@@ -96,6 +96,9 @@ def lib():
             L.oracle_loss_grad.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int,
                                            C.POINTER(OracleSlice), C.POINTER(dp), dp, dp, dp, dp, C.c_int]
             L.oracle_loss_grad.restype = C.c_double
+            L.oracle_vjp.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int,
+                                     C.POINTER(OracleSlice), C.POINTER(dp), dp, dp, dp, dp, C.c_int]
+            L.oracle_vjp.restype = C.c_int
             _lib = L
     return _lib
 
@@ -216,3 +219,22 @@ def loss_grad(model, flux_of, targets: Sequence[np.ndarray], n_threads: int = 0)
     loss = L.oracle_loss_grad(len(tg), H, W, m.n, m.arr, tp, _dptr(gcx), _dptr(gcy), _dptr(gsx), _dptr(gsy),
                               int(n_threads))
     return loss, gcx, gcy, gsx, gsy
+
+
+def vjp(model, flux_of, dLdI: Sequence[np.ndarray], n_threads: int = 0):
+    """(g_cx, g_cy, g_sx, g_sy) = sum over pixels of dL/dI * dI/dtheta, windows frozen."""
+    L = lib()
+    m = _Marshalled(model, flux_of)
+    H = (C.c_int * len(model.det_shape))(*[h for h, w in model.det_shape])
+    W = (C.c_int * len(model.det_shape))(*[w for h, w in model.det_shape])
+    gs = [np.ascontiguousarray(g, dtype=np.float64) for g in dLdI]
+    gp = (C.POINTER(C.c_double) * len(gs))(*[_dptr(g) for g in gs])
+    ncs = [(s.degree + 1) * (s.degree + 2) // 2 for s in model.slices]
+    gcx = np.zeros(sum(ncs))
+    gcy = np.zeros(sum(ncs))
+    gsx = np.zeros(3 * len(model.slices))
+    gsy = np.zeros(3 * len(model.slices))
+    rc = L.oracle_vjp(len(gs), H, W, m.n, m.arr, gp, _dptr(gcx), _dptr(gcy), _dptr(gsx), _dptr(gsy), int(n_threads))
+    if rc != 0:
+        raise ValueError("oracle_vjp rejected the model")
+    return gcx, gcy, gsx, gsy

@@ -363,6 +363,25 @@ static void slice_grad(const oracle_slice* s, int H, int W, const double* R, dou
   free(ax); free(ay); free(dax); free(day); free(sax); free(say);
 }
 
+int oracle_vjp(int n_det, const int* H, const int* W, int n_slices, const oracle_slice* s,
+               const double* const* dLdI, double* g_cx, double* g_cy, double* g_sx, double* g_sy, int n_threads) {
+  if (n_det <= 0 || n_slices < 0) return -1;
+  for (int i = 0; i < n_slices; ++i)
+    if (!valid_slice(&s[i], n_det)) return -1;
+  int* off = (int*)malloc(sizeof(int) * (n_slices + 1));
+  off[0] = 0;
+  for (int i = 0; i < n_slices; ++i) off[i + 1] = off[i] + n_coeffs(s[i].degree);
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int i = 0; i < n_slices; ++i)
+    slice_grad(&s[i], H[s[i].detector], W[s[i].detector], dLdI[s[i].detector], g_cx + off[i], g_cy + off[i],
+               g_sx + 3 * i, g_sy + 3 * i);
+  free(off);
+  return 0;
+}
+
 double oracle_loss_grad(int n_det, const int* H, const int* W, int n_slices, const oracle_slice* s,
                         const double* const* target, double* g_cx, double* g_cy, double* g_sx, double* g_sy,
                         int n_threads) {

@@ -78,6 +78,12 @@ double oracle_loss_grad(int n_det, const int* H, const int* W, int n_slices, con
                         const double* const* target, double* g_cx, double* g_cy, double* g_sx,
                         double* g_sy, int n_threads);
 
+/* Vector-Jacobian product of the render: given dL/dI per detector (frames' layout), the
+ * gradient sum over pixels of dL/dI * dI/dtheta for every order-slice's cx, cy, sx, sy, with
+ * window origins held at the forward render's.  Returns 0, or -1 on an invalid argument. */
+int oracle_vjp(int n_det, const int* H, const int* W, int n_slices, const oracle_slice* s,
+               const double* const* dLdI, double* g_cx, double* g_cy, double* g_sx, double* g_sy, int n_threads);
+
 #ifdef __cplusplus
 }
 #endif

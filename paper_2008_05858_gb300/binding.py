@@ -103,6 +103,11 @@ _SIGS = {
     "e2e_eval_tail": ([C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
     "e2e_render_static": ([C.c_void_p, C.c_uint64, C.c_int32, C.POINTER(C.c_uint64), C.c_int32,
                            C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.c_void_p], C.c_int),
+    "e2e_render_adjoint": ([C.c_void_p, C.c_uint64, C.c_int32, C.POINTER(C.c_uint64), C.c_int32,
+                            C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.c_void_p, C.c_void_p, C.c_void_p,
+                            C.c_void_p, C.c_void_p], C.c_int),
+    "e2e_update_model": ([C.c_void_p, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                          C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
 }
 
 #: size of the library's fixed device scratch used by e2e_render_static
@@ -266,6 +271,24 @@ def e2e_release_frame(ctx: int, frame_id: int) -> None:
     _check(load_library().e2e_release_frame(C.c_void_p(ctx), frame_id))
 
 
+def e2e_render_adjoint(ctx: int, model_id: int, spec_ids: Sequence[int], dtype: int, dldi_ptrs: Sequence[int],
+                       pitch_elems: Optional[Sequence[int]], g_cx: int, g_cy: int, g_sx: int, g_sy: int,
+                       stream=None) -> None:
+    n = len(spec_ids)
+    sids = (C.c_uint64 * max(n, 1))(*spec_ids)
+    dl = (C.c_void_p * len(dldi_ptrs))(*dldi_ptrs)
+    pit = None if pitch_elems is None else (C.c_int64 * len(pitch_elems))(*pitch_elems)
+    _check(load_library().e2e_render_adjoint(C.c_void_p(ctx), model_id, n, sids, dtype, dl, pit, C.c_void_p(g_cx),
+                                             C.c_void_p(g_cy), C.c_void_p(g_sx), C.c_void_p(g_sy),
+                                             C.c_void_p(_stream_handle(stream))))
+
+
+def e2e_update_model(ctx: int, model_id: int, cx: np.ndarray, cy: np.ndarray, sx: np.ndarray, sy: np.ndarray) -> None:
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (cx, cy, sx, sy)]
+    dp = C.POINTER(C.c_double)
+    _check(load_library().e2e_update_model(C.c_void_p(ctx), model_id, *[a.ctypes.data_as(dp) for a in arrs]))
+
+
 def e2e_kernel_times(ctx: int, cap: int = 64):
     """[(kernel name, ms)] of the context's most recent render (needs kernel_timing=1)."""
     names = (C.c_char_p * cap)()
@@ -346,6 +369,42 @@ class Renderer:
 
         td = torch.float32 if dtype == "f32" else torch.float64
         return [torch.empty((h, w), dtype=td, device=f"cuda:{self.device}") for h, w in self.models[mid].det_shape]
+
+    # -------------------------------------------------------------- differentiation
+    def params(self, mid: int):
+        """(cx, cy, sx, sy) of the model, concatenated per order-slice (the adjoint's layout)."""
+        m = self.models[mid]
+        return (np.concatenate([s.cx for s in m.slices]) if m.slices else np.zeros(0),
+                np.concatenate([s.cy for s in m.slices]) if m.slices else np.zeros(0),
+                np.concatenate([s.sigma_x for s in m.slices]) if m.slices else np.zeros(0),
+                np.concatenate([s.sigma_y for s in m.slices]) if m.slices else np.zeros(0))
+
+    def update(self, mid: int, cx, cy, sx, sy) -> None:
+        """Replace the model's coefficients on the device (re-plans) and in the host copy."""
+        e2e_update_model(self.ctx, mid, cx, cy, sx, sy)
+        m = self.models[mid].copy()
+        o = 0
+        for i, s in enumerate(m.slices):
+            nc = W.n_coeffs(s.degree)
+            s.cx = np.array(cx[o:o + nc], dtype=np.float64)
+            s.cy = np.array(cy[o:o + nc], dtype=np.float64)
+            s.sigma_x = np.array(sx[3 * i:3 * i + 3], dtype=np.float64)
+            s.sigma_y = np.array(sy[3 * i:3 * i + 3], dtype=np.float64)
+            o += nc
+        self.models[mid] = m
+
+    def adjoint(self, mid: int, spec_ids: Sequence[int], dldi, stream=None):
+        """(g_cx, g_cy, g_sx, g_sy) device FP64 tensors: sum over pixels of dL/dI * dI/dtheta."""
+        import torch
+
+        m = self.models[mid]
+        nc = sum(W.n_coeffs(s.degree) for s in m.slices)
+        dev = f"cuda:{self.device}"
+        g = [torch.empty(n, dtype=torch.float64, device=dev) for n in (nc, nc, 3 * len(m.slices), 3 * len(m.slices))]
+        dt = E2E_F32 if dldi[0].dtype == torch.float32 else E2E_F64
+        e2e_render_adjoint(self.ctx, mid, spec_ids, dt, [int(t.data_ptr()) for t in dldi],
+                           [int(t.stride(0)) for t in dldi], *[int(t.data_ptr()) for t in g], stream=stream)
+        return tuple(g)
 
     def render(self, mid: int, spec_ids: Sequence[int], precision: str = "mixed", dtype: str = "f32",
                out=None, stream=None):

@@ -1,0 +1,73 @@
+"""Command line: render seeded synthetic frames through the C ABI (for profiling and demos).
+
+    python -m paper_2008_05858_gb300.cli render --config 2 --orders 12 --repeat 3
+    python -m paper_2008_05858_gb300.cli render --config 5 --precision fp64 --save frame.npy
+
+``--orders`` shortens the full-detector workload (config 2) to its first orders so a profiler
+capture stays small; every other shape is the named configuration's.
+"""
+from __future__ import annotations
+
+import argparse
+import sys
+import time
+
+
+def _workload(args):
+    from . import workloads as W
+
+    if args.config == 2:
+        return W.config2(n_orders=args.orders or 85)
+    if args.config == 1:
+        return W.config1()
+    if args.config == 3:
+        return W.config3(orders_per_detector=args.orders or 30)
+    if args.config == 5:
+        return W.config5()
+    raise SystemExit(f"unknown config {args.config}")
+
+
+def cmd_render(args) -> int:
+    import numpy as np
+    import torch
+
+    from .binding import Renderer
+
+    w = _workload(args)
+    r = Renderer(args.device, kernel_timing=1)
+    mid = r.load_model(w.model)
+    sids = r.load_spectra(w)
+    dtype = args.dtype or w.out_dtype
+    out = r.render(mid, sids, args.precision, dtype)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.repeat):
+        r.render(mid, sids, args.precision, dtype, out=out)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / max(args.repeat, 1)
+    print(f"{w.name}: {w.model.n_stamps} stamps, {dt * 1e3:.3f} ms/render (wall), plan {r.plan(mid)}")
+    if args.save:
+        np.save(args.save, np.stack([o.cpu().numpy() for o in out]))
+    r.close()
+    return 0
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(prog="paper_2008_05858_gb300.cli")
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    p = sub.add_parser("render", help="render a synthetic configuration")
+    p.add_argument("--config", type=int, default=2)
+    p.add_argument("--orders", type=int, default=0)
+    p.add_argument("--repeat", type=int, default=3)
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--dtype", default=None, choices=[None, "f32", "f64"])
+    p.add_argument("--device", type=int, default=0)
+    p.add_argument("--save", default=None)
+    args = ap.parse_args(argv)
+    if args.cmd == "render":
+        return cmd_render(args)
+    return 1
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -68,6 +68,8 @@ struct Model {
   int n_det = 0, psf = 0;
   std::vector<int> H, W;
   std::vector<SliceHost> slices;
+  std::vector<DevSlice> dev;  // host copy of d_slices
+  int coef_total = 0;
   DevSlice* d_slices = nullptr;
   double* d_u = nullptr;
   int* d_dims = nullptr;  // [det][2] = (H, W)
@@ -604,6 +606,7 @@ int e2e_load_model(e2e_ctx* ctx, const e2e_model_desc* desc, uint64_t* model_id)
   m->W.assign(desc->width, desc->width + m->n_det);
   std::vector<DevSlice> ds(desc->n_slices);
   std::vector<double> u_all;
+  int32_t coef_total = 0;
   for (int i = 0; i < desc->n_slices; ++i) {
     const auto& s = desc->slices[i];
     SliceHost h;
@@ -637,6 +640,9 @@ int e2e_load_model(e2e_ctx* ctx, const e2e_model_desc* desc, uint64_t* model_id)
     v.W = m->W[s.detector];
     v.flux_slot = i;
     v.u_off = (int64_t)u_all.size();
+    v.coef_off = coef_total;
+    v.index = i;
+    coef_total += nc;
     u_all.insert(u_all.end(), s.slit_weights, s.slit_weights + s.n_slit);
     m->max_stamps = std::max(m->max_stamps, (int64_t)s.n_lambda * s.n_slit);
     if (std::find(m->Ks.begin(), m->Ks.end(), s.K) == m->Ks.end()) m->Ks.push_back(s.K);
@@ -648,6 +654,8 @@ int e2e_load_model(e2e_ctx* ctx, const e2e_model_desc* desc, uint64_t* model_id)
     dims[2 * d] = m->H[d];
     dims[2 * d + 1] = m->W[d];
   }
+  m->dev = ds;
+  m->coef_total = coef_total;
   int rc = upload(&m->d_slices, ds.data(), ds.size());
   if (rc == E2E_OK) rc = upload(&m->d_u, u_all.data(), u_all.size());
   if (rc == E2E_OK) rc = upload(&m->d_dims, dims.data(), dims.size());
@@ -883,6 +891,99 @@ int e2e_render_static(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uin
                                store, P.B, P.JB, P.nk_max, P.max_deg, P.smem, st));
   E2E_CK(launch_merge(P.d_tiles, P.n_tiles, P.d_lists, P.d_items, store, d_dst, dtype, d_pitch, m->d_dims, st));
   return E2E_OK;
+}
+
+int e2e_render_adjoint(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids, int32_t dtype,
+                       const void* const* dldi, const int64_t* pitch_in, double* g_cx, double* g_cy, double* g_sx,
+                       double* g_sy, void* stream) {
+  if (!ctx || !dldi || !g_cx || !g_cy || !g_sx || !g_sy) return fail(E2E_EINVAL, "null argument");
+  if (dtype != E2E_F32 && dtype != E2E_F64) return fail(E2E_EINVAL, "dtype must be E2E_F32 or E2E_F64");
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Model* m = find_model(ctx, model_id);
+  if (!m) return fail(E2E_ENOTFOUND, "unknown model id");
+  if (m->psf != E2E_PSF_SEPARABLE) return fail(E2E_EINVAL, "the adjoint supports the separable PSF");
+  const Plan& P = m->plan;
+  std::vector<int64_t> pitch(m->n_det);
+  for (int d = 0; d < m->n_det; ++d) {
+    if (!dldi[d]) return fail(E2E_EINVAL, "null dL/dI frame");
+    pitch[d] = pitch_in ? pitch_in[d] : m->W[d];
+    if (pitch[d] < m->W[d]) return fail(E2E_EINVAL, "pitch smaller than width");
+  }
+  std::vector<const double*> table;
+  int rc = resolve_flux(ctx, m, n_spec, spec_ids, table);
+  if (rc != E2E_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t ns = m->slices.size();
+  E2E_CK(cudaMemsetAsync(g_cx, 0, sizeof(double) * m->coef_total, st));
+  E2E_CK(cudaMemsetAsync(g_cy, 0, sizeof(double) * m->coef_total, st));
+  E2E_CK(cudaMemsetAsync(g_sx, 0, sizeof(double) * 3 * ns, st));
+  E2E_CK(cudaMemsetAsync(g_sy, 0, sizeof(double) * 3 * ns, st));
+  if (ns == 0 || P.items.empty()) return E2E_OK;
+  Scratch sc{{}, st};
+  const double** d_table = nullptr;
+  int64_t* d_pitch = nullptr;
+  const void** d_dldi = nullptr;
+  E2E_CK(sc.get((void**)&d_table, table.size() * sizeof(double*)));
+  E2E_CK(sc.get((void**)&d_pitch, pitch.size() * sizeof(int64_t)));
+  E2E_CK(sc.get((void**)&d_dldi, m->n_det * sizeof(void*)));
+  E2E_CK(cudaMemcpyAsync(d_table, table.data(), table.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
+  E2E_CK(cudaMemcpyAsync(d_pitch, pitch.data(), pitch.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  E2E_CK(cudaMemcpyAsync(d_dldi, dldi, m->n_det * sizeof(void*), cudaMemcpyHostToDevice, st));
+  const size_t smem = adjoint_smem_bytes(P.max_area, P.max_deg);
+  for (auto& grp : P.groups) {
+    KernelTimer kt(ctx, st, "adjoint");
+    E2E_CK(launch_adjoint(grp.K, m->d_slices, d_table, m->d_u, P.d_items + grp.first, grp.count, d_dldi, d_pitch,
+                          dtype == E2E_F32 ? 0 : 1, P.B, g_cx, g_cy, g_sx, g_sy, smem, st));
+  }
+  return E2E_OK;
+}
+
+int e2e_update_model(e2e_ctx* ctx, uint64_t model_id, const double* cx, const double* cy, const double* sx,
+                     const double* sy) {
+  if (!ctx || !cx || !cy || !sx || !sy) return fail(E2E_EINVAL, "null argument");
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Model* m = find_model(ctx, model_id);
+  if (!m) return fail(E2E_ENOTFOUND, "unknown model id");
+  // validate on copies first so a rejected update leaves the model untouched
+  std::vector<SliceHost> ns = m->slices;
+  std::vector<DevSlice> dv = m->dev;
+  for (size_t i = 0; i < ns.size(); ++i) {
+    SliceHost& h = ns[i];
+    const int nc = n_coeffs(h.d.degree);
+    const int off = dv[i].coef_off;
+    h.cx.assign(cx + off, cx + off + nc);
+    h.cy.assign(cy + off, cy + off + nc);
+    for (int c = 0; c < 3; ++c) {
+      h.d.sigma_x[c] = sx[3 * i + c];
+      h.d.sigma_y[c] = sy[3 * i + c];
+    }
+    h.d.cx = h.cx.data();
+    h.d.cy = h.cy.data();
+    h.d.slit_weights = h.u.data();
+    int rc = validate_slice(h.d, m->n_det, m->psf, (int)i);
+    if (rc != E2E_OK) return rc;
+    for (int c = 0; c < nc; ++c) {
+      dv[i].cx[c] = h.cx[c];
+      dv[i].cy[c] = h.cy[c];
+    }
+    for (int c = 0; c < 3; ++c) {
+      dv[i].sx[c] = h.d.sigma_x[c];
+      dv[i].sy[c] = h.d.sigma_y[c];
+    }
+  }
+  E2E_CK(cudaDeviceSynchronize());
+  if (!dv.empty()) E2E_CK(cudaMemcpy(m->d_slices, dv.data(), dv.size() * sizeof(DevSlice), cudaMemcpyHostToDevice));
+  m->slices = std::move(ns);
+  for (auto& h : m->slices) {  // re-point the descriptors at the moved vectors
+    h.d.cx = h.cx.data();
+    h.d.cy = h.cy.data();
+    h.d.slit_weights = h.u.data();
+  }
+  m->dev = dv;
+  free_plan(m->plan);
+  return plan_model(m);
 }
 
 int e2e_kernel_times(e2e_ctx* ctx, const char** names, float* ms, int32_t cap, int32_t* n) {

@@ -24,6 +24,8 @@ struct DevSlice {
   int32_t det, H, W, flux_slot;  // detector, its size, index into the per-render flux table
   int64_t u_off;                 // offset of this slice's slit weights in the model's weight array
   int64_t stamp_off;             // first global stamp index of this slice (FP64 path)
+  int32_t coef_off;              // offset of this slice's cx / cy in the concatenated gradients
+  int32_t index;                 // position of the slice in the model
 };
 
 // A mixed-path work item: a block of wavelength samples x a block of slit points of one

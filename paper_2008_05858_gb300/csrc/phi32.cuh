@@ -51,6 +51,28 @@ __device__ __forceinline__ float tail2(float wh, float wl) {
   return (ex * P) * rcp_approx(Q);
 }
 
+// As tail2, also returning 2^(-w^2) = exp(-a^2) (the Gaussian density up to a constant).
+__device__ __forceinline__ float tail2_dens(float wh, float wl, float& dens) {
+  const float p = wh * wh;
+  float e = fmaf(wh, wh, -p);
+  e = fmaf(wh + wh, wl, e);
+  const float ex = ex2_approx(-p) * fmaf(e, -0.693147181f, 1.f);
+  dens = ex;
+  const float x = fminf(fabsf(wh), 40.f);
+  float P = kTailP4;
+  P = fmaf(P, x, kTailP3);
+  P = fmaf(P, x, kTailP2);
+  P = fmaf(P, x, kTailP1);
+  P = fmaf(P, x, kTailP0);
+  float Q = kTailQ5;
+  Q = fmaf(Q, x, kTailQ4);
+  Q = fmaf(Q, x, kTailQ3);
+  Q = fmaf(Q, x, kTailQ2);
+  Q = fmaf(Q, x, kTailQ1);
+  Q = fmaf(Q, x, kTailQ0);
+  return (ex * P) * rcp_approx(Q);
+}
+
 // erf(|w| / sqrt(log2 e)) for |w| <= kErfMaxArg (odd polynomial, ~1.7 ulp): near the window
 // centre the pixel integrals are sums and differences of erf, which do not cancel there the
 // way differences of erfc values close to 1 do.

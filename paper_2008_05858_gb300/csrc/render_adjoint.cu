@@ -1,0 +1,275 @@
+// Adjoint of the separable render: the vector-Jacobian product of the frame with respect to
+// the spectral-format polynomial coefficients and the PSF-width coefficients.
+//
+// For calibration fitting (matching rendered frames to observed ones) the gradient of a
+// frame loss L with respect to the optical model is needed.  With dL/dI given per pixel and
+// each stamp's window held at the origin the forward render chose, a stamp (w, A_x, A_y)
+// contributes
+//   dL/dx_c = w sum_m dA_x[m]/dx_c S_x[m],  S_x[m] = sum_n dL/dI[r0+n][i0+m] A_y[n]
+//   dL/dsx  = w sum_m dA_x[m]/dsx  S_x[m]   (and likewise in y with S_y[n] = sum_m dL/dI A_x[m])
+// where, for a pixel between edges e0 < e1 and u = (e - x_c)/sigma,
+//   dA/dx_c = -(phi(u1) - phi(u0)) / sigma,   dA/dsigma = -(u1 phi(u1) - u0 phi(u0)) / sigma,
+// and the chain rule through x_c = sum c_ab lt^a s^b and sigma = sum p_q lt^q gives the
+// coefficient gradients.  The work decomposition is the forward's (items, boxes): dL/dI over
+// the item's box is staged in shared memory, each lane takes a run of slit points of one
+// wavelength sample, gathers its stamps' windows, and the per-run sums are reduced per warp
+// and per CTA in FP64 before one global FP64 add per coefficient per item.
+#include "e2e_device.cuh"
+#include "e2e_kernels.h"
+#include "phi32.cuh"
+
+namespace e2e {
+
+constexpr int kAdjThreads = 128;
+constexpr int kAdjWarps = kAdjThreads / 32;
+
+struct AdjArgs {
+  const DevSlice* slices;
+  const double* const* flux_tab;
+  const double* u_all;
+  const Item* items;
+  const void* const* dldi;  // per detector
+  const int64_t* pitch;
+  int dtype;                // 0 f32, 1 f64
+  int B;
+  double* g_cx;
+  double* g_cy;
+  double* g_sx;
+  double* g_sy;
+};
+
+__device__ __forceinline__ float2 split_pair(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
+// Profile of one axis of a stamp's K-pixel window: A[m] (pixel integrals), and the pixel
+// integrals' derivatives with respect to the centre (dA) and the width (sA).
+template <int K>
+__device__ __forceinline__ void axis_profile(float f, float gh, float gl, float inv_sigma, float* A, float* dA,
+                                             float* sA) {
+  constexpr int H = K / 2;
+  float E[K + 1], Fv[K + 1], ph[K + 1], u[K + 1];
+  const float inv_sqrt2pi = 0.398942280401432678f;
+#pragma unroll
+  for (int m = 0; m <= K; ++m) {
+    float wh, wl, dens;
+    const float e = (float)(m - H) - 0.5f;
+    edge_arg(e, f, gh, gl, wh, wl);
+    E[m] = tail2_dens(wh, wl, dens);
+    ph[m] = dens * inv_sqrt2pi;
+    u[m] = (e - f) * inv_sigma;
+    if (m >= H - 1 && m <= H + 2) Fv[m] = fabsf(wh) < kErfMaxArg ? erf_small(wh) : 1.f - E[m];
+  }
+#pragma unroll
+  for (int m = 0; m < K; ++m) {
+    float v;
+    if (m < H - 1) v = E[m + 1] - E[m];
+    else if (m == H - 1) v = Fv[m] - Fv[m + 1];
+    else if (m == H) v = Fv[m] + Fv[m + 1];
+    else if (m == H + 1) v = Fv[m + 1] - Fv[m];
+    else v = E[m] - E[m + 1];
+    A[m] = 0.5f * v;
+    dA[m] = -(ph[m + 1] - ph[m]) * inv_sigma;
+    sA[m] = -(u[m + 1] * ph[m + 1] - u[m] * ph[m]) * inv_sigma;
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
+  constexpr int H = K / 2;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Item it = a.items[blockIdx.x];
+  const DevSlice& S = a.slices[it.slice];
+  const int area = it.bw * it.bh;
+  const int d = S.degree, nc = (d + 1) * (d + 2) / 2;
+  const int ncoef = 2 * nc + 6;
+  float* R = reinterpret_cast<float*>(smem);                            // dL/dI over the box
+  double* red = reinterpret_cast<double*>(smem + (((size_t)area * 4 + 15) & ~(size_t)15));  // [warps][ncoef]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  {
+    const int64_t P = a.pitch[S.det];
+    for (int p = tid; p < area; p += kAdjThreads) {
+      const int gy = p / it.bw, gx = p - gy * it.bw;
+      const int64_t off = (int64_t)(it.by0 + gy) * P + (it.bx0 + gx);
+      R[p] = a.dtype == 0 ? static_cast<const float*>(a.dldi[S.det])[off]
+                          : (float)static_cast<const double*>(a.dldi[S.det])[off];
+    }
+    for (int q = tid; q < kAdjWarps * ncoef; q += kAdjThreads) red[q] = 0.0;
+  }
+  __syncthreads();
+  const double* flux = a.flux_tab[S.flux_slot];
+  const double* u = a.u_all + S.u_off;
+  const double inv_nl = 1.0 / (double)S.n_lambda, inv_ns = 1.0 / (double)S.n_slit;
+  const double kq = kSqrtLog2eD * 0.70710678118654752440;
+  const int nrc = (it.nk + a.B - 1) / a.B;
+  const int njb = (it.nj + 31) / 32;
+  const int ntask = njb * nrc;
+  for (int task = warp; task < ntask; task += kAdjWarps) {
+    const int jj = (task % njb) * 32 + lane;
+    const bool jvalid = jj < it.nj;
+    const int j = it.j0 + jj;
+    const int k0 = it.k0 + (task / njb) * a.B;
+    const int nb = min(a.B, it.k0 + it.nk - k0);
+    float Hx[9], Hy[9], Gsx = 0.f, Gsy = 0.f;
+#pragma unroll
+    for (int b = 0; b < 9; ++b) Hx[b] = Hy[b] = 0.f;
+    double lt = 0.0;
+    if (jvalid) {
+      lt = (double)(2 * j + 1 - S.n_lambda) * inv_nl;
+      double px[9], py[9];
+#pragma unroll
+      for (int b = 0; b <= 8; ++b) {
+        px[b] = b <= d ? poly_lt_for_b(S.cx, d, b, lt) : 0.0;
+        py[b] = b <= d ? poly_lt_for_b(S.cy, d, b, lt) : 0.0;
+      }
+      const double sgx = fma(fma(S.sx[2], lt, S.sx[1]), lt, S.sx[0]);
+      const double sgy = fma(fma(S.sy[2], lt, S.sy[1]), lt, S.sy[0]);
+      const float2 gx = split_pair(kq / sgx), gy = split_pair(kq / sgy);
+      const float isx = (float)(1.0 / sgx), isy = (float)(1.0 / sgy);
+      const double wj = flux[j] * S.dlam;
+      for (int b = 0; b < nb; ++b) {
+        const int k = k0 + b;
+        const double sd = (double)(2 * k + 1 - S.n_slit) * inv_ns;
+        int ci, ri;
+        float fx, fy;
+        split_coord(horner_s(px, d, sd), ci, fx);
+        split_coord(horner_s(py, d, sd), ri, fy);
+        if (ci == kOffFrame || ri == kOffFrame) continue;
+        const float w = (float)(wj * u[k]);
+        float Ax[K], dAx[K], sAx[K], Ay[K], dAy[K], sAy[K];
+        axis_profile<K>(fx, gx.x, gx.y, isx, Ax, dAx, sAx);
+        axis_profile<K>(fy, gy.x, gy.y, isy, Ay, dAy, sAy);
+        // gather dL/dI over the window (pixels outside the box lie outside the detector)
+        float Sx[K], Sy[K];
+#pragma unroll
+        for (int m = 0; m < K; ++m) Sx[m] = 0.f;
+        const int bx = ci - H - it.bx0, by = ri - H - it.by0;
+#pragma unroll
+        for (int n = 0; n < K; ++n) {
+          float sy = 0.f;
+          const int gy = by + n;
+          if (gy >= 0 && gy < it.bh) {
+#pragma unroll
+            for (int m = 0; m < K; ++m) {
+              const int gx2 = bx + m;
+              const float r = (gx2 >= 0 && gx2 < it.bw) ? R[gy * it.bw + gx2] : 0.f;
+              sy = fmaf(r, Ax[m], sy);
+              Sx[m] = fmaf(r, Ay[n], Sx[m]);
+            }
+          }
+          Sy[n] = sy;
+        }
+        float gxc = 0.f, gsx = 0.f, gyc = 0.f, gsy = 0.f;
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+          gxc = fmaf(dAx[m], Sx[m], gxc);
+          gsx = fmaf(sAx[m], Sx[m], gsx);
+          gyc = fmaf(dAy[m], Sy[m], gyc);
+          gsy = fmaf(sAy[m], Sy[m], gsy);
+        }
+        gxc *= w;
+        gyc *= w;
+        Gsx = fmaf(w, gsx, Gsx);
+        Gsy = fmaf(w, gsy, Gsy);
+        // powers of s for the chain rule through x_c = sum_b P_b(lt) s^b
+        const float s = (float)sd;
+        float sp = 1.f;
+#pragma unroll
+        for (int bb = 0; bb < 9; ++bb) {
+          if (bb <= d) {
+            Hx[bb] = fmaf(gxc, sp, Hx[bb]);
+            Hy[bb] = fmaf(gyc, sp, Hy[bb]);
+          }
+          sp *= s;
+        }
+      }
+    }
+    // coefficient gradients of this run: dL/dc_ab = lt^a H_b, dL/ds_q = lt^q G_s; reduce the
+    // warp in FP64 and keep one partial per warp
+    const double ltv = lt;
+    for (int t = 0; t <= d; ++t)
+      for (int bb = 0; bb <= t; ++bb) {
+        const int aa = t - bb;
+        double lp = 1.0;
+        for (int q = 0; q < aa; ++q) lp *= ltv;
+        float hx = 0.f, hy = 0.f;
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+          if (q == bb) {
+            hx = Hx[q];
+            hy = Hy[q];
+          }
+        double vx = lp * (double)hx, vy = lp * (double)hy;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          vx += __shfl_xor_sync(0xffffffffu, vx, o);
+          vy += __shfl_xor_sync(0xffffffffu, vy, o);
+        }
+        if (lane == 0) {
+          const int idx = t * (t + 1) / 2 + bb;
+          red[warp * ncoef + idx] += vx;
+          red[warp * ncoef + nc + idx] += vy;
+        }
+      }
+    for (int q = 0; q < 3; ++q) {
+      double lp = 1.0;
+      for (int r = 0; r < q; ++r) lp *= ltv;
+      double vx = lp * (double)Gsx, vy = lp * (double)Gsy;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        vx += __shfl_xor_sync(0xffffffffu, vx, o);
+        vy += __shfl_xor_sync(0xffffffffu, vy, o);
+      }
+      if (lane == 0) {
+        red[warp * ncoef + 2 * nc + q] += vx;
+        red[warp * ncoef + 2 * nc + 3 + q] += vy;
+      }
+    }
+  }
+  __syncthreads();
+  for (int q = tid; q < ncoef; q += kAdjThreads) {
+    double v = 0.0;
+    for (int w2 = 0; w2 < kAdjWarps; ++w2) v += red[w2 * ncoef + q];
+    if (v == 0.0) continue;
+    if (q < nc) atomicAdd(a.g_cx + S.coef_off + q, v);
+    else if (q < 2 * nc) atomicAdd(a.g_cy + S.coef_off + q - nc, v);
+    else if (q < 2 * nc + 3) atomicAdd(a.g_sx + 3 * S.index + (q - 2 * nc), v);
+    else atomicAdd(a.g_sy + 3 * S.index + (q - 2 * nc - 3), v);
+  }
+}
+
+size_t adjoint_smem_bytes(int max_area, int max_deg) {
+  const int nc = (max_deg + 1) * (max_deg + 2) / 2;
+  return (((size_t)max_area * 4 + 15) & ~(size_t)15) + (size_t)kAdjWarps * (2 * nc + 6) * 8;
+}
+
+template <int K>
+static cudaError_t launch_adj(const AdjArgs& a, int n_items, size_t smem, cudaStream_t st) {
+  auto kern = k_adjoint<K>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<n_items, kAdjThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(int K, const DevSlice* slices, const double* const* flux_tab, const double* u_all,
+                           const Item* items, int n_items, const void* const* dldi, const int64_t* pitch, int dtype,
+                           int B, double* g_cx, double* g_cy, double* g_sx, double* g_sy, size_t smem,
+                           cudaStream_t st) {
+  if (n_items == 0) return cudaSuccess;
+  AdjArgs a{slices, flux_tab, u_all, items, dldi, pitch, dtype, B, g_cx, g_cy, g_sx, g_sy};
+  switch (K) {
+    case 1: return launch_adj<1>(a, n_items, smem, st);
+    case 3: return launch_adj<3>(a, n_items, smem, st);
+    case 5: return launch_adj<5>(a, n_items, smem, st);
+    case 7: return launch_adj<7>(a, n_items, smem, st);
+    case 9: return launch_adj<9>(a, n_items, smem, st);
+    case 11: return launch_adj<11>(a, n_items, smem, st);
+    case 13: return launch_adj<13>(a, n_items, smem, st);
+    case 15: return launch_adj<15>(a, n_items, smem, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace e2e
