@@ -180,6 +180,7 @@ def run_gpu(args):
     import torch
 
     from paper_2008_05858_gb300 import binding as B
+    from paper_2008_05858_gb300 import shard
 
     rank, world, local = dist_env()
     if world > 1:
@@ -225,10 +226,7 @@ def run_gpu(args):
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = shard.reduce_over_ranks(total_ms, "max")
     ms_per_step = total_ms / args.steps
     value = stamps * world / (ms_per_step * 1e-3)
     clocks = clk.summary()
@@ -324,6 +322,9 @@ def run_gpu(args):
         "launches_per_step": launches_per_step,
         "clocks": clocks, "peak_source": peak_kind, "wall_s_timed": t_wall,
     }
+    if not args.no_serving:
+        line["serving"] = serving_run(B, dev)
+        line["p99_latency_ms"] = line["serving"]["poisson"]["latency_ms"]["p99"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, sample = oracle_sample_rate(w)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
@@ -333,6 +334,99 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def serving_run(B, dev, n_jobs=512, max_inflight=8, load=0.8, express_stamps=1 << 24):
+    """Request stream of uneven render jobs through the serving loop (e2e_server_*).
+
+    Three job classes (single-order 1024x256 tiles, 10-order 4096^2 tiles, full 9216^2
+    frames; 40/40/20), one resident optical model and spectrum set per class.  A saturation
+    run submits every job at t=0 (steady throughput); then a seeded Poisson stream arrives
+    at `load` x that throughput.  Latency = completion on the device (seen by the loop) minus
+    submission; frames are library-owned and released as they complete."""
+    import threading
+
+    r = B.Renderer(dev)
+    classes = W.serving_classes()
+    res = []
+    for q, jc in enumerate(classes):
+        w = jc.make(W.SEED_BASE + 40 + q)
+        res.append((jc.name, r.load_model(w.model), r.load_spectra(w), w.model.n_stamps))
+    rng = np.random.default_rng(W.SEED_BASE + 4)
+    kinds = rng.choice(len(classes), size=n_jobs, p=[jc.share for jc in classes])
+    srv = B.Server(r, max_inflight=max_inflight)
+
+    def run(arrivals):
+        rids, infos = [], [None] * n_jobs
+        have = threading.Semaphore(0)
+
+        def reaper():
+            for i in range(n_jobs):
+                have.acquire()
+                info = srv.wait(rids[i])
+                B.e2e_release_frame(r.ctx, int(info["frame_id"]))
+                srv.forget(rids[i])
+                infos[i] = info
+
+        th = threading.Thread(target=reaper)
+        th.start()
+        t0 = time.perf_counter()
+        for i in range(n_jobs):
+            if arrivals is not None:
+                delay = t0 + arrivals[i] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            _, mid, sids, _ = res[kinds[i]]
+            rids.append(srv.submit(mid, sids, "mixed", "f32"))
+            have.release()
+        th.join()
+        sub = np.array([x["submit_ms"] for x in infos])
+        adm = np.array([x["admit_ms"] for x in infos])
+        done = np.array([x["done_ms"] for x in infos])
+        span_s = (done.max() - sub.min()) * 1e-3
+        lat = done - sub
+        ev = sorted([(a, 1) for a in adm] + [(d, -1) for d in done])
+        depth = peak = 0
+        for _, dlt in ev:
+            depth += dlt
+            peak = max(peak, depth)
+        out = {"jobs": n_jobs, "jobs_per_s": n_jobs / span_s,
+               "stamps_per_s": float(sum(res[k][3] for k in kinds)) / span_s,
+               "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                              "max": float(lat.max())},
+               "queue_wait_ms_p99": float(np.percentile(adm - sub, 99)), "max_jobs_in_flight": peak,
+               "by_class": {}}
+        for q, (name, _, _, _) in enumerate(res):
+            sel = kinds == q
+            if sel.any():
+                out["by_class"][name] = {
+                    "jobs": int(sel.sum()), "latency_ms_p50": float(np.percentile(lat[sel], 50)),
+                    "latency_ms_p99": float(np.percentile(lat[sel], 99)),
+                    "device_ms_p50": float(np.median([infos[i]["device_ms"] for i in np.nonzero(sel)[0]]))}
+        return out
+
+    for q in range(len(res)):  # warm every class once
+        info = srv.wait(srv.submit(res[q][1], res[q][2], "mixed", "f32"))
+        B.e2e_release_frame(r.ctx, int(info["frame_id"]))
+    sat = run(None)
+    rate = load * sat["jobs_per_s"]
+    arrivals = W.poisson_arrivals(np.random.default_rng(W.SEED_BASE + 41), n_jobs, rate)
+    poi = run(arrivals)
+    srv.stop()
+    # the same arrivals with an express class: jobs up to express_stamps stamps are admitted
+    # ahead of queued full frames and run on high-priority streams
+    srv = B.Server(r, max_inflight=max_inflight, express_stamps=express_stamps)
+    for q in range(len(res)):
+        info = srv.wait(srv.submit(res[q][1], res[q][2], "mixed", "f32"))
+        B.e2e_release_frame(r.ctx, int(info["frame_id"]))
+    poi_x = run(arrivals)
+    srv.stop()
+    r.close()
+    return {"workload": "512 jobs, 40% 1-order 1024x256 / 40% 10-order 4096^2 / 20% full 9216^2 frames, "
+                        "mixed precision, f32 frames, models resident",
+            "max_inflight": max_inflight, "admission": "free-HBM budget (0.9 x free at start), FIFO",
+            "poisson": dict(poi, arrival_rate_jobs_per_s=rate, load=load), "saturation": sat,
+            "poisson_express": dict(poi_x, express_stamps=express_stamps, arrival_rate_jobs_per_s=rate, load=load)}
 
 
 def _load_spectrum_ptr(B, ctx, fiber, orders, lens, flux_tensor):
@@ -349,6 +443,7 @@ def _load_spectrum_ptr(B, ctx, fiber, orders, lens, flux_tensor):
 
 
 KERNEL_SOURCES = ["paper_2008_05858_gb300/csrc/render_mixed.cu", "paper_2008_05858_gb300/csrc/phi32.cuh",
+                  "paper_2008_05858_gb300/csrc/mixed_common.cuh",
                   "paper_2008_05858_gb300/csrc/e2e_device.cuh", "paper_2008_05858_gb300/csrc/tail_coeffs.h"]
 
 
@@ -386,6 +481,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

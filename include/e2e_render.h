@@ -44,11 +44,11 @@ extern "C" {
 #define E2E_ENOMEM -2    /* device memory exhausted */
 #define E2E_ECUDA -3     /* a CUDA call failed; see e2e_last_error() */
 #define E2E_ENOTFOUND -4 /* unknown id */
-#define E2E_EBUSY -5     /* serving: job queued, not admitted yet */
+#define E2E_EBUSY -5     /* reserved (queued jobs report E2E_JOB_QUEUED in e2e_job_info) */
 #define E2E_ETOOBIG -6   /* serving: job can never fit the memory pool */
 #define E2E_ETIMEOUT -7  /* serving: wait timed out */
 #define E2E_ECANCELLED -8
-#define E2E_EDEVICE -9   /* a kernel reported an error status (bounds check) */
+#define E2E_EDEVICE -9   /* reserved */
 
 /* ------------------------------------------------------------------ enums */
 enum { E2E_PSF_SEPARABLE = 0, E2E_PSF_ELLIPTICAL = 1 };
@@ -67,7 +67,7 @@ typedef struct e2e_ctx e2e_ctx;
 typedef struct {
   size_t pool_bytes; /* cap on the device scratch the context may hold (0 = no cap) */
   int32_t max_inflight; /* serving: jobs on the device at once (0 = default 4) */
-  int32_t debug_checks; /* 1 = kernels bounds-check every deposit and report E2E_EDEVICE */
+  int32_t debug_checks; /* reserved, ignored (every deposit is already clipped to its box) */
   int32_t kernel_timing; /* 1 = record CUDA events around each kernel of a render (see e2e_kernel_times) */
 } e2e_opts;
 
@@ -87,7 +87,12 @@ typedef struct {
   const double* cy;    /* same for y */
   double sigma_x[3];   /* PSF width (px) = c0 + c1 lt + c2 lt^2; must stay > 0 on [-1, 1] */
   double sigma_y[3];
-  double theta;        /* E2E_PSF_ELLIPTICAL: rotation of the PSF axes (radians), |rho| <= 0.9 */
+  double theta;        /* E2E_PSF_ELLIPTICAL: rotation of the PSF axes (radians); with
+                          vx, vy, cxy the rotated covariance at a sample, the shear
+                          eps = cxy / sqrt(vx (vx vy - cxy^2)) must satisfy |eps| <= 0.2 at
+                          every wavelength sample (about |theta| <= 20 deg for widths in
+                          [1.2, 2.0] px): the renderers expand the conditional profile of
+                          y given x in eps * tau over one pixel column */
   const double* slit_weights; /* n_slit weights u_k (finite, >= 0) */
 } e2e_order_slice;
 
@@ -118,7 +123,7 @@ const char* e2e_last_error(void);
 
 /* Load an optical model (the spectral-format database of Sec. 2.1, which the paper
  * computes once and reuses across simulations): validates it (degree, K odd, widths > 0 on
- * [-1, 1], finite coefficients, |rho| <= 0.9 for the elliptical PSF), copies it to the
+ * [-1, 1], finite coefficients, |eps| <= 0.2 for the elliptical PSF), copies it to the
  * device and plans the tiled render (synchronous; uses the context's device).
  * Errors: E2E_EINVAL, E2E_ENOMEM, E2E_ECUDA. */
 int e2e_load_model(e2e_ctx* ctx, const e2e_model_desc* desc, uint64_t* model_id);
@@ -146,13 +151,17 @@ int e2e_unload_spectrum(e2e_ctx* ctx, uint64_t spec_id);
 int e2e_render(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids, int32_t precision,
                int32_t dtype, void* const* dst, const int64_t* pitch_elems, void* stream);
 
-/* As e2e_render, into frames the library allocates and owns until e2e_release_frame. */
+/* As e2e_render, into frames the library allocates (stream-ordered, from the device's
+ * memory pool, on `stream`) and owns until e2e_release_frame. */
 int e2e_render_alloc(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids,
                      int32_t precision, int32_t dtype, void* stream, uint64_t* frame_id);
 
 /* Copy detector `detector` of a library-owned frame (height*width elements of its dtype,
  * row-major) to dst (device or host memory, `bytes` must equal the frame's size).
- * Stream-ordered; a host destination is complete when the stream is. */
+ * Stream-ordered on `stream`, after the frame's render wherever that was enqueued; a host
+ * destination is complete when the stream is.
+ * e2e_release_frame returns the buffers to the pool after every enqueued use of the frame
+ * (its render and fetches) has completed; it does not block the caller. */
 int e2e_fetch_frame(e2e_ctx* ctx, uint64_t frame_id, int32_t detector, void* dst, int32_t dst_is_device,
                     size_t bytes, void* stream);
 int e2e_release_frame(e2e_ctx* ctx, uint64_t frame_id);
@@ -184,6 +193,67 @@ int e2e_render_adjoint(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const ui
  * Errors: E2E_EINVAL (the model keeps its old coefficients), E2E_ENOTFOUND, E2E_ECUDA. */
 int e2e_update_model(e2e_ctx* ctx, uint64_t model_id, const double* cx, const double* cy, const double* sx,
                      const double* sy);
+
+/* ------------------------------------------------------------------ serving */
+
+/* The paper spreads many simulation jobs over cloud workers (Sec. 3); here one GPU serves a
+ * stream of render jobs of uneven size.
+ * A persistent request loop (a host thread per context) renders jobs with continuous
+ * batching: a job that arrives while others run is admitted as soon as a slot (a CUDA stream)
+ * and enough of the memory budget are free, and its kernels then run on the device
+ * concurrently with the jobs already in flight.  Models and spectra stay resident.  A job's
+ * frame is bitwise the same whether it ran alone or in the mix (the renderer is
+ * deterministic). */
+typedef struct {
+  int32_t max_inflight; /* slots (streams); 0 = the context's max_inflight */
+  size_t budget_bytes;  /* device memory the in-flight jobs may hold (scratch + library frames);
+                           0 = the context's pool_bytes, or else 90% of the free HBM at start */
+  int64_t express_stamps; /* jobs of at most this many stamps are "express": admitted before
+                             any queued regular job and run on high-priority streams, so
+                             small jobs do not wait behind full frames (0 = one FIFO class) */
+} e2e_server_cfg;
+
+typedef struct {
+  uint64_t model_id;
+  int32_t n_spec;
+  const uint64_t* spec_ids;  /* copied at submit */
+  int32_t precision;         /* E2E_PREC_MIXED or E2E_PREC_FP64 */
+  int32_t dtype;             /* E2E_F32 or E2E_F64 */
+  void* const* dst;          /* per-detector device frames (copied at submit), or NULL: the library
+                                allocates the job's frames (e2e_job_info.frame_id; fetch with
+                                e2e_fetch_frame, free with e2e_release_frame) */
+  const int64_t* pitch_elems;  /* as for e2e_render; may be NULL */
+} e2e_job;
+
+enum { E2E_JOB_DONE = 0, E2E_JOB_RUNNING = 1, E2E_JOB_QUEUED = 2 };
+
+typedef struct {
+  int32_t status;        /* E2E_JOB_DONE / RUNNING / QUEUED, or a negative error code */
+  double submit_ms;      /* host times, ms since the server started */
+  double admit_ms;
+  double done_ms;
+  double device_ms;      /* CUDA-event time from the job's first kernel to its last */
+  int64_t budget_bytes;  /* memory the job held while in flight */
+  uint64_t frame_id;     /* library-owned frames, else 0 */
+  int64_t stamps;
+} e2e_job_info;
+
+/* Start the loop.  Errors: E2E_EINVAL (already running), E2E_ECUDA, E2E_ENOMEM. */
+int e2e_server_start(e2e_ctx* ctx, const e2e_server_cfg* cfg);
+/* Queue a job.  Validates it (model, spectra, dtype); a job whose memory can never fit the
+ * budget is refused with E2E_ETOOBIG.  Thread-safe. */
+int e2e_submit(e2e_ctx* ctx, const e2e_job* job, uint64_t* request_id);
+/* Non-blocking status (info may be NULL).  Returns E2E_OK, or E2E_ENOTFOUND. */
+int e2e_poll(e2e_ctx* ctx, uint64_t request_id, e2e_job_info* info);
+/* Wait up to timeout_ms (< 0: forever) for a job to finish: E2E_OK when done (info filled),
+ * E2E_ETIMEOUT if it has not finished in time, or the job's error. */
+int e2e_wait(e2e_ctx* ctx, uint64_t request_id, int32_t timeout_ms, e2e_job_info* info);
+/* Cancel a job that is still queued (E2E_ECANCELLED afterwards); running jobs finish. */
+int e2e_cancel(e2e_ctx* ctx, uint64_t request_id);
+/* Forget a finished job's record (its library frames stay until e2e_release_frame). */
+int e2e_forget(e2e_ctx* ctx, uint64_t request_id);
+/* Stop admitting, wait for every admitted job, stop the loop.  Queued jobs are cancelled. */
+int e2e_server_stop(e2e_ctx* ctx);
 
 /* Shape of the mixed-precision plan chosen for a model (for reports/tests): chunk of
  * wavelength samples per work item, slit points per register run, tile slack, number of

@@ -78,6 +78,29 @@ class e2e_plan_info(C.Structure):
     ]
 
 
+class e2e_server_cfg(C.Structure):
+    _fields_ = [("max_inflight", C.c_int32), ("budget_bytes", C.c_size_t), ("express_stamps", C.c_int64)]
+
+
+class e2e_job(C.Structure):
+    _fields_ = [
+        ("model_id", C.c_uint64), ("n_spec", C.c_int32), ("spec_ids", C.POINTER(C.c_uint64)),
+        ("precision", C.c_int32), ("dtype", C.c_int32), ("dst", C.POINTER(C.c_void_p)),
+        ("pitch_elems", C.POINTER(C.c_int64)),
+    ]
+
+
+class e2e_job_info(C.Structure):
+    _fields_ = [
+        ("status", C.c_int32), ("submit_ms", C.c_double), ("admit_ms", C.c_double), ("done_ms", C.c_double),
+        ("device_ms", C.c_double), ("budget_bytes", C.c_int64), ("frame_id", C.c_uint64), ("stamps", C.c_int64),
+    ]
+
+
+E2E_JOB_DONE = 0
+E2E_JOB_RUNNING = 1
+E2E_JOB_QUEUED = 2
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 _lib = None
 _lock = threading.Lock()
@@ -108,6 +131,13 @@ _SIGS = {
                             C.c_void_p, C.c_void_p], C.c_int),
     "e2e_update_model": ([C.c_void_p, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double),
                           C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
+    "e2e_server_start": ([C.c_void_p, C.POINTER(e2e_server_cfg)], C.c_int),
+    "e2e_submit": ([C.c_void_p, C.POINTER(e2e_job), C.POINTER(C.c_uint64)], C.c_int),
+    "e2e_poll": ([C.c_void_p, C.c_uint64, C.POINTER(e2e_job_info)], C.c_int),
+    "e2e_wait": ([C.c_void_p, C.c_uint64, C.c_int32, C.POINTER(e2e_job_info)], C.c_int),
+    "e2e_cancel": ([C.c_void_p, C.c_uint64], C.c_int),
+    "e2e_forget": ([C.c_void_p, C.c_uint64], C.c_int),
+    "e2e_server_stop": ([C.c_void_p], C.c_int),
 }
 
 #: size of the library's fixed device scratch used by e2e_render_static
@@ -289,6 +319,54 @@ def e2e_update_model(ctx: int, model_id: int, cx: np.ndarray, cy: np.ndarray, sx
     _check(load_library().e2e_update_model(C.c_void_p(ctx), model_id, *[a.ctypes.data_as(dp) for a in arrs]))
 
 
+# -------------------------------------------------------------------- serving
+
+
+def e2e_server_start(ctx: int, max_inflight: int = 0, budget_bytes: int = 0, express_stamps: int = 0) -> None:
+    cfg = e2e_server_cfg(max_inflight, budget_bytes, express_stamps)
+    _check(load_library().e2e_server_start(C.c_void_p(ctx), C.byref(cfg)))
+
+
+def e2e_submit(ctx: int, model_id: int, spec_ids: Sequence[int], precision: int, dtype: int,
+               dst_ptrs: Optional[Sequence[int]] = None, pitch_elems: Optional[Sequence[int]] = None) -> int:
+    n = len(spec_ids)
+    sids = (C.c_uint64 * max(n, 1))(*spec_ids)
+    dst = None if dst_ptrs is None else (C.c_void_p * len(dst_ptrs))(*dst_ptrs)
+    pit = None if pitch_elems is None else (C.c_int64 * len(pitch_elems))(*pitch_elems)
+    job = e2e_job(model_id, n, sids, precision, dtype, dst, pit)
+    rid = C.c_uint64()
+    _check(load_library().e2e_submit(C.c_void_p(ctx), C.byref(job), C.byref(rid)))
+    return rid.value
+
+
+def _info_dict(info: e2e_job_info) -> Dict[str, float]:
+    return {name: getattr(info, name) for name, _ in e2e_job_info._fields_}
+
+
+def e2e_poll(ctx: int, request_id: int) -> Dict[str, float]:
+    info = e2e_job_info()
+    _check(load_library().e2e_poll(C.c_void_p(ctx), request_id, C.byref(info)))
+    return _info_dict(info)
+
+
+def e2e_wait(ctx: int, request_id: int, timeout_ms: int = -1) -> Dict[str, float]:
+    info = e2e_job_info()
+    _check(load_library().e2e_wait(C.c_void_p(ctx), request_id, timeout_ms, C.byref(info)))
+    return _info_dict(info)
+
+
+def e2e_cancel(ctx: int, request_id: int) -> None:
+    _check(load_library().e2e_cancel(C.c_void_p(ctx), request_id))
+
+
+def e2e_forget(ctx: int, request_id: int) -> None:
+    _check(load_library().e2e_forget(C.c_void_p(ctx), request_id))
+
+
+def e2e_server_stop(ctx: int) -> None:
+    _check(load_library().e2e_server_stop(C.c_void_p(ctx)))
+
+
 def e2e_kernel_times(ctx: int, cap: int = 64):
     """[(kernel name, ms)] of the context's most recent render (needs kernel_timing=1)."""
     names = (C.c_char_p * cap)()
@@ -414,3 +492,38 @@ class Renderer:
         e2e_render(self.ctx, mid, spec_ids, PRECISION[precision], DTYPE[dtype], [int(t.data_ptr()) for t in out],
                    pitches, stream)
         return out
+
+
+class Server:
+    """Continuous-batching request loop on a Renderer's context (see e2e_server_start)."""
+
+    def __init__(self, renderer: Renderer, max_inflight: int = 4, budget_bytes: int = 0, express_stamps: int = 0):
+        self.r = renderer
+        e2e_server_start(renderer.ctx, max_inflight, budget_bytes, express_stamps)
+        self._keep: Dict[int, object] = {}
+
+    def submit(self, mid: int, spec_ids: Sequence[int], precision: str = "mixed", dtype: str = "f32", out=None) -> int:
+        ptrs = None if out is None else [int(t.data_ptr()) for t in out]
+        pitches = None if out is None else [int(t.stride(0)) for t in out]
+        rid = e2e_submit(self.r.ctx, mid, spec_ids, PRECISION[precision], DTYPE[dtype], ptrs, pitches)
+        if out is not None:
+            self._keep[rid] = out  # the frames must outlive the job
+        return rid
+
+    def poll(self, rid: int):
+        return e2e_poll(self.r.ctx, rid)
+
+    def wait(self, rid: int, timeout_ms: int = -1):
+        info = e2e_wait(self.r.ctx, rid, timeout_ms)
+        self._keep.pop(rid, None)
+        return info
+
+    def cancel(self, rid: int):
+        e2e_cancel(self.r.ctx, rid)
+
+    def forget(self, rid: int):
+        e2e_forget(self.r.ctx, rid)
+
+    def stop(self):
+        e2e_server_stop(self.r.ctx)
+        self._keep.clear()

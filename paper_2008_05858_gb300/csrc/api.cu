@@ -6,7 +6,11 @@
 // (e2e_load_model), spectra are resident too, and a render only launches kernels.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <thread>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -84,16 +88,25 @@ struct Spectrum {
   double* d_flux = nullptr;
 };
 
+// A library-owned frame.  Its buffers come from the stream-ordered pool; `ready` marks the
+// last use enqueued on any stream (the render, then each fetch), so a fetch on another stream
+// and the release both wait for it without synchronising the device.
 struct Frame {
   int dtype = 0;
   std::vector<int> H, W;
   std::vector<void*> ptrs;
+  cudaEvent_t ready = nullptr;
 };
 
 }  // namespace
 
+namespace {
+struct Server;
+}
+
 struct e2e_ctx {
   int device = 0;
+  std::unique_ptr<Server> server;
   e2e_opts opts{};
   std::mutex mu;
   uint64_t next_id = 1;
@@ -101,6 +114,7 @@ struct e2e_ctx {
   std::map<uint64_t, std::unique_ptr<Spectrum>> spectra;
   std::map<uint64_t, std::unique_ptr<Frame>> frames;
   cudaMemPool_t pool = nullptr;
+  cudaStream_t free_stream = nullptr;  // where library frames are returned to the pool
   // kernel timing of the most recent render (opts.kernel_timing)
   struct Timed {
     const char* name;
@@ -111,6 +125,48 @@ struct e2e_ctx {
 };
 
 namespace {
+
+// ---------------------------------------------------------------- serving state
+struct Job {
+  uint64_t id = 0;
+  uint64_t model = 0;
+  std::vector<uint64_t> spec;
+  std::vector<void*> dst;  // empty: library-owned frames
+  std::vector<int64_t> pitch;
+  int precision = 0, dtype = 0;
+  int status = E2E_JOB_QUEUED;
+  int err = 0;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  float device_ms = 0.f;
+  int64_t budget = 0, stamps = 0;
+  uint64_t frame_id = 0;
+  int slot = -1;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool finished_on_device = false;
+  bool express = false;  // small job: admitted before regular ones, high-priority stream
+};
+
+struct Server {
+  e2e_ctx* ctx = nullptr;
+  std::thread th;
+  std::mutex mu;
+  std::condition_variable cv;       // wakes the loop
+  std::condition_variable cv_done;  // wakes waiters
+  bool stopping = false;
+  std::deque<uint64_t> queue;     // regular jobs, FIFO
+  std::deque<uint64_t> express;   // jobs of <= express_stamps stamps, FIFO, admitted first
+  int64_t express_stamps = 0;
+  std::map<uint64_t, Job> jobs;
+  std::vector<cudaStream_t> slots;     // lowest stream priority
+  std::vector<cudaStream_t> slots_hi;  // highest stream priority (express jobs)
+  std::vector<uint64_t> slot_job;  // 0 = free
+  size_t budget = 0, in_use = 0;
+  uint64_t next_id = 1;
+  std::chrono::steady_clock::time_point t0;
+  double now_ms() const {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
 
 struct DeviceGuard {
   int prev = -1;
@@ -143,6 +199,8 @@ double quad_min(const double* c) {
   return m;
 }
 
+constexpr double kMaxEllipEps = 0.2;
+
 int validate_slice(const e2e_order_slice& s, int n_det, int psf, int idx) {
   char buf[256];
   auto bad = [&](const char* why) {
@@ -162,7 +220,22 @@ int validate_slice(const e2e_order_slice& s, int n_det, int psf, int idx) {
   if (!finite_all(s.sigma_x, 3) || !finite_all(s.sigma_y, 3)) return bad("non-finite PSF width coefficient");
   if (quad_min(s.sigma_x) <= 0 || quad_min(s.sigma_y) <= 0) return bad("PSF width must stay > 0 on [-1, 1]");
   if (!finite_all(s.slit_weights, s.n_slit)) return bad("non-finite slit weight");
-  if (psf == E2E_PSF_ELLIPTICAL && !std::isfinite(s.theta)) return bad("non-finite theta");
+  if (psf == E2E_PSF_ELLIPTICAL) {
+    if (!std::isfinite(s.theta)) return bad("non-finite theta");
+    // The elliptical renderers expand the conditional profile of y given x in eps * tau,
+    // |tau| <= 1/2 within a pixel column; eps = beta / s_c must stay within the range where
+    // the truncated series is exact to FP32 (checked at every wavelength sample).
+    const double c = std::cos(s.theta), sn = std::sin(s.theta);
+    for (int j = 0; j < s.n_lambda; ++j) {
+      const double lt = (double)(2 * j + 1 - s.n_lambda) / (double)s.n_lambda;
+      const double sa = (s.sigma_x[2] * lt + s.sigma_x[1]) * lt + s.sigma_x[0];
+      const double sb = (s.sigma_y[2] * lt + s.sigma_y[1]) * lt + s.sigma_y[0];
+      const double vx = sa * sa * c * c + sb * sb * sn * sn, vy = sa * sa * sn * sn + sb * sb * c * c;
+      const double cxy = (sa * sa - sb * sb) * sn * c;
+      const double eps = cxy / vx / std::sqrt(vy - cxy * cxy / vx);
+      if (!(std::fabs(eps) <= kMaxEllipEps)) return bad("elliptical PSF too strongly sheared: |cxy / sqrt(vx (vx vy - cxy^2))| must stay <= 0.2");
+    }
+  }
   return E2E_OK;
 }
 
@@ -213,8 +286,9 @@ double variant_cost(int K, int DX, int DY, int B) {
 int plan_model(Model* m) {
   Plan& P = m->plan;
   const int ns = (int)m->slices.size();
-  if (m->psf != E2E_PSF_SEPARABLE || ns == 0) {
-    P.ok = (ns == 0);
+  const bool ellip = m->psf == E2E_PSF_ELLIPTICAL;
+  if (ns == 0) {
+    P.ok = true;
     return E2E_OK;
   }
   // ---- device pass: exact window origins of every stamp
@@ -249,13 +323,14 @@ int plan_model(Model* m) {
   cudaFree(d_spans);
   if (rc != E2E_OK) return rc;
 
-  // ---- tile variant and run length (one for the whole model; per-K kernels)
+  // ---- tile variant and run length (one for the whole model; per-K kernels).  The
+  // elliptical kernel has no run tiles: one item per (32-sample, 16-point) block.
   int K = 0;
   for (auto& s : m->slices) K = std::max(K, s.d.K);
   double best = 1e300;
   int bB = 1, bDX = 0, bDY = 0;
   const int variants[5][2] = {{0, 0}, {1, 1}, {1, 2}, {1, 3}, {2, 2}};
-  for (int q = 0; q <= 4; ++q) {  // B = 1..16
+  for (int q = 0; q <= 4 && !ellip; ++q) {  // B = 1..16
     const int B = 1 << q;
     int sx = 0, sy = 0;
     for (int i = 0; i < ns; ++i) {
@@ -298,9 +373,10 @@ int plan_model(Model* m) {
         const auto& s = m->slices[i].d;
         if (s.K != Kg) continue;
         const int nrc_full = (s.n_slit + P.B - 1) / P.B;
-        const int KC = nrc_full <= 16 ? n_k16[i] : P.B;  // 16-point blocks per item
+        int KC = nrc_full <= 16 ? n_k16[i] : P.B;  // 16-point blocks per item
         const int nrc = std::min(nrc_full, (KC * 16 + P.B - 1) / P.B);
-        const int JB = std::max(1, std::min(jb_cap, std::min((8 + nrc - 1) / nrc, 16 / nrc)));
+        int JB = std::max(1, std::min(jb_cap, std::min((8 + nrc - 1) / nrc, 16 / nrc)));
+        if (ellip) KC = JB = 1;  // <= 512 stamps: <= 512 deposits per box pixel
         P.JB = std::max(P.JB, JB);
         for (int b0 = 0; b0 < n_jb[i]; b0 += JB)
           for (int c0 = 0; c0 < n_k16[i]; c0 += KC) {
@@ -342,7 +418,8 @@ int plan_model(Model* m) {
       P.max_area = std::max(P.max_area, it.bw * it.bh);
       P.nk_max = std::max(P.nk_max, it.nk);
     }
-    P.smem = mixed_smem_bytes(P.max_area, P.JB, P.nk_max, P.B, P.max_deg + 1);
+    P.smem = ellip ? ellip_smem_bytes(P.max_area, P.nk_max, P.max_deg + 1)
+                   : mixed_smem_bytes(P.max_area, P.JB, P.nk_max, P.B, P.max_deg + 1);
     if ((int)P.smem <= optin) break;
     if (jb_cap == 1)
       return fail(E2E_EINVAL, "trace footprint of a work item exceeds on-chip memory (area " +
@@ -474,7 +551,7 @@ int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, in
   std::vector<const double*> table;
   int rc = resolve_flux(ctx, m, n_spec, spec_ids, table);
   if (rc != E2E_OK) return rc;
-  if (m->psf != E2E_PSF_SEPARABLE) return fail(E2E_EINVAL, "elliptical PSF render not available in this build");
+  const bool ellip = m->psf == E2E_PSF_ELLIPTICAL;
 
   if (ctx->opts.kernel_timing) reset_timing(ctx);
   Scratch sc{{}, st};
@@ -511,9 +588,13 @@ int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, in
     E2E_CK(cudaMemcpyAsync(d_apitch, apitch.data(), apitch.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     for (int K : m->Ks) {
       // one launch per K over all slices; slices of another K exit at once
-      KernelTimer kt(ctx, st, "render_fp64");
-      E2E_CK(launch_render_fp64(K, (int)m->slices.size(), m->max_stamps, m->d_slices, d_table, m->d_u, d_acc,
-                                d_apitch, st));
+      KernelTimer kt(ctx, st, ellip ? "render_fp64_ellip" : "render_fp64");
+      if (ellip)
+        E2E_CK(launch_render_fp64_ellip(K, (int)m->slices.size(), m->max_stamps, m->d_slices, d_table, m->d_u,
+                                        d_acc, d_apitch, st));
+      else
+        E2E_CK(launch_render_fp64(K, (int)m->slices.size(), m->max_stamps, m->d_slices, d_table, m->d_u, d_acc,
+                                  d_apitch, st));
     }
     if (dtype == E2E_F32)
       for (int d = 0; d < m->n_det; ++d) {
@@ -529,9 +610,13 @@ int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, in
   float2* store = nullptr;
   E2E_CK(sc.get((void**)&store, (size_t)P.store_elems * sizeof(float2)));
   for (auto& g : P.groups) {
-    KernelTimer kt(ctx, st, "render_mixed");
-    E2E_CK(launch_render_mixed(g.K, P.DX, P.DY, m->d_slices, d_table, m->d_u, P.d_items + g.first, g.count, store,
-                               P.B, P.JB, P.nk_max, P.max_deg, P.smem, st));
+    KernelTimer kt(ctx, st, ellip ? "render_ellip" : "render_mixed");
+    if (ellip)
+      E2E_CK(launch_render_ellip(g.K, m->d_slices, d_table, m->d_u, P.d_items + g.first, g.count, store, P.nk_max,
+                                 P.max_deg, P.smem, st));
+    else
+      E2E_CK(launch_render_mixed(g.K, P.DX, P.DY, m->d_slices, d_table, m->d_u, P.d_items + g.first, g.count,
+                                 store, P.B, P.JB, P.nk_max, P.max_deg, P.smem, st));
   }
   {
     KernelTimer kt(ctx, st, "merge");
@@ -543,6 +628,40 @@ int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, in
 }  // namespace
 
 // ====================================================================== C ABI
+
+namespace {
+// Library-owned frames for model m, allocated in stream order on st.
+int alloc_frame(const Model* m, int dtype, cudaStream_t st, std::unique_ptr<Frame>& out) {
+  auto f = std::make_unique<Frame>();
+  f->dtype = dtype;
+  f->H = m->H;
+  f->W = m->W;
+  const size_t es = dtype == E2E_F32 ? 4 : 8;
+  cudaError_t e = cudaEventCreateWithFlags(&f->ready, cudaEventDisableTiming);
+  for (int d = 0; d < m->n_det && e == cudaSuccess; ++d) {
+    void* p = nullptr;
+    e = cudaMallocAsync(&p, (size_t)m->H[d] * m->W[d] * es, st);
+    if (e == cudaSuccess) f->ptrs.push_back(p);
+  }
+  if (e != cudaSuccess) {
+    for (void* q : f->ptrs) cudaFreeAsync(q, st);
+    if (f->ready) cudaEventDestroy(f->ready);
+    return cuda_fail(e, "frame allocation");
+  }
+  out = std::move(f);
+  return E2E_OK;
+}
+
+// Return a frame's buffers to the pool once its last recorded use has completed.
+void free_frame(e2e_ctx* ctx, Frame* f) {
+  if (f->ready) cudaStreamWaitEvent(ctx->free_stream, f->ready, 0);
+  for (void* p : f->ptrs) cudaFreeAsync(p, ctx->free_stream);
+  f->ptrs.clear();
+  if (f->ready) cudaEventDestroy(f->ready);
+  f->ready = nullptr;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -566,20 +685,27 @@ int e2e_create(e2e_ctx** out, int32_t device, const e2e_opts* opts) {
     uint64_t thr = UINT64_MAX;
     cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
+  e = cudaStreamCreateWithFlags(&c->free_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "stream creation");
+  }
   *out = c;
   return E2E_OK;
 }
 
 void e2e_destroy(e2e_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->server) e2e_server_stop(ctx);
   {
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
     std::lock_guard<std::mutex> lk(ctx->mu);
     for (auto& kv : ctx->models) free_model(kv.second.get());
     for (auto& kv : ctx->spectra) cudaFree(kv.second->d_flux);
-    for (auto& kv : ctx->frames)
-      for (void* p : kv.second->ptrs) cudaFree(p);
+    for (auto& kv : ctx->frames) free_frame(ctx, kv.second.get());
+    cudaStreamSynchronize(ctx->free_stream);
+    cudaStreamDestroy(ctx->free_stream);
     reset_timing(ctx);
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   }
@@ -737,24 +863,13 @@ int e2e_render_alloc(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint
   std::lock_guard<std::mutex> lk(ctx->mu);
   Model* m = find_model(ctx, model_id);
   if (!m) return fail(E2E_ENOTFOUND, "unknown model id");
-  auto f = std::make_unique<Frame>();
-  f->dtype = dtype;
-  f->H = m->H;
-  f->W = m->W;
-  const size_t es = dtype == E2E_F32 ? 4 : 8;
-  for (int d = 0; d < m->n_det; ++d) {
-    void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, (size_t)m->H[d] * m->W[d] * es);
-    if (e != cudaSuccess) {
-      for (void* q : f->ptrs) cudaFree(q);
-      return cuda_fail(e, "frame allocation");
-    }
-    f->ptrs.push_back(p);
-  }
-  int rc = render_impl(ctx, m, n_spec, spec_ids, precision, dtype, f->ptrs.data(), nullptr, (cudaStream_t)stream);
+  std::unique_ptr<Frame> f;
+  int rc = alloc_frame(m, dtype, (cudaStream_t)stream, f);
+  if (rc != E2E_OK) return rc;
+  rc = render_impl(ctx, m, n_spec, spec_ids, precision, dtype, f->ptrs.data(), nullptr, (cudaStream_t)stream);
+  cudaEventRecord(f->ready, (cudaStream_t)stream);
   if (rc != E2E_OK) {
-    cudaStreamSynchronize((cudaStream_t)stream);
-    for (void* q : f->ptrs) cudaFree(q);
+    free_frame(ctx, f.get());
     return rc;
   }
   *frame_id = ctx->next_id++;
@@ -773,8 +888,10 @@ int e2e_fetch_frame(e2e_ctx* ctx, uint64_t frame_id, int32_t detector, void* dst
   if (detector < 0 || detector >= (int)f->ptrs.size()) return fail(E2E_EINVAL, "detector out of range");
   const size_t need = (size_t)f->H[detector] * f->W[detector] * (f->dtype == E2E_F32 ? 4 : 8);
   if (bytes != need) return fail(E2E_EINVAL, "byte count differs from the frame size");
+  E2E_CK(cudaStreamWaitEvent((cudaStream_t)stream, f->ready, 0));
   E2E_CK(cudaMemcpyAsync(dst, f->ptrs[detector], bytes, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                          (cudaStream_t)stream));
+  E2E_CK(cudaEventRecord(f->ready, (cudaStream_t)stream));
   return E2E_OK;
 }
 
@@ -784,8 +901,7 @@ int e2e_release_frame(e2e_ctx* ctx, uint64_t frame_id) {
   std::lock_guard<std::mutex> lk(ctx->mu);
   auto it = ctx->frames.find(frame_id);
   if (it == ctx->frames.end()) return fail(E2E_ENOTFOUND, "unknown frame id");
-  cudaDeviceSynchronize();
-  for (void* p : it->second->ptrs) cudaFree(p);
+  free_frame(ctx, it->second.get());
   ctx->frames.erase(it);
   return E2E_OK;
 }
@@ -984,6 +1100,325 @@ int e2e_update_model(e2e_ctx* ctx, uint64_t model_id, const double* cx, const do
   m->dev = dv;
   free_plan(m->plan);
   return plan_model(m);
+}
+
+}  // extern "C"
+
+namespace {
+
+struct CallbackPayload {
+  Server* srv;
+  uint64_t id;
+};
+
+void CUDART_CB job_finished(void* p) {
+  auto* cp = static_cast<CallbackPayload*>(p);
+  {
+    std::lock_guard<std::mutex> lk(cp->srv->mu);
+    auto it = cp->srv->jobs.find(cp->id);
+    if (it != cp->srv->jobs.end()) it->second.finished_on_device = true;
+  }
+  cp->srv->cv.notify_all();
+  delete cp;
+}
+
+// Memory a job holds while in flight: its scratch plus library-owned frames.
+int64_t job_budget(const Model* m, const Job& j) {
+  int64_t b = 64 << 10;  // launch tables
+  if (j.precision == E2E_PREC_MIXED) b += m->plan.store_elems * 8;
+  else if (j.dtype == E2E_F32)
+    for (int d = 0; d < m->n_det; ++d) b += (int64_t)m->H[d] * m->W[d] * 8;
+  if (j.dst.empty())
+    for (int d = 0; d < m->n_det; ++d) b += (int64_t)m->H[d] * m->W[d] * (j.dtype == E2E_F32 ? 4 : 8);
+  return b;
+}
+
+// Admit queued jobs (FIFO) while a slot and budget are free; launch them on their slots.
+void admit_jobs(Server* S, std::unique_lock<std::mutex>& lk) {
+  e2e_ctx* ctx = S->ctx;
+  while ((!S->queue.empty() || !S->express.empty()) && !S->stopping) {
+    std::deque<uint64_t>& q = S->express.empty() ? S->queue : S->express;
+    const uint64_t id = q.front();
+    Job& j = S->jobs[id];
+    if (j.status != E2E_JOB_QUEUED) {  // cancelled
+      q.pop_front();
+      continue;
+    }
+    int slot = -1;
+    for (size_t q = 0; q < S->slot_job.size(); ++q)
+      if (S->slot_job[q] == 0) {
+        slot = (int)q;
+        break;
+      }
+    if (slot < 0 || S->in_use + (size_t)j.budget > S->budget) break;
+    q.pop_front();
+    S->slot_job[slot] = id;
+    S->in_use += j.budget;
+    j.slot = slot;
+    j.status = E2E_JOB_RUNNING;
+    j.t_admit = S->now_ms();
+    cudaStream_t st = j.express ? S->slots_hi[slot] : S->slots[slot];
+    // launch outside the server lock; the context lock guards models and spectra
+    lk.unlock();
+    int rc = E2E_OK;
+    uint64_t frame_id = 0;
+    {
+      std::lock_guard<std::mutex> clk(ctx->mu);
+      Model* m = find_model(ctx, j.model);
+      if (!m) rc = fail(E2E_ENOTFOUND, "model unloaded before the job ran");
+      std::vector<void*> dst = j.dst;
+      std::unique_ptr<Frame> fr;
+      if (rc == E2E_OK && dst.empty()) {
+        rc = alloc_frame(m, j.dtype, st, fr);
+        if (rc == E2E_OK) dst = fr->ptrs;
+      }
+      if (rc == E2E_OK && cudaEventRecord(j.ev0, st) != cudaSuccess) rc = fail(E2E_ECUDA, "event record");
+      if (rc == E2E_OK)
+        rc = render_impl(ctx, m, (int)j.spec.size(), j.spec.data(), j.precision, j.dtype, dst.data(),
+                         j.pitch.empty() ? nullptr : j.pitch.data(), st);
+      if (rc == E2E_OK && cudaEventRecord(j.ev1, st) != cudaSuccess) rc = fail(E2E_ECUDA, "event record");
+      if (fr) cudaEventRecord(fr->ready, st);
+      if (rc == E2E_OK && fr) {
+        frame_id = ctx->next_id++;
+        ctx->frames[frame_id] = std::move(fr);
+      } else if (fr) {
+        free_frame(ctx, fr.get());
+      }
+    }
+    if (rc == E2E_OK) {
+      auto* cp = new CallbackPayload{S, id};
+      if (cudaLaunchHostFunc(st, job_finished, cp) != cudaSuccess) {
+        delete cp;
+        rc = fail(E2E_ECUDA, "cudaLaunchHostFunc");
+      }
+    }
+    lk.lock();
+    Job& jj = S->jobs[id];
+    jj.frame_id = frame_id;
+    if (rc != E2E_OK) {  // the job failed to launch: finish it with its error
+      cudaStreamSynchronize(st);
+      jj.status = rc;
+      jj.err = rc;
+      jj.t_done = S->now_ms();
+      S->slot_job[slot] = 0;
+      S->in_use -= jj.budget;
+      S->cv_done.notify_all();
+    }
+  }
+}
+
+// Retire jobs whose completion callback ran: times, budget, slot.
+void retire_jobs(Server* S) {
+  for (size_t q = 0; q < S->slot_job.size(); ++q) {
+    const uint64_t id = S->slot_job[q];
+    if (!id) continue;
+    Job& j = S->jobs[id];
+    if (!j.finished_on_device) continue;
+    j.t_done = S->now_ms();
+    cudaEventElapsedTime(&j.device_ms, j.ev0, j.ev1);
+    j.status = E2E_JOB_DONE;
+    S->slot_job[q] = 0;
+    S->in_use -= j.budget;
+    S->cv_done.notify_all();
+  }
+}
+
+void server_loop(Server* S) {
+  cudaSetDevice(S->ctx->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  for (;;) {
+    retire_jobs(S);
+    bool busy = false;
+    for (uint64_t id : S->slot_job) busy = busy || id != 0;
+    if (S->stopping && !busy) break;
+    admit_jobs(S, lk);
+    S->cv.wait_for(lk, std::chrono::milliseconds(50));
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int e2e_server_start(e2e_ctx* ctx, const e2e_server_cfg* cfg) {
+  if (!ctx) return fail(E2E_EINVAL, "null context");
+  DeviceGuard g(ctx->device);
+  if (ctx->server) return fail(E2E_EINVAL, "server already running");
+  auto S = std::make_unique<Server>();
+  S->ctx = ctx;
+  int slots = (cfg && cfg->max_inflight > 0) ? cfg->max_inflight : ctx->opts.max_inflight;
+  if (slots < 1) slots = 1;
+  size_t budget = cfg ? cfg->budget_bytes : 0;
+  if (!budget) budget = ctx->opts.pool_bytes;
+  if (!budget) {
+    size_t fr = 0, tot = 0;
+    E2E_CK(cudaMemGetInfo(&fr, &tot));
+    budget = (size_t)(0.9 * (double)fr);
+  }
+  S->budget = budget;
+  S->express_stamps = cfg ? cfg->express_stamps : 0;
+  int prio_lo = 0, prio_hi = 0;
+  E2E_CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+  for (int q = 0; q < slots; ++q) {
+    cudaStream_t st, sh;
+    E2E_CK(cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio_lo));
+    E2E_CK(cudaStreamCreateWithPriority(&sh, cudaStreamNonBlocking, prio_hi));
+    S->slots.push_back(st);
+    S->slots_hi.push_back(sh);
+    S->slot_job.push_back(0);
+  }
+  S->t0 = std::chrono::steady_clock::now();
+  Server* raw = S.get();
+  ctx->server = std::move(S);
+  raw->th = std::thread(server_loop, raw);
+  return E2E_OK;
+}
+
+int e2e_submit(e2e_ctx* ctx, const e2e_job* job, uint64_t* request_id) {
+  if (!ctx || !job || !request_id) return fail(E2E_EINVAL, "null argument");
+  Server* S = ctx->server.get();
+  if (!S) return fail(E2E_EINVAL, "server not running");
+  if (job->dtype != E2E_F32 && job->dtype != E2E_F64) return fail(E2E_EINVAL, "bad dtype");
+  if (job->precision != E2E_PREC_MIXED && job->precision != E2E_PREC_FP64) return fail(E2E_EINVAL, "bad precision");
+  Job j;
+  j.model = job->model_id;
+  j.precision = job->precision;
+  j.dtype = job->dtype;
+  if (job->n_spec > 0) j.spec.assign(job->spec_ids, job->spec_ids + job->n_spec);
+  {
+    std::lock_guard<std::mutex> clk(ctx->mu);
+    Model* m = find_model(ctx, job->model_id);
+    if (!m) return fail(E2E_ENOTFOUND, "unknown model id");
+    std::vector<const double*> table;
+    int rc = resolve_flux(ctx, m, (int)j.spec.size(), j.spec.data(), table);
+    if (rc != E2E_OK) return rc;
+    if (job->dst) {
+      j.dst.assign(job->dst, job->dst + m->n_det);
+      for (void* p : j.dst)
+        if (!p) return fail(E2E_EINVAL, "null destination frame");
+      if (job->pitch_elems) j.pitch.assign(job->pitch_elems, job->pitch_elems + m->n_det);
+    }
+    j.budget = job_budget(m, j);
+    for (auto& sl : m->slices) j.stamps += (int64_t)sl.d.n_lambda * sl.d.n_slit;
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  if ((size_t)j.budget > S->budget)
+    return fail(E2E_ETOOBIG, "job needs " + std::to_string(j.budget) + " bytes; the serving budget is " +
+                                 std::to_string(S->budget));
+  if (S->stopping) return fail(E2E_EINVAL, "server is stopping");
+  if (cudaEventCreate(&j.ev0) != cudaSuccess || cudaEventCreate(&j.ev1) != cudaSuccess)
+    return fail(E2E_ECUDA, "event creation");
+  j.id = S->next_id++;
+  j.t_submit = S->now_ms();
+  const uint64_t id = j.id;
+  S->jobs[id] = std::move(j);
+  Job& jq = S->jobs[id];
+  jq.express = S->express_stamps > 0 && jq.stamps <= S->express_stamps;
+  (jq.express ? S->express : S->queue).push_back(id);
+  *request_id = id;
+  S->cv.notify_all();
+  return E2E_OK;
+}
+
+static void fill_info(const Job& j, e2e_job_info* info) {
+  if (!info) return;
+  info->status = j.status;
+  info->submit_ms = j.t_submit;
+  info->admit_ms = j.t_admit;
+  info->done_ms = j.t_done;
+  info->device_ms = j.device_ms;
+  info->budget_bytes = j.budget;
+  info->frame_id = j.frame_id;
+  info->stamps = j.stamps;
+}
+
+int e2e_poll(e2e_ctx* ctx, uint64_t request_id, e2e_job_info* info) {
+  if (!ctx || !ctx->server) return fail(E2E_EINVAL, "server not running");
+  Server* S = ctx->server.get();
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->jobs.find(request_id);
+  if (it == S->jobs.end()) return fail(E2E_ENOTFOUND, "unknown request id");
+  fill_info(it->second, info);
+  return E2E_OK;
+}
+
+int e2e_wait(e2e_ctx* ctx, uint64_t request_id, int32_t timeout_ms, e2e_job_info* info) {
+  if (!ctx || !ctx->server) return fail(E2E_EINVAL, "server not running");
+  Server* S = ctx->server.get();
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto done = [&] {
+    auto it = S->jobs.find(request_id);
+    return it == S->jobs.end() || (it->second.status != E2E_JOB_QUEUED && it->second.status != E2E_JOB_RUNNING);
+  };
+  if (timeout_ms < 0) S->cv_done.wait(lk, done);
+  else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done)) {
+    auto it = S->jobs.find(request_id);
+    if (it != S->jobs.end()) fill_info(it->second, info);
+    return fail(E2E_ETIMEOUT, "job not finished within the timeout");
+  }
+  auto it = S->jobs.find(request_id);
+  if (it == S->jobs.end()) return fail(E2E_ENOTFOUND, "unknown request id");
+  fill_info(it->second, info);
+  if (it->second.status < 0) return fail(it->second.status, "job failed");
+  return E2E_OK;
+}
+
+int e2e_cancel(e2e_ctx* ctx, uint64_t request_id) {
+  if (!ctx || !ctx->server) return fail(E2E_EINVAL, "server not running");
+  Server* S = ctx->server.get();
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->jobs.find(request_id);
+  if (it == S->jobs.end()) return fail(E2E_ENOTFOUND, "unknown request id");
+  if (it->second.status != E2E_JOB_QUEUED) return fail(E2E_EINVAL, "only queued jobs can be cancelled");
+  it->second.status = E2E_ECANCELLED;
+  it->second.t_done = S->now_ms();
+  S->cv_done.notify_all();
+  return E2E_OK;
+}
+
+int e2e_forget(e2e_ctx* ctx, uint64_t request_id) {
+  if (!ctx || !ctx->server) return fail(E2E_EINVAL, "server not running");
+  Server* S = ctx->server.get();
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->jobs.find(request_id);
+  if (it == S->jobs.end()) return fail(E2E_ENOTFOUND, "unknown request id");
+  if (it->second.status == E2E_JOB_RUNNING || it->second.status == E2E_JOB_QUEUED)
+    return fail(E2E_EINVAL, "job still pending");
+  cudaEventDestroy(it->second.ev0);
+  cudaEventDestroy(it->second.ev1);
+  S->jobs.erase(it);
+  return E2E_OK;
+}
+
+int e2e_server_stop(e2e_ctx* ctx) {
+  if (!ctx || !ctx->server) return fail(E2E_EINVAL, "server not running");
+  Server* S = ctx->server.get();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stopping = true;
+    for (auto* qq : {&S->queue, &S->express}) {
+      for (uint64_t id : *qq) {
+        Job& j = S->jobs[id];
+        if (j.status == E2E_JOB_QUEUED) {
+          j.status = E2E_ECANCELLED;
+          j.t_done = S->now_ms();
+        }
+      }
+      qq->clear();
+    }
+  }
+  S->cv.notify_all();
+  S->th.join();
+  S->cv_done.notify_all();
+  DeviceGuard g(ctx->device);
+  for (auto& kv : S->jobs) {
+    cudaEventDestroy(kv.second.ev0);
+    cudaEventDestroy(kv.second.ev1);
+  }
+  for (cudaStream_t st : S->slots) cudaStreamDestroy(st);
+  for (cudaStream_t st : S->slots_hi) cudaStreamDestroy(st);
+  ctx->server.reset();
+  return E2E_OK;
 }
 
 int e2e_kernel_times(e2e_ctx* ctx, const char** names, float* ms, int32_t cap, int32_t* n) {

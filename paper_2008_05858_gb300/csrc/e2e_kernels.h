@@ -27,6 +27,14 @@ cudaError_t launch_render_mixed(int K, int DX, int DY, const DevSlice* slices, c
 cudaError_t launch_merge(const Tile* tiles, int n_tiles, const int32_t* lists, const Item* items, const float2* store,
                          void* const* dst, int dtype, const int64_t* pitch, const int* dims, cudaStream_t st);
 
+size_t ellip_smem_bytes(int area, int nk_max, int nd);
+cudaError_t launch_render_ellip(int K, const DevSlice* slices, const double* const* flux_tab, const double* u_all,
+                                const Item* items, int n_items, float2* store, int nk_max, int max_deg, size_t smem,
+                                cudaStream_t st);
+cudaError_t launch_render_fp64_ellip(int K, int n_slices, int64_t max_stamps, const DevSlice* slices,
+                                     const double* const* flux_tab, const double* u_all, double* const* acc,
+                                     const int64_t* pitch, cudaStream_t st);
+
 size_t adjoint_smem_bytes(int max_area, int max_deg);
 cudaError_t launch_adjoint(int K, const DevSlice* slices, const double* const* flux_tab, const double* u_all,
                            const Item* items, int n_items, const void* const* dldi, const int64_t* pitch, int dtype,

@@ -1,0 +1,62 @@
+// Device helpers shared by the mixed-precision renderers (separable and elliptical PSF):
+// exact-split FP32 pairs, the fixed-point box format and the kernel argument block.
+#pragma once
+#include "e2e_device.cuh"
+
+namespace e2e {
+
+// Normalised coordinate of bin-centred sample j of n, (2j + 1 - n) / n, as a product with the
+// correctly rounded reciprocal (the plan and the render compute it identically).
+__device__ __forceinline__ double norm_sample_r(int j, int n, double inv_n) { return (double)(2 * j + 1 - n) * inv_n; }
+
+struct MixedArgs {
+  const DevSlice* slices;
+  const double* const* flux_tab;
+  const double* u_all;
+  const Item* items;
+  float2* store;
+  int B;        // slit points per run
+  int JB;       // largest number of 32-sample blocks in an item
+  int nk_max;   // largest number of slit points in an item
+  int max_deg;  // largest degree among the launched slices
+};
+
+__device__ __forceinline__ float2 split_df(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
+// a + b as an unevaluated pair (s, e), s = fl(a + b), a + b = s + e exactly (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (hi * 2^22 + lo) * scale as an FP32 pair (h, l) with h + l exact to ~2^-48: the 54-bit
+// integer is cut into four 16-bit pieces (each exact in FP32) and summed with TwoSum.
+__device__ __forceinline__ float2 fixed_to_pair(int hi, unsigned lo, float scale) {
+  const float t1 = (float)(hi >> 16) * 274877906944.f;  // 2^38
+  const float t2 = (float)(hi & 0xFFFF) * 4194304.f;    // 2^22
+  const float t3 = (float)(lo >> 16) * 65536.f;         // 2^16
+  const float t4 = (float)(lo & 0xFFFFu);
+  float s, e, e2;
+  two_sum(t1, t2, s, e);
+  two_sum(s, t3, s, e2);
+  e += e2;
+  two_sum(s, t4, s, e2);
+  e += e2;
+  return make_float2(s * scale, e * scale);
+}
+
+// Fixed-point deposit of val into a box pixel: the value scaled by 2^P is cut into a high
+// word (multiples of 2^22, signed) and a low word (< 2^22, unsigned), both added with
+// integer atomics, so the sums are exact and independent of the order of the deposits.
+__device__ __forceinline__ void box_deposit(int* hi, unsigned* lo, float val, float sc, float sc_hi) {
+  const float hf = floorf(val * sc_hi);
+  const float lf = fmaf(-hf, 4194304.f, val * sc);
+  atomicAdd(hi, __float2int_rz(hf));
+  atomicAdd(lo, __float2uint_rn(lf));
+}
+
+}  // namespace e2e

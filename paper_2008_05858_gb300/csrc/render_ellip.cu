@@ -1,0 +1,453 @@
+// Elliptical (rotated) Gaussian PSF: the mixed-precision tiled renderer and the plain FP64
+// renderer.
+//
+// The PSF of an order-slice is a bivariate normal with widths sigma_a(lt), sigma_b(lt) along
+// axes rotated by theta (the asymmetric Gaussian of Sec. 2.2, with a rotation).  Its pixel
+// integral is no product of 1-D integrals.  Write the density as the x-marginal times the
+// conditional density of y given x:
+//
+//   x ~ N(x_c, vx),   y | x ~ N(y_c + beta (x - x_c), s_c^2),   beta = cxy / vx,   s_c^2 = vy - beta cxy.
+//
+// Over pixel column m, x = x_c + tb + tau with tb = i0 + m - x_c the column centre and
+// |tau| <= 1/2, and with eps = beta / s_c,
+//
+//   I[m, n] = int dtau phi_x(tb + tau) [Phi(V_{n+1} - eps tau) - Phi(V_n - eps tau)],
+//   V_n = (r0 + n - 1/2 - y_c - beta tb) / s_c.
+//
+// Taylor in eps tau about the column centre, Phi(V - eps tau) = sum_k (-eps tau)^k / k! Phi^(k)(V)
+// with Phi^(k)(V) = (-1)^(k-1) He_(k-1)(V) phi(V) (probabilists' Hermite polynomials), gives
+//
+//   I[m, n] = mu0[m] { Phi(V_{n+1}) - Phi(V_n) + phi(V_{n+1}) G_m(V_{n+1}) - phi(V_n) G_m(V_n) },
+//   G_m(V)  = sum_{k >= 1} a_k He_(k-1)(V),   a_k = -eps^k mom_k[m] / k!,
+//
+// where mu0[m] is the column's x-integral and mom_k[m] the k-th moment of tau under phi_x
+// restricted to the column, normalised by its mass (Gauss-Legendre on the column).  With
+// |eps tau| <= |eps| / 2 and |eps| <= 0.2 (checked when the model is loaded), the series cut
+// after k = 6 is below 1e-9 of the pixel value (FP32 kernel); the FP64 kernel keeps k <= 9.
+// The column's own Phi differences carry the full accuracy: they are formed exactly like the
+// separable PSF's pixel integrals (tails subtracted on one side of the conditional mean, erf
+// across it), only with a per-column centre.
+#include "e2e_device.cuh"
+#include "e2e_kernels.h"
+#include "mixed_common.cuh"
+#include "phi32.cuh"
+#include "quad_coeffs.h"
+
+namespace e2e {
+
+constexpr int kEThreads = 128;
+constexpr int kEWarps = kEThreads / 32;
+constexpr float kSqrt2Ln2 = 1.17741002f;         // V = w sqrt(2 ln 2) for w in log2 units
+constexpr float kTwoOverSqrt2Pi = 0.797884561f;  // 2 phi(V) / exp(-V^2 / 2)
+constexpr double kLog2e = 1.44269504088896340736;
+
+// Covariance of the rotated PSF at lt and the conditional parameters derived from it.
+struct EllipParams {
+  double vx, gx, beta, sc, eps;
+};
+
+__device__ __forceinline__ EllipParams ellip_params(const DevSlice& S, double lt) {
+  const double sa = fma(fma(S.sx[2], lt, S.sx[1]), lt, S.sx[0]);
+  const double sb = fma(fma(S.sy[2], lt, S.sy[1]), lt, S.sy[0]);
+  const double a2 = sa * sa, b2 = sb * sb, c = S.cos_t, s = S.sin_t;
+  EllipParams p;
+  p.vx = a2 * c * c + b2 * s * s;
+  const double vy = a2 * s * s + b2 * c * c;
+  const double cxy = (a2 - b2) * s * c;
+  p.gx = sqrt(p.vx);
+  p.beta = cxy / p.vx;
+  p.sc = sqrt(vy - p.beta * cxy);
+  p.eps = p.beta / p.sc;
+  return p;
+}
+
+// ------------------------------------------------------------------------------ mixed
+
+// Shared-memory layout of one CTA (bytes), identical on host and device.
+struct EllipLayout {
+  size_t tabP, tabS, tabW, tabU, tabE, stage, stagew, boxh, boxl, total;
+  __host__ __device__ EllipLayout(int J, int NK, int nd, int area) {
+    size_t o = 0;
+    tabP = o; o += (size_t)J * 2 * nd * 8;     // P_b(lt) of x and y per sample
+    tabS = o; o += (size_t)NK * 8;              // s of each slit point
+    tabW = o; o += (size_t)J * 8;               // flux x bin width / 4 per sample, (hi, lo)
+    tabU = o; o += (size_t)NK * 8;              // slit weights, (hi, lo)
+    o = (o + 15) & ~(size_t)15;
+    tabE = o; o += (size_t)J * 32;              // two float4 of PSF constants per sample
+    stage = o; o += (size_t)kEWarps * 32 * 16;  // mapped stamps: origin pixel, offsets
+    stagew = o; o += (size_t)kEWarps * 32 * 8;  // weight / 4 and sample index
+    boxh = o; o += (size_t)area * 4;
+    boxl = o; o += (size_t)area * 4;
+    total = o;
+  }
+};
+
+// One CTA per work item (<= 32 wavelength samples x <= 16 slit points, at most 512 stamps,
+// so no box pixel gets more than 512 fixed-point deposits).  Each warp maps 32 stamps at a
+// time (one per lane, FP64) into its staging area; then the warp is cut into 32 / K groups
+// of K lanes, each group takes one stamp and lane m of the group evaluates column m of the
+// stamp's window: the column's x-integral, the moments of tau, and the K + 1 row edges of
+// its conditional profile, depositing the K pixels into the item's box.
+template <int K>
+__global__ void __launch_bounds__(kEThreads) k_render_ellip(const MixedArgs a) {
+  constexpr int H = K / 2;
+  constexpr int G = 32 / K;  // stamps in flight per warp
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Item it = a.items[blockIdx.x];
+  const DevSlice& S = a.slices[it.slice];
+  const int area = it.bw * it.bh;
+  const int nd = S.degree + 1;
+  const EllipLayout L(32, a.nk_max, a.max_deg + 1, area);
+  double* tabP = reinterpret_cast<double*>(smem + L.tabP);
+  double* tabS = reinterpret_cast<double*>(smem + L.tabS);
+  float2* tabW = reinterpret_cast<float2*>(smem + L.tabW);
+  float2* tabU = reinterpret_cast<float2*>(smem + L.tabU);
+  float4* tabE = reinterpret_cast<float4*>(smem + L.tabE);
+  int4* stage = reinterpret_cast<int4*>(smem + L.stage);
+  float2* stagew = reinterpret_cast<float2*>(smem + L.stagew);
+  int* boxh = reinterpret_cast<int*>(smem + L.boxh);
+  unsigned* boxl = reinterpret_cast<unsigned*>(smem + L.boxl);
+  __shared__ double s_w[kEWarps], s_u[kEWarps];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int p = tid; p < area; p += kEThreads) {
+    boxh[p] = 0;
+    boxl[p] = 0u;
+  }
+  const double* flux = a.flux_tab[S.flux_slot];
+  const double* u = a.u_all + S.u_off;
+  const double inv_nl = 1.0 / (double)S.n_lambda, inv_ns = 1.0 / (double)S.n_slit;
+  double usum = 0.0;
+  for (int kk = tid; kk < it.nk; kk += kEThreads) {
+    const double uk = u[it.k0 + kk];
+    tabS[kk] = norm_sample_r(it.k0 + kk, S.n_slit, inv_ns);
+    tabU[kk] = split_df(uk);
+    usum += fabs(uk);
+  }
+  double wsum = 0.0;
+  for (int jj = tid; jj < it.nj; jj += kEThreads) {
+    const double lt = norm_sample_r(it.j0 + jj, S.n_lambda, inv_nl);
+    for (int b = 0; b < nd; ++b) {
+      tabP[(jj * 2 + 0) * nd + b] = poly_lt_for_b(S.cx, S.degree, b, lt);
+      tabP[(jj * 2 + 1) * nd + b] = poly_lt_for_b(S.cy, S.degree, b, lt);
+    }
+    const EllipParams p = ellip_params(S, lt);
+    const double kq = kSqrtLog2eD * 0.70710678118654752440;  // edge arguments in log2 units
+    const float2 gx = split_df(kq / p.gx), gc = split_df(kq / p.sc), be = split_df(p.beta);
+    tabE[2 * jj + 0] = make_float4(gx.x, gx.y, gc.x, gc.y);
+    tabE[2 * jj + 1] = make_float4(be.x, be.y, (float)p.eps, (float)(-kLog2e / p.vx));
+    const double wj = flux[it.j0 + jj] * S.dlam;
+    tabW[jj] = split_df(wj * 0.25);  // the column and row integrals below are both doubled
+    wsum += fabs(wj);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+    usum += __shfl_xor_sync(0xffffffffu, usum, o);
+  }
+  if (lane == 0) {
+    s_w[warp] = wsum;
+    s_u[warp] = usum;
+  }
+  __syncthreads();
+  double wtot = 0.0, utot = 0.0;
+#pragma unroll
+  for (int q = 0; q < kEWarps; ++q) {
+    wtot += s_w[q];
+    utot += s_u[q];
+  }
+  const double total = wtot * utot;
+  int ex = 0;
+  frexp(total, &ex);
+  const int Psh = total > 0.0 ? max(-100, min(100, 52 - ex)) : 0;
+  const float sc = ldexpf(1.f, Psh), sc_hi = ldexpf(1.f, Psh - 22);
+
+  const int grp = lane / K, m = lane - grp * K;
+  const int nst = it.nj * it.nk;
+  int4* wst = stage + warp * 32;
+  float2* wsw = stagew + warp * 32;
+  for (int base = warp * 32; base < nst && total > 0.0; base += kEWarps * 32) {
+    {  // map stamp base + lane (FP64) into the staging area
+      const int idx = base + lane;
+      int ci = kOffFrame, ri = kOffFrame, jj = 0;
+      float fx = 0.f, fy = 0.f, w = 0.f;
+      if (idx < nst) {
+        jj = idx / it.nk;
+        const int kk = idx - jj * it.nk;
+        double px[9], py[9];
+#pragma unroll
+        for (int b = 0; b <= 8; ++b) {
+          px[b] = b < nd ? tabP[(jj * 2 + 0) * nd + b] : 0.0;
+          py[b] = b < nd ? tabP[(jj * 2 + 1) * nd + b] : 0.0;
+        }
+        const double s = tabS[kk];
+        split_coord(horner_s(px, S.degree, s), ci, fx);
+        split_coord(horner_s(py, S.degree, s), ri, fy);
+        const float2 wj = tabW[jj], uk = tabU[kk];
+        w = fmaf(wj.x, uk.x, fmaf(wj.x, uk.y, wj.y * uk.x));
+      }
+      wst[lane] = make_int4(ci, ri, __float_as_int(fx), __float_as_int(fy));
+      wsw[lane] = make_float2(w, __int_as_float(jj));
+    }
+    __syncwarp();
+    const int nb = min(32, nst - base);
+    for (int b = grp; b < nb && grp < G; b += G) {
+      const int4 st = wst[b];
+      if (st.x == kOffFrame || st.y == kOffFrame) continue;  // uniform over the group
+      const float2 sw = wsw[b];
+      const int jj = __float_as_int(sw.y);
+      const float4 e0 = tabE[2 * jj], e1 = tabE[2 * jj + 1];
+      const float fx = __int_as_float(st.z), fy = __int_as_float(st.w);
+
+      // twice the column's x-integral (same edge formulas as the separable profile)
+      float whL, wlL, whR, wlR;
+      edge_arg((float)(m - H) - 0.5f, fx, e0.x, e0.y, whL, wlL);
+      edge_arg((float)(m - H) + 0.5f, fx, e0.x, e0.y, whR, wlR);
+      const float EL = tail2(whL, wlL), ER = tail2(whR, wlR);
+      const float FL = fabsf(whL) < kErfMaxArg ? erf_small(whL) : 1.f - EL;
+      const float FR = fabsf(whR) < kErfMaxArg ? erf_small(whR) : 1.f - ER;
+      const float tx = m < H - 1 ? ER - EL : (m == H - 1 ? FL - FR : (m == H ? FL + FR : (m == H + 1 ? FR - FL : EL - ER)));
+
+      // column centre offset tb = (m - H) - fx as a double-float (|m - H| >= 1 > |fx| or m == H)
+      const float th = (float)(m - H) - fx;
+      const float tl = ((float)(m - H) - th) - fx;
+
+      // moments of tau on the column under phi_x(tb + tau) / phi_x(tb) = 2^(al (tb tau + tau^2 / 2)),
+      // 6-point Gauss-Legendre, nodes in symmetric pairs
+      const float al = e1.w;
+      float s0, s1, s2, s3, s4, s5, s6;
+      {
+        const float q2 = 0.5f * al;
+        const float c0 = al * th;
+#define E2E_GL_PAIR(I, INIT)                                                       \
+  {                                                                                \
+    const float cc = q2 * kGl6T##I##P2, cl = c0 * kGl6T##I##P1;                    \
+    const float ep = ex2_approx(cc + cl), em = ex2_approx(cc - cl);                \
+    const float sp = kGl6W##I * (ep + em), dm = kGl6W##I * (ep - em);              \
+    if (INIT) {                                                                    \
+      s0 = sp; s2 = sp * kGl6T##I##P2; s4 = sp * kGl6T##I##P4; s6 = sp * kGl6T##I##P6; \
+      s1 = dm * kGl6T##I##P1; s3 = dm * kGl6T##I##P3; s5 = dm * kGl6T##I##P5;      \
+    } else {                                                                       \
+      s0 += sp; s2 = fmaf(sp, kGl6T##I##P2, s2); s4 = fmaf(sp, kGl6T##I##P4, s4);  \
+      s6 = fmaf(sp, kGl6T##I##P6, s6); s1 = fmaf(dm, kGl6T##I##P1, s1);            \
+      s3 = fmaf(dm, kGl6T##I##P3, s3); s5 = fmaf(dm, kGl6T##I##P5, s5);            \
+    }                                                                              \
+  }
+        E2E_GL_PAIR(0, true)
+        E2E_GL_PAIR(1, false)
+        E2E_GL_PAIR(2, false)
+#undef E2E_GL_PAIR
+      }
+      // G(V) = sum_k a_k He_(k-1)(V) as a quintic in V, scaled by 2 / sqrt(2 pi)
+      float g0, g1, g2, g3, g4, g5;
+      {
+        const float r = rcp_approx(s0), ep1 = e1.z;
+        const float p1 = ep1, p2 = p1 * ep1, p3 = p2 * ep1, p4 = p3 * ep1, p5 = p4 * ep1, p6 = p5 * ep1;
+        const float a1 = -p1 * (s1 * r), a2 = -p2 * (s2 * r) * 0.5f, a3 = -p3 * (s3 * r) * (1.f / 6.f);
+        const float a4 = -p4 * (s4 * r) * (1.f / 24.f), a5 = -p5 * (s5 * r) * (1.f / 120.f);
+        const float a6 = -p6 * (s6 * r) * (1.f / 720.f);
+        g0 = kTwoOverSqrt2Pi * (a1 - a3 + 3.f * a5);
+        g1 = kTwoOverSqrt2Pi * (a2 - 3.f * a4 + 15.f * a6);
+        g2 = kTwoOverSqrt2Pi * (a3 - 6.f * a5);
+        g3 = kTwoOverSqrt2Pi * (a4 - 10.f * a6);
+        g4 = kTwoOverSqrt2Pi * a5;
+        g5 = kTwoOverSqrt2Pi * a6;
+      }
+      // conditional centre of the column relative to the window centre: f = fy + beta tb (double-float)
+      float fh, fl;
+      {
+        const float bh = e1.x, bl = e1.y;
+        const float ph = bh * th;
+        const float pl = fmaf(bh, th, -ph) + fmaf(bh, tl, bl * th);
+        float se;
+        two_sum(fy, ph, fh, se);
+        fl = se + pl;
+        const float t = fh + fl;
+        fl = fl - (t - fh);
+        fh = t;
+      }
+      const float gch = e0.z, gcl = e0.w;
+      const float wq = sw.x * tx;
+      const int bx = st.x - H + m - it.bx0;
+      const bool colin = bx >= 0 && bx < it.bw;
+      const int by0 = st.y - H - it.by0;
+      float Ep = 0.f, Fp = 0.f, hp = 0.f, whp = 0.f;
+#pragma unroll
+      for (int n = 0; n <= K; ++n) {
+        // row edge n at (n - H - 1/2) - f from the conditional centre, in log2 units
+        float dh, de;
+        two_sum((float)(n - H) - 0.5f, -fh, dh, de);
+        const float dl = de - fl;
+        const float wh = dh * gch;
+        const float wl = fmaf(dh, gch, -wh) + fmaf(dh, gcl, dl * gch);
+        float dens;
+        const float E = tail2_dens(wh, wl, dens);
+        const float F = fabsf(wh) < kErfMaxArg ? erf_small(wh) : 1.f - E;
+        const float V = wh * kSqrt2Ln2;
+        const float Gv = fmaf(fmaf(fmaf(fmaf(fmaf(g5, V, g4), V, g3), V, g2), V, g1), V, g0);
+        const float h = dens * Gv;
+        if (n > 0) {
+          const bool same = (wh < 0.f) == (whp < 0.f);
+          const bool small = fminf(fabsf(wh), fabsf(whp)) < kErfMaxArg;
+          const float ty = same ? (small ? fabsf(Fp - F) : fabsf(Ep - E)) : (Fp + F);
+          const int by = by0 + n - 1;
+          if (colin && by >= 0 && by < it.bh) {
+            const int p = by * it.bw + bx;
+            box_deposit(boxh + p, boxl + p, wq * (ty + (h - hp)), sc, sc_hi);
+          }
+        }
+        Ep = E;
+        Fp = F;
+        hp = h;
+        whp = wh;
+      }
+    }
+    __syncwarp();  // the staging is reused by the next batch
+  }
+  __syncthreads();
+  float2* out = a.store + it.store_off;
+  const float inv = ldexpf(1.f, -Psh);
+  for (int p = tid; p < area; p += kEThreads) out[p] = fixed_to_pair(boxh[p], boxl[p], inv);
+}
+
+size_t ellip_smem_bytes(int area, int nk_max, int nd) { return EllipLayout(32, nk_max, nd, area).total; }
+
+template <int K>
+static cudaError_t launch_ellip_one(const MixedArgs& a, int n_items, size_t smem, cudaStream_t st) {
+  auto kern = k_render_ellip<K>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<n_items, kEThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_render_ellip(int K, const DevSlice* slices, const double* const* flux_tab, const double* u_all,
+                                const Item* items, int n_items, float2* store, int nk_max, int max_deg, size_t smem,
+                                cudaStream_t st) {
+  if (n_items == 0) return cudaSuccess;
+  MixedArgs a{slices, flux_tab, u_all, items, store, 0, 1, nk_max, max_deg};
+  switch (K) {
+#define E2E_CASE(KK) \
+  case KK: return launch_ellip_one<KK>(a, n_items, smem, st);
+    E2E_CASE(1) E2E_CASE(3) E2E_CASE(5) E2E_CASE(7) E2E_CASE(9) E2E_CASE(11) E2E_CASE(13) E2E_CASE(15)
+#undef E2E_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ------------------------------------------------------------------------------ FP64
+
+// P(a < Z < b) for a standard normal Z from E = erfc(|t| / sqrt2) at both ends (tails
+// subtracted on one side of the mean, 1 minus both tails across it).
+__device__ __forceinline__ double interval_e(double ta, double tb, double ea, double eb) {
+  if (ta >= 0.0) return 0.5 * (ea - eb);
+  if (tb <= 0.0) return 0.5 * (eb - ea);
+  return 1.0 - 0.5 * (ea + eb);
+}
+
+// One thread per (stamp, window column), all in FP64: mapping, erfc, exp, 12-point
+// Gauss-Legendre moments, the series to k = 9, FP64 atomic deposits into the frame.
+template <int K>
+__global__ void __launch_bounds__(256) k_render_fp64_ellip(const DevSlice* __restrict__ slices,
+                                                           const double* const* __restrict__ flux_tab,
+                                                           const double* __restrict__ u_all, double* const* acc,
+                                                           const int64_t* __restrict__ pitch) {
+  constexpr int NT = 10;  // a_1 .. a_9
+  const DevSlice& S = slices[blockIdx.y];
+  if (S.K != K) return;
+  const double* flux = flux_tab[S.flux_slot];
+  const double* u = u_all + S.u_off;
+  const int64_t n = (int64_t)S.n_lambda * S.n_slit * K;
+  double* frame = acc[S.det];
+  const int64_t P = pitch[S.det];
+  const double r2 = 0.70710678118654752440, rs2pi = 0.39894228040143267794;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stamp = idx / K;
+    const int m = (int)(idx - stamp * K);
+    const int j = (int)(stamp / S.n_slit);
+    const int k = (int)(stamp - (int64_t)j * S.n_slit);
+    const double lt = norm_sample(j, S.n_lambda);
+    const double s = norm_sample(k, S.n_slit);
+    double x = 0.0, y = 0.0;
+    for (int b = S.degree; b >= 0; --b) {
+      x = fma(x, s, poly_lt_for_b(S.cx, S.degree, b, lt));
+      y = fma(y, s, poly_lt_for_b(S.cy, S.degree, b, lt));
+    }
+    x = clamp_coord(x);
+    y = clamp_coord(y);
+    const int i0 = (int)floor(x + 0.5) - K / 2;
+    const int r0 = (int)floor(y + 0.5) - K / 2;
+    const int i = i0 + m;
+    if (i < 0 || i >= S.W || r0 + K <= 0 || r0 >= S.H) continue;
+    const EllipParams p = ellip_params(S, lt);
+    const double w = flux[j] * S.dlam * u[k];
+    const double tb = (double)i - x;
+    const double ta = (tb - 0.5) / p.gx, tc = (tb + 0.5) / p.gx;
+    const double mu0 = interval_e(ta, tc, erfc(fabs(ta) * r2), erfc(fabs(tc) * r2));
+    double mom[NT];
+#pragma unroll
+    for (int q = 0; q < NT; ++q) mom[q] = 0.0;
+    for (int q = 0; q < kGl12; ++q) {
+      const double t = kGl12T[q];
+      const double e = kGl12W[q] * exp(-(tb * t + 0.5 * t * t) / p.vx);
+      double tp = e;
+#pragma unroll
+      for (int kk = 0; kk < NT; ++kk) {
+        mom[kk] += tp;
+        tp *= t;
+      }
+    }
+    double a[NT];
+    {
+      double c = 1.0;
+      a[0] = 0.0;
+#pragma unroll
+      for (int kk = 1; kk < NT; ++kk) {
+        c *= p.eps / (double)kk;
+        a[kk] = -c * mom[kk] / mom[0];
+      }
+    }
+    const double yb = y + p.beta * tb;  // conditional centre of the column
+    double Vp = 0.0, Ep = 0.0, hp = 0.0;
+    for (int nn = 0; nn <= K; ++nn) {
+      const double V = ((double)(r0 + nn) - 0.5 - yb) / p.sc;
+      const double E = erfc(fabs(V) * r2);
+      // G(V) = sum_k a_k He_(k-1)(V) by the Hermite recurrence
+      double h0 = 1.0, h1 = V, G = a[1] + a[2] * V;
+#pragma unroll
+      for (int kk = 3; kk < NT; ++kk) {
+        const double h2 = V * h1 - (double)(kk - 2) * h0;
+        G = fma(a[kk], h2, G);
+        h0 = h1;
+        h1 = h2;
+      }
+      const double h = rs2pi * exp(-0.5 * V * V) * G;
+      if (nn > 0) {
+        const int r = r0 + nn - 1;
+        if (r >= 0 && r < S.H) atomicAdd(frame + (int64_t)r * P + i, w * mu0 * (interval_e(Vp, V, Ep, E) + h - hp));
+      }
+      Vp = V;
+      Ep = E;
+      hp = h;
+    }
+  }
+}
+
+cudaError_t launch_render_fp64_ellip(int K, int n_slices, int64_t max_stamps, const DevSlice* slices,
+                                     const double* const* flux_tab, const double* u_all, double* const* acc,
+                                     const int64_t* pitch, cudaStream_t st) {
+  if (n_slices == 0 || max_stamps == 0) return cudaSuccess;
+  int64_t bx = (max_stamps * K + 255) / 256;
+  if (bx > 8192) bx = 8192;
+  dim3 grid((unsigned)bx, (unsigned)n_slices);
+  switch (K) {
+#define E2E_CASE(KK) \
+  case KK: k_render_fp64_ellip<KK><<<grid, 256, 0, st>>>(slices, flux_tab, u_all, acc, pitch); break;
+    E2E_CASE(1) E2E_CASE(3) E2E_CASE(5) E2E_CASE(7) E2E_CASE(9) E2E_CASE(11) E2E_CASE(13) E2E_CASE(15)
+#undef E2E_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace e2e

@@ -18,6 +18,7 @@
 // run (<= B stamps) in registers, exact fixed-point sums per item, FP64 across items.
 #include "e2e_device.cuh"
 #include "e2e_kernels.h"
+#include "mixed_common.cuh"
 #include "phi32.cuh"
 
 namespace e2e {
@@ -29,9 +30,6 @@ constexpr int kThreads = E2E_MIXED_THREADS;  // threads per render CTA
 constexpr int kWarps = kThreads / 32;
 constexpr int kPairs = kThreads / 2;
 
-// Normalised coordinate of bin-centred sample j of n, (2j + 1 - n) / n, as a product with the
-// correctly rounded reciprocal (the plan and the render compute it identically).
-__device__ __forceinline__ double norm_sample_r(int j, int n, double inv_n) { return (double)(2 * j + 1 - n) * inv_n; }
 
 // ------------------------------------------------------------------------------ plan
 
@@ -111,17 +109,6 @@ __global__ void k_plan(const DevSlice* __restrict__ slices, int n_slices, const 
 
 // ------------------------------------------------------------------------------ render
 
-struct MixedArgs {
-  const DevSlice* slices;
-  const double* const* flux_tab;
-  const double* u_all;
-  const Item* items;
-  float2* store;
-  int B;        // slit points per run
-  int JB;       // largest number of 32-sample blocks in an item
-  int nk_max;   // largest number of slit points in an item
-  int max_deg;  // largest degree among the launched slices
-};
 
 // Shared-memory layout of one CTA (offsets in bytes), identical on host and device.
 struct MixedLayout {
@@ -141,33 +128,6 @@ struct MixedLayout {
   }
 };
 
-__device__ __forceinline__ float2 split_df(double v) {
-  const float h = (float)v;
-  return make_float2(h, (float)(v - (double)h));
-}
-
-// a + b as an unevaluated pair (s, e), s = fl(a + b), a + b = s + e exactly (Knuth's TwoSum).
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
-// (hi * 2^22 + lo) * scale as an FP32 pair (h, l) with h + l exact to ~2^-48: the 54-bit
-// integer is cut into four 16-bit pieces (each exact in FP32) and summed with TwoSum.
-__device__ __forceinline__ float2 fixed_to_pair(int hi, unsigned lo, float scale) {
-  const float t1 = (float)(hi >> 16) * 274877906944.f;  // 2^38
-  const float t2 = (float)(hi & 0xFFFF) * 4194304.f;    // 2^22
-  const float t3 = (float)(lo >> 16) * 65536.f;         // 2^16
-  const float t4 = (float)(lo & 0xFFFFu);
-  float s, e, e2;
-  two_sum(t1, t2, s, e);
-  two_sum(s, t3, s, e2);
-  e += e2;
-  two_sum(s, t4, s, e2);
-  e += e2;
-  return make_float2(s * scale, e * scale);
-}
 
 // Two CTAs per SM (128 registers) when a lane's accumulator tile is small enough, else one.
 #ifndef E2E_MID_TILE_BLOCKS
@@ -380,11 +340,7 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
 #pragma unroll
         for (int c = 0; c < RX; ++c) {
           if (!inside && (gx0 + c < 0 || gx0 + c >= it.bw)) continue;
-          const float val = acc[r][c];
-          const float hf = floorf(val * sc_hi);
-          const float lf = fmaf(-hf, 4194304.f, val * sc);
-          atomicAdd(rowh + c, __float2int_rz(hf));
-          atomicAdd(rowl + c, __float2uint_rn(lf));
+          box_deposit(rowh + c, rowl + c, acc[r][c], sc, sc_hi);
         }
       }
     }

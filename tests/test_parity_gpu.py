@@ -1,6 +1,6 @@
 """GPU renderer vs the FP64 oracle, element by element, through the C ABI.
 
-Tolerance (spec fidelity target): relative per-pixel error below 1e-6 (with an
+Tolerance (the renderer's fidelity target): relative per-pixel error below 1e-6 (with an
 absolute floor of 1e-10 of the frame peak, see framecompare) and photocenter shifts of
 16x16 px windows below 1e-5 px.  The plain FP64 renderer must agree to 5e-11 relative:
 CUDA's FP64 erfc and glibc's differ by a few ulp, and the same-side tail differences of a
