@@ -152,6 +152,30 @@ def oracle_sample_rate(w: W.Workload, seconds: float = 12.0, max_slices: int = 6
     return stamps / dt, cores, f"first {n} of {len(w.model.slices)} order-slices ({stamps} stamps), FP64, {dt:.1f} s"
 
 
+def oracle_sample_rate_cut(w: W.Workload, n_slices: int = 16, n_lambda: int = 120):
+    """Stamps/s of the FP64 oracle on the first n_slices order-slices of w, each cut to its
+    first n_lambda wavelength samples (the range shortened with them, so the samples keep
+    their spacing and every stamp costs what it costs in the full workload)."""
+    import dataclasses
+
+    import oracle
+
+    cores = os.cpu_count() or 1
+    cut = []
+    for s in w.model.slices[:n_slices]:
+        dl = (s.lambda_hi - s.lambda_lo) / s.n_lambda
+        m = min(n_lambda, s.n_lambda)
+        cut.append(dataclasses.replace(s.copy(), n_lambda=m, lambda_hi=s.lambda_lo + m * dl))
+    sub = W.OpticalModel(w.model.det_shape, cut, w.model.psf)
+    flux = {id(c): w.flux_for(s)[:c.n_lambda] for c, s in zip(cut, w.model.slices)}
+    t0 = time.perf_counter()
+    oracle.render(sub, lambda c: flux[id(c)], n_threads=cores)
+    dt = time.perf_counter() - t0
+    stamps = sub.n_stamps
+    return stamps / dt, cores, (f"first {len(cut)} of {len(w.model.slices)} order-slices, each cut to its first "
+                                f"{n_lambda} wavelength samples ({stamps} stamps), FP64, {dt:.1f} s")
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -322,6 +346,11 @@ def run_gpu(args):
         "launches_per_step": launches_per_step,
         "clocks": clocks, "peak_source": peak_kind, "wall_s_timed": t_wall,
     }
+    if not args.no_noise:
+        line["noise"] = noise_run(B, r, mid, frame, stream, flush)
+    if not args.no_elliptical:
+        line["elliptical"] = elliptical_run(B, dev, rank, world,
+                                            cpu_baseline=(rank == 0 and world == 1 and not args.no_cpu_baseline))
     if not args.no_serving:
         line["serving"] = serving_run(B, dev)
         line["p99_latency_ms"] = line["serving"]["poisson"]["latency_ms"]["p99"]
@@ -334,6 +363,76 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def noise_run(B, r, mid, frame, stream, flush, reps=5):
+    """The detector-noise stage on the rendered full frame: FP32 expected electrons in, 16-bit
+    ADU out (photon and dark shot noise, pixel response, read-out noise, cross-talk)."""
+    import torch
+
+    params = dict(seed=20201105, pattern_seed=17, dark_e=2.5, prnu=0.01, ron_e=3.2, xtalk=2e-4, gain=1.1,
+                  bias=1000.0, saturation=65535)
+    out = r.add_noise(mid, frame, "u16", stream=stream, **params)
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r.add_noise(mid, frame, "u16", out=out, stream=stream, **params)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = statistics.median(ms)
+    px = sum(f.numel() for f in frame)
+    nbytes = px * (4 + 2)
+    peaks, kind = _peaks()
+    hbm = peaks.get("hbm_gbs")
+    return {"ms": t, "pixels": px, "algorithmic_bytes": nbytes, "achieved_gbs": nbytes / (t * 1e-3) / 1e9,
+            "hbm_peak_gbs": hbm, "frac_of_hbm": (nbytes / (t * 1e-3) / 1e9 / hbm) if hbm else None,
+            "peak_source": kind, "params": params,
+            "note": "FP64 draws (Philox4x32-10, Box-Muller, PTRS Poisson) per pixel: FP64-ALU bound, not HBM"}
+
+
+def elliptical_run(B, dev, rank=0, world=1, reps=3, cpu_baseline=False):
+    """The multi-detector instrument with the rotated PSF (4 x 9216^2 FP32, 30 orders per
+    detector x 4 fibers x 2 slices, 8000 x 128 samples, K = 13): mixed precision on the whole
+    instrument (this rank's detectors), and the plain FP64 renderer on its first order per
+    detector (it is ~100x slower), both timed with CUDA events, L2 flushed between renders."""
+    import torch
+
+    from paper_2008_05858_gb300 import shard
+
+    out = {}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for key, orders, prec, n in (("mixed", 30, "mixed", reps), ("fp64", 1, "fp64", 1)):
+        w, _ = shard.shard_workload(W.config3(orders_per_detector=orders), rank, world)
+        r = B.Renderer(dev)
+        mid = r.load_model(w.model)
+        sids = r.load_spectra(w)
+        frames = r.empty_frames(mid, "f32")
+        st = torch.cuda.current_stream()
+        r.render(mid, sids, prec, "f32", out=frames, stream=st)
+        ms = []
+        for _ in range(n):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            r.render(mid, sids, prec, "f32", out=frames, stream=st)
+            b.record(st)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        t = statistics.median(ms)
+        out[key] = {"stamps": w.model.n_stamps, "ms_per_render": t, "value": w.model.n_stamps / (t * 1e-3),
+                    "unit": UNIT, "orders_per_detector": orders, "detectors": len(w.model.det_shape)}
+        del frames
+        r.close()
+    out["speedup_mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    if cpu_baseline:
+        rate, cores, sample = oracle_sample_rate_cut(W.config3(orders_per_detector=1))
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    out["workload"] = "4 x 9216^2 FP32, 30 orders/detector x 4 fibers x 2 slices, 8000 x 128 samples, deg 5, " \
+                      "K=13 rotated elliptical PSF (|theta| <= 10 deg); fp64 leg on 1 order/detector"
+    return out
 
 
 def serving_run(B, dev, n_jobs=512, max_inflight=8, load=0.8, express_stamps=1 << 24):
@@ -442,7 +541,8 @@ def _load_spectrum_ptr(B, ctx, fiber, orders, lens, flux_tensor):
     return sid.value
 
 
-KERNEL_SOURCES = ["paper_2008_05858_gb300/csrc/render_mixed.cu", "paper_2008_05858_gb300/csrc/phi32.cuh",
+KERNEL_SOURCES = ["paper_2008_05858_gb300/csrc/render_mixed.cu", "paper_2008_05858_gb300/csrc/render_mixed.cuh",
+                  "paper_2008_05858_gb300/csrc/phi32.cuh",
                   "paper_2008_05858_gb300/csrc/mixed_common.cuh",
                   "paper_2008_05858_gb300/csrc/e2e_device.cuh", "paper_2008_05858_gb300/csrc/tail_coeffs.h"]
 
@@ -482,6 +582,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-elliptical", action="store_true")
+    ap.add_argument("--no-noise", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -48,7 +48,7 @@ extern "C" {
 #define E2E_ETOOBIG -6   /* serving: job can never fit the memory pool */
 #define E2E_ETIMEOUT -7  /* serving: wait timed out */
 #define E2E_ECANCELLED -8
-#define E2E_EDEVICE -9   /* reserved */
+#define E2E_EDEVICE -9   /* debug checks: a kernel found a deposit its plan did not foresee */
 
 /* ------------------------------------------------------------------ enums */
 enum { E2E_PSF_SEPARABLE = 0, E2E_PSF_ELLIPTICAL = 1 };
@@ -56,7 +56,7 @@ enum { E2E_PSF_SEPARABLE = 0, E2E_PSF_ELLIPTICAL = 1 };
  *                 compensated merge (the fast path).
  * E2E_PREC_FP64:  everything in FP64, one thread per stamp, FP64 global atomics (baseline). */
 enum { E2E_PREC_MIXED = 0, E2E_PREC_FP64 = 1 };
-enum { E2E_F32 = 0, E2E_F64 = 1 };
+enum { E2E_F32 = 0, E2E_F64 = 1, E2E_U16 = 2 /* detector ADU, e2e_add_noise output only */ };
 
 /* ------------------------------------------------------------------ limits */
 #define E2E_MAX_DEGREE 8  /* polynomial total degree */
@@ -67,7 +67,11 @@ typedef struct e2e_ctx e2e_ctx;
 typedef struct {
   size_t pool_bytes; /* cap on the device scratch the context may hold (0 = no cap) */
   int32_t max_inflight; /* serving: jobs on the device at once (0 = default 4) */
-  int32_t debug_checks; /* reserved, ignored (every deposit is already clipped to its box) */
+  int32_t debug_checks; /* 1 = the mixed-precision kernels count every deposit that falls
+                           outside its work item's planned box (or a run that outgrows its
+                           planned tile) while on the detector; such deposits are dropped,
+                           never written out of bounds.  The render then synchronises its
+                           stream and returns E2E_EDEVICE if any were found. */
   int32_t kernel_timing; /* 1 = record CUDA events around each kernel of a render (see e2e_kernel_times) */
 } e2e_opts;
 
@@ -194,6 +198,42 @@ int e2e_render_adjoint(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const ui
 int e2e_update_model(e2e_ctx* ctx, uint64_t model_id, const double* cx, const double* cy, const double* sx,
                      const double* sy);
 
+/* ------------------------------------------------------------------ detector noise */
+
+/* Noise stage applied to rendered frames (Sec. 2.2 ends the simulation by adding photon
+ * noise, dark current, read-out noise, pixel response non-uniformity and cross-talk to the
+ * synthetic frame; it gives no formulas, this is the model used).  For detector d of width W,
+ * pixel (r, c), rendered value S (expected electrons):
+ *   lam = max((1 + prnu z) S + dark_e, 0);  N ~ Poisson(lam) (N = lam when poisson = 0);
+ *   M = N + xtalk N(r, W-1-c)  (the mirror pixel, read by the other amplifier of a two-output
+ *       detector; the middle column of an odd width has none);
+ *   E = M + ron_e g;  ADU = clamp(floor(bias + E / gain + 1/2), 0, saturation);
+ * z (fixed pattern, from pattern_seed) and g (from seed) are standard normals.  Draws come
+ * from Philox4x32-10 keyed by the seeds with counter (pair, detector, trial, stream), so a
+ * frame is a pure function of (S, parameters, seeds): the same on every launch shape. */
+typedef struct {
+  uint64_t seed;          /* frame seed: shot noise and read-out noise */
+  uint64_t pattern_seed;  /* fixed-pattern seed: pixel response */
+  double dark_e;          /* mean dark electrons per pixel over the exposure, >= 0 */
+  double prnu;            /* relative rms of the pixel response, >= 0 */
+  double ron_e;           /* read-out noise rms (electrons), >= 0 */
+  double xtalk;           /* cross-talk fraction, |xtalk| < 1 */
+  double gain;            /* electrons per ADU, > 0 (E2E_U16 output) */
+  double bias;            /* ADU offset (E2E_U16 output) */
+  int32_t saturation;     /* ADU ceiling, 0..65535 (E2E_U16 output) */
+  int32_t poisson;        /* 1 = Poisson shot noise, 0 = expected values */
+} e2e_noise_params;
+
+/* Apply the noise stage to every detector frame of `model` (sizes from the model).
+ *   src[d]: device frame of expected electrons, src_dtype E2E_F32 or E2E_F64, src_pitch[d]
+ *           elements between rows (NULL = width);
+ *   dst[d]: device output, dst_dtype E2E_F32 / E2E_F64 (electrons) or E2E_U16 (ADU),
+ *           dst_pitch as src; dst may be src (same dtype and pitch) for in-place noise.
+ * Asynchronous on `stream`.  Errors: E2E_EINVAL, E2E_ENOTFOUND, E2E_ECUDA. */
+int e2e_add_noise(e2e_ctx* ctx, uint64_t model_id, const e2e_noise_params* params, int32_t src_dtype,
+                  const void* const* src, const int64_t* src_pitch, int32_t dst_dtype, void* const* dst,
+                  const int64_t* dst_pitch, void* stream);
+
 /* ------------------------------------------------------------------ serving */
 
 /* The paper spreads many simulation jobs over cloud workers (Sec. 3); here one GPU serves a
@@ -211,6 +251,8 @@ typedef struct {
   int64_t express_stamps; /* jobs of at most this many stamps are "express": admitted before
                              any queued regular job and run on high-priority streams, so
                              small jobs do not wait behind full frames (0 = one FIFO class) */
+  int32_t express_slots;  /* with express jobs: slots regular jobs leave free for them
+                             (0 = max_inflight / 4, at least 1; at most max_inflight - 1) */
 } e2e_server_cfg;
 
 typedef struct {

@@ -28,12 +28,21 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "noise.c")]
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
 PSF_SEPARABLE = 0
 PSF_ELLIPTICAL = 1
+
+
+class OracleNoise(C.Structure):
+    _fields_ = [
+        ("seed", C.c_uint64), ("pattern_seed", C.c_uint64), ("dark", C.c_double), ("prnu", C.c_double),
+        ("ron", C.c_double), ("xtalk", C.c_double), ("gain", C.c_double), ("bias", C.c_double),
+        ("saturation", C.c_int32), ("poisson", C.c_int32),
+    ]
 
 
 class OracleSlice(C.Structure):
@@ -59,10 +68,10 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (OpenMP) into oracle/_build/liboracle.so."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(
-        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h"))
+        [os.path.getmtime(f) for f in _SRCS] + [os.path.getmtime(os.path.join(_HERE, "oracle.h"))]
     ):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"]
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp] + _SRCS + ["-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -99,6 +108,16 @@ def lib():
             L.oracle_vjp.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int,
                                      C.POINTER(OracleSlice), C.POINTER(dp), dp, dp, dp, dp, C.c_int]
             L.oracle_vjp.restype = C.c_int
+            u32p = C.POINTER(C.c_uint32)
+            L.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
+            L.oracle_philox4x32_10.restype = None
+            L.oracle_normal_pair.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, dp, dp]
+            L.oracle_normal_pair.restype = None
+            L.oracle_poisson.argtypes = [C.c_double, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32]
+            L.oracle_poisson.restype = C.c_long
+            L.oracle_add_noise.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp, C.POINTER(OracleNoise), dp,
+                                           C.POINTER(C.c_int32), dp]
+            L.oracle_add_noise.restype = C.c_int
             _lib = L
     return _lib
 
@@ -238,3 +257,43 @@ def vjp(model, flux_of, dLdI: Sequence[np.ndarray], n_threads: int = 0):
     if rc != 0:
         raise ValueError("oracle_vjp rejected the model")
     return gcx, gcy, gsx, gsy
+
+
+# ---------------------------------------------------------------------------- detector noise
+
+
+def philox4x32_10(counter: Sequence[int], key: Sequence[int]) -> List[int]:
+    """One Philox4x32-10 block (Salmon et al., SC'11)."""
+    c = (C.c_uint32 * 4)(*counter)
+    k = (C.c_uint32 * 2)(*key)
+    out = (C.c_uint32 * 4)()
+    lib().oracle_philox4x32_10(c, k, out)
+    return list(out)
+
+
+def normal_pair(seed: int, q: int, d: int, stream: int) -> Tuple[float, float]:
+    a, b = C.c_double(), C.c_double()
+    lib().oracle_normal_pair(seed, q, d, stream, C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def poisson(lam: float, seed: int, q: int, d: int, side: int = 0) -> int:
+    return int(lib().oracle_poisson(lam, seed, q, d, side))
+
+
+def add_noise(S: np.ndarray, det: int, *, seed: int, pattern_seed: int, dark: float = 0.0, prnu: float = 0.0,
+              ron: float = 0.0, xtalk: float = 0.0, gain: float = 1.0, bias: float = 0.0,
+              saturation: int = 65535, poisson: bool = True, row0: int = 0):
+    """Noise stage of one detector frame, or of its rows row0.. (S holds those rows, full
+    width): (electrons, ADU, Poisson counts)."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    H, W = S.shape
+    p = OracleNoise(seed, pattern_seed, dark, prnu, ron, xtalk, gain, bias, saturation, 1 if poisson else 0)
+    E = np.empty((H, W))
+    A = np.empty((H, W), dtype=np.int32)
+    N = np.empty((H, W))
+    rc = lib().oracle_add_noise(H, W, row0, det, _dptr(S), C.byref(p), _dptr(E),
+                                A.ctypes.data_as(C.POINTER(C.c_int32)), _dptr(N))
+    if rc != 0:
+        raise ValueError("oracle_add_noise: invalid argument")
+    return E, A, N

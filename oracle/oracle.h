@@ -84,6 +84,35 @@ double oracle_loss_grad(int n_det, const int* H, const int* W, int n_slices, con
 int oracle_vjp(int n_det, const int* H, const int* W, int n_slices, const oracle_slice* s,
                const double* const* dLdI, double* g_cx, double* g_cy, double* g_sx, double* g_sy, int n_threads);
 
+/* ---------------------------------------------------------------- detector noise (noise.c) */
+
+#include <stdint.h>
+
+typedef struct {
+  uint64_t seed;          /* frame seed: photon / dark shot noise and read-out noise */
+  uint64_t pattern_seed;  /* fixed-pattern seed: pixel response non-uniformity */
+  double dark;            /* mean dark electrons per pixel over the exposure */
+  double prnu;            /* relative rms of the pixel response */
+  double ron;             /* read-out noise rms, electrons */
+  double xtalk;           /* fraction of the mirror pixel's electrons added */
+  double gain;            /* electrons per ADU */
+  double bias;            /* ADU offset */
+  int32_t saturation;     /* ADU ceiling */
+  int32_t poisson;        /* 1 = Poisson draws, 0 = expected values */
+} oracle_noise;
+
+/* Philox4x32-10 block for counter ctr and key. */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* Box-Muller pair of standard normals from block (seed, (q, d, 0, stream)). */
+void oracle_normal_pair(uint64_t seed, uint32_t q, uint32_t d, uint32_t stream, double* left, double* right);
+/* Poisson(lam) draw of side `side` of pair q on detector d. */
+long oracle_poisson(double lam, uint64_t seed, uint32_t q, uint32_t d, uint32_t side);
+/* Noise stage of rows row0 .. row0+H-1 of one detector frame of width W (S: H x W expected
+ * electrons, row-major): electrons E and/or ADU (either may be NULL), and optionally the
+ * Poisson counts.  Returns 0 or -1. */
+int oracle_add_noise(int H, int W, int row0, int det, const double* S, const oracle_noise* p, double* E,
+                     int32_t* adu, double* counts);
+
 #ifdef __cplusplus
 }
 #endif

@@ -36,6 +36,7 @@ E2E_PREC_MIXED = 0
 E2E_PREC_FP64 = 1
 E2E_F32 = 0
 E2E_F64 = 1
+E2E_U16 = 2
 
 PRECISION = {"mixed": E2E_PREC_MIXED, "fp64": E2E_PREC_FP64}
 DTYPE = {"f32": E2E_F32, "f64": E2E_F64}
@@ -78,8 +79,17 @@ class e2e_plan_info(C.Structure):
     ]
 
 
+class e2e_noise_params(C.Structure):
+    _fields_ = [
+        ("seed", C.c_uint64), ("pattern_seed", C.c_uint64), ("dark_e", C.c_double), ("prnu", C.c_double),
+        ("ron_e", C.c_double), ("xtalk", C.c_double), ("gain", C.c_double), ("bias", C.c_double),
+        ("saturation", C.c_int32), ("poisson", C.c_int32),
+    ]
+
+
 class e2e_server_cfg(C.Structure):
-    _fields_ = [("max_inflight", C.c_int32), ("budget_bytes", C.c_size_t), ("express_stamps", C.c_int64)]
+    _fields_ = [("max_inflight", C.c_int32), ("budget_bytes", C.c_size_t), ("express_stamps", C.c_int64),
+                ("express_slots", C.c_int32)]
 
 
 class e2e_job(C.Structure):
@@ -131,6 +141,9 @@ _SIGS = {
                             C.c_void_p, C.c_void_p], C.c_int),
     "e2e_update_model": ([C.c_void_p, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double),
                           C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
+    "e2e_add_noise": ([C.c_void_p, C.c_uint64, C.POINTER(e2e_noise_params), C.c_int32, C.POINTER(C.c_void_p),
+                       C.POINTER(C.c_int64), C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.c_void_p],
+                      C.c_int),
     "e2e_server_start": ([C.c_void_p, C.POINTER(e2e_server_cfg)], C.c_int),
     "e2e_submit": ([C.c_void_p, C.POINTER(e2e_job), C.POINTER(C.c_uint64)], C.c_int),
     "e2e_poll": ([C.c_void_p, C.c_uint64, C.POINTER(e2e_job_info)], C.c_int),
@@ -319,11 +332,26 @@ def e2e_update_model(ctx: int, model_id: int, cx: np.ndarray, cy: np.ndarray, sx
     _check(load_library().e2e_update_model(C.c_void_p(ctx), model_id, *[a.ctypes.data_as(dp) for a in arrs]))
 
 
+# -------------------------------------------------------------------- detector noise
+
+
+def e2e_add_noise(ctx: int, model_id: int, params: e2e_noise_params, src_dtype: int, src_ptrs: Sequence[int],
+                  src_pitch: Optional[Sequence[int]], dst_dtype: int, dst_ptrs: Sequence[int],
+                  dst_pitch: Optional[Sequence[int]], stream=None) -> None:
+    n = len(src_ptrs)
+    sp = None if src_pitch is None else (C.c_int64 * n)(*src_pitch)
+    dp = None if dst_pitch is None else (C.c_int64 * n)(*dst_pitch)
+    _check(load_library().e2e_add_noise(C.c_void_p(ctx), model_id, C.byref(params), src_dtype,
+                                        (C.c_void_p * n)(*src_ptrs), sp, dst_dtype, (C.c_void_p * n)(*dst_ptrs), dp,
+                                        C.c_void_p(_stream_handle(stream))))
+
+
 # -------------------------------------------------------------------- serving
 
 
-def e2e_server_start(ctx: int, max_inflight: int = 0, budget_bytes: int = 0, express_stamps: int = 0) -> None:
-    cfg = e2e_server_cfg(max_inflight, budget_bytes, express_stamps)
+def e2e_server_start(ctx: int, max_inflight: int = 0, budget_bytes: int = 0, express_stamps: int = 0,
+                     express_slots: int = 0) -> None:
+    cfg = e2e_server_cfg(max_inflight, budget_bytes, express_stamps, express_slots)
     _check(load_library().e2e_server_start(C.c_void_p(ctx), C.byref(cfg)))
 
 
@@ -448,6 +476,26 @@ class Renderer:
         td = torch.float32 if dtype == "f32" else torch.float64
         return [torch.empty((h, w), dtype=td, device=f"cuda:{self.device}") for h, w in self.models[mid].det_shape]
 
+    # -------------------------------------------------------------- detector noise
+    def add_noise(self, mid: int, frames, dtype: str = "f32", out=None, stream=None, *, seed: int,
+                  pattern_seed: int = 1, dark_e: float = 0.0, prnu: float = 0.0, ron_e: float = 0.0,
+                  xtalk: float = 0.0, gain: float = 1.0, bias: float = 0.0, saturation: int = 65535,
+                  poisson: bool = True):
+        """Noise stage on rendered frames (see e2e_add_noise); dtype "f32"/"f64" (electrons)
+        or "u16" (ADU).  out defaults to new frames; out=frames applies it in place."""
+        import torch
+
+        if out is None:
+            td = {"f32": torch.float32, "f64": torch.float64, "u16": torch.uint16}[dtype]
+            out = [torch.empty(f.shape, dtype=td, device=f.device) for f in frames]
+        p = e2e_noise_params(seed, pattern_seed, dark_e, prnu, ron_e, xtalk, gain, bias, saturation,
+                             1 if poisson else 0)
+        sdt = E2E_F32 if frames[0].dtype == torch.float32 else E2E_F64
+        e2e_add_noise(self.ctx, mid, p, sdt, [int(f.data_ptr()) for f in frames], [int(f.stride(0)) for f in frames],
+                      {"f32": E2E_F32, "f64": E2E_F64, "u16": E2E_U16}[dtype], [int(t.data_ptr()) for t in out],
+                      [int(t.stride(0)) for t in out], stream)
+        return out
+
     # -------------------------------------------------------------- differentiation
     def params(self, mid: int):
         """(cx, cy, sx, sy) of the model, concatenated per order-slice (the adjoint's layout)."""
@@ -497,9 +545,10 @@ class Renderer:
 class Server:
     """Continuous-batching request loop on a Renderer's context (see e2e_server_start)."""
 
-    def __init__(self, renderer: Renderer, max_inflight: int = 4, budget_bytes: int = 0, express_stamps: int = 0):
+    def __init__(self, renderer: Renderer, max_inflight: int = 4, budget_bytes: int = 0, express_stamps: int = 0,
+                 express_slots: int = 0):
         self.r = renderer
-        e2e_server_start(renderer.ctx, max_inflight, budget_bytes, express_stamps)
+        e2e_server_start(renderer.ctx, max_inflight, budget_bytes, express_stamps, express_slots)
         self._keep: Dict[int, object] = {}
 
     def submit(self, mid: int, spec_ids: Sequence[int], precision: str = "mixed", dtype: str = "f32", out=None) -> int:

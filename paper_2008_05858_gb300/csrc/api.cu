@@ -115,6 +115,7 @@ struct e2e_ctx {
   std::map<uint64_t, std::unique_ptr<Frame>> frames;
   cudaMemPool_t pool = nullptr;
   cudaStream_t free_stream = nullptr;  // where library frames are returned to the pool
+  int* d_err = nullptr;                // debug checks: deposits outside the planned boxes
   // kernel timing of the most recent render (opts.kernel_timing)
   struct Timed {
     const char* name;
@@ -156,6 +157,7 @@ struct Server {
   std::deque<uint64_t> queue;     // regular jobs, FIFO
   std::deque<uint64_t> express;   // jobs of <= express_stamps stamps, FIFO, admitted first
   int64_t express_stamps = 0;
+  int express_slots = 0;  // slots regular jobs may not take
   std::map<uint64_t, Job> jobs;
   std::vector<cudaStream_t> slots;     // lowest stream priority
   std::vector<cudaStream_t> slots_hi;  // highest stream priority (express jobs)
@@ -609,18 +611,25 @@ int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, in
   if (!P.ok) return fail(E2E_EINVAL, "model has no mixed-precision plan");
   float2* store = nullptr;
   E2E_CK(sc.get((void**)&store, (size_t)P.store_elems * sizeof(float2)));
+  if (ctx->d_err) E2E_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
   for (auto& g : P.groups) {
     KernelTimer kt(ctx, st, ellip ? "render_ellip" : "render_mixed");
     if (ellip)
       E2E_CK(launch_render_ellip(g.K, m->d_slices, d_table, m->d_u, P.d_items + g.first, g.count, store, P.nk_max,
-                                 P.max_deg, P.smem, st));
+                                 P.max_deg, P.smem, st, ctx->d_err));
     else
       E2E_CK(launch_render_mixed(g.K, P.DX, P.DY, m->d_slices, d_table, m->d_u, P.d_items + g.first, g.count,
-                                 store, P.B, P.JB, P.nk_max, P.max_deg, P.smem, st));
+                                 store, P.B, P.JB, P.nk_max, P.max_deg, P.smem, st, ctx->d_err));
   }
   {
     KernelTimer kt(ctx, st, "merge");
     E2E_CK(launch_merge(P.d_tiles, P.n_tiles, P.d_lists, P.d_items, store, d_dst, dtype, d_pitch, m->d_dims, st));
+  }
+  if (ctx->d_err) {  // debug checks: wait for the render and report unplanned deposits
+    int n_bad = 0;
+    E2E_CK(cudaMemcpyAsync(&n_bad, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    E2E_CK(cudaStreamSynchronize(st));
+    if (n_bad) return fail(E2E_EDEVICE, std::to_string(n_bad) + " deposits fell outside the planned boxes");
   }
   return E2E_OK;
 }
@@ -686,9 +695,13 @@ int e2e_create(e2e_ctx** out, int32_t device, const e2e_opts* opts) {
     cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
   e = cudaStreamCreateWithFlags(&c->free_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && c->opts.debug_checks) e = cudaMalloc((void**)&c->d_err, sizeof(int));
+  if (e == cudaSuccess && c->d_err) e = cudaMemset(c->d_err, 0, sizeof(int));
   if (e != cudaSuccess) {
+    if (c->free_stream) cudaStreamDestroy(c->free_stream);
+    cudaFree(c->d_err);
     delete c;
-    return cuda_fail(e, "stream creation");
+    return cuda_fail(e, "context setup");
   }
   *out = c;
   return E2E_OK;
@@ -706,6 +719,7 @@ void e2e_destroy(e2e_ctx* ctx) {
     for (auto& kv : ctx->frames) free_frame(ctx, kv.second.get());
     cudaStreamSynchronize(ctx->free_stream);
     cudaStreamDestroy(ctx->free_stream);
+    cudaFree(ctx->d_err);
     reset_timing(ctx);
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   }
@@ -1151,6 +1165,11 @@ void admit_jobs(Server* S, std::unique_lock<std::mutex>& lk) {
         break;
       }
     if (slot < 0 || S->in_use + (size_t)j.budget > S->budget) break;
+    if (!j.express) {  // keep express_slots free for small jobs
+      int regular = 0;
+      for (uint64_t sid : S->slot_job) regular += (sid != 0 && !S->jobs[sid].express) ? 1 : 0;
+      if (regular >= (int)S->slot_job.size() - S->express_slots) break;
+    }
     q.pop_front();
     S->slot_job[slot] = id;
     S->in_use += j.budget;
@@ -1257,6 +1276,10 @@ int e2e_server_start(e2e_ctx* ctx, const e2e_server_cfg* cfg) {
   }
   S->budget = budget;
   S->express_stamps = cfg ? cfg->express_stamps : 0;
+  if (S->express_stamps > 0) {
+    const int want = (cfg && cfg->express_slots > 0) ? cfg->express_slots : std::max(1, slots / 4);
+    S->express_slots = std::min(want, slots - 1);
+  }
   int prio_lo = 0, prio_hi = 0;
   E2E_CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
   for (int q = 0; q < slots; ++q) {
@@ -1418,6 +1441,39 @@ int e2e_server_stop(e2e_ctx* ctx) {
   for (cudaStream_t st : S->slots) cudaStreamDestroy(st);
   for (cudaStream_t st : S->slots_hi) cudaStreamDestroy(st);
   ctx->server.reset();
+  return E2E_OK;
+}
+
+int e2e_add_noise(e2e_ctx* ctx, uint64_t model_id, const e2e_noise_params* p, int32_t src_dtype,
+                  const void* const* src, const int64_t* src_pitch, int32_t dst_dtype, void* const* dst,
+                  const int64_t* dst_pitch, void* stream) {
+  if (!ctx || !p || !src || !dst) return fail(E2E_EINVAL, "null argument");
+  if (src_dtype != E2E_F32 && src_dtype != E2E_F64) return fail(E2E_EINVAL, "src dtype must be E2E_F32 or E2E_F64");
+  if (dst_dtype != E2E_F32 && dst_dtype != E2E_F64 && dst_dtype != E2E_U16) return fail(E2E_EINVAL, "bad dst dtype");
+  if (!(p->dark_e >= 0) || !(p->prnu >= 0) || !(p->ron_e >= 0) || !(std::fabs(p->xtalk) < 1) ||
+      !std::isfinite(p->bias) || !(p->gain > 0) || !std::isfinite(p->gain) || p->saturation < 0 ||
+      p->saturation > 65535 || !std::isfinite(p->dark_e) || !std::isfinite(p->prnu) || !std::isfinite(p->ron_e))
+    return fail(E2E_EINVAL, "noise parameters out of range");
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Model* m = find_model(ctx, model_id);
+  if (!m) return fail(E2E_ENOTFOUND, "unknown model id");
+  for (int d = 0; d < m->n_det; ++d) {
+    const int64_t sp = src_pitch ? src_pitch[d] : m->W[d], dp = dst_pitch ? dst_pitch[d] : m->W[d];
+    if (!src[d] || !dst[d]) return fail(E2E_EINVAL, "null frame");
+    if (sp < m->W[d] || dp < m->W[d]) return fail(E2E_EINVAL, "pitch smaller than width");
+    if ((int64_t)m->H[d] * ((m->W[d] + 1) / 2) >= ((int64_t)1 << 32)) return fail(E2E_EINVAL, "frame too large");
+    if (src[d] == dst[d] && (src_dtype != dst_dtype || sp != dp))
+      return fail(E2E_EINVAL, "in-place noise needs the same dtype and pitch");
+  }
+  if (ctx->opts.kernel_timing) reset_timing(ctx);
+  for (int d = 0; d < m->n_det; ++d) {
+    const int64_t sp = src_pitch ? src_pitch[d] : m->W[d], dp = dst_pitch ? dst_pitch[d] : m->W[d];
+    KernelTimer kt(ctx, (cudaStream_t)stream, "noise");
+    E2E_CK(launch_noise(p->seed, p->pattern_seed, p->dark_e, p->prnu, p->ron_e, p->xtalk, p->gain, p->bias,
+                        p->saturation, p->poisson, src_dtype, src[d], sp, dst_dtype, dst[d], dp, m->H[d], m->W[d], d,
+                        (cudaStream_t)stream));
+  }
   return E2E_OK;
 }
 

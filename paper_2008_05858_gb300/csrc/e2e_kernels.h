@@ -23,17 +23,22 @@ bool mixed_variant_supported(int K, int DX, int DY);
 size_t mixed_smem_bytes(int area, int JB, int nk_max, int B, int nd);
 cudaError_t launch_render_mixed(int K, int DX, int DY, const DevSlice* slices, const double* const* flux_tab,
                                 const double* u_all, const Item* items, int n_items, float2* store, int B, int JB,
-                                int nk_max, int max_deg, size_t smem, cudaStream_t st);
+                                int nk_max, int max_deg, size_t smem, cudaStream_t st, int* err = nullptr);
 cudaError_t launch_merge(const Tile* tiles, int n_tiles, const int32_t* lists, const Item* items, const float2* store,
                          void* const* dst, int dtype, const int64_t* pitch, const int* dims, cudaStream_t st);
 
 size_t ellip_smem_bytes(int area, int nk_max, int nd);
 cudaError_t launch_render_ellip(int K, const DevSlice* slices, const double* const* flux_tab, const double* u_all,
                                 const Item* items, int n_items, float2* store, int nk_max, int max_deg, size_t smem,
-                                cudaStream_t st);
+                                cudaStream_t st, int* err = nullptr);
 cudaError_t launch_render_fp64_ellip(int K, int n_slices, int64_t max_stamps, const DevSlice* slices,
                                      const double* const* flux_tab, const double* u_all, double* const* acc,
                                      const int64_t* pitch, cudaStream_t st);
+
+cudaError_t launch_noise(uint64_t seed, uint64_t pattern_seed, double dark, double prnu, double ron, double xtalk,
+                         double gain, double bias, int saturation, int poisson, int src_dtype, const void* src,
+                         int64_t src_pitch, int dst_dtype, void* dst, int64_t dst_pitch, int H, int W, int det,
+                         cudaStream_t st);
 
 size_t adjoint_smem_bytes(int max_area, int max_deg);
 cudaError_t launch_adjoint(int K, const DevSlice* slices, const double* const* flux_tab, const double* u_all,

@@ -19,6 +19,7 @@ struct MixedArgs {
   int JB;       // largest number of 32-sample blocks in an item
   int nk_max;   // largest number of slit points in an item
   int max_deg;  // largest degree among the launched slices
+  int* err;     // debug checks: counts deposits the plan did not foresee (nullptr = off)
 };
 
 __device__ __forceinline__ float2 split_df(double v) {

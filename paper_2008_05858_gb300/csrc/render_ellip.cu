@@ -84,14 +84,13 @@ struct EllipLayout {
 
 // One CTA per work item (<= 32 wavelength samples x <= 16 slit points, at most 512 stamps,
 // so no box pixel gets more than 512 fixed-point deposits).  Each warp maps 32 stamps at a
-// time (one per lane, FP64) into its staging area; then the warp is cut into 32 / K groups
-// of K lanes, each group takes one stamp and lane m of the group evaluates column m of the
-// stamp's window: the column's x-integral, the moments of tau, and the K + 1 row edges of
+// time (one per lane, FP64) into its staging area; then the batch's 32 K (stamp, column)
+// pairs are spread over the 32 lanes (no idle lanes), and the lane holding column m of a
+// stamp evaluates the column's x-integral, the moments of tau, and the K + 1 row edges of
 // its conditional profile, depositing the K pixels into the item's box.
 template <int K>
-__global__ void __launch_bounds__(kEThreads) k_render_ellip(const MixedArgs a) {
+__global__ void __launch_bounds__(kEThreads, 6) k_render_ellip(const MixedArgs a) {
   constexpr int H = K / 2;
-  constexpr int G = 32 / K;  // stamps in flight per warp
   extern __shared__ __align__(16) unsigned char smem[];
   const Item it = a.items[blockIdx.x];
   const DevSlice& S = a.slices[it.slice];
@@ -162,7 +161,6 @@ __global__ void __launch_bounds__(kEThreads) k_render_ellip(const MixedArgs a) {
   const int Psh = total > 0.0 ? max(-100, min(100, 52 - ex)) : 0;
   const float sc = ldexpf(1.f, Psh), sc_hi = ldexpf(1.f, Psh - 22);
 
-  const int grp = lane / K, m = lane - grp * K;
   const int nst = it.nj * it.nk;
   int4* wst = stage + warp * 32;
   float2* wsw = stagew + warp * 32;
@@ -191,9 +189,14 @@ __global__ void __launch_bounds__(kEThreads) k_render_ellip(const MixedArgs a) {
     }
     __syncwarp();
     const int nb = min(32, nst - base);
-    for (int b = grp; b < nb && grp < G; b += G) {
+    // (stamp, column) pairs of the batch, flattened over the warp's 32 lanes
+    const int npairs = nb * K;
+    for (int p0 = 0; p0 < npairs; p0 += 32) {
+      const int p = p0 + lane;
+      const int b = p < npairs ? p / K : 0;
+      const int m = p < npairs ? p - b * K : 0;
       const int4 st = wst[b];
-      if (st.x == kOffFrame || st.y == kOffFrame) continue;  // uniform over the group
+      const bool valid = p < npairs && st.x != kOffFrame && st.y != kOffFrame;
       const float2 sw = wsw[b];
       const int jj = __float_as_int(sw.y);
       const float4 e0 = tabE[2 * jj], e1 = tabE[2 * jj + 1];
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__(kEThreads) k_render_ellip(const MixedArgs a) {
       const float gch = e0.z, gcl = e0.w;
       const float wq = sw.x * tx;
       const int bx = st.x - H + m - it.bx0;
-      const bool colin = bx >= 0 && bx < it.bw;
+      const bool colin = valid && bx >= 0 && bx < it.bw;
       const int by0 = st.y - H - it.by0;
       float Ep = 0.f, Fp = 0.f, hp = 0.f, whp = 0.f;
 #pragma unroll
@@ -282,7 +285,11 @@ __global__ void __launch_bounds__(kEThreads) k_render_ellip(const MixedArgs a) {
         const float wl = fmaf(dh, gch, -wh) + fmaf(dh, gcl, dl * gch);
         float dens;
         const float E = tail2_dens(wh, wl, dens);
-        const float F = fabsf(wh) < kErfMaxArg ? erf_small(wh) : 1.f - E;
+        // erf only near the conditional centre; the branch is skipped when no lane of the
+        // warp has an edge there
+        const bool near = fabsf(wh) < kErfMaxArg;
+        float F = 1.f - E;
+        if (__any_sync(0xffffffffu, near)) F = near ? erf_small(wh) : F;
         const float V = wh * kSqrt2Ln2;
         const float Gv = fmaf(fmaf(fmaf(fmaf(fmaf(g5, V, g4), V, g3), V, g2), V, g1), V, g0);
         const float h = dens * Gv;
@@ -292,8 +299,11 @@ __global__ void __launch_bounds__(kEThreads) k_render_ellip(const MixedArgs a) {
           const float ty = same ? (small ? fabsf(Fp - F) : fabsf(Ep - E)) : (Fp + F);
           const int by = by0 + n - 1;
           if (colin && by >= 0 && by < it.bh) {
-            const int p = by * it.bw + bx;
-            box_deposit(boxh + p, boxl + p, wq * (ty + (h - hp)), sc, sc_hi);
+            const int q = by * it.bw + bx;
+            box_deposit(boxh + q, boxl + q, wq * (ty + (h - hp)), sc, sc_hi);
+          } else if (a.err && valid) {  // outside the box: legitimate only off the detector
+            const int X = it.bx0 + bx, Y = it.by0 + by;
+            if (X >= 0 && X < S.W && Y >= 0 && Y < S.H) atomicAdd(a.err, 1);
           }
         }
         Ep = E;
@@ -323,9 +333,9 @@ static cudaError_t launch_ellip_one(const MixedArgs& a, int n_items, size_t smem
 
 cudaError_t launch_render_ellip(int K, const DevSlice* slices, const double* const* flux_tab, const double* u_all,
                                 const Item* items, int n_items, float2* store, int nk_max, int max_deg, size_t smem,
-                                cudaStream_t st) {
+                                cudaStream_t st, int* err) {
   if (n_items == 0) return cudaSuccess;
-  MixedArgs a{slices, flux_tab, u_all, items, store, 0, 1, nk_max, max_deg};
+  MixedArgs a{slices, flux_tab, u_all, items, store, 0, 1, nk_max, max_deg, err};
   switch (K) {
 #define E2E_CASE(KK) \
   case KK: return launch_ellip_one<KK>(a, n_items, smem, st);

@@ -16,20 +16,9 @@
 // mapping in FP64, the centre split exactly into an integer pixel and an FP32 offset, PSF
 // pixel integrals in FP32 with double-float edge arguments (phi32.cuh), FP32 sums over one
 // run (<= B stamps) in registers, exact fixed-point sums per item, FP64 across items.
-#include "e2e_device.cuh"
-#include "e2e_kernels.h"
-#include "mixed_common.cuh"
-#include "phi32.cuh"
+#include "render_mixed.cuh"
 
 namespace e2e {
-
-#ifndef E2E_MIXED_THREADS
-#define E2E_MIXED_THREADS 128
-#endif
-constexpr int kThreads = E2E_MIXED_THREADS;  // threads per render CTA
-constexpr int kWarps = kThreads / 32;
-constexpr int kPairs = kThreads / 2;
-
 
 // ------------------------------------------------------------------------------ plan
 
@@ -107,254 +96,10 @@ __global__ void k_plan(const DevSlice* __restrict__ slices, int n_slices, const 
   }
 }
 
-// ------------------------------------------------------------------------------ render
-
-
-// Shared-memory layout of one CTA (offsets in bytes), identical on host and device.
-struct MixedLayout {
-  size_t tabP, tabS, tabW, tabU, tabG, stage, boxh, boxl, total;
-  __host__ __device__ MixedLayout(int J, int NK, int nd, int B, int area) {
-    size_t o = 0;
-    tabP = o; o += (size_t)J * 2 * nd * 8;   // P_b(lt) of x and y per sample
-    tabS = o; o += (size_t)NK * 8;            // s of each slit point
-    tabW = o; o += (size_t)J * 8;             // flux x bin width / 4 per sample, (hi, lo) floats
-    tabU = o; o += (size_t)NK * 8;            // slit weights, (hi, lo) floats
-    o = (o + 15) & ~(size_t)15;
-    tabG = o; o += (size_t)J * 16;            // 1/(sqrt2 sigma) of x and y, (hi, lo) each
-    stage = o; o += (size_t)B * kPairs * 16;  // mapped stamps of the runs in flight
-    boxh = o; o += (size_t)area * 4;          // fixed-point box, high words
-    boxl = o; o += (size_t)area * 4;          // low words
-    total = o;
-  }
-};
-
-
-// Two CTAs per SM (128 registers) when a lane's accumulator tile is small enough, else one.
-#ifndef E2E_MID_TILE_BLOCKS
-#define E2E_MID_TILE_BLOCKS 4
-#endif
-// CTAs per SM the register budget is set for (128-thread CTAs): 4 (128 registers) for lane
-// tiles up to 72 accumulators, E2E_MID_TILE_BLOCKS up to 84, else 2.
-template <int K, int DX, int DY>
-constexpr int mixed_min_blocks() {
-  return ((K + DX) * ((K + DY + 1) / 2) <= 72 ? 4 : ((K + DX) * ((K + DY + 1) / 2) <= 84 ? E2E_MID_TILE_BLOCKS : 2)) *
-         128 / kThreads;
-}
-
-template <int K, int DX, int DY>
-__global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_render_mixed(const MixedArgs a) {
-  constexpr int RX = K + DX, RY = K + DY, H = K / 2;
-  constexpr int D = DX > DY ? DX : DY;  // slack of the profile a lane evaluates
-  constexpr int R = K + D;              // pixels of that profile
-  constexpr int RYH = (RY + 1) / 2;     // tile rows accumulated per lane of a pair
-  extern __shared__ __align__(16) unsigned char smem[];
-  const Item it = a.items[blockIdx.x];
-  const DevSlice& S = a.slices[it.slice];
-  const int area = it.bw * it.bh;
-  const int nd = S.degree + 1;
-  const MixedLayout L(32 * a.JB, a.nk_max, a.max_deg + 1, a.B, area);
-  double* tabP = reinterpret_cast<double*>(smem + L.tabP);
-  double* tabS = reinterpret_cast<double*>(smem + L.tabS);
-  float2* tabW = reinterpret_cast<float2*>(smem + L.tabW);
-  float2* tabU = reinterpret_cast<float2*>(smem + L.tabU);
-  float4* tabG = reinterpret_cast<float4*>(smem + L.tabG);
-  int4* stage = reinterpret_cast<int4*>(smem + L.stage);
-  int* boxh = reinterpret_cast<int*>(smem + L.boxh);
-  unsigned* boxl = reinterpret_cast<unsigned*>(smem + L.boxl);
-  __shared__ double s_w[kWarps], s_u[kWarps];
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int p = tid; p < area; p += kThreads) {
-    boxh[p] = 0;
-    boxl[p] = 0u;
-  }
-  const double* flux = a.flux_tab[S.flux_slot];
-  const double* u = a.u_all + S.u_off;
-  const double inv_nl = 1.0 / (double)S.n_lambda, inv_ns = 1.0 / (double)S.n_slit;
-  double usum = 0.0;
-  for (int kk = tid; kk < it.nk; kk += kThreads) {
-    const double uk = u[it.k0 + kk];
-    tabS[kk] = norm_sample_r(it.k0 + kk, S.n_slit, inv_ns);
-    tabU[kk] = split_df(uk);
-    usum += fabs(uk);
-  }
-  double wsum = 0.0;
-  for (int jj = tid; jj < it.nj; jj += kThreads) {
-    const double lt = norm_sample_r(it.j0 + jj, S.n_lambda, inv_nl);
-    for (int b = 0; b < nd; ++b) {
-      tabP[(jj * 2 + 0) * nd + b] = poly_lt_for_b(S.cx, S.degree, b, lt);
-      tabP[(jj * 2 + 1) * nd + b] = poly_lt_for_b(S.cy, S.degree, b, lt);
-    }
-    // edge arguments are carried in log2 units: w = (edge - centre) sqrt(log2 e) / (sqrt2 sigma)
-    const double sgx = fma(fma(S.sx[2], lt, S.sx[1]), lt, S.sx[0]);
-    const double sgy = fma(fma(S.sy[2], lt, S.sy[1]), lt, S.sy[0]);
-    const double kq = kSqrtLog2eD * 0.70710678118654752440;
-    const float2 gx = split_df(kq / sgx), gy = split_df(kq / sgy);
-    tabG[jj] = make_float4(gx.x, gx.y, gy.x, gy.y);
-    const double wj = flux[it.j0 + jj] * S.dlam;
-    tabW[jj] = split_df(wj * 0.25);  // 0.25: the profiles below are 2x the pixel integrals
-    wsum += fabs(wj);
-  }
-  // flux bound of the item: sum over its stamps of |w| (bounds every pixel of its box)
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
-    usum += __shfl_xor_sync(0xffffffffu, usum, o);
-  }
-  if (lane == 0) {
-    s_w[warp] = wsum;
-    s_u[warp] = usum;
-  }
-  __syncthreads();
-  double wtot = 0.0, utot = 0.0;
-#pragma unroll
-  for (int q = 0; q < kWarps; ++q) {
-    wtot += s_w[q];
-    utot += s_u[q];
-  }
-  const double total = wtot * utot;
-  // scale 2^P with |box sums| <= total < 2^(52-P); clamp so 2^P stays a normal FP32
-  int ex = 0;
-  frexp(total, &ex);
-  const int Psh = total > 0.0 ? max(-100, min(100, 52 - ex)) : 0;
-  const float sc = ldexpf(1.f, Psh), sc_hi = ldexpf(1.f, Psh - 22);
-
-  // A lane pair owns one run: lane 0 evaluates the x profile, lane 1 the y profile (same
-  // code, different inputs), they swap profiles by shuffle, and each accumulates half of
-  // the tile's rows.
-  const int q = lane >> 1, par = lane & 1;
-  const int nrc = (it.nk + a.B - 1) / a.B;
-  const int njh = (it.nj + 15) / 16;
-  const int ntask = njh * nrc;
-  int4* mystage = stage + warp * 16 + q;
-  for (int task = warp; task < ntask && total > 0.0; task += kWarps) {
-    const int jj = (task % njh) * 16 + q;
-    const bool jvalid = jj < it.nj;      // uniform over the pair
-    const int kk0 = (task / njh) * a.B;  // first slit point of the run, relative to the item
-    const int nb = min(a.B, it.nk - kk0);
-    // map the run's stamps (FP64), half each, into the staging area
-    {
-      double px[9], py[9];
-#pragma unroll
-      for (int b = 0; b <= 8; ++b) {
-        px[b] = (jvalid && b < nd) ? tabP[(jj * 2 + 0) * nd + b] : 0.0;
-        py[b] = (jvalid && b < nd) ? tabP[(jj * 2 + 1) * nd + b] : 0.0;
-      }
-      for (int b = par; b < nb; b += 2) {
-        int ci = kOffFrame, ri = kOffFrame;
-        float fx = 0.f, fy = 0.f;
-        if (jvalid) {
-          const double s = tabS[kk0 + b];
-          split_coord(horner_s(px, S.degree, s), ci, fx);
-          split_coord(horner_s(py, S.degree, s), ri, fy);
-        }
-        mystage[b * kPairs] = make_int4(ci, ri, __float_as_int(fx), __float_as_int(fy));
-      }
-    }
-    __syncwarp();
-    int xmn = 1 << 30, ymn = 1 << 30;
-    for (int b = 0; b < nb; ++b) {
-      const int4 st = mystage[b * kPairs];
-      if (st.x != kOffFrame && st.y != kOffFrame) {
-        xmn = min(xmn, st.x);
-        ymn = min(ymn, st.y);
-      }
-    }
-    const float4 g4 = jvalid ? tabG[jj] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float gh = par ? g4.z : g4.x, gl = par ? g4.w : g4.y;
-    const float2 wj = jvalid ? tabW[jj] : make_float2(0.f, 0.f);
-    float acc[RYH][RX];
-#pragma unroll
-    for (int r = 0; r < RYH; ++r)
-#pragma unroll
-      for (int c = 0; c < RX; ++c) acc[r][c] = 0.f;
-    for (int b = 0; b < nb; ++b) {
-      const int4 st = mystage[b * kPairs];
-      const bool on = st.x != kOffFrame && st.y != kOffFrame;
-      const int o = on ? (par ? st.y - ymn : st.x - xmn) : 0;  // window offset in the tile, 0..D
-      const float f = __int_as_float(par ? st.w : st.z);
-      const float2 uk = tabU[kk0 + b];
-      const float w = on ? fmaf(wj.x, uk.x, fmaf(wj.x, uk.y, wj.y * uk.x)) : 0.f;
-      const float mult = par ? (on ? 1.f : 0.f) : w;  // the weight rides on the x profile
-      // Profile of the stamp's own K-pixel window, window pixel m spanning edges m and m+1
-      // at offsets (m - H -+ 1/2) - f from the stamp centre: tails E = erfc(|w|) at every
-      // edge, and erf F = erf(|w|) at the four edges around the centre pixel H.  Twice the
-      // pixel integrals are differences of left tails (m < H-1), of right tails (m > H+1),
-      // and sums / differences of erf for the centre pixel and its two neighbours.
-      float E[K + 1], F[K + 1];
-#pragma unroll
-      for (int m = 0; m <= K; ++m) {
-        float wh, wl;
-        edge_arg((float)(m - H) - 0.5f, f, gh, gl, wh, wl);
-        E[m] = tail2(wh, wl);
-        if (m >= H - 1 && m <= H + 2) F[m] = fabsf(wh) < kErfMaxArg ? erf_small(wh) : 1.f - E[m];
-      }
-      float win[K];
-#pragma unroll
-      for (int m = 0; m < K; ++m) {
-        float v;
-        if (m < H - 1) v = E[m + 1] - E[m];
-        else if (m == H - 1) v = F[m] - F[m + 1];
-        else if (m == H) v = F[m] + F[m + 1];
-        else if (m == H + 1) v = F[m + 1] - F[m];
-        else v = E[m] - E[m + 1];
-        win[m] = mult * v;
-      }
-      // place the window at its offset o (0..D) in the tile: prof[c] = win[c - o]
-      float prof[R];
-#pragma unroll
-      for (int c = 0; c < R; ++c) {
-        float v = 0.f;
-#pragma unroll
-        for (int d = 0; d <= D; ++d)
-          if (c - d >= 0 && c - d < K) v = (o == d) ? win[c - d] : v;
-        prof[c] = v;
-      }
-      float ax[RX], ay[RYH];
-#pragma unroll
-      for (int c = 0; c < R; ++c) {
-        const float other = __shfl_xor_sync(0xffffffffu, prof[c], 1);
-        if (c < RX) ax[c] = par ? other : prof[c];
-        if (c < RYH) ay[c] = par ? 0.f : other;  // lane 0: rows 0..RYH-1 of lane 1's y profile
-      }
-#pragma unroll
-      for (int i = 0; i < RYH; ++i)
-        if (RYH + i < RY) ay[i] = par ? prof[RYH + i] : ay[i];  // lane 1: its own rows RYH..RY-1
-#pragma unroll
-      for (int r = 0; r < RYH; ++r)
-#pragma unroll
-        for (int c = 0; c < RX; ++c) acc[r][c] = fmaf(ay[r], ax[c], acc[r][c]);
-    }
-    __syncwarp();  // the staging is reused by the next task
-    // flush this lane's rows of the run tile as exact fixed-point increments
-    if (xmn != (1 << 30)) {
-      const int gx0 = xmn - H - it.bx0, gy0 = ymn - H - it.by0 + par * RYH;
-      const int nrow = min(RYH, RY - par * RYH);
-      const bool inside = gx0 >= 0 && gx0 + RX <= it.bw && gy0 >= 0 && gy0 + nrow <= it.bh;
-#pragma unroll
-      for (int r = 0; r < RYH; ++r) {
-        const int gy = gy0 + r;
-        if (r >= nrow || (!inside && (gy < 0 || gy >= it.bh))) continue;
-        int* rowh = boxh + gy * it.bw + gx0;
-        unsigned* rowl = boxl + gy * it.bw + gx0;
-#pragma unroll
-        for (int c = 0; c < RX; ++c) {
-          if (!inside && (gx0 + c < 0 || gx0 + c >= it.bw)) continue;
-          box_deposit(rowh + c, rowl + c, acc[r][c], sc, sc_hi);
-        }
-      }
-    }
-  }
-  __syncthreads();
-  // box value = (hi word * 2^22 + lo word) * 2^-P, written as an unevaluated FP32 pair
-  float2* out = a.store + it.store_off;
-  const float inv = ldexpf(1.f, -Psh);
-  for (int p = tid; p < area; p += kThreads) out[p] = fixed_to_pair(boxh[p], boxl[p], inv);
-}
-
 size_t mixed_smem_bytes(int area, int JB, int nk_max, int B, int nd) {
   return MixedLayout(32 * JB, nk_max, nd, B, area).total;
 }
+
 
 // ------------------------------------------------------------------------------ merge
 
@@ -422,14 +167,6 @@ cudaError_t launch_plan(const DevSlice* slices, int n_slices, const int64_t* tas
   return cudaGetLastError();
 }
 
-template <int K, int DX, int DY>
-static cudaError_t launch_one(const MixedArgs& a, int n_items, size_t smem, cudaStream_t st) {
-  auto kern = k_render_mixed<K, DX, DY>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  kern<<<n_items, kThreads, smem, st>>>(a);
-  return cudaGetLastError();
-}
 
 bool mixed_variant_supported(int K, int DX, int DY) {
   if (K < 1 || K > 15 || (K % 2) == 0) return false;
@@ -443,17 +180,13 @@ bool mixed_variant_supported(int K, int DX, int DY) {
 
 cudaError_t launch_render_mixed(int K, int DX, int DY, const DevSlice* slices, const double* const* flux_tab,
                                 const double* u_all, const Item* items, int n_items, float2* store, int B, int JB,
-                                int nk_max, int max_deg, size_t smem, cudaStream_t st) {
+                                int nk_max, int max_deg, size_t smem, cudaStream_t st, int* err) {
   if (n_items == 0) return cudaSuccess;
-  MixedArgs a{slices, flux_tab, u_all, items, store, B, JB, nk_max, max_deg};
+  MixedArgs a{slices, flux_tab, u_all, items, store, B, JB, nk_max, max_deg, err};
+  if (err) return launch_render_mixed_checked(K, DX, DY, a, n_items, smem, st);
 #define E2E_V(KK, X, Y) \
-  if (K == KK && DX == X && DY == Y) return launch_one<KK, X, Y>(a, n_items, smem, st);
-  E2E_V(1, 0, 0) E2E_V(3, 0, 0) E2E_V(5, 0, 0) E2E_V(7, 0, 0) E2E_V(9, 0, 0) E2E_V(11, 0, 0) E2E_V(13, 0, 0)
-  E2E_V(15, 0, 0)
-  E2E_V(1, 1, 1) E2E_V(3, 1, 1) E2E_V(5, 1, 1) E2E_V(7, 1, 1) E2E_V(9, 1, 1) E2E_V(11, 1, 1) E2E_V(13, 1, 1)
-  E2E_V(1, 1, 2) E2E_V(3, 1, 2) E2E_V(5, 1, 2) E2E_V(7, 1, 2) E2E_V(9, 1, 2) E2E_V(11, 1, 2) E2E_V(13, 1, 2)
-  E2E_V(1, 1, 3) E2E_V(3, 1, 3) E2E_V(5, 1, 3) E2E_V(7, 1, 3) E2E_V(9, 1, 3) E2E_V(11, 1, 3)
-  E2E_V(1, 2, 2) E2E_V(3, 2, 2) E2E_V(5, 2, 2) E2E_V(7, 2, 2) E2E_V(9, 2, 2)
+  if (K == KK && DX == X && DY == Y) return launch_one<KK, X, Y, false>(a, n_items, smem, st);
+  E2E_MIXED_VARIANTS(E2E_V)
 #undef E2E_V
   return cudaErrorInvalidValue;
 }

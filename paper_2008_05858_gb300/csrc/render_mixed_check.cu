@@ -1,0 +1,17 @@
+// Debug-check instantiations of the separable-PSF mixed render kernel (e2e_opts.debug_checks):
+// the same kernel, also counting every deposit the plan did not foresee.  A separate
+// translation unit so that the library's two sets of instantiations compile in parallel.
+#include "render_mixed.cuh"
+
+namespace e2e {
+
+cudaError_t launch_render_mixed_checked(int K, int DX, int DY, const MixedArgs& a, int n_items, size_t smem,
+                                        cudaStream_t st) {
+#define E2E_V(KK, X, Y) \
+  if (K == KK && DX == X && DY == Y) return launch_one<KK, X, Y, true>(a, n_items, smem, st);
+  E2E_MIXED_VARIANTS(E2E_V)
+#undef E2E_V
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace e2e

@@ -224,3 +224,24 @@ def test_render_alloc_and_fetch(renderer):
     assert compare(host.astype(np.float64), ref).ok
     with pytest.raises(B.E2EError):
         B.e2e_release_frame(renderer.ctx, fid)
+
+
+@pytest.mark.parametrize("kind", ["separable", "elliptical"])
+def test_debug_checks_find_nothing_and_change_nothing(kind):
+    # debug mode counts deposits outside the planned boxes; the plan covers every stamp, so
+    # a checked render succeeds and is bitwise the unchecked one
+    from paper_2008_05858_gb300.binding import Renderer
+
+    psf = W.PSF_ELLIPTICAL if kind == "elliptical" else W.PSF_SEPARABLE
+    ws = [W.small_config(seed=301, psf=psf), W.small_config(seed=302, K=7, n_lambda=500, n_slit=40, psf=psf),
+          W.config2(n_orders=6)]
+    plain, checked = Renderer(0), Renderer(0, debug_checks=1)
+    try:
+        for w in ws[: 3 if kind == "separable" else 2]:
+            a = gpu_frames(plain, w, "mixed", "f32")
+            b = gpu_frames(checked, w, "mixed", "f32")
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y)
+    finally:
+        plain.close()
+        checked.close()
