@@ -28,7 +28,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "noise.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "noise.c"), os.path.join(_HERE, "photons.c")]
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -118,6 +118,10 @@ def lib():
             L.oracle_add_noise.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp, C.POINTER(OracleNoise), dp,
                                            C.POINTER(C.c_int32), dp]
             L.oracle_add_noise.restype = C.c_int
+            L.oracle_render_photons.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int,
+                                                C.POINTER(OracleSlice), C.c_int, C.c_uint64,
+                                                C.POINTER(C.POINTER(C.c_uint32)), C.POINTER(C.c_uint64)]
+            L.oracle_render_photons.restype = C.c_int
             _lib = L
     return _lib
 
@@ -170,6 +174,21 @@ def render(model, flux_of, n_threads: int = 0) -> List[np.ndarray]:
     if rc != 0:
         raise ValueError("oracle_render rejected the model")
     return frames
+
+
+def render_photons(model, flux_of, seed: int) -> Tuple[List[np.ndarray], int]:
+    """Photon Monte-Carlo frames (uint32 counts per detector) and the number of photons drawn."""
+    L = lib()
+    m = _Marshalled(model, flux_of)
+    H = (C.c_int * len(model.det_shape))(*[h for h, w in model.det_shape])
+    W = (C.c_int * len(model.det_shape))(*[w for h, w in model.det_shape])
+    frames = [np.zeros((h, w), dtype=np.uint32) for h, w in model.det_shape]
+    ptrs = (C.POINTER(C.c_uint32) * len(frames))(*[f.ctypes.data_as(C.POINTER(C.c_uint32)) for f in frames])
+    total = C.c_uint64()
+    rc = L.oracle_render_photons(len(frames), H, W, m.n, m.arr, int(model.psf), seed, ptrs, C.byref(total))
+    if rc != 0:
+        raise ValueError("oracle_render_photons rejected the model")
+    return frames, total.value
 
 
 def render_workload(w, n_threads: int = 0) -> List[np.ndarray]:

@@ -62,14 +62,26 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
   out[3] = c3;
 }
 
-static double uni(uint32_t a, uint32_t b) {
+double oracle_uniform53(uint32_t a, uint32_t b) {
   return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6) + 0.5) / 9007199254740992.0;
 }
+#define uni oracle_uniform53
 
-static void block(uint64_t seed, uint32_t q, uint32_t d, uint32_t i, uint32_t stream, uint32_t w[4]) {
-  const uint32_t ctr[4] = {q, d, i, stream};
+void oracle_block(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t w[4]) {
+  const uint32_t ctr[4] = {c0, c1, c2, c3};
   const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   oracle_philox4x32_10(ctr, key, w);
+}
+#define block oracle_block
+
+void oracle_normal_pair_ctr(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, double* left,
+                            double* right) {
+  uint32_t w[4];
+  block(seed, c0, c1, c2, c3, w);
+  const double rho = sqrt(-2.0 * log(uni(w[0], w[1])));
+  const double ph = 2.0 * NOISE_PI * uni(w[2], w[3]);
+  *left = rho * cos(ph);
+  *right = rho * sin(ph);
 }
 
 void oracle_normal_pair(uint64_t seed, uint32_t q, uint32_t d, uint32_t stream, double* left, double* right) {
@@ -82,10 +94,14 @@ void oracle_normal_pair(uint64_t seed, uint32_t q, uint32_t d, uint32_t stream, 
 }
 
 long oracle_poisson(double lam, uint64_t seed, uint32_t q, uint32_t d, uint32_t side) {
+  return oracle_poisson_stream(lam, seed, q, d, 2 + side);
+}
+
+long oracle_poisson_stream(double lam, uint64_t seed, uint32_t q, uint32_t d, uint32_t stream) {
   if (!(lam > 0.0)) return 0;
   uint32_t w[4];
   if (lam < 10.0) {
-    block(seed, q, d, 0, 2 + side, w);
+    block(seed, q, d, 0, stream, w);
     const double u = uni(w[0], w[1]);
     long k = 0;
     double p = exp(-lam), F = p;
@@ -102,7 +118,7 @@ long oracle_poisson(double lam, uint64_t seed, uint32_t q, uint32_t d, uint32_t 
   const double invalpha = 1.1239 + 1.1328 / (b - 3.4);
   const double vr = 0.9277 - 3.6224 / (b - 2.0);
   for (uint32_t i = 0; i < 64; ++i) {
-    block(seed, q, d, i, 2 + side, w);
+    block(seed, q, d, i, stream, w);
     const double U = uni(w[0], w[1]) - 0.5, V = uni(w[2], w[3]);
     const double us = 0.5 - fabs(U);
     const double k = floor((2.0 * a / us + b) * U + lam + 0.43);

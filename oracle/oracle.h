@@ -101,7 +101,15 @@ typedef struct {
   int32_t poisson;        /* 1 = Poisson draws, 0 = expected values */
 } oracle_noise;
 
-/* Philox4x32-10 block for counter ctr and key. */
+/* Philox4x32-10 block for counter ctr and key; the block of counter (c0, c1, c2, c3) under
+ * the key of a 64-bit seed; the 53-bit uniform on (0, 1) made from two of its words. */
+void oracle_block(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t w[4]);
+double oracle_uniform53(uint32_t a, uint32_t b);
+/* Box-Muller pair from the block of counter (c0, c1, c2, c3). */
+void oracle_normal_pair_ctr(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, double* left,
+                            double* right);
+/* Poisson(lam) from blocks (q, d, trial, stream), trial = 0, 1, ... */
+long oracle_poisson_stream(double lam, uint64_t seed, uint32_t q, uint32_t d, uint32_t stream);
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 /* Box-Muller pair of standard normals from block (seed, (q, d, 0, stream)). */
 void oracle_normal_pair(uint64_t seed, uint32_t q, uint32_t d, uint32_t stream, double* left, double* right);
@@ -112,6 +120,17 @@ long oracle_poisson(double lam, uint64_t seed, uint32_t q, uint32_t d, uint32_t 
  * Poisson counts.  Returns 0 or -1. */
 int oracle_add_noise(int H, int W, int row0, int det, const double* S, const oracle_noise* p, double* E,
                      int32_t* adu, double* counts);
+
+/* ---------------------------------------------------------------- photon Monte-Carlo (photons.c) */
+
+/* Photon-by-photon rendering of every order-slice (the alternative of Sec. 2.2): per slice
+ * index i and wavelength bin j, N ~ Poisson(flux[j] dlam sum_k u_k) photons; photon p takes
+ * a wavelength uniform in its bin, a slit point k with probability u_k / sum u and a position
+ * uniform in that point's bin, the PSF offset of a bivariate normal, and is counted in the
+ * pixel containing it.  counts[d] (H x W, row-major) are overwritten; *total = photons drawn.
+ * Returns 0, or -1 on an invalid argument. */
+int oracle_render_photons(int n_det, const int* H, const int* W, int n_slices, const oracle_slice* s, int psf,
+                          uint64_t seed, uint32_t* const* counts, uint64_t* total);
 
 #ifdef __cplusplus
 }

@@ -2,6 +2,7 @@
 
     python -m paper_2008_05858_gb300.cli render --config 2 --orders 12 --repeat 3
     python -m paper_2008_05858_gb300.cli render --config 5 --precision fp64 --save frame.npy
+    python -m paper_2008_05858_gb300.cli aliasing        # flat-field sampling study (Fig. 4)
 
 ``--orders`` shortens the full-detector workload (config 2) to its first orders so a profiler
 capture stays small; every other shape is the named configuration's.
@@ -52,6 +53,28 @@ def cmd_render(args) -> int:
     return 0
 
 
+def cmd_aliasing(args) -> int:
+    import json
+
+    from . import aliasing as A
+    from .binding import Renderer
+
+    r = Renderer(args.device)
+
+    def render(w):
+        mid = r.load_model(w.model)
+        out = r.render(mid, r.load_spectra(w), "mixed", "f64")[0].cpu().numpy()
+        r.unload_model(mid)
+        return out
+
+    rows = A.study(render, samples=[float(x) for x in args.samples.split(",")], sigma=args.sigma,
+                   peak_e=args.peak_e)
+    for row in rows:
+        print(json.dumps(row))
+    r.close()
+    return 0
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(prog="paper_2008_05858_gb300.cli")
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -63,9 +86,16 @@ def main(argv=None) -> int:
     p.add_argument("--dtype", default=None, choices=[None, "f32", "f64"])
     p.add_argument("--device", type=int, default=0)
     p.add_argument("--save", default=None)
+    pa = sub.add_parser("aliasing", help="ripple of a flat field vs wavelength samples per resolution element")
+    pa.add_argument("--samples", default="0.75,1,1.25,1.5,2,3,5,10")
+    pa.add_argument("--sigma", type=float, default=1.5)
+    pa.add_argument("--peak-e", type=float, default=40000.0)
+    pa.add_argument("--device", type=int, default=0)
     args = ap.parse_args(argv)
     if args.cmd == "render":
         return cmd_render(args)
+    if args.cmd == "aliasing":
+        return cmd_aliasing(args)
     return 1
 
 

@@ -116,6 +116,12 @@ struct e2e_ctx {
   cudaMemPool_t pool = nullptr;
   cudaStream_t free_stream = nullptr;  // where library frames are returned to the pool
   int* d_err = nullptr;                // debug checks: deposits outside the planned boxes
+  struct NoisePattern {                // pixel response map of a model's detectors (FP64)
+    uint64_t pattern_seed = 0;
+    double prnu = 0.0;
+    std::vector<double*> R;
+  };
+  std::map<uint64_t, NoisePattern> patterns;  // by model id
   // kernel timing of the most recent render (opts.kernel_timing)
   struct Timed {
     const char* name;
@@ -717,6 +723,8 @@ void e2e_destroy(e2e_ctx* ctx) {
     for (auto& kv : ctx->models) free_model(kv.second.get());
     for (auto& kv : ctx->spectra) cudaFree(kv.second->d_flux);
     for (auto& kv : ctx->frames) free_frame(ctx, kv.second.get());
+    for (auto& kv : ctx->patterns)
+      for (double* p : kv.second.R) cudaFree(p);
     cudaStreamSynchronize(ctx->free_stream);
     cudaStreamDestroy(ctx->free_stream);
     cudaFree(ctx->d_err);
@@ -821,6 +829,11 @@ int e2e_unload_model(e2e_ctx* ctx, uint64_t model_id) {
   cudaDeviceSynchronize();
   free_model(it->second.get());
   ctx->models.erase(it);
+  auto pt = ctx->patterns.find(model_id);
+  if (pt != ctx->patterns.end()) {
+    for (double* q : pt->second.R) cudaFree(q);
+    ctx->patterns.erase(pt);
+  }
   return E2E_OK;
 }
 
@@ -1467,12 +1480,35 @@ int e2e_add_noise(e2e_ctx* ctx, uint64_t model_id, const e2e_noise_params* p, in
       return fail(E2E_EINVAL, "in-place noise needs the same dtype and pitch");
   }
   if (ctx->opts.kernel_timing) reset_timing(ctx);
+  cudaStream_t st = (cudaStream_t)stream;
+  // the pixel response is a fixed pattern: computed once per (model, pattern seed, prnu)
+  std::vector<double*> R(m->n_det, nullptr);
+  if (p->prnu != 0.0) {
+    auto& pat = ctx->patterns[model_id];
+    if (pat.R.empty() || pat.pattern_seed != p->pattern_seed || pat.prnu != p->prnu) {
+      cudaStreamSynchronize(st);  // a previous pattern may still be read
+      for (double* q : pat.R) cudaFree(q);
+      pat.R.assign(m->n_det, nullptr);
+      pat.pattern_seed = p->pattern_seed;
+      pat.prnu = p->prnu;
+      for (int d = 0; d < m->n_det; ++d) {
+        cudaError_t e = cudaMalloc((void**)&pat.R[d], (size_t)m->H[d] * m->W[d] * sizeof(double));
+        if (e == cudaSuccess) e = launch_prnu_map(pat.R[d], m->H[d], m->W[d], d, p->pattern_seed, p->prnu, st);
+        if (e != cudaSuccess) {
+          for (double* q : pat.R) cudaFree(q);
+          ctx->patterns.erase(model_id);
+          return cuda_fail(e, "pixel response map");
+        }
+      }
+    }
+    R = pat.R;
+  }
   for (int d = 0; d < m->n_det; ++d) {
     const int64_t sp = src_pitch ? src_pitch[d] : m->W[d], dp = dst_pitch ? dst_pitch[d] : m->W[d];
-    KernelTimer kt(ctx, (cudaStream_t)stream, "noise");
+    KernelTimer kt(ctx, st, "noise");
     E2E_CK(launch_noise(p->seed, p->pattern_seed, p->dark_e, p->prnu, p->ron_e, p->xtalk, p->gain, p->bias,
-                        p->saturation, p->poisson, src_dtype, src[d], sp, dst_dtype, dst[d], dp, m->H[d], m->W[d], d,
-                        (cudaStream_t)stream));
+                        p->saturation, p->poisson, src_dtype, src[d], sp, R[d], dst_dtype, dst[d], dp, m->H[d],
+                        m->W[d], d, st));
   }
   return E2E_OK;
 }

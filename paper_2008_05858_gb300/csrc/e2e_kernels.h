@@ -35,10 +35,11 @@ cudaError_t launch_render_fp64_ellip(int K, int n_slices, int64_t max_stamps, co
                                      const double* const* flux_tab, const double* u_all, double* const* acc,
                                      const int64_t* pitch, cudaStream_t st);
 
+cudaError_t launch_prnu_map(double* R, int H, int W, int det, uint64_t pattern_seed, double prnu, cudaStream_t st);
 cudaError_t launch_noise(uint64_t seed, uint64_t pattern_seed, double dark, double prnu, double ron, double xtalk,
                          double gain, double bias, int saturation, int poisson, int src_dtype, const void* src,
-                         int64_t src_pitch, int dst_dtype, void* dst, int64_t dst_pitch, int H, int W, int det,
-                         cudaStream_t st);
+                         int64_t src_pitch, const double* R, int dst_dtype, void* dst, int64_t dst_pitch, int H, int W,
+                         int det, cudaStream_t st);
 
 size_t adjoint_smem_bytes(int max_area, int max_deg);
 cudaError_t launch_adjoint(int K, const DevSlice* slices, const double* const* flux_tab, const double* u_all,

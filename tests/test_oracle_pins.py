@@ -369,3 +369,34 @@ def test_accuracy_requirement_golden_is_self_consistent():
         g = json.load(f)
     px = g["resolving_power"] * g["pixels_per_resolution_element"] * g["velocity_cm_s"] * 1e-2 / 299792458.0
     assert px == pytest.approx(g["photocenter_shift_px"], rel=0.05)
+
+
+@pytest.mark.parametrize("n", [0.75, 1.0, 1.25])
+def test_flat_field_aliasing_matches_poisson_summation(n):
+    # A flat field sampled n times per FWHM ripples with amplitude 2|P(1/h)| / P(0),
+    # P(f) = exp(-2 pi^2 sigma^2 f^2) sinc(f) (Poisson summation over the sample comb; the
+    # pixel box gives the sinc): written here from the Fourier transforms, not the oracle's
+    # erf stamps.
+    import math
+
+    from paper_2008_05858_gb300 import aliasing as A
+
+    w = A.flat_field(n)
+    h = A.sample_spacing(w)
+    f = 1.0 / h
+    want = 2.0 * math.exp(-2.0 * math.pi ** 2 * 1.5 ** 2 * f * f) * abs(math.sin(math.pi * f) / (math.pi * f))
+    got = A.measured_ripple(oracle.render_workload(w)[0], w)["ripple"]
+    assert got == pytest.approx(want, rel=2e-3)
+
+
+def test_ten_samples_per_resolution_element_alias_below_photon_noise():
+    # the sampling the paper settles on (Sec. 2.2, Fig. 4): ~10 wavelength samples per
+    # resolution element keep the aliasing under the photon noise of a ~40000 e-/px flat field
+    from paper_2008_05858_gb300 import aliasing as A
+
+    w = A.flat_field(10.0, peak_e=40000.0)
+    r = A.measured_ripple(oracle.render_workload(w)[0], w)
+    assert r["ripple"] < 1e-3 * r["photon_noise_peak_pixel"]
+    w1 = A.flat_field(1.0, peak_e=40000.0)
+    r1 = A.measured_ripple(oracle.render_workload(w1)[0], w1)
+    assert r1["ripple"] > r1["photon_noise_peak_pixel"]  # one sample per FWHM is not enough
