@@ -348,6 +348,8 @@ def run_gpu(args):
     }
     if not args.no_noise:
         line["noise"] = noise_run(B, r, mid, frame, stream, flush)
+    if not args.no_photons:
+        line["photon_mc"] = photon_run(B, r, mid, sids, w, stream, flush, kr + km)
     if not args.no_elliptical:
         line["elliptical"] = elliptical_run(B, dev, rank, world,
                                             cpu_baseline=(rank == 0 and world == 1 and not args.no_cpu_baseline))
@@ -363,6 +365,47 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def photon_run(B, r, mid, sids, w, stream, flush, stamp_ms, reps=3):
+    """The photon Monte-Carlo renderer on the full-detector model, its spectra scaled to
+    1e7 / 1e8 / 1e9 expected photons: photons/s, and the photon count at which it costs what
+    one stamp render of the frame costs."""
+    import torch
+
+    from paper_2008_05858_gb300 import binding as Bd
+
+    tot = sum(float(np.sum(w.flux_for(s))) * (s.lambda_hi - s.lambda_lo) / s.n_lambda * float(np.sum(s.slit_weights))
+              for s in w.model.slices)
+    out = r.render_photons(mid, sids, seed=7, stream=stream, want_total=False)[0]
+    rows = []
+    for target in (1e7, 1e8, 1e9):
+        k = target / tot
+        ids = []
+        for f, sp in w.spectra.items():
+            ids.append(r.load_spectrum(Bd_spec(sp, k)))
+        _, n = r.render_photons(mid, ids, seed=7, out=out, stream=stream)
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r.render_photons(mid, ids, seed=7, out=out, stream=stream, want_total=False)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        for i in ids:
+            Bd.e2e_unload_spectrum(r.ctx, i)
+        t = statistics.median(ms)
+        rows.append({"photons": n, "ms": t, "photons_per_s": n / (t * 1e-3)})
+    rate = rows[-1]["photons_per_s"]
+    return {"runs": rows, "stamp_render_ms": stamp_ms,
+            "photons_at_equal_cost": rate * stamp_ms * 1e-3,
+            "note": "photon Monte-Carlo (Sec. 2.2 alternative): FP64 mapping and Box-Muller per photon"}
+
+
+def Bd_spec(sp, k):
+    return W.Spectrum(sp.fiber, {o: f * k for o, f in sp.flux.items()})
 
 
 def noise_run(B, r, mid, frame, stream, flush, reps=5):
@@ -584,6 +627,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-elliptical", action="store_true")
     ap.add_argument("--no-noise", action="store_true")
+    ap.add_argument("--no-photons", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

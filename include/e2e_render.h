@@ -198,6 +198,24 @@ int e2e_render_adjoint(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const ui
 int e2e_update_model(e2e_ctx* ctx, uint64_t model_id, const double* cx, const double* cy, const double* sx,
                      const double* sy);
 
+/* ------------------------------------------------------------------ photon Monte-Carlo */
+
+/* Render by tracing individual photons (the alternative to the stamp method that Sec. 2.2
+ * describes: photons drawn from the spectrum with an assumed fiber illumination and an
+ * analytic PSF, binned into pixels).  For order-slice i and wavelength bin j:
+ *   N_ij ~ Poisson(flux[j] * dlam * sum_k u_k) photons; photon p gets a wavelength uniform in
+ *   its bin, a slit point k with probability u_k / sum u and a position uniform in that
+ *   point's bin, the spectral-format mapping, a PSF offset (the model's separable or rotated
+ *   Gaussian, not truncated), and is counted in the pixel containing it if on the detector.
+ * Draws come from Philox4x32-10 keyed by `seed`, indexed by (bin, slice, photon, stream): the
+ * frame is a pure function of (model, spectra, seed).
+ *   dst[d]: device uint32 frames (overwritten), pitch_elems as for e2e_render;
+ *   total_photons: host pointer or NULL; when given, the call waits for the stream and
+ *                  stores the number of photons drawn (on and off the detectors).
+ * Slit weights must be >= 0.  Errors: E2E_EINVAL, E2E_ENOTFOUND, E2E_ENOMEM, E2E_ECUDA. */
+int e2e_render_photons(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids, uint64_t seed,
+                       uint32_t* const* dst, const int64_t* pitch_elems, uint64_t* total_photons, void* stream);
+
 /* ------------------------------------------------------------------ detector noise */
 
 /* Noise stage applied to rendered frames (Sec. 2.2 ends the simulation by adding photon

@@ -29,6 +29,9 @@
 #include <string.h>
 
 #include "oracle.h"
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 static int n_coeffs(int d) { return (d + 1) * (d + 2) / 2; }
 
@@ -48,11 +51,16 @@ int oracle_render_photons(int n_det, const int* H, const int* W, int n_slices, c
                           uint64_t seed, uint32_t* const* counts, uint64_t* total) {
   if (n_det <= 0 || n_slices < 0 || !counts) return -1;
   for (int d = 0; d < n_det; ++d) memset(counts[d], 0, sizeof(uint32_t) * (size_t)H[d] * W[d]);
+  for (int i = 0; i < n_slices; ++i)
+    if (s[i].detector < 0 || s[i].detector >= n_det || s[i].n_lambda < 1 || s[i].n_slit < 1) return -1;
+  (void)n_coeffs;
   uint64_t tot = 0;
+  /* slices in parallel; integer counts, so the result does not depend on the threads */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : tot)
+#endif
   for (int i = 0; i < n_slices; ++i) {
     const oracle_slice* S = &s[i];
-    if (S->detector < 0 || S->detector >= n_det || S->n_lambda < 1 || S->n_slit < 1) return -1;
-    (void)n_coeffs;
     const int h = H[S->detector], w = W[S->detector];
     uint32_t* frame = counts[S->detector];
     const double dl = (S->lambda_hi - S->lambda_lo) / S->n_lambda;
@@ -94,8 +102,12 @@ int oracle_render_photons(int n_det, const int* H, const int* W, int n_slices, c
           y = yc + beta * dx + sc * z2;
         }
         const double fx = floor(x + 0.5), fy = floor(y + 0.5);
-        if (fx >= 0.0 && fx < (double)w && fy >= 0.0 && fy < (double)h)
+        if (fx >= 0.0 && fx < (double)w && fy >= 0.0 && fy < (double)h) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
           frame[(int64_t)fy * w + (int64_t)fx] += 1u;
+        }
       }
     }
   }

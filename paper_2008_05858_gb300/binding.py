@@ -141,6 +141,8 @@ _SIGS = {
                             C.c_void_p, C.c_void_p], C.c_int),
     "e2e_update_model": ([C.c_void_p, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double),
                           C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
+    "e2e_render_photons": ([C.c_void_p, C.c_uint64, C.c_int32, C.POINTER(C.c_uint64), C.c_uint64,
+                            C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.POINTER(C.c_uint64), C.c_void_p], C.c_int),
     "e2e_add_noise": ([C.c_void_p, C.c_uint64, C.POINTER(e2e_noise_params), C.c_int32, C.POINTER(C.c_void_p),
                        C.POINTER(C.c_int64), C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.c_void_p],
                       C.c_int),
@@ -332,6 +334,22 @@ def e2e_update_model(ctx: int, model_id: int, cx: np.ndarray, cy: np.ndarray, sx
     _check(load_library().e2e_update_model(C.c_void_p(ctx), model_id, *[a.ctypes.data_as(dp) for a in arrs]))
 
 
+# -------------------------------------------------------------------- photon Monte-Carlo
+
+
+def e2e_render_photons(ctx: int, model_id: int, spec_ids: Sequence[int], seed: int, dst_ptrs: Sequence[int],
+                       pitch_elems: Optional[Sequence[int]] = None, want_total: bool = True, stream=None):
+    n = len(spec_ids)
+    sids = (C.c_uint64 * max(n, 1))(*spec_ids)
+    nd = len(dst_ptrs)
+    pit = None if pitch_elems is None else (C.c_int64 * nd)(*pitch_elems)
+    tot = C.c_uint64()
+    _check(load_library().e2e_render_photons(C.c_void_p(ctx), model_id, n, sids, seed, (C.c_void_p * nd)(*dst_ptrs),
+                                             pit, C.byref(tot) if want_total else None,
+                                             C.c_void_p(_stream_handle(stream))))
+    return tot.value if want_total else None
+
+
 # -------------------------------------------------------------------- detector noise
 
 
@@ -475,6 +493,19 @@ class Renderer:
 
         td = torch.float32 if dtype == "f32" else torch.float64
         return [torch.empty((h, w), dtype=td, device=f"cuda:{self.device}") for h, w in self.models[mid].det_shape]
+
+    # -------------------------------------------------------------- photon Monte-Carlo
+    def render_photons(self, mid: int, spec_ids: Sequence[int], seed: int, out=None, stream=None,
+                       want_total: bool = True):
+        """Photon-by-photon frames (int32 tensors holding the uint32 counts) and the photon total."""
+        import torch
+
+        if out is None:
+            out = [torch.empty((h, w), dtype=torch.int32, device=f"cuda:{self.device}")
+                   for h, w in self.models[mid].det_shape]
+        total = e2e_render_photons(self.ctx, mid, spec_ids, seed, [int(t.data_ptr()) for t in out],
+                                   [int(t.stride(0)) for t in out], want_total, stream)
+        return out, total
 
     # -------------------------------------------------------------- detector noise
     def add_noise(self, mid: int, frames, dtype: str = "f32", out=None, stream=None, *, seed: int,

@@ -76,6 +76,11 @@ struct Model {
   int coef_total = 0;
   DevSlice* d_slices = nullptr;
   double* d_u = nullptr;
+  double* d_ucum = nullptr;     // running sums of the slit weights (photon renderer)
+  double* d_usum = nullptr;     // their totals, per slice
+  int64_t* d_bin_off = nullptr; // first wavelength bin of each slice (photon renderer)
+  int64_t n_bins = 0;
+  bool u_nonneg = true;
   int* d_dims = nullptr;  // [det][2] = (H, W)
   int64_t max_stamps = 0;
   std::vector<int> Ks;    // distinct K values
@@ -262,6 +267,9 @@ void free_plan(Plan& p) {
 void free_model(Model* m) {
   cudaFree(m->d_slices);
   cudaFree(m->d_u);
+  cudaFree(m->d_ucum);
+  cudaFree(m->d_usum);
+  cudaFree(m->d_bin_off);
   cudaFree(m->d_dims);
   free_plan(m->plan);
 }
@@ -804,8 +812,28 @@ int e2e_load_model(e2e_ctx* ctx, const e2e_model_desc* desc, uint64_t* model_id)
   }
   m->dev = ds;
   m->coef_total = coef_total;
+  // running sums of the slit weights, each slice summed in order (the photon renderer's slit
+  // choice), and the wavelength-bin offsets of the slices
+  std::vector<double> ucum(u_all.size()), usum(m->slices.size());
+  std::vector<int64_t> bin_off(m->slices.size() + 1, 0);
+  for (size_t i = 0; i < m->slices.size(); ++i) {
+    const DevSlice& v = ds[i];
+    double acc = 0.0;
+    for (int k = 0; k < v.n_slit; ++k) {
+      const double uk = u_all[v.u_off + k];
+      m->u_nonneg = m->u_nonneg && uk >= 0.0;
+      acc = k == 0 ? uk : acc + uk;
+      ucum[v.u_off + k] = acc;
+    }
+    usum[i] = acc;
+    bin_off[i + 1] = bin_off[i] + v.n_lambda;
+  }
+  m->n_bins = bin_off.back();
   int rc = upload(&m->d_slices, ds.data(), ds.size());
   if (rc == E2E_OK) rc = upload(&m->d_u, u_all.data(), u_all.size());
+  if (rc == E2E_OK) rc = upload(&m->d_ucum, ucum.data(), ucum.size());
+  if (rc == E2E_OK) rc = upload(&m->d_usum, usum.data(), usum.size());
+  if (rc == E2E_OK) rc = upload(&m->d_bin_off, bin_off.data(), bin_off.size());
   if (rc == E2E_OK) rc = upload(&m->d_dims, dims.data(), dims.size());
   if (rc == E2E_OK) rc = plan_model(m.get());
   if (rc != E2E_OK) {
@@ -1454,6 +1482,66 @@ int e2e_server_stop(e2e_ctx* ctx) {
   for (cudaStream_t st : S->slots) cudaStreamDestroy(st);
   for (cudaStream_t st : S->slots_hi) cudaStreamDestroy(st);
   ctx->server.reset();
+  return E2E_OK;
+}
+
+int e2e_render_photons(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids, uint64_t seed,
+                       uint32_t* const* dst, const int64_t* pitch_elems, uint64_t* total_photons, void* stream) {
+  if (!ctx || !dst) return fail(E2E_EINVAL, "null argument");
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Model* m = find_model(ctx, model_id);
+  if (!m) return fail(E2E_ENOTFOUND, "unknown model id");
+  if (!m->u_nonneg) return fail(E2E_EINVAL, "photon rendering needs slit weights >= 0");
+  std::vector<int64_t> pitch(m->n_det);
+  for (int d = 0; d < m->n_det; ++d) {
+    if (!dst[d]) return fail(E2E_EINVAL, "null destination frame");
+    pitch[d] = pitch_elems ? pitch_elems[d] : m->W[d];
+    if (pitch[d] < m->W[d]) return fail(E2E_EINVAL, "pitch smaller than width");
+  }
+  std::vector<const double*> table;
+  int rc = resolve_flux(ctx, m, n_spec, spec_ids, table);
+  if (rc != E2E_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (ctx->opts.kernel_timing) reset_timing(ctx);
+  for (int d = 0; d < m->n_det; ++d)
+    E2E_CK(cudaMemset2DAsync(dst[d], pitch[d] * 4, 0, (size_t)m->W[d] * 4, m->H[d], st));
+  if (m->slices.empty()) {
+    if (total_photons) *total_photons = 0;
+    return E2E_OK;
+  }
+  Scratch sc{{}, st};
+  const double** d_table = nullptr;
+  int64_t* d_pitch = nullptr;
+  uint32_t** d_dst = nullptr;
+  uint64_t *counts = nullptr, *offsets = nullptr, *scan = nullptr;
+  E2E_CK(sc.get((void**)&d_table, table.size() * sizeof(double*)));
+  E2E_CK(sc.get((void**)&d_pitch, pitch.size() * sizeof(int64_t)));
+  E2E_CK(sc.get((void**)&d_dst, m->n_det * sizeof(uint32_t*)));
+  E2E_CK(sc.get((void**)&counts, (size_t)m->n_bins * sizeof(uint64_t)));
+  E2E_CK(sc.get((void**)&offsets, (size_t)(m->n_bins + 1) * sizeof(uint64_t)));
+  E2E_CK(sc.get((void**)&scan, scan_scratch_elems(m->n_bins) * sizeof(uint64_t)));
+  E2E_CK(cudaMemcpyAsync(d_table, table.data(), table.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
+  E2E_CK(cudaMemcpyAsync(d_pitch, pitch.data(), pitch.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  E2E_CK(cudaMemcpyAsync(d_dst, dst, m->n_det * sizeof(uint32_t*), cudaMemcpyHostToDevice, st));
+  const int ns = (int)m->slices.size();
+  {
+    KernelTimer kt(ctx, st, "photon_bins");
+    E2E_CK(launch_photon_bins(m->d_slices, ns, d_table, m->d_usum, m->d_bin_off, m->n_bins, seed, counts, st));
+  }
+  {
+    KernelTimer kt(ctx, st, "photon_scan");
+    E2E_CK(launch_scan_exclusive(counts, offsets, m->n_bins, scan, st));
+  }
+  {
+    KernelTimer kt(ctx, st, "photons");
+    E2E_CK(launch_photons(m->d_slices, ns, m->d_ucum, m->d_usum, m->d_bin_off, offsets, m->psf, seed, d_dst, d_pitch,
+                          UINT64_MAX, st));
+  }
+  if (total_photons) {
+    E2E_CK(cudaMemcpyAsync(total_photons, offsets + m->n_bins, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    E2E_CK(cudaStreamSynchronize(st));
+  }
   return E2E_OK;
 }
 

@@ -41,6 +41,15 @@ cudaError_t launch_noise(uint64_t seed, uint64_t pattern_seed, double dark, doub
                          int64_t src_pitch, const double* R, int dst_dtype, void* dst, int64_t dst_pitch, int H, int W,
                          int det, cudaStream_t st);
 
+cudaError_t launch_photon_bins(const DevSlice* slices, int n_slices, const double* const* flux_tab, const double* usum,
+                               const int64_t* bin_off, int64_t n_bins, uint64_t seed, uint64_t* counts,
+                               cudaStream_t st);
+size_t scan_scratch_elems(int64_t n);
+cudaError_t launch_scan_exclusive(const uint64_t* in, uint64_t* out, int64_t n, uint64_t* scratch, cudaStream_t st);
+cudaError_t launch_photons(const DevSlice* slices, int n_slices, const double* ucum, const double* usum,
+                           const int64_t* bin_off, const uint64_t* offsets, int psf, uint64_t seed,
+                           uint32_t* const* dst, const int64_t* pitch, uint64_t max_photons, cudaStream_t st);
+
 size_t adjoint_smem_bytes(int max_area, int max_deg);
 cudaError_t launch_adjoint(int K, const DevSlice* slices, const double* const* flux_tab, const double* u_all,
                            const Item* items, int n_items, const void* const* dldi, const int64_t* pitch, int dtype,

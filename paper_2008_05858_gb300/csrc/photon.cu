@@ -1,0 +1,214 @@
+// Photon Monte-Carlo renderer: the alternative to the stamp method that Sec. 2.2 describes
+// (photons drawn from the input spectrum, traced with an assumed fiber illumination and an
+// analytic PSF to non-integer detector positions, and binned into pixels).
+//
+// For order-slice i and wavelength bin j (n bins, width dlam):
+//   N_ij ~ Poisson(flux[j] dlam U),  U = sum_k u_k            blocks (j, i, trial, 4)
+//   photon p < N_ij:  v, t from block (j, i, p, 5);  c from block (j, i, p, 6)
+//     slit point k = the first with c U <= u_0 + .. + u_k;  lt = (2 (j + v) - n) / n,
+//     s = (2 (k + t) - n_s) / n_s;  (x_c, y_c) = the spectral-format polynomials at (lt, s);
+//     (z1, z2) = Box-Muller of block (j, i, p, 7);
+//     separable PSF: (x, y) = (x_c + sigma_x z1, y_c + sigma_y z2); rotated PSF: the
+//     x-marginal and y | x of the rotated covariance, x = x_c + g_x z1,
+//     y = y_c + beta g_x z1 + s_c z2;
+//     counted in pixel (floor(x + 1/2), floor(y + 1/2)) if that is on the detector.
+//
+// Three kernels: the photon count of every bin (one thread per bin, the Poisson sampler of
+// philox.cuh), an exclusive scan of the counts, and one thread per photon, which finds its
+// bin by binary search in the scan, so that every photon is a pure function of
+// (seed, bin, slice, index) whatever the launch shape.  The pixel decisions are taken in FP64;
+// counts are added with 32-bit integer atomics (exact, order-independent).
+#include <cstdint>
+
+#include "e2e_device.cuh"
+#include "e2e_kernels.h"
+#include "philox.cuh"
+
+namespace e2e {
+
+__global__ void __launch_bounds__(256) k_photon_bins(const DevSlice* __restrict__ slices, int n_slices,
+                                                     const double* const* __restrict__ flux_tab,
+                                                     const double* __restrict__ usum, const int64_t* __restrict__ bin_off,
+                                                     uint64_t seed, uint64_t* __restrict__ counts) {
+  const int64_t nb = bin_off[n_slices];
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = n_slices - 1;
+    while (lo < hi) {  // slice owning bin b
+      const int mid = (lo + hi + 1) >> 1;
+      if (bin_off[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    const DevSlice& S = slices[lo];
+    const int j = (int)(b - bin_off[lo]);
+    const double lam = __dmul_rn(__dmul_rn(flux_tab[S.flux_slot][j], S.dlam), usum[lo]);
+    counts[b] = (uint64_t)poisson_filtered(lam, seed, (uint32_t)j, (uint32_t)S.index, 4);
+  }
+}
+
+// ---------------------------------------------------------------- exclusive scan (uint64)
+
+constexpr int kScanThreads = 1024;
+
+__device__ __forceinline__ uint64_t block_inclusive_scan(uint64_t v, uint64_t* s_warp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) s_warp[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    s_warp[lane] = w;
+  }
+  __syncthreads();
+  return v + (warp > 0 ? s_warp[warp - 1] : 0);
+}
+
+// Per-block exclusive scan of in[] into out[], block totals into sums[].
+__global__ void __launch_bounds__(kScanThreads) k_scan_local(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                                                             int64_t n, uint64_t* __restrict__ sums) {
+  __shared__ uint64_t s_warp[32];
+  const int64_t i = (int64_t)blockIdx.x * kScanThreads + threadIdx.x;
+  const uint64_t v = i < n ? in[i] : 0;
+  const uint64_t inc = block_inclusive_scan(v, s_warp);
+  if (i < n) out[i] = inc - v;
+  if (threadIdx.x == kScanThreads - 1) sums[blockIdx.x] = inc;
+}
+
+// One block: exclusive scan of the block totals in place; total into *total.
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(uint64_t* __restrict__ sums, int64_t nblocks,
+                                                            uint64_t* __restrict__ total) {
+  __shared__ uint64_t s_warp[32];
+  __shared__ uint64_t s_carry;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nblocks; base += kScanThreads) {
+    const int64_t i = base + threadIdx.x;
+    const uint64_t v = i < nblocks ? sums[i] : 0;
+    const uint64_t inc = block_inclusive_scan(v, s_warp);
+    const uint64_t carry = s_carry;
+    if (i < nblocks) sums[i] = carry + inc - v;
+    __syncthreads();
+    if (threadIdx.x == kScanThreads - 1) s_carry = carry + inc;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = s_carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_add(uint64_t* __restrict__ out, int64_t n,
+                                                           const uint64_t* __restrict__ sums,
+                                                           const uint64_t* __restrict__ total) {
+  const int64_t i = (int64_t)blockIdx.x * kScanThreads + threadIdx.x;
+  if (i < n) out[i] += sums[blockIdx.x];
+  if (i == n) out[n] = *total;
+}
+
+// ---------------------------------------------------------------- photons
+
+__global__ void __launch_bounds__(256) k_photons(const DevSlice* __restrict__ slices, int n_slices,
+                                                 const double* __restrict__ ucum, const double* __restrict__ usum,
+                                                 const int64_t* __restrict__ bin_off,
+                                                 const uint64_t* __restrict__ offsets, int psf, uint64_t seed,
+                                                 uint32_t* const* __restrict__ dst, const int64_t* __restrict__ pitch) {
+  const int64_t nb = bin_off[n_slices];
+  const uint64_t total = offsets[nb];
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    int64_t lo = 0, hi = nb - 1;
+    while (lo < hi) {  // bin holding photon p: the last b with offsets[b] <= p
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if (offsets[mid] <= p) lo = mid; else hi = mid - 1;
+    }
+    const int64_t b = lo;
+    int sl = 0, sh = n_slices - 1;
+    while (sl < sh) {
+      const int mid = (sl + sh + 1) >> 1;
+      if (bin_off[mid] <= b) sl = mid; else sh = mid - 1;
+    }
+    const DevSlice& S = slices[sl];
+    const uint32_t j = (uint32_t)(b - bin_off[sl]);
+    const uint32_t pp = (uint32_t)(p - offsets[b]);
+    const uint32_t si = (uint32_t)S.index;
+    const uint4 wa = rng_block(seed, j, si, pp, 5), wb = rng_block(seed, j, si, pp, 6);
+    const double v = uni53(wa.x, wa.y), t = uni53(wa.z, wa.w);
+    const double cu = __dmul_rn(uni53(wb.x, wb.y), usum[sl]);
+    // slit point: the first k with cu <= C_k (C nondecreasing), else the last
+    const double* C = ucum + S.u_off;
+    int k0 = 0, k1 = S.n_slit - 1;
+    while (k0 < k1) {
+      const int mid = (k0 + k1) >> 1;
+      if (cu <= C[mid]) k1 = mid; else k0 = mid + 1;
+    }
+    const double n = (double)S.n_lambda, ns = (double)S.n_slit;
+    const double lt = __ddiv_rn(__dadd_rn(__dmul_rn(2.0, __dadd_rn((double)j, v)), -n), n);
+    const double s = __ddiv_rn(__dadd_rn(__dmul_rn(2.0, __dadd_rn((double)k0, t)), -ns), ns);
+    double px[9], py[9];
+#pragma unroll
+    for (int bb = 0; bb <= 8; ++bb) {
+      px[bb] = bb <= S.degree ? poly_lt_for_b(S.cx, S.degree, bb, lt) : 0.0;
+      py[bb] = bb <= S.degree ? poly_lt_for_b(S.cy, S.degree, bb, lt) : 0.0;
+    }
+    const double xc = horner_s(px, S.degree, s), yc = horner_s(py, S.degree, s);
+    const double sa = fma(fma(S.sx[2], lt, S.sx[1]), lt, S.sx[0]);
+    const double sb = fma(fma(S.sy[2], lt, S.sy[1]), lt, S.sy[0]);
+    double z1, z2;
+    normal_pair_ctr(seed, j, si, pp, 7, z1, z2);
+    double x, y;
+    if (psf == 0) {
+      x = __dadd_rn(xc, __dmul_rn(sa, z1));
+      y = __dadd_rn(yc, __dmul_rn(sb, z2));
+    } else {
+      const double a2 = sa * sa, b2 = sb * sb, c = S.cos_t, sn = S.sin_t;
+      const double vx = a2 * c * c + b2 * sn * sn, vy = a2 * sn * sn + b2 * c * c, cxy = (a2 - b2) * sn * c;
+      const double gx = sqrt(vx), beta = cxy / vx, sc = sqrt(vy - beta * cxy);
+      const double dx = __dmul_rn(gx, z1);
+      x = __dadd_rn(xc, dx);
+      y = __dadd_rn(__dadd_rn(yc, __dmul_rn(beta, dx)), __dmul_rn(sc, z2));
+    }
+    const double fx = floor(__dadd_rn(x, 0.5)), fy = floor(__dadd_rn(y, 0.5));
+    if (fx >= 0.0 && fx < (double)S.W && fy >= 0.0 && fy < (double)S.H)
+      atomicAdd(dst[S.det] + (int64_t)fy * pitch[S.det] + (int64_t)fx, 1u);
+  }
+}
+
+static unsigned grid_for(uint64_t n, int threads, uint64_t cap) {
+  const uint64_t b = n / threads + (n % threads ? 1 : 0);  // no overflow for any n
+  return (unsigned)(b == 0 ? 1 : (b > cap ? cap : b));
+}
+
+cudaError_t launch_photon_bins(const DevSlice* slices, int n_slices, const double* const* flux_tab, const double* usum,
+                               const int64_t* bin_off, int64_t n_bins, uint64_t seed, uint64_t* counts,
+                               cudaStream_t st) {
+  if (n_bins == 0) return cudaSuccess;
+  k_photon_bins<<<grid_for((uint64_t)n_bins, 256, 152 * 64), 256, 0, st>>>(slices, n_slices, flux_tab, usum, bin_off,
+                                                                         seed, counts);
+  return cudaGetLastError();
+}
+
+size_t scan_scratch_elems(int64_t n) { return (size_t)((n + kScanThreads - 1) / kScanThreads) + 1; }
+
+cudaError_t launch_scan_exclusive(const uint64_t* in, uint64_t* out, int64_t n, uint64_t* scratch, cudaStream_t st) {
+  const int64_t nblocks = (n + kScanThreads - 1) / kScanThreads;
+  uint64_t* total = scratch + nblocks;
+  if (nblocks > 0) k_scan_local<<<(unsigned)nblocks, kScanThreads, 0, st>>>(in, out, n, scratch);
+  k_scan_sums<<<1, kScanThreads, 0, st>>>(scratch, nblocks, total);
+  k_scan_add<<<(unsigned)(n / kScanThreads + 1), kScanThreads, 0, st>>>(out, n, scratch, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_photons(const DevSlice* slices, int n_slices, const double* ucum, const double* usum,
+                           const int64_t* bin_off, const uint64_t* offsets, int psf, uint64_t seed,
+                           uint32_t* const* dst, const int64_t* pitch, uint64_t max_photons, cudaStream_t st) {
+  if (max_photons == 0) return cudaSuccess;
+  k_photons<<<grid_for(max_photons, 256, 152 * 32), 256, 0, st>>>(slices, n_slices, ucum, usum, bin_off, offsets, psf,
+                                                                   seed, dst, pitch);
+  return cudaGetLastError();
+}
+
+}  // namespace e2e
