@@ -51,7 +51,7 @@ extern "C" {
 #define E2E_EDEVICE -9   /* debug checks: a kernel found a deposit its plan did not foresee */
 
 /* ------------------------------------------------------------------ enums */
-enum { E2E_PSF_SEPARABLE = 0, E2E_PSF_ELLIPTICAL = 1 };
+enum { E2E_PSF_SEPARABLE = 0, E2E_PSF_ELLIPTICAL = 1, E2E_PSF_TABLE = 2 };
 /* E2E_PREC_MIXED: FP64 mapping, FP32 PSF stamps in on-chip tiles, FP64 tile accumulation,
  *                 compensated merge (the fast path).
  * E2E_PREC_FP64:  everything in FP64, one thread per stamp, FP64 global atomics (baseline). */
@@ -98,6 +98,23 @@ typedef struct {
                           [1.2, 2.0] px): the renderers expand the conditional profile of
                           y given x in eps * tau over one pixel column */
   const double* slit_weights; /* n_slit weights u_k (finite, >= 0) */
+  double blaze_order;  /* echelle blaze of the order (the paper computes each order's blaze
+                          profile analytically, Sec. 4.2): every sample's weight is multiplied by
+                          B(lambda) = sinc^2(nu), nu = blaze_order * (1 - blaze_lambda / lambda),
+                          sinc(x) = sin(pi x) / (pi x), at the sample's wavelength; 0 = no blaze */
+  double blaze_lambda; /* blaze wavelength of the order (> 0 when blaze_order != 0) */
+  /* E2E_PSF_TABLE: the PSF as tabulated maps (Sec. 2.1: the spectrograph unit delivers PSF
+   * maps per projected fiber image; here sampled densities at field points along the order).
+   * Map f samples the PSF density at offsets ((u - c)/q, (v - c)/q) px from the PSF centre,
+   * c = (map_size - 1)/2, q = map_oversample; between samples the density is their bilinear
+   * interpolant (zero beyond the grid).  A stamp's pixel values are the pixel integrals of
+   * that density, tabulated at load time for (psf_phases + 1)^2 sub-pixel centre phases, then
+   * interpolated bilinearly in the stamp's phase and linearly in lt between field nodes. */
+  int32_t n_field;          /* field nodes (>= 1) */
+  const double* field_lt;   /* their normalised wavelengths, strictly increasing, in [-1, 1] */
+  int32_t map_size;         /* M >= 2: each map is M x M samples, row v, column u */
+  double map_oversample;    /* q > 0: samples per pixel */
+  const double* maps;       /* n_field * M * M densities, finite, >= 0, each map's sum > 0 */
 } e2e_order_slice;
 
 typedef struct {
@@ -106,7 +123,8 @@ typedef struct {
   const int32_t* width;  /* columns per detector (x) */
   int32_t n_slices;
   const e2e_order_slice* slices;
-  int32_t psf;           /* E2E_PSF_SEPARABLE or E2E_PSF_ELLIPTICAL */
+  int32_t psf;           /* E2E_PSF_SEPARABLE, E2E_PSF_ELLIPTICAL or E2E_PSF_TABLE */
+  int32_t psf_phases;    /* E2E_PSF_TABLE: sub-pixel phases per axis of the tables, 1..64 (0 = 8) */
 } e2e_model_desc;
 
 /* ------------------------------------------------------------------ context */

@@ -35,6 +35,7 @@ _lib = None
 
 PSF_SEPARABLE = 0
 PSF_ELLIPTICAL = 1
+PSF_TABLE = 2
 
 
 class OracleNoise(C.Structure):
@@ -61,6 +62,14 @@ class OracleSlice(C.Structure):
         ("theta", C.c_double),
         ("u", C.POINTER(C.c_double)),
         ("flux", C.POINTER(C.c_double)),
+        ("blaze_order", C.c_double),
+        ("blaze_lambda", C.c_double),
+        ("n_field", C.c_int),
+        ("field_lt", C.POINTER(C.c_double)),
+        ("map_size", C.c_int),
+        ("map_oversample", C.c_double),
+        ("maps", C.POINTER(C.c_double)),
+        ("phases", C.c_int),
     ]
 
 
@@ -108,6 +117,8 @@ def lib():
             L.oracle_vjp.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int,
                                      C.POINTER(OracleSlice), C.POINTER(dp), dp, dp, dp, dp, C.c_int]
             L.oracle_vjp.restype = C.c_int
+            L.oracle_epsf_pixel.argtypes = [C.POINTER(OracleSlice), C.c_int, C.c_double, C.c_double, C.c_int, C.c_int]
+            L.oracle_epsf_pixel.restype = C.c_double
             u32p = C.POINTER(C.c_uint32)
             L.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
             L.oracle_philox4x32_10.restype = None
@@ -153,6 +164,16 @@ class _Marshalled:
                 o.sx[p] = float(s.sigma_x[p])
                 o.sy[p] = float(s.sigma_y[p])
             o.theta = float(s.theta)
+            o.blaze_order = float(getattr(s, "blaze_order", 0.0))
+            o.blaze_lambda = float(getattr(s, "blaze_lambda", 0.0))
+            psf_map = getattr(s, "psf_map", None)
+            if psf_map is not None:
+                lt = np.ascontiguousarray(psf_map.field_lt, dtype=np.float64)
+                mp = np.ascontiguousarray(psf_map.maps, dtype=np.float64)
+                self.keep += [lt, mp]
+                o.n_field, o.field_lt = len(lt), _dptr(lt)
+                o.map_size, o.map_oversample, o.maps = mp.shape[-1], float(psf_map.oversample), _dptr(mp)
+                o.phases = int(psf_map.phases)
         self.n = n
 
 
@@ -316,3 +337,15 @@ def add_noise(S: np.ndarray, det: int, *, seed: int, pattern_seed: int, dark: fl
     if rc != 0:
         raise ValueError("oracle_add_noise: invalid argument")
     return E, A, N
+
+
+def epsf_pixel(s, f: int, phx: float, phy: float, m: int, n: int) -> float:
+    """Effective-PSF value of window pixel (m, n) of slice s's map f at phase (phx, phy)."""
+    mm = _Marshalled(W_OpticalModel_one(s), lambda _s: np.zeros(_s.n_lambda))
+    return float(lib().oracle_epsf_pixel(C.byref(mm.arr[0]), f, phx, phy, m, n))
+
+
+def W_OpticalModel_one(s):
+    class _M:
+        slices = [s]
+    return _M

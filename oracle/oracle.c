@@ -147,6 +147,17 @@ double oracle_bvn_rect(double h0, double h1, double k0, double k1, double rho) {
 
 /* ---------------------------------------------------------------- mapping */
 
+/* Blaze of the order at wavelength lam: the grating's single-groove diffraction envelope in the
+ * order's phase variable nu = m (1 - lambda_b / lam), sinc^2(nu) with sinc(x) = sin(pi x)/(pi x)
+ * (the paper weights each order by its blaze profile, computed analytically, Sec. 4.2). */
+double oracle_blaze(const oracle_slice* s, double lam) {
+  if (s->blaze_order == 0.0) return 1.0;
+  const double nu = s->blaze_order * (1.0 - s->blaze_lambda / lam);
+  if (nu == 0.0) return 1.0;
+  const double sc = sin(ORACLE_PI * nu) / (ORACLE_PI * nu);
+  return sc * sc;
+}
+
 /* Sample j of n_lambda sits at the centre of the j-th equal bin of [lambda_lo, lambda_hi]
  * (the wavelength grid of Sec. 2); the polynomial variable is that wavelength normalised
  * to [-1, 1].  Slit point k of n_slit sits at the centre of the k-th equal bin of [-1, 1].
@@ -162,7 +173,7 @@ void oracle_map(const oracle_slice* s, int j, int k, double* x_c, double* y_c, d
   *y_c = poly2(s->cy, s->degree, lt, sk);
   *sig_x = quad(s->sx, lt);
   *sig_y = quad(s->sy, lt);
-  *weight = s->flux[j] * dl * s->u[k];
+  *weight = s->flux[j] * dl * s->u[k] * oracle_blaze(s, lam);
 }
 
 /* Window rule: the K x K window is centred on the pixel containing the mapped point;
@@ -177,6 +188,94 @@ static void ellipse_cov(double sa, double sb, double theta, double* vx, double* 
   *cxy = (sa * sa - sb * sb) * s * c;
 }
 
+/* ---------------------------------------------------------------- tabulated PSF */
+
+/* Integral of the unit tent max(0, 1 - |t|) from -inf to t. */
+static double tent_cdf(double t) {
+  if (t <= -1.0) return 0.0;
+  if (t <= 0.0) return 0.5 * (1.0 + t) * (1.0 + t);
+  if (t <= 1.0) return 1.0 - 0.5 * (1.0 - t) * (1.0 - t);
+  return 1.0;
+}
+
+/* Integral over [a, b) (px, PSF-relative) of the tent of map sample u: the bilinear density is
+ * sum_uv S_uv tent(q x - (u - c)) tent(q y - (v - c)), so a pixel integral factorises into
+ * x-weights of the columns times y-weights of the rows. */
+static double tent_weight(double a, double b, int u, double c, double q) {
+  const double xu = (u - c) / q;
+  return (tent_cdf(q * (b - xu)) - tent_cdf(q * (a - xu))) / q;
+}
+
+double oracle_epsf_pixel(const oracle_slice* s, int f, double phx, double phy, int m, int n) {
+  const int M = s->map_size, H = s->K / 2;
+  const double q = s->map_oversample, c = 0.5 * (M - 1);
+  const double* S = s->maps + (size_t)f * M * M;
+  double norm = 0.0;
+  for (int i = 0; i < M * M; ++i) norm += S[i];
+  norm /= q * q;  /* integral of the bilinear density */
+  const double ax = m - H - 0.5 - phx, bx = ax + 1.0, ay = n - H - 0.5 - phy, by = ay + 1.0;
+  double sum = 0.0;
+  for (int v = 0; v < M; ++v) {
+    const double wy = tent_weight(ay, by, v, c, q);
+    if (wy == 0.0) continue;
+    for (int u = 0; u < M; ++u) sum += S[(size_t)v * M + u] * tent_weight(ax, bx, u, c, q) * wy;
+  }
+  return sum / norm;
+}
+
+/* Effective-PSF tables of one slice: T[f][py][px][n][m] for phases -1/2 + p/P, p = 0..P. */
+static double* epsf_tables(const oracle_slice* s) {
+  const int K = s->K, P = s->phases, F = s->n_field;
+  double* T = (double*)malloc(sizeof(double) * (size_t)F * (P + 1) * (P + 1) * K * K);
+  for (int f = 0; f < F; ++f)
+    for (int py = 0; py <= P; ++py)
+      for (int px = 0; px <= P; ++px)
+        for (int n = 0; n < K; ++n)
+          for (int m = 0; m < K; ++m)
+            T[((((size_t)f * (P + 1) + py) * (P + 1) + px) * K + n) * K + m] =
+                oracle_epsf_pixel(s, f, -0.5 + (double)px / P, -0.5 + (double)py / P, m, n);
+  return T;
+}
+
+/* Stamp of a tabulated PSF: the tables bilinearly interpolated in the centre's sub-pixel phase
+ * and linearly in lt between the two field nodes around it (the end node beyond the ends). */
+static void table_stamp(const oracle_slice* s, const double* T, double lt, double fx, double fy, double w,
+                        double* out) {
+  const int K = s->K, P = s->phases, F = s->n_field;
+  int f0 = 0, f1 = 0;
+  double wf = 0.0;
+  if (lt <= s->field_lt[0]) {
+    f0 = f1 = 0;
+  } else if (lt >= s->field_lt[F - 1]) {
+    f0 = f1 = F - 1;
+  } else {
+    while (f0 + 1 < F && s->field_lt[f0 + 1] <= lt) ++f0;
+    f1 = f0 + 1 < F ? f0 + 1 : f0;
+    if (f1 != f0) wf = (lt - s->field_lt[f0]) / (s->field_lt[f1] - s->field_lt[f0]);
+  }
+  double rx = (fx + 0.5) * P, ry = (fy + 0.5) * P;
+  int px = (int)floor(rx), py = (int)floor(ry);
+  if (px > P - 1) px = P - 1;
+  if (py > P - 1) py = P - 1;
+  if (px < 0) px = 0;
+  if (py < 0) py = 0;
+  const double ax = rx - px, ay = ry - py;
+  for (int n = 0; n < K; ++n)
+    for (int m = 0; m < K; ++m) {
+      double v = 0.0;
+      for (int e = 0; e < 2; ++e) {
+        const int f = e ? f1 : f0;
+        const double we = e ? wf : 1.0 - wf;
+        if (we == 0.0) continue;
+#define TT(Y, X) T[((((size_t)f * (P + 1) + (Y)) * (P + 1) + (X)) * K + n) * K + m]
+        v += we * ((1.0 - ay) * ((1.0 - ax) * TT(py, px) + ax * TT(py, px + 1)) +
+                   ay * ((1.0 - ax) * TT(py + 1, px) + ax * TT(py + 1, px + 1)));
+#undef TT
+      }
+      out[n * K + m] = w * v;
+    }
+}
+
 void oracle_stamp(const oracle_slice* s, int psf, int j, int k, double* out, int* i0p, int* r0p) {
   double xc, yc, sx, sy, w;
   oracle_map(s, j, k, &xc, &yc, &sx, &sy, &w);
@@ -184,7 +283,14 @@ void oracle_stamp(const oracle_slice* s, int psf, int j, int k, double* out, int
   int i0 = window_origin(xc, K), r0 = window_origin(yc, K);
   *i0p = i0;
   *r0p = r0;
-  if (psf == ORACLE_PSF_SEPARABLE) {
+  if (psf == ORACLE_PSF_TABLE) {
+    double* T = epsf_tables(s);
+    const double dl = (s->lambda_hi - s->lambda_lo) / s->n_lambda;
+    const double lam = s->lambda_lo + (j + 0.5) * dl;
+    const double lt = 2.0 * (lam - s->lambda_lo) / (s->lambda_hi - s->lambda_lo) - 1.0;
+    table_stamp(s, T, lt, xc - (i0 + K / 2), yc - (r0 + K / 2), w, out);
+    free(T);
+  } else if (psf == ORACLE_PSF_SEPARABLE) {
     for (int n = 0; n < K; ++n) {
       double ay = oracle_normal_interval((r0 + n - 0.5 - yc) / sy, (r0 + n + 0.5 - yc) / sy);
       for (int m = 0; m < K; ++m) {
@@ -258,10 +364,22 @@ static void render_slice(const oracle_slice* s, int psf, int H, int W, band_t* b
   band->h = ymax - ymin + 1;
   band->buf = (double*)calloc((size_t)band->w * band->h, sizeof(double));
   double* st = (double*)malloc(sizeof(double) * K * K);
+  double* T = psf == ORACLE_PSF_TABLE ? epsf_tables(s) : NULL;  /* once per slice */
+  const double dl = (s->lambda_hi - s->lambda_lo) / s->n_lambda;
   for (int j = 0; j < s->n_lambda; ++j)
     for (int k = 0; k < s->n_slit; ++k) {
       int i0, r0;
-      oracle_stamp(s, psf, j, k, st, &i0, &r0);
+      if (T) {
+        double xc, yc, sx, sy, w;
+        oracle_map(s, j, k, &xc, &yc, &sx, &sy, &w);
+        i0 = window_origin(xc, K);
+        r0 = window_origin(yc, K);
+        const double lam = s->lambda_lo + (j + 0.5) * dl;
+        const double lt = 2.0 * (lam - s->lambda_lo) / (s->lambda_hi - s->lambda_lo) - 1.0;
+        table_stamp(s, T, lt, xc - (i0 + K / 2), yc - (r0 + K / 2), w, st);
+      } else {
+        oracle_stamp(s, psf, j, k, st, &i0, &r0);
+      }
       for (int n = 0; n < K; ++n) {
         int r = r0 + n;
         if (r < band->y0 || r >= band->y0 + band->h) continue; /* outside the frame: dropped */
@@ -273,6 +391,7 @@ static void render_slice(const oracle_slice* s, int psf, int H, int W, band_t* b
       }
     }
   free(st);
+  free(T);
 }
 
 int oracle_render(int n_det, const int* H, const int* W, int n_slices, const oracle_slice* s, int psf,

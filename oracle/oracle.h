@@ -22,7 +22,7 @@
 extern "C" {
 #endif
 
-enum { ORACLE_PSF_SEPARABLE = 0, ORACLE_PSF_ELLIPTICAL = 1 };
+enum { ORACLE_PSF_SEPARABLE = 0, ORACLE_PSF_ELLIPTICAL = 1, ORACLE_PSF_TABLE = 2 };
 
 typedef struct {
   int detector;
@@ -38,6 +38,20 @@ typedef struct {
   double theta;     /* rotation of the elliptical PSF axes, radians */
   const double* u;  /* n_slit slit weights */
   const double* flux; /* n_lambda flux samples (photons / Angstrom) at the bin centres */
+  double blaze_order;  /* blaze B(lambda) = sinc^2(m (1 - lambda_b / lambda)) weights every
+                          sample (0 = none); lambda_b = blaze_lambda */
+  double blaze_lambda;
+  /* ORACLE_PSF_TABLE: tabulated PSF maps at n_field wavelengths field_lt[f] (increasing, in
+   * [-1, 1]); map f is map_size^2 samples maps[f][v][u] of the PSF density at offsets
+   * ((u - c)/q, (v - c)/q) px from the PSF centre, c = (map_size - 1)/2, q = map_oversample;
+   * the density between samples is their bilinear interpolant (zero beyond the grid).
+   * phases: sub-pixel phases per axis of the effective-PSF tables. */
+  int n_field;
+  const double* field_lt;
+  int map_size;
+  double map_oversample;
+  const double* maps;
+  int phases;
 } oracle_slice;
 
 /* Render every order-slice into its detector frame.  frames[d] points to H[d]*W[d]
@@ -45,6 +59,14 @@ typedef struct {
  * Returns 0, or -1 on an invalid argument. */
 int oracle_render(int n_det, const int* H, const int* W, int n_slices, const oracle_slice* s,
                   int psf, double** frames, int n_threads);
+
+/* Effective-PSF value (the pixel integral of map f's bilinear density, normalised to unit
+ * integral) of window pixel (m, n), relative to the window's centre pixel, for a PSF centred
+ * at sub-pixel offset (phx, phy) from that pixel's centre. */
+double oracle_epsf_pixel(const oracle_slice* s, int f, double phx, double phy, int m, int n);
+
+/* Blaze weight of the slice at wavelength lam (1 when it has none). */
+double oracle_blaze(const oracle_slice* s, double lam);
 
 /* Mapped position and PSF widths of stamp (j, k) of one order-slice. */
 void oracle_map(const oracle_slice* s, int j, int k, double* x_c, double* y_c, double* sig_x,

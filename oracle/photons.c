@@ -68,7 +68,9 @@ int oracle_render_photons(int n_det, const int* H, const int* W, int n_slices, c
     for (int k = 0; k < S->n_slit; ++k) U += S->u[k];
     const double c = cos(S->theta), sn = sin(S->theta);
     for (int j = 0; j < S->n_lambda; ++j) {
-      const long N = oracle_poisson_stream(S->flux[j] * dl * U, seed, (uint32_t)j, (uint32_t)i, 4);
+      const double lam_j = S->lambda_lo + (j + 0.5) * dl;  /* bin centre: the blaze weight */
+      const long N = oracle_poisson_stream(S->flux[j] * oracle_blaze(S, lam_j) * dl * U, seed, (uint32_t)j,
+                                           (uint32_t)i, 4);
       tot += (uint64_t)N;
       for (long p = 0; p < N; ++p) {
         uint32_t wa[4], wb[4];

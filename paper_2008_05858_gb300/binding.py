@@ -32,6 +32,7 @@ E2E_EDEVICE = -9
 
 E2E_PSF_SEPARABLE = 0
 E2E_PSF_ELLIPTICAL = 1
+E2E_PSF_TABLE = 2
 E2E_PREC_MIXED = 0
 E2E_PREC_FP64 = 1
 E2E_F32 = 0
@@ -60,7 +61,9 @@ class e2e_order_slice(C.Structure):
         ("lambda_lo", C.c_double), ("lambda_hi", C.c_double),
         ("cx", C.POINTER(C.c_double)), ("cy", C.POINTER(C.c_double)),
         ("sigma_x", C.c_double * 3), ("sigma_y", C.c_double * 3), ("theta", C.c_double),
-        ("slit_weights", C.POINTER(C.c_double)),
+        ("slit_weights", C.POINTER(C.c_double)), ("blaze_order", C.c_double), ("blaze_lambda", C.c_double),
+        ("n_field", C.c_int32), ("field_lt", C.POINTER(C.c_double)), ("map_size", C.c_int32),
+        ("map_oversample", C.c_double), ("maps", C.POINTER(C.c_double)),
     ]
 
 
@@ -68,6 +71,7 @@ class e2e_model_desc(C.Structure):
     _fields_ = [
         ("n_detectors", C.c_int32), ("height", C.POINTER(C.c_int32)), ("width", C.POINTER(C.c_int32)),
         ("n_slices", C.c_int32), ("slices", C.POINTER(e2e_order_slice)), ("psf", C.c_int32),
+        ("psf_phases", C.c_int32),
     ]
 
 
@@ -217,6 +221,7 @@ class _ModelDesc:
         n = len(model.slices)
         self.sl = (e2e_order_slice * max(n, 1))()
         dp = C.POINTER(C.c_double)
+        phases = 0
         for i, s in enumerate(model.slices):
             cx = np.ascontiguousarray(s.cx, dtype=np.float64)
             cy = np.ascontiguousarray(s.cy, dtype=np.float64)
@@ -231,10 +236,20 @@ class _ModelDesc:
                 o.sigma_x[p] = float(s.sigma_x[p])
                 o.sigma_y[p] = float(s.sigma_y[p])
             o.theta = float(s.theta)
+            o.blaze_order = float(getattr(s, "blaze_order", 0.0))
+            o.blaze_lambda = float(getattr(s, "blaze_lambda", 0.0))
+            pm = getattr(s, "psf_map", None)
+            if pm is not None:
+                lt = np.ascontiguousarray(pm.field_lt, dtype=np.float64)
+                mp = np.ascontiguousarray(pm.maps, dtype=np.float64)
+                self.keep += [lt, mp]
+                o.n_field, o.field_lt = len(lt), lt.ctypes.data_as(dp)
+                o.map_size, o.map_oversample, o.maps = mp.shape[-1], float(pm.oversample), mp.ctypes.data_as(dp)
+                phases = int(pm.phases)
         nd = len(model.det_shape)
         self.h = (C.c_int32 * nd)(*[h for h, w in model.det_shape])
         self.w = (C.c_int32 * nd)(*[w for h, w in model.det_shape])
-        self.desc = e2e_model_desc(nd, self.h, self.w, n, self.sl, int(model.psf))
+        self.desc = e2e_model_desc(nd, self.h, self.w, n, self.sl, int(model.psf), phases)
 
 
 def e2e_load_model(ctx: int, model: W.OpticalModel) -> int:

@@ -47,7 +47,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 struct SliceHost {
   e2e_order_slice d;
-  std::vector<double> cx, cy, u;
+  std::vector<double> cx, cy, u, field_lt, maps;
 };
 
 struct Plan {
@@ -78,9 +78,17 @@ struct Model {
   double* d_u = nullptr;
   double* d_ucum = nullptr;     // running sums of the slit weights (photon renderer)
   double* d_usum = nullptr;     // their totals, per slice
-  int64_t* d_bin_off = nullptr; // first wavelength bin of each slice (photon renderer)
+  int64_t* d_bin_off = nullptr; // first wavelength bin of each slice (photon renderer, blaze)
+  std::vector<int64_t> bin_off;
   int64_t n_bins = 0;
   bool u_nonneg = true;
+  bool has_blaze = false;  // some slice weights its samples by a blaze function
+  // tabulated PSF: per-slice layout, field nodes, effective-PSF tables (FP64 and FP32)
+  int phases = 8;
+  TableSlice* d_ts = nullptr;
+  double* d_field = nullptr;
+  double* d_T64 = nullptr;
+  float* d_T32 = nullptr;
   int* d_dims = nullptr;  // [det][2] = (H, W)
   int64_t max_stamps = 0;
   std::vector<int> Ks;    // distinct K values
@@ -233,6 +241,25 @@ int validate_slice(const e2e_order_slice& s, int n_det, int psf, int idx) {
   if (!finite_all(s.sigma_x, 3) || !finite_all(s.sigma_y, 3)) return bad("non-finite PSF width coefficient");
   if (quad_min(s.sigma_x) <= 0 || quad_min(s.sigma_y) <= 0) return bad("PSF width must stay > 0 on [-1, 1]");
   if (!finite_all(s.slit_weights, s.n_slit)) return bad("non-finite slit weight");
+  if (!std::isfinite(s.blaze_order) || (s.blaze_order != 0.0 && !(s.blaze_lambda > 0.0 && std::isfinite(s.blaze_lambda))))
+    return bad("blaze: finite order and a positive, finite blaze wavelength required");
+  if (psf == E2E_PSF_TABLE) {
+    if (s.n_field < 1 || !s.field_lt || !s.maps) return bad("tabulated PSF needs n_field >= 1 and maps");
+    if (s.map_size < 2 || s.map_size > 4096) return bad("map_size must be 2..4096");
+    if (!(s.map_oversample > 0.0) || !std::isfinite(s.map_oversample)) return bad("map_oversample must be > 0");
+    for (int f = 0; f < s.n_field; ++f) {
+      if (!std::isfinite(s.field_lt[f]) || s.field_lt[f] < -1.0 || s.field_lt[f] > 1.0 ||
+          (f > 0 && !(s.field_lt[f] > s.field_lt[f - 1])))
+        return bad("field_lt must be strictly increasing in [-1, 1]");
+      double sum = 0.0;
+      const double* mp = s.maps + (size_t)f * s.map_size * s.map_size;
+      for (int i = 0; i < s.map_size * s.map_size; ++i) {
+        if (!std::isfinite(mp[i]) || mp[i] < 0.0) return bad("PSF map samples must be finite and >= 0");
+        sum += mp[i];
+      }
+      if (!(sum > 0.0)) return bad("every PSF map needs a positive sum");
+    }
+  }
   if (psf == E2E_PSF_ELLIPTICAL) {
     if (!std::isfinite(s.theta)) return bad("non-finite theta");
     // The elliptical renderers expand the conditional profile of y given x in eps * tau,
@@ -270,6 +297,10 @@ void free_model(Model* m) {
   cudaFree(m->d_ucum);
   cudaFree(m->d_usum);
   cudaFree(m->d_bin_off);
+  cudaFree(m->d_ts);
+  cudaFree(m->d_field);
+  cudaFree(m->d_T64);
+  cudaFree(m->d_T32);
   cudaFree(m->d_dims);
   free_plan(m->plan);
 }
@@ -299,10 +330,54 @@ double variant_cost(int K, int DX, int DY, int B) {
   return c;
 }
 
+// Effective-PSF tables of a tabulated-PSF model, built on the device at load time.
+int build_psf_tables(Model* m, int P) {
+  m->phases = P;
+  const int ns = (int)m->slices.size();
+  std::vector<TableSlice> ts(ns);
+  std::vector<double> field, maps;
+  int64_t tab = 0;
+  int max_field = 1;
+  for (int i = 0; i < ns; ++i) {
+    const e2e_order_slice& s = m->slices[i].d;
+    TableSlice& t = ts[i];
+    t.tab_off = tab;
+    t.map_off = (int64_t)maps.size();
+    t.field_off = (int32_t)field.size();
+    t.n_field = s.n_field;
+    t.map_size = s.map_size;
+    t.K = s.K;
+    t.q = s.map_oversample;
+    field.insert(field.end(), s.field_lt, s.field_lt + s.n_field);
+    maps.insert(maps.end(), s.maps, s.maps + (size_t)s.n_field * s.map_size * s.map_size);
+    tab += (int64_t)s.n_field * (P + 1) * (P + 1) * s.K * s.K;
+    max_field = std::max(max_field, s.n_field);
+  }
+  if ((int64_t)max_field * (P + 1) * (P + 1) > 65535) return fail(E2E_EINVAL, "too many field nodes x phases");
+  double* d_maps = nullptr;
+  double* d_norms = nullptr;
+  int rc = upload(&m->d_ts, ts.data(), ts.size());
+  if (rc == E2E_OK) rc = upload(&m->d_field, field.data(), field.size());
+  if (rc == E2E_OK) rc = upload(&d_maps, maps.data(), maps.size());
+  if (rc == E2E_OK && cudaMalloc((void**)&d_norms, std::max<size_t>(1, field.size()) * sizeof(double)) != cudaSuccess)
+    rc = fail(E2E_ENOMEM, "map norms");
+  if (rc == E2E_OK && (cudaMalloc((void**)&m->d_T64, std::max<int64_t>(1, tab) * sizeof(double)) != cudaSuccess ||
+                       cudaMalloc((void**)&m->d_T32, std::max<int64_t>(1, tab) * sizeof(float)) != cudaSuccess))
+    rc = fail(E2E_ENOMEM, "PSF tables");
+  if (rc == E2E_OK) {
+    cudaError_t e = launch_epsf_build(m->d_ts, ns, max_field, d_maps, d_norms, P, m->d_T64, m->d_T32, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) rc = cuda_fail(e, "PSF table build");
+  }
+  cudaFree(d_maps);
+  cudaFree(d_norms);
+  return rc;
+}
+
 int plan_model(Model* m) {
   Plan& P = m->plan;
   const int ns = (int)m->slices.size();
-  const bool ellip = m->psf == E2E_PSF_ELLIPTICAL;
+  const bool ellip = m->psf != E2E_PSF_SEPARABLE;  // item shape of the non-separable kernels
   if (ns == 0) {
     P.ok = true;
     return E2E_OK;
@@ -434,8 +509,9 @@ int plan_model(Model* m) {
       P.max_area = std::max(P.max_area, it.bw * it.bh);
       P.nk_max = std::max(P.nk_max, it.nk);
     }
-    P.smem = ellip ? ellip_smem_bytes(P.max_area, P.nk_max, P.max_deg + 1)
-                   : mixed_smem_bytes(P.max_area, P.JB, P.nk_max, P.B, P.max_deg + 1);
+    P.smem = m->psf == E2E_PSF_TABLE ? table_smem_bytes(P.max_area, P.nk_max, P.max_deg + 1)
+             : ellip ? ellip_smem_bytes(P.max_area, P.nk_max, P.max_deg + 1)
+                     : mixed_smem_bytes(P.max_area, P.JB, P.nk_max, P.B, P.max_deg + 1);
     if ((int)P.smem <= optin) break;
     if (jb_cap == 1)
       return fail(E2E_EINVAL, "trace footprint of a work item exceeds on-chip memory (area " +
@@ -553,6 +629,24 @@ int resolve_flux(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, s
   return E2E_OK;
 }
 
+// Blazed model: redirect the flux table to B(lambda_j) * flux[j], computed into `out`
+// (n_bins doubles) with `d_in` (n_slices pointers) as the upload of the original table.
+int blaze_into(Model* m, std::vector<const double*>& table, double* out, const double** d_in, cudaStream_t st) {
+  E2E_CK(cudaMemcpyAsync(d_in, table.data(), table.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
+  E2E_CK(launch_blaze(m->d_slices, (int)m->slices.size(), d_in, m->d_bin_off, m->n_bins, out, st));
+  for (size_t i = 0; i < table.size(); ++i) table[i] = out + m->bin_off[i];
+  return E2E_OK;
+}
+
+int blaze_scratch(Model* m, std::vector<const double*>& table, Scratch& sc, cudaStream_t st) {
+  if (!m->has_blaze || table.empty()) return E2E_OK;
+  double* out = nullptr;
+  const double** d_in = nullptr;
+  E2E_CK(sc.get((void**)&out, (size_t)m->n_bins * sizeof(double)));
+  E2E_CK(sc.get((void**)&d_in, table.size() * sizeof(double*)));
+  return blaze_into(m, table, out, d_in, st);
+}
+
 int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, int precision, int dtype,
                 void* const* dst, const int64_t* pitch_in, cudaStream_t st) {
   if (dtype != E2E_F32 && dtype != E2E_F64) return fail(E2E_EINVAL, "dtype must be E2E_F32 or E2E_F64");
@@ -568,9 +662,12 @@ int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, in
   int rc = resolve_flux(ctx, m, n_spec, spec_ids, table);
   if (rc != E2E_OK) return rc;
   const bool ellip = m->psf == E2E_PSF_ELLIPTICAL;
+  const bool tab = m->psf == E2E_PSF_TABLE;
 
   if (ctx->opts.kernel_timing) reset_timing(ctx);
   Scratch sc{{}, st};
+  rc = blaze_scratch(m, table, sc, st);
+  if (rc != E2E_OK) return rc;
   const double** d_table = nullptr;
   int64_t* d_pitch = nullptr;
   void** d_dst = nullptr;
@@ -604,8 +701,11 @@ int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, in
     E2E_CK(cudaMemcpyAsync(d_apitch, apitch.data(), apitch.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     for (int K : m->Ks) {
       // one launch per K over all slices; slices of another K exit at once
-      KernelTimer kt(ctx, st, ellip ? "render_fp64_ellip" : "render_fp64");
-      if (ellip)
+      KernelTimer kt(ctx, st, tab ? "render_fp64_table" : ellip ? "render_fp64_ellip" : "render_fp64");
+      if (tab)
+        E2E_CK(launch_render_fp64_table(K, (int)m->slices.size(), m->max_stamps, m->d_slices, m->d_ts, m->d_T64,
+                                        m->d_field, m->phases, d_table, m->d_u, d_acc, d_apitch, st));
+      else if (ellip)
         E2E_CK(launch_render_fp64_ellip(K, (int)m->slices.size(), m->max_stamps, m->d_slices, d_table, m->d_u,
                                         d_acc, d_apitch, st));
       else
@@ -627,8 +727,11 @@ int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, in
   E2E_CK(sc.get((void**)&store, (size_t)P.store_elems * sizeof(float2)));
   if (ctx->d_err) E2E_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
   for (auto& g : P.groups) {
-    KernelTimer kt(ctx, st, ellip ? "render_ellip" : "render_mixed");
-    if (ellip)
+    KernelTimer kt(ctx, st, tab ? "render_table" : ellip ? "render_ellip" : "render_mixed");
+    if (tab)
+      E2E_CK(launch_render_table(g.K, m->d_slices, m->d_ts, m->d_T32, m->d_field, m->phases, d_table, m->d_u,
+                                 P.d_items + g.first, g.count, store, P.nk_max, P.max_deg, P.smem, st, ctx->d_err));
+    else if (ellip)
       E2E_CK(launch_render_ellip(g.K, m->d_slices, d_table, m->d_u, P.d_items + g.first, g.count, store, P.nk_max,
                                  P.max_deg, P.smem, st, ctx->d_err));
     else
@@ -746,7 +849,10 @@ int e2e_load_model(e2e_ctx* ctx, const e2e_model_desc* desc, uint64_t* model_id)
   if (!ctx || !desc || !model_id) return fail(E2E_EINVAL, "null argument");
   if (desc->n_detectors < 1 || !desc->height || !desc->width) return fail(E2E_EINVAL, "need >= 1 detector");
   if (desc->n_slices < 0 || (desc->n_slices > 0 && !desc->slices)) return fail(E2E_EINVAL, "bad slice list");
-  if (desc->psf != E2E_PSF_SEPARABLE && desc->psf != E2E_PSF_ELLIPTICAL) return fail(E2E_EINVAL, "bad psf kind");
+  if (desc->psf != E2E_PSF_SEPARABLE && desc->psf != E2E_PSF_ELLIPTICAL && desc->psf != E2E_PSF_TABLE)
+    return fail(E2E_EINVAL, "bad psf kind");
+  const int phases = desc->psf_phases > 0 ? desc->psf_phases : 8;
+  if (desc->psf == E2E_PSF_TABLE && phases > 64) return fail(E2E_EINVAL, "psf_phases must be 1..64");
   for (int d = 0; d < desc->n_detectors; ++d)
     if (desc->height[d] < 1 || desc->width[d] < 1 || desc->height[d] > 16000 || desc->width[d] > 16000)
       return fail(E2E_EINVAL, "detector size must be 1..16000 px");
@@ -774,6 +880,16 @@ int e2e_load_model(e2e_ctx* ctx, const e2e_model_desc* desc, uint64_t* model_id)
     h.d.cx = h.cx.data();
     h.d.cy = h.cy.data();
     h.d.slit_weights = h.u.data();
+    if (desc->psf == E2E_PSF_TABLE) {
+      h.field_lt.assign(s.field_lt, s.field_lt + s.n_field);
+      h.maps.assign(s.maps, s.maps + (size_t)s.n_field * s.map_size * s.map_size);
+      h.d.field_lt = h.field_lt.data();
+      h.d.maps = h.maps.data();
+    } else {
+      h.d.field_lt = nullptr;
+      h.d.maps = nullptr;
+      h.d.n_field = 0;
+    }
     DevSlice& v = ds[i];
     memset(&v, 0, sizeof v);
     for (int c = 0; c < nc; ++c) {
@@ -787,6 +903,10 @@ int e2e_load_model(e2e_ctx* ctx, const e2e_model_desc* desc, uint64_t* model_id)
     v.dlam = (s.lambda_hi - s.lambda_lo) / s.n_lambda;
     v.cos_t = std::cos(s.theta);
     v.sin_t = std::sin(s.theta);
+    v.blaze_m = s.blaze_order;
+    v.blaze_lc = s.blaze_lambda;
+    v.lambda_lo = s.lambda_lo;
+    m->has_blaze = m->has_blaze || s.blaze_order != 0.0;
     v.degree = s.degree;
     v.K = s.K;
     v.n_lambda = s.n_lambda;
@@ -829,11 +949,13 @@ int e2e_load_model(e2e_ctx* ctx, const e2e_model_desc* desc, uint64_t* model_id)
     bin_off[i + 1] = bin_off[i] + v.n_lambda;
   }
   m->n_bins = bin_off.back();
+  m->bin_off = bin_off;
   int rc = upload(&m->d_slices, ds.data(), ds.size());
   if (rc == E2E_OK) rc = upload(&m->d_u, u_all.data(), u_all.size());
   if (rc == E2E_OK) rc = upload(&m->d_ucum, ucum.data(), ucum.size());
   if (rc == E2E_OK) rc = upload(&m->d_usum, usum.data(), usum.size());
   if (rc == E2E_OK) rc = upload(&m->d_bin_off, bin_off.data(), bin_off.size());
+  if (rc == E2E_OK && m->psf == E2E_PSF_TABLE) rc = build_psf_tables(m.get(), phases);
   if (rc == E2E_OK) rc = upload(&m->d_dims, dims.data(), dims.size());
   if (rc == E2E_OK) rc = plan_model(m.get());
   if (rc != E2E_OK) {
@@ -1036,11 +1158,14 @@ int e2e_render_static(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uin
   int rc = resolve_flux(ctx, m, n_spec, spec_ids, table);
   if (rc != E2E_OK) return rc;
   // layout in the fixed buffer: flux table | pitches | destination pointers | box store
+  // [| blazed spectra | original flux table]
   const size_t off_table = 0;
   const size_t off_pitch = align256(off_table + table.size() * sizeof(double*));
   const size_t off_dst = align256(off_pitch + pitch.size() * sizeof(int64_t));
   const size_t off_store = align256(off_dst + (size_t)m->n_det * sizeof(void*));
-  const size_t need = off_store + (size_t)P.store_elems * sizeof(float2);
+  const size_t off_blaze = align256(off_store + (size_t)P.store_elems * sizeof(float2));
+  const size_t off_tin = align256(off_blaze + (m->has_blaze ? (size_t)m->n_bins * sizeof(double) : 0));
+  const size_t need = m->has_blaze ? off_tin + table.size() * sizeof(double*) : off_blaze;
   if (need > E2E_STATIC_SCRATCH_BYTES)
     return fail(E2E_ETOOBIG, "model needs " + std::to_string(need) + " bytes of scratch; the fixed buffer holds " +
                                  std::to_string((size_t)E2E_STATIC_SCRATCH_BYTES));
@@ -1053,6 +1178,11 @@ int e2e_render_static(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uin
   void** d_dst = reinterpret_cast<void**>(b + off_dst);
   float2* store = reinterpret_cast<float2*>(b + off_store);
   cudaStream_t st = (cudaStream_t)stream;
+  if (m->has_blaze && !table.empty()) {
+    rc = blaze_into(m, table, reinterpret_cast<double*>(b + off_blaze), reinterpret_cast<const double**>(b + off_tin),
+                    st);
+    if (rc != E2E_OK) return rc;
+  }
   if (!table.empty())
     E2E_CK(cudaMemcpyAsync(d_table, table.data(), table.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
   E2E_CK(cudaMemcpyAsync(d_pitch, pitch.data(), pitch.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
@@ -1092,6 +1222,8 @@ int e2e_render_adjoint(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const ui
   E2E_CK(cudaMemsetAsync(g_sy, 0, sizeof(double) * 3 * ns, st));
   if (ns == 0 || P.items.empty()) return E2E_OK;
   Scratch sc{{}, st};
+  rc = blaze_scratch(m, table, sc, st);
+  if (rc != E2E_OK) return rc;
   const double** d_table = nullptr;
   int64_t* d_pitch = nullptr;
   const void** d_dldi = nullptr;
@@ -1180,6 +1312,7 @@ void CUDART_CB job_finished(void* p) {
 // Memory a job holds while in flight: its scratch plus library-owned frames.
 int64_t job_budget(const Model* m, const Job& j) {
   int64_t b = 64 << 10;  // launch tables
+  if (m->has_blaze) b += m->n_bins * 8 + (int64_t)m->slices.size() * 8;  // blazed spectra
   if (j.precision == E2E_PREC_MIXED) b += m->plan.store_elems * 8;
   else if (j.dtype == E2E_F32)
     for (int d = 0; d < m->n_det; ++d) b += (int64_t)m->H[d] * m->W[d] * 8;
@@ -1493,6 +1626,7 @@ int e2e_render_photons(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const ui
   Model* m = find_model(ctx, model_id);
   if (!m) return fail(E2E_ENOTFOUND, "unknown model id");
   if (!m->u_nonneg) return fail(E2E_EINVAL, "photon rendering needs slit weights >= 0");
+  if (m->psf == E2E_PSF_TABLE) return fail(E2E_EINVAL, "photon rendering supports the analytic PSFs");
   std::vector<int64_t> pitch(m->n_det);
   for (int d = 0; d < m->n_det; ++d) {
     if (!dst[d]) return fail(E2E_EINVAL, "null destination frame");
@@ -1511,6 +1645,8 @@ int e2e_render_photons(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const ui
     return E2E_OK;
   }
   Scratch sc{{}, st};
+  rc = blaze_scratch(m, table, sc, st);
+  if (rc != E2E_OK) return rc;
   const double** d_table = nullptr;
   int64_t* d_pitch = nullptr;
   uint32_t** d_dst = nullptr;

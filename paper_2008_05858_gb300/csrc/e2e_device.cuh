@@ -20,6 +20,8 @@ struct DevSlice {
   double sx[3], sy[3];  // PSF width quadratics in lt (px)
   double dlam;          // wavelength bin width (lambda_hi - lambda_lo) / n_lambda
   double cos_t, sin_t;  // elliptical PSF axis rotation
+  double blaze_m, blaze_lc;  // blaze function: order (0 = none) and blaze wavelength
+  double lambda_lo;          // start of the wavelength range
   int32_t degree, K, n_lambda, n_slit;
   int32_t det, H, W, flux_slot;  // detector, its size, index into the per-render flux table
   int64_t u_off;                 // offset of this slice's slit weights in the model's weight array
@@ -35,6 +37,15 @@ struct Item {
   int32_t bx0, by0, bw, bh;
   int32_t pad;
   int64_t store_off;  // offset (elements) of this item's box in the render's box store
+};
+
+// Tabulated-PSF slice: its maps, field nodes and effective-PSF tables in the model's arrays.
+struct TableSlice {
+  int64_t tab_off;    // first table entry (n_field x (P+1)^2 x K^2)
+  int64_t map_off;    // first map sample (n_field x M^2)
+  int32_t field_off;  // first field node
+  int32_t n_field, map_size, K;
+  double q;           // map samples per pixel
 };
 
 // Output tile of the merge: tile (tx, ty) of detector det lists items[list_off .. list_off+n).

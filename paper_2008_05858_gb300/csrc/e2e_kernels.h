@@ -41,6 +41,19 @@ cudaError_t launch_noise(uint64_t seed, uint64_t pattern_seed, double dark, doub
                          int64_t src_pitch, const double* R, int dst_dtype, void* dst, int64_t dst_pitch, int H, int W,
                          int det, cudaStream_t st);
 
+cudaError_t launch_epsf_build(const TableSlice* ts, int n_slices, int max_field, const double* maps, double* norms,
+                              int P, double* T64, float* T32, cudaStream_t st);
+size_t table_smem_bytes(int area, int nk_max, int nd);
+cudaError_t launch_render_table(int K, const DevSlice* slices, const TableSlice* ts, const float* T32,
+                                const double* field_lt, int P, const double* const* flux_tab, const double* u_all,
+                                const Item* items, int n_items, float2* store, int nk_max, int max_deg, size_t smem,
+                                cudaStream_t st, int* err = nullptr);
+cudaError_t launch_render_fp64_table(int K, int n_slices, int64_t max_stamps, const DevSlice* slices,
+                                     const TableSlice* ts, const double* T64, const double* field_lt, int P,
+                                     const double* const* flux_tab, const double* u_all, double* const* acc,
+                                     const int64_t* pitch, cudaStream_t st);
+cudaError_t launch_blaze(const DevSlice* slices, int n_slices, const double* const* flux_in, const int64_t* bin_off,
+                         int64_t n_bins, double* out, cudaStream_t st);
 cudaError_t launch_photon_bins(const DevSlice* slices, int n_slices, const double* const* flux_tab, const double* usum,
                                const int64_t* bin_off, int64_t n_bins, uint64_t seed, uint64_t* counts,
                                cudaStream_t st);

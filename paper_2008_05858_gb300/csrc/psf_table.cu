@@ -1,0 +1,410 @@
+// Tabulated PSF: effective-PSF tables and the stamp renderers that read them.
+//
+// A slice's PSF is given as maps (Sec. 2.1: the spectrograph unit delivers PSF maps per
+// projected fiber image) at field nodes lt_f along the order: map f samples the density at
+// offsets ((u - c)/q, (v - c)/q) px from the PSF centre, c = (M - 1)/2, and the density
+// between samples is the bilinear interpolant, sum_uv S_uv T(q x - (u - c)) T(q y - (v - c))
+// with T the unit tent.  Its integral over a pixel [a, b) x [a', b') therefore factorises:
+//
+//   I = sum_v sum_u S_uv X_u Y_v / norm,  X_u = (G(q (b - x_u)) - G(q (a - x_u))) / q,
+//   G(t) = integral of the tent up to t (0, (1+t)^2/2, 1 - (1-t)^2/2, 1),  norm = sum S / q^2,
+//
+// and only the ~q + 2 columns and rows whose tents meet the pixel contribute.  At load time
+// k_epsf_build tabulates, for every node, the K x K window's pixel integrals for the PSF
+// centre at sub-pixel phases -1/2 + p/P, p = 0..P (P + 1 per axis), in FP64 (and FP32 for the
+// mixed renderer).  A stamp then interpolates bilinearly between the four phases around its
+// sub-pixel offset and linearly in lt between the two field nodes around its wavelength (the
+// end node beyond the ends): 8 table reads and 8 FMAs per pixel.
+#include "e2e_device.cuh"
+#include "e2e_kernels.h"
+#include "mixed_common.cuh"
+
+namespace e2e {
+
+__device__ __forceinline__ double tent_cdf(double t) {
+  if (t <= -1.0) return 0.0;
+  if (t <= 0.0) return 0.5 * (1.0 + t) * (1.0 + t);
+  if (t <= 1.0) return 1.0 - 0.5 * (1.0 - t) * (1.0 - t);
+  return 1.0;
+}
+
+// One block per (slice, node): the map's norm, sum S / q^2.
+__global__ void __launch_bounds__(256) k_map_norm(const TableSlice* __restrict__ ts, const double* __restrict__ maps,
+                                                  double* __restrict__ norms) {
+  const TableSlice& t = ts[blockIdx.x];
+  const int f = blockIdx.y;
+  if (f >= t.n_field) return;
+  const int M = t.map_size;
+  const double* S = maps + t.map_off + (int64_t)f * M * M;
+  double sum = 0.0;
+  for (int i = threadIdx.x; i < M * M; i += blockDim.x) sum += S[i];
+  __shared__ double red[256];
+  red[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) norms[t.field_off + f] = red[0] / (t.q * t.q);
+}
+
+// One block per (slice, node, phase): thread (n, m) integrates the map over window pixel
+// (m, n) for the PSF centred at the phase's offset from the centre pixel's centre.
+__global__ void __launch_bounds__(256) k_epsf_build(const TableSlice* __restrict__ ts, const double* __restrict__ maps,
+                                                    const double* __restrict__ norms, int P, double* __restrict__ T64,
+                                                    float* __restrict__ T32) {
+  const TableSlice& t = ts[blockIdx.x];
+  const int f = blockIdx.y / ((P + 1) * (P + 1));
+  const int ph = blockIdx.y - f * (P + 1) * (P + 1);
+  if (f >= t.n_field) return;
+  const int py = ph / (P + 1), px = ph - py * (P + 1);
+  const int K = t.K, H = K / 2, M = t.map_size;
+  const double q = t.q, c = 0.5 * (M - 1);
+  const double phx = -0.5 + (double)px / P, phy = -0.5 + (double)py / P;
+  const double* S = maps + t.map_off + (int64_t)f * M * M;
+  const double norm = norms[t.field_off + f];
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int n = e / K, m = e - n * K;
+    const double ax = m - H - 0.5 - phx, bx = ax + 1.0, ay = n - H - 0.5 - phy, by = ay + 1.0;
+    // samples whose tents meet [a, b): c + q a - 1 < u < c + q b + 1
+    const int u0 = max(0, (int)floor(c + q * ax - 1.0)), u1 = min(M - 1, (int)ceil(c + q * bx + 1.0));
+    const int v0 = max(0, (int)floor(c + q * ay - 1.0)), v1 = min(M - 1, (int)ceil(c + q * by + 1.0));
+    double sum = 0.0;
+    for (int v = v0; v <= v1; ++v) {
+      const double yv = (v - c) / q;
+      const double wy = (tent_cdf(q * (by - yv)) - tent_cdf(q * (ay - yv))) / q;
+      if (wy == 0.0) continue;
+      double row = 0.0;
+      for (int u = u0; u <= u1; ++u) {
+        const double xu = (u - c) / q;
+        row += S[(int64_t)v * M + u] * ((tent_cdf(q * (bx - xu)) - tent_cdf(q * (ax - xu))) / q);
+      }
+      sum += row * wy;
+    }
+    const double val = sum / norm;
+    const int64_t idx = t.tab_off + ((int64_t)ph + (int64_t)f * (P + 1) * (P + 1)) * K * K + e;
+    T64[idx] = val;
+    T32[idx] = (float)val;
+  }
+}
+
+cudaError_t launch_epsf_build(const TableSlice* ts, int n_slices, int max_field, const double* maps, double* norms,
+                              int P, double* T64, float* T32, cudaStream_t st) {
+  if (n_slices == 0) return cudaSuccess;
+  k_map_norm<<<dim3(n_slices, max_field), 256, 0, st>>>(ts, maps, norms);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_epsf_build<<<dim3(n_slices, max_field * (P + 1) * (P + 1)), 128, 0, st>>>(ts, maps, norms, P, T64, T32);
+  return cudaGetLastError();
+}
+
+// Field node pair and weight of normalised wavelength lt (the end node beyond the ends).
+__device__ __forceinline__ void field_weight(const double* lt_nodes, int F, double lt, int& f0, int& f1, double& wf) {
+  f0 = 0;
+  f1 = 0;
+  wf = 0.0;
+  if (lt <= lt_nodes[0]) return;
+  if (lt >= lt_nodes[F - 1]) {
+    f0 = f1 = F - 1;
+    return;
+  }
+  while (f0 + 1 < F && lt_nodes[f0 + 1] <= lt) ++f0;
+  f1 = f0 + 1;
+  wf = (lt - lt_nodes[f0]) / (lt_nodes[f1] - lt_nodes[f0]);
+}
+
+// ------------------------------------------------------------------ mixed precision
+
+constexpr int kTThreads = 128;
+constexpr int kTWarps = kTThreads / 32;
+
+struct TableLayout {
+  size_t tabP, tabS, tabW, tabU, tabF, stage, stagew, boxh, boxl, total;
+  __host__ __device__ TableLayout(int J, int NK, int nd, int area) {
+    size_t o = 0;
+    tabP = o; o += (size_t)J * 2 * nd * 8;
+    tabS = o; o += (size_t)NK * 8;
+    tabW = o; o += (size_t)J * 8;
+    tabU = o; o += (size_t)NK * 8;
+    o = (o + 15) & ~(size_t)15;
+    tabF = o; o += (size_t)J * 16;              // (f0, f1, weight of f1, -) per sample
+    stage = o; o += (size_t)kTWarps * 32 * 16;
+    stagew = o; o += (size_t)kTWarps * 32 * 8;
+    boxh = o; o += (size_t)area * 4;
+    boxl = o; o += (size_t)area * 4;
+    total = o;
+  }
+};
+
+struct TableArgs {
+  MixedArgs m;
+  const TableSlice* ts;
+  const float* T32;
+  const double* field_lt;
+  int P;
+};
+
+// One CTA per work item (<= 32 samples x <= 16 slit points); the warp's 32 stamps are mapped
+// into staging, then the (stamp, pixel) pairs of the batch are spread over the lanes: each
+// lane reads its pixel from the 8 tables around the stamp's phase and wavelength, blends, and
+// deposits into the item's box as exact fixed point.
+template <int K>
+__global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) {
+  const MixedArgs& a = ta.m;
+  constexpr int KK = K * K;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Item it = a.items[blockIdx.x];
+  const DevSlice& S = a.slices[it.slice];
+  const TableSlice& TS = ta.ts[it.slice];
+  const int P = ta.P;
+  const int area = it.bw * it.bh;
+  const int nd = S.degree + 1;
+  const TableLayout L(32, a.nk_max, a.max_deg + 1, area);
+  double* tabP = reinterpret_cast<double*>(smem + L.tabP);
+  double* tabS = reinterpret_cast<double*>(smem + L.tabS);
+  float2* tabW = reinterpret_cast<float2*>(smem + L.tabW);
+  float2* tabU = reinterpret_cast<float2*>(smem + L.tabU);
+  int4* tabF = reinterpret_cast<int4*>(smem + L.tabF);
+  int4* stage = reinterpret_cast<int4*>(smem + L.stage);
+  float2* stagew = reinterpret_cast<float2*>(smem + L.stagew);
+  int* boxh = reinterpret_cast<int*>(smem + L.boxh);
+  unsigned* boxl = reinterpret_cast<unsigned*>(smem + L.boxl);
+  __shared__ double s_w[kTWarps], s_u[kTWarps];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int p = tid; p < area; p += kTThreads) {
+    boxh[p] = 0;
+    boxl[p] = 0u;
+  }
+  const double* flux = a.flux_tab[S.flux_slot];
+  const double* u = a.u_all + S.u_off;
+  const double inv_nl = 1.0 / (double)S.n_lambda, inv_ns = 1.0 / (double)S.n_slit;
+  double usum = 0.0;
+  for (int kk = tid; kk < it.nk; kk += kTThreads) {
+    const double uk = u[it.k0 + kk];
+    tabS[kk] = norm_sample_r(it.k0 + kk, S.n_slit, inv_ns);
+    tabU[kk] = split_df(uk);
+    usum += fabs(uk);
+  }
+  double wsum = 0.0;
+  for (int jj = tid; jj < it.nj; jj += kTThreads) {
+    const double lt = norm_sample_r(it.j0 + jj, S.n_lambda, inv_nl);
+    for (int b = 0; b < nd; ++b) {
+      tabP[(jj * 2 + 0) * nd + b] = poly_lt_for_b(S.cx, S.degree, b, lt);
+      tabP[(jj * 2 + 1) * nd + b] = poly_lt_for_b(S.cy, S.degree, b, lt);
+    }
+    int f0, f1;
+    double wf;
+    field_weight(ta.field_lt + TS.field_off, TS.n_field, lt, f0, f1, wf);
+    tabF[jj] = make_int4(f0, f1, __float_as_int((float)wf), 0);
+    const double wj = flux[it.j0 + jj] * S.dlam;
+    tabW[jj] = split_df(wj);
+    wsum += fabs(wj);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+    usum += __shfl_xor_sync(0xffffffffu, usum, o);
+  }
+  if (lane == 0) {
+    s_w[warp] = wsum;
+    s_u[warp] = usum;
+  }
+  __syncthreads();
+  double wtot = 0.0, utot = 0.0;
+#pragma unroll
+  for (int q = 0; q < kTWarps; ++q) {
+    wtot += s_w[q];
+    utot += s_u[q];
+  }
+  const double total = wtot * utot;
+  int ex = 0;
+  frexp(total, &ex);
+  const int Psh = total > 0.0 ? max(-100, min(100, 52 - ex)) : 0;
+  const float sc = ldexpf(1.f, Psh), sc_hi = ldexpf(1.f, Psh - 22);
+  const float* T = ta.T32 + TS.tab_off;
+  const int64_t node_stride = (int64_t)(P + 1) * (P + 1) * KK;
+
+  const int nst = it.nj * it.nk;
+  int4* wst = stage + warp * 32;
+  float2* wsw = stagew + warp * 32;
+  for (int base = warp * 32; base < nst && total > 0.0; base += kTWarps * 32) {
+    {
+      const int idx = base + lane;
+      int ci = kOffFrame, ri = kOffFrame, jj = 0;
+      float fx = 0.f, fy = 0.f, w = 0.f;
+      if (idx < nst) {
+        jj = idx / it.nk;
+        const int kk = idx - jj * it.nk;
+        double px[9], py[9];
+#pragma unroll
+        for (int b = 0; b <= 8; ++b) {
+          px[b] = b < nd ? tabP[(jj * 2 + 0) * nd + b] : 0.0;
+          py[b] = b < nd ? tabP[(jj * 2 + 1) * nd + b] : 0.0;
+        }
+        const double s = tabS[kk];
+        split_coord(horner_s(px, S.degree, s), ci, fx);
+        split_coord(horner_s(py, S.degree, s), ri, fy);
+        const float2 wj = tabW[jj], uk = tabU[kk];
+        w = fmaf(wj.x, uk.x, fmaf(wj.x, uk.y, wj.y * uk.x));
+      }
+      wst[lane] = make_int4(ci, ri, __float_as_int(fx), __float_as_int(fy));
+      wsw[lane] = make_float2(w, __int_as_float(jj));
+    }
+    __syncwarp();
+    const int nb = min(32, nst - base);
+    const int npairs = nb * KK;
+    for (int p0 = 0; p0 < npairs; p0 += 32) {
+      const int p = p0 + lane;
+      if (p >= npairs) continue;
+      const int b = p / KK, e = p - b * KK;
+      const int4 st = wst[b];
+      if (st.x == kOffFrame || st.y == kOffFrame) continue;
+      const int n = e / K, m = e - n * K;
+      const int bx = st.x - K / 2 + m - it.bx0, by = st.y - K / 2 + n - it.by0;
+      if (bx < 0 || bx >= it.bw || by < 0 || by >= it.bh) {
+        if (a.err) {
+          const int X = it.bx0 + bx, Y = it.by0 + by;
+          if (X >= 0 && X < S.W && Y >= 0 && Y < S.H) atomicAdd(a.err, 1);
+        }
+        continue;
+      }
+      const float2 sw = wsw[b];
+      const int4 fw = tabF[__float_as_int(sw.y)];
+      const float rx = (__int_as_float(st.z) + 0.5f) * (float)P, ry = (__int_as_float(st.w) + 0.5f) * (float)P;
+      const int ipx = min(P - 1, max(0, (int)floorf(rx))), ipy = min(P - 1, max(0, (int)floorf(ry)));
+      const float ax = rx - (float)ipx, ay = ry - (float)ipy;
+      const float wf1 = __int_as_float(fw.z);
+      float v = 0.f;
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const float we = side ? wf1 : 1.f - wf1;
+        const float* Tn = T + (int64_t)(side ? fw.y : fw.x) * node_stride + e;
+        const int r0 = (ipy * (P + 1) + ipx) * KK, r1 = r0 + (P + 1) * KK;
+        const float t = fmaf(1.f - ay, fmaf(1.f - ax, __ldg(Tn + r0), ax * __ldg(Tn + r0 + KK)),
+                             ay * fmaf(1.f - ax, __ldg(Tn + r1), ax * __ldg(Tn + r1 + KK)));
+        v = fmaf(we, t, v);
+      }
+      const int q = by * it.bw + bx;
+      box_deposit(boxh + q, boxl + q, sw.x * v, sc, sc_hi);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  float2* out = a.store + it.store_off;
+  const float inv = ldexpf(1.f, -Psh);
+  for (int p = tid; p < area; p += kTThreads) out[p] = fixed_to_pair(boxh[p], boxl[p], inv);
+}
+
+size_t table_smem_bytes(int area, int nk_max, int nd) { return TableLayout(32, nk_max, nd, area).total; }
+
+template <int K>
+static cudaError_t launch_table_one(const TableArgs& a, int n_items, size_t smem, cudaStream_t st) {
+  auto kern = k_render_table<K>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<n_items, kTThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_render_table(int K, const DevSlice* slices, const TableSlice* ts, const float* T32,
+                                const double* field_lt, int P, const double* const* flux_tab, const double* u_all,
+                                const Item* items, int n_items, float2* store, int nk_max, int max_deg, size_t smem,
+                                cudaStream_t st, int* err) {
+  if (n_items == 0) return cudaSuccess;
+  TableArgs a{MixedArgs{slices, flux_tab, u_all, items, store, 0, 1, nk_max, max_deg, err}, ts, T32, field_lt, P};
+  switch (K) {
+#define E2E_CASE(KK) \
+  case KK: return launch_table_one<KK>(a, n_items, smem, st);
+    E2E_CASE(1) E2E_CASE(3) E2E_CASE(5) E2E_CASE(7) E2E_CASE(9) E2E_CASE(11) E2E_CASE(13) E2E_CASE(15)
+#undef E2E_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ------------------------------------------------------------------ FP64
+
+// One thread per stamp: FP64 mapping, FP64 tables, FP64 blend, FP64 atomics.
+template <int K>
+__global__ void __launch_bounds__(256) k_render_fp64_table(const DevSlice* __restrict__ slices,
+                                                           const TableSlice* __restrict__ ts,
+                                                           const double* __restrict__ T64,
+                                                           const double* __restrict__ field_lt, int P,
+                                                           const double* const* __restrict__ flux_tab,
+                                                           const double* __restrict__ u_all, double* const* acc,
+                                                           const int64_t* __restrict__ pitch) {
+  const DevSlice& S = slices[blockIdx.y];
+  if (S.K != K) return;
+  const TableSlice& TS = ts[blockIdx.y];
+  const double* flux = flux_tab[S.flux_slot];
+  const double* u = u_all + S.u_off;
+  const int64_t n = (int64_t)S.n_lambda * S.n_slit;
+  double* frame = acc[S.det];
+  const int64_t Pf = pitch[S.det];
+  constexpr int KK = K * K, H = K / 2;
+  const int64_t node_stride = (int64_t)(P + 1) * (P + 1) * KK;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / S.n_slit);
+    const int k = (int)(idx - (int64_t)j * S.n_slit);
+    const double lt = norm_sample(j, S.n_lambda);
+    const double s = norm_sample(k, S.n_slit);
+    double x = 0.0, y = 0.0;
+    for (int b = S.degree; b >= 0; --b) {
+      x = fma(x, s, poly_lt_for_b(S.cx, S.degree, b, lt));
+      y = fma(y, s, poly_lt_for_b(S.cy, S.degree, b, lt));
+    }
+    x = clamp_coord(x);
+    y = clamp_coord(y);
+    const double ci = floor(x + 0.5), ri = floor(y + 0.5);
+    const int i0 = (int)ci - H, r0 = (int)ri - H;
+    if (i0 + K <= 0 || i0 >= S.W || r0 + K <= 0 || r0 >= S.H) continue;
+    const double w = flux[j] * S.dlam * u[k];
+    int f0, f1;
+    double wf;
+    field_weight(field_lt + TS.field_off, TS.n_field, lt, f0, f1, wf);
+    const double rx = (x - ci + 0.5) * P, ry = (y - ri + 0.5) * P;
+    const int ipx = min(P - 1, max(0, (int)floor(rx))), ipy = min(P - 1, max(0, (int)floor(ry)));
+    const double ax = rx - ipx, ay = ry - ipy;
+    const double* T0 = T64 + TS.tab_off + (int64_t)f0 * node_stride;
+    const double* T1 = T64 + TS.tab_off + (int64_t)f1 * node_stride;
+    const int r00 = (ipy * (P + 1) + ipx) * KK, r10 = r00 + (P + 1) * KK;
+    for (int nn = 0; nn < K; ++nn) {
+      const int r = r0 + nn;
+      if (r < 0 || r >= S.H) continue;
+      for (int m = 0; m < K; ++m) {
+        const int i = i0 + m;
+        if (i < 0 || i >= S.W) continue;
+        const int e = nn * K + m;
+        double v = 0.0;
+        for (int side = 0; side < 2; ++side) {
+          const double we = side ? wf : 1.0 - wf;
+          if (we == 0.0) continue;
+          const double* Tn = side ? T1 : T0;
+          v += we * ((1.0 - ay) * ((1.0 - ax) * Tn[r00 + e] + ax * Tn[r00 + KK + e]) +
+                     ay * ((1.0 - ax) * Tn[r10 + e] + ax * Tn[r10 + KK + e]));
+        }
+        atomicAdd(frame + (int64_t)r * Pf + i, w * v);
+      }
+    }
+  }
+}
+
+cudaError_t launch_render_fp64_table(int K, int n_slices, int64_t max_stamps, const DevSlice* slices,
+                                     const TableSlice* ts, const double* T64, const double* field_lt, int P,
+                                     const double* const* flux_tab, const double* u_all, double* const* acc,
+                                     const int64_t* pitch, cudaStream_t st) {
+  if (n_slices == 0 || max_stamps == 0) return cudaSuccess;
+  int64_t bx = (max_stamps + 255) / 256;
+  if (bx > 4096) bx = 4096;
+  dim3 grid((unsigned)bx, (unsigned)n_slices);
+  switch (K) {
+#define E2E_CASE(KK) \
+  case KK: k_render_fp64_table<KK><<<grid, 256, 0, st>>>(slices, ts, T64, field_lt, P, flux_tab, u_all, acc, pitch); break;
+    E2E_CASE(1) E2E_CASE(3) E2E_CASE(5) E2E_CASE(7) E2E_CASE(9) E2E_CASE(11) E2E_CASE(13) E2E_CASE(15)
+#undef E2E_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace e2e

@@ -38,6 +38,7 @@ import numpy as np
 
 PSF_SEPARABLE = 0
 PSF_ELLIPTICAL = 1
+PSF_TABLE = 2
 
 #: seed base: the arXiv identifier of the paper; config i uses SEED_BASE + i
 SEED_BASE = 200805858
@@ -77,16 +78,68 @@ class OrderSlice:
     sigma_y: np.ndarray
     theta: float
     slit_weights: np.ndarray
+    blaze_order: float = 0.0   # echelle order of the blaze function (0: no blaze)
+    blaze_lambda: float = 0.0  # its blaze wavelength (Angstrom)
+    psf_map: "PsfMap | None" = None  # tabulated PSF (models with psf = PSF_TABLE)
 
     def copy(self) -> "OrderSlice":
         return dataclasses.replace(
             self,
+            psf_map=None if self.psf_map is None else self.psf_map.copy(),
             cx=self.cx.copy(),
             cy=self.cy.copy(),
             sigma_x=self.sigma_x.copy(),
             sigma_y=self.sigma_y.copy(),
             slit_weights=self.slit_weights.copy(),
         )
+
+
+@dataclass
+class PsfMap:
+    """Tabulated PSF of one order-slice: maps[f] samples the PSF density at offsets
+    ((u - c)/oversample, (v - c)/oversample) px from the centre (c = (M - 1)/2) at the
+    normalised wavelength field_lt[f]; `phases` sub-pixel phases per axis for the tables."""
+
+    field_lt: np.ndarray
+    maps: np.ndarray  # (n_field, M, M)
+    oversample: float
+    phases: int = 8
+
+    def copy(self) -> "PsfMap":
+        return PsfMap(self.field_lt.copy(), self.maps.copy(), self.oversample, self.phases)
+
+
+def psf_maps(s: "OrderSlice", *, n_field: int = 5, oversample: float = 10.0, half_px: float = 8.0,
+             phases: int = 8, coma: float = 0.0) -> PsfMap:
+    """Synthetic PSF maps (the optical design's maps are not available): at n_field
+    wavelengths the slice's Gaussian (widths sigma_x, sigma_y at that wavelength), plus, when
+    coma > 0, a fainter Gaussian displaced along x by 1.5 sigma_x (a comatic tail) carrying
+    that fraction of the light."""
+    M = int(2 * round(half_px * oversample) + 1)
+    c = (M - 1) / 2.0
+    lt = np.linspace(-1.0, 1.0, n_field)
+    x = (np.arange(M) - c) / oversample
+    maps = np.empty((n_field, M, M))
+    for f, l in enumerate(lt):
+        sx = s.sigma_x[0] + s.sigma_x[1] * l + s.sigma_x[2] * l * l
+        sy = s.sigma_y[0] + s.sigma_y[1] * l + s.sigma_y[2] * l * l
+        gx = np.exp(-0.5 * (x / sx) ** 2) / sx
+        gy = np.exp(-0.5 * (x / sy) ** 2) / sy
+        img = np.outer(gy, gx)
+        if coma > 0:
+            gx2 = np.exp(-0.5 * ((x - 1.5 * sx) / (1.3 * sx)) ** 2) / (1.3 * sx)
+            img = (1 - coma) * img + coma * np.outer(gy, gx2)
+        maps[f] = img / (2 * np.pi)
+    return PsfMap(lt, maps, oversample, phases)
+
+
+def with_psf_maps(model: "OpticalModel", **kw) -> "OpticalModel":
+    """The model with every slice's PSF replaced by synthetic tabulated maps (psf_maps)."""
+    m = model.copy()
+    for s in m.slices:
+        s.psf_map = psf_maps(s, **kw)
+    m.psf = PSF_TABLE
+    return m
 
 
 @dataclass

@@ -400,3 +400,38 @@ def test_ten_samples_per_resolution_element_alias_below_photon_noise():
     w1 = A.flat_field(1.0, peak_e=40000.0)
     r1 = A.measured_ripple(oracle.render_workload(w1)[0], w1)
     assert r1["ripple"] > r1["photon_noise_peak_pixel"]  # one sample per FWHM is not enough
+
+
+def _blazed(seed=501, m=110.0):
+    w = W.small_config(seed=seed, orders=2)
+    for s in w.model.slices:
+        s.blaze_order = m
+        s.blaze_lambda = 0.5 * (s.lambda_lo + s.lambda_hi) * (1.0 + 0.3 / m)  # off-centre peak
+    return w
+
+
+def test_blaze_is_a_weight_multiplier_with_the_grating_envelope():
+    # Blaze (Sec. 4.2: each order weighted by its grating blaze profile): B = sinc^2(nu),
+    # nu = m (1 - lambda_b / lambda).  The blazed render must equal the unblazed render of the
+    # spectrum multiplied by B at the bin centres; B is 1 at lambda_b and 0 at nu = +-1.
+    w = _blazed()
+    plain = w.model.copy()
+    for s in plain.slices:
+        s.blaze_order = 0.0
+
+    def blaze(s, lam):
+        nu = s.blaze_order * (1.0 - s.blaze_lambda / lam)
+        return np.sinc(nu) ** 2
+
+    blazed_of = {id(p): q for p, q in zip(plain.slices, w.model.slices)}
+
+    def flux_b(s):
+        lam = s.lambda_lo + (np.arange(s.n_lambda) + 0.5) * (s.lambda_hi - s.lambda_lo) / s.n_lambda
+        return w.flux_for(s) * blaze(blazed_of[id(s)], lam)
+
+    a = oracle.render(w.model, w.flux_for)[0]
+    b = oracle.render(plain, flux_b)[0]
+    np.testing.assert_allclose(a, b, rtol=1e-13, atol=1e-15 * np.abs(b).max())
+    s = w.model.slices[0]
+    assert blaze(s, s.blaze_lambda) == 1.0
+    assert abs(blaze(s, s.blaze_lambda / (1.0 - 1.0 / s.blaze_order))) < 1e-25

@@ -245,3 +245,15 @@ def test_debug_checks_find_nothing_and_change_nothing(kind):
     finally:
         plain.close()
         checked.close()
+
+
+@pytest.mark.parametrize("psf", [W.PSF_SEPARABLE, W.PSF_ELLIPTICAL], ids=["separable", "elliptical"])
+def test_blazed_model_matches_oracle(renderer, psf):
+    w = W.small_config(seed=511 + psf, orders=2, psf=psf)
+    for s in w.model.slices:
+        s.blaze_order = 110.0
+        s.blaze_lambda = 0.5 * (s.lambda_lo + s.lambda_hi)
+    ref = oracle.render_workload(w)[0]
+    assert compare(gpu_frames(renderer, w, "mixed", "f32")[0], ref).ok
+    g64 = gpu_frames(renderer, w, "fp64", "f64")[0]
+    assert np.all(np.abs(g64 - ref) <= FP64_REL * np.abs(ref) + 1e-15 * np.abs(ref).max())

@@ -68,3 +68,17 @@ def test_empty_model_and_zero_flux(renderer):
     torch.cuda.synchronize()
     assert total == 0 and not out[0].any().item()
     renderer.unload_model(mid)
+
+
+def test_blazed_photons_bit_exact(renderer):
+    w = scaled_workload(W.small_config(seed=321, orders=2), 2e5)
+    for s in w.model.slices:
+        s.blaze_order = 110.0
+        s.blaze_lambda = 0.5 * (s.lambda_lo + s.lambda_hi)
+    ref, ref_total = oracle.render_photons(w.model, w.flux_for, seed=77)
+    mid = renderer.load_model(w.model)
+    out, total = renderer.render_photons(mid, renderer.load_spectra(w), seed=77)
+    torch.cuda.synchronize()
+    assert total == ref_total
+    assert np.array_equal(out[0].cpu().numpy().view(np.uint32), ref[0])
+    renderer.unload_model(mid)
