@@ -47,11 +47,13 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# FP32 lane operations of one separable stamp of window K, counted algorithmically:
-# 2(K+1) Gaussian-tail (erf) evaluations at 16 FP32 operations each (an exponential on the
-# SFU plus a ~12-term rational), 2K edge differences, K^2 products and K^2 sums.
-def fp32_ops_per_stamp(K: int) -> float:
-    return 2 * (K + 1) * 16 + 2 * K + 2 * K * K
+# FP32 FLOP of one separable stamp of window K, counted algorithmically (an FMA is 2 FLOP, an
+# SFU operation 1): 2(K+1) pixel-edge tail evaluations at 28 FLOP each (the double-float edge
+# argument: 6; its exact square: 3; the exponential: 1 + 2; the (4,5) rational: 18 - 2 = 16,
+# with its reciprocal), 2K edge differences, and the K^2 products with the weight folded in,
+# accumulated by FMA (2 K^2).
+def fp32_flop_per_stamp(K: int) -> float:
+    return 2 * (K + 1) * 28 + 2 * K + 2 * K * K
 
 
 # FP64 FMAs of one stamp: Horner in s of both coordinates (2 d), plus the per-sample
@@ -312,7 +314,7 @@ def run_gpu(args):
     ns = w.model.slices[0].n_slit
     fp32_peak = n_sm * 128 * 2 * mhz * 1e6  # FLOP/s, FMA = 2
     fp64_peak = n_sm * 2 * 2 * mhz * 1e6  # 2 DFMA/clk/SM measured (FMA = 2 FLOP)
-    a32 = fp32_ops_per_stamp(K) * 2 * stamps / (kr * 1e-3)  # ops counted as FMA-slots -> FLOP
+    a32 = fp32_flop_per_stamp(K) * stamps / (kr * 1e-3)
     a64 = fp64_fma_per_stamp(d, ns) * 2 * stamps / (kr * 1e-3)
     traffic = _load_traffic()
     roof32 = {"bound": "alu", "achieved": a32 / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",

@@ -78,6 +78,8 @@ struct Model {
   double* d_u = nullptr;
   double* d_ucum = nullptr;     // running sums of the slit weights (photon renderer)
   double* d_usum = nullptr;     // their totals, per slice
+  float* d_ucum32 = nullptr;    // FP32 copies for the photon fast path
+  float* d_cf32 = nullptr;      // FP32 mapping coefficients and bounds per slice (photon fast path)
   int64_t* d_bin_off = nullptr; // first wavelength bin of each slice (photon renderer, blaze)
   std::vector<int64_t> bin_off;
   int64_t n_bins = 0;
@@ -296,6 +298,8 @@ void free_model(Model* m) {
   cudaFree(m->d_u);
   cudaFree(m->d_ucum);
   cudaFree(m->d_usum);
+  cudaFree(m->d_ucum32);
+  cudaFree(m->d_cf32);
   cudaFree(m->d_bin_off);
   cudaFree(m->d_ts);
   cudaFree(m->d_field);
@@ -954,6 +958,30 @@ int e2e_load_model(e2e_ctx* ctx, const e2e_model_desc* desc, uint64_t* model_id)
   if (rc == E2E_OK) rc = upload(&m->d_u, u_all.data(), u_all.size());
   if (rc == E2E_OK) rc = upload(&m->d_ucum, ucum.data(), ucum.size());
   if (rc == E2E_OK) rc = upload(&m->d_usum, usum.data(), usum.size());
+  {
+    std::vector<float> ucum32(ucum.begin(), ucum.end());
+    const size_t nf = photon_coef_floats();
+    std::vector<float> cf(nf * m->slices.size(), 0.f);
+    for (size_t i = 0; i < m->slices.size(); ++i) {
+      const DevSlice& v = ds[i];
+      for (int c = 0; c < 2; ++c) {
+        const double* co = c ? v.cy : v.cx;
+        float* o = cf.data() + i * nf + c * (E2E_MAXC + 2);
+        double qb = 0.0, sb = 0.0;
+        for (int a = 0; a <= v.degree; ++a)
+          for (int b = 0; a + b <= v.degree; ++b) {
+            const int t = a + b, idx = t * (t + 1) / 2 + b;
+            o[idx] = (float)co[idx];
+            if (b == 0) qb += a * std::fabs(co[idx]);
+            else sb += std::fabs(co[idx]);
+          }
+        o[E2E_MAXC] = (float)qb;
+        o[E2E_MAXC + 1] = (float)sb;
+      }
+    }
+    if (rc == E2E_OK) rc = upload(&m->d_ucum32, ucum32.data(), ucum32.size());
+    if (rc == E2E_OK) rc = upload(&m->d_cf32, cf.data(), cf.size());
+  }
   if (rc == E2E_OK) rc = upload(&m->d_bin_off, bin_off.data(), bin_off.size());
   if (rc == E2E_OK && m->psf == E2E_PSF_TABLE) rc = build_psf_tables(m.get(), phases);
   if (rc == E2E_OK) rc = upload(&m->d_dims, dims.data(), dims.size());
@@ -1651,19 +1679,21 @@ int e2e_render_photons(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const ui
   int64_t* d_pitch = nullptr;
   uint32_t** d_dst = nullptr;
   uint64_t *counts = nullptr, *offsets = nullptr, *scan = nullptr;
+  int4* anchors = nullptr;
   E2E_CK(sc.get((void**)&d_table, table.size() * sizeof(double*)));
   E2E_CK(sc.get((void**)&d_pitch, pitch.size() * sizeof(int64_t)));
   E2E_CK(sc.get((void**)&d_dst, m->n_det * sizeof(uint32_t*)));
   E2E_CK(sc.get((void**)&counts, (size_t)m->n_bins * sizeof(uint64_t)));
   E2E_CK(sc.get((void**)&offsets, (size_t)(m->n_bins + 1) * sizeof(uint64_t)));
   E2E_CK(sc.get((void**)&scan, scan_scratch_elems(m->n_bins) * sizeof(uint64_t)));
+  E2E_CK(sc.get((void**)&anchors, (size_t)m->n_bins * sizeof(int4)));
   E2E_CK(cudaMemcpyAsync(d_table, table.data(), table.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
   E2E_CK(cudaMemcpyAsync(d_pitch, pitch.data(), pitch.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
   E2E_CK(cudaMemcpyAsync(d_dst, dst, m->n_det * sizeof(uint32_t*), cudaMemcpyHostToDevice, st));
   const int ns = (int)m->slices.size();
   {
     KernelTimer kt(ctx, st, "photon_bins");
-    E2E_CK(launch_photon_bins(m->d_slices, ns, d_table, m->d_usum, m->d_bin_off, m->n_bins, seed, counts, st));
+    E2E_CK(launch_photon_bins(m->d_slices, ns, d_table, m->d_usum, m->d_bin_off, m->n_bins, seed, counts, anchors, st));
   }
   {
     KernelTimer kt(ctx, st, "photon_scan");
@@ -1672,7 +1702,7 @@ int e2e_render_photons(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const ui
   {
     KernelTimer kt(ctx, st, "photons");
     E2E_CK(launch_photons(m->d_slices, ns, m->d_ucum, m->d_usum, m->d_bin_off, offsets, m->psf, seed, d_dst, d_pitch,
-                          UINT64_MAX, st));
+                          UINT64_MAX, m->d_ucum32, m->d_cf32, anchors, st));
   }
   if (total_photons) {
     E2E_CK(cudaMemcpyAsync(total_photons, offsets + m->n_bins, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));

@@ -99,9 +99,9 @@ __device__ __forceinline__ float one_minus_uni53_f32(uint32_t a, uint32_t b) {
 // Box-Muller pair in FP32 and a bound eg on |g - g_exact| for both members: ln u from logf
 // (u < 1/2) or log1pf(-(1 - u)) (u >= 1/2), each within 1 ulp of a correctly rounded
 // argument; the phase from sincospif(2u) (1 ulp) with 2u exact.
-__device__ __forceinline__ void normal_pair_f32(uint64_t seed, uint32_t q, uint32_t d, uint32_t stream, float& g0,
-                                                float& g1, float& eg) {
-  const uint4 w = rng_block(seed, q, d, 0, stream);
+__device__ __forceinline__ void normal_pair_f32_ctr(uint64_t seed, uint32_t q, uint32_t d, uint32_t i,
+                                                    uint32_t stream, float& g0, float& g1, float& eg) {
+  const uint4 w = rng_block(seed, q, d, i, stream);
   const float u1 = uni53_f32(w.x, w.y);
   const float ln = u1 < 0.5f ? logf(u1) : log1pf(-one_minus_uni53_f32(w.x, w.y));
   const float rho = sqrtf(-2.f * ln);
@@ -110,6 +110,11 @@ __device__ __forceinline__ void normal_pair_f32(uint64_t seed, uint32_t q, uint3
   g0 = rho * c;
   g1 = rho * s;
   eg = fmaf(rho, 1.5e-6f, 1e-7f);  // also covers a 2e-7 relative rounding of products with g
+}
+
+__device__ __forceinline__ void normal_pair_f32(uint64_t seed, uint32_t q, uint32_t d, uint32_t stream, float& g0,
+                                                float& g1, float& eg) {
+  normal_pair_f32_ctr(seed, q, d, 0, stream, g0, g1, eg);
 }
 
 // Poisson draw with the exact function's integer result, from FP32 arithmetic whenever its

@@ -18,6 +18,7 @@
 // bin by binary search in the scan, so that every photon is a pure function of
 // (seed, bin, slice, index) whatever the launch shape.  The pixel decisions are taken in FP64;
 // counts are added with 32-bit integer atomics (exact, order-independent).
+#include <climits>
 #include <cstdint>
 
 #include "e2e_device.cuh"
@@ -26,10 +27,18 @@
 
 namespace e2e {
 
+// FP32 copy of a slice's mapping coefficients and the bounds its fast path uses: per
+// coordinate 45 coefficients, then sum_a a |c_a0| (bounds the divided difference of the b = 0
+// polynomial) and sum_{b >= 1} |c_ab| (bounds the slit terms).
+constexpr int kCf = 2 * (E2E_MAXC + 2);
+
+// Per bin: the photon count, and the bin centre's position at s = 0 in FP64, split into the
+// nearest integer and an FP32 remainder (the anchor the FP32 fast path adds small terms to).
 __global__ void __launch_bounds__(256) k_photon_bins(const DevSlice* __restrict__ slices, int n_slices,
                                                      const double* const* __restrict__ flux_tab,
                                                      const double* __restrict__ usum, const int64_t* __restrict__ bin_off,
-                                                     uint64_t seed, uint64_t* __restrict__ counts) {
+                                                     uint64_t seed, uint64_t* __restrict__ counts,
+                                                     int4* __restrict__ anchors) {
   const int64_t nb = bin_off[n_slices];
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
     int lo = 0, hi = n_slices - 1;
@@ -41,6 +50,12 @@ __global__ void __launch_bounds__(256) k_photon_bins(const DevSlice* __restrict_
     const int j = (int)(b - bin_off[lo]);
     const double lam = __dmul_rn(__dmul_rn(flux_tab[S.flux_slot][j], S.dlam), usum[lo]);
     counts[b] = (uint64_t)poisson_filtered(lam, seed, (uint32_t)j, (uint32_t)S.index, 4);
+    const double ltj = norm_sample(j, S.n_lambda);
+    const double X0 = poly_lt_for_b(S.cx, S.degree, 0, ltj), Y0 = poly_lt_for_b(S.cy, S.degree, 0, ltj);
+    const bool ok = fabs(X0) < 1e9 && fabs(Y0) < 1e9;
+    const double Xi = ok ? rint(X0) : 0.0, Yi = ok ? rint(Y0) : 0.0;
+    anchors[b] = make_int4(ok ? (int)Xi : INT_MIN, __float_as_int((float)(X0 - Xi)), (int)Yi,
+                           __float_as_int((float)(Y0 - Yi)));
   }
 }
 
@@ -111,11 +126,89 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_add(uint64_t* __restrict_
 
 // ---------------------------------------------------------------- photons
 
+// The photon's pixel by the definition, in FP64 (fx, fy: the pixel's column and row).
+__device__ void photon_exact(const DevSlice& S, const double* __restrict__ C, double U, int psf, uint64_t seed,
+                             uint32_t j, uint32_t si, uint32_t pp, const uint4& wa, const uint4& wb, double& fxo,
+                             double& fyo) {
+  const double v = uni53(wa.x, wa.y), t = uni53(wa.z, wa.w);
+  const double cu = __dmul_rn(uni53(wb.x, wb.y), U);
+  int k0 = 0, k1 = S.n_slit - 1;  // slit point: the first k with cu <= C_k, else the last
+  while (k0 < k1) {
+    const int mid = (k0 + k1) >> 1;
+    if (cu <= C[mid]) k1 = mid; else k0 = mid + 1;
+  }
+  const double n = (double)S.n_lambda, ns = (double)S.n_slit;
+  const double lt = __ddiv_rn(__dadd_rn(__dmul_rn(2.0, __dadd_rn((double)j, v)), -n), n);
+  const double s = __ddiv_rn(__dadd_rn(__dmul_rn(2.0, __dadd_rn((double)k0, t)), -ns), ns);
+  double px[9], py[9];
+#pragma unroll
+  for (int bb = 0; bb <= 8; ++bb) {
+    px[bb] = bb <= S.degree ? poly_lt_for_b(S.cx, S.degree, bb, lt) : 0.0;
+    py[bb] = bb <= S.degree ? poly_lt_for_b(S.cy, S.degree, bb, lt) : 0.0;
+  }
+  const double xc = horner_s(px, S.degree, s), yc = horner_s(py, S.degree, s);
+  const double sa = fma(fma(S.sx[2], lt, S.sx[1]), lt, S.sx[0]);
+  const double sb = fma(fma(S.sy[2], lt, S.sy[1]), lt, S.sy[0]);
+  double z1, z2;
+  normal_pair_ctr(seed, j, si, pp, 7, z1, z2);
+  double x, y;
+  if (psf == 0) {
+    x = __dadd_rn(xc, __dmul_rn(sa, z1));
+    y = __dadd_rn(yc, __dmul_rn(sb, z2));
+  } else {
+    const double a2 = sa * sa, b2 = sb * sb, c = S.cos_t, sn = S.sin_t;
+    const double vx = a2 * c * c + b2 * sn * sn, vy = a2 * sn * sn + b2 * c * c, cxy = (a2 - b2) * sn * c;
+    const double gx = sqrt(vx), beta = cxy / vx, sc = sqrt(vy - beta * cxy);
+    const double dx = __dmul_rn(gx, z1);
+    x = __dadd_rn(xc, dx);
+    y = __dadd_rn(__dadd_rn(yc, __dmul_rn(beta, dx)), __dmul_rn(sc, z2));
+  }
+  fxo = floor(__dadd_rn(x, 0.5));
+  fyo = floor(__dadd_rn(y, 0.5));
+}
+
+// Offset of the photon from the bin's anchor along one coordinate, in FP32, and a bound on its
+// distance from the exact value: delta * Q(lt, lt_j) for the b = 0 polynomial (its divided
+// difference, so no large terms cancel) plus the slit terms sum_{b>=1} P_b(lt) s^b.
+__device__ __forceinline__ float photon_offset(const float* cf, int d, float lt, float ltj, float delta, float s,
+                                               float& mag) {
+  float q[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) q[a] = 0.f;
+  // q_a = c_a0 + ltj q_{a+1} (a = d .. 1), Q = sum_a q_a lt^(a-1)
+  float acc = 0.f;
+#pragma unroll
+  for (int a = 8; a >= 1; --a) {
+    if (a <= d) acc = fmaf(ltj, acc, cf[a * (a + 1) / 2]);  // index(a, 0) = a(a+1)/2
+    if (a <= d) q[a - 1] = acc;
+  }
+  float Q = 0.f;
+#pragma unroll
+  for (int a = 8; a >= 1; --a)
+    if (a <= d) Q = fmaf(Q, lt, q[a - 1]);
+  // slit terms: Horner in s over P_b(lt), b = d .. 1
+  float sb = 0.f;
+#pragma unroll
+  for (int b = 8; b >= 1; --b) {
+    if (b > d) continue;
+    float pb = 0.f;
+#pragma unroll
+    for (int a = 8; a >= 0; --a)
+      if (a <= d - b) pb = fmaf(pb, lt, cf[(a + b) * (a + b + 1) / 2 + b]);
+    sb = fmaf(sb, s, pb);
+  }
+  sb *= s;
+  mag = fabsf(delta) * cf[E2E_MAXC] + cf[E2E_MAXC + 1];
+  return fmaf(delta, Q, sb);
+}
+
 __global__ void __launch_bounds__(256) k_photons(const DevSlice* __restrict__ slices, int n_slices,
                                                  const double* __restrict__ ucum, const double* __restrict__ usum,
                                                  const int64_t* __restrict__ bin_off,
                                                  const uint64_t* __restrict__ offsets, int psf, uint64_t seed,
-                                                 uint32_t* const* __restrict__ dst, const int64_t* __restrict__ pitch) {
+                                                 uint32_t* const* __restrict__ dst, const int64_t* __restrict__ pitch,
+                                                 const float* __restrict__ ucum32, const float* __restrict__ cf32,
+                                                 const int4* __restrict__ anchors) {
   const int64_t nb = bin_off[n_slices];
   const uint64_t total = offsets[nb];
   for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
@@ -136,42 +229,46 @@ __global__ void __launch_bounds__(256) k_photons(const DevSlice* __restrict__ sl
     const uint32_t pp = (uint32_t)(p - offsets[b]);
     const uint32_t si = (uint32_t)S.index;
     const uint4 wa = rng_block(seed, j, si, pp, 5), wb = rng_block(seed, j, si, pp, 6);
-    const double v = uni53(wa.x, wa.y), t = uni53(wa.z, wa.w);
-    const double cu = __dmul_rn(uni53(wb.x, wb.y), usum[sl]);
-    // slit point: the first k with cu <= C_k (C nondecreasing), else the last
-    const double* C = ucum + S.u_off;
-    int k0 = 0, k1 = S.n_slit - 1;
-    while (k0 < k1) {
-      const int mid = (k0 + k1) >> 1;
-      if (cu <= C[mid]) k1 = mid; else k0 = mid + 1;
+    const int4 an = anchors[b];
+    double fx = 0.0, fy = 0.0;
+    bool exact = psf != 0 || an.x == INT_MIN;
+    if (!exact) {
+      // FP32 fast path: every decision is checked against its error bound; a photon too close
+      // to a slit-point boundary or a pixel edge is redone in FP64 below
+      const float* C32 = ucum32 + S.u_off;
+      const float cu = uni53_f32(wb.x, wb.y) * (float)usum[sl];
+      int k0 = 0, k1 = S.n_slit - 1;
+      while (k0 < k1) {
+        const int mid = (k0 + k1) >> 1;
+        if (cu <= C32[mid]) k1 = mid; else k0 = mid + 1;
+      }
+      const float tol = 5e-7f * fabsf(cu) + 1e-30f;
+      if (k0 < S.n_slit - 1 && !(C32[k0] - cu > tol)) exact = true;
+      if (k0 > 0 && !(cu - C32[k0 - 1] > tol)) exact = true;
+      const float n = (float)S.n_lambda, ns = (float)S.n_slit;
+      const float delta = (2.f * uni53_f32(wa.x, wa.y) - 1.f) / n;
+      const float ltj = (float)(2 * (int)j + 1 - S.n_lambda) / n;
+      const float lt = ltj + delta;
+      const float s = (2.f * ((float)k0 + uni53_f32(wa.z, wa.w)) - ns) / ns;
+      float z1, z2, eg;
+      normal_pair_f32_ctr(seed, j, si, pp, 7, z1, z2, eg);
+      const float* cf = cf32 + (int64_t)sl * kCf;
+      const float sx = fmaf(fmaf((float)S.sx[2], lt, (float)S.sx[1]), lt, (float)S.sx[0]);
+      const float sy = fmaf(fmaf((float)S.sy[2], lt, (float)S.sy[1]), lt, (float)S.sy[0]);
+      float mx, my;
+      const float ox = photon_offset(cf, S.degree, lt, ltj, delta, s, mx) + sx * z1;
+      const float oy = photon_offset(cf + E2E_MAXC + 2, S.degree, lt, ltj, delta, s, my) + sy * z2;
+      const float rx = __int_as_float(an.y) + ox + 0.5f, ry = __int_as_float(an.w) + oy + 0.5f;
+      const float ein = 4e-7f * ((cf[E2E_MAXC] / n) + (float)S.degree * cf[E2E_MAXC + 1] / ns);
+      const float einy = 4e-7f * ((cf[2 * E2E_MAXC + 2] / n) + (float)S.degree * cf[2 * E2E_MAXC + 3] / ns);
+      const float ex = 1e-5f * (mx + fabsf(sx * z1) + 1.f) + ein + 1.5f * sx * eg;
+      const float ey = 1e-5f * (my + fabsf(sy * z2) + 1.f) + einy + 1.5f * sy * eg;
+      const float kx = floorf(rx - ex), ky = floorf(ry - ey);
+      if (kx != floorf(rx + ex) || ky != floorf(ry + ey)) exact = true;
+      fx = (double)an.x + (double)kx;
+      fy = (double)an.z + (double)ky;
     }
-    const double n = (double)S.n_lambda, ns = (double)S.n_slit;
-    const double lt = __ddiv_rn(__dadd_rn(__dmul_rn(2.0, __dadd_rn((double)j, v)), -n), n);
-    const double s = __ddiv_rn(__dadd_rn(__dmul_rn(2.0, __dadd_rn((double)k0, t)), -ns), ns);
-    double px[9], py[9];
-#pragma unroll
-    for (int bb = 0; bb <= 8; ++bb) {
-      px[bb] = bb <= S.degree ? poly_lt_for_b(S.cx, S.degree, bb, lt) : 0.0;
-      py[bb] = bb <= S.degree ? poly_lt_for_b(S.cy, S.degree, bb, lt) : 0.0;
-    }
-    const double xc = horner_s(px, S.degree, s), yc = horner_s(py, S.degree, s);
-    const double sa = fma(fma(S.sx[2], lt, S.sx[1]), lt, S.sx[0]);
-    const double sb = fma(fma(S.sy[2], lt, S.sy[1]), lt, S.sy[0]);
-    double z1, z2;
-    normal_pair_ctr(seed, j, si, pp, 7, z1, z2);
-    double x, y;
-    if (psf == 0) {
-      x = __dadd_rn(xc, __dmul_rn(sa, z1));
-      y = __dadd_rn(yc, __dmul_rn(sb, z2));
-    } else {
-      const double a2 = sa * sa, b2 = sb * sb, c = S.cos_t, sn = S.sin_t;
-      const double vx = a2 * c * c + b2 * sn * sn, vy = a2 * sn * sn + b2 * c * c, cxy = (a2 - b2) * sn * c;
-      const double gx = sqrt(vx), beta = cxy / vx, sc = sqrt(vy - beta * cxy);
-      const double dx = __dmul_rn(gx, z1);
-      x = __dadd_rn(xc, dx);
-      y = __dadd_rn(__dadd_rn(yc, __dmul_rn(beta, dx)), __dmul_rn(sc, z2));
-    }
-    const double fx = floor(__dadd_rn(x, 0.5)), fy = floor(__dadd_rn(y, 0.5));
+    if (exact) photon_exact(S, ucum + S.u_off, usum[sl], psf, seed, j, si, pp, wa, wb, fx, fy);
     if (fx >= 0.0 && fx < (double)S.W && fy >= 0.0 && fy < (double)S.H)
       atomicAdd(dst[S.det] + (int64_t)fy * pitch[S.det] + (int64_t)fx, 1u);
   }
@@ -184,10 +281,10 @@ static unsigned grid_for(uint64_t n, int threads, uint64_t cap) {
 
 cudaError_t launch_photon_bins(const DevSlice* slices, int n_slices, const double* const* flux_tab, const double* usum,
                                const int64_t* bin_off, int64_t n_bins, uint64_t seed, uint64_t* counts,
-                               cudaStream_t st) {
+                               int4* anchors, cudaStream_t st) {
   if (n_bins == 0) return cudaSuccess;
   k_photon_bins<<<grid_for((uint64_t)n_bins, 256, 152 * 64), 256, 0, st>>>(slices, n_slices, flux_tab, usum, bin_off,
-                                                                         seed, counts);
+                                                                         seed, counts, anchors);
   return cudaGetLastError();
 }
 
@@ -202,12 +299,15 @@ cudaError_t launch_scan_exclusive(const uint64_t* in, uint64_t* out, int64_t n, 
   return cudaGetLastError();
 }
 
+size_t photon_coef_floats() { return (size_t)kCf; }
+
 cudaError_t launch_photons(const DevSlice* slices, int n_slices, const double* ucum, const double* usum,
                            const int64_t* bin_off, const uint64_t* offsets, int psf, uint64_t seed,
-                           uint32_t* const* dst, const int64_t* pitch, uint64_t max_photons, cudaStream_t st) {
+                           uint32_t* const* dst, const int64_t* pitch, uint64_t max_photons, const float* ucum32,
+                           const float* cf32, const int4* anchors, cudaStream_t st) {
   if (max_photons == 0) return cudaSuccess;
   k_photons<<<grid_for(max_photons, 256, 152 * 32), 256, 0, st>>>(slices, n_slices, ucum, usum, bin_off, offsets, psf,
-                                                                   seed, dst, pitch);
+                                                                   seed, dst, pitch, ucum32, cf32, anchors);
   return cudaGetLastError();
 }
 

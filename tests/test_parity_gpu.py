@@ -257,3 +257,22 @@ def test_blazed_model_matches_oracle(renderer, psf):
     assert compare(gpu_frames(renderer, w, "mixed", "f32")[0], ref).ok
     g64 = gpu_frames(renderer, w, "fp64", "f64")[0]
     assert np.all(np.abs(g64 - ref) <= FP64_REL * np.abs(ref) + 1e-15 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("psf", [W.PSF_SEPARABLE, W.PSF_ELLIPTICAL, W.PSF_TABLE], ids=["sep", "ellip", "table"])
+@pytest.mark.parametrize("shape", [dict(n_lambda=1, n_slit=1), dict(n_lambda=1, n_slit=40), dict(n_lambda=33, n_slit=1),
+                                   dict(n_lambda=5, n_slit=3, K=1)], ids=["1x1", "1x40", "33x1", "K1"])
+def test_degenerate_sizes_every_psf(renderer, psf, shape):
+    # single samples, single slit points and a one-pixel window, for every PSF kind and both
+    # precisions
+    kw = dict(seed=801, orders=2, fibers=1, slices=2)
+    kw.update(shape)
+    w = W.small_config(psf=psf if psf != W.PSF_TABLE else W.PSF_SEPARABLE, **kw)
+    if psf == W.PSF_TABLE:
+        w = W.Workload(w.name, W.with_psf_maps(w.model, oversample=6.0, half_px=6.0, n_field=3), w.spectra, "f32",
+                       "mixed")
+    ref = oracle_frames(w)
+    for g, o in zip(gpu_frames(renderer, w, "mixed", "f32"), ref):
+        assert compare(g, o).ok
+    for g, o in zip(gpu_frames(renderer, w, "fp64", "f64"), ref):
+        assert np.all(np.abs(g - o) <= FP64_REL * np.abs(o) + 1e-15 * max(np.abs(o).max(), 1e-300))
