@@ -135,6 +135,7 @@ struct e2e_ctx {
     uint64_t pattern_seed = 0;
     double prnu = 0.0;
     std::vector<double*> R;
+    std::vector<float*> R32;
   };
   std::map<uint64_t, NoisePattern> patterns;  // by model id
   // kernel timing of the most recent render (opts.kernel_timing)
@@ -838,8 +839,10 @@ void e2e_destroy(e2e_ctx* ctx) {
     for (auto& kv : ctx->models) free_model(kv.second.get());
     for (auto& kv : ctx->spectra) cudaFree(kv.second->d_flux);
     for (auto& kv : ctx->frames) free_frame(ctx, kv.second.get());
-    for (auto& kv : ctx->patterns)
+    for (auto& kv : ctx->patterns) {
       for (double* p : kv.second.R) cudaFree(p);
+      for (float* p : kv.second.R32) cudaFree(p);
+    }
     cudaStreamSynchronize(ctx->free_stream);
     cudaStreamDestroy(ctx->free_stream);
     cudaFree(ctx->d_err);
@@ -1010,6 +1013,7 @@ int e2e_unload_model(e2e_ctx* ctx, uint64_t model_id) {
   auto pt = ctx->patterns.find(model_id);
   if (pt != ctx->patterns.end()) {
     for (double* q : pt->second.R) cudaFree(q);
+    for (float* q : pt->second.R32) cudaFree(q);
     ctx->patterns.erase(pt);
   }
   return E2E_OK;
@@ -1737,32 +1741,40 @@ int e2e_add_noise(e2e_ctx* ctx, uint64_t model_id, const e2e_noise_params* p, in
   cudaStream_t st = (cudaStream_t)stream;
   // the pixel response is a fixed pattern: computed once per (model, pattern seed, prnu)
   std::vector<double*> R(m->n_det, nullptr);
+  std::vector<float*> R32(m->n_det, nullptr);
   if (p->prnu != 0.0) {
     auto& pat = ctx->patterns[model_id];
     if (pat.R.empty() || pat.pattern_seed != p->pattern_seed || pat.prnu != p->prnu) {
       cudaStreamSynchronize(st);  // a previous pattern may still be read
       for (double* q : pat.R) cudaFree(q);
+      for (float* q : pat.R32) cudaFree(q);
       pat.R.assign(m->n_det, nullptr);
+      pat.R32.assign(m->n_det, nullptr);
       pat.pattern_seed = p->pattern_seed;
       pat.prnu = p->prnu;
       for (int d = 0; d < m->n_det; ++d) {
-        cudaError_t e = cudaMalloc((void**)&pat.R[d], (size_t)m->H[d] * m->W[d] * sizeof(double));
-        if (e == cudaSuccess) e = launch_prnu_map(pat.R[d], m->H[d], m->W[d], d, p->pattern_seed, p->prnu, st);
+        const size_t npx = (size_t)m->H[d] * m->W[d];
+        cudaError_t e = cudaMalloc((void**)&pat.R[d], npx * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&pat.R32[d], npx * sizeof(float));
+        if (e == cudaSuccess)
+          e = launch_prnu_map(pat.R[d], pat.R32[d], m->H[d], m->W[d], d, p->pattern_seed, p->prnu, st);
         if (e != cudaSuccess) {
           for (double* q : pat.R) cudaFree(q);
+          for (float* q : pat.R32) cudaFree(q);
           ctx->patterns.erase(model_id);
           return cuda_fail(e, "pixel response map");
         }
       }
     }
     R = pat.R;
+    R32 = pat.R32;
   }
   for (int d = 0; d < m->n_det; ++d) {
     const int64_t sp = src_pitch ? src_pitch[d] : m->W[d], dp = dst_pitch ? dst_pitch[d] : m->W[d];
     KernelTimer kt(ctx, st, "noise");
     E2E_CK(launch_noise(p->seed, p->pattern_seed, p->dark_e, p->prnu, p->ron_e, p->xtalk, p->gain, p->bias,
-                        p->saturation, p->poisson, src_dtype, src[d], sp, R[d], dst_dtype, dst[d], dp, m->H[d],
-                        m->W[d], d, st));
+                        p->saturation, p->poisson, src_dtype, src[d], sp, R[d], R32[d], dst_dtype, dst[d], dp,
+                        m->H[d], m->W[d], d, st));
   }
   return E2E_OK;
 }

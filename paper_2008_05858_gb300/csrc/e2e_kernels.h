@@ -35,11 +35,12 @@ cudaError_t launch_render_fp64_ellip(int K, int n_slices, int64_t max_stamps, co
                                      const double* const* flux_tab, const double* u_all, double* const* acc,
                                      const int64_t* pitch, cudaStream_t st);
 
-cudaError_t launch_prnu_map(double* R, int H, int W, int det, uint64_t pattern_seed, double prnu, cudaStream_t st);
+cudaError_t launch_prnu_map(double* R, float* R32, int H, int W, int det, uint64_t pattern_seed, double prnu,
+                            cudaStream_t st);
 cudaError_t launch_noise(uint64_t seed, uint64_t pattern_seed, double dark, double prnu, double ron, double xtalk,
                          double gain, double bias, int saturation, int poisson, int src_dtype, const void* src,
-                         int64_t src_pitch, const double* R, int dst_dtype, void* dst, int64_t dst_pitch, int H, int W,
-                         int det, cudaStream_t st);
+                         int64_t src_pitch, const double* R, const float* R32, int dst_dtype, void* dst,
+                         int64_t dst_pitch, int H, int W, int det, cudaStream_t st);
 
 cudaError_t launch_epsf_build(const TableSlice* ts, int n_slices, int max_field, const double* maps, double* norms,
                               int P, double* T64, float* T32, cudaStream_t st);

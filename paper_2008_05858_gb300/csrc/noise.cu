@@ -35,50 +35,71 @@ struct NoiseArgs {
   uint64_t seed, pattern_seed;
   double dark, prnu, ron, xtalk, gain, bias;
   int saturation, poisson;
+  float dark32, inv_gain32;  // FP32 copies for the filtered path
 };
 
 // ------------------------------------------------------------------ kernels
 
 // Pixel response R = 1 + prnu z of every pixel (FP64, the fixed pattern; computed once per
 // model, pattern seed and prnu and kept by the library).
-__global__ void __launch_bounds__(256) k_prnu_map(double* R, int H, int W, int det, uint64_t pattern_seed, double prnu) {
+__global__ void __launch_bounds__(256) k_prnu_map(double* R, float* R32, int H, int W, int det, uint64_t pattern_seed,
+                                                  double prnu) {
   const int half = (W + 1) / 2;
   const int64_t n = (int64_t)H * half;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(t / half), c = (int)(t - (int64_t)r * half);
     double z0, z1;
     normal_pair(pattern_seed, (uint32_t)t, (uint32_t)det, 0, z0, z1);
-    R[(int64_t)r * W + c] = __dadd_rn(1.0, __dmul_rn(prnu, z0));
-    if (W - 1 - c != c) R[(int64_t)r * W + (W - 1 - c)] = __dadd_rn(1.0, __dmul_rn(prnu, z1));
+    const double r0 = __dadd_rn(1.0, __dmul_rn(prnu, z0)), r1 = __dadd_rn(1.0, __dmul_rn(prnu, z1));
+    R[(int64_t)r * W + c] = r0;
+    R32[(int64_t)r * W + c] = (float)r0;
+    if (W - 1 - c != c) {
+      R[(int64_t)r * W + (W - 1 - c)] = r1;
+      R32[(int64_t)r * W + (W - 1 - c)] = (float)r1;
+    }
   }
 }
-
-template <typename TI>
-__device__ __forceinline__ double load_px(const TI* p) { return (double)*p; }
 
 // One thread per mirror pair.  TO = double: electrons in FP64 (exact read-out noise);
 // float: electrons rounded to FP32 (FP32 read-out noise, within a few ulp of FP64);
 // uint16_t: ADU, exact (filtered, FP64 read-out noise where the rounding is too close).
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(256) k_noise(const NoiseArgs a, const TI* __restrict__ src, int64_t src_pitch,
-                                               const double* __restrict__ R, TO* dst, int64_t dst_pitch, int H, int W,
-                                               int det) {
+                                               const double* __restrict__ R, const float* __restrict__ R32, TO* dst,
+                                               int64_t dst_pitch, int H, int W, int det) {
   const int half = (W + 1) / 2;
   const int64_t n = (int64_t)H * half;
-  const float inv_gain = (float)(1.0 / a.gain);
+  const float inv_gain = a.inv_gain32;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(t / half), c = (int)(t - (int64_t)r * half);
     const uint32_t q = (uint32_t)t;
     const int cm = W - 1 - c;
     const bool two = cm != c;
     const TI* srow = src + (int64_t)r * src_pitch;
-    const double s0 = load_px(srow + c), s1 = two ? load_px(srow + cm) : 0.0;
-    const double R0 = R ? R[(int64_t)r * W + c] : 1.0, R1 = (R && two) ? R[(int64_t)r * W + cm] : 1.0;
-    double l0 = __dadd_rn(__dmul_rn(R0, s0), a.dark), l1 = __dadd_rn(__dmul_rn(R1, s1), a.dark);
-    l0 = l0 > 0.0 ? l0 : 0.0;
-    l1 = l1 > 0.0 ? l1 : 0.0;
-    const double n0 = a.poisson ? poisson_filtered(l0, a.seed, q, (uint32_t)det, 2) : l0;
-    const double n1 = (two && a.poisson) ? poisson_filtered(l1, a.seed, q, (uint32_t)det, 3) : l1;
+    const TI S0 = srow[c], S1 = two ? srow[cm] : (TI)0;
+    const int64_t i0 = (int64_t)r * W + c, i1 = (int64_t)r * W + cm;
+    // the mean lam = max(R S + dark, 0): exactly (FP64) when a decision needs it, else in FP32
+    auto lam_exact0 = [&]() {
+      const double l = __dadd_rn(__dmul_rn(R ? R[i0] : 1.0, (double)S0), a.dark);
+      return l > 0.0 ? l : 0.0;
+    };
+    auto lam_exact1 = [&]() {
+      const double l = __dadd_rn(__dmul_rn(R ? R[i1] : 1.0, (double)S1), a.dark);
+      return l > 0.0 ? l : 0.0;
+    };
+    double n0, n1 = 0.0;
+    if (a.poisson) {
+      const float rs0 = (R32 ? R32[i0] : 1.f) * (float)S0, rs1 = two ? (R32 ? R32[i1] : 1.f) * (float)S1 : 0.f;
+      const float l0 = rs0 + a.dark32, l1 = rs1 + a.dark32;
+      // |l - lam| <= 2.4e-7 (|R S| + dark): R and S rounded to FP32, one product, one sum (bound 6e-7)
+      const float le0 = 6e-7f * (fabsf(rs0) + fabsf(a.dark32)) + 1e-37f;
+      const float le1 = 6e-7f * (fabsf(rs1) + fabsf(a.dark32)) + 1e-37f;
+      n0 = poisson_f32mean(l0, le0, lam_exact0, a.seed, q, (uint32_t)det, 2);
+      if (two) n1 = poisson_f32mean(l1, le1, lam_exact1, a.seed, q, (uint32_t)det, 3);
+    } else {
+      n0 = lam_exact0();
+      n1 = two ? lam_exact1() : 0.0;
+    }
     TO* drow = dst + (int64_t)r * dst_pitch;
     if constexpr (sizeof(TO) == 8) {  // FP64 electrons: exact read-out noise
       double g0, g1;
@@ -137,29 +158,31 @@ static int64_t grid_blocks(int64_t n) {
 }
 
 template <typename TI, typename TO>
-static cudaError_t launch_noise_t(const NoiseArgs& a, const void* src, int64_t sp, const double* R, void* dst,
-                                  int64_t dp, int H, int W, int det, cudaStream_t st) {
+static cudaError_t launch_noise_t(const NoiseArgs& a, const void* src, int64_t sp, const double* R, const float* R32,
+                                  void* dst, int64_t dp, int H, int W, int det, cudaStream_t st) {
   const int64_t n = (int64_t)H * ((W + 1) / 2);
   if (n == 0) return cudaSuccess;
-  k_noise<TI, TO><<<(unsigned)grid_blocks(n), 256, 0, st>>>(a, (const TI*)src, sp, R, (TO*)dst, dp, H, W, det);
+  k_noise<TI, TO><<<(unsigned)grid_blocks(n), 256, 0, st>>>(a, (const TI*)src, sp, R, R32, (TO*)dst, dp, H, W, det);
   return cudaGetLastError();
 }
 
-cudaError_t launch_prnu_map(double* R, int H, int W, int det, uint64_t pattern_seed, double prnu, cudaStream_t st) {
+cudaError_t launch_prnu_map(double* R, float* R32, int H, int W, int det, uint64_t pattern_seed, double prnu,
+                            cudaStream_t st) {
   const int64_t n = (int64_t)H * ((W + 1) / 2);
   if (n == 0) return cudaSuccess;
-  k_prnu_map<<<(unsigned)grid_blocks(n), 256, 0, st>>>(R, H, W, det, pattern_seed, prnu);
+  k_prnu_map<<<(unsigned)grid_blocks(n), 256, 0, st>>>(R, R32, H, W, det, pattern_seed, prnu);
   return cudaGetLastError();
 }
 
 cudaError_t launch_noise(uint64_t seed, uint64_t pattern_seed, double dark, double prnu, double ron, double xtalk,
                          double gain, double bias, int saturation, int poisson, int src_dtype, const void* src,
-                         int64_t src_pitch, const double* R, int dst_dtype, void* dst, int64_t dst_pitch, int H, int W,
-                         int det, cudaStream_t st) {
-  const NoiseArgs a{seed, pattern_seed, dark, prnu, ron, xtalk, gain, bias, saturation, poisson};
+                         int64_t src_pitch, const double* R, const float* R32, int dst_dtype, void* dst,
+                         int64_t dst_pitch, int H, int W, int det, cudaStream_t st) {
+  const NoiseArgs a{seed, pattern_seed, dark, prnu, ron, xtalk, gain, bias, saturation, poisson, (float)dark,
+                    (float)(1.0 / gain)};
 #define E2E_N(SI, TI, DI, TO) \
   if (src_dtype == SI && dst_dtype == DI)  \
-    return launch_noise_t<TI, TO>(a, src, src_pitch, R, dst, dst_pitch, H, W, det, st);
+    return launch_noise_t<TI, TO>(a, src, src_pitch, R, R32, dst, dst_pitch, H, W, det, st);
   E2E_N(0, float, 0, float) E2E_N(0, float, 1, double) E2E_N(0, float, 2, uint16_t)
   E2E_N(1, double, 0, float) E2E_N(1, double, 1, double) E2E_N(1, double, 2, uint16_t)
 #undef E2E_N

@@ -119,27 +119,35 @@ __device__ __forceinline__ void normal_pair_f32(uint64_t seed, uint32_t q, uint3
 
 // Poisson draw with the exact function's integer result, from FP32 arithmetic whenever its
 // error bound decides every comparison (see the file comment).
+// Sequential-inversion Poisson draw in FP32 for a mean l known to relative accuracy lrel:
+// F_k within F (8.4e-7 + 2.4e-7 k) of the FP64 sums plus F (k + l) lrel for the mean's own
+// error, u within 2^-24 relative; all bounds doubled.  Returns the count, or -1 when some
+// comparison is too close to call (the caller then draws exactly).
+static __device__ double inversion_f32(float l, float lrel, uint64_t seed, uint32_t q, uint32_t d, uint32_t stream) {
+  const uint4 w = rng_block(seed, q, d, 0, stream);
+  const float u = uni53_f32(w.x, w.y);
+  float p = expf(-l), F = p;
+  for (int k = 0; k < 200; ++k) {
+    const float rel = fmaf(1e-6f, (float)k, 4e-6f) + 2.f * ((float)k + l) * lrel;
+    const float tol = fmaf(F, rel, fmaf(u, 2.5e-7f, 1e-12f));
+    const float diff = u - F;
+    if (diff > tol) {  // u > F_k: one more
+      p = p * (l / (float)(k + 1));
+      F = F + p;
+      continue;
+    }
+    if (-diff > tol) return (double)k;  // u <= F_k
+    return -1.0;
+  }
+  return 200.0;
+}
+
 static __device__ double poisson_filtered(double lam, uint64_t seed, uint32_t q, uint32_t d, uint32_t stream) {
   if (!(lam > 0.0)) return 0.0;
   const float l = __double2float_rn(lam);
   if (lam < 10.0) {
-    // F_k in FP32: exp(-l) within 2 ulp, l within 2^-24 relative, each step within ~3 ulp:
-    // |F32_k - F64_k| <= F (8.4e-7 + 2.4e-7 k); u within 2^-24 relative.  Bounds doubled.
-    const uint4 w = rng_block(seed, q, d, 0, stream);
-    const float u = uni53_f32(w.x, w.y);
-    float p = expf(-l), F = p;
-    for (int k = 0; k < 200; ++k) {
-      const float tol = fmaf(F, fmaf(1e-6f, (float)k, 4e-6f), fmaf(u, 2.5e-7f, 1e-12f));
-      const float diff = u - F;
-      if (diff > tol) {  // u > F_k: one more
-        p = p * (l / (float)(k + 1));
-        F = F + p;
-        continue;
-      }
-      if (-diff > tol) return (double)k;      // u <= F_k
-      return poisson_draw(lam, seed, q, d, stream);  // too close to call
-    }
-    return 200.0;
+    const double k = inversion_f32(l, 6e-8f, seed, q, d, stream);
+    return k >= 0.0 ? k : poisson_draw(lam, seed, q, d, stream);
   }
   // PTRS in FP32; k's final sum in FP64 (y + lam + 0.43), the rare slow acceptance in FP64
   const float sl = sqrtf(l);
@@ -188,6 +196,19 @@ static __device__ double poisson_filtered(double lam, uint64_t seed, uint32_t q,
     if (lhs <= rhs) return k;
   }
   return floor(__dadd_rn(lam, 0.5));
+}
+
+// Poisson draw whose mean is known in FP32 (l within le of it), with the exact mean computed
+// only when needed (lam_exact(): FP64, the definition's value): dim means never touch FP64.
+template <typename LamExact>
+static __device__ double poisson_f32mean(float l, float le, LamExact lam_exact, uint64_t seed, uint32_t q, uint32_t d,
+                                         uint32_t stream) {
+  if (l + le <= 0.f) return 0.0;  // the mean is <= 0: no photons
+  if (l - le > 0.f && l + le < 10.f) {
+    const double k = inversion_f32(l, le / l, seed, q, d, stream);
+    if (k >= 0.0) return k;
+  }
+  return poisson_filtered(lam_exact(), seed, q, d, stream);
 }
 
 }  // namespace e2e

@@ -145,9 +145,9 @@ struct TableArgs {
 };
 
 // One CTA per work item (<= 32 samples x <= 16 slit points); the warp's 32 stamps are mapped
-// into staging, then the (stamp, pixel) pairs of the batch are spread over the lanes: each
-// lane reads its pixel from the 8 tables around the stamp's phase and wavelength, blends, and
-// deposits into the item's box as exact fixed point.
+// into staging, then taken one after the other by the whole warp: each lane reads its pixels
+// from the 8 tables around the stamp's phase and wavelength, blends, and deposits into the
+// item's box as exact fixed point.
 template <int K>
 __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) {
   const MixedArgs& a = ta.m;
@@ -253,40 +253,44 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
     }
     __syncwarp();
     const int nb = min(32, nst - base);
-    const int npairs = nb * KK;
-    for (int p0 = 0; p0 < npairs; p0 += 32) {
-      const int p = p0 + lane;
-      if (p >= npairs) continue;
-      const int b = p / KK, e = p - b * KK;
+    // stamp by stamp (warp-uniform), each lane owning the pixels lane, lane + 32, ... of the
+    // window: the phase, the field weight and the 8 table rows are computed once per stamp,
+    // a pixel costs 8 coalesced table reads, 8 FMAs and its deposit
+    for (int b = 0; b < nb; ++b) {
       const int4 st = wst[b];
       if (st.x == kOffFrame || st.y == kOffFrame) continue;
-      const int n = e / K, m = e - n * K;
-      const int bx = st.x - K / 2 + m - it.bx0, by = st.y - K / 2 + n - it.by0;
-      if (bx < 0 || bx >= it.bw || by < 0 || by >= it.bh) {
-        if (a.err) {
-          const int X = it.bx0 + bx, Y = it.by0 + by;
-          if (X >= 0 && X < S.W && Y >= 0 && Y < S.H) atomicAdd(a.err, 1);
-        }
-        continue;
-      }
       const float2 sw = wsw[b];
       const int4 fw = tabF[__float_as_int(sw.y)];
       const float rx = (__int_as_float(st.z) + 0.5f) * (float)P, ry = (__int_as_float(st.w) + 0.5f) * (float)P;
       const int ipx = min(P - 1, max(0, (int)floorf(rx))), ipy = min(P - 1, max(0, (int)floorf(ry)));
       const float ax = rx - (float)ipx, ay = ry - (float)ipy;
-      const float wf1 = __int_as_float(fw.z);
-      float v = 0.f;
+      const float wf1 = __int_as_float(fw.z), wf0 = 1.f - wf1;
+      const float c00 = (1.f - ay) * (1.f - ax) * sw.x, c01 = (1.f - ay) * ax * sw.x;
+      const float c10 = ay * (1.f - ax) * sw.x, c11 = ay * ax * sw.x;
+      const int row = (ipy * (P + 1) + ipx) * KK, drow = (P + 1) * KK;
+      const float* A = T + (int64_t)fw.x * node_stride + row;  // node f0
+      const float* Bn = T + (int64_t)fw.y * node_stride + row; // node f1
+      const int bxs = st.x - K / 2 - it.bx0, bys = st.y - K / 2 - it.by0;
 #pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        const float we = side ? wf1 : 1.f - wf1;
-        const float* Tn = T + (int64_t)(side ? fw.y : fw.x) * node_stride + e;
-        const int r0 = (ipy * (P + 1) + ipx) * KK, r1 = r0 + (P + 1) * KK;
-        const float t = fmaf(1.f - ay, fmaf(1.f - ax, __ldg(Tn + r0), ax * __ldg(Tn + r0 + KK)),
-                             ay * fmaf(1.f - ax, __ldg(Tn + r1), ax * __ldg(Tn + r1 + KK)));
-        v = fmaf(we, t, v);
+      for (int i = 0; i < (KK + 31) / 32; ++i) {
+        const int e = lane + 32 * i;
+        if (e >= KK) break;
+        const int n = e / K, m = e - n * K;
+        const int bx = bxs + m, by = bys + n;
+        if (bx < 0 || bx >= it.bw || by < 0 || by >= it.bh) {
+          if (a.err) {
+            const int X = it.bx0 + bx, Y = it.by0 + by;
+            if (X >= 0 && X < S.W && Y >= 0 && Y < S.H) atomicAdd(a.err, 1);
+          }
+          continue;
+        }
+        const float t0 = fmaf(c00, __ldg(A + e), fmaf(c01, __ldg(A + e + KK),
+                         fmaf(c10, __ldg(A + e + drow), c11 * __ldg(A + e + drow + KK))));
+        const float t1 = fmaf(c00, __ldg(Bn + e), fmaf(c01, __ldg(Bn + e + KK),
+                         fmaf(c10, __ldg(Bn + e + drow), c11 * __ldg(Bn + e + drow + KK))));
+        const int q = by * it.bw + bx;
+        box_deposit(boxh + q, boxl + q, fmaf(wf0, t0, wf1 * t1), sc, sc_hi);
       }
-      const int q = by * it.bw + bx;
-      box_deposit(boxh + q, boxl + q, sw.x * v, sc, sc_hi);
     }
     __syncwarp();
   }
