@@ -10,8 +10,9 @@ One step = one render of the whole frame (mapping, PSF stamps, on-chip accumulat
 merge, frame write) through the C ABI.  ``value`` is stamps/s with the model and spectra
 resident in HBM, timed with CUDA events on the render stream; L2 is flushed between steps
 (a 256 MiB memset outside the timed events).  ``e2e`` is the same metric through the public
-API from pinned host memory: per step the spectra are uploaded (e2e_load_spectrum), the
-frame rendered into a library-owned buffer and fetched to pinned host memory.
+API from pinned host memory: per step the spectra are uploaded (e2e_load_spectrum) and the
+frame is rendered into pinned host memory (e2e_render_host: bands of rows are copied out as
+they finish, overlapping the render of the later bands).
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead (bounded sample of
 the same workload per step).  Under torchrun each rank renders its own detector frame
@@ -286,10 +287,10 @@ def run_gpu(args):
         ids = []
         for f, (orders, lens, flux) in pinned.items():
             ids.append(_load_spectrum_ptr(B, r.ctx, f, orders, lens, flux))
-        fid = B.e2e_render_alloc(r.ctx, mid, ids, B.E2E_PREC_MIXED, B.E2E_F32, stream)
-        B.e2e_fetch_frame(r.ctx, fid, 0, host_frame.data_ptr(), False, d2h, stream)
+        # rendered into pinned host memory: each finished band of rows is copied while the
+        # later bands still render
+        B.e2e_render_host(r.ctx, mid, ids, B.E2E_PREC_MIXED, B.E2E_F32, [host_frame.data_ptr()], None, stream)
         stream.synchronize()
-        B.e2e_release_frame(r.ctx, fid)
         for i in ids:
             B.e2e_unload_spectrum(r.ctx, i)
 
@@ -405,7 +406,7 @@ def photon_run(B, r, mid, sids, w, stream, flush, stamp_ms, reps=3):
     rate = rows[-1]["photons_per_s"]
     return {"runs": rows, "stamp_render_ms": stamp_ms,
             "photons_at_equal_cost": rate * stamp_ms * 1e-3,
-            "note": "photon Monte-Carlo (Sec. 2.2 alternative): FP64 mapping and Box-Muller per photon"}
+            "note": "photon Monte-Carlo (Sec. 2.2 alternative): FP32 mapping from per-bin FP64 anchors and FP32 Box-Muller, each pixel decision bounded, FP64 redo when too close; bit-exact counts"}
 
 
 def Bd_spec(sp, k):
@@ -471,7 +472,7 @@ def noise_run(B, r, mid, frame, stream, flush, reps=5):
     return {"ms": t, "pixels": px, "algorithmic_bytes": nbytes, "achieved_gbs": nbytes / (t * 1e-3) / 1e9,
             "hbm_peak_gbs": hbm, "frac_of_hbm": (nbytes / (t * 1e-3) / 1e9 / hbm) if hbm else None,
             "peak_source": kind, "params": params,
-            "note": "FP64 draws (Philox4x32-10, Box-Muller, PTRS Poisson) per pixel: FP64-ALU bound, not HBM"}
+            "note": "Philox4x32-10 draws per pixel in FP32 with error bounds (inversion, PTRS, Box-Muller, ADU rounding), FP64 only for decisions too close to call: bit-exact ADU; ALU-bound, not HBM"}
 
 
 def elliptical_run(B, dev, rank=0, world=1, reps=3, cpu_baseline=False):

@@ -188,6 +188,25 @@ int e2e_fetch_frame(e2e_ctx* ctx, uint64_t frame_id, int32_t detector, void* dst
                     size_t bytes, void* stream);
 int e2e_release_frame(e2e_ctx* ctx, uint64_t frame_id);
 
+/* Render every detector of `model` (as e2e_render) into HOST memory, overlapping the
+ * device-to-host copy with the render: the mixed-precision frame is rendered in up to 16
+ * bands of rows (whole merge tiles, the same fraction of every detector), and each band is
+ * copied to host_dst[d] as soon as its pixels are final, while later bands still render.
+ * The pixels equal those e2e_render writes for the same model and spectra.  E2E_PREC_FP64
+ * renders the whole frame first and then copies it.
+ *   host_dst[d]: host pointer to detector d's frame, row-major, dtype E2E_F32 or E2E_F64,
+ *                pitch_elems[d] elements between rows (pitch_elems may be NULL = width).
+ *                Page-locked memory (cudaHostAlloc / cudaHostRegister) lets the copies run
+ *                asynchronously; pageable memory is accepted, but then each band's copy
+ *                blocks the calling thread until that band is done.  Device memory is
+ *                rejected (E2E_EINVAL).
+ * The frame is complete when `stream` is.  Scratch (the device frame, box store) comes from
+ * the context, in stream order on `stream`; the library's own side streams wait for work
+ * enqueued on `stream` before the call and `stream` waits for them.
+ * Errors: E2E_EINVAL, E2E_ENOTFOUND, E2E_ENOMEM, E2E_ECUDA, E2E_EDEVICE (debug checks). */
+int e2e_render_host(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids, int32_t precision,
+                    int32_t dtype, void* const* host_dst, const int64_t* pitch_elems, void* stream);
+
 /* ------------------------------------------------------------------ differentiation */
 
 /* Gradient of a frame loss L with respect to the optical model, for calibration fitting:

@@ -130,6 +130,8 @@ _SIGS = {
     "e2e_unload_spectrum": ([C.c_void_p, C.c_uint64], C.c_int),
     "e2e_render": ([C.c_void_p, C.c_uint64, C.c_int32, C.POINTER(C.c_uint64), C.c_int32, C.c_int32,
                     C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.c_void_p], C.c_int),
+    "e2e_render_host": ([C.c_void_p, C.c_uint64, C.c_int32, C.POINTER(C.c_uint64), C.c_int32, C.c_int32,
+                         C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.c_void_p], C.c_int),
     "e2e_render_alloc": ([C.c_void_p, C.c_uint64, C.c_int32, C.POINTER(C.c_uint64), C.c_int32, C.c_int32,
                           C.c_void_p, C.POINTER(C.c_uint64)], C.c_int),
     "e2e_fetch_frame": ([C.c_void_p, C.c_uint64, C.c_int32, C.c_void_p, C.c_int32, C.c_size_t, C.c_void_p], C.c_int),
@@ -297,6 +299,18 @@ def e2e_render(ctx: int, model_id: int, spec_ids: Sequence[int], precision: int,
     pit = None if pitch_elems is None else (C.c_int64 * len(pitch_elems))(*pitch_elems)
     _check(load_library().e2e_render(C.c_void_p(ctx), model_id, n, sids, precision, dtype, dst, pit,
                                      C.c_void_p(_stream_handle(stream))))
+
+
+def e2e_render_host(ctx: int, model_id: int, spec_ids: Sequence[int], precision: int, dtype: int,
+                    host_ptrs: Sequence[int], pitch_elems: Optional[Sequence[int]] = None, stream=None) -> None:
+    """Render into host memory, the device-to-host copy of each finished band of rows
+    overlapping the render of the later bands; complete when ``stream`` is."""
+    n = len(spec_ids)
+    sids = (C.c_uint64 * max(n, 1))(*spec_ids)
+    dst = (C.c_void_p * len(host_ptrs))(*host_ptrs)
+    pit = None if pitch_elems is None else (C.c_int64 * len(pitch_elems))(*pitch_elems)
+    _check(load_library().e2e_render_host(C.c_void_p(ctx), model_id, n, sids, precision, dtype, dst, pit,
+                                          C.c_void_p(_stream_handle(stream))))
 
 
 def e2e_render_static(ctx: int, model_id: int, spec_ids: Sequence[int], dtype: int, dst_ptrs: Sequence[int],
@@ -508,6 +522,28 @@ class Renderer:
 
         td = torch.float32 if dtype == "f32" else torch.float64
         return [torch.empty((h, w), dtype=td, device=f"cuda:{self.device}") for h, w in self.models[mid].det_shape]
+
+    def render_host(self, mid: int, spec_ids: Sequence[int], precision: str = "mixed", dtype: str = "f32",
+                    out=None, stream=None, sync: bool = True):
+        """Frames rendered into page-locked host tensors (allocated when ``out`` is None), the
+        copies overlapping the render; waits for ``stream`` unless ``sync`` is False."""
+        import torch
+
+        if out is None:
+            td = torch.float32 if dtype == "f32" else torch.float64
+            out = [torch.empty((h, w), dtype=td).pin_memory() for h, w in self.models[mid].det_shape]
+        e2e_render_host(self.ctx, mid, spec_ids, PRECISION[precision], DTYPE[dtype],
+                        [int(t.data_ptr()) for t in out], [int(t.stride(0)) for t in out], stream)
+        if sync:
+            if stream is None:
+                torch.cuda.current_stream(self.device).synchronize()
+            elif hasattr(stream, "synchronize"):
+                stream.synchronize()
+            elif stream:
+                torch.cuda.ExternalStream(stream).synchronize()
+            else:
+                torch.cuda.synchronize(self.device)
+        return out
 
     # -------------------------------------------------------------- photon Monte-Carlo
     def render_photons(self, mid: int, spec_ids: Sequence[int], seed: int, out=None, stream=None,

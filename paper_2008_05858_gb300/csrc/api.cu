@@ -66,7 +66,17 @@ struct Plan {
     int K, first, count;
   };
   std::vector<Group> groups;
+  // y-bands: within each K group the items are ordered by the band of their box's first row,
+  // and the merge tiles by band, so band b of every detector is final once the items of bands
+  // <= b are rendered (no item reaches above its box)
+  int n_bands = 1;
+  std::vector<int> band_tile_rows;  // per detector: tile rows per band
+  std::vector<int> seg_first;       // [group * n_bands + band]: first item of the segment
+  std::vector<int> seg_count;
+  std::vector<int> tile_first;      // [n_bands + 1]: merge tiles of each band
 };
+
+constexpr int kBands = 16;  // y-bands of a frame rendered into host memory
 
 struct Model {
   int n_det = 0, psf = 0;
@@ -145,6 +155,11 @@ struct e2e_ctx {
   };
   std::vector<Timed> timed;
   std::vector<cudaEvent_t> event_pool;
+  // banded render into host memory (e2e_render_host): two render streams, a high-priority
+  // merge stream, a copy stream and per-band events, created on first use
+  cudaStream_t band_st[2] = {nullptr, nullptr};
+  cudaStream_t merge_st = nullptr, copy_st = nullptr;
+  std::vector<cudaEvent_t> band_ev;
 };
 
 namespace {
@@ -379,14 +394,87 @@ int build_psf_tables(Model* m, int P) {
   return rc;
 }
 
+// Bands and merge tiles of a planned model (every model, including one without slices, whose
+// tiles are all empty and merge to zeros).
+int plan_bands_and_tiles(Model* m) {
+  Plan& P = m->plan;
+  std::vector<int> tile_base(m->n_det + 1, 0);
+  std::vector<int> ntx(m->n_det), nty(m->n_det);
+  int max_ty = 1;
+  for (int d = 0; d < m->n_det; ++d) {
+    ntx[d] = (m->W[d] + kTileW - 1) / kTileW;
+    nty[d] = (m->H[d] + kTileH - 1) / kTileH;
+    tile_base[d + 1] = tile_base[d] + ntx[d] * nty[d];
+    max_ty = std::max(max_ty, nty[d]);
+  }
+
+  // ---- y-bands: order each K group's items by the band of their first row (stable, so the
+  // items of one band keep the slice-major order) and lay out their boxes in that order
+  P.n_bands = std::min(kBands, max_ty);
+  P.band_tile_rows.assign(m->n_det, 1);
+  for (int d = 0; d < m->n_det; ++d) P.band_tile_rows[d] = (nty[d] + P.n_bands - 1) / P.n_bands;
+  auto band_of = [&](const Item& it) {
+    const int d = m->slices[it.slice].d.detector;
+    return (it.by0 / kTileH) / P.band_tile_rows[d];
+  };
+  P.seg_first.assign(P.groups.size() * P.n_bands, 0);
+  P.seg_count.assign(P.groups.size() * P.n_bands, 0);
+  for (size_t g = 0; g < P.groups.size(); ++g) {
+    auto first = P.items.begin() + P.groups[g].first;
+    std::stable_sort(first, first + P.groups[g].count,
+                     [&](const Item& a, const Item& b) { return band_of(a) < band_of(b); });
+    for (int n = P.groups[g].first; n < P.groups[g].first + P.groups[g].count; ++n) {
+      const int b = band_of(P.items[n]);
+      if (P.seg_count[g * P.n_bands + b]++ == 0) P.seg_first[g * P.n_bands + b] = n;
+    }
+  }
+  {
+    int64_t off = 0;
+    for (auto& it : P.items) {
+      it.store_off = off;
+      off += (int64_t)it.bw * it.bh;
+    }
+  }
+
+  // ---- merge tiles: every tile of every detector, with the items overlapping it, in band order
+  std::vector<Tile> tiles;
+  std::vector<std::vector<int32_t>> lists;
+  lists.resize(tile_base[m->n_det]);
+  for (size_t n = 0; n < P.items.size(); ++n) {
+    const Item& it = P.items[n];
+    const int d = m->slices[it.slice].d.detector;
+    for (int ty = it.by0 / kTileH; ty <= (it.by0 + it.bh - 1) / kTileH; ++ty)
+      for (int tx = it.bx0 / kTileW; tx <= (it.bx0 + it.bw - 1) / kTileW; ++tx)
+        lists[tile_base[d] + ty * ntx[d] + tx].push_back((int32_t)n);
+  }
+  std::vector<int32_t> flat;
+  P.tile_first.clear();
+  for (int b = 0; b < P.n_bands; ++b) {
+    P.tile_first.push_back((int)tiles.size());
+    for (int d = 0; d < m->n_det; ++d)
+      for (int ty = b * P.band_tile_rows[d]; ty < std::min(nty[d], (b + 1) * P.band_tile_rows[d]); ++ty)
+        for (int tx = 0; tx < ntx[d]; ++tx) {
+          const auto& l = lists[tile_base[d] + ty * ntx[d] + tx];
+          Tile t{d, tx * kTileW, ty * kTileH, (int)l.size(), (int64_t)flat.size()};
+          flat.insert(flat.end(), l.begin(), l.end());
+          tiles.push_back(t);
+        }
+  }
+  P.tile_first.push_back((int)tiles.size());
+  P.n_tiles = (int)tiles.size();
+  int rc = upload(&P.d_items, P.items.data(), P.items.size());
+  if (rc == E2E_OK) rc = upload(&P.d_tiles, tiles.data(), tiles.size());
+  if (rc == E2E_OK) rc = upload(&P.d_lists, flat.data(), flat.size());
+  if (rc != E2E_OK) return rc;
+  P.ok = true;
+  return E2E_OK;
+}
+
 int plan_model(Model* m) {
   Plan& P = m->plan;
   const int ns = (int)m->slices.size();
   const bool ellip = m->psf != E2E_PSF_SEPARABLE;  // item shape of the non-separable kernels
-  if (ns == 0) {
-    P.ok = true;
-    return E2E_OK;
-  }
+  if (ns == 0) return plan_bands_and_tiles(m);
   // ---- device pass: exact window origins of every stamp
   std::vector<int64_t> task_off(ns + 1, 0), bb_off(ns + 1, 0);
   std::vector<int> n_jb(ns), n_k16(ns);
@@ -523,41 +611,7 @@ int plan_model(Model* m) {
                                   std::to_string(P.max_area) + " px)");
   }
   P.NB = 1;
-
-  // ---- merge tiles: every tile of every detector, with the items overlapping it
-  std::vector<Tile> tiles;
-  std::vector<std::vector<int32_t>> lists;
-  std::vector<int> tile_base(m->n_det + 1, 0);
-  std::vector<int> ntx(m->n_det), nty(m->n_det);
-  for (int d = 0; d < m->n_det; ++d) {
-    ntx[d] = (m->W[d] + kTileW - 1) / kTileW;
-    nty[d] = (m->H[d] + kTileH - 1) / kTileH;
-    tile_base[d + 1] = tile_base[d] + ntx[d] * nty[d];
-  }
-  lists.resize(tile_base[m->n_det]);
-  for (size_t n = 0; n < P.items.size(); ++n) {
-    const Item& it = P.items[n];
-    const int d = m->slices[it.slice].d.detector;
-    for (int ty = it.by0 / kTileH; ty <= (it.by0 + it.bh - 1) / kTileH; ++ty)
-      for (int tx = it.bx0 / kTileW; tx <= (it.bx0 + it.bw - 1) / kTileW; ++tx)
-        lists[tile_base[d] + ty * ntx[d] + tx].push_back((int32_t)n);
-  }
-  std::vector<int32_t> flat;
-  for (int d = 0; d < m->n_det; ++d)
-    for (int ty = 0; ty < nty[d]; ++ty)
-      for (int tx = 0; tx < ntx[d]; ++tx) {
-        const auto& l = lists[tile_base[d] + ty * ntx[d] + tx];
-        Tile t{d, tx * kTileW, ty * kTileH, (int)l.size(), (int64_t)flat.size()};
-        flat.insert(flat.end(), l.begin(), l.end());
-        tiles.push_back(t);
-      }
-  P.n_tiles = (int)tiles.size();
-  rc = upload(&P.d_items, P.items.data(), P.items.size());
-  if (rc == E2E_OK) rc = upload(&P.d_tiles, tiles.data(), tiles.size());
-  if (rc == E2E_OK) rc = upload(&P.d_lists, flat.data(), flat.size());
-  if (rc != E2E_OK) return rc;
-  P.ok = true;
-  return E2E_OK;
+  return plan_bands_and_tiles(m);
 }
 
 // ------------------------------------------------------------------ render
@@ -652,6 +706,21 @@ int blaze_scratch(Model* m, std::vector<const double*>& table, Scratch& sc, cuda
   return blaze_into(m, table, out, d_in, st);
 }
 
+// Render items [first, first + count) of the model's plan (all of PSF width K) into the box
+// store, on `st`.
+cudaError_t launch_items(e2e_ctx* ctx, Model* m, int K, int first, int count, const double** d_table, float2* store,
+                         cudaStream_t st) {
+  const Plan& P = m->plan;
+  if (m->psf == E2E_PSF_TABLE)
+    return launch_render_table(K, m->d_slices, m->d_ts, m->d_T32, m->d_field, m->phases, d_table, m->d_u,
+                               P.d_items + first, count, store, P.nk_max, P.max_deg, P.smem, st, ctx->d_err);
+  if (m->psf == E2E_PSF_ELLIPTICAL)
+    return launch_render_ellip(K, m->d_slices, d_table, m->d_u, P.d_items + first, count, store, P.nk_max,
+                               P.max_deg, P.smem, st, ctx->d_err);
+  return launch_render_mixed(K, P.DX, P.DY, m->d_slices, d_table, m->d_u, P.d_items + first, count, store, P.B,
+                             P.JB, P.nk_max, P.max_deg, P.smem, st, ctx->d_err);
+}
+
 int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, int precision, int dtype,
                 void* const* dst, const int64_t* pitch_in, cudaStream_t st) {
   if (dtype != E2E_F32 && dtype != E2E_F64) return fail(E2E_EINVAL, "dtype must be E2E_F32 or E2E_F64");
@@ -733,15 +802,7 @@ int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, in
   if (ctx->d_err) E2E_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
   for (auto& g : P.groups) {
     KernelTimer kt(ctx, st, tab ? "render_table" : ellip ? "render_ellip" : "render_mixed");
-    if (tab)
-      E2E_CK(launch_render_table(g.K, m->d_slices, m->d_ts, m->d_T32, m->d_field, m->phases, d_table, m->d_u,
-                                 P.d_items + g.first, g.count, store, P.nk_max, P.max_deg, P.smem, st, ctx->d_err));
-    else if (ellip)
-      E2E_CK(launch_render_ellip(g.K, m->d_slices, d_table, m->d_u, P.d_items + g.first, g.count, store, P.nk_max,
-                                 P.max_deg, P.smem, st, ctx->d_err));
-    else
-      E2E_CK(launch_render_mixed(g.K, P.DX, P.DY, m->d_slices, d_table, m->d_u, P.d_items + g.first, g.count,
-                                 store, P.B, P.JB, P.nk_max, P.max_deg, P.smem, st, ctx->d_err));
+    E2E_CK(launch_items(ctx, m, g.K, g.first, g.count, d_table, store, st));
   }
   {
     KernelTimer kt(ctx, st, "merge");
@@ -753,6 +814,111 @@ int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, in
     E2E_CK(cudaStreamSynchronize(st));
     if (n_bad) return fail(E2E_EDEVICE, std::to_string(n_bad) + " deposits fell outside the planned boxes");
   }
+  return E2E_OK;
+}
+
+// Streams and events of the banded host render, created once per context.
+int ensure_band_streams(e2e_ctx* ctx) {
+  if (ctx->copy_st) return E2E_OK;
+  int lo = 0, hi = 0;
+  E2E_CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  for (cudaStream_t& s : ctx->band_st) E2E_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  E2E_CK(cudaStreamCreateWithPriority(&ctx->merge_st, cudaStreamNonBlocking, hi));
+  E2E_CK(cudaStreamCreateWithFlags(&ctx->copy_st, cudaStreamNonBlocking));
+  ctx->band_ev.assign(1 + 2 * kBands + 4, nullptr);  // fork, per band rendered / merged, 4 stream ends
+  for (cudaEvent_t& e : ctx->band_ev) E2E_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  return E2E_OK;
+}
+
+// Rows [r0, r1) of detector d that belong to band b of the plan.
+void band_rows(const Model* m, int d, int b, int& r0, int& r1) {
+  const int rows = m->plan.band_tile_rows[d] * kTileH;
+  r0 = std::min(m->H[d], b * rows);
+  r1 = std::min(m->H[d], (b + 1) * rows);
+}
+
+// Mixed-precision render into host memory, band by band: the items of band b render on one of
+// two streams (consecutive bands alternate, so one band's last CTAs overlap the next band's
+// first), the merge of band b's tiles follows on a high-priority stream once the bands <= b
+// are rendered, and the copy of band b's rows to the host follows on a copy stream, while
+// later bands still render.  The frame is the one e2e_render writes: same items, same order.
+int render_host_banded(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, int dtype, void* const* host,
+                       const std::vector<int64_t>& pitch, cudaStream_t st) {
+  Plan& P = m->plan;
+  if (!P.ok) return fail(E2E_EINVAL, "model has no mixed-precision plan");
+  std::vector<const double*> table;
+  int rc = resolve_flux(ctx, m, n_spec, spec_ids, table);
+  if (rc != E2E_OK) return rc;
+  rc = ensure_band_streams(ctx);
+  if (rc != E2E_OK) return rc;
+  const size_t es = dtype == E2E_F32 ? 4 : 8;
+  Scratch sc{{}, st};
+  rc = blaze_scratch(m, table, sc, st);
+  if (rc != E2E_OK) return rc;
+  std::vector<void*> frame(m->n_det);
+  std::vector<int64_t> fpitch(m->W.begin(), m->W.end());
+  for (int d = 0; d < m->n_det; ++d) E2E_CK(sc.get(&frame[d], (size_t)m->H[d] * m->W[d] * es));
+  const double** d_table = nullptr;
+  int64_t* d_pitch = nullptr;
+  void** d_dst = nullptr;
+  float2* store = nullptr;
+  E2E_CK(sc.get((void**)&d_table, table.size() * sizeof(double*)));
+  E2E_CK(sc.get((void**)&d_pitch, fpitch.size() * sizeof(int64_t)));
+  E2E_CK(sc.get((void**)&d_dst, m->n_det * sizeof(void*)));
+  E2E_CK(sc.get((void**)&store, (size_t)P.store_elems * sizeof(float2)));
+  E2E_CK(cudaMemcpyAsync(d_table, table.data(), table.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
+  E2E_CK(cudaMemcpyAsync(d_pitch, fpitch.data(), fpitch.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  E2E_CK(cudaMemcpyAsync(d_dst, frame.data(), m->n_det * sizeof(void*), cudaMemcpyHostToDevice, st));
+  if (ctx->d_err) E2E_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
+
+  // events: [0] fork, [1 + b] band b rendered, [1 + kBands + b] band b merged, then the
+  // ends of the two render streams, the merge stream and the copy stream
+  cudaEvent_t* ev = ctx->band_ev.data();
+  cudaStream_t R[2] = {ctx->band_st[0], ctx->band_st[1]}, M = ctx->merge_st, C = ctx->copy_st;
+  E2E_CK(cudaEventRecord(ev[0], st));
+  for (cudaStream_t s : {R[0], R[1], M, C}) E2E_CK(cudaStreamWaitEvent(s, ev[0], 0));
+  // From here on `st` must wait for the side streams before the scratch is released, on
+  // every return path (an error path joins in the destructor, its own errors then moot).
+  struct Join {
+    cudaStream_t st, side[4];
+    cudaEvent_t* end;
+    bool done = false;
+    cudaError_t run() {
+      done = true;
+      for (int i = 0; i < 4; ++i) {
+        cudaError_t e = cudaEventRecord(end[i], side[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, end[i], 0);
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    }
+    ~Join() {
+      if (!done) run();
+    }
+  } join{st, {R[0], R[1], M, C}, ev + 1 + 2 * kBands};
+  const int nb = P.n_bands;
+  for (int b = 0; b < nb; ++b) {
+    cudaStream_t r = R[b & 1];
+    for (size_t g = 0; g < P.groups.size(); ++g) {
+      const int cnt = P.seg_count[g * nb + b];
+      if (cnt) E2E_CK(launch_items(ctx, m, P.groups[g].K, P.seg_first[g * nb + b], cnt, d_table, store, r));
+    }
+    E2E_CK(cudaEventRecord(ev[1 + b], r));
+    E2E_CK(cudaStreamWaitEvent(M, ev[1 + b], 0));  // bands < b: waited for by earlier merges
+    E2E_CK(launch_merge(P.d_tiles + P.tile_first[b], P.tile_first[b + 1] - P.tile_first[b], P.d_lists, P.d_items,
+                        store, d_dst, dtype, d_pitch, m->d_dims, M));
+    E2E_CK(cudaEventRecord(ev[1 + kBands + b], M));
+    E2E_CK(cudaStreamWaitEvent(C, ev[1 + kBands + b], 0));
+    for (int d = 0; d < m->n_det; ++d) {
+      int r0, r1;
+      band_rows(m, d, b, r0, r1);
+      if (r1 > r0)
+        E2E_CK(cudaMemcpy2DAsync(static_cast<char*>(host[d]) + (size_t)r0 * pitch[d] * es, (size_t)pitch[d] * es,
+                                 static_cast<const char*>(frame[d]) + (size_t)r0 * m->W[d] * es, (size_t)m->W[d] * es,
+                                 (size_t)m->W[d] * es, (size_t)(r1 - r0), cudaMemcpyDeviceToHost, C));
+    }
+  }
+  E2E_CK(join.run());
   return E2E_OK;
 }
 
@@ -848,6 +1014,9 @@ void e2e_destroy(e2e_ctx* ctx) {
     cudaFree(ctx->d_err);
     reset_timing(ctx);
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->band_ev) cudaEventDestroy(e);
+    for (cudaStream_t s : {ctx->band_st[0], ctx->band_st[1], ctx->merge_st, ctx->copy_st})
+      if (s) cudaStreamDestroy(s);
   }
   delete ctx;
 }
@@ -981,6 +1150,12 @@ int e2e_load_model(e2e_ctx* ctx, const e2e_model_desc* desc, uint64_t* model_id)
         o[E2E_MAXC] = (float)qb;
         o[E2E_MAXC + 1] = (float)sb;
       }
+      float* e = cf.data() + i * nf + 2 * (E2E_MAXC + 2);  // sigma_x, sigma_y, slit-weight total
+      for (int k = 0; k < 3; ++k) {
+        e[k] = (float)v.sx[k];
+        e[3 + k] = (float)v.sy[k];
+      }
+      e[6] = (float)usum[i];
     }
     if (rc == E2E_OK) rc = upload(&m->d_ucum32, ucum32.data(), ucum32.size());
     if (rc == E2E_OK) rc = upload(&m->d_cf32, cf.data(), cf.size());
@@ -1101,6 +1276,51 @@ int e2e_fetch_frame(e2e_ctx* ctx, uint64_t frame_id, int32_t detector, void* dst
   E2E_CK(cudaMemcpyAsync(dst, f->ptrs[detector], bytes, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                          (cudaStream_t)stream));
   E2E_CK(cudaEventRecord(f->ready, (cudaStream_t)stream));
+  return E2E_OK;
+}
+
+int e2e_render_host(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids, int32_t precision,
+                    int32_t dtype, void* const* host_dst, const int64_t* pitch_elems, void* stream) {
+  if (!ctx || !host_dst) return fail(E2E_EINVAL, "null argument");
+  if (dtype != E2E_F32 && dtype != E2E_F64) return fail(E2E_EINVAL, "dtype must be E2E_F32 or E2E_F64");
+  if (precision != E2E_PREC_MIXED && precision != E2E_PREC_FP64) return fail(E2E_EINVAL, "bad precision");
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Model* m = find_model(ctx, model_id);
+  if (!m) return fail(E2E_ENOTFOUND, "unknown model id");
+  std::vector<int64_t> pitch(m->n_det);
+  for (int d = 0; d < m->n_det; ++d) {
+    if (!host_dst[d]) return fail(E2E_EINVAL, "null destination frame");
+    pitch[d] = pitch_elems ? pitch_elems[d] : m->W[d];
+    if (pitch[d] < m->W[d]) return fail(E2E_EINVAL, "pitch smaller than width");
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, host_dst[d]) == cudaSuccess) {
+      if (at.type == cudaMemoryTypeDevice) return fail(E2E_EINVAL, "destination is device memory (use e2e_render)");
+    } else {
+      cudaGetLastError();  // an unknown host pointer is host memory
+    }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t es = dtype == E2E_F32 ? 4 : 8;
+  if (precision == E2E_PREC_FP64) {  // render whole, then copy
+    Scratch sc{{}, st};
+    std::vector<void*> frame(m->n_det);
+    for (int d = 0; d < m->n_det; ++d) E2E_CK(sc.get(&frame[d], (size_t)m->H[d] * m->W[d] * es));
+    int rc = render_impl(ctx, m, n_spec, spec_ids, precision, dtype, frame.data(), nullptr, st);
+    if (rc != E2E_OK) return rc;
+    for (int d = 0; d < m->n_det; ++d)
+      E2E_CK(cudaMemcpy2DAsync(host_dst[d], (size_t)pitch[d] * es, frame[d], (size_t)m->W[d] * es,
+                               (size_t)m->W[d] * es, (size_t)m->H[d], cudaMemcpyDeviceToHost, st));
+    return E2E_OK;
+  }
+  int rc = render_host_banded(ctx, m, n_spec, spec_ids, dtype, host_dst, pitch, st);
+  if (rc != E2E_OK) return rc;
+  if (ctx->d_err) {  // debug checks: wait for the render and report unplanned deposits
+    int n_bad = 0;
+    E2E_CK(cudaMemcpyAsync(&n_bad, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    E2E_CK(cudaStreamSynchronize(st));
+    if (n_bad) return fail(E2E_EDEVICE, std::to_string(n_bad) + " deposits fell outside the planned boxes");
+  }
   return E2E_OK;
 }
 

@@ -35,7 +35,7 @@ struct NoiseArgs {
   uint64_t seed, pattern_seed;
   double dark, prnu, ron, xtalk, gain, bias;
   int saturation, poisson;
-  float dark32, inv_gain32;  // FP32 copies for the filtered path
+  float dark32, inv_gain32, ron32, xtalk32, bias32, sat32;  // FP32 copies for the filtered path
 };
 
 // ------------------------------------------------------------------ kernels
@@ -68,10 +68,10 @@ __global__ void __launch_bounds__(256) k_noise(const NoiseArgs a, const TI* __re
                                                const double* __restrict__ R, const float* __restrict__ R32, TO* dst,
                                                int64_t dst_pitch, int H, int W, int det) {
   const int half = (W + 1) / 2;
-  const int64_t n = (int64_t)H * half;
+  const int n = H * half;  // < 2^31 (the launcher checks)
   const float inv_gain = a.inv_gain32;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t / half), c = (int)(t - (int64_t)r * half);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int r = t / half, c = t - r * half;
     const uint32_t q = (uint32_t)t;
     const int cm = W - 1 - c;
     const bool two = cm != c;
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) k_noise(const NoiseArgs a, const TI* __re
       const double l = __dadd_rn(__dmul_rn(R ? R[i1] : 1.0, (double)S1), a.dark);
       return l > 0.0 ? l : 0.0;
     };
-    double n0, n1 = 0.0;
+    Count n0, n1{0, 0.0};
     if (a.poisson) {
       const float rs0 = (R32 ? R32[i0] : 1.f) * (float)S0, rs1 = two ? (R32 ? R32[i1] : 1.f) * (float)S1 : 0.f;
       const float l0 = rs0 + a.dark32, l1 = rs1 + a.dark32;
@@ -97,34 +97,34 @@ __global__ void __launch_bounds__(256) k_noise(const NoiseArgs a, const TI* __re
       n0 = poisson_f32mean(l0, le0, lam_exact0, a.seed, q, (uint32_t)det, 2);
       if (two) n1 = poisson_f32mean(l1, le1, lam_exact1, a.seed, q, (uint32_t)det, 3);
     } else {
-      n0 = lam_exact0();
-      n1 = two ? lam_exact1() : 0.0;
+      n0 = Count{-1, lam_exact0()};
+      n1 = Count{-1, two ? lam_exact1() : 0.0};
     }
     TO* drow = dst + (int64_t)r * dst_pitch;
     if constexpr (sizeof(TO) == 8) {  // FP64 electrons: exact read-out noise
       double g0, g1;
       normal_pair(a.seed, q, (uint32_t)det, 1, g0, g1);
-      const double m0 = two ? __dadd_rn(n0, __dmul_rn(a.xtalk, n1)) : __dadd_rn(n0, 0.0);
+      const double m0 = two ? __dadd_rn(n0.f64(), __dmul_rn(a.xtalk, n1.f64())) : __dadd_rn(n0.f64(), 0.0);
       drow[c] = (TO)__dadd_rn(m0, __dmul_rn(a.ron, g0));
-      if (two) drow[cm] = (TO)__dadd_rn(__dadd_rn(n1, __dmul_rn(a.xtalk, n0)), __dmul_rn(a.ron, g1));
+      if (two) drow[cm] = (TO)__dadd_rn(__dadd_rn(n1.f64(), __dmul_rn(a.xtalk, n0.f64())), __dmul_rn(a.ron, g1));
     } else {
       float g0, g1, eg;
       normal_pair_f32(a.seed, q, (uint32_t)det, 1, g0, g1, eg);
-      const float ron = (float)a.ron, xt = (float)a.xtalk;
-      const float e0 = fmaf(ron, g0, fmaf(xt, two ? (float)n1 : 0.f, (float)n0));
-      const float e1 = fmaf(ron, g1, fmaf(xt, (float)n0, (float)n1));
+      const float ron = a.ron32, xt = a.xtalk32, nf0 = n0.f32(), nf1 = n1.f32();
+      const float e0 = fmaf(ron, g0, fmaf(xt, two ? nf1 : 0.f, nf0));
+      const float e1 = fmaf(ron, g1, fmaf(xt, nf0, nf1));
       if constexpr (sizeof(TO) == 4) {
         drow[c] = (TO)e0;
         if (two) drow[cm] = (TO)e1;
       } else {  // ADU = clamp(floor((bias + E / gain) + 1/2)), decided exactly
-        const float ig = inv_gain, bias = (float)a.bias;
+        const float ig = inv_gain, bias = a.bias32;
         bool exact = false;
         float t[2] = {fmaf(e0, ig, bias) + 0.5f, fmaf(e1, ig, bias) + 0.5f};
         const float ee[2] = {e0, e1};
         float v[2];
 #pragma unroll
         for (int s2 = 0; s2 < 2; ++s2) {
-          const float xn = fabsf(xt) * (float)(s2 ? n0 : n1);
+          const float xn = fabsf(xt) * (s2 ? nf0 : nf1);
           const float mt = fmaf(fmaf(fabsf(ee[s2]), 4e-7f, fmaf(fabsf(ron), eg, xn * 2e-7f)), ig,
                                 fmaf(fabsf(t[s2]), 4e-7f, 1e-6f));
           const float lo = floorf(t[s2] - mt);
@@ -134,15 +134,16 @@ __global__ void __launch_bounds__(256) k_noise(const NoiseArgs a, const TI* __re
         if (exact) {  // too close to a rounding boundary: FP64 read-out noise, as the definition
           double g0d, g1d;
           normal_pair(a.seed, q, (uint32_t)det, 1, g0d, g1d);
-          const double m0 = two ? __dadd_rn(n0, __dmul_rn(a.xtalk, n1)) : __dadd_rn(n0, 0.0);
-          const double m1 = __dadd_rn(n1, __dmul_rn(a.xtalk, n0));
+          const double d0 = n0.f64(), d1 = n1.f64();
+          const double m0 = two ? __dadd_rn(d0, __dmul_rn(a.xtalk, d1)) : __dadd_rn(d0, 0.0);
+          const double m1 = __dadd_rn(d1, __dmul_rn(a.xtalk, d0));
           // clamped to [-1, 65536] first: integers there are exact in FP32
           const double vd0 = floor(__dadd_rn(__dadd_rn(a.bias, __ddiv_rn(__dadd_rn(m0, __dmul_rn(a.ron, g0d)), a.gain)), 0.5));
           const double vd1 = floor(__dadd_rn(__dadd_rn(a.bias, __ddiv_rn(__dadd_rn(m1, __dmul_rn(a.ron, g1d)), a.gain)), 0.5));
           v[0] = (float)fmin(fmax(vd0, -1.0), 65536.0);
           v[1] = (float)fmin(fmax(vd1, -1.0), 65536.0);
         }
-        const float sat = (float)a.saturation;
+        const float sat = a.sat32;
 #pragma unroll
         for (int s2 = 0; s2 < 2; ++s2) v[s2] = fminf(fmaxf(v[s2], 0.f), sat);
         drow[c] = (TO)v[0];
@@ -162,6 +163,7 @@ static cudaError_t launch_noise_t(const NoiseArgs& a, const void* src, int64_t s
                                   void* dst, int64_t dp, int H, int W, int det, cudaStream_t st) {
   const int64_t n = (int64_t)H * ((W + 1) / 2);
   if (n == 0) return cudaSuccess;
+  if (n > INT32_MAX - 256 * grid_blocks(n)) return cudaErrorInvalidValue;  // the kernel indexes in 32 bits
   k_noise<TI, TO><<<(unsigned)grid_blocks(n), 256, 0, st>>>(a, (const TI*)src, sp, R, R32, (TO*)dst, dp, H, W, det);
   return cudaGetLastError();
 }
@@ -178,8 +180,9 @@ cudaError_t launch_noise(uint64_t seed, uint64_t pattern_seed, double dark, doub
                          double gain, double bias, int saturation, int poisson, int src_dtype, const void* src,
                          int64_t src_pitch, const double* R, const float* R32, int dst_dtype, void* dst,
                          int64_t dst_pitch, int H, int W, int det, cudaStream_t st) {
-  const NoiseArgs a{seed, pattern_seed, dark, prnu, ron, xtalk, gain, bias, saturation, poisson, (float)dark,
-                    (float)(1.0 / gain)};
+  const NoiseArgs a{seed,        pattern_seed, dark,        prnu,        ron,         xtalk,
+                    gain,        bias,         saturation,  poisson,     (float)dark, (float)(1.0 / gain),
+                    (float)ron,  (float)xtalk, (float)bias, (float)saturation};
 #define E2E_N(SI, TI, DI, TO) \
   if (src_dtype == SI && dst_dtype == DI)  \
     return launch_noise_t<TI, TO>(a, src, src_pitch, R, R32, dst, dst_pitch, H, W, det, st);

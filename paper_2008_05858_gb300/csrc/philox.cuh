@@ -86,19 +86,24 @@ static __device__ double poisson_draw(double lam, uint64_t seed, uint32_t q, uin
 
 // ------------------------------------------------------------------ FP32 filtered draws
 
-// fl32 of the 53-bit uniform u = (2X + 1) 2^-54, X = (a >> 5) 2^26 + (b >> 6) (correctly
-// rounded: one conversion of the exact integer), and fl32 of 1 - u.
-__device__ __forceinline__ uint64_t uni53_num(uint32_t a, uint32_t b) {
-  return ((((uint64_t)(a >> 5) << 26) | (uint64_t)(b >> 6)) << 1) | 1ull;
+// The 53-bit uniform u = A 2^-27 + (B + 1/2) 2^-53, A = a >> 5 (27 bits), B = b >> 6 (26 bits),
+// in FP32 from two 32-bit conversions and two FMAs: the conversion of A, the conversion of B
+// and each FMA round once, so |fl - u| <= 2^-23 u (+ a term below 2^-77).  And 1 - u, which
+// has the same form with A' = 2^27 - 1 - A, B' = 2^26 - 1 - B, so it keeps its relative
+// accuracy as u approaches 1.  (No 64-bit integer arithmetic: the FP32 samplers never touch
+// the FP64 unit.)
+__device__ __forceinline__ float uni53_parts_f32(uint32_t A, uint32_t B) {
+  return fmaf(__uint2float_rn(A), 0x1p-27f, fmaf(__uint2float_rn(B), 0x1p-53f, 0x1p-54f));
 }
-__device__ __forceinline__ float uni53_f32(uint32_t a, uint32_t b) { return __ull2float_rn(uni53_num(a, b)) * 0x1p-54f; }
+__device__ __forceinline__ float uni53_f32(uint32_t a, uint32_t b) { return uni53_parts_f32(a >> 5, b >> 6); }
 __device__ __forceinline__ float one_minus_uni53_f32(uint32_t a, uint32_t b) {
-  return __ull2float_rn((1ull << 54) - uni53_num(a, b)) * 0x1p-54f;
+  return uni53_parts_f32(0x7FFFFFFu - (a >> 5), 0x3FFFFFFu - (b >> 6));
 }
 
 // Box-Muller pair in FP32 and a bound eg on |g - g_exact| for both members: ln u from logf
-// (u < 1/2) or log1pf(-(1 - u)) (u >= 1/2), each within 1 ulp of a correctly rounded
-// argument; the phase from sincospif(2u) (1 ulp) with 2u exact.
+// (u < 1/2) or log1pf(-(1 - u)) (u >= 1/2), 1 ulp, of an argument within 2^-23 relative; the
+// phase from sincospif(2u), 1 ulp, whose argument is within 2.4e-7 u of 2u (a phase error
+// below 7.5e-7 rho in g).  Summed: |g - g_exact| < 1.1e-6 rho + 1e-7.
 __device__ __forceinline__ void normal_pair_f32_ctr(uint64_t seed, uint32_t q, uint32_t d, uint32_t i,
                                                     uint32_t stream, float& g0, float& g1, float& eg) {
   const uint4 w = rng_block(seed, q, d, i, stream);
@@ -109,7 +114,7 @@ __device__ __forceinline__ void normal_pair_f32_ctr(uint64_t seed, uint32_t q, u
   sincospif(2.f * uni53_f32(w.z, w.w), &s, &c);
   g0 = rho * c;
   g1 = rho * s;
-  eg = fmaf(rho, 1.5e-6f, 1e-7f);  // also covers a 2e-7 relative rounding of products with g
+  eg = fmaf(rho, 2e-6f, 1e-7f);  // also covers a 2e-7 relative rounding of products with g
 }
 
 __device__ __forceinline__ void normal_pair_f32(uint64_t seed, uint32_t q, uint32_t d, uint32_t stream, float& g0,
@@ -121,9 +126,9 @@ __device__ __forceinline__ void normal_pair_f32(uint64_t seed, uint32_t q, uint3
 // error bound decides every comparison (see the file comment).
 // Sequential-inversion Poisson draw in FP32 for a mean l known to relative accuracy lrel:
 // F_k within F (8.4e-7 + 2.4e-7 k) of the FP64 sums plus F (k + l) lrel for the mean's own
-// error, u within 2^-24 relative; all bounds doubled.  Returns the count, or -1 when some
+// error, u within 2^-23 relative; all bounds doubled.  Returns the count, or -1 when some
 // comparison is too close to call (the caller then draws exactly).
-static __device__ double inversion_f32(float l, float lrel, uint64_t seed, uint32_t q, uint32_t d, uint32_t stream) {
+static __device__ int inversion_f32(float l, float lrel, uint64_t seed, uint32_t q, uint32_t d, uint32_t stream) {
   const uint4 w = rng_block(seed, q, d, 0, stream);
   const float u = uni53_f32(w.x, w.y);
   float p = expf(-l), F = p;
@@ -136,18 +141,18 @@ static __device__ double inversion_f32(float l, float lrel, uint64_t seed, uint3
       F = F + p;
       continue;
     }
-    if (-diff > tol) return (double)k;  // u <= F_k
-    return -1.0;
+    if (-diff > tol) return k;  // u <= F_k
+    return -1;
   }
-  return 200.0;
+  return 200;
 }
 
 static __device__ double poisson_filtered(double lam, uint64_t seed, uint32_t q, uint32_t d, uint32_t stream) {
   if (!(lam > 0.0)) return 0.0;
   const float l = __double2float_rn(lam);
   if (lam < 10.0) {
-    const double k = inversion_f32(l, 6e-8f, seed, q, d, stream);
-    return k >= 0.0 ? k : poisson_draw(lam, seed, q, d, stream);
+    const int k = inversion_f32(l, 6e-8f, seed, q, d, stream);
+    return k >= 0 ? (double)k : poisson_draw(lam, seed, q, d, stream);
   }
   // PTRS in FP32; k's final sum in FP64 (y + lam + 0.43), the rare slow acceptance in FP64
   const float sl = sqrtf(l);
@@ -161,7 +166,7 @@ static __device__ double poisson_filtered(double lam, uint64_t seed, uint32_t q,
   for (uint32_t i = 0; i < 64; ++i) {
     const uint4 w = rng_block(seed, q, d, i, stream);
     const float U = uni53_f32(w.x, w.y) - 0.5f, V = uni53_f32(w.z, w.w);
-    const float us = 0.5f - fabsf(U);  // within 1.5e-7 of the exact us
+    const float us = 0.5f - fabsf(U);  // within 1.2e-7 of the exact us (u within 2^-23 u)
     const float T = 2.f * a / us + b;
     const float y = T * U;
     const float yerr = fabsf(T) * fmaf(fabsf(U), fmaf(3e-7f, 1.f / us, 4e-6f), 2e-7f) + 1e-6f;
@@ -198,17 +203,25 @@ static __device__ double poisson_filtered(double lam, uint64_t seed, uint32_t q,
   return floor(__dadd_rn(lam, 0.5));
 }
 
+// A Poisson count: k when the FP32 draw decided it, else (k < 0) the FP64 value x.
+struct Count {
+  int k;
+  double x;
+  __device__ float f32() const { return k >= 0 ? (float)k : (float)x; }
+  __device__ double f64() const { return k >= 0 ? (double)k : x; }
+};
+
 // Poisson draw whose mean is known in FP32 (l within le of it), with the exact mean computed
 // only when needed (lam_exact(): FP64, the definition's value): dim means never touch FP64.
 template <typename LamExact>
-static __device__ double poisson_f32mean(float l, float le, LamExact lam_exact, uint64_t seed, uint32_t q, uint32_t d,
-                                         uint32_t stream) {
-  if (l + le <= 0.f) return 0.0;  // the mean is <= 0: no photons
+static __device__ Count poisson_f32mean(float l, float le, LamExact lam_exact, uint64_t seed, uint32_t q, uint32_t d,
+                                        uint32_t stream) {
+  if (l + le <= 0.f) return Count{0, 0.0};  // the mean is <= 0: no photons
   if (l - le > 0.f && l + le < 10.f) {
-    const double k = inversion_f32(l, le / l, seed, q, d, stream);
-    if (k >= 0.0) return k;
+    const int k = inversion_f32(l, le / l, seed, q, d, stream);
+    if (k >= 0) return Count{k, 0.0};
   }
-  return poisson_filtered(lam_exact(), seed, q, d, stream);
+  return Count{-1, poisson_filtered(lam_exact(), seed, q, d, stream)};
 }
 
 }  // namespace e2e

@@ -29,8 +29,11 @@ namespace e2e {
 
 // FP32 copy of a slice's mapping coefficients and the bounds its fast path uses: per
 // coordinate 45 coefficients, then sum_a a |c_a0| (bounds the divided difference of the b = 0
-// polynomial) and sum_{b >= 1} |c_ab| (bounds the slit terms).
-constexpr int kCf = 2 * (E2E_MAXC + 2);
+// polynomial) and sum_{b >= 1} |c_ab| (bounds the slit terms); then the PSF-width
+// coefficients sigma_x[0..2], sigma_y[0..2], the slit-weight total and one pad, all rounded
+// to FP32 once on the host.
+constexpr int kCfExtra = 2 * (E2E_MAXC + 2);
+constexpr int kCf = kCfExtra + 8;
 
 // Per bin: the photon count, and the bin centre's position at s = 0 in FP64, split into the
 // nearest integer and an FP32 remainder (the anchor the FP32 fast path adds small terms to).
@@ -231,12 +234,15 @@ __global__ void __launch_bounds__(256) k_photons(const DevSlice* __restrict__ sl
     const uint4 wa = rng_block(seed, j, si, pp, 5), wb = rng_block(seed, j, si, pp, 6);
     const int4 an = anchors[b];
     double fx = 0.0, fy = 0.0;
+    int ix = -1, iy = -1;
     bool exact = psf != 0 || an.x == INT_MIN;
     if (!exact) {
       // FP32 fast path: every decision is checked against its error bound; a photon too close
       // to a slit-point boundary or a pixel edge is redone in FP64 below
       const float* C32 = ucum32 + S.u_off;
-      const float cu = uni53_f32(wb.x, wb.y) * (float)usum[sl];
+      const float* cf = cf32 + (int64_t)sl * kCf;
+      const float* ce = cf + kCfExtra;
+      const float cu = uni53_f32(wb.x, wb.y) * ce[6];
       int k0 = 0, k1 = S.n_slit - 1;
       while (k0 < k1) {
         const int mid = (k0 + k1) >> 1;
@@ -252,9 +258,8 @@ __global__ void __launch_bounds__(256) k_photons(const DevSlice* __restrict__ sl
       const float s = (2.f * ((float)k0 + uni53_f32(wa.z, wa.w)) - ns) / ns;
       float z1, z2, eg;
       normal_pair_f32_ctr(seed, j, si, pp, 7, z1, z2, eg);
-      const float* cf = cf32 + (int64_t)sl * kCf;
-      const float sx = fmaf(fmaf((float)S.sx[2], lt, (float)S.sx[1]), lt, (float)S.sx[0]);
-      const float sy = fmaf(fmaf((float)S.sy[2], lt, (float)S.sy[1]), lt, (float)S.sy[0]);
+      const float sx = fmaf(fmaf(ce[2], lt, ce[1]), lt, ce[0]);
+      const float sy = fmaf(fmaf(ce[5], lt, ce[4]), lt, ce[3]);
       float mx, my;
       const float ox = photon_offset(cf, S.degree, lt, ltj, delta, s, mx) + sx * z1;
       const float oy = photon_offset(cf + E2E_MAXC + 2, S.degree, lt, ltj, delta, s, my) + sy * z2;
@@ -265,12 +270,17 @@ __global__ void __launch_bounds__(256) k_photons(const DevSlice* __restrict__ sl
       const float ey = 1e-5f * (my + fabsf(sy * z2) + 1.f) + einy + 1.5f * sy * eg;
       const float kx = floorf(rx - ex), ky = floorf(ry - ey);
       if (kx != floorf(rx + ex) || ky != floorf(ry + ey)) exact = true;
-      fx = (double)an.x + (double)kx;
-      fy = (double)an.z + (double)ky;
+      if (!(fabsf(kx) < 0x1p30f && fabsf(ky) < 0x1p30f)) exact = true;  // also NaN
+      ix = exact ? -1 : an.x + (int)kx;  // integers below 2^30: exact conversions, no overflow
+      iy = exact ? -1 : an.z + (int)ky;
     }
-    if (exact) photon_exact(S, ucum + S.u_off, usum[sl], psf, seed, j, si, pp, wa, wb, fx, fy);
-    if (fx >= 0.0 && fx < (double)S.W && fy >= 0.0 && fy < (double)S.H)
-      atomicAdd(dst[S.det] + (int64_t)fy * pitch[S.det] + (int64_t)fx, 1u);
+    if (exact) {
+      photon_exact(S, ucum + S.u_off, usum[sl], psf, seed, j, si, pp, wa, wb, fx, fy);
+      const bool in = fx >= 0.0 && fx < (double)S.W && fy >= 0.0 && fy < (double)S.H;
+      ix = in ? (int)fx : -1;
+      iy = in ? (int)fy : -1;
+    }
+    if (ix >= 0 && ix < S.W && iy >= 0 && iy < S.H) atomicAdd(dst[S.det] + (int64_t)iy * pitch[S.det] + ix, 1u);
   }
 }
 

@@ -133,7 +133,8 @@ def test_multi_detector_and_empty_detector(renderer):
 def test_model_without_slices_renders_zeros(renderer):
     m = W.OpticalModel([(40, 50)], [])
     mid = renderer.load_model(m)
-    out = renderer.render(mid, [], "mixed", "f32")
+    # prefilled: every pixel must be written (the merge writes the empty tiles as zeros)
+    out = renderer.render(mid, [], "mixed", "f32", out=[torch.full((40, 50), 5.0, device="cuda:0")])
     torch.cuda.synchronize()
     assert not out[0].any().item()
     renderer.unload_model(mid)
