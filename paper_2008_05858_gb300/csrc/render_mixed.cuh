@@ -213,15 +213,25 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
         else v = E[m] - E[m + 1];
         win[m] = mult * v;
       }
-      // place the window at its offset o (0..D) in the tile: prof[c] = win[c - o]
+      // place the window at its offset o (0..D) in the tile, prof[c] = win[c - o], as a shift
+      // by o & 1 and then by o & 2: two selects per tile pixel
       float prof[R];
+      if constexpr (D == 0) {
 #pragma unroll
-      for (int c = 0; c < R; ++c) {
-        float v = 0.f;
+        for (int c = 0; c < R; ++c) prof[c] = win[c];
+      } else {
+        const bool s1 = (o & 1) != 0, s2 = (o & 2) != 0;
+        float t[K + 1];  // win shifted by o & 1
 #pragma unroll
-        for (int d = 0; d <= D; ++d)
-          if (c - d >= 0 && c - d < K) v = (o == d) ? win[c - d] : v;
-        prof[c] = v;
+        for (int c = 0; c <= K; ++c) t[c] = s1 ? (c >= 1 ? win[c - 1] : 0.f) : (c < K ? win[c] : 0.f);
+#pragma unroll
+        for (int c = 0; c < R; ++c) {
+          if constexpr (D == 1) {
+            prof[c] = t[c];  // R = K + 1
+          } else {
+            prof[c] = s2 ? (c >= 2 && c - 2 <= K ? t[c - 2] : 0.f) : (c <= K ? t[c] : 0.f);
+          }
+        }
       }
       float ax[RX], ay[RYH];
 #pragma unroll
