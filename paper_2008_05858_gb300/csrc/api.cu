@@ -74,6 +74,12 @@ struct Plan {
   std::vector<int> seg_first;       // [group * n_bands + band]: first item of the segment
   std::vector<int> seg_count;
   std::vector<int> tile_first;      // [n_bands + 1]: merge tiles of each band
+  // fused merge: tile index of each (detector, tile row, tile column), and the tiles that no
+  // item overlaps (written as zeros by the merge kernel)
+  int32_t* d_tile_of = nullptr;
+  int32_t* d_grid_off = nullptr;
+  Tile* d_zero_tiles = nullptr;
+  int n_zero_tiles = 0;
 };
 
 constexpr int kBands = 16;  // y-bands of a frame rendered into host memory
@@ -306,6 +312,9 @@ void free_plan(Plan& p) {
   cudaFree(p.d_items);
   cudaFree(p.d_tiles);
   cudaFree(p.d_lists);
+  cudaFree(p.d_tile_of);
+  cudaFree(p.d_grid_off);
+  cudaFree(p.d_zero_tiles);
   p = Plan{};
 }
 
@@ -462,9 +471,20 @@ int plan_bands_and_tiles(Model* m) {
   }
   P.tile_first.push_back((int)tiles.size());
   P.n_tiles = (int)tiles.size();
+  std::vector<int32_t> tile_of(tile_base[m->n_det]), grid_off(tile_base.begin(), tile_base.end() - 1);
+  std::vector<Tile> zero_tiles;
+  for (size_t i = 0; i < tiles.size(); ++i) {
+    const Tile& t = tiles[i];
+    tile_of[tile_base[t.det] + (t.y0 / kTileH) * ntx[t.det] + t.x0 / kTileW] = (int32_t)i;
+    if (t.n == 0) zero_tiles.push_back(t);
+  }
+  P.n_zero_tiles = (int)zero_tiles.size();
   int rc = upload(&P.d_items, P.items.data(), P.items.size());
   if (rc == E2E_OK) rc = upload(&P.d_tiles, tiles.data(), tiles.size());
   if (rc == E2E_OK) rc = upload(&P.d_lists, flat.data(), flat.size());
+  if (rc == E2E_OK) rc = upload(&P.d_tile_of, tile_of.data(), tile_of.size());
+  if (rc == E2E_OK) rc = upload(&P.d_grid_off, grid_off.data(), grid_off.size());
+  if (rc == E2E_OK) rc = upload(&P.d_zero_tiles, zero_tiles.data(), zero_tiles.size());
   if (rc != E2E_OK) return rc;
   P.ok = true;
   return E2E_OK;
@@ -605,7 +625,7 @@ int plan_model(Model* m) {
     P.smem = m->psf == E2E_PSF_TABLE ? table_smem_bytes(P.max_area, P.nk_max, P.max_deg + 1)
              : ellip ? ellip_smem_bytes(P.max_area, P.nk_max, P.max_deg + 1)
                      : mixed_smem_bytes(P.max_area, P.JB, P.nk_max, P.B, P.max_deg + 1);
-    if ((int)P.smem <= optin) break;
+    if ((int)P.smem + kStaticSmemReserve <= optin) break;
     if (jb_cap == 1)
       return fail(E2E_EINVAL, "trace footprint of a work item exceeds on-chip memory (area " +
                                   std::to_string(P.max_area) + " px)");
@@ -707,9 +727,10 @@ int blaze_scratch(Model* m, std::vector<const double*>& table, Scratch& sc, cuda
 }
 
 // Render items [first, first + count) of the model's plan (all of PSF width K) into the box
-// store, on `st`.
+// store, on `st`; with mg (separable PSF only), each CTA also merges the tiles its item
+// completes.
 cudaError_t launch_items(e2e_ctx* ctx, Model* m, int K, int first, int count, const double** d_table, float2* store,
-                         cudaStream_t st) {
+                         cudaStream_t st, const MergeArgs* mg = nullptr) {
   const Plan& P = m->plan;
   if (m->psf == E2E_PSF_TABLE)
     return launch_render_table(K, m->d_slices, m->d_ts, m->d_T32, m->d_field, m->phases, d_table, m->d_u,
@@ -718,7 +739,7 @@ cudaError_t launch_items(e2e_ctx* ctx, Model* m, int K, int first, int count, co
     return launch_render_ellip(K, m->d_slices, d_table, m->d_u, P.d_items + first, count, store, P.nk_max,
                                P.max_deg, P.smem, st, ctx->d_err);
   return launch_render_mixed(K, P.DX, P.DY, m->d_slices, d_table, m->d_u, P.d_items + first, count, store, P.B,
-                             P.JB, P.nk_max, P.max_deg, P.smem, st, ctx->d_err);
+                             P.JB, P.nk_max, P.max_deg, P.smem, st, ctx->d_err, mg);
 }
 
 int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, int precision, int dtype,
@@ -800,11 +821,28 @@ int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, in
   float2* store = nullptr;
   E2E_CK(sc.get((void**)&store, (size_t)P.store_elems * sizeof(float2)));
   if (ctx->d_err) E2E_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
-  for (auto& g : P.groups) {
-    KernelTimer kt(ctx, st, tab ? "render_table" : ellip ? "render_ellip" : "render_mixed");
-    E2E_CK(launch_items(ctx, m, g.K, g.first, g.count, d_table, store, st));
-  }
-  {
+  if (!tab && !ellip) {
+    // separable PSF: the render CTA that finishes a tile's last item merges the tile; the
+    // tiles no item overlaps are written as zeros first
+    int* count = nullptr;
+    E2E_CK(sc.get((void**)&count, (size_t)P.n_tiles * sizeof(int)));
+    if (count) E2E_CK(cudaMemsetAsync(count, 0, (size_t)P.n_tiles * sizeof(int), st));
+    {
+      KernelTimer kt(ctx, st, "merge_zero");
+      E2E_CK(launch_merge(P.d_zero_tiles, P.n_zero_tiles, P.d_lists, P.d_items, store, d_dst, dtype, d_pitch,
+                          m->d_dims, st));
+    }
+    const MergeArgs mg{P.d_items, P.d_tiles, P.d_lists, P.d_tile_of, P.d_grid_off, m->d_dims, count, d_dst, d_pitch,
+                       dtype == E2E_F32 ? 0 : 1};
+    for (auto& g : P.groups) {
+      KernelTimer kt(ctx, st, "render_mixed");
+      E2E_CK(launch_items(ctx, m, g.K, g.first, g.count, d_table, store, st, &mg));
+    }
+  } else {
+    for (auto& g : P.groups) {
+      KernelTimer kt(ctx, st, tab ? "render_table" : "render_ellip");
+      E2E_CK(launch_items(ctx, m, g.K, g.first, g.count, d_table, store, st));
+    }
     KernelTimer kt(ctx, st, "merge");
     E2E_CK(launch_merge(P.d_tiles, P.n_tiles, P.d_lists, P.d_items, store, d_dst, dtype, d_pitch, m->d_dims, st));
   }
@@ -839,9 +877,10 @@ void band_rows(const Model* m, int d, int b, int& r0, int& r1) {
 
 // Mixed-precision render into host memory, band by band: the items of band b render on one of
 // two streams (consecutive bands alternate, so one band's last CTAs overlap the next band's
-// first), the merge of band b's tiles follows on a high-priority stream once the bands <= b
-// are rendered, and the copy of band b's rows to the host follows on a copy stream, while
-// later bands still render.  The frame is the one e2e_render writes: same items, same order.
+// first); band b's tiles are merged inside those renders (separable PSF) or, for the other
+// PSFs, on a high-priority stream once the bands <= b are rendered; and the copy of band b's
+// rows to the host follows on a copy stream, while later bands still render.  The frame is
+// the one e2e_render writes: same items, same order, same merge.
 int render_host_banded(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, int dtype, void* const* host,
                        const std::vector<int64_t>& pitch, cudaStream_t st) {
   Plan& P = m->plan;
@@ -870,6 +909,18 @@ int render_host_banded(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_
   E2E_CK(cudaMemcpyAsync(d_pitch, fpitch.data(), fpitch.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
   E2E_CK(cudaMemcpyAsync(d_dst, frame.data(), m->n_det * sizeof(void*), cudaMemcpyHostToDevice, st));
   if (ctx->d_err) E2E_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
+  // separable PSF: the tile merge is fused into the render (the CTA that finishes a tile's last
+  // item merges it), so band b is final once the renders of bands <= b are done
+  const bool fused = m->psf == E2E_PSF_SEPARABLE;
+  int* count = nullptr;
+  if (fused) {
+    E2E_CK(sc.get((void**)&count, (size_t)P.n_tiles * sizeof(int)));
+    if (count) E2E_CK(cudaMemsetAsync(count, 0, (size_t)P.n_tiles * sizeof(int), st));
+    E2E_CK(launch_merge(P.d_zero_tiles, P.n_zero_tiles, P.d_lists, P.d_items, store, d_dst, dtype, d_pitch,
+                        m->d_dims, st));
+  }
+  const MergeArgs mg{P.d_items, P.d_tiles, P.d_lists, P.d_tile_of, P.d_grid_off, m->d_dims, count, d_dst, d_pitch,
+                     dtype == E2E_F32 ? 0 : 1};
 
   // events: [0] fork, [1 + b] band b rendered, [1 + kBands + b] band b merged, then the
   // ends of the two render streams, the merge stream and the copy stream
@@ -901,14 +952,21 @@ int render_host_banded(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_
     cudaStream_t r = R[b & 1];
     for (size_t g = 0; g < P.groups.size(); ++g) {
       const int cnt = P.seg_count[g * nb + b];
-      if (cnt) E2E_CK(launch_items(ctx, m, P.groups[g].K, P.seg_first[g * nb + b], cnt, d_table, store, r));
+      if (cnt)
+        E2E_CK(launch_items(ctx, m, P.groups[g].K, P.seg_first[g * nb + b], cnt, d_table, store, r,
+                            fused ? &mg : nullptr));
     }
     E2E_CK(cudaEventRecord(ev[1 + b], r));
-    E2E_CK(cudaStreamWaitEvent(M, ev[1 + b], 0));  // bands < b: waited for by earlier merges
-    E2E_CK(launch_merge(P.d_tiles + P.tile_first[b], P.tile_first[b + 1] - P.tile_first[b], P.d_lists, P.d_items,
-                        store, d_dst, dtype, d_pitch, m->d_dims, M));
-    E2E_CK(cudaEventRecord(ev[1 + kBands + b], M));
-    E2E_CK(cudaStreamWaitEvent(C, ev[1 + kBands + b], 0));
+    if (fused) {  // bands b and b - 1 end the two render streams' work on bands <= b
+      E2E_CK(cudaStreamWaitEvent(C, ev[1 + b], 0));
+      if (b > 0) E2E_CK(cudaStreamWaitEvent(C, ev[b], 0));
+    } else {
+      E2E_CK(cudaStreamWaitEvent(M, ev[1 + b], 0));  // bands < b: waited for by earlier merges
+      E2E_CK(launch_merge(P.d_tiles + P.tile_first[b], P.tile_first[b + 1] - P.tile_first[b], P.d_lists, P.d_items,
+                          store, d_dst, dtype, d_pitch, m->d_dims, M));
+      E2E_CK(cudaEventRecord(ev[1 + kBands + b], M));
+      E2E_CK(cudaStreamWaitEvent(C, ev[1 + kBands + b], 0));
+    }
     for (int d = 0; d < m->n_det; ++d) {
       int r0, r1;
       band_rows(m, d, b, r0, r1);

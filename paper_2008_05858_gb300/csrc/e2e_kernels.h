@@ -10,6 +10,22 @@ namespace e2e {
 
 constexpr int kTileW = 64;  // merge tile (pixels); 256 threads x 8 pixels
 constexpr int kTileH = 32;
+constexpr int kStaticSmemReserve = 1024;  // static shared memory of the render kernels (bytes, upper bound)
+
+// The fused tile merge of the separable render kernel (merge_tile.cuh): per-tile item counts,
+// the plan's tiles and lists, and the frames.  count == nullptr: no fused merge.
+struct MergeArgs {
+  const Item* items;        // the plan's items (the tile lists hold indices into this array)
+  const Tile* tiles;
+  const int32_t* lists;     // CSR item lists of the tiles (item order)
+  const int32_t* tile_of;   // tile index of (detector, tile row, tile column)
+  const int32_t* grid_off;  // per detector: its first entry in tile_of
+  const int* dims;          // per detector: (H, W)
+  int* count;               // per tile: items finished, zero before the render
+  void* const* dst;         // frames
+  const int64_t* pitch;     // their pitches (elements)
+  int dtype;                // 0 = FP32 frame, 1 = FP64 frame
+};
 
 cudaError_t launch_render_fp64(int K, int n_slices, int64_t max_stamps, const DevSlice* slices,
                                const double* const* flux_tab, const double* u_all, double* const* acc,
@@ -23,7 +39,8 @@ bool mixed_variant_supported(int K, int DX, int DY);
 size_t mixed_smem_bytes(int area, int JB, int nk_max, int B, int nd);
 cudaError_t launch_render_mixed(int K, int DX, int DY, const DevSlice* slices, const double* const* flux_tab,
                                 const double* u_all, const Item* items, int n_items, float2* store, int B, int JB,
-                                int nk_max, int max_deg, size_t smem, cudaStream_t st, int* err = nullptr);
+                                int nk_max, int max_deg, size_t smem, cudaStream_t st, int* err = nullptr,
+                                const MergeArgs* mg = nullptr);
 cudaError_t launch_merge(const Tile* tiles, int n_tiles, const int32_t* lists, const Item* items, const float2* store,
                          void* const* dst, int dtype, const int64_t* pitch, const int* dims, cudaStream_t st);
 

@@ -316,7 +316,8 @@ cudaError_t launch_render_table(int K, const DevSlice* slices, const TableSlice*
                                 const Item* items, int n_items, float2* store, int nk_max, int max_deg, size_t smem,
                                 cudaStream_t st, int* err) {
   if (n_items == 0) return cudaSuccess;
-  TableArgs a{MixedArgs{slices, flux_tab, u_all, items, store, 0, 1, nk_max, max_deg, err}, ts, T32, field_lt, P};
+  TableArgs a{MixedArgs{slices, flux_tab, u_all, items, store, 0, 1, nk_max, max_deg, err}, ts,
+              T32, field_lt, P};
   switch (K) {
 #define E2E_CASE(KK) \
   case KK: return launch_table_one<KK>(a, n_items, smem, st);

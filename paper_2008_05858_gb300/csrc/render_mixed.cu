@@ -103,57 +103,14 @@ size_t mixed_smem_bytes(int area, int JB, int nk_max, int B, int nd) {
 
 // ------------------------------------------------------------------------------ merge
 
-// One CTA per output tile: sum, in item order, the boxes of the items overlapping the tile
-// with compensated summation (TwoSum on the FP32 pairs: Neumaier's correction carried in a
-// second word), convert and write every pixel once.  Tiles that no item touches are zeros.
+// One CTA of 256 threads per output tile (merge_tile.cuh).  Tiles that no item touches are zeros.
 template <typename T>
 __global__ void __launch_bounds__(256) k_merge(const Tile* __restrict__ tiles, const int32_t* __restrict__ lists,
                                                const Item* __restrict__ items, const float2* __restrict__ store,
                                                T* const* dst, const int64_t* __restrict__ pitch, const int* __restrict__ dims) {
   const Tile t = tiles[blockIdx.x];
-  const int H = dims[2 * t.det], W = dims[2 * t.det + 1];
-  const int tx = threadIdx.x & (kTileW - 1), ty0 = threadIdx.x / kTileW;
-  constexpr int kRows = kTileW * kTileH / 256;  // pixels per thread
-  constexpr int kStep = 256 / kTileW;
-  const int x = t.x0 + tx;
-  T* frame = dst[t.det];
-  const int64_t P = pitch[t.det];
-  if (t.n == 0) {
-    if (x < W) {
-#pragma unroll
-      for (int q = 0; q < kRows; ++q) {
-        const int y = t.y0 + ty0 + q * kStep;
-        if (y < H) frame[(int64_t)y * P + x] = (T)0;
-      }
-    }
-    return;
-  }
-  float sum[kRows], comp[kRows];
-#pragma unroll
-  for (int q = 0; q < kRows; ++q) sum[q] = comp[q] = 0.f;
-  for (int n = 0; n < t.n; ++n) {
-    const Item it = items[lists[t.list_off + n]];
-    const int gx = x - it.bx0;
-    if (gx < 0 || gx >= it.bw) continue;
-    const float2* box = store + it.store_off;
-#pragma unroll
-    for (int q = 0; q < kRows; ++q) {
-      const int gy = t.y0 + ty0 + q * kStep - it.by0;
-      if (gy >= 0 && gy < it.bh) {
-        const float2 v = box[(int64_t)gy * it.bw + gx];
-        float s, e;
-        two_sum(sum[q], v.x, s, e);
-        sum[q] = s;
-        comp[q] += e + v.y;
-      }
-    }
-  }
-  if (x >= W) return;
-#pragma unroll
-  for (int q = 0; q < kRows; ++q) {
-    const int y = t.y0 + ty0 + q * kStep;
-    if (y < H) frame[(int64_t)y * P + x] = sizeof(T) == 8 ? (T)((double)sum[q] + (double)comp[q]) : (T)(sum[q] + comp[q]);
-  }
+  merge_tile<256, false, T>(t, lists, items, store, dst[t.det], pitch[t.det], dims[2 * t.det], dims[2 * t.det + 1],
+                            threadIdx.x);
 }
 
 // ------------------------------------------------------------------------------ launchers
@@ -180,12 +137,13 @@ bool mixed_variant_supported(int K, int DX, int DY) {
 
 cudaError_t launch_render_mixed(int K, int DX, int DY, const DevSlice* slices, const double* const* flux_tab,
                                 const double* u_all, const Item* items, int n_items, float2* store, int B, int JB,
-                                int nk_max, int max_deg, size_t smem, cudaStream_t st, int* err) {
+                                int nk_max, int max_deg, size_t smem, cudaStream_t st, int* err, const MergeArgs* mg) {
   if (n_items == 0) return cudaSuccess;
   MixedArgs a{slices, flux_tab, u_all, items, store, B, JB, nk_max, max_deg, err};
-  if (err) return launch_render_mixed_checked(K, DX, DY, a, n_items, smem, st);
+  const MergeArgs g = mg ? *mg : MergeArgs{};
+  if (err) return launch_render_mixed_checked(K, DX, DY, a, g, n_items, smem, st);
 #define E2E_V(KK, X, Y) \
-  if (K == KK && DX == X && DY == Y) return launch_one<KK, X, Y, false>(a, n_items, smem, st);
+  if (K == KK && DX == X && DY == Y) return launch_one<KK, X, Y, false>(a, g, n_items, smem, st);
   E2E_MIXED_VARIANTS(E2E_V)
 #undef E2E_V
   return cudaErrorInvalidValue;

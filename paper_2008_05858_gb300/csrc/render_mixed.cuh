@@ -3,6 +3,7 @@
 #pragma once
 #include "e2e_device.cuh"
 #include "e2e_kernels.h"
+#include "merge_tile.cuh"
 #include "mixed_common.cuh"
 #include "phi32.cuh"
 
@@ -49,10 +50,18 @@ constexpr int mixed_min_blocks() {
          128 / kThreads;
 }
 
+// The separable kernel's arguments: the render's, then the fused tile merge's.
+struct FusedArgs {
+  MixedArgs a;
+  MergeArgs mg;
+};
+
 // CHECK: debug build of the same kernel, counting into a.err every deposit the plan did not
 // foresee (the non-checking instantiation carries none of that code).
 template <int K, int DX, int DY, bool CHECK>
-__global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_render_mixed(const MixedArgs a) {
+__global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_render_mixed(const FusedArgs fa) {
+  const MixedArgs& a = fa.a;
+  const MergeArgs& mg = fa.mg;
   constexpr int RX = K + DX, RY = K + DY, H = K / 2;
   constexpr int D = DX > DY ? DX : DY;  // slack of the profile a lane evaluates
   constexpr int R = K + D;              // pixels of that profile
@@ -288,20 +297,22 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
   float2* out = a.store + it.store_off;
   const float inv = ldexpf(1.f, -Psh);
   for (int p = tid; p < area; p += kThreads) out[p] = fixed_to_pair(boxh[p], boxl[p], inv);
+  if (mg.count) fused_merge_epilogue<kThreads>(mg, a.store, it, S.det);
 }
 
 
 template <int K, int DX, int DY, bool CHECK>
-static cudaError_t launch_one(const MixedArgs& a, int n_items, size_t smem, cudaStream_t st) {
+static cudaError_t launch_one(const MixedArgs& a, const MergeArgs& mg, int n_items, size_t smem, cudaStream_t st) {
   auto kern = k_render_mixed<K, DX, DY, CHECK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<n_items, kThreads, smem, st>>>(a);
+  kern<<<n_items, kThreads, smem, st>>>(FusedArgs{a, mg});
   return cudaGetLastError();
 }
 
 // Debug-check instantiations (render_mixed_check.cu).
-cudaError_t launch_render_mixed_checked(int K, int DX, int DY, const MixedArgs& a, int n_items, size_t smem,
+cudaError_t launch_render_mixed_checked(int K, int DX, int DY, const MixedArgs& a, const MergeArgs& mg, int n_items,
+                                        size_t smem,
                                         cudaStream_t st);
 
 // The tile variants (K, DX, DY) the library instantiates.

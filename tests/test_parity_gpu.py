@@ -277,3 +277,27 @@ def test_degenerate_sizes_every_psf(renderer, psf, shape):
         assert compare(g, o).ok
     for g, o in zip(gpu_frames(renderer, w, "fp64", "f64"), ref):
         assert np.all(np.abs(g - o) <= FP64_REL * np.abs(o) + 1e-15 * max(np.abs(o).max(), 1e-300))
+
+
+def test_several_window_sizes_in_one_model(renderer):
+    # slices of K = 7, 11 and 9 on overlapping traces: one render launch per K, with tiles
+    # shared between the launches (their fused merge counts items across launches)
+    w = W.small_config(seed=71, orders=3, trace_pitch=6.0, height=200)
+    for i, s in enumerate(w.model.slices):
+        s.K = (7, 11, 9)[i % 3]
+    ref = oracle.render_workload(w)
+    got = gpu_frames(renderer, w, "mixed", "f32")
+    for g, o in zip(got, ref):
+        rep = compare(g, o)
+        assert rep.ok, str(rep)
+    mid = renderer.load_model(w.model)
+    sids = renderer.load_spectra(w)
+    try:
+        host = renderer.render_host(mid, sids)
+        assert all(np.array_equal(h.numpy(), g) for h, g in zip(host, got))
+    finally:
+        from paper_2008_05858_gb300.binding import e2e_unload_spectrum
+
+        for s in sids:
+            e2e_unload_spectrum(renderer.ctx, s)
+        renderer.unload_model(mid)
