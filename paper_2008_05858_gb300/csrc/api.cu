@@ -877,10 +877,11 @@ void band_rows(const Model* m, int d, int b, int& r0, int& r1) {
 
 // Mixed-precision render into host memory, band by band: the items of band b render on one of
 // two streams (consecutive bands alternate, so one band's last CTAs overlap the next band's
-// first); band b's tiles are merged inside those renders (separable PSF) or, for the other
-// PSFs, on a high-priority stream once the bands <= b are rendered; and the copy of band b's
-// rows to the host follows on a copy stream, while later bands still render.  The frame is
-// the one e2e_render writes: same items, same order, same merge.
+// first), the merge of band b's tiles follows on a high-priority stream once the bands <= b
+// are rendered, and the copy of band b's rows to the host follows on a copy stream, while
+// later bands still render.  (Fusing the merge into the band renders, as e2e_render does,
+// made the whole step slower here: each band's launch then ends only after its merges.)
+// The frame is the one e2e_render writes: same items, same order, same merge.
 int render_host_banded(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, int dtype, void* const* host,
                        const std::vector<int64_t>& pitch, cudaStream_t st) {
   Plan& P = m->plan;
@@ -909,19 +910,6 @@ int render_host_banded(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_
   E2E_CK(cudaMemcpyAsync(d_pitch, fpitch.data(), fpitch.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
   E2E_CK(cudaMemcpyAsync(d_dst, frame.data(), m->n_det * sizeof(void*), cudaMemcpyHostToDevice, st));
   if (ctx->d_err) E2E_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
-  // separable PSF: the tile merge is fused into the render (the CTA that finishes a tile's last
-  // item merges it), so band b is final once the renders of bands <= b are done
-  const bool fused = m->psf == E2E_PSF_SEPARABLE;
-  int* count = nullptr;
-  if (fused) {
-    E2E_CK(sc.get((void**)&count, (size_t)P.n_tiles * sizeof(int)));
-    if (count) E2E_CK(cudaMemsetAsync(count, 0, (size_t)P.n_tiles * sizeof(int), st));
-    E2E_CK(launch_merge(P.d_zero_tiles, P.n_zero_tiles, P.d_lists, P.d_items, store, d_dst, dtype, d_pitch,
-                        m->d_dims, st));
-  }
-  const MergeArgs mg{P.d_items, P.d_tiles, P.d_lists, P.d_tile_of, P.d_grid_off, m->d_dims, count, d_dst, d_pitch,
-                     dtype == E2E_F32 ? 0 : 1};
-
   // events: [0] fork, [1 + b] band b rendered, [1 + kBands + b] band b merged, then the
   // ends of the two render streams, the merge stream and the copy stream
   cudaEvent_t* ev = ctx->band_ev.data();
@@ -952,21 +940,14 @@ int render_host_banded(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_
     cudaStream_t r = R[b & 1];
     for (size_t g = 0; g < P.groups.size(); ++g) {
       const int cnt = P.seg_count[g * nb + b];
-      if (cnt)
-        E2E_CK(launch_items(ctx, m, P.groups[g].K, P.seg_first[g * nb + b], cnt, d_table, store, r,
-                            fused ? &mg : nullptr));
+      if (cnt) E2E_CK(launch_items(ctx, m, P.groups[g].K, P.seg_first[g * nb + b], cnt, d_table, store, r));
     }
     E2E_CK(cudaEventRecord(ev[1 + b], r));
-    if (fused) {  // bands b and b - 1 end the two render streams' work on bands <= b
-      E2E_CK(cudaStreamWaitEvent(C, ev[1 + b], 0));
-      if (b > 0) E2E_CK(cudaStreamWaitEvent(C, ev[b], 0));
-    } else {
-      E2E_CK(cudaStreamWaitEvent(M, ev[1 + b], 0));  // bands < b: waited for by earlier merges
-      E2E_CK(launch_merge(P.d_tiles + P.tile_first[b], P.tile_first[b + 1] - P.tile_first[b], P.d_lists, P.d_items,
-                          store, d_dst, dtype, d_pitch, m->d_dims, M));
-      E2E_CK(cudaEventRecord(ev[1 + kBands + b], M));
-      E2E_CK(cudaStreamWaitEvent(C, ev[1 + kBands + b], 0));
-    }
+    E2E_CK(cudaStreamWaitEvent(M, ev[1 + b], 0));  // bands < b: waited for by earlier merges
+    E2E_CK(launch_merge(P.d_tiles + P.tile_first[b], P.tile_first[b + 1] - P.tile_first[b], P.d_lists, P.d_items,
+                        store, d_dst, dtype, d_pitch, m->d_dims, M));
+    E2E_CK(cudaEventRecord(ev[1 + kBands + b], M));
+    E2E_CK(cudaStreamWaitEvent(C, ev[1 + kBands + b], 0));
     for (int d = 0; d < m->n_det; ++d) {
       int r0, r1;
       band_rows(m, d, b, r0, r1);
