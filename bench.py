@@ -366,6 +366,8 @@ def run_gpu(args):
         line["photon_mc"] = photon_run(B, r, mid, sids, w, stream, flush, kr + km)
     if not args.no_table:
         line["psf_table"] = table_run(B, dev, w, flush)
+    if not args.no_adjoint:
+        line["adjoint"] = adjoint_run(B, dev, flush, cpu_baseline=(rank == 0 and world == 1 and not args.no_cpu_baseline))
     if not args.no_elliptical:
         line["elliptical"] = elliptical_run(B, dev, rank, world,
                                             cpu_baseline=(rank == 0 and world == 1 and not args.no_cpu_baseline))
@@ -484,6 +486,75 @@ def noise_run(B, r, mid, frame, stream, flush, reps=5):
             "hbm_peak_gbs": hbm, "frac_of_hbm": (nbytes / (t * 1e-3) / 1e9 / hbm) if hbm else None,
             "peak_source": kind, "params": params,
             "note": "Philox4x32-10 draws per pixel in FP32 with error bounds (inversion, PTRS, Box-Muller, ADU rounding), FP64 only for decisions too close to call: bit-exact ADU; ALU-bound, not HBM"}
+
+
+def adjoint_run(B, dev, flush, reps=10, cpu_baseline=False):
+    """Calibration-fitting step on the differentiation tile (2048^2, 10 orders x 4000 x 32, K=9):
+    the residual against a target rendered from coefficients shifted by up to 0.01 px, and the
+    gradient of the squared residual with respect to every mapping and PSF-width coefficient by
+    the adjoint kernel (e2e_render_adjoint).  Reports the adjoint alone and the whole step."""
+    import torch
+
+    w = W.config5()
+    rng = np.random.default_rng(W.SEED_BASE + 5)
+    shifted = w.model.copy()
+    for s in shifted.slices:
+        s.cx[0] += rng.uniform(-0.01, 0.01)
+        s.cy[0] += rng.uniform(-0.01, 0.01)
+    stamps = w.model.n_stamps
+    n_grad = sum(2 * W.n_coeffs(s.degree) + 6 for s in w.model.slices)
+    r = B.Renderer(dev, kernel_timing=1)
+    try:
+        mid, mt = r.load_model(w.model), r.load_model(shifted)
+        sids = r.load_spectra(w)
+        target = r.render(mt, sids)[0].double()
+        frame = r.empty_frames(mid)
+        stream = torch.cuda.current_stream()
+        dldi = 2.0 * (r.render(mid, sids, out=frame)[0].double() - target)
+
+        def fit_step():
+            I = r.render(mid, sids, out=frame)[0]
+            return r.adjoint(mid, sids, [2.0 * (I.double() - target)])
+
+        for _ in range(3):
+            fit_step()
+        torch.cuda.synchronize()
+        adj_ms, step_ms, kern = [], [], []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r.adjoint(mid, sids, [dldi])
+            b.record(stream)
+            torch.cuda.synchronize()
+            adj_ms.append(a.elapsed_time(b))
+            kern += [ms for name, ms in B.e2e_kernel_times(r.ctx) if name == "adjoint"]
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fit_step()
+            b.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(a.elapsed_time(b))
+        out = {"workload": w.name, "stamps": stamps, "gradient_entries": n_grad,
+               "adjoint": {"ms": statistics.median(adj_ms), "kernel_ms": statistics.median(kern) if kern else None,
+                           "value": stamps / (statistics.median(adj_ms) * 1e-3), "unit": UNIT},
+               "fit_step": {"ms": statistics.median(step_ms),
+                            "note": "render + residual + adjoint (the loss gradient of one fitting iteration)"}}
+    finally:
+        r.close()
+    if cpu_baseline:
+        import oracle
+
+        cores = min(os.cpu_count() or 1, len(w.model.slices))  # the oracle runs one thread per slice
+        g = dldi.cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.vjp(w.model, w.flux_for, [g], n_threads=cores)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": stamps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"the oracle's FP64 vector-Jacobian product over the whole tile "
+                                         f"({stamps} stamps), {dt:.2f} s"}
+    return out
 
 
 def elliptical_run(B, dev, rank=0, world=1, reps=3, cpu_baseline=False):
@@ -679,6 +750,7 @@ def main():
     ap.add_argument("--no-noise", action="store_true")
     ap.add_argument("--no-photons", action="store_true")
     ap.add_argument("--no-table", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--shard", default="frame", choices=["frame", "band"],
                     help="with several GPUs: an independent frame per GPU (weak scaling) or bands of one frame (strong)")
     args = ap.parse_args()

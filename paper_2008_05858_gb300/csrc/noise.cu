@@ -63,8 +63,12 @@ __global__ void __launch_bounds__(256) k_prnu_map(double* R, float* R32, int H, 
 // One thread per mirror pair.  TO = double: electrons in FP64 (exact read-out noise);
 // float: electrons rounded to FP32 (FP32 read-out noise, within a few ulp of FP64);
 // uint16_t: ADU, exact (filtered, FP64 read-out noise where the rounding is too close).
+// Eight CTAs per SM (32 registers, full occupancy): the draws are latency-bound (dependent
+// Philox, transcendental and filter chains), and the resident warps outweigh the spills this
+// costs.  A 9216^2 frame, minimum CTAs per SM 2 (90 registers) / 3 / 4 / 5 / 6 / 8:
+// 2.05 / 1.68 / 1.55 / 1.47 / 1.42 / 1.35 ms, the same ADU bits each time.
 template <typename TI, typename TO>
-__global__ void __launch_bounds__(256) k_noise(const NoiseArgs a, const TI* __restrict__ src, int64_t src_pitch,
+__global__ void __launch_bounds__(256, 8) k_noise(const NoiseArgs a, const TI* __restrict__ src, int64_t src_pitch,
                                                const double* __restrict__ R, const float* __restrict__ R32, TO* dst,
                                                int64_t dst_pitch, int H, int W, int det) {
   const int half = (W + 1) / 2;
@@ -87,7 +91,7 @@ __global__ void __launch_bounds__(256) k_noise(const NoiseArgs a, const TI* __re
       const double l = __dadd_rn(__dmul_rn(R ? R[i1] : 1.0, (double)S1), a.dark);
       return l > 0.0 ? l : 0.0;
     };
-    Count n0, n1{0, 0.0};
+    Count n0, n1{0, 0.f, 0.0};
     if (a.poisson) {
       const float rs0 = (R32 ? R32[i0] : 1.f) * (float)S0, rs1 = two ? (R32 ? R32[i1] : 1.f) * (float)S1 : 0.f;
       const float l0 = rs0 + a.dark32, l1 = rs1 + a.dark32;
@@ -97,8 +101,8 @@ __global__ void __launch_bounds__(256) k_noise(const NoiseArgs a, const TI* __re
       n0 = poisson_f32mean(l0, le0, lam_exact0, a.seed, q, (uint32_t)det, 2);
       if (two) n1 = poisson_f32mean(l1, le1, lam_exact1, a.seed, q, (uint32_t)det, 3);
     } else {
-      n0 = Count{-1, lam_exact0()};
-      n1 = Count{-1, two ? lam_exact1() : 0.0};
+      n0 = exact_count(lam_exact0());
+      n1 = exact_count(two ? lam_exact1() : 0.0);
     }
     TO* drow = dst + (int64_t)r * dst_pitch;
     if constexpr (sizeof(TO) == 8) {  // FP64 electrons: exact read-out noise

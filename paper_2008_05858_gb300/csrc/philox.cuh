@@ -206,22 +206,24 @@ static __device__ double poisson_filtered(double lam, uint64_t seed, uint32_t q,
 // A Poisson count: k when the FP32 draw decided it, else (k < 0) the FP64 value x.
 struct Count {
   int k;
+  float xf;
   double x;
-  __device__ float f32() const { return k >= 0 ? (float)k : (float)x; }
+  __device__ float f32() const { return k >= 0 ? (float)k : xf; }
   __device__ double f64() const { return k >= 0 ? (double)k : x; }
 };
+__device__ __forceinline__ Count exact_count(double x) { return Count{-1, (float)x, x}; }
 
 // Poisson draw whose mean is known in FP32 (l within le of it), with the exact mean computed
 // only when needed (lam_exact(): FP64, the definition's value): dim means never touch FP64.
 template <typename LamExact>
 static __device__ Count poisson_f32mean(float l, float le, LamExact lam_exact, uint64_t seed, uint32_t q, uint32_t d,
                                         uint32_t stream) {
-  if (l + le <= 0.f) return Count{0, 0.0};  // the mean is <= 0: no photons
+  if (l + le <= 0.f) return Count{0, 0.f, 0.0};  // the mean is <= 0: no photons
   if (l - le > 0.f && l + le < 10.f) {
     const int k = inversion_f32(l, le / l, seed, q, d, stream);
-    if (k >= 0) return Count{k, 0.0};
+    if (k >= 0) return Count{k, 0.f, 0.0};
   }
-  return Count{-1, poisson_filtered(lam_exact(), seed, q, d, stream)};
+  return exact_count(poisson_filtered(lam_exact(), seed, q, d, stream));
 }
 
 }  // namespace e2e
