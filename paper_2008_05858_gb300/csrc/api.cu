@@ -146,6 +146,11 @@ struct e2e_ctx {
   std::map<uint64_t, std::unique_ptr<Frame>> frames;
   cudaMemPool_t pool = nullptr;
   cudaStream_t free_stream = nullptr;  // where library frames are returned to the pool
+  // spectrum uploads: pool allocation, copy and finiteness check on their own stream
+  std::mutex load_mu;
+  cudaStream_t load_stream = nullptr;
+  int* d_flag = nullptr;
+  int* h_flag = nullptr;  // page-locked
   int* d_err = nullptr;                // debug checks: deposits outside the planned boxes
   struct NoisePattern {                // pixel response map of a model's detectors (FP64)
     uint64_t pattern_seed = 0;
@@ -1022,10 +1027,16 @@ int e2e_create(e2e_ctx** out, int32_t device, const e2e_opts* opts) {
     cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
   e = cudaStreamCreateWithFlags(&c->free_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->load_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_flag, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_flag, sizeof(int));
   if (e == cudaSuccess && c->opts.debug_checks) e = cudaMalloc((void**)&c->d_err, sizeof(int));
   if (e == cudaSuccess && c->d_err) e = cudaMemset(c->d_err, 0, sizeof(int));
   if (e != cudaSuccess) {
     if (c->free_stream) cudaStreamDestroy(c->free_stream);
+    if (c->load_stream) cudaStreamDestroy(c->load_stream);
+    cudaFree(c->d_flag);
+    cudaFreeHost(c->h_flag);
     cudaFree(c->d_err);
     delete c;
     return cuda_fail(e, "context setup");
@@ -1042,7 +1053,11 @@ void e2e_destroy(e2e_ctx* ctx) {
     cudaDeviceSynchronize();
     std::lock_guard<std::mutex> lk(ctx->mu);
     for (auto& kv : ctx->models) free_model(kv.second.get());
-    for (auto& kv : ctx->spectra) cudaFree(kv.second->d_flux);
+    for (auto& kv : ctx->spectra) cudaFreeAsync(kv.second->d_flux, ctx->load_stream);
+    cudaStreamSynchronize(ctx->load_stream);
+    cudaStreamDestroy(ctx->load_stream);
+    cudaFree(ctx->d_flag);
+    cudaFreeHost(ctx->h_flag);
     for (auto& kv : ctx->frames) free_frame(ctx, kv.second.get());
     for (auto& kv : ctx->patterns) {
       for (double* p : kv.second.R) cudaFree(p);
@@ -1246,10 +1261,25 @@ int e2e_load_spectrum(e2e_ctx* ctx, int32_t fiber, int32_t n_orders, const int32
     sp->rows[order_ids[i]] = {total, n_lambda[i]};
     total += n_lambda[i];
   }
-  if (!finite_all(flux, (size_t)total)) return fail(E2E_EINVAL, "non-finite flux");
   DeviceGuard g(ctx->device);
-  int rc = upload(&sp->d_flux, flux, (size_t)total);
-  if (rc != E2E_OK) return rc;
+  if (total > 0) {
+    // from the pool on the load stream; the finiteness check runs on the uploaded copy
+    std::lock_guard<std::mutex> lk(ctx->load_mu);
+    const size_t bytes = (size_t)total * sizeof(double);
+    cudaStream_t ls = ctx->load_stream;
+    E2E_CK(ctx->pool ? cudaMallocFromPoolAsync((void**)&sp->d_flux, bytes, ctx->pool, ls)
+                     : cudaMallocAsync((void**)&sp->d_flux, bytes, ls));
+    cudaError_t e = cudaMemcpyAsync(sp->d_flux, flux, bytes, cudaMemcpyHostToDevice, ls);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ls);
+    if (e == cudaSuccess) e = launch_flag_nonfinite(sp->d_flux, total, ctx->d_flag, ls);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ls);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ls);
+    if (e != cudaSuccess || *ctx->h_flag) {
+      cudaFreeAsync(sp->d_flux, ls);
+      cudaStreamSynchronize(ls);
+      return e != cudaSuccess ? cuda_fail(e, "spectrum upload") : fail(E2E_EINVAL, "non-finite flux");
+    }
+  }
   std::lock_guard<std::mutex> lk(ctx->mu);
   *spec_id = ctx->next_id++;
   ctx->spectra[*spec_id] = std::move(sp);
@@ -1262,8 +1292,8 @@ int e2e_unload_spectrum(e2e_ctx* ctx, uint64_t spec_id) {
   std::lock_guard<std::mutex> lk(ctx->mu);
   auto it = ctx->spectra.find(spec_id);
   if (it == ctx->spectra.end()) return fail(E2E_ENOTFOUND, "unknown spectrum id");
-  cudaDeviceSynchronize();
-  cudaFree(it->second->d_flux);
+  cudaDeviceSynchronize();  // no render enqueued before this call still reads the spectrum
+  cudaFreeAsync(it->second->d_flux, ctx->load_stream);  // back to the pool
   ctx->spectra.erase(it);
   return E2E_OK;
 }

@@ -42,4 +42,21 @@ cudaError_t launch_blaze(const DevSlice* slices, int n_slices, const double* con
   return cudaGetLastError();
 }
 
+// Flag (flag = 1) if any of the n values is not finite: the check e2e_load_spectrum makes of
+// an uploaded spectrum, on the device instead of a host pass over the host copy.
+__global__ void __launch_bounds__(256) k_flag_nonfinite(const double* __restrict__ p, int64_t n, int* flag) {
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(p[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) *flag = 1;
+}
+
+cudaError_t launch_flag_nonfinite(const double* p, int64_t n, int* flag, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_flag_nonfinite<<<(unsigned)blocks, 256, 0, st>>>(p, n, flag);
+  return cudaGetLastError();
+}
+
 }  // namespace e2e

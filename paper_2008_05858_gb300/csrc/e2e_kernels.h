@@ -70,6 +70,7 @@ cudaError_t launch_render_fp64_table(int K, int n_slices, int64_t max_stamps, co
                                      const TableSlice* ts, const double* T64, const double* field_lt, int P,
                                      const double* const* flux_tab, const double* u_all, double* const* acc,
                                      const int64_t* pitch, cudaStream_t st);
+cudaError_t launch_flag_nonfinite(const double* p, int64_t n, int* flag, cudaStream_t st);
 cudaError_t launch_blaze(const DevSlice* slices, int n_slices, const double* const* flux_in, const int64_t* bin_off,
                          int64_t n_bins, double* out, cudaStream_t st);
 cudaError_t launch_photon_bins(const DevSlice* slices, int n_slices, const double* const* flux_tab, const double* usum,

@@ -209,6 +209,30 @@ def test_spectrum_length_mismatch_is_rejected(renderer):
     renderer.unload_model(mid)
 
 
+@pytest.mark.parametrize("bad_value", [float("nan"), float("inf"), -float("inf")], ids=["nan", "inf", "-inf"])
+@pytest.mark.parametrize("where", ["first", "last", "middle"])
+def test_non_finite_flux_is_rejected(renderer, bad_value, where):
+    # the upload is checked on the device: a single bad sample anywhere refuses the spectrum,
+    # and a good spectrum still loads and renders afterwards
+    from paper_2008_05858_gb300.binding import E2EError, E2E_EINVAL
+
+    w = W.small_config(seed=83)
+    orders = sorted(w.spectra[0].flux)
+    flux = {o: np.array(w.spectra[0].flux[o], dtype=np.float64) for o in orders}
+    cat = np.concatenate([flux[o] for o in orders])
+    cat[{"first": 0, "last": len(cat) - 1, "middle": len(cat) // 2 + 1}[where]] = bad_value
+    off = 0
+    for o in orders:
+        n = len(flux[o])
+        flux[o] = cat[off:off + n]
+        off += n
+    with pytest.raises(E2EError) as e:
+        renderer.load_spectrum(W.Spectrum(0, flux))
+    assert e.value.code == E2E_EINVAL and "non-finite" in str(e.value)
+    ref = oracle_frames(w)
+    assert compare(gpu_frames(renderer, w, "mixed", "f32")[0], ref[0]).ok
+
+
 def test_render_alloc_and_fetch(renderer):
     from paper_2008_05858_gb300 import binding as B
 
