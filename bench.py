@@ -711,13 +711,25 @@ KERNEL_SOURCES = ["paper_2008_05858_gb300/csrc/render_mixed.cu", "paper_2008_058
                   "paper_2008_05858_gb300/csrc/e2e_device.cuh", "paper_2008_05858_gb300/csrc/tail_coeffs.h"]
 
 
+def _strip_comments(src: str) -> str:
+    """C/C++ source without comments and blank lines (string literals in these files hold no
+    comment markers), so that editing a comment does not invalidate the traffic counters."""
+    import re
+
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+
+
 def kernel_source_hash() -> str:
+    """sha256[:16] of the render kernel's source files with comments stripped (the code the
+    traffic counters refer to)."""
     import hashlib
 
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as f:
+            h.update(_strip_comments(f.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -1,4 +1,4 @@
-// Mixed-precision tiled renderer (separable Gaussian PSF) and the halo merge.
+// Mixed-precision tiled renderer (separable Gaussian PSF), its planner and the tile merge kernel.
 //
 // Work item = one order-slice x a block of wavelength samples x a block of slit points.
 // Inside the item, each lane owns a *run* of B consecutive slit points of one wavelength
@@ -7,10 +7,12 @@
 // FP32 registers and flushes the tile once per run into the item's box in shared memory.
 // The box holds 52-bit fixed-point sums (two 32-bit words per pixel, scaled by a power of
 // two above the item's total flux) updated with integer atomics: the accumulation is exact
-// and independent of the order of the flushes.  At the end the box is written, in FP64, to a
-// scratch "box store".  The merge kernel then owns every output pixel: it adds, with
-// compensated summation, the boxes of all items overlapping its tile, in item order, and
-// writes the frame once.  No global atomics; the frame does not depend on scheduling.
+// and independent of the order of the flushes.  At the end the box is written to a scratch
+// "box store" as unevaluated FP32 pairs (hi + lo, ~48 bits).  Each output tile is then merged
+// once (merge_tile.cuh): the boxes of all items overlapping it are added in item order with
+// compensated summation and the frame is written once, either by the render CTA that finishes
+// the tile's last item (fused) or by the merge kernel below.  No global atomics on the frame;
+// the frame does not depend on scheduling.
 //
 // Precision (the paper's fidelity target, Sec. 2.2, is a photocenter shift below ~1e-5 px):
 // mapping in FP64, the centre split exactly into an integer pixel and an FP32 offset, PSF
