@@ -271,8 +271,22 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
       const float* A = T + (int64_t)fw.x * node_stride + row;  // node f0
       const float* Bn = T + (int64_t)fw.y * node_stride + row; // node f1
       const int bxs = st.x - K / 2 - it.bx0, bys = st.y - K / 2 - it.by0;
+      // all table reads of this lane's pixels first (they do not depend on the deposits),
+      // then the blends and deposits
+      constexpr int NI = (KK + 31) / 32;
+      float tv[NI][8];
 #pragma unroll
-      for (int i = 0; i < (KK + 31) / 32; ++i) {
+      for (int i = 0; i < NI; ++i) {
+        const int e = lane + 32 * i;
+        if (e < KK) {
+          tv[i][0] = __ldg(A + e); tv[i][1] = __ldg(A + e + KK);
+          tv[i][2] = __ldg(A + e + drow); tv[i][3] = __ldg(A + e + drow + KK);
+          tv[i][4] = __ldg(Bn + e); tv[i][5] = __ldg(Bn + e + KK);
+          tv[i][6] = __ldg(Bn + e + drow); tv[i][7] = __ldg(Bn + e + drow + KK);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NI; ++i) {
         const int e = lane + 32 * i;
         if (e >= KK) break;
         const int n = e / K, m = e - n * K;
@@ -284,10 +298,8 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
           }
           continue;
         }
-        const float t0 = fmaf(c00, __ldg(A + e), fmaf(c01, __ldg(A + e + KK),
-                         fmaf(c10, __ldg(A + e + drow), c11 * __ldg(A + e + drow + KK))));
-        const float t1 = fmaf(c00, __ldg(Bn + e), fmaf(c01, __ldg(Bn + e + KK),
-                         fmaf(c10, __ldg(Bn + e + drow), c11 * __ldg(Bn + e + drow + KK))));
+        const float t0 = fmaf(c00, tv[i][0], fmaf(c01, tv[i][1], fmaf(c10, tv[i][2], c11 * tv[i][3])));
+        const float t1 = fmaf(c00, tv[i][4], fmaf(c01, tv[i][5], fmaf(c10, tv[i][6], c11 * tv[i][7])));
         const int q = by * it.bw + bx;
         box_deposit(boxh + q, boxl + q, fmaf(wf0, t0, wf1 * t1), sc, sc_hi);
       }
