@@ -325,3 +325,50 @@ def test_several_window_sizes_in_one_model(renderer):
         for s in sids:
             e2e_unload_spectrum(renderer.ctx, s)
         renderer.unload_model(mid)
+
+
+def _poly2(c, degree, lt, s):
+    """x or y of a slice's mapping on the grid lt x s (a plain evaluation for choosing windows)."""
+    out = np.zeros((len(lt), len(s)))
+    for a in range(degree + 1):
+        for b in range(degree + 1 - a):
+            out += c[W.coeff_index(a, b)] * np.outer(lt ** a, s ** b)
+    return out
+
+
+def test_config2_full_frame_sampled_windows(renderer):
+    # The benchmark's frame itself (85 orders x 2 fibers x 2 slices x 6000 x 64 stamps, K = 11,
+    # 9216^2), rendered as the benchmark renders it.  64 x 64 windows on the traces are checked
+    # against the oracle, which renders each window alone: only the slices whose traces come
+    # within reach of it, translated so the window is the oracle's whole frame.
+    import dataclasses
+
+    w = W.config2()
+    got = gpu_frames(renderer, w, "mixed", "f32")[0]
+    H, Wd = w.model.det_shape[0]
+    lt, ss = np.linspace(-1.0, 1.0, 513), np.linspace(-1.0, 1.0, 9)
+    yr = []
+    for s in w.model.slices:
+        y = _poly2(s.cy, s.degree, lt, ss)
+        yr.append((y.min(), y.max()))
+    rng = np.random.default_rng(2008)
+    n_win, size = 6, 64
+    for _ in range(n_win):
+        s = w.model.slices[int(rng.integers(len(w.model.slices)))]
+        t = rng.uniform(-0.95, 0.95)
+        xc = float(_poly2(s.cx, s.degree, np.array([t]), np.array([0.0]))[0, 0])
+        yc = float(_poly2(s.cy, s.degree, np.array([t]), np.array([0.0]))[0, 0])
+        x0 = int(min(max(round(xc) - size // 2, 0), Wd - size))
+        y0 = int(min(max(round(yc) - size // 2, 0), H - size))
+        reach = 2 + s.K
+        sub = []
+        for q, (lo, hi) in zip(w.model.slices, yr):
+            if hi + reach >= y0 and lo - reach <= y0 + size:
+                c = q.copy()
+                c.cx[0] -= x0
+                c.cy[0] -= y0
+                sub.append(c)
+        ref = oracle.render(W.OpticalModel([(size, size)], sub, w.model.psf), w.flux_for)[0]
+        assert np.abs(ref).max() > 0
+        rep = compare(got[y0:y0 + size, x0:x0 + size], ref)
+        assert rep.ok, f"window at ({x0}, {y0}): {rep}"
