@@ -1556,11 +1556,14 @@ int e2e_render_adjoint(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const ui
   E2E_CK(cudaMemcpyAsync(d_table, table.data(), table.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
   E2E_CK(cudaMemcpyAsync(d_pitch, pitch.data(), pitch.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
   E2E_CK(cudaMemcpyAsync(d_dldi, dldi, m->n_det * sizeof(void*), cudaMemcpyHostToDevice, st));
-  const size_t smem = adjoint_smem_bytes(P.max_area, P.max_deg);
+  const size_t smem = adjoint_smem_bytes(P.max_area, P.max_deg, P.nk_max);
+  int max_tasks = 1;  // warp tasks of the largest item: 32-sample blocks x runs
+  for (const Item& it : P.items) max_tasks = std::max(max_tasks, ((it.nj + 31) / 32) * ((it.nk + P.B - 1) / P.B));
+  const int parts = adjoint_parts(max_tasks);
   for (auto& grp : P.groups) {
     KernelTimer kt(ctx, st, "adjoint");
     E2E_CK(launch_adjoint(grp.K, m->d_slices, d_table, m->d_u, P.d_items + grp.first, grp.count, d_dldi, d_pitch,
-                          dtype == E2E_F32 ? 0 : 1, P.B, g_cx, g_cy, g_sx, g_sy, smem, st));
+                          dtype == E2E_F32 ? 0 : 1, P.B, P.nk_max, parts, g_cx, g_cy, g_sx, g_sy, smem, st));
   }
   return E2E_OK;
 }

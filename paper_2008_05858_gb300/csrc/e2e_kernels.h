@@ -84,10 +84,11 @@ cudaError_t launch_photons(const DevSlice* slices, int n_slices, const double* u
                            uint32_t* const* dst, const int64_t* pitch, uint64_t max_photons, const float* ucum32,
                            const float* cf32, const int4* anchors, cudaStream_t st);
 
-size_t adjoint_smem_bytes(int max_area, int max_deg);
+size_t adjoint_smem_bytes(int max_area, int max_deg, int nk_max);
+int adjoint_parts(int max_tasks);  // CTAs per item sharing its warp tasks
 cudaError_t launch_adjoint(int K, const DevSlice* slices, const double* const* flux_tab, const double* u_all,
                            const Item* items, int n_items, const void* const* dldi, const int64_t* pitch, int dtype,
-                           int B, double* g_cx, double* g_cy, double* g_sx, double* g_sy, size_t smem,
-                           cudaStream_t st);
+                           int B, int nk_max, int parts, double* g_cx, double* g_cy, double* g_sx, double* g_sy,
+                           size_t smem, cudaStream_t st);
 
 }  // namespace e2e

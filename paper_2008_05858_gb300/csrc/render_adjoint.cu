@@ -13,7 +13,11 @@
 // coefficient gradients.  The work decomposition is the forward's (items, boxes): dL/dI over
 // the item's box is staged in shared memory, each lane takes a run of slit points of one
 // wavelength sample, gathers its stamps' windows, and the per-run sums are reduced per warp
-// and per CTA in FP64 before one global FP64 add per coefficient per item.
+// and per CTA in FP64 before one global FP64 add per coefficient per CTA.  An item's warp
+// tasks are spread over gridDim.y CTAs (each stages the item's dL/dI), so that small grids
+// still fill the GPU.
+#include <algorithm>
+
 #include "e2e_device.cuh"
 #include "e2e_kernels.h"
 #include "phi32.cuh"
@@ -32,6 +36,7 @@ struct AdjArgs {
   const int64_t* pitch;
   int dtype;                // 0 f32, 1 f64
   int B;
+  int nk_max;               // largest number of slit points in an item
   double* g_cx;
   double* g_cy;
   double* g_sx;
@@ -84,8 +89,15 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
   const int area = it.bw * it.bh;
   const int d = S.degree, nc = (d + 1) * (d + 2) / 2;
   const int ncoef = 2 * nc + 6;
+  const int nrc = (it.nk + a.B - 1) / a.B;
+  const int njb = (it.nj + 31) / 32;
+  const int ntask = njb * nrc;
+  if ((int)blockIdx.y * kAdjWarps >= ntask) return;  // no task of this item for this CTA
   float* R = reinterpret_cast<float*>(smem);                            // dL/dI over the box
-  double* red = reinterpret_cast<double*>(smem + (((size_t)area * 4 + 15) & ~(size_t)15));  // [warps][ncoef]
+  const size_t o_red = ((size_t)area * 4 + 15) & ~(size_t)15;
+  double* red = reinterpret_cast<double*>(smem + o_red);                // [warps][ncoef]
+  double* tabS = red + kAdjWarps * ncoef;                               // s of the item's slit points
+  float2* tabU = reinterpret_cast<float2*>(tabS + a.nk_max);           // their weights, (hi, lo)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   {
     const int64_t P = a.pitch[S.det];
@@ -96,16 +108,18 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
                           : (float)static_cast<const double*>(a.dldi[S.det])[off];
     }
     for (int q = tid; q < kAdjWarps * ncoef; q += kAdjThreads) red[q] = 0.0;
+    const double* u = a.u_all + S.u_off;
+    const double inv_ns = 1.0 / (double)S.n_slit;
+    for (int kk = tid; kk < it.nk; kk += kAdjThreads) {
+      tabS[kk] = (double)(2 * (it.k0 + kk) + 1 - S.n_slit) * inv_ns;
+      tabU[kk] = split_pair(u[it.k0 + kk]);
+    }
   }
   __syncthreads();
   const double* flux = a.flux_tab[S.flux_slot];
-  const double* u = a.u_all + S.u_off;
-  const double inv_nl = 1.0 / (double)S.n_lambda, inv_ns = 1.0 / (double)S.n_slit;
+  const double inv_nl = 1.0 / (double)S.n_lambda;
   const double kq = kSqrtLog2eD * 0.70710678118654752440;
-  const int nrc = (it.nk + a.B - 1) / a.B;
-  const int njb = (it.nj + 31) / 32;
-  const int ntask = njb * nrc;
-  for (int task = warp; task < ntask; task += kAdjWarps) {
+  for (int task = blockIdx.y * kAdjWarps + warp; task < ntask; task += gridDim.y * kAdjWarps) {
     const int jj = (task % njb) * 32 + lane;
     const bool jvalid = jj < it.nj;
     const int j = it.j0 + jj;
@@ -127,16 +141,17 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
       const double sgy = fma(fma(S.sy[2], lt, S.sy[1]), lt, S.sy[0]);
       const float2 gx = split_pair(kq / sgx), gy = split_pair(kq / sgy);
       const float isx = (float)(1.0 / sgx), isy = (float)(1.0 / sgy);
-      const double wj = flux[j] * S.dlam;
+      const float2 wj = split_pair(flux[j] * S.dlam);
       for (int b = 0; b < nb; ++b) {
         const int k = k0 + b;
-        const double sd = (double)(2 * k + 1 - S.n_slit) * inv_ns;
+        const double sd = tabS[k - it.k0];
         int ci, ri;
         float fx, fy;
         split_coord(horner_s(px, d, sd), ci, fx);
         split_coord(horner_s(py, d, sd), ri, fy);
         if (ci == kOffFrame || ri == kOffFrame) continue;
-        const float w = (float)(wj * u[k]);
+        const float2 uk = tabU[k - it.k0];
+        const float w = fmaf(wj.x, uk.x, fmaf(wj.x, uk.y, wj.y * uk.x));
         float Ax[K], dAx[K], sAx[K], Ay[K], dAy[K], sAy[K];
         axis_profile<K>(fx, gx.x, gx.y, isx, Ax, dAx, sAx);
         axis_profile<K>(fy, gy.x, gy.y, isy, Ay, dAy, sAy);
@@ -239,35 +254,37 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
   }
 }
 
-size_t adjoint_smem_bytes(int max_area, int max_deg) {
+size_t adjoint_smem_bytes(int max_area, int max_deg, int nk_max) {
   const int nc = (max_deg + 1) * (max_deg + 2) / 2;
-  return (((size_t)max_area * 4 + 15) & ~(size_t)15) + (size_t)kAdjWarps * (2 * nc + 6) * 8;
+  return (((size_t)max_area * 4 + 15) & ~(size_t)15) + (size_t)kAdjWarps * (2 * nc + 6) * 8 + (size_t)nk_max * 16;
 }
 
+int adjoint_parts(int max_tasks) { return std::max(1, std::min(4, (max_tasks + kAdjWarps - 1) / kAdjWarps)); }
+
 template <int K>
-static cudaError_t launch_adj(const AdjArgs& a, int n_items, size_t smem, cudaStream_t st) {
+static cudaError_t launch_adj(const AdjArgs& a, int n_items, int parts, size_t smem, cudaStream_t st) {
   auto kern = k_adjoint<K>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<n_items, kAdjThreads, smem, st>>>(a);
+  kern<<<dim3(n_items, parts), kAdjThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint(int K, const DevSlice* slices, const double* const* flux_tab, const double* u_all,
                            const Item* items, int n_items, const void* const* dldi, const int64_t* pitch, int dtype,
-                           int B, double* g_cx, double* g_cy, double* g_sx, double* g_sy, size_t smem,
-                           cudaStream_t st) {
+                           int B, int nk_max, int parts, double* g_cx, double* g_cy, double* g_sx, double* g_sy,
+                           size_t smem, cudaStream_t st) {
   if (n_items == 0) return cudaSuccess;
-  AdjArgs a{slices, flux_tab, u_all, items, dldi, pitch, dtype, B, g_cx, g_cy, g_sx, g_sy};
+  AdjArgs a{slices, flux_tab, u_all, items, dldi, pitch, dtype, B, nk_max, g_cx, g_cy, g_sx, g_sy};
   switch (K) {
-    case 1: return launch_adj<1>(a, n_items, smem, st);
-    case 3: return launch_adj<3>(a, n_items, smem, st);
-    case 5: return launch_adj<5>(a, n_items, smem, st);
-    case 7: return launch_adj<7>(a, n_items, smem, st);
-    case 9: return launch_adj<9>(a, n_items, smem, st);
-    case 11: return launch_adj<11>(a, n_items, smem, st);
-    case 13: return launch_adj<13>(a, n_items, smem, st);
-    case 15: return launch_adj<15>(a, n_items, smem, st);
+    case 1: return launch_adj<1>(a, n_items, parts, smem, st);
+    case 3: return launch_adj<3>(a, n_items, parts, smem, st);
+    case 5: return launch_adj<5>(a, n_items, parts, smem, st);
+    case 7: return launch_adj<7>(a, n_items, parts, smem, st);
+    case 9: return launch_adj<9>(a, n_items, parts, smem, st);
+    case 11: return launch_adj<11>(a, n_items, parts, smem, st);
+    case 13: return launch_adj<13>(a, n_items, parts, smem, st);
+    case 15: return launch_adj<15>(a, n_items, parts, smem, st);
     default: return cudaErrorInvalidValue;
   }
 }
