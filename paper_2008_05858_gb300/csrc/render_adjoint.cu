@@ -12,8 +12,9 @@
 // and the chain rule through x_c = sum c_ab lt^a s^b and sigma = sum p_q lt^q gives the
 // coefficient gradients.  The work decomposition is the forward's (items, boxes): dL/dI over
 // the item's box is staged in shared memory, each lane takes a run of slit points of one
-// wavelength sample, gathers its stamps' windows, and the per-run sums are reduced per warp
-// and per CTA in FP64 before one global FP64 add per coefficient per CTA.  An item's warp
+// wavelength sample, gathers its stamps' windows, and the per-run sums are reduced over the
+// warp in FP32 and over the warp's tasks and the CTA in FP64 before one global FP64 add per
+// coefficient per CTA.  An item's warp
 // tasks are spread over gridDim.y CTAs (each stages the item's dL/dI), so that small grids
 // still fill the GPU.
 #include <algorithm>
@@ -200,14 +201,15 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
         }
       }
     }
-    // coefficient gradients of this run: dL/dc_ab = lt^a H_b, dL/ds_q = lt^q G_s; reduce the
-    // warp in FP64 and keep one partial per warp
-    const double ltv = lt;
+    // coefficient gradients of this run: dL/dc_ab = lt^a H_b, dL/ds_q = lt^q G_s.  The warp's
+    // 32 samples are summed in FP32 (|lt| <= 1; the run sums are FP32 already), the partials
+    // of the warp's tasks in FP64
+    const float ltf = (float)lt;
     for (int t = 0; t <= d; ++t)
       for (int bb = 0; bb <= t; ++bb) {
         const int aa = t - bb;
-        double lp = 1.0;
-        for (int q = 0; q < aa; ++q) lp *= ltv;
+        float lp = 1.f;
+        for (int q = 0; q < aa; ++q) lp *= ltf;
         float hx = 0.f, hy = 0.f;
 #pragma unroll
         for (int q = 0; q < 9; ++q)
@@ -215,7 +217,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
             hx = Hx[q];
             hy = Hy[q];
           }
-        double vx = lp * (double)hx, vy = lp * (double)hy;
+        float vx = lp * hx, vy = lp * hy;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           vx += __shfl_xor_sync(0xffffffffu, vx, o);
@@ -223,22 +225,24 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
         }
         if (lane == 0) {
           const int idx = t * (t + 1) / 2 + bb;
-          red[warp * ncoef + idx] += vx;
-          red[warp * ncoef + nc + idx] += vy;
+          red[warp * ncoef + idx] += (double)vx;
+          red[warp * ncoef + nc + idx] += (double)vy;
         }
       }
-    for (int q = 0; q < 3; ++q) {
-      double lp = 1.0;
-      for (int r = 0; r < q; ++r) lp *= ltv;
-      double vx = lp * (double)Gsx, vy = lp * (double)Gsy;
+    {
+      float lp = 1.f;
+      for (int q = 0; q < 3; ++q) {
+        float vx = lp * Gsx, vy = lp * Gsy;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        vx += __shfl_xor_sync(0xffffffffu, vx, o);
-        vy += __shfl_xor_sync(0xffffffffu, vy, o);
-      }
-      if (lane == 0) {
-        red[warp * ncoef + 2 * nc + q] += vx;
-        red[warp * ncoef + 2 * nc + 3 + q] += vy;
+        for (int o = 16; o > 0; o >>= 1) {
+          vx += __shfl_xor_sync(0xffffffffu, vx, o);
+          vy += __shfl_xor_sync(0xffffffffu, vy, o);
+        }
+        if (lane == 0) {
+          red[warp * ncoef + 2 * nc + q] += (double)vx;
+          red[warp * ncoef + 2 * nc + 3 + q] += (double)vy;
+        }
+        lp *= ltf;
       }
     }
   }
