@@ -6,6 +6,7 @@
     python -m paper_2008_05858_gb300.cli render --config 2 --orders 12 --psf table
     python -m paper_2008_05858_gb300.cli noise --config 2 --orders 12
     python -m paper_2008_05858_gb300.cli photons --config 2 --orders 12 --photons 1e8
+    python -m paper_2008_05858_gb300.cli adjoint --config 5
 
 ``--orders`` shortens the full-detector workload (config 2) to its first orders so a profiler
 capture stays small; every other shape is the named configuration's.
@@ -108,6 +109,32 @@ def cmd_photons(args) -> int:
     return 0
 
 
+def cmd_adjoint(args) -> int:
+    import torch
+
+    from .binding import Renderer
+
+    w = _workload(args)
+    r = Renderer(args.device, kernel_timing=1)
+    mid = r.load_model(w.model)
+    sids = r.load_spectra(w)
+    frame = r.render(mid, sids, "mixed", "f32")[0]
+    g = torch.Generator(device=frame.device)
+    g.manual_seed(5)
+    dldi = torch.randn(frame.shape, dtype=torch.float64, device=frame.device, generator=g)  # a seeded dL/dI
+    grads = r.adjoint(mid, sids, [dldi])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.repeat):
+        grads = r.adjoint(mid, sids, [dldi])
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / max(args.repeat, 1)
+    n = sum(int(t.numel()) for t in grads)
+    print(f"{w.name}: gradient of {n} coefficients over {w.model.n_stamps} stamps, {dt * 1e3:.3f} ms (wall)")
+    r.close()
+    return 0
+
+
 def cmd_aliasing(args) -> int:
     import json
 
@@ -144,7 +171,8 @@ def main(argv=None) -> int:
     p.add_argument("--psf", default="analytic", choices=["analytic", "table"])
     pn = sub.add_parser("noise", help="detector noise stage on a rendered frame")
     pp = sub.add_parser("photons", help="photon Monte-Carlo render")
-    for q in (pn, pp):
+    pj = sub.add_parser("adjoint", help="gradient of a frame loss (adjoint kernel) for a seeded dL/dI")
+    for q in (pn, pp, pj):
         q.add_argument("--config", type=int, default=2)
         q.add_argument("--orders", type=int, default=0)
         q.add_argument("--repeat", type=int, default=3)
@@ -164,6 +192,8 @@ def main(argv=None) -> int:
         return cmd_noise(args)
     if args.cmd == "photons":
         return cmd_photons(args)
+    if args.cmd == "adjoint":
+        return cmd_adjoint(args)
     return 1
 
 
