@@ -4,6 +4,8 @@
 // The spectral-format "database" of the paper (Sec. 2.1) is computed once and reused across
 // simulations; here an optical model is validated, copied to the device and planned once
 // (e2e_load_model), spectra are resident too, and a render only launches kernels.
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -38,6 +40,15 @@ int cuda_fail(cudaError_t e, const char* what) {
   g_err = std::string(what) + ": " + cudaGetErrorString(e);
   return e == cudaErrorMemoryAllocation ? E2E_ENOMEM : E2E_ECUDA;
 }
+
+// An NVTX range around one stage of the runtime (visible to profilers that record NVTX; a
+// pointer check otherwise).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 #define E2E_CK(call)                                       \
   do {                                                     \
@@ -368,6 +379,7 @@ double variant_cost(int K, int DX, int DY, int B) {
 
 // Effective-PSF tables of a tabulated-PSF model, built on the device at load time.
 int build_psf_tables(Model* m, int P) {
+  NvtxRange nvtx_("e2e psf tables");
   m->phases = P;
   const int ns = (int)m->slices.size();
   std::vector<TableSlice> ts(ns);
@@ -498,6 +510,7 @@ int plan_bands_and_tiles(Model* m) {
 }
 
 int plan_model(Model* m) {
+  NvtxRange nvtx_("e2e plan");
   Plan& P = m->plan;
   const int ns = (int)m->slices.size();
   const bool ellip = m->psf != E2E_PSF_SEPARABLE;  // item shape of the non-separable kernels
@@ -751,6 +764,7 @@ cudaError_t launch_items(e2e_ctx* ctx, Model* m, int K, int first, int count, co
 
 int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, int precision, int dtype,
                 void* const* dst, const int64_t* pitch_in, cudaStream_t st) {
+  NvtxRange nvtx_("e2e render");
   if (dtype != E2E_F32 && dtype != E2E_F64) return fail(E2E_EINVAL, "dtype must be E2E_F32 or E2E_F64");
   if (precision != E2E_PREC_MIXED && precision != E2E_PREC_FP64) return fail(E2E_EINVAL, "bad precision");
   if (!dst) return fail(E2E_EINVAL, "null destination list");
@@ -891,6 +905,7 @@ void band_rows(const Model* m, int d, int b, int& r0, int& r1) {
 // The frame is the one e2e_render writes: same items, same order, same merge.
 int render_host_banded(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, int dtype, void* const* host,
                        const std::vector<int64_t>& pitch, cudaStream_t st) {
+  NvtxRange nvtx_("e2e render host");
   Plan& P = m->plan;
   if (!P.ok) return fail(E2E_EINVAL, "model has no mixed-precision plan");
   std::vector<const double*> table;
@@ -1078,6 +1093,7 @@ void e2e_destroy(e2e_ctx* ctx) {
 }
 
 int e2e_load_model(e2e_ctx* ctx, const e2e_model_desc* desc, uint64_t* model_id) {
+  NvtxRange nvtx_("e2e load model");
   if (!ctx || !desc || !model_id) return fail(E2E_EINVAL, "null argument");
   if (desc->n_detectors < 1 || !desc->height || !desc->width) return fail(E2E_EINVAL, "need >= 1 detector");
   if (desc->n_slices < 0 || (desc->n_slices > 0 && !desc->slices)) return fail(E2E_EINVAL, "bad slice list");
@@ -1252,6 +1268,7 @@ int e2e_unload_model(e2e_ctx* ctx, uint64_t model_id) {
 
 int e2e_load_spectrum(e2e_ctx* ctx, int32_t fiber, int32_t n_orders, const int32_t* order_ids,
                       const int32_t* n_lambda, const double* flux, uint64_t* spec_id) {
+  NvtxRange nvtx_("e2e load spectrum");
   if (!ctx || !spec_id || n_orders < 0 || (n_orders > 0 && (!order_ids || !n_lambda || !flux)))
     return fail(E2E_EINVAL, "null or negative argument");
   auto sp = std::make_unique<Spectrum>();
@@ -1520,6 +1537,7 @@ int e2e_render_static(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uin
 int e2e_render_adjoint(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids, int32_t dtype,
                        const void* const* dldi, const int64_t* pitch_in, double* g_cx, double* g_cy, double* g_sx,
                        double* g_sy, void* stream) {
+  NvtxRange nvtx_("e2e adjoint");
   if (!ctx || !dldi || !g_cx || !g_cy || !g_sx || !g_sy) return fail(E2E_EINVAL, "null argument");
   if (dtype != E2E_F32 && dtype != E2E_F64) return fail(E2E_EINVAL, "dtype must be E2E_F32 or E2E_F64");
   DeviceGuard g(ctx->device);
@@ -1946,6 +1964,7 @@ int e2e_server_stop(e2e_ctx* ctx) {
 
 int e2e_render_photons(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids, uint64_t seed,
                        uint32_t* const* dst, const int64_t* pitch_elems, uint64_t* total_photons, void* stream) {
+  NvtxRange nvtx_("e2e photons");
   if (!ctx || !dst) return fail(E2E_EINVAL, "null argument");
   DeviceGuard g(ctx->device);
   std::lock_guard<std::mutex> lk(ctx->mu);
@@ -2012,6 +2031,7 @@ int e2e_render_photons(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const ui
 int e2e_add_noise(e2e_ctx* ctx, uint64_t model_id, const e2e_noise_params* p, int32_t src_dtype,
                   const void* const* src, const int64_t* src_pitch, int32_t dst_dtype, void* const* dst,
                   const int64_t* dst_pitch, void* stream) {
+  NvtxRange nvtx_("e2e noise");
   if (!ctx || !p || !src || !dst) return fail(E2E_EINVAL, "null argument");
   if (src_dtype != E2E_F32 && src_dtype != E2E_F64) return fail(E2E_EINVAL, "src dtype must be E2E_F32 or E2E_F64");
   if (dst_dtype != E2E_F32 && dst_dtype != E2E_F64 && dst_dtype != E2E_U16) return fail(E2E_EINVAL, "bad dst dtype");

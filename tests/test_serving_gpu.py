@@ -129,3 +129,41 @@ def test_express_jobs_overtake_queued_frames(renderer):
     ref = renderer.render(sid, ss, "mixed", "f32")
     torch.cuda.synchronize()
     assert torch.equal(ref[0], s_out[0])
+
+
+def test_failed_job_leaves_other_jobs_and_the_model_intact(renderer):
+    # A job that passes submission but fails when it is launched (its destination pitch is
+    # below the frame width, which the render checks) reports its error and frees its slot
+    # and budget; the jobs queued around it and the resident model are not affected.
+    from paper_2008_05858_gb300.binding import E2E_EINVAL, E2EError, Server
+
+    ms = _models(renderer)
+    alone = []
+    for mid, sids, w in ms:
+        f = renderer.render(mid, sids, "mixed", "f32")
+        torch.cuda.synchronize()
+        alone.append([t.clone() for t in f])
+    srv = Server(renderer, max_inflight=2)
+    outs, rids, bad = [], [], []
+    for q, (mid, sids, w) in enumerate(ms):
+        out = renderer.empty_frames(mid, "f32")
+        rids.append(srv.submit(mid, sids, "mixed", "f32", out=out))
+        outs.append((q, out))
+        h, wd = w.model.det_shape[0]
+        narrow = [torch.empty(h * wd, device="cuda").as_strided((h, wd), (wd - 1, 1))]
+        bad.append(srv.submit(mid, sids, "mixed", "f32", out=narrow))
+    for b in bad:
+        with pytest.raises(E2EError) as e:
+            srv.wait(b)
+        assert e.value.code == E2E_EINVAL
+    infos = [srv.wait(r) for r in rids]
+    srv.stop()
+    for (q, out), info in zip(outs, infos):
+        assert info["status"] == 0
+        for a, b in zip(out, alone[q]):
+            assert torch.equal(a, b)
+    for (mid, sids, w), ref in zip(ms, alone):  # the models still render the same frames
+        again = renderer.render(mid, sids, "mixed", "f32")
+        torch.cuda.synchronize()
+        for a, b in zip(again, ref):
+            assert torch.equal(a, b)
