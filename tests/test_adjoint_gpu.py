@@ -35,8 +35,9 @@ def check_groups(got, ref, atol_frac=2e-5, rtol=2e-4):
 
 @pytest.mark.parametrize("kw", [dict(seed=5, K=9, degree=3, n_lambda=90, n_slit=9),
                                 dict(seed=6, K=11, degree=5, n_lambda=200, n_slit=32),
-                                dict(seed=7, K=7, degree=4, n_lambda=333, n_slit=13, orders=3)],
-                         ids=["k9", "k11", "k7"])
+                                dict(seed=7, K=7, degree=4, n_lambda=333, n_slit=13, orders=3),
+                                dict(seed=8, K=15, degree=8, n_lambda=120, n_slit=20)],
+                         ids=["k9", "k11", "k7", "k15-degree8"])
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 def test_adjoint_matches_oracle_vjp(renderer, kw, dtype):
     w = W.small_config(**kw)

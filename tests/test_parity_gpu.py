@@ -60,6 +60,7 @@ SMALL = [
     dict(seed=13, K=1, degree=0, n_lambda=31, n_slit=2),
     dict(seed=14, K=15, degree=5, n_lambda=60, n_slit=7, width=400, height=200),
     dict(seed=15, K=11, degree=5, n_lambda=2000, n_slit=128, orders=1, fibers=1, slices=1, width=512, height=64),
+    dict(seed=16, K=15, degree=8, n_lambda=150, n_slit=20),  # the largest window and degree accepted
 ]
 
 
@@ -178,6 +179,70 @@ def test_linearity_in_the_spectrum(renderer):
     a = gpu_frames(renderer, w, "mixed", "f64")[0]
     b = gpu_frames(renderer, w2, "mixed", "f64")[0]
     assert np.allclose(b, 2.5 * a, rtol=2e-6, atol=1e-10 * np.abs(b).max())
+
+
+def _scaled(seed, fn):
+    w = W.small_config(seed=seed, n_lambda=300, n_slit=17)
+    for f in w.spectra:
+        for o in w.spectra[f].flux:
+            w.spectra[f].flux[o] = fn(f, o, np.asarray(w.spectra[f].flux[o], dtype=np.float64))
+    return w
+
+
+@pytest.mark.parametrize("scale", [1e-15, 1e15], ids=["1e-15", "1e15"])
+def test_flux_far_from_unity(renderer, scale):
+    """Each item's fixed-point scale follows its own flux bound: a spectrum at 1e-15 or 1e15
+    renders to the same relative accuracy as one near 1."""
+    w = _scaled(91, lambda f, o, x: x * scale)
+    for dtype in ("f32", "f64"):
+        g = gpu_frames(renderer, w, "mixed", dtype)
+        ref = oracle_frames(w)
+        for a, b in zip(g, ref):
+            rep = compare(a, b)
+            assert rep.ok, f"{dtype}: {rep}"
+
+
+def test_fibers_six_decades_apart(renderer):
+    """A bright fiber (x1e3) beside a faint one (x1e-3): the faint trace's pixels, 1e-6 of the
+    frame's peak, keep the per-pixel relative accuracy (per-item scales, compensated merge)."""
+    w = _scaled(92, lambda f, o, x: x * (1e3 if f == 0 else 1e-3))
+    g = gpu_frames(renderer, w, "mixed", "f32")
+    ref = oracle_frames(w)
+    bright = _scaled(92, lambda f, o, x: x * (1e3 if f == 0 else 0.0))
+    ref_bright = oracle.render_workload(bright)
+    for a, b, bb in zip(g, ref, ref_bright):
+        rep = compare(a, b)
+        assert rep.ok, str(rep)
+        # the faint trace's pixels that no bright stamp reaches, down to 1e-4 of the faint
+        # fiber's peak (1e-10 of the frame's), keep the relative bound without its floor
+        faint_peak = np.abs(np.where(bb == 0, b, 0)).max()
+        sel = (bb == 0) & (np.abs(b) > 1e-4 * faint_peak)
+        assert sel.sum() > 100 and faint_peak < 1e-5 * np.abs(b).max()
+        assert np.all(np.abs(a[sel] - b[sel]) <= 1e-6 * np.abs(b[sel])), float(
+            np.max(np.abs(a[sel] - b[sel]) / np.abs(b[sel])))
+
+
+def test_signed_spectrum(renderer):
+    """A spectrum of both signs (a continuum-subtracted template): the fixed-point words are
+    signed, and the error is bounded by the relative bound applied to the render of |flux|
+    (cancelling contributions cannot be more accurate than their parts)."""
+    rng = np.random.default_rng(93)
+    signs = {}
+
+    def signed(f, o, x):
+        signs[(f, o)] = rng.choice([-1.0, 1.0], size=x.shape)
+        return x * signs[(f, o)]
+
+    w = _scaled(93, signed)
+    w_abs = _scaled(93, lambda f, o, x: x)
+    g = gpu_frames(renderer, w, "mixed", "f64")
+    ref = oracle_frames(w)
+    ref_abs = oracle.render_workload(w_abs)
+    for a, b, babs in zip(g, ref, ref_abs):
+        assert np.any(b < 0) and np.any(b > 0)
+        err = np.abs(a - b)
+        assert np.all(err <= 1e-6 * np.abs(babs) + 1e-10 * np.abs(babs).max()), float(
+            np.max(err / (np.abs(babs) + 1e-300)))
 
 
 @pytest.mark.parametrize("mutate,msg", [
