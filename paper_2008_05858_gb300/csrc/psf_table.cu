@@ -146,8 +146,8 @@ struct TableArgs {
 
 // One CTA per work item (<= 32 samples x <= 16 slit points); the warp's 32 stamps are mapped
 // into staging, then taken one after the other by the whole warp: each lane reads its pixels
-// from the 8 tables around the stamp's phase and wavelength, blends, and deposits into the
-// item's box as exact fixed point.
+// from the 8 tables around the stamp's phase and wavelength, blends, sums them over stamps
+// with the same window origin, and deposits the sums into the item's box as exact fixed point.
 template <int K>
 __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) {
   const MixedArgs& a = ta.m;
@@ -228,6 +228,36 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
   const int nst = it.nj * it.nk;
   int4* wst = stage + warp * 32;
   float2* wsw = stagew + warp * 32;
+  // Each lane owns the pixels e = lane, lane + 32, ... of the window.  Consecutive stamps of a
+  // warp are consecutive slit points of one sample, whose windows often share their origin:
+  // a lane adds its pixels' values in FP32 registers while the origin stays the same (at most
+  // kTRun stamps) and deposits them into the box when it moves.
+  constexpr int NI = (KK + 31) / 32;
+  constexpr int kTRun = 16;
+  float acc[NI];
+#pragma unroll
+  for (int i = 0; i < NI; ++i) acc[i] = 0.f;
+  int cx = kOffFrame, cy = kOffFrame, n_acc = 0;  // warp-uniform: origin and stamps held
+  auto flush = [&]() {
+    const int bxs = cx - K / 2 - it.bx0, bys = cy - K / 2 - it.by0;
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      const int e = lane + 32 * i;
+      if (e >= KK) break;
+      const int n = e / K, m = e - n * K;
+      const int bx = bxs + m, by = bys + n;
+      const float v = acc[i];
+      acc[i] = 0.f;
+      if (bx < 0 || bx >= it.bw || by < 0 || by >= it.bh) {
+        if (a.err) {
+          const int X = it.bx0 + bx, Y = it.by0 + by;
+          if (X >= 0 && X < S.W && Y >= 0 && Y < S.H) atomicAdd(a.err, 1);
+        }
+        continue;
+      }
+      box_deposit(boxh + by * it.bw + bx, boxl + by * it.bw + bx, v, sc, sc_hi);
+    }
+  };
   for (int base = warp * 32; base < nst && total > 0.0; base += kTWarps * 32) {
     {
       const int idx = base + lane;
@@ -253,12 +283,18 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
     }
     __syncwarp();
     const int nb = min(32, nst - base);
-    // stamp by stamp (warp-uniform), each lane owning the pixels lane, lane + 32, ... of the
-    // window: the phase, the field weight and the 8 table rows are computed once per stamp,
-    // a pixel costs 8 coalesced table reads, 8 FMAs and its deposit
+    // stamp by stamp (warp-uniform): the phase, the field weight and the 8 table rows are
+    // computed once per stamp, a pixel costs 8 coalesced table reads and 8 FMAs
     for (int b = 0; b < nb; ++b) {
       const int4 st = wst[b];
       if (st.x == kOffFrame || st.y == kOffFrame) continue;
+      if (st.x != cx || st.y != cy || n_acc == kTRun) {
+        if (n_acc) flush();
+        cx = st.x;
+        cy = st.y;
+        n_acc = 0;
+      }
+      ++n_acc;
       const float2 sw = wsw[b];
       const int4 fw = tabF[__float_as_int(sw.y)];
       const float rx = (__int_as_float(st.z) + 0.5f) * (float)P, ry = (__int_as_float(st.w) + 0.5f) * (float)P;
@@ -270,10 +306,7 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
       const int row = (ipy * (P + 1) + ipx) * KK, drow = (P + 1) * KK;
       const float* A = T + (int64_t)fw.x * node_stride + row;  // node f0
       const float* Bn = T + (int64_t)fw.y * node_stride + row; // node f1
-      const int bxs = st.x - K / 2 - it.bx0, bys = st.y - K / 2 - it.by0;
-      // all table reads of this lane's pixels first (they do not depend on the deposits),
-      // then the blends and deposits
-      constexpr int NI = (KK + 31) / 32;
+      // all table reads of this lane's pixels first, then the blends
       float tv[NI][8];
 #pragma unroll
       for (int i = 0; i < NI; ++i) {
@@ -289,23 +322,14 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
       for (int i = 0; i < NI; ++i) {
         const int e = lane + 32 * i;
         if (e >= KK) break;
-        const int n = e / K, m = e - n * K;
-        const int bx = bxs + m, by = bys + n;
-        if (bx < 0 || bx >= it.bw || by < 0 || by >= it.bh) {
-          if (a.err) {
-            const int X = it.bx0 + bx, Y = it.by0 + by;
-            if (X >= 0 && X < S.W && Y >= 0 && Y < S.H) atomicAdd(a.err, 1);
-          }
-          continue;
-        }
         const float t0 = fmaf(c00, tv[i][0], fmaf(c01, tv[i][1], fmaf(c10, tv[i][2], c11 * tv[i][3])));
         const float t1 = fmaf(c00, tv[i][4], fmaf(c01, tv[i][5], fmaf(c10, tv[i][6], c11 * tv[i][7])));
-        const int q = by * it.bw + bx;
-        box_deposit(boxh + q, boxl + q, fmaf(wf0, t0, wf1 * t1), sc, sc_hi);
+        acc[i] += fmaf(wf0, t0, wf1 * t1);
       }
     }
     __syncwarp();
   }
+  if (n_acc) flush();
   __syncthreads();
   float2* out = a.store + it.store_off;
   const float inv = ldexpf(1.f, -Psh);
