@@ -128,8 +128,8 @@ struct TableLayout {
     tabU = o; o += (size_t)NK * 8;
     o = (o + 15) & ~(size_t)15;
     tabF = o; o += (size_t)J * 16;              // (f0, f1, weight of f1, -) per sample
-    stage = o; o += (size_t)kTWarps * 32 * 16;
-    stagew = o; o += (size_t)kTWarps * 32 * 8;
+    stage = o; o += (size_t)kTWarps * 32 * 16;   // per staged stamp: origin, table row offsets
+    stagew = o; o += (size_t)kTWarps * 32 * 32;  // blend coefficients of the 8 table reads
     boxh = o; o += (size_t)area * 4;
     boxl = o; o += (size_t)area * 4;
     total = o;
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
   float2* tabU = reinterpret_cast<float2*>(smem + L.tabU);
   int4* tabF = reinterpret_cast<int4*>(smem + L.tabF);
   int4* stage = reinterpret_cast<int4*>(smem + L.stage);
-  float2* stagew = reinterpret_cast<float2*>(smem + L.stagew);
+  float4* stagew = reinterpret_cast<float4*>(smem + L.stagew);
   int* boxh = reinterpret_cast<int*>(smem + L.boxh);
   unsigned* boxl = reinterpret_cast<unsigned*>(smem + L.boxl);
   __shared__ double s_w[kTWarps], s_u[kTWarps];
@@ -223,11 +223,12 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
   const int Psh = total > 0.0 ? max(-100, min(100, 52 - ex)) : 0;
   const float sc = ldexpf(1.f, Psh), sc_hi = ldexpf(1.f, Psh - 22);
   const float* T = ta.T32 + TS.tab_off;
-  const int64_t node_stride = (int64_t)(P + 1) * (P + 1) * KK;
+  const int node_stride = (P + 1) * (P + 1) * KK;  // n_field (P + 1)^2 <= 65535: offsets fit in 32 bits
+  const int drow = (P + 1) * KK;
 
   const int nst = it.nj * it.nk;
   int4* wst = stage + warp * 32;
-  float2* wsw = stagew + warp * 32;
+  float4* wsw = stagew + warp * 64;
   // Each lane owns the pixels e = lane, lane + 32, ... of the window.  Consecutive stamps of a
   // warp are consecutive slit points of one sample, whose windows often share their origin:
   // a lane adds its pixels' values in FP32 registers while the origin stays the same (at most
@@ -260,11 +261,14 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
   };
   for (int base = warp * 32; base < nst && total > 0.0; base += kTWarps * 32) {
     {
+      // lane i maps stamp base + i and prepares what the whole warp needs of it: the window
+      // origin, the offsets of the table rows around its phase at its two field nodes, and the
+      // 8 blend coefficients (bilinear in phase, linear in wavelength, times the stamp weight)
       const int idx = base + lane;
-      int ci = kOffFrame, ri = kOffFrame, jj = 0;
-      float fx = 0.f, fy = 0.f, w = 0.f;
+      int ci = kOffFrame, ri = kOffFrame, aoff = 0, boff = 0;
+      float4 ca = make_float4(0.f, 0.f, 0.f, 0.f), cb = ca;
       if (idx < nst) {
-        jj = idx / it.nk;
+        const int jj = idx / it.nk;
         const int kk = idx - jj * it.nk;
         double px[9], py[9];
 #pragma unroll
@@ -273,18 +277,31 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
           py[b] = b < nd ? tabP[(jj * 2 + 1) * nd + b] : 0.0;
         }
         const double s = tabS[kk];
+        float fx, fy;
         split_coord(horner_s(px, S.degree, s), ci, fx);
         split_coord(horner_s(py, S.degree, s), ri, fy);
         const float2 wj = tabW[jj], uk = tabU[kk];
-        w = fmaf(wj.x, uk.x, fmaf(wj.x, uk.y, wj.y * uk.x));
+        const float w = fmaf(wj.x, uk.x, fmaf(wj.x, uk.y, wj.y * uk.x));
+        const int4 fw = tabF[jj];
+        const float rx = (fx + 0.5f) * (float)P, ry = (fy + 0.5f) * (float)P;
+        const int ipx = min(P - 1, max(0, (int)floorf(rx))), ipy = min(P - 1, max(0, (int)floorf(ry)));
+        const float ax = rx - (float)ipx, ay = ry - (float)ipy;
+        const float wf1 = __int_as_float(fw.z), wf0 = 1.f - wf1;
+        const float c00 = (1.f - ay) * (1.f - ax) * w, c01 = (1.f - ay) * ax * w;
+        const float c10 = ay * (1.f - ax) * w, c11 = ay * ax * w;
+        ca = make_float4(wf0 * c00, wf0 * c01, wf0 * c10, wf0 * c11);
+        cb = make_float4(wf1 * c00, wf1 * c01, wf1 * c10, wf1 * c11);
+        const int row = (ipy * (P + 1) + ipx) * KK;
+        aoff = fw.x * node_stride + row;
+        boff = fw.y * node_stride + row;
       }
-      wst[lane] = make_int4(ci, ri, __float_as_int(fx), __float_as_int(fy));
-      wsw[lane] = make_float2(w, __int_as_float(jj));
+      wst[lane] = make_int4(ci, ri, aoff, boff);
+      wsw[2 * lane] = ca;
+      wsw[2 * lane + 1] = cb;
     }
     __syncwarp();
     const int nb = min(32, nst - base);
-    // stamp by stamp (warp-uniform): the phase, the field weight and the 8 table rows are
-    // computed once per stamp, a pixel costs 8 coalesced table reads and 8 FMAs
+    // stamp by stamp (warp-uniform): a pixel costs 8 coalesced table reads and 8 FMAs
     for (int b = 0; b < nb; ++b) {
       const int4 st = wst[b];
       if (st.x == kOffFrame || st.y == kOffFrame) continue;
@@ -295,17 +312,9 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
         n_acc = 0;
       }
       ++n_acc;
-      const float2 sw = wsw[b];
-      const int4 fw = tabF[__float_as_int(sw.y)];
-      const float rx = (__int_as_float(st.z) + 0.5f) * (float)P, ry = (__int_as_float(st.w) + 0.5f) * (float)P;
-      const int ipx = min(P - 1, max(0, (int)floorf(rx))), ipy = min(P - 1, max(0, (int)floorf(ry)));
-      const float ax = rx - (float)ipx, ay = ry - (float)ipy;
-      const float wf1 = __int_as_float(fw.z), wf0 = 1.f - wf1;
-      const float c00 = (1.f - ay) * (1.f - ax) * sw.x, c01 = (1.f - ay) * ax * sw.x;
-      const float c10 = ay * (1.f - ax) * sw.x, c11 = ay * ax * sw.x;
-      const int row = (ipy * (P + 1) + ipx) * KK, drow = (P + 1) * KK;
-      const float* A = T + (int64_t)fw.x * node_stride + row;  // node f0
-      const float* Bn = T + (int64_t)fw.y * node_stride + row; // node f1
+      const float4 ca = wsw[2 * b], cb = wsw[2 * b + 1];
+      const float* A = T + st.z;   // node f0
+      const float* Bn = T + st.w;  // node f1
       // all table reads of this lane's pixels first, then the blends
       float tv[NI][8];
 #pragma unroll
@@ -322,9 +331,14 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
       for (int i = 0; i < NI; ++i) {
         const int e = lane + 32 * i;
         if (e >= KK) break;
-        const float t0 = fmaf(c00, tv[i][0], fmaf(c01, tv[i][1], fmaf(c10, tv[i][2], c11 * tv[i][3])));
-        const float t1 = fmaf(c00, tv[i][4], fmaf(c01, tv[i][5], fmaf(c10, tv[i][6], c11 * tv[i][7])));
-        acc[i] += fmaf(wf0, t0, wf1 * t1);
+        float t = ca.x * tv[i][0];  // the stamp's value first, then one rounding into the sum
+        t = fmaf(ca.y, tv[i][1], t);
+        t = fmaf(ca.z, tv[i][2], t);
+        t = fmaf(ca.w, tv[i][3], t);
+        t = fmaf(cb.x, tv[i][4], t);
+        t = fmaf(cb.y, tv[i][5], t);
+        t = fmaf(cb.z, tv[i][6], t);
+        acc[i] += fmaf(cb.w, tv[i][7], t);
       }
     }
     __syncwarp();
