@@ -384,12 +384,13 @@ int build_psf_tables(Model* m, int P) {
   const int ns = (int)m->slices.size();
   std::vector<TableSlice> ts(ns);
   std::vector<double> field, maps;
-  int64_t tab = 0;
+  int64_t tab = 0, tab32 = 0;
   int max_field = 1;
   for (int i = 0; i < ns; ++i) {
     const e2e_order_slice& s = m->slices[i].d;
     TableSlice& t = ts[i];
     t.tab_off = tab;
+    t.tab_off32 = tab32;
     t.map_off = (int64_t)maps.size();
     t.field_off = (int32_t)field.size();
     t.n_field = s.n_field;
@@ -399,6 +400,7 @@ int build_psf_tables(Model* m, int P) {
     field.insert(field.end(), s.field_lt, s.field_lt + s.n_field);
     maps.insert(maps.end(), s.maps, s.maps + (size_t)s.n_field * s.map_size * s.map_size);
     tab += (int64_t)s.n_field * (P + 1) * (P + 1) * s.K * s.K;
+    tab32 += (int64_t)s.n_field * (P + 1) * (P + 1) * table_row32(s.K);
     max_field = std::max(max_field, s.n_field);
   }
   if ((int64_t)max_field * (P + 1) * (P + 1) > 65535) return fail(E2E_EINVAL, "too many field nodes x phases");
@@ -410,8 +412,12 @@ int build_psf_tables(Model* m, int P) {
   if (rc == E2E_OK && cudaMalloc((void**)&d_norms, std::max<size_t>(1, field.size()) * sizeof(double)) != cudaSuccess)
     rc = fail(E2E_ENOMEM, "map norms");
   if (rc == E2E_OK && (cudaMalloc((void**)&m->d_T64, std::max<int64_t>(1, tab) * sizeof(double)) != cudaSuccess ||
-                       cudaMalloc((void**)&m->d_T32, std::max<int64_t>(1, tab) * sizeof(float)) != cudaSuccess))
+                       cudaMalloc((void**)&m->d_T32, std::max<int64_t>(1, tab32) * sizeof(float)) != cudaSuccess))
     rc = fail(E2E_ENOMEM, "PSF tables");
+  if (rc == E2E_OK) {  // the FP32 rows' padding is never read; zero it all the same
+    const cudaError_t e = cudaMemset(m->d_T32, 0, std::max<int64_t>(1, tab32) * sizeof(float));
+    if (e != cudaSuccess) rc = cuda_fail(e, "PSF tables");
+  }
   if (rc == E2E_OK) {
     cudaError_t e = launch_epsf_build(m->d_ts, ns, max_field, d_maps, d_norms, P, m->d_T64, m->d_T32, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();

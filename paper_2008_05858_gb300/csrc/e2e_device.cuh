@@ -41,12 +41,17 @@ struct Item {
 
 // Tabulated-PSF slice: its maps, field nodes and effective-PSF tables in the model's arrays.
 struct TableSlice {
-  int64_t tab_off;    // first table entry (n_field x (P+1)^2 x K^2)
+  int64_t tab_off;    // first FP64 table entry (n_field x (P+1)^2 x K^2)
+  int64_t tab_off32;  // first FP32 table entry (n_field x (P+1)^2 rows of table_row32(K) floats)
   int64_t map_off;    // first map sample (n_field x M^2)
   int32_t field_off;  // first field node
   int32_t n_field, map_size, K;
   double q;           // map samples per pixel
 };
+
+// Floats per FP32 table row: the K^2 window pixels padded to a multiple of 32, so that every
+// row starts on a 128-byte line and a warp's 32 consecutive reads touch 4 sectors, not 5.
+__host__ __device__ constexpr int table_row32(int K) { return (K * K + 31) / 32 * 32; }
 
 // Output tile of the merge: tile (tx, ty) of detector det lists items[list_off .. list_off+n).
 struct Tile {

@@ -82,9 +82,9 @@ __global__ void __launch_bounds__(256) k_epsf_build(const TableSlice* __restrict
       sum += row * wy;
     }
     const double val = sum / norm;
-    const int64_t idx = t.tab_off + ((int64_t)ph + (int64_t)f * (P + 1) * (P + 1)) * K * K + e;
-    T64[idx] = val;
-    T32[idx] = (float)val;
+    const int64_t r = (int64_t)ph + (int64_t)f * (P + 1) * (P + 1);
+    T64[t.tab_off + r * K * K + e] = val;
+    T32[t.tab_off32 + r * table_row32(K) + e] = (float)val;
   }
 }
 
@@ -222,9 +222,10 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
   frexp(total, &ex);
   const int Psh = total > 0.0 ? max(-100, min(100, 52 - ex)) : 0;
   const float sc = ldexpf(1.f, Psh), sc_hi = ldexpf(1.f, Psh - 22);
-  const float* T = ta.T32 + TS.tab_off;
-  const int node_stride = (P + 1) * (P + 1) * KK;  // n_field (P + 1)^2 <= 65535: offsets fit in 32 bits
-  const int drow = (P + 1) * KK;
+  constexpr int KR = table_row32(K);  // floats per table row
+  const float* T = ta.T32 + TS.tab_off32;
+  const int node_stride = (P + 1) * (P + 1) * KR;  // n_field (P + 1)^2 <= 65535: offsets fit in 32 bits
+  const int drow = (P + 1) * KR;
 
   const int nst = it.nj * it.nk;
   int4* wst = stage + warp * 32;
@@ -291,7 +292,7 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
         const float c10 = ay * (1.f - ax) * w, c11 = ay * ax * w;
         ca = make_float4(wf0 * c00, wf0 * c01, wf0 * c10, wf0 * c11);
         cb = make_float4(wf1 * c00, wf1 * c01, wf1 * c10, wf1 * c11);
-        const int row = (ipy * (P + 1) + ipx) * KK;
+        const int row = (ipy * (P + 1) + ipx) * KR;
         aoff = fw.x * node_stride + row;
         boff = fw.y * node_stride + row;
       }
@@ -321,10 +322,10 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
       for (int i = 0; i < NI; ++i) {
         const int e = lane + 32 * i;
         if (e < KK) {
-          tv[i][0] = __ldg(A + e); tv[i][1] = __ldg(A + e + KK);
-          tv[i][2] = __ldg(A + e + drow); tv[i][3] = __ldg(A + e + drow + KK);
-          tv[i][4] = __ldg(Bn + e); tv[i][5] = __ldg(Bn + e + KK);
-          tv[i][6] = __ldg(Bn + e + drow); tv[i][7] = __ldg(Bn + e + drow + KK);
+          tv[i][0] = __ldg(A + e); tv[i][1] = __ldg(A + e + KR);
+          tv[i][2] = __ldg(A + e + drow); tv[i][3] = __ldg(A + e + drow + KR);
+          tv[i][4] = __ldg(Bn + e); tv[i][5] = __ldg(Bn + e + KR);
+          tv[i][6] = __ldg(Bn + e + drow); tv[i][7] = __ldg(Bn + e + drow + KR);
         }
       }
 #pragma unroll
