@@ -31,8 +31,12 @@ def frames(r, w, precision, dtype):
     return res
 
 
+# K = 11, 9, 13, 15 and 3: FP32 table rows of 121, 81, 169, 225 and 9 floats padded to 128, 96,
+# 192, 256 and 32
 CASES = [dict(seed=701, coma=0.0), dict(seed=702, coma=0.3, K=9, n_lambda=200, n_slit=12),
-         dict(seed=703, coma=0.2, K=13, n_lambda=90, n_slit=20, phases=4)]
+         dict(seed=703, coma=0.2, K=13, n_lambda=90, n_slit=20, phases=4),
+         dict(seed=704, coma=0.1, K=15, n_lambda=60, n_slit=9, phases=2),
+         dict(seed=705, coma=0.2, K=3, n_lambda=120, n_slit=6, phases=16)]
 
 
 @pytest.mark.parametrize("kw", CASES, ids=[f"t{c['seed']}" for c in CASES])
