@@ -172,37 +172,53 @@ __device__ void photon_exact(const DevSlice& S, const double* __restrict__ C, do
 
 // Offset of the photon from the bin's anchor along one coordinate, in FP32, and a bound on its
 // distance from the exact value: delta * Q(lt, lt_j) for the b = 0 polynomial (its divided
-// difference, so no large terms cancel) plus the slit terms sum_{b>=1} P_b(lt) s^b.
-__device__ __forceinline__ float photon_offset(const float* cf, int d, float lt, float ltj, float delta, float s,
+// difference, so no large terms cancel) plus the slit terms sum_{b>=1} P_b(lt) s^b.  D is the
+// slice's degree, a template parameter so that only its terms are evaluated.
+template <int D>
+__device__ __forceinline__ float photon_offset(const float* cf, float lt, float ltj, float delta, float s,
                                                float& mag) {
   float q[8];
 #pragma unroll
   for (int a = 0; a < 8; ++a) q[a] = 0.f;
-  // q_a = c_a0 + ltj q_{a+1} (a = d .. 1), Q = sum_a q_a lt^(a-1)
+  // q_a = c_a0 + ltj q_{a+1} (a = D .. 1), Q = sum_a q_a lt^(a-1)
   float acc = 0.f;
 #pragma unroll
-  for (int a = 8; a >= 1; --a) {
-    if (a <= d) acc = fmaf(ltj, acc, cf[a * (a + 1) / 2]);  // index(a, 0) = a(a+1)/2
-    if (a <= d) q[a - 1] = acc;
+  for (int a = D; a >= 1; --a) {
+    acc = fmaf(ltj, acc, cf[a * (a + 1) / 2]);  // index(a, 0) = a(a+1)/2
+    q[a - 1] = acc;
   }
   float Q = 0.f;
 #pragma unroll
-  for (int a = 8; a >= 1; --a)
-    if (a <= d) Q = fmaf(Q, lt, q[a - 1]);
-  // slit terms: Horner in s over P_b(lt), b = d .. 1
+  for (int a = D; a >= 1; --a) Q = fmaf(Q, lt, q[a - 1]);
+  // slit terms: Horner in s over P_b(lt), b = D .. 1
   float sb = 0.f;
 #pragma unroll
-  for (int b = 8; b >= 1; --b) {
-    if (b > d) continue;
+  for (int b = D; b >= 1; --b) {
     float pb = 0.f;
 #pragma unroll
-    for (int a = 8; a >= 0; --a)
-      if (a <= d - b) pb = fmaf(pb, lt, cf[(a + b) * (a + b + 1) / 2 + b]);
+    for (int a = D - b; a >= 0; --a) pb = fmaf(pb, lt, cf[(a + b) * (a + b + 1) / 2 + b]);
     sb = fmaf(sb, s, pb);
   }
   sb *= s;
   mag = fabsf(delta) * cf[E2E_MAXC] + cf[E2E_MAXC + 1];
   return fmaf(delta, Q, sb);
+}
+
+// Both coordinates' offsets for a slice of degree d (0 .. E2E_MAX_DEGREE).
+__device__ __forceinline__ void photon_offsets(int d, const float* cf, float lt, float ltj, float delta, float s,
+                                               float& ox, float& oy, float& mx, float& my) {
+  switch (d) {
+#define E2E_PO(D)                                                                   \
+  case D:                                                                           \
+    ox = photon_offset<D>(cf, lt, ltj, delta, s, mx);                               \
+    oy = photon_offset<D>(cf + E2E_MAXC + 2, lt, ltj, delta, s, my);                \
+    return;
+    E2E_PO(0) E2E_PO(1) E2E_PO(2) E2E_PO(3) E2E_PO(4) E2E_PO(5) E2E_PO(6) E2E_PO(7)
+#undef E2E_PO
+    default:
+      ox = photon_offset<8>(cf, lt, ltj, delta, s, mx);
+      oy = photon_offset<8>(cf + E2E_MAXC + 2, lt, ltj, delta, s, my);
+  }
 }
 
 __global__ void __launch_bounds__(256) k_photons(const DevSlice* __restrict__ slices, int n_slices,
@@ -260,9 +276,10 @@ __global__ void __launch_bounds__(256) k_photons(const DevSlice* __restrict__ sl
       normal_pair_f32_ctr(seed, j, si, pp, 7, z1, z2, eg);
       const float sx = fmaf(fmaf(ce[2], lt, ce[1]), lt, ce[0]);
       const float sy = fmaf(fmaf(ce[5], lt, ce[4]), lt, ce[3]);
-      float mx, my;
-      const float ox = photon_offset(cf, S.degree, lt, ltj, delta, s, mx) + sx * z1;
-      const float oy = photon_offset(cf + E2E_MAXC + 2, S.degree, lt, ltj, delta, s, my) + sy * z2;
+      float mx, my, ox, oy;
+      photon_offsets(S.degree, cf, lt, ltj, delta, s, ox, oy, mx, my);
+      ox += sx * z1;
+      oy += sy * z2;
       const float rx = __int_as_float(an.y) + ox + 0.5f, ry = __int_as_float(an.w) + oy + 0.5f;
       const float ein = 4e-7f * ((cf[E2E_MAXC] / n) + (float)S.degree * cf[E2E_MAXC + 1] / ns);
       const float einy = 4e-7f * ((cf[2 * E2E_MAXC + 2] / n) + (float)S.degree * cf[2 * E2E_MAXC + 3] / ns);
