@@ -2003,6 +2003,8 @@ int e2e_render_photons(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const ui
   uint32_t** d_dst = nullptr;
   uint64_t *counts = nullptr, *offsets = nullptr, *scan = nullptr;
   int4* anchors = nullptr;
+  int* bin_slice = nullptr;
+  int64_t* guide = nullptr;
   E2E_CK(sc.get((void**)&d_table, table.size() * sizeof(double*)));
   E2E_CK(sc.get((void**)&d_pitch, pitch.size() * sizeof(int64_t)));
   E2E_CK(sc.get((void**)&d_dst, m->n_det * sizeof(uint32_t*)));
@@ -2010,22 +2012,26 @@ int e2e_render_photons(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const ui
   E2E_CK(sc.get((void**)&offsets, (size_t)(m->n_bins + 1) * sizeof(uint64_t)));
   E2E_CK(sc.get((void**)&scan, scan_scratch_elems(m->n_bins) * sizeof(uint64_t)));
   E2E_CK(sc.get((void**)&anchors, (size_t)m->n_bins * sizeof(int4)));
+  E2E_CK(sc.get((void**)&bin_slice, (size_t)m->n_bins * sizeof(int)));
+  E2E_CK(sc.get((void**)&guide, (size_t)(kPhotonGuide + 1) * sizeof(int64_t)));
   E2E_CK(cudaMemcpyAsync(d_table, table.data(), table.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
   E2E_CK(cudaMemcpyAsync(d_pitch, pitch.data(), pitch.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
   E2E_CK(cudaMemcpyAsync(d_dst, dst, m->n_det * sizeof(uint32_t*), cudaMemcpyHostToDevice, st));
   const int ns = (int)m->slices.size();
   {
     KernelTimer kt(ctx, st, "photon_bins");
-    E2E_CK(launch_photon_bins(m->d_slices, ns, d_table, m->d_usum, m->d_bin_off, m->n_bins, seed, counts, anchors, st));
+    E2E_CK(launch_photon_bins(m->d_slices, ns, d_table, m->d_usum, m->d_bin_off, m->n_bins, seed, counts, anchors,
+                              bin_slice, st));
   }
   {
     KernelTimer kt(ctx, st, "photon_scan");
     E2E_CK(launch_scan_exclusive(counts, offsets, m->n_bins, scan, st));
+    E2E_CK(launch_photon_guide(offsets, m->n_bins, guide, st));
   }
   {
     KernelTimer kt(ctx, st, "photons");
     E2E_CK(launch_photons(m->d_slices, ns, m->d_ucum, m->d_usum, m->d_bin_off, offsets, m->psf, seed, d_dst, d_pitch,
-                          UINT64_MAX, m->d_ucum32, m->d_cf32, anchors, st));
+                          UINT64_MAX, m->d_ucum32, m->d_cf32, anchors, bin_slice, guide, st));
   }
   if (total_photons) {
     E2E_CK(cudaMemcpyAsync(total_photons, offsets + m->n_bins, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));

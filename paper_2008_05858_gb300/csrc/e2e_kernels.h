@@ -75,14 +75,17 @@ cudaError_t launch_blaze(const DevSlice* slices, int n_slices, const double* con
                          int64_t n_bins, double* out, cudaStream_t st);
 cudaError_t launch_photon_bins(const DevSlice* slices, int n_slices, const double* const* flux_tab, const double* usum,
                                const int64_t* bin_off, int64_t n_bins, uint64_t seed, uint64_t* counts,
-                               int4* anchors, cudaStream_t st);
+                               int4* anchors, int* bin_slice, cudaStream_t st);
+constexpr int kPhotonGuide = 1 << 20;  // entries of the photon -> bin guide table (+1)
+cudaError_t launch_photon_guide(const uint64_t* offsets, int64_t n_bins, int64_t* guide, cudaStream_t st);
 size_t photon_coef_floats();
 size_t scan_scratch_elems(int64_t n);
 cudaError_t launch_scan_exclusive(const uint64_t* in, uint64_t* out, int64_t n, uint64_t* scratch, cudaStream_t st);
 cudaError_t launch_photons(const DevSlice* slices, int n_slices, const double* ucum, const double* usum,
                            const int64_t* bin_off, const uint64_t* offsets, int psf, uint64_t seed,
                            uint32_t* const* dst, const int64_t* pitch, uint64_t max_photons, const float* ucum32,
-                           const float* cf32, const int4* anchors, cudaStream_t st);
+                           const float* cf32, const int4* anchors, const int* bin_slice, const int64_t* guide,
+                           cudaStream_t st);
 
 size_t adjoint_smem_bytes(int max_area, int max_deg, int nk_max);
 int adjoint_parts(int max_tasks);  // CTAs per item sharing its warp tasks

@@ -13,9 +13,10 @@
 //     y = y_c + beta g_x z1 + s_c z2;
 //     counted in pixel (floor(x + 1/2), floor(y + 1/2)) if that is on the detector.
 //
-// Three kernels: the photon count of every bin (one thread per bin, the Poisson sampler of
-// philox.cuh), an exclusive scan of the counts, and one thread per photon, which finds its
-// bin by binary search in the scan, so that every photon is a pure function of
+// Four kernels: the photon count of every bin (one thread per bin, the Poisson sampler of
+// philox.cuh), an exclusive scan of the counts, a guide table from evenly spaced photon numbers
+// to their bins, and one thread per photon, which finds its bin by binary search in the scan
+// between two guide entries, so that every photon is a pure function of
 // (seed, bin, slice, index) whatever the launch shape.  The pixel decisions are taken in FP64;
 // counts are added with 32-bit integer atomics (exact, order-independent).
 #include <climits>
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(256) k_photon_bins(const DevSlice* __restrict_
                                                      const double* const* __restrict__ flux_tab,
                                                      const double* __restrict__ usum, const int64_t* __restrict__ bin_off,
                                                      uint64_t seed, uint64_t* __restrict__ counts,
-                                                     int4* __restrict__ anchors) {
+                                                     int4* __restrict__ anchors, int* __restrict__ bin_slice) {
   const int64_t nb = bin_off[n_slices];
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
     int lo = 0, hi = n_slices - 1;
@@ -50,6 +51,7 @@ __global__ void __launch_bounds__(256) k_photon_bins(const DevSlice* __restrict_
       if (bin_off[mid] <= b) lo = mid; else hi = mid - 1;
     }
     const DevSlice& S = slices[lo];
+    bin_slice[b] = lo;
     const int j = (int)(b - bin_off[lo]);
     const double lam = __dmul_rn(__dmul_rn(flux_tab[S.flux_slot][j], S.dlam), usum[lo]);
     counts[b] = (uint64_t)poisson_filtered(lam, seed, (uint32_t)j, (uint32_t)S.index, 4);
@@ -128,6 +130,28 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_add(uint64_t* __restrict_
 }
 
 // ---------------------------------------------------------------- photons
+
+// Bin holding photon p: the last b in [lo, hi] with offsets[b] <= p.
+__device__ __forceinline__ int64_t photon_bin(const uint64_t* __restrict__ offsets, uint64_t p, int64_t lo, int64_t hi) {
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (offsets[mid] <= p) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// guide[g] = the bin of photon floor(g total / G), g = 0 .. G (G = kPhotonGuide): photon p
+// lies in a bin between guide[g] and guide[g + 1] for g = floor(p G / total), so its search
+// covers the few bins of one guide step instead of all of them.  Products g total and p G stay
+// below 2^64 for totals below kGuidedPhotons; beyond, photons search all bins.
+constexpr uint64_t kGuidedPhotons = 1ull << 44;
+__global__ void __launch_bounds__(256) k_photon_guide(const uint64_t* __restrict__ offsets, int64_t nb,
+                                                      int64_t* __restrict__ guide) {
+  const uint64_t total = offsets[nb];
+  if (total >= kGuidedPhotons) return;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g <= kPhotonGuide; g += gridDim.x * blockDim.x)
+    guide[g] = photon_bin(offsets, (uint64_t)g * total / kPhotonGuide, 0, nb - 1);
+}
 
 // The photon's pixel by the definition, in FP64 (fx, fy: the pixel's column and row).
 __device__ void photon_exact(const DevSlice& S, const double* __restrict__ C, double U, int psf, uint64_t seed,
@@ -221,28 +245,32 @@ __device__ __forceinline__ void photon_offsets(int d, const float* cf, float lt,
   }
 }
 
-__global__ void __launch_bounds__(256) k_photons(const DevSlice* __restrict__ slices, int n_slices,
+// Four CTAs of 256 per SM (64 registers): the photons are latency-bound on their dependent
+// Philox, search and coefficient loads; at the 80 registers the compiler picks unbounded, three
+// CTAs fit and 1e9 photons took 75 ms against 32 ms.
+#ifndef E2E_PHOTON_MIN_BLOCKS
+#define E2E_PHOTON_MIN_BLOCKS 4
+#endif
+__global__ void __launch_bounds__(256, E2E_PHOTON_MIN_BLOCKS) k_photons(const DevSlice* __restrict__ slices, int n_slices,
                                                  const double* __restrict__ ucum, const double* __restrict__ usum,
                                                  const int64_t* __restrict__ bin_off,
                                                  const uint64_t* __restrict__ offsets, int psf, uint64_t seed,
                                                  uint32_t* const* __restrict__ dst, const int64_t* __restrict__ pitch,
                                                  const float* __restrict__ ucum32, const float* __restrict__ cf32,
-                                                 const int4* __restrict__ anchors) {
+                                                 const int4* __restrict__ anchors, const int* __restrict__ bin_slice,
+                                                 const int64_t* __restrict__ guide) {
   const int64_t nb = bin_off[n_slices];
   const uint64_t total = offsets[nb];
   for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
        p += (uint64_t)gridDim.x * blockDim.x) {
     int64_t lo = 0, hi = nb - 1;
-    while (lo < hi) {  // bin holding photon p: the last b with offsets[b] <= p
-      const int64_t mid = (lo + hi + 1) >> 1;
-      if (offsets[mid] <= p) lo = mid; else hi = mid - 1;
+    if (total < kGuidedPhotons) {
+      const uint64_t g = p * kPhotonGuide / total;  // g < G since p < total
+      lo = guide[g];
+      hi = guide[g + 1];
     }
-    const int64_t b = lo;
-    int sl = 0, sh = n_slices - 1;
-    while (sl < sh) {
-      const int mid = (sl + sh + 1) >> 1;
-      if (bin_off[mid] <= b) sl = mid; else sh = mid - 1;
-    }
+    const int64_t b = photon_bin(offsets, p, lo, hi);
+    const int sl = bin_slice[b];
     const DevSlice& S = slices[sl];
     const uint32_t j = (uint32_t)(b - bin_off[sl]);
     const uint32_t pp = (uint32_t)(p - offsets[b]);
@@ -308,10 +336,16 @@ static unsigned grid_for(uint64_t n, int threads, uint64_t cap) {
 
 cudaError_t launch_photon_bins(const DevSlice* slices, int n_slices, const double* const* flux_tab, const double* usum,
                                const int64_t* bin_off, int64_t n_bins, uint64_t seed, uint64_t* counts,
-                               int4* anchors, cudaStream_t st) {
+                               int4* anchors, int* bin_slice, cudaStream_t st) {
   if (n_bins == 0) return cudaSuccess;
   k_photon_bins<<<grid_for((uint64_t)n_bins, 256, 152 * 64), 256, 0, st>>>(slices, n_slices, flux_tab, usum, bin_off,
-                                                                         seed, counts, anchors);
+                                                                         seed, counts, anchors, bin_slice);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_photon_guide(const uint64_t* offsets, int64_t n_bins, int64_t* guide, cudaStream_t st) {
+  if (n_bins == 0) return cudaSuccess;
+  k_photon_guide<<<(kPhotonGuide + 1 + 255) / 256, 256, 0, st>>>(offsets, n_bins, guide);
   return cudaGetLastError();
 }
 
@@ -331,10 +365,12 @@ size_t photon_coef_floats() { return (size_t)kCf; }
 cudaError_t launch_photons(const DevSlice* slices, int n_slices, const double* ucum, const double* usum,
                            const int64_t* bin_off, const uint64_t* offsets, int psf, uint64_t seed,
                            uint32_t* const* dst, const int64_t* pitch, uint64_t max_photons, const float* ucum32,
-                           const float* cf32, const int4* anchors, cudaStream_t st) {
+                           const float* cf32, const int4* anchors, const int* bin_slice, const int64_t* guide,
+                           cudaStream_t st) {
   if (max_photons == 0) return cudaSuccess;
   k_photons<<<grid_for(max_photons, 256, 152 * 32), 256, 0, st>>>(slices, n_slices, ucum, usum, bin_off, offsets, psf,
-                                                                   seed, dst, pitch, ucum32, cf32, anchors);
+                                                                   seed, dst, pitch, ucum32, cf32, anchors, bin_slice,
+                                                                   guide);
   return cudaGetLastError();
 }
 
