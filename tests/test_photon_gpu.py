@@ -52,6 +52,29 @@ def test_photon_counts_bit_exact(renderer, kw, photons):
     renderer.unload_model(mid)
 
 
+@pytest.mark.parametrize("photons", [3e2, 3e6])
+def test_sparse_spectrum_bit_exact(renderer, photons):
+    """An emission-line spectrum: all but every 97th bin empty, so photons sit in a few heavy
+    bins between long runs of empty ones (the bin search between two guide entries must skip
+    the empty bins), with fewer photons than guide entries (3e2) and more (3e6)."""
+    w = W.small_config(seed=306, n_lambda=1000, n_slit=7)
+    for fib, sp in w.spectra.items():
+        for o in sp.flux:
+            x = np.zeros_like(np.asarray(sp.flux[o], dtype=np.float64))
+            x[(o * 13 + fib * 5) % 97::97] = 1.0
+            sp.flux[o] = x
+    w = scaled_workload(w, photons)
+    ref, ref_total = oracle.render_photons(w.model, w.flux_for, seed=77)
+    mid = renderer.load_model(w.model)
+    out, total = renderer.render_photons(mid, renderer.load_spectra(w), seed=77)
+    torch.cuda.synchronize()
+    assert total == ref_total and total > 0
+    for g, o in zip(out, ref):
+        got = g.cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, o), int((got != o).sum())
+    renderer.unload_model(mid)
+
+
 def test_empty_model_and_zero_flux(renderer):
     m = W.OpticalModel([(20, 30)], [])
     mid = renderer.load_model(m)
