@@ -404,6 +404,8 @@ int oracle_render(int n_det, const int* H, const int* W, int n_slices, const ora
 #ifdef _OPENMP
   if (n_threads > 0) omp_set_num_threads(n_threads);
 #pragma omp parallel for schedule(dynamic, 1)
+#else
+  (void)n_threads;
 #endif
   for (int i = 0; i < n_slices; ++i) render_slice(&s[i], psf, H[s[i].detector], W[s[i].detector], &bands[i]);
   /* merge the private bands in slice order so the result does not depend on threads */
@@ -493,6 +495,8 @@ int oracle_vjp(int n_det, const int* H, const int* W, int n_slices, const oracle
 #ifdef _OPENMP
   if (n_threads > 0) omp_set_num_threads(n_threads);
 #pragma omp parallel for schedule(dynamic, 1)
+#else
+  (void)n_threads;
 #endif
   for (int i = 0; i < n_slices; ++i)
     slice_grad(&s[i], H[s[i].detector], W[s[i].detector], dLdI[s[i].detector], g_cx + off[i], g_cy + off[i],
@@ -524,6 +528,8 @@ double oracle_loss_grad(int n_det, const int* H, const int* W, int n_slices, con
 #ifdef _OPENMP
   if (n_threads > 0) omp_set_num_threads(n_threads);
 #pragma omp parallel for schedule(dynamic, 1)
+#else
+  (void)n_threads;
 #endif
   for (int i = 0; i < n_slices; ++i)
     slice_grad(&s[i], H[s[i].detector], W[s[i].detector], frames[s[i].detector], g_cx + off[i], g_cy + off[i],
