@@ -52,8 +52,11 @@ extern "C" {
 
 /* ------------------------------------------------------------------ enums */
 enum { E2E_PSF_SEPARABLE = 0, E2E_PSF_ELLIPTICAL = 1, E2E_PSF_TABLE = 2 };
-/* E2E_PREC_MIXED: FP64 mapping, FP32 PSF stamps in on-chip tiles, FP64 tile accumulation,
- *                 compensated merge (the fast path).
+/* E2E_PREC_MIXED: FP64 mapping; FP32 PSF stamps from double-float edge arguments; FP32 sums
+ *                 over runs of <= 16 stamps in registers; each item's box summed exactly in
+ *                 52-bit fixed point (shared-memory integer atomics) and stored as an FP32
+ *                 (hi, lo) pair; boxes merged into the frame with TwoSum compensation (the
+ *                 fast path: per-pixel error <= 1e-6 relative against the FP64 definition).
  * E2E_PREC_FP64:  everything in FP64, one thread per stamp, FP64 global atomics (baseline). */
 enum { E2E_PREC_MIXED = 0, E2E_PREC_FP64 = 1 };
 enum { E2E_F32 = 0, E2E_F64 = 1, E2E_U16 = 2 /* detector ADU, e2e_add_noise output only */ };
@@ -386,8 +389,12 @@ int e2e_kernel_times(e2e_ctx* ctx, const char** names, float* ms, int32_t cap, i
  *     it needs to start at zero (every call rewrites all it reads).  Calls whose work
  *     overlaps on the GPU (different streams, or another thread) race on the buffer: order
  *     them on one stream or synchronise between them.
+ *   - The frames are bitwise those of e2e_render with E2E_PREC_MIXED (same kernels, same
+ *     exact box sums, same merge order).  Kernel timing and debug checks work as there: the
+ *     timing events come from the context's pool and the check counter was allocated with
+ *     the context.
  * Arguments as for e2e_render (dst/pitch per detector, dtype E2E_F32 or E2E_F64).
- * Errors: E2E_EINVAL, E2E_ENOTFOUND, E2E_ETOOBIG, E2E_ECUDA. */
+ * Errors: E2E_EINVAL, E2E_ENOTFOUND, E2E_ETOOBIG, E2E_ECUDA, E2E_EDEVICE (debug checks). */
 #define E2E_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
 int e2e_render_static(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids, int32_t dtype,
                       void* const* dst, const int64_t* pitch_elems, void* stream);

@@ -1533,10 +1533,25 @@ int e2e_render_static(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uin
     E2E_CK(cudaMemcpyAsync(d_table, table.data(), table.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
   E2E_CK(cudaMemcpyAsync(d_pitch, pitch.data(), pitch.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
   E2E_CK(cudaMemcpyAsync(d_dst, dst, m->n_det * sizeof(void*), cudaMemcpyHostToDevice, st));
-  for (auto& grp : P.groups)
+  // kernel timings and debug checks as in e2e_render: the timing events come from the
+  // context's pool and the error counter was allocated with the context
+  if (ctx->opts.kernel_timing) reset_timing(ctx);
+  if (ctx->d_err) E2E_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
+  for (auto& grp : P.groups) {
+    KernelTimer kt(ctx, st, "render_mixed");
     E2E_CK(launch_render_mixed(grp.K, P.DX, P.DY, m->d_slices, d_table, m->d_u, P.d_items + grp.first, grp.count,
-                               store, P.B, P.JB, P.nk_max, P.max_deg, P.smem, st));
-  E2E_CK(launch_merge(P.d_tiles, P.n_tiles, P.d_lists, P.d_items, store, d_dst, dtype, d_pitch, m->d_dims, st));
+                               store, P.B, P.JB, P.nk_max, P.max_deg, P.smem, st, ctx->d_err));
+  }
+  {
+    KernelTimer kt(ctx, st, "merge");
+    E2E_CK(launch_merge(P.d_tiles, P.n_tiles, P.d_lists, P.d_items, store, d_dst, dtype, d_pitch, m->d_dims, st));
+  }
+  if (ctx->d_err) {  // debug checks: wait for the render and report unplanned deposits
+    int n_bad = 0;
+    E2E_CK(cudaMemcpyAsync(&n_bad, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    E2E_CK(cudaStreamSynchronize(st));
+    if (n_bad) return fail(E2E_EDEVICE, std::to_string(n_bad) + " deposits fell outside the planned boxes");
+  }
   return E2E_OK;
 }
 
