@@ -69,7 +69,6 @@ class OracleSlice(C.Structure):
         ("map_size", C.c_int),
         ("map_oversample", C.c_double),
         ("maps", C.POINTER(C.c_double)),
-        ("phases", C.c_int),
     ]
 
 
@@ -119,6 +118,8 @@ def lib():
             L.oracle_vjp.restype = C.c_int
             L.oracle_epsf_pixel.argtypes = [C.POINTER(OracleSlice), C.c_int, C.c_double, C.c_double, C.c_int, C.c_int]
             L.oracle_epsf_pixel.restype = C.c_double
+            L.oracle_epsf_window.argtypes = [C.POINTER(OracleSlice), C.c_int, C.c_double, C.c_double, dp]
+            L.oracle_epsf_window.restype = None
             u32p = C.POINTER(C.c_uint32)
             L.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
             L.oracle_philox4x32_10.restype = None
@@ -173,7 +174,6 @@ class _Marshalled:
                 self.keep += [lt, mp]
                 o.n_field, o.field_lt = len(lt), _dptr(lt)
                 o.map_size, o.map_oversample, o.maps = mp.shape[-1], float(psf_map.oversample), _dptr(mp)
-                o.phases = int(psf_map.phases)
         self.n = n
 
 
@@ -343,6 +343,14 @@ def epsf_pixel(s, f: int, phx: float, phy: float, m: int, n: int) -> float:
     """Effective-PSF value of window pixel (m, n) of slice s's map f at phase (phx, phy)."""
     mm = _Marshalled(W_OpticalModel_one(s), lambda _s: np.zeros(_s.n_lambda))
     return float(lib().oracle_epsf_pixel(C.byref(mm.arr[0]), f, phx, phy, m, n))
+
+
+def epsf_window(s, f: int, phx: float, phy: float) -> np.ndarray:
+    """All K x K effective-PSF values (rows n, columns m) of slice s's map f at phase (phx, phy)."""
+    mm = _Marshalled(W_OpticalModel_one(s), lambda _s: np.zeros(_s.n_lambda))
+    out = np.empty((s.K, s.K))
+    lib().oracle_epsf_window(C.byref(mm.arr[0]), f, phx, phy, _dptr(out))
+    return out
 
 
 def W_OpticalModel_one(s):

@@ -223,25 +223,62 @@ double oracle_epsf_pixel(const oracle_slice* s, int f, double phx, double phy, i
   return sum / norm;
 }
 
-/* Effective-PSF tables of one slice: T[f][py][px][n][m] for phases -1/2 + p/P, p = 0..P. */
-static double* epsf_tables(const oracle_slice* s) {
-  const int K = s->K, P = s->phases, F = s->n_field;
-  double* T = (double*)malloc(sizeof(double) * (size_t)F * (P + 1) * (P + 1) * K * K);
-  for (int f = 0; f < F; ++f)
-    for (int py = 0; py <= P; ++py)
-      for (int px = 0; px <= P; ++px)
-        for (int n = 0; n < K; ++n)
-          for (int m = 0; m < K; ++m)
-            T[((((size_t)f * (P + 1) + py) * (P + 1) + px) * K + n) * K + m] =
-                oracle_epsf_pixel(s, f, -0.5 + (double)px / P, -0.5 + (double)py / P, m, n);
-  return T;
+/* All K x K pixel integrals of map f's normalised bilinear density for the PSF centred at
+ * sub-pixel offset (phx, phy) from the window's centre pixel: the same sum as
+ * oracle_epsf_pixel, with the column weights of every window column and the row weights of
+ * every window row formed once, and the loops kept to the samples whose tents meet the pixel
+ * (every other term is exactly zero). */
+void oracle_epsf_window(const oracle_slice* s, int f, double phx, double phy, double* out) {
+  const int M = s->map_size, K = s->K, H = K / 2;
+  const double q = s->map_oversample, c = 0.5 * (M - 1);
+  const double* S = s->maps + (size_t)f * M * M;
+  double norm = 0.0;
+  for (int i = 0; i < M * M; ++i) norm += S[i];
+  norm /= q * q;
+  double* X = (double*)malloc(sizeof(double) * (size_t)K * M);
+  double* Y = (double*)malloc(sizeof(double) * (size_t)K * M);
+  int* span = (int*)malloc(sizeof(int) * 4 * (size_t)K);
+  for (int m = 0; m < K; ++m) {
+    const double ax = m - H - 0.5 - phx, ay = m - H - 0.5 - phy;
+    int xl = M, xh = -1, yl = M, yh = -1;
+    for (int u = 0; u < M; ++u) {
+      X[(size_t)m * M + u] = tent_weight(ax, ax + 1.0, u, c, q);
+      Y[(size_t)m * M + u] = tent_weight(ay, ay + 1.0, u, c, q);
+      if (X[(size_t)m * M + u] != 0.0) {
+        if (u < xl) xl = u;
+        xh = u;
+      }
+      if (Y[(size_t)m * M + u] != 0.0) {
+        if (u < yl) yl = u;
+        yh = u;
+      }
+    }
+    span[4 * m] = xl;
+    span[4 * m + 1] = xh;
+    span[4 * m + 2] = yl;
+    span[4 * m + 3] = yh;
+  }
+  for (int n = 0; n < K; ++n)
+    for (int m = 0; m < K; ++m) {
+      double sum = 0.0;
+      for (int v = span[4 * n + 2]; v <= span[4 * n + 3]; ++v) {
+        const double wy = Y[(size_t)n * M + v];
+        for (int u = span[4 * m]; u <= span[4 * m + 1]; ++u)
+          sum += S[(size_t)v * M + u] * X[(size_t)m * M + u] * wy;
+      }
+      out[n * K + m] = sum / norm;
+    }
+  free(X);
+  free(Y);
+  free(span);
 }
 
-/* Stamp of a tabulated PSF: the tables bilinearly interpolated in the centre's sub-pixel phase
- * and linearly in lt between the two field nodes around it (the end node beyond the ends). */
-static void table_stamp(const oracle_slice* s, const double* T, double lt, double fx, double fy, double w,
-                        double* out) {
-  const int K = s->K, P = s->phases, F = s->n_field;
+/* Stamp of a tabulated PSF (Sec. 2.1: PSF maps given per field point; Sec. 2.2: each image is
+ * the PSF integrated over the pixels): the pixel integrals of the normalised maps at the two
+ * field nodes around the sample's lt (the end node beyond the ends), each at the stamp's exact
+ * sub-pixel centre (fx, fy), blended linearly in lt, times the weight. */
+static void table_stamp(const oracle_slice* s, double lt, double fx, double fy, double w, double* out) {
+  const int K = s->K, F = s->n_field;
   int f0 = 0, f1 = 0;
   double wf = 0.0;
   if (lt <= s->field_lt[0]) {
@@ -253,27 +290,12 @@ static void table_stamp(const oracle_slice* s, const double* T, double lt, doubl
     f1 = f0 + 1 < F ? f0 + 1 : f0;
     if (f1 != f0) wf = (lt - s->field_lt[f0]) / (s->field_lt[f1] - s->field_lt[f0]);
   }
-  double rx = (fx + 0.5) * P, ry = (fy + 0.5) * P;
-  int px = (int)floor(rx), py = (int)floor(ry);
-  if (px > P - 1) px = P - 1;
-  if (py > P - 1) py = P - 1;
-  if (px < 0) px = 0;
-  if (py < 0) py = 0;
-  const double ax = rx - px, ay = ry - py;
-  for (int n = 0; n < K; ++n)
-    for (int m = 0; m < K; ++m) {
-      double v = 0.0;
-      for (int e = 0; e < 2; ++e) {
-        const int f = e ? f1 : f0;
-        const double we = e ? wf : 1.0 - wf;
-        if (we == 0.0) continue;
-#define TT(Y, X) T[((((size_t)f * (P + 1) + (Y)) * (P + 1) + (X)) * K + n) * K + m]
-        v += we * ((1.0 - ay) * ((1.0 - ax) * TT(py, px) + ax * TT(py, px + 1)) +
-                   ay * ((1.0 - ax) * TT(py + 1, px) + ax * TT(py + 1, px + 1)));
-#undef TT
-      }
-      out[n * K + m] = w * v;
-    }
+  double* e0 = (double*)malloc(sizeof(double) * 2 * (size_t)K * K);
+  double* e1 = e0 + (size_t)K * K;
+  oracle_epsf_window(s, f0, fx, fy, e0);
+  if (wf != 0.0) oracle_epsf_window(s, f1, fx, fy, e1);
+  for (int i = 0; i < K * K; ++i) out[i] = w * ((1.0 - wf) * e0[i] + (wf != 0.0 ? wf * e1[i] : 0.0));
+  free(e0);
 }
 
 void oracle_stamp(const oracle_slice* s, int psf, int j, int k, double* out, int* i0p, int* r0p) {
@@ -284,12 +306,10 @@ void oracle_stamp(const oracle_slice* s, int psf, int j, int k, double* out, int
   *i0p = i0;
   *r0p = r0;
   if (psf == ORACLE_PSF_TABLE) {
-    double* T = epsf_tables(s);
     const double dl = (s->lambda_hi - s->lambda_lo) / s->n_lambda;
     const double lam = s->lambda_lo + (j + 0.5) * dl;
     const double lt = 2.0 * (lam - s->lambda_lo) / (s->lambda_hi - s->lambda_lo) - 1.0;
-    table_stamp(s, T, lt, xc - (i0 + K / 2), yc - (r0 + K / 2), w, out);
-    free(T);
+    table_stamp(s, lt, xc - (i0 + K / 2), yc - (r0 + K / 2), w, out);
   } else if (psf == ORACLE_PSF_SEPARABLE) {
     for (int n = 0; n < K; ++n) {
       double ay = oracle_normal_interval((r0 + n - 0.5 - yc) / sy, (r0 + n + 0.5 - yc) / sy);
@@ -364,19 +384,18 @@ static void render_slice(const oracle_slice* s, int psf, int H, int W, band_t* b
   band->h = ymax - ymin + 1;
   band->buf = (double*)calloc((size_t)band->w * band->h, sizeof(double));
   double* st = (double*)malloc(sizeof(double) * K * K);
-  double* T = psf == ORACLE_PSF_TABLE ? epsf_tables(s) : NULL;  /* once per slice */
   const double dl = (s->lambda_hi - s->lambda_lo) / s->n_lambda;
   for (int j = 0; j < s->n_lambda; ++j)
     for (int k = 0; k < s->n_slit; ++k) {
       int i0, r0;
-      if (T) {
+      if (psf == ORACLE_PSF_TABLE) {
         double xc, yc, sx, sy, w;
         oracle_map(s, j, k, &xc, &yc, &sx, &sy, &w);
         i0 = window_origin(xc, K);
         r0 = window_origin(yc, K);
         const double lam = s->lambda_lo + (j + 0.5) * dl;
         const double lt = 2.0 * (lam - s->lambda_lo) / (s->lambda_hi - s->lambda_lo) - 1.0;
-        table_stamp(s, T, lt, xc - (i0 + K / 2), yc - (r0 + K / 2), w, st);
+        table_stamp(s, lt, xc - (i0 + K / 2), yc - (r0 + K / 2), w, st);
       } else {
         oracle_stamp(s, psf, j, k, st, &i0, &r0);
       }
@@ -391,7 +410,6 @@ static void render_slice(const oracle_slice* s, int psf, int H, int W, band_t* b
       }
     }
   free(st);
-  free(T);
 }
 
 int oracle_render(int n_det, const int* H, const int* W, int n_slices, const oracle_slice* s, int psf,

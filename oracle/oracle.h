@@ -44,14 +44,15 @@ typedef struct {
   /* ORACLE_PSF_TABLE: tabulated PSF maps at n_field wavelengths field_lt[f] (increasing, in
    * [-1, 1]); map f is map_size^2 samples maps[f][v][u] of the PSF density at offsets
    * ((u - c)/q, (v - c)/q) px from the PSF centre, c = (map_size - 1)/2, q = map_oversample;
-   * the density between samples is their bilinear interpolant (zero beyond the grid).
-   * phases: sub-pixel phases per axis of the effective-PSF tables. */
+   * the density between samples is their bilinear interpolant (zero beyond the grid), and
+   * between field nodes the PSF is the linear blend in lt of the two unit-mass maps around
+   * it.  A stamp's pixel values are that density's integrals over the pixels for the PSF
+   * centred at the stamp's exact mapped position. */
   int n_field;
   const double* field_lt;
   int map_size;
   double map_oversample;
   const double* maps;
-  int phases;
 } oracle_slice;
 
 /* Render every order-slice into its detector frame.  frames[d] points to H[d]*W[d]
@@ -64,6 +65,9 @@ int oracle_render(int n_det, const int* H, const int* W, int n_slices, const ora
  * integral) of window pixel (m, n), relative to the window's centre pixel, for a PSF centred
  * at sub-pixel offset (phx, phy) from that pixel's centre. */
 double oracle_epsf_pixel(const oracle_slice* s, int f, double phx, double phy, int m, int n);
+
+/* The same for all K x K window pixels at once (out[n*K + m]). */
+void oracle_epsf_window(const oracle_slice* s, int f, double phx, double phy, double* out);
 
 /* Blaze weight of the slice at wavelength lam (1 when it has none). */
 double oracle_blaze(const oracle_slice* s, double lam);

@@ -98,19 +98,18 @@ class OrderSlice:
 class PsfMap:
     """Tabulated PSF of one order-slice: maps[f] samples the PSF density at offsets
     ((u - c)/oversample, (v - c)/oversample) px from the centre (c = (M - 1)/2) at the
-    normalised wavelength field_lt[f]; `phases` sub-pixel phases per axis for the tables."""
+    normalised wavelength field_lt[f]."""
 
     field_lt: np.ndarray
     maps: np.ndarray  # (n_field, M, M)
     oversample: float
-    phases: int = 8
 
     def copy(self) -> "PsfMap":
-        return PsfMap(self.field_lt.copy(), self.maps.copy(), self.oversample, self.phases)
+        return PsfMap(self.field_lt.copy(), self.maps.copy(), self.oversample)
 
 
 def psf_maps(s: "OrderSlice", *, n_field: int = 5, oversample: float = 10.0, half_px: float = 8.0,
-             phases: int = 8, coma: float = 0.0) -> PsfMap:
+             coma: float = 0.0) -> PsfMap:
     """Synthetic PSF maps (the optical design's maps are not available): at n_field
     wavelengths the slice's Gaussian (widths sigma_x, sigma_y at that wavelength), plus, when
     coma > 0, a fainter Gaussian displaced along x by 1.5 sigma_x (a comatic tail) carrying
@@ -130,7 +129,7 @@ def psf_maps(s: "OrderSlice", *, n_field: int = 5, oversample: float = 10.0, hal
             gx2 = np.exp(-0.5 * ((x - 1.5 * sx) / (1.3 * sx)) ** 2) / (1.3 * sx)
             img = (1 - coma) * img + coma * np.outer(gy, gx2)
         maps[f] = img / (2 * np.pi)
-    return PsfMap(lt, maps, oversample, phases)
+    return PsfMap(lt, maps, oversample)
 
 
 def with_psf_maps(model: "OpticalModel", **kw) -> "OpticalModel":
