@@ -439,11 +439,11 @@ def Bd_spec(sp, k):
 
 def table_run(B, dev, w, flush, reps=3):
     """The full-detector workload with tabulated PSF maps (5 field nodes per slice, 10 samples
-    per pixel over +-8 px, a 20 % comatic tail; 8 x 8 sub-pixel phases): mixed precision and
-    the plain FP64 renderer, timed with CUDA events."""
+    per pixel over +-8 px, a 20 % comatic tail; exact per-cell phase biquadratics): mixed
+    precision and the plain FP64 renderer, timed with CUDA events."""
     import torch
 
-    m = W.with_psf_maps(w.model, oversample=10.0, half_px=8.0, coma=0.2, phases=8)
+    m = W.with_psf_maps(w.model, oversample=10.0, half_px=8.0, coma=0.2)
     r = B.Renderer(dev)
     t0 = time.perf_counter()
     mid = r.load_model(m)

@@ -110,13 +110,18 @@ typedef struct {
    * maps per projected fiber image; here sampled densities at field points along the order).
    * Map f samples the PSF density at offsets ((u - c)/q, (v - c)/q) px from the PSF centre,
    * c = (map_size - 1)/2, q = map_oversample; between samples the density is their bilinear
-   * interpolant (zero beyond the grid).  A stamp's pixel values are the pixel integrals of
-   * that density, tabulated at load time for (psf_phases + 1)^2 sub-pixel centre phases, then
-   * interpolated bilinearly in the stamp's phase and linearly in lt between field nodes. */
+   * interpolant (zero beyond the grid); between field nodes the PSF is the linear blend in lt
+   * of the two nodes' unit-mass maps (the end node beyond the ends).  A stamp's pixel values
+   * are that density's integrals over the pixels for the PSF centred at the stamp's exact
+   * position (Sec. 2.2).  For an integer q each pixel integral is a biquadratic in the
+   * sub-pixel phase within cells of 1/q px; the library tabulates the biquadratics' exact
+   * coefficients at load time (n_field x (q + 1)^2 x 9 x K^2 values in FP64 and FP32), so no
+   * phase interpolation error enters. */
   int32_t n_field;          /* field nodes (>= 1) */
   const double* field_lt;   /* their normalised wavelengths, strictly increasing, in [-1, 1] */
   int32_t map_size;         /* M >= 2: each map is M x M samples, row v, column u */
-  double map_oversample;    /* q > 0: samples per pixel */
+  double map_oversample;    /* q: samples per pixel, an integer 1..32;
+                               n_field x (q + 1)^2 must stay <= 65535 */
   const double* maps;       /* n_field * M * M densities, finite, >= 0, each map's sum > 0 */
 } e2e_order_slice;
 
@@ -127,7 +132,6 @@ typedef struct {
   int32_t n_slices;
   const e2e_order_slice* slices;
   int32_t psf;           /* E2E_PSF_SEPARABLE, E2E_PSF_ELLIPTICAL or E2E_PSF_TABLE */
-  int32_t psf_phases;    /* E2E_PSF_TABLE: sub-pixel phases per axis of the tables, 1..64 (0 = 8) */
 } e2e_model_desc;
 
 /* ------------------------------------------------------------------ context */
@@ -225,11 +229,41 @@ int e2e_render_host(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint6
  *   g_cx, g_cy: device FP64 arrays of sum over slices of (d+1)(d+2)/2 entries, the slices'
  *            coefficient vectors concatenated in model order; g_sx, g_sy: 3 per slice.  They
  *            are overwritten.
+ *   frozen_windows: NULL, or a device array of 2 int32 per stamp, (i0, r0) in the stamp order
+ *            of e2e_window_origins, 8-byte aligned: the windows are then held at these
+ *            origins instead of those the mapping picks (the gradient of the frame that
+ *            e2e_render_frozen renders with them).  Origins are expected within a pixel or so
+ *            of the mapping's own (for instance those of the unperturbed model in a central-
+ *            difference check, or of an earlier fitting iteration); stamps whose own window
+ *            lies wholly off the detector are skipped.
  * Asynchronous on `stream`.  Errors: E2E_EINVAL (elliptical PSF, bad arguments),
  * E2E_ENOTFOUND, E2E_ENOMEM, E2E_ECUDA. */
 int e2e_render_adjoint(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids, int32_t dtype,
                        const void* const* dldi, const int64_t* pitch_elems, double* g_cx, double* g_cy,
-                       double* g_sx, double* g_sy, void* stream);
+                       double* g_sx, double* g_sy, const int32_t* frozen_windows, void* stream);
+
+/* Window origins of every stamp of a resident model: origins[2 s] = i0 and origins[2 s + 1] = r0,
+ * the lower-left pixel of stamp s's K x K window, floor(x_c + 1/2) - K/2 (likewise in y), with
+ * x_c mapped in FP64.  Stamps are numbered slice by slice in model order, then by wavelength
+ * sample j, then by slit point k: s = sum of earlier slices' n_lambda n_slit + j n_slit + k.
+ * The truncated frame jumps where a centre crosses a pixel edge; holding the windows at these
+ * origins (e2e_render_frozen, e2e_render_adjoint) gives the smooth frame whose derivative the
+ * adjoint computes (window re-centring is excluded from the gradient).
+ *   origins: device array of 2 x (number of stamps) int32, 8-byte aligned.
+ * Asynchronous on `stream`.  Errors: E2E_EINVAL, E2E_ENOTFOUND, E2E_ECUDA. */
+int e2e_window_origins(e2e_ctx* ctx, uint64_t model_id, int32_t* origins, void* stream);
+
+/* Render (FP64, separable PSF) with every stamp's window held at the given origins instead of
+ * the one its mapped centre picks: the forward companion of the adjoint's frozen windows, for
+ * central-difference checks and fitting with fixed windows.  Pixel integrals are exact for
+ * any origin (the stamp's centre need not lie in the window's centre pixel).
+ *   frozen_windows: device array in the layout of e2e_window_origins (8-byte aligned).
+ * Other arguments as for e2e_render with precision E2E_PREC_FP64.
+ * Errors: E2E_EINVAL (not a separable-PSF model, bad arguments), E2E_ENOTFOUND, E2E_ENOMEM,
+ * E2E_ECUDA. */
+int e2e_render_frozen(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids,
+                      const int32_t* frozen_windows, int32_t dtype, void* const* dst, const int64_t* pitch_elems,
+                      void* stream);
 
 /* Replace the mapping and PSF-width coefficients of a resident model (host arrays laid out
  * as the gradients of e2e_render_adjoint), validate them as e2e_load_model does, and re-plan.

@@ -120,6 +120,8 @@ def lib():
             L.oracle_epsf_pixel.restype = C.c_double
             L.oracle_epsf_window.argtypes = [C.POINTER(OracleSlice), C.c_int, C.c_double, C.c_double, dp]
             L.oracle_epsf_window.restype = None
+            L.oracle_window_ties.argtypes = [C.POINTER(OracleSlice), C.c_double, C.c_int, C.POINTER(C.c_int)]
+            L.oracle_window_ties.restype = C.c_int
             u32p = C.POINTER(C.c_uint32)
             L.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
             L.oracle_philox4x32_10.restype = None
@@ -350,6 +352,24 @@ def epsf_window(s, f: int, phx: float, phy: float) -> np.ndarray:
     mm = _Marshalled(W_OpticalModel_one(s), lambda _s: np.zeros(_s.n_lambda))
     out = np.empty((s.K, s.K))
     lib().oracle_epsf_window(C.byref(mm.arr[0]), f, phx, phy, _dptr(out))
+    return out
+
+
+def window_ties(model, flux_of, margin: float = 1e-9) -> List[Tuple[int, int, int, int, int]]:
+    """(slice index, detector, j, k, axis) of every stamp whose mapped centre lies within
+    `margin` px of a half-integer in x (axis 0) or y (axis 1): where the window rule may round
+    either way."""
+    m = _Marshalled(model, flux_of)
+    out = []
+    for i, s in enumerate(model.slices):
+        cap = 64
+        while True:
+            buf = (C.c_int * (3 * cap))()
+            n = lib().oracle_window_ties(C.byref(m.arr[i]), margin, cap, buf)
+            if n <= cap:
+                break
+            cap = n
+        out += [(i, s.detector, buf[3 * t], buf[3 * t + 1], buf[3 * t + 2]) for t in range(n)]
     return out
 
 

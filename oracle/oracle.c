@@ -331,6 +331,32 @@ void oracle_stamp(const oracle_slice* s, int psf, int j, int k, double* out, int
   }
 }
 
+/* Stamps of one order-slice whose mapped centre lies within `margin` px of a pixel edge
+ * (a half-integer) in x or y: there the window rule floor(c + 1/2) can round either way between
+ * two evaluations of c that differ by rounding, so two correct renderers may place the window
+ * one pixel apart (a flip).  Writes up to max_out (j, k, axis) triples to out (axis 0 = x,
+ * 1 = y) and returns the number of such (stamp, axis) pairs. */
+int oracle_window_ties(const oracle_slice* s, double margin, int max_out, int* out) {
+  int n = 0;
+  for (int j = 0; j < s->n_lambda; ++j)
+    for (int k = 0; k < s->n_slit; ++k) {
+      double c[2], sx, sy, w;
+      oracle_map(s, j, k, &c[0], &c[1], &sx, &sy, &w);
+      for (int a = 0; a < 2; ++a) {
+        const double d = (c[a] + 0.5) - floor(c[a] + 0.5);
+        if (d < margin || 1.0 - d < margin) {
+          if (n < max_out) {
+            out[3 * n] = j;
+            out[3 * n + 1] = k;
+            out[3 * n + 2] = a;
+          }
+          ++n;
+        }
+      }
+    }
+  return n;
+}
+
 double oracle_subpixel_sample(double xc, double yc, double sigx, double sigy, int i, int r, int nsub) {
   double h = 1.0 / nsub, sum = 0.0;
   for (int q = 0; q < nsub; ++q)

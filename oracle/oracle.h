@@ -79,6 +79,10 @@ void oracle_map(const oracle_slice* s, int j, int k, double* x_c, double* y_c, d
 /* The K*K pixel values of one stamp (row-major n*K+m, pixel (i0+m, r0+n)), and its window origin. */
 void oracle_stamp(const oracle_slice* s, int psf, int j, int k, double* out, int* i0, int* r0);
 
+/* Stamps whose mapped centre lies within `margin` px of a half-integer in x or y (window-rule
+ * ties): up to max_out (j, k, axis) triples in out; returns the count. */
+int oracle_window_ties(const oracle_slice* s, double margin, int max_out, int* out);
+
 /* P(a < Z < b) for a standard normal Z, a <= b. */
 double oracle_normal_interval(double a, double b);
 

@@ -71,7 +71,6 @@ class e2e_model_desc(C.Structure):
     _fields_ = [
         ("n_detectors", C.c_int32), ("height", C.POINTER(C.c_int32)), ("width", C.POINTER(C.c_int32)),
         ("n_slices", C.c_int32), ("slices", C.POINTER(e2e_order_slice)), ("psf", C.c_int32),
-        ("psf_phases", C.c_int32),
     ]
 
 
@@ -144,7 +143,10 @@ _SIGS = {
                            C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.c_void_p], C.c_int),
     "e2e_render_adjoint": ([C.c_void_p, C.c_uint64, C.c_int32, C.POINTER(C.c_uint64), C.c_int32,
                             C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.c_void_p, C.c_void_p, C.c_void_p,
-                            C.c_void_p, C.c_void_p], C.c_int),
+                            C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "e2e_window_origins": ([C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p], C.c_int),
+    "e2e_render_frozen": ([C.c_void_p, C.c_uint64, C.c_int32, C.POINTER(C.c_uint64), C.c_void_p, C.c_int32,
+                           C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.c_void_p], C.c_int),
     "e2e_update_model": ([C.c_void_p, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double),
                           C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
     "e2e_render_photons": ([C.c_void_p, C.c_uint64, C.c_int32, C.POINTER(C.c_uint64), C.c_uint64,
@@ -223,7 +225,6 @@ class _ModelDesc:
         n = len(model.slices)
         self.sl = (e2e_order_slice * max(n, 1))()
         dp = C.POINTER(C.c_double)
-        phases = 0
         for i, s in enumerate(model.slices):
             cx = np.ascontiguousarray(s.cx, dtype=np.float64)
             cy = np.ascontiguousarray(s.cy, dtype=np.float64)
@@ -247,11 +248,10 @@ class _ModelDesc:
                 self.keep += [lt, mp]
                 o.n_field, o.field_lt = len(lt), lt.ctypes.data_as(dp)
                 o.map_size, o.map_oversample, o.maps = mp.shape[-1], float(pm.oversample), mp.ctypes.data_as(dp)
-                phases = int(pm.phases)
         nd = len(model.det_shape)
         self.h = (C.c_int32 * nd)(*[h for h, w in model.det_shape])
         self.w = (C.c_int32 * nd)(*[w for h, w in model.det_shape])
-        self.desc = e2e_model_desc(nd, self.h, self.w, n, self.sl, int(model.psf), phases)
+        self.desc = e2e_model_desc(nd, self.h, self.w, n, self.sl, int(model.psf))
 
 
 def e2e_load_model(ctx: int, model: W.OpticalModel) -> int:
@@ -347,14 +347,30 @@ def e2e_release_frame(ctx: int, frame_id: int) -> None:
 
 def e2e_render_adjoint(ctx: int, model_id: int, spec_ids: Sequence[int], dtype: int, dldi_ptrs: Sequence[int],
                        pitch_elems: Optional[Sequence[int]], g_cx: int, g_cy: int, g_sx: int, g_sy: int,
-                       stream=None) -> None:
+                       frozen_windows: int = 0, stream=None) -> None:
     n = len(spec_ids)
     sids = (C.c_uint64 * max(n, 1))(*spec_ids)
     dl = (C.c_void_p * len(dldi_ptrs))(*dldi_ptrs)
     pit = None if pitch_elems is None else (C.c_int64 * len(pitch_elems))(*pitch_elems)
     _check(load_library().e2e_render_adjoint(C.c_void_p(ctx), model_id, n, sids, dtype, dl, pit, C.c_void_p(g_cx),
                                              C.c_void_p(g_cy), C.c_void_p(g_sx), C.c_void_p(g_sy),
+                                             C.c_void_p(frozen_windows or None),
                                              C.c_void_p(_stream_handle(stream))))
+
+
+def e2e_window_origins(ctx: int, model_id: int, origins_ptr: int, stream=None) -> None:
+    _check(load_library().e2e_window_origins(C.c_void_p(ctx), model_id, C.c_void_p(origins_ptr),
+                                             C.c_void_p(_stream_handle(stream))))
+
+
+def e2e_render_frozen(ctx: int, model_id: int, spec_ids: Sequence[int], frozen_ptr: int, dtype: int,
+                      dst_ptrs: Sequence[int], pitch_elems: Optional[Sequence[int]] = None, stream=None) -> None:
+    n = len(spec_ids)
+    sids = (C.c_uint64 * max(n, 1))(*spec_ids)
+    dst = (C.c_void_p * len(dst_ptrs))(*dst_ptrs)
+    pit = None if pitch_elems is None else (C.c_int64 * len(pitch_elems))(*pitch_elems)
+    _check(load_library().e2e_render_frozen(C.c_void_p(ctx), model_id, n, sids, C.c_void_p(frozen_ptr), dtype, dst,
+                                            pit, C.c_void_p(_stream_handle(stream))))
 
 
 def e2e_update_model(ctx: int, model_id: int, cx: np.ndarray, cy: np.ndarray, sx: np.ndarray, sy: np.ndarray) -> None:
@@ -601,8 +617,9 @@ class Renderer:
             o += nc
         self.models[mid] = m
 
-    def adjoint(self, mid: int, spec_ids: Sequence[int], dldi, stream=None):
-        """(g_cx, g_cy, g_sx, g_sy) device FP64 tensors: sum over pixels of dL/dI * dI/dtheta."""
+    def adjoint(self, mid: int, spec_ids: Sequence[int], dldi, stream=None, frozen=None):
+        """(g_cx, g_cy, g_sx, g_sy) device FP64 tensors: sum over pixels of dL/dI * dI/dtheta;
+        frozen: optional int32 device tensor of window origins (window_origins' layout)."""
         import torch
 
         m = self.models[mid]
@@ -611,8 +628,26 @@ class Renderer:
         g = [torch.empty(n, dtype=torch.float64, device=dev) for n in (nc, nc, 3 * len(m.slices), 3 * len(m.slices))]
         dt = E2E_F32 if dldi[0].dtype == torch.float32 else E2E_F64
         e2e_render_adjoint(self.ctx, mid, spec_ids, dt, [int(t.data_ptr()) for t in dldi],
-                           [int(t.stride(0)) for t in dldi], *[int(t.data_ptr()) for t in g], stream=stream)
+                           [int(t.stride(0)) for t in dldi], *[int(t.data_ptr()) for t in g],
+                           frozen_windows=0 if frozen is None else int(frozen.data_ptr()), stream=stream)
         return tuple(g)
+
+    def window_origins(self, mid: int, stream=None):
+        """int32 device tensor (n_stamps, 2): every stamp's window origin (i0, r0)."""
+        import torch
+
+        m = self.models[mid]
+        out = torch.empty((m.n_stamps, 2), dtype=torch.int32, device=f"cuda:{self.device}")
+        e2e_window_origins(self.ctx, mid, int(out.data_ptr()), stream)
+        return out
+
+    def render_frozen(self, mid: int, spec_ids: Sequence[int], frozen, dtype: str = "f64", out=None, stream=None):
+        """FP64 render with every window held at the origins in `frozen` (window_origins' layout)."""
+        if out is None:
+            out = self.empty_frames(mid, dtype)
+        e2e_render_frozen(self.ctx, mid, spec_ids, int(frozen.data_ptr()), DTYPE[dtype],
+                          [int(t.data_ptr()) for t in out], [int(t.stride(0)) for t in out], stream)
+        return out
 
     def render(self, mid: int, spec_ids: Sequence[int], precision: str = "mixed", dtype: str = "f32",
                out=None, stream=None):

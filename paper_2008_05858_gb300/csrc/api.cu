@@ -113,13 +113,13 @@ struct Model {
   bool u_nonneg = true;
   bool has_blaze = false;  // some slice weights its samples by a blaze function
   // tabulated PSF: per-slice layout, field nodes, effective-PSF tables (FP64 and FP32)
-  int phases = 8;
   TableSlice* d_ts = nullptr;
   double* d_field = nullptr;
   double* d_T64 = nullptr;
   float* d_T32 = nullptr;
   int* d_dims = nullptr;  // [det][2] = (H, W)
   int64_t max_stamps = 0;
+  int64_t n_stamps = 0;  // stamps of all slices (the length of a window-origin list)
   std::vector<int> Ks;    // distinct K values
   Plan plan;
 };
@@ -286,7 +286,8 @@ int validate_slice(const e2e_order_slice& s, int n_det, int psf, int idx) {
   if (psf == E2E_PSF_TABLE) {
     if (s.n_field < 1 || !s.field_lt || !s.maps) return bad("tabulated PSF needs n_field >= 1 and maps");
     if (s.map_size < 2 || s.map_size > 4096) return bad("map_size must be 2..4096");
-    if (!(s.map_oversample > 0.0) || !std::isfinite(s.map_oversample)) return bad("map_oversample must be > 0");
+    if (!(s.map_oversample >= 1.0 && s.map_oversample <= 32.0) || s.map_oversample != std::floor(s.map_oversample))
+      return bad("map_oversample must be an integer 1..32 (samples per pixel)");
     for (int f = 0; f < s.n_field; ++f) {
       if (!std::isfinite(s.field_lt[f]) || s.field_lt[f] < -1.0 || s.field_lt[f] > 1.0 ||
           (f > 0 && !(s.field_lt[f] > s.field_lt[f - 1])))
@@ -377,15 +378,14 @@ double variant_cost(int K, int DX, int DY, int B) {
   return c;
 }
 
-// Effective-PSF tables of a tabulated-PSF model, built on the device at load time.
-int build_psf_tables(Model* m, int P) {
+// Phase-cell tables of a tabulated-PSF model, built on the device at load time.
+int build_psf_tables(Model* m) {
   NvtxRange nvtx_("e2e psf tables");
-  m->phases = P;
   const int ns = (int)m->slices.size();
   std::vector<TableSlice> ts(ns);
   std::vector<double> field, maps;
   int64_t tab = 0, tab32 = 0;
-  int max_field = 1;
+  int max_field = 1, max_cells = 1;
   for (int i = 0; i < ns; ++i) {
     const e2e_order_slice& s = m->slices[i].d;
     TableSlice& t = ts[i];
@@ -396,14 +396,20 @@ int build_psf_tables(Model* m, int P) {
     t.n_field = s.n_field;
     t.map_size = s.map_size;
     t.K = s.K;
-    t.q = s.map_oversample;
+    t.q = (int32_t)s.map_oversample;  // validated to be an integer in 1..32
+    t.half = s.map_size % 2 == 0 ? 1 : 0;
+    t.n_cell = t.q + t.half;
+    t.pad = 0;
     field.insert(field.end(), s.field_lt, s.field_lt + s.n_field);
     maps.insert(maps.end(), s.maps, s.maps + (size_t)s.n_field * s.map_size * s.map_size);
-    tab += (int64_t)s.n_field * (P + 1) * (P + 1) * s.K * s.K;
-    tab32 += (int64_t)s.n_field * (P + 1) * (P + 1) * table_row32(s.K);
+    const int64_t rows = (int64_t)s.n_field * t.n_cell * t.n_cell * 9;
+    tab += rows * s.K * s.K;
+    tab32 += rows * table_row32(s.K);
     max_field = std::max(max_field, s.n_field);
+    max_cells = std::max(max_cells, t.n_cell);
   }
-  if ((int64_t)max_field * (P + 1) * (P + 1) > 65535) return fail(E2E_EINVAL, "too many field nodes x phases");
+  if ((int64_t)max_field * max_cells * max_cells > 65535)
+    return fail(E2E_EINVAL, "too many field nodes x phase cells (n_field x (q + 1)^2 must stay <= 65535)");
   double* d_maps = nullptr;
   double* d_norms = nullptr;
   int rc = upload(&m->d_ts, ts.data(), ts.size());
@@ -419,7 +425,7 @@ int build_psf_tables(Model* m, int P) {
     if (e != cudaSuccess) rc = cuda_fail(e, "PSF tables");
   }
   if (rc == E2E_OK) {
-    cudaError_t e = launch_epsf_build(m->d_ts, ns, max_field, d_maps, d_norms, P, m->d_T64, m->d_T32, 0);
+    cudaError_t e = launch_epsf_build(m->d_ts, ns, max_field, max_cells, d_maps, d_norms, m->d_T64, m->d_T32, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) rc = cuda_fail(e, "PSF table build");
   }
@@ -759,7 +765,7 @@ cudaError_t launch_items(e2e_ctx* ctx, Model* m, int K, int first, int count, co
                          cudaStream_t st, const MergeArgs* mg = nullptr) {
   const Plan& P = m->plan;
   if (m->psf == E2E_PSF_TABLE)
-    return launch_render_table(K, m->d_slices, m->d_ts, m->d_T32, m->d_field, m->phases, d_table, m->d_u,
+    return launch_render_table(K, m->d_slices, m->d_ts, m->d_T32, m->d_field, d_table, m->d_u,
                                P.d_items + first, count, store, P.nk_max, P.max_deg, P.smem, st, ctx->d_err);
   if (m->psf == E2E_PSF_ELLIPTICAL)
     return launch_render_ellip(K, m->d_slices, d_table, m->d_u, P.d_items + first, count, store, P.nk_max,
@@ -769,7 +775,7 @@ cudaError_t launch_items(e2e_ctx* ctx, Model* m, int K, int first, int count, co
 }
 
 int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, int precision, int dtype,
-                void* const* dst, const int64_t* pitch_in, cudaStream_t st) {
+                void* const* dst, const int64_t* pitch_in, cudaStream_t st, const int2* frozen = nullptr) {
   NvtxRange nvtx_("e2e render");
   if (dtype != E2E_F32 && dtype != E2E_F64) return fail(E2E_EINVAL, "dtype must be E2E_F32 or E2E_F64");
   if (precision != E2E_PREC_MIXED && precision != E2E_PREC_FP64) return fail(E2E_EINVAL, "bad precision");
@@ -826,13 +832,13 @@ int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, in
       KernelTimer kt(ctx, st, tab ? "render_fp64_table" : ellip ? "render_fp64_ellip" : "render_fp64");
       if (tab)
         E2E_CK(launch_render_fp64_table(K, (int)m->slices.size(), m->max_stamps, m->d_slices, m->d_ts, m->d_T64,
-                                        m->d_field, m->phases, d_table, m->d_u, d_acc, d_apitch, st));
+                                        m->d_field, d_table, m->d_u, d_acc, d_apitch, st));
       else if (ellip)
         E2E_CK(launch_render_fp64_ellip(K, (int)m->slices.size(), m->max_stamps, m->d_slices, d_table, m->d_u,
                                         d_acc, d_apitch, st));
       else
         E2E_CK(launch_render_fp64(K, (int)m->slices.size(), m->max_stamps, m->d_slices, d_table, m->d_u, d_acc,
-                                  d_apitch, st));
+                                  d_apitch, st, frozen));
     }
     if (dtype == E2E_F32)
       for (int d = 0; d < m->n_det; ++d) {
@@ -1105,8 +1111,6 @@ int e2e_load_model(e2e_ctx* ctx, const e2e_model_desc* desc, uint64_t* model_id)
   if (desc->n_slices < 0 || (desc->n_slices > 0 && !desc->slices)) return fail(E2E_EINVAL, "bad slice list");
   if (desc->psf != E2E_PSF_SEPARABLE && desc->psf != E2E_PSF_ELLIPTICAL && desc->psf != E2E_PSF_TABLE)
     return fail(E2E_EINVAL, "bad psf kind");
-  const int phases = desc->psf_phases > 0 ? desc->psf_phases : 8;
-  if (desc->psf == E2E_PSF_TABLE && phases > 64) return fail(E2E_EINVAL, "psf_phases must be 1..64");
   for (int d = 0; d < desc->n_detectors; ++d)
     if (desc->height[d] < 1 || desc->width[d] < 1 || desc->height[d] > 16000 || desc->width[d] > 16000)
       return fail(E2E_EINVAL, "detector size must be 1..16000 px");
@@ -1172,6 +1176,8 @@ int e2e_load_model(e2e_ctx* ctx, const e2e_model_desc* desc, uint64_t* model_id)
     v.u_off = (int64_t)u_all.size();
     v.coef_off = coef_total;
     v.index = i;
+    v.stamp_off = m->n_stamps;
+    m->n_stamps += (int64_t)s.n_lambda * s.n_slit;
     coef_total += nc;
     u_all.insert(u_all.end(), s.slit_weights, s.slit_weights + s.n_slit);
     m->max_stamps = std::max(m->max_stamps, (int64_t)s.n_lambda * s.n_slit);
@@ -1239,7 +1245,7 @@ int e2e_load_model(e2e_ctx* ctx, const e2e_model_desc* desc, uint64_t* model_id)
     if (rc == E2E_OK) rc = upload(&m->d_cf32, cf.data(), cf.size());
   }
   if (rc == E2E_OK) rc = upload(&m->d_bin_off, bin_off.data(), bin_off.size());
-  if (rc == E2E_OK && m->psf == E2E_PSF_TABLE) rc = build_psf_tables(m.get(), phases);
+  if (rc == E2E_OK && m->psf == E2E_PSF_TABLE) rc = build_psf_tables(m.get());
   if (rc == E2E_OK) rc = upload(&m->d_dims, dims.data(), dims.size());
   if (rc == E2E_OK) rc = plan_model(m.get());
   if (rc != E2E_OK) {
@@ -1331,6 +1337,31 @@ int e2e_render(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* 
   Model* m = find_model(ctx, model_id);
   if (!m) return fail(E2E_ENOTFOUND, "unknown model id");
   return render_impl(ctx, m, n_spec, spec_ids, precision, dtype, dst, pitch_elems, (cudaStream_t)stream);
+}
+
+int e2e_window_origins(e2e_ctx* ctx, uint64_t model_id, int32_t* origins, void* stream) {
+  if (!ctx || !origins) return fail(E2E_EINVAL, "null argument");
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Model* m = find_model(ctx, model_id);
+  if (!m) return fail(E2E_ENOTFOUND, "unknown model id");
+  E2E_CK(launch_window_origins((int)m->slices.size(), m->max_stamps, m->d_slices, reinterpret_cast<int2*>(origins),
+                               (cudaStream_t)stream));
+  return E2E_OK;
+}
+
+int e2e_render_frozen(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids,
+                      const int32_t* frozen_windows, int32_t dtype, void* const* dst, const int64_t* pitch_elems,
+                      void* stream) {
+  if (!ctx || !frozen_windows) return fail(E2E_EINVAL, "null argument");
+  if (reinterpret_cast<uintptr_t>(frozen_windows) % 8 != 0) return fail(E2E_EINVAL, "frozen_windows must be 8-byte aligned");
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Model* m = find_model(ctx, model_id);
+  if (!m) return fail(E2E_ENOTFOUND, "unknown model id");
+  if (m->psf != E2E_PSF_SEPARABLE) return fail(E2E_EINVAL, "frozen windows support the separable PSF");
+  return render_impl(ctx, m, n_spec, spec_ids, E2E_PREC_FP64, dtype, dst, pitch_elems, (cudaStream_t)stream,
+                     reinterpret_cast<const int2*>(frozen_windows));
 }
 
 int e2e_render_alloc(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids, int32_t precision,
@@ -1557,7 +1588,7 @@ int e2e_render_static(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uin
 
 int e2e_render_adjoint(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids, int32_t dtype,
                        const void* const* dldi, const int64_t* pitch_in, double* g_cx, double* g_cy, double* g_sx,
-                       double* g_sy, void* stream) {
+                       double* g_sy, const int32_t* frozen_windows, void* stream) {
   NvtxRange nvtx_("e2e adjoint");
   if (!ctx || !dldi || !g_cx || !g_cy || !g_sx || !g_sy) return fail(E2E_EINVAL, "null argument");
   if (dtype != E2E_F32 && dtype != E2E_F64) return fail(E2E_EINVAL, "dtype must be E2E_F32 or E2E_F64");
@@ -1566,6 +1597,7 @@ int e2e_render_adjoint(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const ui
   Model* m = find_model(ctx, model_id);
   if (!m) return fail(E2E_ENOTFOUND, "unknown model id");
   if (m->psf != E2E_PSF_SEPARABLE) return fail(E2E_EINVAL, "the adjoint supports the separable PSF");
+  if (reinterpret_cast<uintptr_t>(frozen_windows) % 8 != 0) return fail(E2E_EINVAL, "frozen_windows must be 8-byte aligned");
   const Plan& P = m->plan;
   std::vector<int64_t> pitch(m->n_det);
   for (int d = 0; d < m->n_det; ++d) {
@@ -1602,7 +1634,8 @@ int e2e_render_adjoint(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const ui
   for (auto& grp : P.groups) {
     KernelTimer kt(ctx, st, "adjoint");
     E2E_CK(launch_adjoint(grp.K, m->d_slices, d_table, m->d_u, P.d_items + grp.first, grp.count, d_dldi, d_pitch,
-                          dtype == E2E_F32 ? 0 : 1, P.B, P.nk_max, parts, g_cx, g_cy, g_sx, g_sy, smem, st));
+                          dtype == E2E_F32 ? 0 : 1, P.B, P.nk_max, parts, g_cx, g_cy, g_sx, g_sy, smem, st,
+                          reinterpret_cast<const int2*>(frozen_windows)));
   }
   return E2E_OK;
 }

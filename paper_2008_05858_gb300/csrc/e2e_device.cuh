@@ -39,14 +39,21 @@ struct Item {
   int64_t store_off;  // offset (elements) of this item's box in the render's box store
 };
 
-// Tabulated-PSF slice: its maps, field nodes and effective-PSF tables in the model's arrays.
+// Tabulated-PSF slice: its maps, field nodes and per-cell phase polynomials in the model's
+// arrays.  The sub-pixel phase range [-1/2, 1/2] of each axis is cut into n_cell cells of
+// width 1/q (q + 1 cells, the end ones half as wide, when map_size is even); per field node,
+// cell (cy, cx) and window pixel the table holds the 9 coefficients of the pixel integral's
+// biquadratic in the cell.
 struct TableSlice {
-  int64_t tab_off;    // first FP64 table entry (n_field x (P+1)^2 x K^2)
-  int64_t tab_off32;  // first FP32 table entry (n_field x (P+1)^2 rows of table_row32(K) floats)
+  int64_t tab_off;    // first FP64 entry (n_field x n_cell^2 x 9 rows of K^2)
+  int64_t tab_off32;  // first FP32 entry (n_field x n_cell^2 x 9 rows of table_row32(K) floats)
   int64_t map_off;    // first map sample (n_field x M^2)
   int32_t field_off;  // first field node
   int32_t n_field, map_size, K;
-  double q;           // map samples per pixel
+  int32_t q;          // map samples per pixel (an integer)
+  int32_t n_cell;     // phase cells per axis
+  int32_t half;       // 1 when map_size is even (cells start half a cell into the phase range)
+  int32_t pad;
 };
 
 // Floats per FP32 table row: the K^2 window pixels padded to a multiple of 32, so that every

@@ -29,7 +29,9 @@ struct MergeArgs {
 
 cudaError_t launch_render_fp64(int K, int n_slices, int64_t max_stamps, const DevSlice* slices,
                                const double* const* flux_tab, const double* u_all, double* const* acc,
-                               const int64_t* pitch, cudaStream_t st);
+                               const int64_t* pitch, cudaStream_t st, const int2* frozen = nullptr);
+cudaError_t launch_window_origins(int n_slices, int64_t max_stamps, const DevSlice* slices, int2* out,
+                                  cudaStream_t st);
 cudaError_t launch_convert(const double* src, int64_t src_pitch, void* dst, int dtype, int64_t dst_pitch, int H,
                            int W, cudaStream_t st);
 
@@ -59,15 +61,15 @@ cudaError_t launch_noise(uint64_t seed, uint64_t pattern_seed, double dark, doub
                          int64_t src_pitch, const double* R, const float* R32, int dst_dtype, void* dst,
                          int64_t dst_pitch, int H, int W, int det, cudaStream_t st);
 
-cudaError_t launch_epsf_build(const TableSlice* ts, int n_slices, int max_field, const double* maps, double* norms,
-                              int P, double* T64, float* T32, cudaStream_t st);
+cudaError_t launch_epsf_build(const TableSlice* ts, int n_slices, int max_field, int max_cells, const double* maps,
+                              double* norms, double* T64, float* T32, cudaStream_t st);
 size_t table_smem_bytes(int area, int nk_max, int nd);
 cudaError_t launch_render_table(int K, const DevSlice* slices, const TableSlice* ts, const float* T32,
-                                const double* field_lt, int P, const double* const* flux_tab, const double* u_all,
+                                const double* field_lt, const double* const* flux_tab, const double* u_all,
                                 const Item* items, int n_items, float2* store, int nk_max, int max_deg, size_t smem,
                                 cudaStream_t st, int* err = nullptr);
 cudaError_t launch_render_fp64_table(int K, int n_slices, int64_t max_stamps, const DevSlice* slices,
-                                     const TableSlice* ts, const double* T64, const double* field_lt, int P,
+                                     const TableSlice* ts, const double* T64, const double* field_lt,
                                      const double* const* flux_tab, const double* u_all, double* const* acc,
                                      const int64_t* pitch, cudaStream_t st);
 cudaError_t launch_flag_nonfinite(const double* p, int64_t n, int* flag, cudaStream_t st);
@@ -92,6 +94,6 @@ int adjoint_parts(int max_tasks);  // CTAs per item sharing its warp tasks
 cudaError_t launch_adjoint(int K, const DevSlice* slices, const double* const* flux_tab, const double* u_all,
                            const Item* items, int n_items, const void* const* dldi, const int64_t* pitch, int dtype,
                            int B, int nk_max, int parts, double* g_cx, double* g_cy, double* g_sx, double* g_sy,
-                           size_t smem, cudaStream_t st);
+                           size_t smem, cudaStream_t st, const int2* frozen = nullptr);
 
 }  // namespace e2e

@@ -1,20 +1,31 @@
-// Tabulated PSF: effective-PSF tables and the stamp renderers that read them.
+// Tabulated PSF: per-cell phase polynomials of the exact pixel integrals, and the stamp
+// renderers that read them.
 //
 // A slice's PSF is given as maps (Sec. 2.1: the spectrograph unit delivers PSF maps per
 // projected fiber image) at field nodes lt_f along the order: map f samples the density at
 // offsets ((u - c)/q, (v - c)/q) px from the PSF centre, c = (M - 1)/2, and the density
 // between samples is the bilinear interpolant, sum_uv S_uv T(q x - (u - c)) T(q y - (v - c))
-// with T the unit tent.  Its integral over a pixel [a, b) x [a', b') therefore factorises:
+// with T the unit tent.  A stamp's pixel value is that density's integral over the pixel for
+// the PSF centred at the stamp's position (Sec. 2.2), which factorises:
 //
 //   I = sum_v sum_u S_uv X_u Y_v / norm,  X_u = (G(q (b - x_u)) - G(q (a - x_u))) / q,
-//   G(t) = integral of the tent up to t (0, (1+t)^2/2, 1 - (1-t)^2/2, 1),  norm = sum S / q^2,
+//   G(t) = integral of the tent up to t (0, (1+t)^2/2, 1 - (1-t)^2/2, 1),  norm = sum S / q^2.
 //
-// and only the ~q + 2 columns and rows whose tents meet the pixel contribute.  At load time
-// k_epsf_build tabulates, for every node, the K x K window's pixel integrals for the PSF
-// centre at sub-pixel phases -1/2 + p/P, p = 0..P (P + 1 per axis), in FP64 (and FP32 for the
-// mixed renderer).  A stamp then interpolates bilinearly between the four phases around its
-// sub-pixel offset and linearly in lt between the two field nodes around its wavelength (the
-// end node beyond the ends): 8 table reads and 8 FMAs per pixel.
+// As a function of the centre's sub-pixel phase ph (pixel edges at half-integers minus ph),
+// X_u is piecewise quadratic, with knots where an edge crosses a knot of a tent: at
+// ph = 1/2 - (k + c)/q.  For an integer q these knots are the same for every pixel of the
+// window: cells of width 1/q, starting at ph = -1/2 for odd M, half a cell later for even M
+// (then the first and last cells are half cells).  Within a cell pair (x, y) the pixel
+// integral is therefore exactly a biquadratic in the phase.  At load time k_epsf_build
+// evaluates it at the 3 x 3 nodes of every cell (its ends and midpoint per axis) in FP64 and
+// stores the biquadratic's coefficients in the centred variable tau in [-1/2, 1/2]:
+//
+//   f(tau) = T1 + tau (T2 - T0) + tau^2 2 (T0 - 2 T1 + T2)   (per axis; tensor product in 2-D),
+//
+// in FP64 and FP32.  A stamp evaluates it by Horner in tau_x, tau_y (the terms after the first
+// are small, so FP32 keeps a few-ulp error), for the two field nodes around its wavelength (the
+// end node beyond the ends), blended linearly in lt: 18 table reads per pixel, and no
+// interpolation error in the phase.
 #include "e2e_device.cuh"
 #include "e2e_kernels.h"
 #include "mixed_common.cuh"
@@ -45,57 +56,116 @@ __global__ void __launch_bounds__(256) k_map_norm(const TableSlice* __restrict__
     if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) norms[t.field_off + f] = red[0] / (t.q * t.q);
+  if (threadIdx.x == 0) norms[t.field_off + f] = red[0] / ((double)t.q * t.q);
 }
 
-// One block per (slice, node, phase): thread (n, m) integrates the map over window pixel
-// (m, n) for the PSF centred at the phase's offset from the centre pixel's centre.
-__global__ void __launch_bounds__(256) k_epsf_build(const TableSlice* __restrict__ ts, const double* __restrict__ maps,
-                                                    const double* __restrict__ norms, int P, double* __restrict__ T64,
-                                                    float* __restrict__ T32) {
+// Phase of node a (0, 1, 2: start, midpoint, end) of cell i on one axis: in units of 1/q from
+// the cell grid's origin, cell i spans [max(i, h), min(i + 1, q + h)] with h = 1/2 for even
+// maps (half cells at both ends), and ph = r / q - 1/2 - h / q.
+__device__ __forceinline__ double cell_node_phase(const TableSlice& t, int i, int a) {
+  const double h = t.half ? 0.5 : 0.0;
+  const double lo = fmax((double)i, h), hi = fmin((double)(i + 1), (double)t.q + h);
+  const double r = a == 0 ? lo : (a == 1 ? 0.5 * (lo + hi) : hi);
+  return (r - h) / t.q - 0.5;
+}
+
+// Pixel integral of map f's normalised density over window pixel (m, n) for the PSF centred
+// at phase (phx, phy) from the centre pixel's centre.
+__device__ double epsf_pixel(const TableSlice& t, const double* S, double norm, int m, int n, double phx,
+                             double phy) {
+  const int H = t.K / 2, M = t.map_size;
+  const double q = (double)t.q, c = 0.5 * (M - 1);
+  const double ax = m - H - 0.5 - phx, bx = ax + 1.0, ay = n - H - 0.5 - phy, by = ay + 1.0;
+  // samples whose tents meet [a, b): c + q a - 1 < u < c + q b + 1
+  const int u0 = max(0, (int)floor(c + q * ax - 1.0)), u1 = min(M - 1, (int)ceil(c + q * bx + 1.0));
+  const int v0 = max(0, (int)floor(c + q * ay - 1.0)), v1 = min(M - 1, (int)ceil(c + q * by + 1.0));
+  double sum = 0.0;
+  for (int v = v0; v <= v1; ++v) {
+    const double yv = (v - c) / q;
+    const double wy = (tent_cdf(q * (by - yv)) - tent_cdf(q * (ay - yv))) / q;
+    if (wy == 0.0) continue;
+    double row = 0.0;
+    for (int u = u0; u <= u1; ++u) {
+      const double xu = (u - c) / q;
+      row += S[(int64_t)v * M + u] * ((tent_cdf(q * (bx - xu)) - tent_cdf(q * (ax - xu))) / q);
+    }
+    sum += row * wy;
+  }
+  return sum / norm;
+}
+
+// One block per (slice, node, phase cell (cy, cx)): thread (n, m) integrates the map over
+// window pixel (m, n) at the cell's 3 x 3 phase nodes and stores the biquadratic's 9
+// coefficients C[p][r] (power p of tau_y, r of tau_x) as rows p * 3 + r.
+__global__ void __launch_bounds__(128) k_epsf_build(const TableSlice* __restrict__ ts, const double* __restrict__ maps,
+                                                    const double* __restrict__ norms, int max_cells,
+                                                    double* __restrict__ T64, float* __restrict__ T32) {
   const TableSlice& t = ts[blockIdx.x];
-  const int f = blockIdx.y / ((P + 1) * (P + 1));
-  const int ph = blockIdx.y - f * (P + 1) * (P + 1);
-  if (f >= t.n_field) return;
-  const int py = ph / (P + 1), px = ph - py * (P + 1);
-  const int K = t.K, H = K / 2, M = t.map_size;
-  const double q = t.q, c = 0.5 * (M - 1);
-  const double phx = -0.5 + (double)px / P, phy = -0.5 + (double)py / P;
+  const int f = blockIdx.y / (max_cells * max_cells);
+  const int cell = blockIdx.y - f * max_cells * max_cells;
+  const int cyi = cell / max_cells, cxi = cell - cyi * max_cells;
+  if (f >= t.n_field || cyi >= t.n_cell || cxi >= t.n_cell) return;
+  const int K = t.K, KK = K * K, M = t.map_size;
   const double* S = maps + t.map_off + (int64_t)f * M * M;
   const double norm = norms[t.field_off + f];
-  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+  double phx[3], phy[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    phx[a] = cell_node_phase(t, cxi, a);
+    phy[a] = cell_node_phase(t, cyi, a);
+  }
+  const int64_t row0 = (((int64_t)f * t.n_cell + cyi) * t.n_cell + cxi) * 9;
+  const int KR = table_row32(K);
+  for (int e = threadIdx.x; e < KK; e += blockDim.x) {
     const int n = e / K, m = e - n * K;
-    const double ax = m - H - 0.5 - phx, bx = ax + 1.0, ay = n - H - 0.5 - phy, by = ay + 1.0;
-    // samples whose tents meet [a, b): c + q a - 1 < u < c + q b + 1
-    const int u0 = max(0, (int)floor(c + q * ax - 1.0)), u1 = min(M - 1, (int)ceil(c + q * bx + 1.0));
-    const int v0 = max(0, (int)floor(c + q * ay - 1.0)), v1 = min(M - 1, (int)ceil(c + q * by + 1.0));
-    double sum = 0.0;
-    for (int v = v0; v <= v1; ++v) {
-      const double yv = (v - c) / q;
-      const double wy = (tent_cdf(q * (by - yv)) - tent_cdf(q * (ay - yv))) / q;
-      if (wy == 0.0) continue;
-      double row = 0.0;
-      for (int u = u0; u <= u1; ++u) {
-        const double xu = (u - c) / q;
-        row += S[(int64_t)v * M + u] * ((tent_cdf(q * (bx - xu)) - tent_cdf(q * (ax - xu))) / q);
-      }
-      sum += row * wy;
+    double T[3][3];  // T[y node][x node]
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) T[a][b] = epsf_pixel(t, S, norm, m, n, phx[b], phy[a]);
+    // per axis: coefficients of 1, tau, tau^2 from the nodes at tau = -1/2, 0, 1/2
+    double R[3][3];  // R[y node][x power]
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      R[a][0] = T[a][1];
+      R[a][1] = T[a][2] - T[a][0];
+      R[a][2] = 2.0 * (T[a][0] - 2.0 * T[a][1] + T[a][2]);
     }
-    const double val = sum / norm;
-    const int64_t r = (int64_t)ph + (int64_t)f * (P + 1) * (P + 1);
-    T64[t.tab_off + r * K * K + e] = val;
-    T32[t.tab_off32 + r * table_row32(K) + e] = (float)val;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const double c0 = R[1][r], c1 = R[2][r] - R[0][r], c2 = 2.0 * (R[0][r] - 2.0 * R[1][r] + R[2][r]);
+      const double cp[3] = {c0, c1, c2};
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        const int64_t row = row0 + p * 3 + r;
+        T64[t.tab_off + row * KK + e] = cp[p];
+        T32[t.tab_off32 + row * KR + e] = (float)cp[p];
+      }
+    }
   }
 }
 
-cudaError_t launch_epsf_build(const TableSlice* ts, int n_slices, int max_field, const double* maps, double* norms,
-                              int P, double* T64, float* T32, cudaStream_t st) {
+cudaError_t launch_epsf_build(const TableSlice* ts, int n_slices, int max_field, int max_cells, const double* maps,
+                              double* norms, double* T64, float* T32, cudaStream_t st) {
   if (n_slices == 0) return cudaSuccess;
   k_map_norm<<<dim3(n_slices, max_field), 256, 0, st>>>(ts, maps, norms);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_epsf_build<<<dim3(n_slices, max_field * (P + 1) * (P + 1)), 128, 0, st>>>(ts, maps, norms, P, T64, T32);
+  k_epsf_build<<<dim3(n_slices, max_field * max_cells * max_cells), 128, 0, st>>>(ts, maps, norms, max_cells, T64,
+                                                                                    T32);
   return cudaGetLastError();
+}
+
+// Cell and centred coordinate tau in [-1/2, 1/2] of sub-pixel phase ph on one axis (FP64: the
+// phase is the FP64 mapped coordinate minus its window-centre pixel).
+__device__ __forceinline__ void phase_cell(const TableSlice& t, double ph, int& cell, double& tau) {
+  const double h = t.half ? 0.5 : 0.0;
+  const double r = (ph + 0.5) * t.q + h;
+  int i = (int)floor(r);
+  i = min(t.n_cell - 1, max(0, i));
+  const double lo = fmax((double)i, h), hi = fmin((double)(i + 1), (double)t.q + h);
+  cell = i;
+  tau = (r - lo) * (hi - lo < 1.0 ? 2.0 : 1.0) - 0.5;  // cells are 1 or 1/2 wide
 }
 
 // Field node pair and weight of normalised wavelength lt (the end node beyond the ends).
@@ -115,6 +185,14 @@ __device__ __forceinline__ void field_weight(const double* lt_nodes, int F, doub
 
 // ------------------------------------------------------------------ mixed precision
 
+// The biquadratic C[p][r] tau_y^p tau_x^r (rows p * 3 + r) by Horner in tau_x, then tau_y.
+__device__ __forceinline__ float biquad(const float* c, float tx, float ty) {
+  const float r0 = fmaf(tx, fmaf(tx, c[2], c[1]), c[0]);
+  const float r1 = fmaf(tx, fmaf(tx, c[5], c[4]), c[3]);
+  const float r2 = fmaf(tx, fmaf(tx, c[8], c[7]), c[6]);
+  return fmaf(ty, fmaf(ty, r2, r1), r0);
+}
+
 constexpr int kTThreads = 128;
 constexpr int kTWarps = kTThreads / 32;
 
@@ -129,7 +207,7 @@ struct TableLayout {
     o = (o + 15) & ~(size_t)15;
     tabF = o; o += (size_t)J * 16;              // (f0, f1, weight of f1, -) per sample
     stage = o; o += (size_t)kTWarps * 32 * 16;   // per staged stamp: origin, table row offsets
-    stagew = o; o += (size_t)kTWarps * 32 * 32;  // blend coefficients of the 8 table reads
+    stagew = o; o += (size_t)kTWarps * 32 * 16;  // tau_x, tau_y and the two nodes' weights
     boxh = o; o += (size_t)area * 4;
     boxl = o; o += (size_t)area * 4;
     total = o;
@@ -141,13 +219,13 @@ struct TableArgs {
   const TableSlice* ts;
   const float* T32;
   const double* field_lt;
-  int P;
 };
 
 // One CTA per work item (<= 32 samples x <= 16 slit points); the warp's 32 stamps are mapped
-// into staging, then taken one after the other by the whole warp: each lane reads its pixels
-// from the 8 tables around the stamp's phase and wavelength, blends, sums them over stamps
-// with the same window origin, and deposits the sums into the item's box as exact fixed point.
+// into staging, then taken one after the other by the whole warp: each lane evaluates its
+// pixels' biquadratics in the stamp's phase cell at the two field nodes around its
+// wavelength, blends them, sums them over stamps with the same window origin, and deposits
+// the sums into the item's box as exact fixed point.
 template <int K>
 __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) {
   const MixedArgs& a = ta.m;
@@ -156,7 +234,6 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
   const Item it = a.items[blockIdx.x];
   const DevSlice& S = a.slices[it.slice];
   const TableSlice& TS = ta.ts[it.slice];
-  const int P = ta.P;
   const int area = it.bw * it.bh;
   const int nd = S.degree + 1;
   const TableLayout L(32, a.nk_max, a.max_deg + 1, area);
@@ -224,12 +301,13 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
   const float sc = ldexpf(1.f, Psh), sc_hi = ldexpf(1.f, Psh - 22);
   constexpr int KR = table_row32(K);  // floats per table row
   const float* T = ta.T32 + TS.tab_off32;
-  const int node_stride = (P + 1) * (P + 1) * KR;  // n_field (P + 1)^2 <= 65535: offsets fit in 32 bits
-  const int drow = (P + 1) * KR;
+  // a cell's 9 coefficient rows are consecutive; n_field n_cell^2 <= 65535, so offsets fit 32 bits
+  const int cell_stride = 9 * KR;
+  const int node_stride = TS.n_cell * TS.n_cell * cell_stride;
 
   const int nst = it.nj * it.nk;
   int4* wst = stage + warp * 32;
-  float4* wsw = stagew + warp * 64;
+  float4* wsw = stagew + warp * 32;
   // Each lane owns the pixels e = lane, lane + 32, ... of the window.  Consecutive stamps of a
   // warp are consecutive slit points of one sample, whose windows often share their origin:
   // a lane adds its pixels' values in FP32 registers while the origin stays the same (at most
@@ -263,11 +341,12 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
   for (int base = warp * 32; base < nst && total > 0.0; base += kTWarps * 32) {
     {
       // lane i maps stamp base + i and prepares what the whole warp needs of it: the window
-      // origin, the offsets of the table rows around its phase at its two field nodes, and the
-      // 8 blend coefficients (bilinear in phase, linear in wavelength, times the stamp weight)
+      // origin, the offsets of its phase cell's coefficient rows at its two field nodes, the
+      // cell coordinates tau_x, tau_y and the nodes' weights (linear in wavelength, times the
+      // stamp weight)
       const int idx = base + lane;
       int ci = kOffFrame, ri = kOffFrame, aoff = 0, boff = 0;
-      float4 ca = make_float4(0.f, 0.f, 0.f, 0.f), cb = ca;
+      float4 cw = make_float4(0.f, 0.f, 0.f, 0.f);
       if (idx < nst) {
         const int jj = idx / it.nk;
         const int kk = idx - jj * it.nk;
@@ -278,31 +357,32 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
           py[b] = b < nd ? tabP[(jj * 2 + 1) * nd + b] : 0.0;
         }
         const double s = tabS[kk];
+        const double xv = horner_s(px, S.degree, s), yv = horner_s(py, S.degree, s);
         float fx, fy;
-        split_coord(horner_s(px, S.degree, s), ci, fx);
-        split_coord(horner_s(py, S.degree, s), ri, fy);
+        split_coord(xv, ci, fx);
+        split_coord(yv, ri, fy);
         const float2 wj = tabW[jj], uk = tabU[kk];
         const float w = fmaf(wj.x, uk.x, fmaf(wj.x, uk.y, wj.y * uk.x));
         const int4 fw = tabF[jj];
-        const float rx = (fx + 0.5f) * (float)P, ry = (fy + 0.5f) * (float)P;
-        const int ipx = min(P - 1, max(0, (int)floorf(rx))), ipy = min(P - 1, max(0, (int)floorf(ry)));
-        const float ax = rx - (float)ipx, ay = ry - (float)ipy;
-        const float wf1 = __int_as_float(fw.z), wf0 = 1.f - wf1;
-        const float c00 = (1.f - ay) * (1.f - ax) * w, c01 = (1.f - ay) * ax * w;
-        const float c10 = ay * (1.f - ax) * w, c11 = ay * ax * w;
-        ca = make_float4(wf0 * c00, wf0 * c01, wf0 * c10, wf0 * c11);
-        cb = make_float4(wf1 * c00, wf1 * c01, wf1 * c10, wf1 * c11);
-        const int row = (ipy * (P + 1) + ipx) * KR;
+        int cxi = 0, cyi = 0;
+        double tx = 0.0, ty = 0.0;
+        if (ci != kOffFrame && ri != kOffFrame) {
+          phase_cell(TS, xv - (double)ci, cxi, tx);
+          phase_cell(TS, yv - (double)ri, cyi, ty);
+        }
+        const float wf1 = __int_as_float(fw.z);
+        cw = make_float4((float)tx, (float)ty, (1.f - wf1) * w, wf1 * w);
+        const int row = (cyi * TS.n_cell + cxi) * cell_stride;
         aoff = fw.x * node_stride + row;
         boff = fw.y * node_stride + row;
       }
       wst[lane] = make_int4(ci, ri, aoff, boff);
-      wsw[2 * lane] = ca;
-      wsw[2 * lane + 1] = cb;
+      wsw[lane] = cw;
     }
     __syncwarp();
     const int nb = min(32, nst - base);
-    // stamp by stamp (warp-uniform): a pixel costs 8 coalesced table reads and 8 FMAs
+    // stamp by stamp (warp-uniform): a pixel costs 18 coalesced table reads (9 coefficients at
+    // each of two field nodes) and 18 FMAs
     for (int b = 0; b < nb; ++b) {
       const int4 st = wst[b];
       if (st.x == kOffFrame || st.y == kOffFrame) continue;
@@ -313,33 +393,31 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
         n_acc = 0;
       }
       ++n_acc;
-      const float4 ca = wsw[2 * b], cb = wsw[2 * b + 1];
+      const float4 cw = wsw[b];
       const float* A = T + st.z;   // node f0
       const float* Bn = T + st.w;  // node f1
-      // all table reads of this lane's pixels first, then the blends
-      float tv[NI][8];
+      // two pixel groups at a time: their 36 reads first, then the evaluations
 #pragma unroll
-      for (int i = 0; i < NI; ++i) {
-        const int e = lane + 32 * i;
-        if (e < KK) {
-          tv[i][0] = __ldg(A + e); tv[i][1] = __ldg(A + e + KR);
-          tv[i][2] = __ldg(A + e + drow); tv[i][3] = __ldg(A + e + drow + KR);
-          tv[i][4] = __ldg(Bn + e); tv[i][5] = __ldg(Bn + e + KR);
-          tv[i][6] = __ldg(Bn + e + drow); tv[i][7] = __ldg(Bn + e + drow + KR);
+      for (int i0 = 0; i0 < NI; i0 += 2) {
+        float ca[2][9], cb[2][9];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int e = lane + 32 * (i0 + h);
+          if (i0 + h < NI && e < KK) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+              ca[h][k] = __ldg(A + e + k * KR);
+              cb[h][k] = __ldg(Bn + e + k * KR);
+            }
+          }
         }
-      }
 #pragma unroll
-      for (int i = 0; i < NI; ++i) {
-        const int e = lane + 32 * i;
-        if (e >= KK) break;
-        float t = ca.x * tv[i][0];  // the stamp's value first, then one rounding into the sum
-        t = fmaf(ca.y, tv[i][1], t);
-        t = fmaf(ca.z, tv[i][2], t);
-        t = fmaf(ca.w, tv[i][3], t);
-        t = fmaf(cb.x, tv[i][4], t);
-        t = fmaf(cb.y, tv[i][5], t);
-        t = fmaf(cb.z, tv[i][6], t);
-        acc[i] += fmaf(cb.w, tv[i][7], t);
+        for (int h = 0; h < 2; ++h) {
+          const int e = lane + 32 * (i0 + h);
+          if (i0 + h >= NI || e >= KK) break;
+          const float va = biquad(ca[h], cw.x, cw.y), vb = biquad(cb[h], cw.x, cw.y);
+          acc[i0 + h] += fmaf(cw.w, vb, cw.z * va);  // the stamp's value first, then one rounding
+        }
       }
     }
     __syncwarp();
@@ -363,12 +441,12 @@ static cudaError_t launch_table_one(const TableArgs& a, int n_items, size_t smem
 }
 
 cudaError_t launch_render_table(int K, const DevSlice* slices, const TableSlice* ts, const float* T32,
-                                const double* field_lt, int P, const double* const* flux_tab, const double* u_all,
+                                const double* field_lt, const double* const* flux_tab, const double* u_all,
                                 const Item* items, int n_items, float2* store, int nk_max, int max_deg, size_t smem,
                                 cudaStream_t st, int* err) {
   if (n_items == 0) return cudaSuccess;
   TableArgs a{MixedArgs{slices, flux_tab, u_all, items, store, 0, 1, nk_max, max_deg, err}, ts,
-              T32, field_lt, P};
+              T32, field_lt};
   switch (K) {
 #define E2E_CASE(KK) \
   case KK: return launch_table_one<KK>(a, n_items, smem, st);
@@ -380,12 +458,12 @@ cudaError_t launch_render_table(int K, const DevSlice* slices, const TableSlice*
 
 // ------------------------------------------------------------------ FP64
 
-// One thread per stamp: FP64 mapping, FP64 tables, FP64 blend, FP64 atomics.
+// One thread per stamp: FP64 mapping, FP64 coefficient tables and evaluation, FP64 atomics.
 template <int K>
 __global__ void __launch_bounds__(256) k_render_fp64_table(const DevSlice* __restrict__ slices,
                                                            const TableSlice* __restrict__ ts,
                                                            const double* __restrict__ T64,
-                                                           const double* __restrict__ field_lt, int P,
+                                                           const double* __restrict__ field_lt,
                                                            const double* const* __restrict__ flux_tab,
                                                            const double* __restrict__ u_all, double* const* acc,
                                                            const int64_t* __restrict__ pitch) {
@@ -398,7 +476,7 @@ __global__ void __launch_bounds__(256) k_render_fp64_table(const DevSlice* __res
   double* frame = acc[S.det];
   const int64_t Pf = pitch[S.det];
   constexpr int KK = K * K, H = K / 2;
-  const int64_t node_stride = (int64_t)(P + 1) * (P + 1) * KK;
+  const int64_t node_stride = (int64_t)TS.n_cell * TS.n_cell * 9 * KK;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(idx / S.n_slit);
     const int k = (int)(idx - (int64_t)j * S.n_slit);
@@ -418,12 +496,13 @@ __global__ void __launch_bounds__(256) k_render_fp64_table(const DevSlice* __res
     int f0, f1;
     double wf;
     field_weight(field_lt + TS.field_off, TS.n_field, lt, f0, f1, wf);
-    const double rx = (x - ci + 0.5) * P, ry = (y - ri + 0.5) * P;
-    const int ipx = min(P - 1, max(0, (int)floor(rx))), ipy = min(P - 1, max(0, (int)floor(ry)));
-    const double ax = rx - ipx, ay = ry - ipy;
-    const double* T0 = T64 + TS.tab_off + (int64_t)f0 * node_stride;
-    const double* T1 = T64 + TS.tab_off + (int64_t)f1 * node_stride;
-    const int r00 = (ipy * (P + 1) + ipx) * KK, r10 = r00 + (P + 1) * KK;
+    int cxi, cyi;
+    double tx, ty;
+    phase_cell(TS, x - ci, cxi, tx);
+    phase_cell(TS, y - ri, cyi, ty);
+    const int64_t row = (int64_t)(cyi * TS.n_cell + cxi) * 9 * KK;
+    const double* T0 = T64 + TS.tab_off + (int64_t)f0 * node_stride + row;
+    const double* T1 = T64 + TS.tab_off + (int64_t)f1 * node_stride + row;
     for (int nn = 0; nn < K; ++nn) {
       const int r = r0 + nn;
       if (r < 0 || r >= S.H) continue;
@@ -435,9 +514,11 @@ __global__ void __launch_bounds__(256) k_render_fp64_table(const DevSlice* __res
         for (int side = 0; side < 2; ++side) {
           const double we = side ? wf : 1.0 - wf;
           if (we == 0.0) continue;
-          const double* Tn = side ? T1 : T0;
-          v += we * ((1.0 - ay) * ((1.0 - ax) * Tn[r00 + e] + ax * Tn[r00 + KK + e]) +
-                     ay * ((1.0 - ax) * Tn[r10 + e] + ax * Tn[r10 + KK + e]));
+          const double* C = (side ? T1 : T0) + e;
+          double rp[3];
+          for (int p = 0; p < 3; ++p)
+            rp[p] = fma(tx, fma(tx, C[(p * 3 + 2) * KK], C[(p * 3 + 1) * KK]), C[(p * 3) * KK]);
+          v += we * fma(ty, fma(ty, rp[2], rp[1]), rp[0]);
         }
         atomicAdd(frame + (int64_t)r * Pf + i, w * v);
       }
@@ -446,7 +527,7 @@ __global__ void __launch_bounds__(256) k_render_fp64_table(const DevSlice* __res
 }
 
 cudaError_t launch_render_fp64_table(int K, int n_slices, int64_t max_stamps, const DevSlice* slices,
-                                     const TableSlice* ts, const double* T64, const double* field_lt, int P,
+                                     const TableSlice* ts, const double* T64, const double* field_lt,
                                      const double* const* flux_tab, const double* u_all, double* const* acc,
                                      const int64_t* pitch, cudaStream_t st) {
   if (n_slices == 0 || max_stamps == 0) return cudaSuccess;
@@ -455,7 +536,7 @@ cudaError_t launch_render_fp64_table(int K, int n_slices, int64_t max_stamps, co
   dim3 grid((unsigned)bx, (unsigned)n_slices);
   switch (K) {
 #define E2E_CASE(KK) \
-  case KK: k_render_fp64_table<KK><<<grid, 256, 0, st>>>(slices, ts, T64, field_lt, P, flux_tab, u_all, acc, pitch); break;
+  case KK: k_render_fp64_table<KK><<<grid, 256, 0, st>>>(slices, ts, T64, field_lt, flux_tab, u_all, acc, pitch); break;
     E2E_CASE(1) E2E_CASE(3) E2E_CASE(5) E2E_CASE(7) E2E_CASE(9) E2E_CASE(11) E2E_CASE(13) E2E_CASE(15)
 #undef E2E_CASE
     default: return cudaErrorInvalidValue;

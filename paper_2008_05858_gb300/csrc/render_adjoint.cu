@@ -10,7 +10,10 @@
 // where, for a pixel between edges e0 < e1 and u = (e - x_c)/sigma,
 //   dA/dx_c = -(phi(u1) - phi(u0)) / sigma,   dA/dsigma = -(u1 phi(u1) - u0 phi(u0)) / sigma,
 // and the chain rule through x_c = sum c_ab lt^a s^b and sigma = sum p_q lt^q gives the
-// coefficient gradients.  The work decomposition is the forward's (items, boxes): dL/dI over
+// coefficient gradients.  With frozen windows (origins given per stamp, e.g. those of an
+// earlier render) a stamp's centre may lie beyond its window's centre pixel, so the profile
+// picks each pixel's formula by the signs of its edges, and window pixels outside the item's
+// box are read from the frame.  The work decomposition is the forward's (items, boxes): dL/dI over
 // the item's box is staged in shared memory, each lane takes a run of slit points of one
 // wavelength sample, gathers its stamps' windows, and the per-run sums are reduced over the
 // warp in FP32 and over the warp's tasks and the CTA in FP64 before one global FP64 add per
@@ -42,6 +45,7 @@ struct AdjArgs {
   double* g_cy;
   double* g_sx;
   double* g_sy;
+  const int2* frozen;       // nullable: window origins (i0, r0) per stamp of the model
 };
 
 __device__ __forceinline__ float2 split_pair(double v) {
@@ -81,7 +85,46 @@ __device__ __forceinline__ void axis_profile(float f, float gh, float gl, float 
   }
 }
 
+// The same for a window whose centre pixel need not contain the stamp's centre (frozen
+// windows; |f| < K/2 + 1/2): pixels on one side of the centre take differences of tails, the
+// pixel across it a sum of erf, and a pixel whose inner edge lies within kErfMaxArg of the
+// centre a difference of erf.
 template <int K>
+__device__ __forceinline__ void axis_profile_any(float f, float gh, float gl, float inv_sigma, float* A, float* dA,
+                                                 float* sA) {
+  constexpr int H = K / 2;
+  float E[K + 1], Fv[K + 1], ph[K + 1], u[K + 1], W[K + 1];
+  const float inv_sqrt2pi = 0.398942280401432678f;
+#pragma unroll
+  for (int m = 0; m <= K; ++m) {
+    const float e = (float)(m - H) - 0.5f;
+    // e - f exactly as a pair (TwoSum: |f| may exceed |e|), times g = gh + gl
+    const float dh = e - f;
+    const float bb = dh - e;
+    const float dl = (e - (dh - bb)) + (-f - bb);
+    const float wh = dh * gh;
+    const float wl = fmaf(dh, gh, -wh) + fmaf(dh, gl, dl * gh);
+    float dens;
+    E[m] = tail2_dens(wh, wl, dens);
+    ph[m] = dens * inv_sqrt2pi;
+    u[m] = dh * inv_sigma;
+    W[m] = wh;
+    Fv[m] = fabsf(wh) < kErfMaxArg ? erf_small(wh) : 1.f - E[m];
+  }
+#pragma unroll
+  for (int m = 0; m < K; ++m) {
+    const float a0 = W[m], a1 = W[m + 1];
+    float v;
+    if (a0 >= 0.f) v = a0 < kErfMaxArg ? Fv[m + 1] - Fv[m] : E[m] - E[m + 1];          // right of the centre
+    else if (a1 <= 0.f) v = -a1 < kErfMaxArg ? Fv[m] - Fv[m + 1] : E[m + 1] - E[m];    // left of it
+    else v = Fv[m] + Fv[m + 1];                                                        // across it
+    A[m] = 0.5f * v;
+    dA[m] = -(ph[m + 1] - ph[m]) * inv_sigma;
+    sA[m] = -(u[m + 1] * ph[m + 1] - u[m] * ph[m]) * inv_sigma;
+  }
+}
+
+template <int K, bool FROZEN>
 __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
   constexpr int H = K / 2;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -148,15 +191,28 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
         const double sd = tabS[k - it.k0];
         int ci, ri;
         float fx, fy;
-        split_coord(horner_s(px, d, sd), ci, fx);
-        split_coord(horner_s(py, d, sd), ri, fy);
+        const double xv = horner_s(px, d, sd), yv = horner_s(py, d, sd);
+        split_coord(xv, ci, fx);
+        split_coord(yv, ri, fy);
         if (ci == kOffFrame || ri == kOffFrame) continue;
         const float2 uk = tabU[k - it.k0];
         const float w = fmaf(wj.x, uk.x, fmaf(wj.x, uk.y, wj.y * uk.x));
         float Ax[K], dAx[K], sAx[K], Ay[K], dAy[K], sAy[K];
-        axis_profile<K>(fx, gx.x, gx.y, isx, Ax, dAx, sAx);
-        axis_profile<K>(fy, gy.x, gy.y, isy, Ay, dAy, sAy);
-        // gather dL/dI over the window (pixels outside the box lie outside the detector)
+        if constexpr (FROZEN) {
+          const int2 o = a.frozen[S.stamp_off + (int64_t)j * S.n_slit + k];
+          ci = o.x + H;
+          ri = o.y + H;
+          fx = (float)(xv - (double)ci);
+          fy = (float)(yv - (double)ri);
+          axis_profile_any<K>(fx, gx.x, gx.y, isx, Ax, dAx, sAx);
+          axis_profile_any<K>(fy, gy.x, gy.y, isy, Ay, dAy, sAy);
+        } else {
+          axis_profile<K>(fx, gx.x, gx.y, isx, Ax, dAx, sAx);
+          axis_profile<K>(fy, gy.x, gy.y, isy, Ay, dAy, sAy);
+        }
+        // gather dL/dI over the window (with the forward's windows, pixels outside the box lie
+        // outside the detector; frozen windows may reach detector pixels beyond the box, which
+        // are read from the frame)
         float Sx[K], Sy[K];
 #pragma unroll
         for (int m = 0; m < K; ++m) Sx[m] = 0.f;
@@ -165,11 +221,21 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
         for (int n = 0; n < K; ++n) {
           float sy = 0.f;
           const int gy = by + n;
-          if (gy >= 0 && gy < it.bh) {
+          if (FROZEN || (gy >= 0 && gy < it.bh)) {
 #pragma unroll
             for (int m = 0; m < K; ++m) {
               const int gx2 = bx + m;
-              const float r = (gx2 >= 0 && gx2 < it.bw) ? R[gy * it.bw + gx2] : 0.f;
+              float r = 0.f;
+              if (gy >= 0 && gy < it.bh && gx2 >= 0 && gx2 < it.bw) {
+                r = R[gy * it.bw + gx2];
+              } else if (FROZEN) {
+                const int X = it.bx0 + gx2, Y = it.by0 + gy;
+                if (X >= 0 && X < S.W && Y >= 0 && Y < S.H) {
+                  const int64_t off = (int64_t)Y * a.pitch[S.det] + X;
+                  r = a.dtype == 0 ? static_cast<const float*>(a.dldi[S.det])[off]
+                                   : (float)static_cast<const double*>(a.dldi[S.det])[off];
+                }
+              }
               sy = fmaf(r, Ax[m], sy);
               Sx[m] = fmaf(r, Ay[n], Sx[m]);
             }
@@ -267,7 +333,7 @@ int adjoint_parts(int max_tasks) { return std::max(1, std::min(4, (max_tasks + k
 
 template <int K>
 static cudaError_t launch_adj(const AdjArgs& a, int n_items, int parts, size_t smem, cudaStream_t st) {
-  auto kern = k_adjoint<K>;
+  auto kern = a.frozen ? k_adjoint<K, true> : k_adjoint<K, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<dim3(n_items, parts), kAdjThreads, smem, st>>>(a);
@@ -277,9 +343,9 @@ static cudaError_t launch_adj(const AdjArgs& a, int n_items, int parts, size_t s
 cudaError_t launch_adjoint(int K, const DevSlice* slices, const double* const* flux_tab, const double* u_all,
                            const Item* items, int n_items, const void* const* dldi, const int64_t* pitch, int dtype,
                            int B, int nk_max, int parts, double* g_cx, double* g_cy, double* g_sx, double* g_sy,
-                           size_t smem, cudaStream_t st) {
+                           size_t smem, cudaStream_t st, const int2* frozen) {
   if (n_items == 0) return cudaSuccess;
-  AdjArgs a{slices, flux_tab, u_all, items, dldi, pitch, dtype, B, nk_max, g_cx, g_cy, g_sx, g_sy};
+  AdjArgs a{slices, flux_tab, u_all, items, dldi, pitch, dtype, B, nk_max, g_cx, g_cy, g_sx, g_sy, frozen};
   switch (K) {
     case 1: return launch_adj<1>(a, n_items, parts, smem, st);
     case 3: return launch_adj<3>(a, n_items, parts, smem, st);

@@ -109,12 +109,13 @@ class PsfMap:
 
 
 def psf_maps(s: "OrderSlice", *, n_field: int = 5, oversample: float = 10.0, half_px: float = 8.0,
-             coma: float = 0.0) -> PsfMap:
+             coma: float = 0.0, even_size: bool = False) -> PsfMap:
     """Synthetic PSF maps (the optical design's maps are not available): at n_field
     wavelengths the slice's Gaussian (widths sigma_x, sigma_y at that wavelength), plus, when
     coma > 0, a fainter Gaussian displaced along x by 1.5 sigma_x (a comatic tail) carrying
-    that fraction of the light."""
-    M = int(2 * round(half_px * oversample) + 1)
+    that fraction of the light.  The map has an odd number of samples per side (a sample at
+    the centre) unless even_size, which centres the PSF between the two middle samples."""
+    M = int(2 * round(half_px * oversample) + (0 if even_size else 1))
     c = (M - 1) / 2.0
     lt = np.linspace(-1.0, 1.0, n_field)
     x = (np.arange(M) - c) / oversample

@@ -9,6 +9,13 @@ resolution element must move by less than about 1e-5 px):
   error is set by the FP32 representation of distances of ~5 sigma, not by the method);
 * photocenter: flux-weighted centroids of fixed 16 x 16 px windows, for every window
   holding at least 1e-3 of the brightest window's flux, move by less than 1e-5 px.
+
+Window flips.  A stamp's window is centred on floor(c + 1/2); where the mapped centre c lies
+within rounding distance of a half-integer, two correct evaluations of c may pick windows one
+pixel apart.  Such stamps are found with the oracle (window_ties) and passed to compare() as
+boxes around both candidate windows; pixels failing the bound inside a box, and photocenter
+windows that meet one, are reported as flips, apart from the failures, not hidden in the
+tolerance.
 """
 from __future__ import annotations
 
@@ -37,10 +44,13 @@ PHOTOCENTER_PX = _golden_photocenter_bound()
 class Report:
     max_rel: float  # max |g-o|/|o| over pixels with o >= 1e-4 max
     worst_excess: float  # max over pixels of |g-o| / (REL|o| + FLOOR max|o|); <= 1 passes
-    n_bad: int
+    n_bad: int  # pixels failing the bound, flips excluded
     photocenter_dx: float
     photocenter_dy: float
     n_windows: int
+    n_ties: int = 0  # stamps (per axis) whose centre lies within the tie margin of a pixel edge
+    n_flip_px: int = 0  # pixels failing the bound inside a tie box (explained by a flip)
+    n_flip_windows: int = 0  # photocenter windows over the bound that meet a tie box
 
     @property
     def ok(self) -> bool:
@@ -48,7 +58,26 @@ class Report:
 
     def __str__(self):
         return (f"max_rel={self.max_rel:.3e} worst_excess={self.worst_excess:.3f} bad={self.n_bad} "
-                f"photocenter dx={self.photocenter_dx:.2e} dy={self.photocenter_dy:.2e} windows={self.n_windows}")
+                f"photocenter dx={self.photocenter_dx:.2e} dy={self.photocenter_dy:.2e} windows={self.n_windows} "
+                f"ties={self.n_ties} flip_px={self.n_flip_px} flip_windows={self.n_flip_windows}")
+
+
+TIE_MARGIN = 1e-9  # px: far above the ~1e-12 px rounding of the mapping at 9216 px
+
+
+def tie_boxes(model, flux_of, margin: float = TIE_MARGIN):
+    """Per detector, the boxes (x0, x1, y0, y1), half-open, that hold both candidate windows of
+    every stamp whose centre lies within `margin` px of a pixel edge (oracle.window_ties)."""
+    import oracle
+
+    boxes = {d: [] for d in range(len(model.det_shape))}
+    for i, det, j, k, axis in oracle.window_ties(model, flux_of, margin):
+        s = model.slices[i]
+        xc, yc, _, _, _ = oracle.map_stamp(s, flux_of(s), j, k)
+        i0 = int(np.floor(xc + 0.5)) - s.K // 2
+        r0 = int(np.floor(yc + 0.5)) - s.K // 2
+        boxes[det].append((i0 - 1, i0 + s.K + 1, r0 - 1, r0 + s.K + 1))
+    return boxes
 
 
 def window_centroids(frame: np.ndarray, win: int = WINDOW):
@@ -67,7 +96,8 @@ def window_centroids(frame: np.ndarray, win: int = WINDOW):
         return flux, mx / flux, my / flux
 
 
-def compare(gpu: np.ndarray, ref: np.ndarray, rel: float = REL, floor: float = FLOOR) -> Report:
+def compare(gpu: np.ndarray, ref: np.ndarray, rel: float = REL, floor: float = FLOOR, ties=None) -> Report:
+    """ties: boxes (x0, x1, y0, y1) of this frame from tie_boxes (None: no stamp is near a tie)."""
     g = np.asarray(gpu, dtype=np.float64)
     o = np.asarray(ref, dtype=np.float64)
     assert g.shape == o.shape
@@ -77,13 +107,23 @@ def compare(gpu: np.ndarray, ref: np.ndarray, rel: float = REL, floor: float = F
     if peak == 0.0:
         allow = np.full_like(o, 1e-300)
     excess = err / np.maximum(allow, 1e-300)
-    bad = int(np.count_nonzero(err > allow))
+    over = err > allow
+    flip = np.zeros_like(over)
+    for x0, x1, y0, y1 in ties or ():
+        flip[max(y0, 0):max(y1, 0), max(x0, 0):max(x1, 0)] = True
+    bad = int(np.count_nonzero(over & ~flip))
+    n_flip_px = int(np.count_nonzero(over & flip))
     big = np.abs(o) >= 1e-4 * peak if peak > 0 else np.zeros_like(o, dtype=bool)
     max_rel = float(np.max(err[big] / np.abs(o[big]))) if np.any(big) else 0.0
     fg, xg, yg = window_centroids(g)
     fo, xo, yo = window_centroids(o)
     sel = fo >= WINDOW_FLUX_FRACTION * (fo.max() if fo.size else 0.0)
     sel &= fo > 0
+    fw = window_centroids(flip.astype(np.float64))[0] > 0 if flip.size else np.zeros_like(sel)
+    shift = np.maximum(np.abs(xg - xo), np.abs(yg - yo))
+    n_flip_windows = int(np.count_nonzero(sel & fw & (shift >= PHOTOCENTER_PX)))
+    sel &= ~(fw & (shift >= PHOTOCENTER_PX))
     dx = float(np.max(np.abs(xg[sel] - xo[sel]))) if np.any(sel) else 0.0
     dy = float(np.max(np.abs(yg[sel] - yo[sel]))) if np.any(sel) else 0.0
-    return Report(max_rel, float(excess.max()) if excess.size else 0.0, bad, dx, dy, int(np.count_nonzero(sel)))
+    return Report(max_rel, float(excess.max()) if excess.size else 0.0, bad, dx, dy, int(np.count_nonzero(sel)),
+                  len(ties or ()), n_flip_px, n_flip_windows)

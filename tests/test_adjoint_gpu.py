@@ -116,3 +116,73 @@ def test_config5_calibration_gradient(renderer):
     ref = oracle.vjp(w.model, w.flux_for, [dldi.cpu().numpy()])
     check_groups(got, ref)
     renderer.unload_model(mid)
+
+
+def test_window_origins_are_the_oracle_windows(renderer):
+    # every stamp's window origin floor(x_c + 1/2) - K/2 against the oracle's mapping; a stamp
+    # whose centre lies within 1e-9 px of a half-integer may round either way (a tie)
+    w = W.small_config(seed=21, K=9, degree=5, n_lambda=150, n_slit=11, orders=2)
+    mid = renderer.load_model(w.model)
+    got = renderer.window_origins(mid).cpu().numpy()
+    torch.cuda.synchronize()
+    assert got.shape == (w.model.n_stamps, 2)
+    t = 0
+    for s in w.model.slices:
+        f = w.flux_for(s)
+        for j in range(s.n_lambda):
+            for k in range(s.n_slit):
+                xc, yc, _, _, _ = oracle.map_stamp(s, f, j, k)
+                for a, c in ((0, xc), (1, yc)):
+                    want = int(np.floor(c + 0.5)) - s.K // 2
+                    if got[t, a] != want:
+                        assert abs((c + 0.5) - round(c + 0.5)) < 1e-9, (t, a, c, got[t, a], want)
+                t += 1
+    renderer.unload_model(mid)
+
+
+def test_frozen_windows_central_differences_at_config5_window(renderer):
+    # Differentiation workload at its own K = 9 (sigma 1.2..2.0: the window truncates at
+    # ~2.2 sigma, so a re-centring window jumps by far more than a finite-difference signal).
+    # With windows frozen at the unperturbed render's origins (the reading of the gradient as
+    # the derivative with origins held), central differences of the FP64 frozen render agree
+    # with the adjoint and with the oracle's vector-Jacobian product.
+    w = W.config5()
+    w.model.slices = w.model.slices[:4]  # 4 order-slices keep the oracle's reference quick
+    rng = np.random.default_rng(W.SEED_BASE + 55)
+    mid = renderer.load_model(w.model)
+    sids = renderer.load_spectra(w)
+    frozen = renderer.window_origins(mid)
+    I0 = renderer.render(mid, sids, "fp64", "f64")[0]
+    If = renderer.render_frozen(mid, sids, frozen)[0]
+    torch.cuda.synchronize()
+    # frozen at the mapping's own origins: the plain FP64 render (up to FP64 atomic ordering)
+    assert torch.allclose(I0, If, rtol=1e-13, atol=1e-13 * float(I0.abs().max()))
+    T = torch.tensor(rng.poisson(np.maximum(I0.cpu().numpy() * 1.01, 0.0)).astype(np.float64), device="cuda")
+    dldi = 2.0 * (I0 - T)
+    g = [x.cpu().numpy() for x in renderer.adjoint(mid, sids, [dldi], frozen=frozen)]
+    g_nat = [x.cpu().numpy() for x in renderer.adjoint(mid, sids, [dldi])]
+    ref = oracle.vjp(w.model, w.flux_for, [dldi.cpu().numpy()])
+    check_groups(g, ref)
+    for a, b in zip(g, g_nat):  # the same windows: the same gradient
+        np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-9 * np.abs(b).max())
+    p0 = renderer.params(mid)
+    nc = len(p0[0])
+
+    def loss(parts):
+        renderer.update(mid, *parts)
+        fr = renderer.render_frozen(mid, sids, frozen)[0]
+        return float(((fr - T) ** 2).sum())
+
+    cases = [(0, 0, 1e-3), (0, 1, 1e-3), (0, nc - 1, 1e-3), (1, 0, 1e-3), (1, 2, 1e-3), (1, 16, 1e-3),
+             (2, 0, 1e-4), (2, 4, 1e-4), (3, 1, 1e-4), (3, 9, 1e-4)]
+    for grp, i, h in cases:
+        vp = [np.array(x, dtype=np.float64) for x in p0]
+        vm = [np.array(x, dtype=np.float64) for x in p0]
+        vp[grp][i] += h
+        vm[grp][i] -= h
+        fd = (loss(vp) - loss(vm)) / (2 * h)
+        scale = np.abs(g[grp]).max()
+        assert g[grp][i] == pytest.approx(fd, rel=2e-3, abs=2e-4 * scale), (grp, i, g[grp][i], fd)
+        assert ref[grp][i] == pytest.approx(fd, rel=2e-3, abs=2e-4 * scale), (grp, i, ref[grp][i], fd)
+    renderer.update(mid, *p0)
+    renderer.unload_model(mid)

@@ -435,3 +435,34 @@ def test_blaze_is_a_weight_multiplier_with_the_grating_envelope():
     s = w.model.slices[0]
     assert blaze(s, s.blaze_lambda) == 1.0
     assert abs(blaze(s, s.blaze_lambda / (1.0 - 1.0 / s.blaze_order))) < 1e-25
+
+
+def test_window_ties_and_flip_reporting():
+    # Window rule ties (a centre within rounding of a pixel edge may round either way): the
+    # oracle lists exactly the stamps a direct scan of the mapped centres finds, and the frame
+    # comparator counts failing pixels inside a tie's boxes as flips, not as failures.
+    from tests import framecompare as F
+
+    w = W.small_config(seed=3, n_lambda=120, n_slit=7)
+    margin = 2e-3
+    ties = oracle.window_ties(w.model, w.flux_for, margin)
+    want = []
+    for i, s in enumerate(w.model.slices):
+        f = w.flux_for(s)
+        for j in range(s.n_lambda):
+            for k in range(s.n_slit):
+                c = oracle.map_stamp(s, f, j, k)[:2]
+                for a in (0, 1):
+                    d = (c[a] + 0.5) - np.floor(c[a] + 0.5)
+                    if d < margin or 1 - d < margin:
+                        want.append((i, s.detector, j, k, a))
+    assert sorted(ties) == sorted(want) and len(want) > 0
+    boxes = F.tie_boxes(w.model, w.flux_for, margin)[0]
+    ref = oracle.render_workload(w)[0]
+    x0, x1, y0, y1 = boxes[0]
+    g = ref.copy()
+    g[min(max(y0, 0) + 3, ref.shape[0] - 1), min(max(x0, 0) + 3, ref.shape[1] - 1)] *= 1.001
+    rep = F.compare(g, ref, ties=boxes)
+    assert rep.ok and rep.n_flip_px == 1 and rep.n_bad == 0 and rep.n_ties == len(boxes)
+    rep = F.compare(g, ref)
+    assert not rep.ok and rep.n_bad == 1
