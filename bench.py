@@ -15,8 +15,16 @@ frame is rendered into pinned host memory (e2e_render_host: bands of rows are co
 they finish, overlapping the render of the later bands) and the spectra are unloaded; steps
 are pipelined as a streaming caller runs them (the next step's upload overlaps this render).
 
-``--impl reference`` times the FP64 CPU oracle on the host cores instead (bounded sample of
-the same workload per step).  Under torchrun each rank renders its own detector frame
+Accuracy: every leg that times a renderer carries the error of what it rendered against the
+FP64 oracle (per-pixel relative error, the tolerance's worst excess, photocenter shifts of
+16 x 16 px windows, window-rule ties): the headline on six seeded 64 x 64 windows of the timed
+frame, the other legs on a cut sample.  The oracle runs only in these CPU-baseline legs, where
+it is also timed as the baseline.  Other legs: the plain single-fiber case (config 1), the
+elliptical PSF, tabulated PSF, adjoint, detector noise, photon Monte-Carlo and serving, and an
+FMA probe that measures the FP32 and FP64 pipes the roofline is quoted against.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (one step renders a
+bounded sample of the same workload: its first order-slices, one per host core).  Under torchrun each rank renders its own detector frame
 (independent frames, no collective: weak scaling), or with ``--shard band`` its band of rows of
 one frame (halo stamps rendered by both neighbours, no collective: strong scaling).
 """
@@ -134,70 +142,176 @@ def dist_env():
     return rank, world, local
 
 
-def oracle_sample_rate(w: W.Workload, seconds: float = 12.0, max_slices: int = 64):
-    """Stamps/s of the FP64 oracle on a bounded sample (the first order-slices of w)."""
+# ------------------------------------------------------------------ accuracy (oracle legs)
+#
+# The stamps/s figures count only frames that meet the accuracy target, so every leg that
+# times a renderer also compares what it rendered with the FP64 oracle.  The oracle runs only
+# inside these CPU-baseline legs (it is timed there as the baseline too), on a bounded sample.
+
+
+def _poly2(c, degree, lt, s):
+    """x or y of a slice's mapping on the grid lt x s (a plain evaluation for choosing windows)."""
+    out = np.zeros((len(lt), len(s)))
+    for a in range(degree + 1):
+        for b in range(degree + 1 - a):
+            out += c[W.coeff_index(a, b)] * np.outer(lt ** a, s ** b)
+    return out
+
+
+def _summarise(reps):
+    """Worst figures over a list of framecompare reports."""
+    return {"max_rel": max(r.max_rel for r in reps), "worst_excess": max(r.worst_excess for r in reps),
+            "bad_pixels": sum(r.n_bad for r in reps),
+            "photocenter_dx_px": max(r.photocenter_dx for r in reps),
+            "photocenter_dy_px": max(r.photocenter_dy for r in reps),
+            "photocenter_windows": sum(r.n_windows for r in reps),
+            "window_ties": sum(r.n_ties for r in reps), "flip_pixels": sum(r.n_flip_px for r in reps),
+            "ok": all(r.ok for r in reps),
+            "bound": "|g-o| <= 1e-6 |o| + 1e-10 max|o| per pixel; photocenter of 16x16 px windows < 1e-5 px"}
+
+
+def frame_windows_oracle(w: W.Workload, frame: np.ndarray, n_win: int = 6, size: int = 64, seed: int = 2008):
+    """The CPU-baseline leg of the headline: the oracle renders n_win seeded size x size windows
+    on the traces of the timed frame (each window one detector of a model holding every slice
+    whose trace comes within reach of it, translated so the window is that detector), timed as
+    the baseline, and the windows of the GPU frame are compared with them."""
     import oracle
+    from tests.framecompare import compare, tie_boxes
 
+    H, Wd = w.model.det_shape[0]
+    lt, ss = np.linspace(-1.0, 1.0, 513), np.linspace(-1.0, 1.0, 9)
+    yr = [(_poly2(s.cy, s.degree, lt, ss).min(), _poly2(s.cy, s.degree, lt, ss).max()) for s in w.model.slices]
+    rng = np.random.default_rng(seed)
+    wins, sub, src = [], [], {}
+    for d in range(n_win):
+        s = w.model.slices[int(rng.integers(len(w.model.slices)))]
+        t = rng.uniform(-0.95, 0.95)
+        xc = float(_poly2(s.cx, s.degree, np.array([t]), np.array([0.0]))[0, 0])
+        yc = float(_poly2(s.cy, s.degree, np.array([t]), np.array([0.0]))[0, 0])
+        x0 = int(min(max(round(xc) - size // 2, 0), Wd - size))
+        y0 = int(min(max(round(yc) - size // 2, 0), H - size))
+        wins.append((x0, y0))
+        for q, (lo, hi) in zip(w.model.slices, yr):
+            if hi + 2 + q.K >= y0 and lo - 2 - q.K <= y0 + size:
+                c = q.copy()
+                c.cx[0] -= x0
+                c.cy[0] -= y0
+                c.detector = d
+                src[id(c)] = q
+                sub.append(c)
+    model = W.OpticalModel([(size, size)] * n_win, sub, w.model.psf)
+    flux_of = lambda c: w.flux_for(src[id(c)])  # noqa: E731
     cores = os.cpu_count() or 1
-    per = w.model.slices[0].n_lambda * w.model.slices[0].n_slit
-    n = min(len(w.model.slices), max_slices, max(cores, 1))
-    sub = W.OpticalModel(w.model.det_shape, w.model.slices[:n], w.model.psf)
     t0 = time.perf_counter()
-    oracle.render(sub, w.flux_for, n_threads=cores)
+    ref = oracle.render(model, flux_of, n_threads=cores)
     dt = time.perf_counter() - t0
-    # scale the sample to ~`seconds` of work if the first pass was short
-    if dt < seconds / 4 and n < len(w.model.slices):
-        n2 = min(len(w.model.slices), max_slices, int(n * min(8.0, seconds / max(dt, 1e-3))))
-        sub = W.OpticalModel(w.model.det_shape, w.model.slices[:n2], w.model.psf)
-        t0 = time.perf_counter()
-        oracle.render(sub, w.flux_for, n_threads=cores)
-        dt = time.perf_counter() - t0
-        n = n2
-    stamps = n * per
-    return stamps / dt, cores, f"first {n} of {len(w.model.slices)} order-slices ({stamps} stamps), FP64, {dt:.1f} s"
+    ties = tie_boxes(model, flux_of)
+    reps = [compare(frame[y0:y0 + size, x0:x0 + size], ref[d], ties=ties[d]) for d, (x0, y0) in enumerate(wins)]
+    acc = _summarise(reps)
+    acc.update(windows=[list(p) for p in wins], window_px=size, source="cpu_baseline leg (oracle windows)")
+    stamps = model.n_stamps
+    base = {"value": stamps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(sub)} order-slices ({stamps} stamps) reaching {n_win} seeded {size}x{size} windows of "
+                      f"the timed frame, each rendered in full and clipped to its window, FP64, {dt:.1f} s"}
+    return base, acc
 
 
-def oracle_sample_rate_cut(w: W.Workload, n_slices: int = 16, n_lambda: int = 120):
-    """Stamps/s of the FP64 oracle on the first n_slices order-slices of w, each cut to its
-    first n_lambda wavelength samples (the range shortened with them, so the samples keep
-    their spacing and every stamp costs what it costs in the full workload)."""
+def cut_model(w: W.Workload, n_slices: int, n_lambda: int, model=None):
+    """The first n_slices order-slices of w (or of `model`), each cut to its first n_lambda
+    wavelength samples (the range shortened with them, so the samples keep their spacing),
+    and a flux lookup for them."""
     import dataclasses
 
-    import oracle
-
-    cores = os.cpu_count() or 1
-    cut = []
-    for s in w.model.slices[:n_slices]:
+    m = w.model if model is None else model
+    cut, flux = [], {}
+    for s in m.slices[:n_slices]:
         dl = (s.lambda_hi - s.lambda_lo) / s.n_lambda
-        m = min(n_lambda, s.n_lambda)
-        cut.append(dataclasses.replace(s.copy(), n_lambda=m, lambda_hi=s.lambda_lo + m * dl))
-    sub = W.OpticalModel(w.model.det_shape, cut, w.model.psf)
-    flux = {id(c): w.flux_for(s)[:c.n_lambda] for c, s in zip(cut, w.model.slices)}
+        k = min(n_lambda, s.n_lambda)
+        c = dataclasses.replace(s.copy(), n_lambda=k, lambda_hi=s.lambda_lo + k * dl)
+        flux[id(c)] = w.flux_for(s)[:k]
+        cut.append(c)
+    return W.OpticalModel(m.det_shape, cut, m.psf), (lambda c: flux[id(c)])
+
+
+def cut_sample_oracle(B, dev, w: W.Workload, model, n_slices: int, n_lambda: int, precisions=("mixed",)):
+    """CPU-baseline leg on a cut sample (cut_model): the oracle renders it (timed as the
+    baseline) and the GPU renders of the same sample are compared with it, per precision.
+    Comparisons run on the rows and columns the sample touches (16-px aligned, so the
+    photocenter windows are the frame's own)."""
+    import torch
+
+    import oracle
+    from tests.framecompare import compare, tie_boxes
+
+    sub, flux_of = cut_model(w, n_slices, n_lambda, model)
+    cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    oracle.render(sub, lambda c: flux[id(c)], n_threads=cores)
+    ref = oracle.render(sub, flux_of, n_threads=cores)
     dt = time.perf_counter() - t0
+    ties = tie_boxes(sub, flux_of)
+    r = B.Renderer(dev)
+    acc = {}
+    try:
+        mid = r.load_model(sub)
+        sids = []
+        for f in sorted({s.fiber for s in sub.slices}):
+            orders = {s.order: flux_of(s) for s in sub.slices if s.fiber == f}
+            sids.append(r.load_spectrum(W.Spectrum(f, orders)))
+        for prec in precisions:
+            got = r.render(mid, sids, prec, "f32" if prec == "mixed" else "f64")
+            torch.cuda.synchronize()
+            reps = []
+            for d, (g, o) in enumerate(zip(got, ref)):
+                nz = np.nonzero(o)
+                if len(nz[0]) == 0:
+                    continue
+                y0, y1 = nz[0].min() // 16 * 16, min(o.shape[0], (nz[0].max() // 16 + 2) * 16)
+                x0, x1 = nz[1].min() // 16 * 16, min(o.shape[1], (nz[1].max() // 16 + 2) * 16)
+                bx = [(a - x0, b - x0, c - y0, e - y0) for a, b, c, e in ties[d]]
+                reps.append(compare(g[y0:y1, x0:x1].double().cpu().numpy(), o[y0:y1, x0:x1], ties=bx))
+            acc[prec] = _summarise(reps)
+            if prec == "fp64":
+                acc[prec]["bound"] = "FP64 renderer: reported against the 1e-6 bound (its own tests hold it to 5e-11)"
+    finally:
+        r.close()
     stamps = sub.n_stamps
-    return stamps / dt, cores, (f"first {len(cut)} of {len(w.model.slices)} order-slices, each cut to its first "
-                                f"{n_lambda} wavelength samples ({stamps} stamps), FP64, {dt:.1f} s")
+    base = {"value": stamps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {len(sub.slices)} of {len(model.slices)} order-slices, each cut to its first {n_lambda} "
+                      f"wavelength samples ({stamps} stamps), FP64, {dt:.1f} s"}
+    return base, acc
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores.  One step renders a bounded sample
+    of the headline workload -- its first order-slices in full, one per host core (up to 16) --
+    and the line reports that sample's own time per step and stamps/s."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    import oracle
+
     w = W.config2()
-    steps = []
+    cores = os.cpu_count() or 1
+    n = max(1, min(16, cores, len(w.model.slices)))
+    sub = W.OpticalModel(w.model.det_shape, w.model.slices[:n], w.model.psf)
+    stamps = sub.n_stamps
+    times = []
     for i in range(args.warmup + args.steps):
-        rate, cores, sample = oracle_sample_rate(w, seconds=4.0, max_slices=16)
+        t0 = time.perf_counter()
+        oracle.render(sub, w.flux_for, n_threads=cores)
+        dt = time.perf_counter() - t0
         if i >= args.warmup:
-            steps.append(rate)
-    value = statistics.median(steps)
-    stamps = w.model.n_stamps
+            times.append(dt)
+    t = statistics.median(times)
+    value = stamps / t
+    sample = (f"first {n} of {len(w.model.slices)} order-slices of {w.name} in full ({stamps} stamps per step), "
+              f"FP64, median {t:.2f} s per step")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": stamps / value * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "stamps_per_frame": stamps, "frame": "9216x9216", "parallelism": "host cores"},
+        "config": {"workload": f"{w.name}: sample of {n} order-slices", "stamps_per_step": stamps,
+                   "frame": "9216x9216 f64 (the sample's traces)", "parallelism": f"{cores} host cores (OpenMP)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -330,8 +444,13 @@ def run_gpu(args):
     km = statistics.median(kern.get("merge_zero", [float("nan")]))  # the tiles no item overlaps; the rest merge inside the render
     d = w.model.slices[0].degree
     ns = w.model.slices[0].n_slit
-    fp32_peak = n_sm * 128 * 2 * mhz * 1e6  # FLOP/s, FMA = 2
-    fp64_peak = n_sm * 2 * 2 * mhz * 1e6  # 2 DFMA/clk/SM measured (FMA = 2 FLOP)
+    # peaks from unit counts and the sampled clock: 128 FP32 lanes per SM; FP64 from the
+    # part's nominal 1.25 TFLOP/s at 2070 MHz over 152 SMs (1.99 DFMA per clock per SM); an FMA
+    # is 2 FLOP.  The FMA probe's measured rates are reported beside them.
+    dfma_per_clk_sm = 1.25e12 / (2 * 152 * 2070e6)
+    fp32_peak = n_sm * 128 * 2 * mhz * 1e6
+    fp64_peak = n_sm * dfma_per_clk_sm * 2 * mhz * 1e6
+    probe = pipe_rates(B, dev)
     a32 = fp32_flop_per_stamp(K) * stamps_rank / (kr * 1e-3)
     a64 = fp64_fma_per_stamp(d, ns) * 2 * stamps_rank / (kr * 1e-3)
     traffic = _load_traffic()
@@ -341,7 +460,12 @@ def run_gpu(args):
               "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (median SM clock under load)"}
     roof64 = {"bound": "alu", "achieved": a64 / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
               "frac": a64 / fp64_peak, "traffic": traffic, "kernel": "render_mixed", "pipe": "fp64", "kernel_ms": kr,
-              "peak_basis": f"{n_sm} SMs x 2 DFMA/clk (probe) x 2 x {mhz:.0f} MHz"}
+              "peak_basis": f"{n_sm} SMs x {dfma_per_clk_sm:.2f} DFMA/clk (nominal 1.25 TFLOP/s at 2070 MHz) x 2 x "
+                            f"{mhz:.0f} MHz"}
+    roof32["probe_tflops"] = probe["fp32"]["tflops"]
+    roof32["frac_of_probe"] = a32 / (probe["fp32"]["tflops"] * 1e12)
+    roof64["probe_tflops"] = probe["fp64"]["tflops"]
+    roof64["frac_of_probe"] = a64 / (probe["fp64"]["tflops"] * 1e12)
     roof = roof32 if roof32["frac"] >= roof64["frac"] else roof64
     other = roof64 if roof is roof32 else roof32
     launches_per_step = sum(1 for _ in kern)  # distinct kernels per render
@@ -370,13 +494,15 @@ def run_gpu(args):
         "gpu_launches": n_launch,
         "launches_per_step": launches_per_step,
         "clocks": clocks, "peak_source": peak_kind, "wall_s_timed": t_wall,
+        "fma_probe": probe,
     }
+    line["config1"] = config1_run(B, dev, flush, cpu_baseline=(rank == 0 and world == 1 and not args.no_cpu_baseline))
     if not args.no_noise:
         line["noise"] = noise_run(B, r, mid, frame, stream, flush)
     if not args.no_photons:
         line["photon_mc"] = photon_run(B, r, mid, sids, w, stream, flush, kr + km)
     if not args.no_table:
-        line["psf_table"] = table_run(B, dev, w, flush)
+        line["psf_table"] = table_run(B, dev, w, flush, cpu_baseline=(rank == 0 and world == 1 and not args.no_cpu_baseline))
     if not args.no_adjoint:
         line["adjoint"] = adjoint_run(B, dev, flush, cpu_baseline=(rank == 0 and world == 1 and not args.no_cpu_baseline))
     if not args.no_elliptical:
@@ -386,14 +512,90 @@ def run_gpu(args):
         line["serving"] = serving_run(B, dev)
         line["p99_latency_ms"] = line["serving"]["poisson"]["latency_ms"]["p99"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, cores, sample = oracle_sample_rate(w)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        r.render(mid, sids, "mixed", "f32", out=frame, stream=stream)  # the timed step's frame
+        host = frame[0].cpu().numpy()
+        line["cpu_baseline"], line["accuracy"] = frame_windows_oracle(w, host)
+        del host
     if rank == 0:
         print(json.dumps(line), flush=True)
     r.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def config1_run(B, dev, flush, reps=20, cpu_baseline=False):
+    """The plain method's single-fiber case (one order, one fiber, 1024 x 256, 2000 x 16
+    samples, degree 3, sigma 1.5, K = 7): the plain FP64 renderer and the mixed form, timed with
+    CUDA events (a launch-latency-sized frame), and both compared with the oracle."""
+    import torch
+
+    w = W.config1()
+    r = B.Renderer(dev)
+    out = {"workload": w.name, "stamps": w.model.n_stamps, "frame": "1024x256"}
+    try:
+        mid = r.load_model(w.model)
+        sids = r.load_spectra(w)
+        st = torch.cuda.current_stream()
+        frames = {}
+        for prec, dt in (("fp64", "f64"), ("mixed", "f32")):
+            fr = r.render(mid, sids, prec, dt, stream=st)
+            ms = []
+            for _ in range(reps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                r.render(mid, sids, prec, dt, out=fr, stream=st)
+                b.record(st)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            t = statistics.median(ms)
+            out[prec] = {"ms_per_render": t, "value": w.model.n_stamps / (t * 1e-3), "unit": UNIT}
+            frames[prec] = fr[0].double().cpu().numpy()
+        out["speedup_mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    finally:
+        r.close()
+    if cpu_baseline:
+        import oracle
+        from tests.framecompare import compare, tie_boxes
+
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        ref = oracle.render_workload(w, n_threads=cores)[0]
+        dt = time.perf_counter() - t0
+        ties = tie_boxes(w.model, w.flux_for)[0]
+        out["cpu_baseline"] = {"value": w.model.n_stamps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"the whole frame ({w.model.n_stamps} stamps), FP64, {dt:.2f} s"}
+        out["accuracy"] = {k: _summarise([compare(frames[k], ref, ties=ties)]) for k in ("mixed", "fp64")}
+        err = np.abs(frames["fp64"] - ref)
+        out["accuracy"]["fp64"]["max_rel_all_pixels"] = float(np.max(err[ref > 0] / ref[ref > 0]))
+    return out
+
+
+def pipe_rates(B, dev, reps=3):
+    """FMA rates of the FP32 and FP64 pipes, measured with the library's FMA probe (8 CTAs of
+    256 threads per SM, 8 independent chains per thread), best of `reps` CUDA-event timings."""
+    import torch
+
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = n_sm * 8
+    out = {}
+    for name, fp64, iters, td in (("fp32", False, 100000, torch.float32), ("fp64", True, 2000, torch.float64)):
+        sink = torch.empty(blocks * 256, dtype=td, device="cuda")
+        st = torch.cuda.current_stream()
+        B.e2e_fma_probe(fp64, blocks, iters, sink.data_ptr(), st)
+        best = float("inf")
+        n = 0
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            n = B.e2e_fma_probe(fp64, blocks, iters, sink.data_ptr(), st)
+            b.record(st)
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        rate = n / (best * 1e-3)
+        out[name] = {"fma_per_s": rate, "tflops": 2 * rate / 1e12, "ms": best, "fmas": n}
+    return out
 
 
 def photon_run(B, r, mid, sids, w, stream, flush, stamp_ms, reps=3):
@@ -437,7 +639,7 @@ def Bd_spec(sp, k):
     return W.Spectrum(sp.fiber, {o: f * k for o, f in sp.flux.items()})
 
 
-def table_run(B, dev, w, flush, reps=3):
+def table_run(B, dev, w, flush, reps=3, cpu_baseline=False):
     """The full-detector workload with tabulated PSF maps (5 field nodes per slice, 10 samples
     per pixel over +-8 px, a 20 % comatic tail; exact per-cell phase biquadratics): mixed
     precision and the plain FP64 renderer, timed with CUDA events."""
@@ -466,8 +668,11 @@ def table_run(B, dev, w, flush, reps=3):
         out[prec] = {"ms_per_render": t, "value": m.n_stamps / (t * 1e-3), "unit": UNIT}
     out["speedup_mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
     out["model_load_s"] = load_s
-    out["workload"] = "full-detector frame (9216^2, 85 orders x 2 x 2, 6000 x 64, K=11) with tabulated PSF maps"
     r.close()
+    if cpu_baseline:
+        tw = W.Workload(w.name, m, w.spectra, "f32", "mixed")
+        out["cpu_baseline"], out["accuracy"] = cut_sample_oracle(B, dev, tw, m, 16, 120, ("mixed", "fp64"))
+    out["workload"] = "full-detector frame (9216^2, 85 orders x 2 x 2, 6000 x 64, K=11) with tabulated PSF maps"
     return out
 
 
@@ -547,6 +752,7 @@ def adjoint_run(B, dev, flush, reps=10, cpu_baseline=False):
             b.record(stream)
             torch.cuda.synchronize()
             step_ms.append(a.elapsed_time(b))
+        grads = [x.cpu().numpy() for x in r.adjoint(mid, sids, [dldi])]
         out = {"workload": w.name, "stamps": stamps, "gradient_entries": n_grad,
                "adjoint": {"ms": statistics.median(adj_ms), "kernel_ms": statistics.median(kern) if kern else None,
                            "value": stamps / (statistics.median(adj_ms) * 1e-3), "unit": UNIT},
@@ -560,11 +766,22 @@ def adjoint_run(B, dev, flush, reps=10, cpu_baseline=False):
         cores = min(os.cpu_count() or 1, len(w.model.slices))  # the oracle runs one thread per slice
         g = dldi.cpu().numpy()
         t0 = time.perf_counter()
-        oracle.vjp(w.model, w.flux_for, [g], n_threads=cores)
+        ref = oracle.vjp(w.model, w.flux_for, [g], n_threads=cores)
         dt = time.perf_counter() - t0
         out["cpu_baseline"] = {"value": stamps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"the oracle's FP64 vector-Jacobian product over the whole tile "
                                          f"({stamps} stamps), {dt:.2f} s"}
+        acc = {}
+        for name, gg, oo in zip(("cx", "cy", "sigma_x", "sigma_y"), grads, ref):
+            scale = float(np.abs(oo).max())
+            err = np.abs(gg - oo)
+            big = np.abs(oo) >= 1e-3 * scale
+            acc[name] = {"max_abs_err_over_max": float(err.max() / scale) if scale else 0.0,
+                         "max_rel_err_entries_ge_1e-3_max": float(np.max(err[big] / np.abs(oo[big]))) if big.any() else 0.0}
+        acc["bound"] = "per group |g - o| <= 2e-5 max|o| + 2e-4 |o| (the adjoint tests' tolerance)"
+        acc["ok"] = all(bool(np.all(np.abs(gg - oo) <= 2e-5 * np.abs(oo).max() + 2e-4 * np.abs(oo)))
+                        for gg, oo in zip(grads, ref))
+        out["accuracy"] = acc
     return out
 
 
@@ -603,8 +820,8 @@ def elliptical_run(B, dev, rank=0, world=1, reps=3, cpu_baseline=False):
         r.close()
     out["speedup_mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
     if cpu_baseline:
-        rate, cores, sample = oracle_sample_rate_cut(W.config3(orders_per_detector=1))
-        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        w3 = W.config3(orders_per_detector=1)
+        out["cpu_baseline"], out["accuracy"] = cut_sample_oracle(B, dev, w3, w3.model, 16, 120, ("mixed", "fp64"))
     out["workload"] = "4 x 9216^2 FP32, 30 orders/detector x 4 fibers x 2 slices, 8000 x 128 samples, deg 5, " \
                       "K=13 rotated elliptical PSF (|theta| <= 10 deg); fp64 leg on 1 order/detector"
     return out

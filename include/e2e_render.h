@@ -440,6 +440,14 @@ int e2e_render_static(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uin
  * E2E_ECUDA. */
 int e2e_eval_tail(const double* u_dev, int64_t n, float* out_dev, void* stream);
 
+/* Diagnostic (no counterpart in the paper): the fused multiply-add probe behind the roofline
+ * of the ALU-bound renderers.  Launches `blocks` CTAs of 256 threads, each thread running 8
+ * independent FMA chains of `iters` steps in FP64 (fp64 != 0) or FP32, and writes one value
+ * per thread to sink_dev (blocks * 256 elements of that type, device memory).  *fmas receives
+ * the number of FMAs the launch performs; the caller times it (CUDA events on `stream`) to get
+ * the pipe's FMA rate.  Errors: E2E_EINVAL, E2E_ECUDA. */
+int e2e_fma_probe(int32_t fp64, int32_t blocks, int32_t iters, void* sink_dev, int64_t* fmas, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -359,18 +359,23 @@ def window_ties(model, flux_of, margin: float = 1e-9) -> List[Tuple[int, int, in
     """(slice index, detector, j, k, axis) of every stamp whose mapped centre lies within
     `margin` px of a half-integer in x (axis 0) or y (axis 1): where the window rule may round
     either way."""
+    from concurrent.futures import ThreadPoolExecutor
+
     m = _Marshalled(model, flux_of)
-    out = []
-    for i, s in enumerate(model.slices):
+    L = lib()
+
+    def one(i):  # ctypes releases the GIL during the call, so slices scan in parallel
         cap = 64
         while True:
             buf = (C.c_int * (3 * cap))()
-            n = lib().oracle_window_ties(C.byref(m.arr[i]), margin, cap, buf)
+            n = L.oracle_window_ties(C.byref(m.arr[i]), margin, cap, buf)
             if n <= cap:
-                break
+                return [(i, model.slices[i].detector, buf[3 * t], buf[3 * t + 1], buf[3 * t + 2]) for t in range(n)]
             cap = n
-        out += [(i, s.detector, buf[3 * t], buf[3 * t + 1], buf[3 * t + 2]) for t in range(n)]
-    return out
+
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        parts = list(ex.map(one, range(len(model.slices))))
+    return [t for p in parts for t in p]
 
 
 def W_OpticalModel_one(s):

@@ -139,6 +139,7 @@ _SIGS = {
     "e2e_kernel_times": ([C.c_void_p, C.POINTER(C.c_char_p), C.POINTER(C.c_float), C.c_int32,
                           C.POINTER(C.c_int32)], C.c_int),
     "e2e_eval_tail": ([C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
+    "e2e_fma_probe": ([C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_int64), C.c_void_p], C.c_int),
     "e2e_render_static": ([C.c_void_p, C.c_uint64, C.c_int32, C.POINTER(C.c_uint64), C.c_int32,
                            C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.c_void_p], C.c_int),
     "e2e_render_adjoint": ([C.c_void_p, C.c_uint64, C.c_int32, C.POINTER(C.c_uint64), C.c_int32,
@@ -473,6 +474,16 @@ def e2e_eval_tail(u_dev_ptr: int, n: int, out_dev_ptr: int, stream=None) -> None
                                       C.c_void_p(_stream_handle(stream)))
     if rc != E2E_OK:
         raise E2EError(rc, "e2e_eval_tail failed")
+
+
+def e2e_fma_probe(fp64: bool, blocks: int, iters: int, sink_dev_ptr: int, stream=None) -> int:
+    """Launch the FMA-rate probe (blocks x 256 threads x 8 chains x iters FMAs); returns the FMA count."""
+    n = C.c_int64()
+    rc = load_library().e2e_fma_probe(1 if fp64 else 0, blocks, iters, C.c_void_p(sink_dev_ptr), C.byref(n),
+                                      C.c_void_p(_stream_handle(stream)))
+    if rc != E2E_OK:
+        raise E2EError(rc, "e2e_fma_probe failed")
+    return n.value
 
 
 def e2e_model_plan(ctx: int, model_id: int) -> Dict[str, int]:

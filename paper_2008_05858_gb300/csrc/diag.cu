@@ -1,5 +1,7 @@
-// Diagnostic entry point: evaluate the renderer's FP32 Gaussian-tail function on given
-// arguments, so tests can check it against CUDA's FP64 erfc.
+// Diagnostic entry points: evaluate the renderer's FP32 Gaussian-tail function on given
+// arguments, so tests can check it against CUDA's FP64 erfc; and a fused multiply-add probe
+// that measures the FP32 and FP64 FMA rates the roofline of the ALU-bound kernels is quoted
+// against.
 #include "../../include/e2e_render.h"
 #include "phi32.cuh"
 
@@ -14,7 +16,38 @@ __global__ void k_eval_tail(const double* __restrict__ u, int64_t n, float* __re
   }
 }
 
+// Each thread runs kChains independent FMA chains of `iters` steps (no chain waits on another,
+// so the pipe, not latency, sets the rate) and stores their sum, which keeps them live.
+constexpr int kChains = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_probe(int iters, T a, T b, T* __restrict__ sink) {
+  T v[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) v[c] = (T)(threadIdx.x + c);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) v[c] = v[c] * a + b;  // contracted to one FMA
+  }
+  T s = 0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += v[c];
+  sink[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace
+
+extern "C" int e2e_fma_probe(int32_t fp64, int32_t blocks, int32_t iters, void* sink_dev, int64_t* fmas,
+                             void* stream) {
+  if (blocks < 1 || iters < 1 || !sink_dev || !fmas) return E2E_EINVAL;
+  const cudaStream_t st = (cudaStream_t)stream;
+  if (fp64)
+    k_fma_probe<double><<<blocks, 256, 0, st>>>(iters, 0.999999, 1e-7, static_cast<double*>(sink_dev));
+  else
+    k_fma_probe<float><<<blocks, 256, 0, st>>>(iters, 0.999999f, 1e-7f, static_cast<float*>(sink_dev));
+  *fmas = (int64_t)blocks * 256 * iters * kChains;
+  return cudaGetLastError() == cudaSuccess ? E2E_OK : E2E_ECUDA;
+}
 
 extern "C" int e2e_eval_tail(const double* u_dev, int64_t n, float* out_dev, void* stream) {
   if (n < 0 || (n > 0 && (!u_dev || !out_dev))) return E2E_EINVAL;
