@@ -216,24 +216,24 @@ def frame_windows_oracle(w: W.Workload, frame: np.ndarray, n_win: int = 6, size:
     return base, acc
 
 
-def cut_model(w: W.Workload, n_slices: int, n_lambda: int, model=None):
-    """The first n_slices order-slices of w (or of `model`), each cut to its first n_lambda
-    wavelength samples (the range shortened with them, so the samples keep their spacing),
-    and a flux lookup for them."""
+def cut_model(w: W.Workload, n_slices: int, n_slit: int, model=None):
+    """The first n_slices order-slices of w (or of `model`), each with its wavelength grid and
+    geometry kept but only n_slit slit points (bin centres of [-1, 1], uniform weights of the
+    same total), and a flux lookup for them."""
     import dataclasses
 
     m = w.model if model is None else model
     cut, flux = [], {}
     for s in m.slices[:n_slices]:
-        dl = (s.lambda_hi - s.lambda_lo) / s.n_lambda
-        k = min(n_lambda, s.n_lambda)
-        c = dataclasses.replace(s.copy(), n_lambda=k, lambda_hi=s.lambda_lo + k * dl)
-        flux[id(c)] = w.flux_for(s)[:k]
+        k = min(n_slit, s.n_slit)
+        tot = float(np.sum(s.slit_weights))
+        c = dataclasses.replace(s.copy(), n_slit=k, slit_weights=np.full(k, tot / k))
+        flux[id(c)] = w.flux_for(s)
         cut.append(c)
     return W.OpticalModel(m.det_shape, cut, m.psf), (lambda c: flux[id(c)])
 
 
-def cut_sample_oracle(B, dev, w: W.Workload, model, n_slices: int, n_lambda: int, precisions=("mixed",)):
+def cut_sample_oracle(B, dev, w: W.Workload, model, n_slices: int, n_slit: int, precisions=("mixed",)):
     """CPU-baseline leg on a cut sample (cut_model): the oracle renders it (timed as the
     baseline) and the GPU renders of the same sample are compared with it, per precision.
     Comparisons run on the rows and columns the sample touches (16-px aligned, so the
@@ -243,7 +243,7 @@ def cut_sample_oracle(B, dev, w: W.Workload, model, n_slices: int, n_lambda: int
     import oracle
     from tests.framecompare import compare, tie_boxes
 
-    sub, flux_of = cut_model(w, n_slices, n_lambda, model)
+    sub, flux_of = cut_model(w, n_slices, n_slit, model)
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
     ref = oracle.render(sub, flux_of, n_threads=cores)
@@ -276,8 +276,8 @@ def cut_sample_oracle(B, dev, w: W.Workload, model, n_slices: int, n_lambda: int
         r.close()
     stamps = sub.n_stamps
     base = {"value": stamps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {len(sub.slices)} of {len(model.slices)} order-slices, each cut to its first {n_lambda} "
-                      f"wavelength samples ({stamps} stamps), FP64, {dt:.1f} s"}
+            "sample": f"first {len(sub.slices)} of {len(model.slices)} order-slices, each with its full wavelength grid "
+                      f"and {n_slit} slit points ({stamps} stamps), FP64, {dt:.1f} s"}
     return base, acc
 
 
@@ -671,7 +671,7 @@ def table_run(B, dev, w, flush, reps=3, cpu_baseline=False):
     r.close()
     if cpu_baseline:
         tw = W.Workload(w.name, m, w.spectra, "f32", "mixed")
-        out["cpu_baseline"], out["accuracy"] = cut_sample_oracle(B, dev, tw, m, 16, 120, ("mixed", "fp64"))
+        out["cpu_baseline"], out["accuracy"] = cut_sample_oracle(B, dev, tw, m, 16, 4, ("mixed", "fp64"))
     out["workload"] = "full-detector frame (9216^2, 85 orders x 2 x 2, 6000 x 64, K=11) with tabulated PSF maps"
     return out
 
@@ -821,7 +821,7 @@ def elliptical_run(B, dev, rank=0, world=1, reps=3, cpu_baseline=False):
     out["speedup_mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
     if cpu_baseline:
         w3 = W.config3(orders_per_detector=1)
-        out["cpu_baseline"], out["accuracy"] = cut_sample_oracle(B, dev, w3, w3.model, 16, 120, ("mixed", "fp64"))
+        out["cpu_baseline"], out["accuracy"] = cut_sample_oracle(B, dev, w3, w3.model, 8, 4, ("mixed", "fp64"))
     out["workload"] = "4 x 9216^2 FP32, 30 orders/detector x 4 fibers x 2 slices, 8000 x 128 samples, deg 5, " \
                       "K=13 rotated elliptical PSF (|theta| <= 10 deg); fp64 leg on 1 order/detector"
     return out

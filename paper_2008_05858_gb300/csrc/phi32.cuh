@@ -97,4 +97,53 @@ __device__ __forceinline__ void edge_arg(float e, float f, float gh, float gl, f
   wl = fmaf(dh, gh, -wh) + fmaf(dh, gl, dl * gh);
 }
 
+// ---- the same functions on two arguments at once (packed FP32x2 arithmetic, sm_100+: one
+// issue slot for two lanes' worth of FMAs); per component the arithmetic is the scalar
+// functions' own, operation by operation, so the results are the same bits.
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// tail2 of (wh.x, wl.x) and (wh.y, wl.y).
+__device__ __forceinline__ float2 tail2x2(float2 wh, float2 wl) {
+  const float2 p = __fmul2_rn(wh, wh);
+  float2 e = __ffma2_rn(wh, wh, f2(-p.x, -p.y));
+  e = __ffma2_rn(__fadd2_rn(wh, wh), wl, e);
+  const float2 ex = __fmul2_rn(f2(ex2_approx(-p.x), ex2_approx(-p.y)),
+                               __ffma2_rn(e, f2(-0.693147181f, -0.693147181f), f2(1.f, 1.f)));
+  const float2 x = f2(fminf(fabsf(wh.x), 40.f), fminf(fabsf(wh.y), 40.f));
+  float2 P = f2(kTailP4, kTailP4);
+  P = __ffma2_rn(P, x, f2(kTailP3, kTailP3));
+  P = __ffma2_rn(P, x, f2(kTailP2, kTailP2));
+  P = __ffma2_rn(P, x, f2(kTailP1, kTailP1));
+  P = __ffma2_rn(P, x, f2(kTailP0, kTailP0));
+  float2 Q = f2(kTailQ5, kTailQ5);
+  Q = __ffma2_rn(Q, x, f2(kTailQ4, kTailQ4));
+  Q = __ffma2_rn(Q, x, f2(kTailQ3, kTailQ3));
+  Q = __ffma2_rn(Q, x, f2(kTailQ2, kTailQ2));
+  Q = __ffma2_rn(Q, x, f2(kTailQ1, kTailQ1));
+  Q = __ffma2_rn(Q, x, f2(kTailQ0, kTailQ0));
+  return __fmul2_rn(__fmul2_rn(ex, P), f2(rcp_approx(Q.x), rcp_approx(Q.y)));
+}
+
+// erf_small of w.x and w.y.
+__device__ __forceinline__ float2 erf_small2(float2 w) {
+  const float2 a = f2(fabsf(w.x), fabsf(w.y));
+  const float2 z = __fmul2_rn(a, a);
+  float2 S = f2(kErfS4, kErfS4);
+  S = __ffma2_rn(S, z, f2(kErfS3, kErfS3));
+  S = __ffma2_rn(S, z, f2(kErfS2, kErfS2));
+  S = __ffma2_rn(S, z, f2(kErfS1, kErfS1));
+  S = __ffma2_rn(S, z, f2(kErfS0, kErfS0));
+  return __fmul2_rn(a, S);
+}
+
+// edge_arg of the half-integers e.x and e.y against the same offset f and factor (gh, gl).
+__device__ __forceinline__ void edge_arg2(float2 e, float f, float gh, float gl, float2& wh, float2& wl) {
+  const float2 ff = f2(f, f), g = f2(gh, gh);
+  const float2 dh = __fadd2_rn(e, f2(-f, -f));
+  const float2 dl = __fadd2_rn(__fadd2_rn(e, f2(-dh.x, -dh.y)), f2(-ff.x, -ff.y));
+  wh = __fmul2_rn(dh, g);
+  wl = __fadd2_rn(__ffma2_rn(dh, g, f2(-wh.x, -wh.y)), __ffma2_rn(dh, f2(gl, gl), __fmul2_rn(dl, g)));
+}
+
 }  // namespace e2e

@@ -203,13 +203,22 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
       // edge, and erf F = erf(|w|) at the four edges around the centre pixel H.  Twice the
       // pixel integrals are differences of left tails (m < H-1), of right tails (m > H+1),
       // and sums / differences of erf for the centre pixel and its two neighbours.
+      // edges in pairs (m, m + 1): K + 1 is even, and the four centre edges H-1..H+2 are two
+      // pairs, since H - 1 = K/2 - 1 is even for K = 4n + 3 and odd for K = 4n + 1 (then the
+      // pairs are (H-2, H-1), (H, H+1), (H+2, H+3) and the extra erf values are not used)
       float E[K + 1], F[K + 1];
 #pragma unroll
-      for (int m = 0; m <= K; ++m) {
-        float wh, wl;
-        edge_arg((float)(m - H) - 0.5f, f, gh, gl, wh, wl);
-        E[m] = tail2(wh, wl);
-        if (m >= H - 1 && m <= H + 2) F[m] = fabsf(wh) < kErfMaxArg ? erf_small(wh) : 1.f - E[m];
+      for (int m = 0; m <= K; m += 2) {
+        float2 wh, wl;
+        edge_arg2(f2((float)(m - H) - 0.5f, (float)(m + 1 - H) - 0.5f), f, gh, gl, wh, wl);
+        const float2 t = tail2x2(wh, wl);
+        E[m] = t.x;
+        E[m + 1] = t.y;
+        if (m + 1 >= H - 1 && m <= H + 2) {
+          const float2 fe = erf_small2(wh);
+          F[m] = fabsf(wh.x) < kErfMaxArg ? fe.x : 1.f - E[m];
+          F[m + 1] = fabsf(wh.y) < kErfMaxArg ? fe.y : 1.f - E[m + 1];
+        }
       }
       float win[K];
 #pragma unroll
@@ -253,9 +262,16 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
       for (int i = 0; i < RYH; ++i)
         if (RYH + i < RY) ay[i] = par ? prof[RYH + i] : ay[i];  // lane 1: its own rows RYH..RY-1
 #pragma unroll
-      for (int r = 0; r < RYH; ++r)
+      for (int r = 0; r < RYH; ++r) {
+        const float2 yy = f2(ay[r], ay[r]);
 #pragma unroll
-        for (int c = 0; c < RX; ++c) acc[r][c] = fmaf(ay[r], ax[c], acc[r][c]);
+        for (int c = 0; c + 1 < RX; c += 2) {
+          const float2 v = __ffma2_rn(yy, f2(ax[c], ax[c + 1]), f2(acc[r][c], acc[r][c + 1]));
+          acc[r][c] = v.x;
+          acc[r][c + 1] = v.y;
+        }
+        if constexpr (RX % 2 == 1) acc[r][RX - 1] = fmaf(ay[r], ax[RX - 1], acc[r][RX - 1]);
+      }
     }
     __syncwarp();  // the staging is reused by the next task
     // flush this lane's rows of the run tile as exact fixed-point increments
