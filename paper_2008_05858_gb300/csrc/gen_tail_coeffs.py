@@ -12,7 +12,7 @@ the minimax relative error, on Chebyshev points.  Reference values: scipy.specia
 Near the window centre the kernels use erf itself, as an odd polynomial in w fitted the
 same way (relative error, Lawson-reweighted least squares on Chebyshev points):
 
-    erf(w / sqrt(log2 e))  ~=  w * S4(w^2),   |w| <= 0.7
+    erf(w / sqrt(log2 e))  ~=  w * S5(w^2),   |w| <= 1.0
 
 Run:  python gen_tail_coeffs.py   (needs numpy and scipy; only at build-authoring time).
 """
@@ -50,7 +50,7 @@ def fit(m=M, n=N, amax=A * KAPPA, iters=120, npts=6000):
     return best
 
 
-ERF_W, ERF_TERMS = 0.7, 5
+ERF_W, ERF_TERMS = 1.0, 6
 
 
 def fit_erf(wmax=ERF_W, nt=ERF_TERMS, iters=80, npts=4000):

@@ -60,4 +60,14 @@ __device__ __forceinline__ void box_deposit(int* hi, unsigned* lo, float val, fl
   atomicAdd(lo, __float2uint_rn(lf));
 }
 
+// box_deposit's fixed-point words of two values at once: the same operations on each
+// component (packed FP32x2 for the multiplies and the FMA), so the same words.
+__device__ __forceinline__ void fixed_split2(float2 val, float sc, float sc_hi, int2& hi, uint2& lo) {
+  const float2 t = __fmul2_rn(val, make_float2(sc_hi, sc_hi));
+  const float2 hf = make_float2(floorf(t.x), floorf(t.y));
+  const float2 lf = __ffma2_rn(hf, make_float2(-4194304.f, -4194304.f), __fmul2_rn(val, make_float2(sc, sc)));
+  hi = make_int2(__float2int_rz(hf.x), __float2int_rz(hf.y));
+  lo = make_uint2(__float2uint_rn(lf.x), __float2uint_rn(lf.y));
+}
+
 }  // namespace e2e

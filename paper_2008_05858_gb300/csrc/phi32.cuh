@@ -73,13 +73,14 @@ __device__ __forceinline__ float tail2_dens(float wh, float wl, float& dens) {
   return (ex * P) * rcp_approx(Q);
 }
 
-// erf(|w| / sqrt(log2 e)) for |w| <= kErfMaxArg (odd polynomial, ~1.7 ulp): near the window
+// erf(|w| / sqrt(log2 e)) for |w| <= kErfMaxArg (odd polynomial, fit error 5e-9): near the window
 // centre the pixel integrals are sums and differences of erf, which do not cancel there the
 // way differences of erfc values close to 1 do.
 __device__ __forceinline__ float erf_small(float w) {
   const float a = fabsf(w);
   const float z = a * a;
-  float S = kErfS4;
+  float S = kErfS5;
+  S = fmaf(S, z, kErfS4);
   S = fmaf(S, z, kErfS3);
   S = fmaf(S, z, kErfS2);
   S = fmaf(S, z, kErfS1);
@@ -129,7 +130,8 @@ __device__ __forceinline__ float2 tail2x2(float2 wh, float2 wl) {
 __device__ __forceinline__ float2 erf_small2(float2 w) {
   const float2 a = f2(fabsf(w.x), fabsf(w.y));
   const float2 z = __fmul2_rn(a, a);
-  float2 S = f2(kErfS4, kErfS4);
+  float2 S = f2(kErfS5, kErfS5);
+  S = __ffma2_rn(S, z, f2(kErfS4, kErfS4));
   S = __ffma2_rn(S, z, f2(kErfS3, kErfS3));
   S = __ffma2_rn(S, z, f2(kErfS2, kErfS2));
   S = __ffma2_rn(S, z, f2(kErfS1, kErfS1));

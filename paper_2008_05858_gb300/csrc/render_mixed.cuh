@@ -199,26 +199,50 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
       const float w = on ? fmaf(wj.x, uk.x, fmaf(wj.x, uk.y, wj.y * uk.x)) : 0.f;
       const float mult = par ? (on ? 1.f : 0.f) : w;  // the weight rides on the x profile
       // Profile of the stamp's own K-pixel window, window pixel m spanning edges m and m+1
-      // at offsets (m - H -+ 1/2) - f from the stamp centre: tails E = erfc(|w|) at every
-      // edge, and erf F = erf(|w|) at the four edges around the centre pixel H.  Twice the
-      // pixel integrals are differences of left tails (m < H-1), of right tails (m > H+1),
-      // and sums / differences of erf for the centre pixel and its two neighbours.
-      // edges in pairs (m, m + 1): K + 1 is even, and the four centre edges H-1..H+2 are two
-      // pairs, since H - 1 = K/2 - 1 is even for K = 4n + 3 and odd for K = 4n + 1 (then the
-      // pairs are (H-2, H-1), (H, H+1), (H+2, H+3) and the extra erf values are not used)
-      float E[K + 1], F[K + 1];
+      // at offsets (m - H -+ 1/2) - f from the stamp centre: tails E = erfc(|w|) at the edges
+      // off the centre pixel, and erf F = erf(|w|) at the four edges around the centre pixel H.
+      // Twice the pixel integrals are differences of left tails (m < H-1), of right tails
+      // (m > H+1), and sums / differences of erf for the centre pixel and its two neighbours.
+      // The tails of the centre pixel's own edges H and H+1 enter only where erf is out of its
+      // range (|w| >= kErfMaxArg, a PSF narrower than ~0.85 px), so they are evaluated only
+      // when some lane of the warp needs them.  Edges are taken in pairs (packed arithmetic).
+      float E[K + 1], F[K + 1], Wd[K + 1];
+      constexpr int NT = K - 1;  // edges 0..H-1 and H+2..K
 #pragma unroll
-      for (int m = 0; m <= K; m += 2) {
+      for (int i = 0; i < NT; i += 2) {
+        const int m0 = i < H ? i : i + 2, m1 = i + 1 < H ? i + 1 : i + 3;
         float2 wh, wl;
-        edge_arg2(f2((float)(m - H) - 0.5f, (float)(m + 1 - H) - 0.5f), f, gh, gl, wh, wl);
+        edge_arg2(f2((float)(m0 - H) - 0.5f, (float)(m1 - H) - 0.5f), f, gh, gl, wh, wl);
         const float2 t = tail2x2(wh, wl);
-        E[m] = t.x;
-        E[m + 1] = t.y;
-        if (m + 1 >= H - 1 && m <= H + 2) {
-          const float2 fe = erf_small2(wh);
-          F[m] = fabsf(wh.x) < kErfMaxArg ? fe.x : 1.f - E[m];
-          F[m + 1] = fabsf(wh.y) < kErfMaxArg ? fe.y : 1.f - E[m + 1];
+        E[m0] = t.x;
+        E[m1] = t.y;
+        Wd[m0] = wh.x;
+        Wd[m1] = wh.y;
+      }
+      {
+        float2 wc, wlc;  // edges H and H+1
+        edge_arg2(f2(-0.5f, 0.5f), f, gh, gl, wc, wlc);
+        Wd[H] = wc.x;
+        Wd[H + 1] = wc.y;
+        const bool far = fabsf(wc.x) >= kErfMaxArg || fabsf(wc.y) >= kErfMaxArg;
+        if (__any_sync(0xffffffffu, far)) {
+          const float2 t = tail2x2(wc, wlc);
+          E[H] = t.x;
+          E[H + 1] = t.y;
+        } else {
+          E[H] = E[H + 1] = 0.f;  // not read: every F below comes from the polynomial
         }
+      }
+      if constexpr (K >= 3) {
+        const float2 fa = erf_small2(f2(Wd[H - 1], Wd[H])), fb = erf_small2(f2(Wd[H + 1], Wd[H + 2]));
+        F[H - 1] = fabsf(Wd[H - 1]) < kErfMaxArg ? fa.x : 1.f - E[H - 1];
+        F[H] = fabsf(Wd[H]) < kErfMaxArg ? fa.y : 1.f - E[H];
+        F[H + 1] = fabsf(Wd[H + 1]) < kErfMaxArg ? fb.x : 1.f - E[H + 1];
+        F[H + 2] = fabsf(Wd[H + 2]) < kErfMaxArg ? fb.y : 1.f - E[H + 2];
+      } else {
+        const float2 fa = erf_small2(f2(Wd[0], Wd[1]));
+        F[0] = fabsf(Wd[0]) < kErfMaxArg ? fa.x : 1.f - E[0];
+        F[1] = fabsf(Wd[1]) < kErfMaxArg ? fa.y : 1.f - E[1];
       }
       float win[K];
 #pragma unroll
@@ -229,8 +253,15 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
         else if (m == H) v = F[m] + F[m + 1];
         else if (m == H + 1) v = F[m + 1] - F[m];
         else v = E[m] - E[m + 1];
-        win[m] = mult * v;
+        win[m] = v;
       }
+#pragma unroll
+      for (int m = 0; m + 1 < K; m += 2) {
+        const float2 p2 = __fmul2_rn(f2(mult, mult), f2(win[m], win[m + 1]));
+        win[m] = p2.x;
+        win[m + 1] = p2.y;
+      }
+      win[K - 1] *= mult;
       // place the window at its offset o (0..D) in the tile, prof[c] = win[c - o], as a shift
       // by o & 1 and then by o & 2: two selects per tile pixel
       float prof[R];
@@ -296,14 +327,22 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
         int* rowh = boxh + gy * it.bw + gx0;
         unsigned* rowl = boxl + gy * it.bw + gx0;
 #pragma unroll
-        for (int c = 0; c < RX; ++c) {
-          if constexpr (CHECK) {
-            const int X = it.bx0 + gx0 + c;
-            if (!inside && (gx0 + c < 0 || gx0 + c >= it.bw) && acc[r][c] != 0.f && X >= 0 && X < S.W)
-              atomicAdd(a.err, 1);
+        for (int c = 0; c < RX; c += 2) {
+          int2 hw;
+          uint2 lw;
+          fixed_split2(make_float2(acc[r][c], c + 1 < RX ? acc[r][c + 1] : 0.f), sc, sc_hi, hw, lw);
+#pragma unroll
+          for (int h = 0; h < 2 && c + h < RX; ++h) {
+            const int cc = c + h;
+            if constexpr (CHECK) {
+              const int X = it.bx0 + gx0 + cc;
+              if (!inside && (gx0 + cc < 0 || gx0 + cc >= it.bw) && acc[r][cc] != 0.f && X >= 0 && X < S.W)
+                atomicAdd(a.err, 1);
+            }
+            if (!inside && (gx0 + cc < 0 || gx0 + cc >= it.bw)) continue;
+            atomicAdd(rowh + cc, h ? hw.y : hw.x);
+            atomicAdd(rowl + cc, h ? lw.y : lw.x);
           }
-          if (!inside && (gx0 + c < 0 || gx0 + c >= it.bw)) continue;
-          box_deposit(rowh + c, rowl + c, acc[r][c], sc, sc_hi);
         }
       }
     }

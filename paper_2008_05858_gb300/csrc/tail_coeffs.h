@@ -16,11 +16,12 @@ constexpr float kTailQ5 = 2.032556214e-02f;
 constexpr float kTailMaxArg = 7.8073f;  // largest w the fit covers
 constexpr float kSqrtLog2e = 1.201122409f;
 constexpr double kSqrtLog2eD = 1.2011224087864498;
-// erf(w / sqrt(log2 e)) ~= w * S(w^2) for |w| <= 0.70, 5 terms, max relative fit error 6.12e-09
-constexpr float kErfS0 = 9.394372730e-01f;
-constexpr float kErfS1 = -2.170555199e-01f;
-constexpr float kErfS2 = 4.512608812e-02f;
-constexpr float kErfS3 = -7.394556502e-03f;
-constexpr float kErfS4 = 8.743762265e-04f;
-constexpr float kErfMaxArg = 0.70f;
+// erf(w / sqrt(log2 e)) ~= w * S(w^2) for |w| <= 1.00, 6 terms, max relative fit error 4.78e-09
+constexpr float kErfS0 = 9.394372742e-01f;
+constexpr float kErfS1 = -2.170557832e-01f;
+constexpr float kErfS2 = 4.513187456e-02f;
+constexpr float kErfS3 = -7.433231989e-03f;
+constexpr float kErfS4 = 9.731278067e-04f;
+constexpr float kErfS5 = -8.515646385e-05f;
+constexpr float kErfMaxArg = 1.00f;
 }  // namespace e2e
