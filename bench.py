@@ -58,20 +58,22 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# FP32 FLOP of one separable stamp of window K, counted algorithmically (an FMA is 2 FLOP, an
-# SFU operation 1): 2(K+1) pixel-edge tail evaluations at 28 FLOP each (the double-float edge
-# argument: 6; its exact square: 3; the exponential: 1 + 2; the (4,5) rational: 18 - 2 = 16,
-# with its reciprocal), 2K edge differences, and the K^2 products with the weight folded in,
-# accumulated by FMA (2 K^2).
-def fp32_flop_per_stamp(K: int) -> float:
-    return 2 * (K + 1) * 28 + 2 * K + 2 * K * K
+# FP32 FLOP of one separable stamp of window K and degree d, counted algorithmically (an FMA
+# is 2 FLOP, an SFU operation 1): 2(K+1) pixel-edge tail evaluations at 28 FLOP each (the
+# double-float edge argument: 6; its exact square: 3; the exponential: 1 + 2; the (4,5)
+# rational: 18 - 2 = 16, with its reciprocal), 2K edge differences, the K^2 products with the
+# weight folded in, accumulated by FMA (2 K^2), and the mapping's Horner in s of both
+# coordinates (2d FMAs; evaluated in double-float FP32 arithmetic, counted once).
+def fp32_flop_per_stamp(K: int, d: int = 5) -> float:
+    return 2 * (K + 1) * 28 + 2 * K + 2 * K * K + 4 * d
 
 
-# FP64 FMAs of one stamp: Horner in s of both coordinates (2 d), plus the per-sample
-# Horner in lambda (2 n_c) spread over the n_slit stamps of the sample.
+# FP64 FMAs of one stamp: the per-sample Horner in lambda of the coefficients of s (2 n_c per
+# wavelength sample, spread over the n_slit stamps of the sample); the rest of the mapping runs
+# in double-float FP32 arithmetic.
 def fp64_fma_per_stamp(d: int, n_slit: int) -> float:
     nc = (d + 1) * (d + 2) / 2
-    return 2 * d + 2 * nc / n_slit
+    return 2 * nc / n_slit
 
 
 class ClockSampler:
@@ -451,7 +453,7 @@ def run_gpu(args):
     fp32_peak = n_sm * 128 * 2 * mhz * 1e6
     fp64_peak = n_sm * dfma_per_clk_sm * 2 * mhz * 1e6
     probe = pipe_rates(B, dev)
-    a32 = fp32_flop_per_stamp(K) * stamps_rank / (kr * 1e-3)
+    a32 = fp32_flop_per_stamp(K, d) * stamps_rank / (kr * 1e-3)
     a64 = fp64_fma_per_stamp(d, ns) * 2 * stamps_rank / (kr * 1e-3)
     traffic = _load_traffic()
     roof32 = {"bound": "alu", "achieved": a32 / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",

@@ -655,7 +655,7 @@ int plan_model(Model* m) {
       P.nk_max = std::max(P.nk_max, it.nk);
     }
     P.smem = m->psf == E2E_PSF_TABLE ? table_smem_bytes(P.max_area, P.nk_max, P.max_deg + 1)
-             : ellip ? ellip_smem_bytes(P.max_area, P.nk_max, P.max_deg + 1)
+             : ellip ? ellip_smem_bytes(P.max_area, P.nk_max, P.max_deg + 1, m->Ks.empty() ? 15 : m->Ks.front())
                      : mixed_smem_bytes(P.max_area, P.JB, P.nk_max, P.B, P.max_deg + 1);
     if ((int)P.smem + kStaticSmemReserve <= optin) break;
     if (jb_cap == 1)
@@ -1627,7 +1627,9 @@ int e2e_render_adjoint(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const ui
   E2E_CK(cudaMemcpyAsync(d_table, table.data(), table.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
   E2E_CK(cudaMemcpyAsync(d_pitch, pitch.data(), pitch.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
   E2E_CK(cudaMemcpyAsync(d_dldi, dldi, m->n_det * sizeof(void*), cudaMemcpyHostToDevice, st));
-  const size_t smem = adjoint_smem_bytes(P.max_area, P.max_deg, P.nk_max);
+  int nj_max = 1;
+  for (const Item& it : P.items) nj_max = std::max(nj_max, it.nj);
+  const size_t smem = adjoint_smem_bytes(P.max_area, P.max_deg, P.nk_max, nj_max);
   int max_tasks = 1;  // warp tasks of the largest item: 32-sample blocks x runs
   for (const Item& it : P.items) max_tasks = std::max(max_tasks, ((it.nj + 31) / 32) * ((it.nk + P.B - 1) / P.B));
   const int parts = adjoint_parts(max_tasks);
@@ -2129,9 +2131,11 @@ int e2e_add_noise(e2e_ctx* ctx, uint64_t model_id, const e2e_noise_params* p, in
       for (int d = 0; d < m->n_det; ++d) {
         const size_t npx = (size_t)m->H[d] * m->W[d];
         cudaError_t e = cudaMalloc((void**)&pat.R[d], npx * sizeof(double));
-        if (e == cudaSuccess) e = cudaMalloc((void**)&pat.R32[d], npx * sizeof(float));
+        // FP32 words of R: the high words, then the low words (R as double-float pairs)
+        if (e == cudaSuccess) e = cudaMalloc((void**)&pat.R32[d], 2 * npx * sizeof(float));
         if (e == cudaSuccess)
-          e = launch_prnu_map(pat.R[d], pat.R32[d], m->H[d], m->W[d], d, p->pattern_seed, p->prnu, st);
+          e = launch_prnu_map(pat.R[d], pat.R32[d], pat.R32[d] + npx, m->H[d], m->W[d], d, p->pattern_seed, p->prnu,
+                              st);
         if (e != cudaSuccess) {
           for (double* q : pat.R) cudaFree(q);
           for (float* q : pat.R32) cudaFree(q);
@@ -2143,12 +2147,32 @@ int e2e_add_noise(e2e_ctx* ctx, uint64_t model_id, const e2e_noise_params* p, in
     R = pat.R;
     R32 = pat.R32;
   }
+  // photon noise into FP32 electrons or ADU: the two-pass form (FP32 first pass, the pairs too
+  // close to call redone in FP64 from a compacted list); FP64 electrons and expected values
+  // (no shot noise) keep the one-pass kernel, whose FP64 paths are the output's own arithmetic
+  const bool two_pass = p->poisson && dst_dtype != E2E_F64;
+  Scratch sc{{}, st};
+  unsigned* list = nullptr;
+  unsigned* n_list = nullptr;
+  if (two_pass) {
+    int64_t most = 0;
+    for (int d = 0; d < m->n_det; ++d) most = std::max(most, (int64_t)m->H[d] * ((m->W[d] + 1) / 2));
+    E2E_CK(sc.get((void**)&n_list, sizeof(unsigned)));
+    E2E_CK(sc.get((void**)&list, std::max<int64_t>(1, most) * sizeof(unsigned)));
+  }
   for (int d = 0; d < m->n_det; ++d) {
     const int64_t sp = src_pitch ? src_pitch[d] : m->W[d], dp = dst_pitch ? dst_pitch[d] : m->W[d];
     KernelTimer kt(ctx, st, "noise");
-    E2E_CK(launch_noise(p->seed, p->pattern_seed, p->dark_e, p->prnu, p->ron_e, p->xtalk, p->gain, p->bias,
-                        p->saturation, p->poisson, src_dtype, src[d], sp, R[d], R32[d], dst_dtype, dst[d], dp,
-                        m->H[d], m->W[d], d, st));
+    if (two_pass) {
+      const float* lo = R32[d] ? R32[d] + (size_t)m->H[d] * m->W[d] : nullptr;
+      E2E_CK(launch_noise_two_pass(p->seed, p->pattern_seed, p->dark_e, p->prnu, p->ron_e, p->xtalk, p->gain,
+                                   p->bias, p->saturation, src_dtype, src[d], sp, R[d], R32[d], lo, dst_dtype, dst[d],
+                                   dp, m->H[d], m->W[d], d, list, n_list, st));
+    } else {
+      E2E_CK(launch_noise(p->seed, p->pattern_seed, p->dark_e, p->prnu, p->ron_e, p->xtalk, p->gain, p->bias,
+                          p->saturation, p->poisson, src_dtype, src[d], sp, R[d], R32[d], dst_dtype, dst[d], dp,
+                          m->H[d], m->W[d], d, st));
+    }
   }
   return E2E_OK;
 }

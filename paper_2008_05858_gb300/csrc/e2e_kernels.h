@@ -46,7 +46,7 @@ cudaError_t launch_render_mixed(int K, int DX, int DY, const DevSlice* slices, c
 cudaError_t launch_merge(const Tile* tiles, int n_tiles, const int32_t* lists, const Item* items, const float2* store,
                          void* const* dst, int dtype, const int64_t* pitch, const int* dims, cudaStream_t st);
 
-size_t ellip_smem_bytes(int area, int nk_max, int nd);
+size_t ellip_smem_bytes(int area, int nk_max, int nd, int k_min);
 cudaError_t launch_render_ellip(int K, const DevSlice* slices, const double* const* flux_tab, const double* u_all,
                                 const Item* items, int n_items, float2* store, int nk_max, int max_deg, size_t smem,
                                 cudaStream_t st, int* err = nullptr);
@@ -54,8 +54,13 @@ cudaError_t launch_render_fp64_ellip(int K, int n_slices, int64_t max_stamps, co
                                      const double* const* flux_tab, const double* u_all, double* const* acc,
                                      const int64_t* pitch, cudaStream_t st);
 
-cudaError_t launch_prnu_map(double* R, float* R32, int H, int W, int det, uint64_t pattern_seed, double prnu,
-                            cudaStream_t st);
+cudaError_t launch_prnu_map(double* R, float* R32, float* R32lo, int H, int W, int det, uint64_t pattern_seed,
+                            double prnu, cudaStream_t st);
+cudaError_t launch_noise_two_pass(uint64_t seed, uint64_t pattern_seed, double dark, double prnu, double ron,
+                                  double xtalk, double gain, double bias, int saturation, int src_dtype,
+                                  const void* src, int64_t src_pitch, const double* R, const float* R32,
+                                  const float* R32lo, int dst_dtype, void* dst, int64_t dst_pitch, int H, int W,
+                                  int det, unsigned* list, unsigned* n_list, cudaStream_t st);
 cudaError_t launch_noise(uint64_t seed, uint64_t pattern_seed, double dark, double prnu, double ron, double xtalk,
                          double gain, double bias, int saturation, int poisson, int src_dtype, const void* src,
                          int64_t src_pitch, const double* R, const float* R32, int dst_dtype, void* dst,
@@ -89,7 +94,7 @@ cudaError_t launch_photons(const DevSlice* slices, int n_slices, const double* u
                            const float* cf32, const int4* anchors, const int* bin_slice, const int64_t* guide,
                            cudaStream_t st);
 
-size_t adjoint_smem_bytes(int max_area, int max_deg, int nk_max);
+size_t adjoint_smem_bytes(int max_area, int max_deg, int nk_max, int nj_max);
 int adjoint_parts(int max_tasks);  // CTAs per item sharing its warp tasks
 cudaError_t launch_adjoint(int K, const DevSlice* slices, const double* const* flux_tab, const double* u_all,
                            const Item* items, int n_items, const void* const* dldi, const int64_t* pitch, int dtype,

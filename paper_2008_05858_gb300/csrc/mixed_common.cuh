@@ -60,6 +60,76 @@ __device__ __forceinline__ void box_deposit(int* hi, unsigned* lo, float val, fl
   atomicAdd(lo, __float2uint_rn(lf));
 }
 
+// ---- the stamp mapping of the mixed-precision kernels and their planner, in double-float
+// FP32 arithmetic (x and y together, packed FP32x2): FP64 runs at 1/64 of the FP32 rate on
+// this part, and a double-float (~48 significant bits) keeps the mapped centre within
+// ~1e-10 px at 9216 px.  The planner and every mixed kernel call these same functions, so
+// they agree on every window origin.
+
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// The coefficients P_b(lt) of x and y of one wavelength sample, as (xh, yh, xl, yl).
+__device__ __forceinline__ float4 split_xy(double px, double py) {
+  const float xh = (float)px, yh = (float)py;
+  return make_float4(xh, yh, (float)(px - (double)xh), (float)(py - (double)yh));
+}
+
+// v = h + l (|l| <= ulp(h)/2) split into the window-centre pixel c = floor(v + 1/2) and the
+// offset f = v - c in [-1/2, 1/2), rounded to FP32; |v| >= 2^15 px or not finite: kOffFrame.
+__device__ __forceinline__ void split_coord_df(float h, float l, int& c, float& f) {
+  if (!(fabsf(h) < 32768.f)) {
+    c = kOffFrame;
+    f = 0.f;
+    return;
+  }
+  const int ci = __float2int_rd(h + 0.5f);  // within one of floor(v + 1/2)
+  const float f0 = h - (float)ci;            // exact: |h - ci| <= 1
+  float fr = f0 + l;
+  int cc = ci;
+  if (fr < -0.5f) {
+    cc = ci - 1;
+    fr = (f0 + 1.f) + l;
+  } else if (fr >= 0.5f) {
+    cc = ci + 1;
+    fr = (f0 - 1.f) + l;
+  }
+  c = cc;
+  f = fr;
+}
+
+// Horner in s = (sh, sl) over P[b] = split_xy(P_b of x, P_b of y), b = 0..d: the stamp's x and
+// y as double-floats, each step a double-float product (FMA error terms) and a TwoSum.
+__device__ __forceinline__ void map_xy_df(const float4* P, int d, float2 s, float2& hi, float2& lo) {
+  float4 c = P[d];
+  float2 qh = make_float2(c.x, c.y), ql = make_float2(c.z, c.w);
+  const float2 sh = make_float2(s.x, s.x), sl = make_float2(s.y, s.y);
+  for (int b = d - 1; b >= 0; --b) {
+    const float2 ph = __fmul2_rn(qh, sh);
+    float2 pe = __ffma2_rn(qh, sh, neg2(ph));
+    pe = __ffma2_rn(qh, sl, pe);
+    pe = __ffma2_rn(ql, sh, pe);
+    c = P[b];
+    const float2 bh = make_float2(c.x, c.y), bl = make_float2(c.z, c.w);
+    const float2 t = __fadd2_rn(ph, bh);
+    const float2 bb = __fadd2_rn(t, neg2(ph));
+    const float2 e = __fadd2_rn(__fadd2_rn(ph, neg2(__fadd2_rn(t, neg2(bb)))), __fadd2_rn(bh, neg2(bb)));
+    const float2 e2 = __fadd2_rn(e, __fadd2_rn(pe, bl));
+    qh = __fadd2_rn(t, e2);
+    ql = __fadd2_rn(e2, neg2(__fadd2_rn(qh, neg2(t))));
+  }
+  hi = qh;
+  lo = ql;
+}
+
+// Window-centre pixels and FP32 offsets of a stamp (map_xy_df, then split_coord_df).
+__device__ __forceinline__ void map_stamp_df(const float4* P, int d, float2 s, int& ci, float& fx, int& ri,
+                                             float& fy) {
+  float2 hi, lo;
+  map_xy_df(P, d, s, hi, lo);
+  split_coord_df(hi.x, lo.x, ci, fx);
+  split_coord_df(hi.y, lo.y, ri, fy);
+}
+
 // box_deposit's fixed-point words of two values at once: the same operations on each
 // component (packed FP32x2 for the multiplies and the FMA), so the same words.
 __device__ __forceinline__ void fixed_split2(float2 val, float sc, float sc_hi, int2& hi, uint2& lo) {

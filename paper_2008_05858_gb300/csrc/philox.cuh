@@ -203,6 +203,94 @@ static __device__ double poisson_filtered(double lam, uint64_t seed, uint32_t q,
   return floor(__dadd_rn(lam, 0.5));
 }
 
+// ------------------------------------------------------------------ FP32 only (no FP64)
+//
+// The first pass of the noise stage decides draws in FP32 alone and defers the rest to an
+// exact FP64 pass over a compacted list; these helpers return -1 for "too close to call".
+
+// log of the Poisson pmf at k >= 0, -lam + k ln lam - lgamma(k + 1), for lam >= 10 given as
+// Lf + frac (Lf an integer, frac in [0, 1)), and a bound on its error.  For n = k + 1 >= 10 the
+// Stirling series in the well-conditioned form
+//   -lam phi(x) + log1p(x) - ln(n)/2 - ln(2 pi)/2 - 1/(12n) + 1/(360n^3) - 1/(1260n^5),
+//   x = (n - lam)/lam,  phi(x) = (1 + x) log1p(x) - x,
+// (phi by its alternating series sum_j (-1)^j x^j / (j (j - 1)) for |x| < 1/4), which never
+// subtracts terms of the size of lam; below, the direct form with lgammaf.
+__device__ __forceinline__ float log_poisson_pmf_f32(float kr, float Lf, float frac, float& err) {
+  const float lam = Lf + frac;
+  const float n = Lf + kr + 1.f;  // k + 1, exact (integers below 2^24)
+  if (n >= 10.f) {
+    const float D = (kr + 1.f) - frac;  // n - lam, one rounding
+    const float x = D / lam;
+    float phi;
+    if (fabsf(x) < 0.25f) {
+      float t = -1.f / 132.f;  // j = 12
+      t = fmaf(t, x, 1.f / 110.f);
+      t = fmaf(t, x, -1.f / 90.f);
+      t = fmaf(t, x, 1.f / 72.f);
+      t = fmaf(t, x, -1.f / 56.f);
+      t = fmaf(t, x, 1.f / 42.f);
+      t = fmaf(t, x, -1.f / 30.f);
+      t = fmaf(t, x, 1.f / 20.f);
+      t = fmaf(t, x, -1.f / 12.f);
+      t = fmaf(t, x, 1.f / 6.f);
+      t = fmaf(t, -x, 0.5f);  // 1/2 - x/6 + x^2/12 - ...
+      phi = x * x * t;
+    } else {
+      phi = fmaf(1.f + x, log1pf(x), -x);
+    }
+    const float in = 1.f / n, in2 = in * in;
+    const float c = in * fmaf(in2, fmaf(in2, -1.f / 1260.f, 1.f / 360.f), -1.f / 12.f);  // -(1/12n - ...)
+    const float lp = fmaf(-lam, phi, log1pf(x)) + fmaf(-0.5f, logf(n), -0.918938533f) + c;
+    err = fmaf(2e-5f, fabsf(lam * phi), 2e-5f);
+    return lp;
+  }
+  const float lp = fmaf(kr + Lf, logf(lam), -lam) - lgammaf(n);
+  err = fmaf(1e-6f, lam + (kr + Lf) * fabsf(logf(lam)), 5e-5f);
+  return lp;
+}
+
+// Hormann's PTRS in FP32 for lam = Lf + frac >= 10 known to le: the count, or -1 when a
+// comparison (the floor that makes k, the quick acceptance, the rejection, the slow
+// acceptance test) is too close to call, or 64 trials pass.
+static __device__ int ptrs_f32(float Lf, float frac, float le, uint64_t seed, uint32_t q, uint32_t d,
+                               uint32_t stream) {
+  const float l = Lf + frac;
+  const float sl = sqrtf(l);
+  const float b = fmaf(2.53f, sl, 0.931f);
+  const float a = fmaf(0.02483f, b, -0.059f);
+  const float vr = 0.9277f - 3.6224f / (b - 2.f);
+  const float lia = logf(1.1239f + 1.1328f / (b - 3.4f));  // ln(1 / alpha)
+  for (uint32_t i = 0; i < 64; ++i) {
+    const uint4 w = rng_block(seed, q, d, i, stream);
+    const float U = uni53_f32(w.x, w.y) - 0.5f, V = uni53_f32(w.z, w.w);
+    const float us = 0.5f - fabsf(U);
+    const float T = 2.f * a / us + b;
+    const float y = T * U;
+    const float yerr = fabsf(T) * fmaf(fabsf(U), fmaf(3e-7f, 1.f / us, 4e-6f), 2e-7f) + 1e-6f;
+    const float xr = (y + frac) + 0.43f;
+    const float xe = yerr + fmaf(fabsf(xr), 2.5e-7f, 1e-7f) + le;
+    const float kr = floorf(xr - xe);
+    if (floorf(xr + xe) != kr) return -1;
+    const float mu = 3e-7f, mv = 8e-7f;
+    const bool c1t = us - 0.07f > mu, c1f = 0.07f - us > mu, c2t = vr - V > mv, c2f = V - vr > mv;
+    if (c1t && c2t) return (int)(Lf + kr);
+    if (!(c1f || c2f)) return -1;
+    if (Lf + kr < 0.f) continue;
+    const bool d1t = 0.013f - us > mu, d1f = us - 0.013f > mu, d2t = V - us > mu, d2f = us - V > mu;
+    if (d1t && d2t) continue;
+    if (!(d1f || d2f)) return -1;
+    // slow acceptance: ln V + ln(1/alpha) - ln(a / us^2 + b) <= ln p(k)
+    const float lhs = logf(V) + lia - logf(a / (us * us) + b);
+    const float elhs = fmaf(1e-6f, fabsf(lhs), 6e-6f) + 3e-7f / us;
+    float erhs;
+    const float rhs = log_poisson_pmf_f32(kr, Lf, frac, erhs);
+    if (lhs + elhs < rhs - erhs) return (int)(Lf + kr);
+    if (lhs - elhs > rhs + erhs) continue;
+    return -1;
+  }
+  return -1;
+}
+
 // A Poisson count: k when the FP32 draw decided it, else (k < 0) the FP64 value x.
 struct Count {
   int k;

@@ -200,8 +200,8 @@ struct TableLayout {
   size_t tabP, tabS, tabW, tabU, tabF, stage, stagew, boxh, boxl, total;
   __host__ __device__ TableLayout(int J, int NK, int nd, int area) {
     size_t o = 0;
-    tabP = o; o += (size_t)J * 2 * nd * 8;
-    tabS = o; o += (size_t)NK * 8;
+    tabP = o; o += (size_t)J * nd * 16;        // P_b(lt) of x and y, split_xy pairs
+    tabS = o; o += (size_t)NK * 8;              // s, (hi, lo) floats
     tabW = o; o += (size_t)J * 8;
     tabU = o; o += (size_t)NK * 8;
     o = (o + 15) & ~(size_t)15;
@@ -237,8 +237,8 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
   const int area = it.bw * it.bh;
   const int nd = S.degree + 1;
   const TableLayout L(32, a.nk_max, a.max_deg + 1, area);
-  double* tabP = reinterpret_cast<double*>(smem + L.tabP);
-  double* tabS = reinterpret_cast<double*>(smem + L.tabS);
+  float4* tabP = reinterpret_cast<float4*>(smem + L.tabP);
+  float2* tabS = reinterpret_cast<float2*>(smem + L.tabS);
   float2* tabW = reinterpret_cast<float2*>(smem + L.tabW);
   float2* tabU = reinterpret_cast<float2*>(smem + L.tabU);
   int4* tabF = reinterpret_cast<int4*>(smem + L.tabF);
@@ -259,17 +259,15 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
   double usum = 0.0;
   for (int kk = tid; kk < it.nk; kk += kTThreads) {
     const double uk = u[it.k0 + kk];
-    tabS[kk] = norm_sample_r(it.k0 + kk, S.n_slit, inv_ns);
+    tabS[kk] = split_df(norm_sample_r(it.k0 + kk, S.n_slit, inv_ns));
     tabU[kk] = split_df(uk);
     usum += fabs(uk);
   }
   double wsum = 0.0;
   for (int jj = tid; jj < it.nj; jj += kTThreads) {
     const double lt = norm_sample_r(it.j0 + jj, S.n_lambda, inv_nl);
-    for (int b = 0; b < nd; ++b) {
-      tabP[(jj * 2 + 0) * nd + b] = poly_lt_for_b(S.cx, S.degree, b, lt);
-      tabP[(jj * 2 + 1) * nd + b] = poly_lt_for_b(S.cy, S.degree, b, lt);
-    }
+    for (int b = 0; b < nd; ++b)
+      tabP[jj * nd + b] = split_xy(poly_lt_for_b(S.cx, S.degree, b, lt), poly_lt_for_b(S.cy, S.degree, b, lt));
     int f0, f1;
     double wf;
     field_weight(ta.field_lt + TS.field_off, TS.n_field, lt, f0, f1, wf);
@@ -350,25 +348,20 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
       if (idx < nst) {
         const int jj = idx / it.nk;
         const int kk = idx - jj * it.nk;
-        double px[9], py[9];
-#pragma unroll
-        for (int b = 0; b <= 8; ++b) {
-          px[b] = b < nd ? tabP[(jj * 2 + 0) * nd + b] : 0.0;
-          py[b] = b < nd ? tabP[(jj * 2 + 1) * nd + b] : 0.0;
-        }
-        const double s = tabS[kk];
-        const double xv = horner_s(px, S.degree, s), yv = horner_s(py, S.degree, s);
+        float2 mh, ml;  // the centre as double-floats, as the planner maps it
+        map_xy_df(tabP + jj * nd, S.degree, tabS[kk], mh, ml);
         float fx, fy;
-        split_coord(xv, ci, fx);
-        split_coord(yv, ri, fy);
+        split_coord_df(mh.x, ml.x, ci, fx);
+        split_coord_df(mh.y, ml.y, ri, fy);
         const float2 wj = tabW[jj], uk = tabU[kk];
         const float w = fmaf(wj.x, uk.x, fmaf(wj.x, uk.y, wj.y * uk.x));
         const int4 fw = tabF[jj];
         int cxi = 0, cyi = 0;
         double tx = 0.0, ty = 0.0;
         if (ci != kOffFrame && ri != kOffFrame) {
-          phase_cell(TS, xv - (double)ci, cxi, tx);
-          phase_cell(TS, yv - (double)ri, cyi, ty);
+          // the phase v - c exactly in FP64 (h - c is exact in FP32, the low word adds exactly)
+          phase_cell(TS, (double)(mh.x - (float)ci) + (double)ml.x, cxi, tx);
+          phase_cell(TS, (double)(mh.y - (float)ri) + (double)ml.y, cyi, ty);
         }
         const float wf1 = __int_as_float(fw.z);
         cw = make_float4((float)tx, (float)ty, (1.f - wf1) * w, wf1 * w);

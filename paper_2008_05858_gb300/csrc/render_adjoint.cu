@@ -24,6 +24,7 @@
 
 #include "e2e_device.cuh"
 #include "e2e_kernels.h"
+#include "mixed_common.cuh"
 #include "phi32.cuh"
 
 namespace e2e {
@@ -142,6 +143,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
   double* red = reinterpret_cast<double*>(smem + o_red);                // [warps][ncoef]
   double* tabS = red + kAdjWarps * ncoef;                               // s of the item's slit points
   float2* tabU = reinterpret_cast<float2*>(tabS + a.nk_max);           // their weights, (hi, lo)
+  // P_b(lt) of the item's samples as split_xy pairs, on a 16-byte boundary
+  float4* tabP = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(tabU + a.nk_max) + 15) & ~(uintptr_t)15);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   {
     const int64_t P = a.pitch[S.det];
@@ -157,6 +160,13 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
     for (int kk = tid; kk < it.nk; kk += kAdjThreads) {
       tabS[kk] = (double)(2 * (it.k0 + kk) + 1 - S.n_slit) * inv_ns;
       tabU[kk] = split_pair(u[it.k0 + kk]);
+    }
+    // the mapping's per-sample coefficients, as the planner forms them
+    const double inv_nl0 = 1.0 / (double)S.n_lambda;
+    for (int jj = tid; jj < it.nj; jj += kAdjThreads) {
+      const double lt0 = (double)(2 * (it.j0 + jj) + 1 - S.n_lambda) * inv_nl0;
+      for (int b = 0; b <= d; ++b)
+        tabP[jj * (d + 1) + b] = split_xy(poly_lt_for_b(S.cx, d, b, lt0), poly_lt_for_b(S.cy, d, b, lt0));
     }
   }
   __syncthreads();
@@ -175,12 +185,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
     double lt = 0.0;
     if (jvalid) {
       lt = (double)(2 * j + 1 - S.n_lambda) * inv_nl;
-      double px[9], py[9];
-#pragma unroll
-      for (int b = 0; b <= 8; ++b) {
-        px[b] = b <= d ? poly_lt_for_b(S.cx, d, b, lt) : 0.0;
-        py[b] = b <= d ? poly_lt_for_b(S.cy, d, b, lt) : 0.0;
-      }
+      const float4* P = tabP + jj * (d + 1);  // P_b(lt) of x and y (the planner's mapping)
       const double sgx = fma(fma(S.sx[2], lt, S.sx[1]), lt, S.sx[0]);
       const double sgy = fma(fma(S.sy[2], lt, S.sy[1]), lt, S.sy[0]);
       const float2 gx = split_pair(kq / sgx), gy = split_pair(kq / sgy);
@@ -191,9 +196,10 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
         const double sd = tabS[k - it.k0];
         int ci, ri;
         float fx, fy;
-        const double xv = horner_s(px, d, sd), yv = horner_s(py, d, sd);
-        split_coord(xv, ci, fx);
-        split_coord(yv, ri, fy);
+        float2 mh, ml;
+        map_xy_df(P, d, split_df(sd), mh, ml);
+        split_coord_df(mh.x, ml.x, ci, fx);
+        split_coord_df(mh.y, ml.y, ri, fy);
         if (ci == kOffFrame || ri == kOffFrame) continue;
         const float2 uk = tabU[k - it.k0];
         const float w = fmaf(wj.x, uk.x, fmaf(wj.x, uk.y, wj.y * uk.x));
@@ -202,8 +208,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
           const int2 o = a.frozen[S.stamp_off + (int64_t)j * S.n_slit + k];
           ci = o.x + H;
           ri = o.y + H;
-          fx = (float)(xv - (double)ci);
-          fy = (float)(yv - (double)ri);
+          fx = (mh.x - (float)ci) + ml.x;  // h - c exact (|h - c| small against h), one rounding
+          fy = (mh.y - (float)ri) + ml.y;
           axis_profile_any<K>(fx, gx.x, gx.y, isx, Ax, dAx, sAx);
           axis_profile_any<K>(fy, gy.x, gy.y, isy, Ay, dAy, sAy);
         } else {
@@ -324,9 +330,11 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
   }
 }
 
-size_t adjoint_smem_bytes(int max_area, int max_deg, int nk_max) {
+size_t adjoint_smem_bytes(int max_area, int max_deg, int nk_max, int nj_max) {
   const int nc = (max_deg + 1) * (max_deg + 2) / 2;
-  return (((size_t)max_area * 4 + 15) & ~(size_t)15) + (size_t)kAdjWarps * (2 * nc + 6) * 8 + (size_t)nk_max * 16;
+  // dL/dI box, warp partials, s and u of the slit points, then (16-byte aligned) the tables
+  return (((size_t)max_area * 4 + 15) & ~(size_t)15) + (size_t)kAdjWarps * (2 * nc + 6) * 8 + (size_t)nk_max * 16 +
+         16 + (size_t)nj_max * (max_deg + 1) * 16;
 }
 
 int adjoint_parts(int max_tasks) { return std::max(1, std::min(4, (max_tasks + kAdjWarps - 1) / kAdjWarps)); }

@@ -63,19 +63,19 @@ __device__ __forceinline__ EllipParams ellip_params(const DevSlice& S, double lt
 
 // ------------------------------------------------------------------------------ mixed
 
-// Shared-memory layout of one CTA (bytes), identical on host and device.
+// Shared-memory layout of one CTA (bytes), identical on host and device.  Lane groups of K
+// lanes (one per window column) stage the 16 stamps of a run each: 32 / K groups per warp.
 struct EllipLayout {
-  size_t tabP, tabS, tabW, tabU, tabE, stage, stagew, boxh, boxl, total;
-  __host__ __device__ EllipLayout(int J, int NK, int nd, int area) {
+  size_t tabP, tabS, tabW, tabU, tabE, stage, boxh, boxl, total;
+  __host__ __device__ EllipLayout(int J, int NK, int nd, int area, int K) {
     size_t o = 0;
-    tabP = o; o += (size_t)J * 2 * nd * 8;     // P_b(lt) of x and y per sample
-    tabS = o; o += (size_t)NK * 8;              // s of each slit point
+    tabP = o; o += (size_t)J * nd * 16;        // P_b(lt) of x and y per sample, split_xy pairs
+    tabS = o; o += (size_t)NK * 8;              // s of each slit point, (hi, lo) floats
     tabW = o; o += (size_t)J * 8;               // flux x bin width / 4 per sample, (hi, lo)
     tabU = o; o += (size_t)NK * 8;              // slit weights, (hi, lo)
     o = (o + 15) & ~(size_t)15;
     tabE = o; o += (size_t)J * 32;              // two float4 of PSF constants per sample
-    stage = o; o += (size_t)kEWarps * 32 * 16;  // mapped stamps: origin pixel, offsets
-    stagew = o; o += (size_t)kEWarps * 32 * 8;  // weight / 4 and sample index
+    stage = o; o += (size_t)kEWarps * (32 / K) * 16 * 16;  // mapped stamps of the groups' runs
     boxh = o; o += (size_t)area * 4;
     boxl = o; o += (size_t)area * 4;
     total = o;
@@ -83,27 +83,30 @@ struct EllipLayout {
 };
 
 // One CTA per work item (<= 32 wavelength samples x <= 16 slit points, at most 512 stamps,
-// so no box pixel gets more than 512 fixed-point deposits).  Each warp maps 32 stamps at a
-// time (one per lane, FP64) into its staging area; then the batch's 32 K (stamp, column)
-// pairs are spread over the 32 lanes (no idle lanes), and the lane holding column m of a
-// stamp evaluates the column's x-integral, the moments of tau, and the K + 1 row edges of
-// its conditional profile, depositing the K pixels into the item's box.
+// so no box pixel gets more than 512 fixed-point deposits).  A warp holds 32 / K groups of K
+// lanes, lane m of a group owning window column m.  A group takes one wavelength sample and
+// walks the run of its slit points in order: the run's stamps are mapped into the group's
+// staging, then for each stamp every lane evaluates its column (the two x-edges, the moments
+// of tau, the K + 1 row edges of the conditional profile, in packed pairs) and adds the K
+// pixels to its registers.  Consecutive slit points mostly share their window origin, so the
+// lanes deposit their columns into the item's box (exact fixed point, shared-memory integer
+// atomics) only when the origin moves and at the end of the run.
 template <int K>
 __global__ void __launch_bounds__(kEThreads, 6) k_render_ellip(const MixedArgs a) {
   constexpr int H = K / 2;
+  constexpr int NG = 32 / K;  // lane groups per warp
   extern __shared__ __align__(16) unsigned char smem[];
   const Item it = a.items[blockIdx.x];
   const DevSlice& S = a.slices[it.slice];
   const int area = it.bw * it.bh;
   const int nd = S.degree + 1;
-  const EllipLayout L(32, a.nk_max, a.max_deg + 1, area);
-  double* tabP = reinterpret_cast<double*>(smem + L.tabP);
-  double* tabS = reinterpret_cast<double*>(smem + L.tabS);
+  const EllipLayout L(32, a.nk_max, a.max_deg + 1, area, K);
+  float4* tabP = reinterpret_cast<float4*>(smem + L.tabP);
+  float2* tabS = reinterpret_cast<float2*>(smem + L.tabS);
   float2* tabW = reinterpret_cast<float2*>(smem + L.tabW);
   float2* tabU = reinterpret_cast<float2*>(smem + L.tabU);
   float4* tabE = reinterpret_cast<float4*>(smem + L.tabE);
   int4* stage = reinterpret_cast<int4*>(smem + L.stage);
-  float2* stagew = reinterpret_cast<float2*>(smem + L.stagew);
   int* boxh = reinterpret_cast<int*>(smem + L.boxh);
   unsigned* boxl = reinterpret_cast<unsigned*>(smem + L.boxl);
   __shared__ double s_w[kEWarps], s_u[kEWarps];
@@ -119,17 +122,15 @@ __global__ void __launch_bounds__(kEThreads, 6) k_render_ellip(const MixedArgs a
   double usum = 0.0;
   for (int kk = tid; kk < it.nk; kk += kEThreads) {
     const double uk = u[it.k0 + kk];
-    tabS[kk] = norm_sample_r(it.k0 + kk, S.n_slit, inv_ns);
+    tabS[kk] = split_df(norm_sample_r(it.k0 + kk, S.n_slit, inv_ns));
     tabU[kk] = split_df(uk);
     usum += fabs(uk);
   }
   double wsum = 0.0;
   for (int jj = tid; jj < it.nj; jj += kEThreads) {
     const double lt = norm_sample_r(it.j0 + jj, S.n_lambda, inv_nl);
-    for (int b = 0; b < nd; ++b) {
-      tabP[(jj * 2 + 0) * nd + b] = poly_lt_for_b(S.cx, S.degree, b, lt);
-      tabP[(jj * 2 + 1) * nd + b] = poly_lt_for_b(S.cy, S.degree, b, lt);
-    }
+    for (int b = 0; b < nd; ++b)
+      tabP[jj * nd + b] = split_xy(poly_lt_for_b(S.cx, S.degree, b, lt), poly_lt_for_b(S.cy, S.degree, b, lt));
     const EllipParams p = ellip_params(S, lt);
     const double kq = kSqrtLog2eD * 0.70710678118654752440;  // edge arguments in log2 units
     const float2 gx = split_df(kq / p.gx), gc = split_df(kq / p.sc), be = split_df(p.beta);
@@ -161,54 +162,70 @@ __global__ void __launch_bounds__(kEThreads, 6) k_render_ellip(const MixedArgs a
   const int Psh = total > 0.0 ? max(-100, min(100, 52 - ex)) : 0;
   const float sc = ldexpf(1.f, Psh), sc_hi = ldexpf(1.f, Psh - 22);
 
-  const int nst = it.nj * it.nk;
-  int4* wst = stage + warp * 32;
-  float2* wsw = stagew + warp * 32;
-  for (int base = warp * 32; base < nst && total > 0.0; base += kEWarps * 32) {
-    {  // map stamp base + lane (FP64) into the staging area
-      const int idx = base + lane;
-      int ci = kOffFrame, ri = kOffFrame, jj = 0;
-      float fx = 0.f, fy = 0.f, w = 0.f;
-      if (idx < nst) {
-        jj = idx / it.nk;
-        const int kk = idx - jj * it.nk;
-        double px[9], py[9];
-#pragma unroll
-        for (int b = 0; b <= 8; ++b) {
-          px[b] = b < nd ? tabP[(jj * 2 + 0) * nd + b] : 0.0;
-          py[b] = b < nd ? tabP[(jj * 2 + 1) * nd + b] : 0.0;
-        }
-        const double s = tabS[kk];
-        split_coord(horner_s(px, S.degree, s), ci, fx);
-        split_coord(horner_s(py, S.degree, s), ri, fy);
-        const float2 wj = tabW[jj], uk = tabU[kk];
-        w = fmaf(wj.x, uk.x, fmaf(wj.x, uk.y, wj.y * uk.x));
+  const int g = lane / K, m = lane - g * K;  // group and window column (g == NG: spare lane)
+  const bool in_group = g < NG;
+  int4* gst = stage + (warp * NG + (in_group ? g : 0)) * 16;
+  float acc[K];
+  // the groups of a warp take samples kEWarps apart, so their columns rarely share a box pixel
+  const int n_rounds = (it.nj + kEWarps * NG - 1) / (kEWarps * NG);
+  for (int round = 0; round < n_rounds && total > 0.0; ++round) {
+    const int jj = warp + kEWarps * (g + NG * round);
+    const bool active = in_group && jj < it.nj;  // uniform over the group
+    // map the run's stamps (double-float, as the planner), lane m taking b = m, m + K, ...
+    if (active)
+      for (int b = m; b < it.nk; b += K) {
+        int ci, ri;
+        float fx, fy;
+        map_stamp_df(tabP + jj * nd, S.degree, tabS[b], ci, fx, ri, fy);
+        gst[b] = make_int4(ci, ri, __float_as_int(fx), __float_as_int(fy));
       }
-      wst[lane] = make_int4(ci, ri, __float_as_int(fx), __float_as_int(fy));
-      wsw[lane] = make_float2(w, __int_as_float(jj));
-    }
     __syncwarp();
-    const int nb = min(32, nst - base);
-    // (stamp, column) pairs of the batch, flattened over the warp's 32 lanes
-    const int npairs = nb * K;
-    for (int p0 = 0; p0 < npairs; p0 += 32) {
-      const int p = p0 + lane;
-      const int b = p < npairs ? p / K : 0;
-      const int m = p < npairs ? p - b * K : 0;
-      const int4 st = wst[b];
-      const bool valid = p < npairs && st.x != kOffFrame && st.y != kOffFrame;
-      const float2 sw = wsw[b];
-      const int jj = __float_as_int(sw.y);
-      const float4 e0 = tabE[2 * jj], e1 = tabE[2 * jj + 1];
+    float4 e0 = make_float4(0.f, 0.f, 0.f, 0.f), e1 = e0;
+    float2 wj = make_float2(0.f, 0.f);
+    if (active) {
+      e0 = tabE[2 * jj];
+      e1 = tabE[2 * jj + 1];
+      wj = tabW[jj];
+    }
+    int cx = kOffFrame, cy = kOffFrame;  // origin of the stamps held in acc (uniform over the group)
+#pragma unroll
+    for (int n = 0; n < K; ++n) acc[n] = 0.f;
+    auto flush = [&]() {
+      const int bx = cx - H + m - it.bx0, by0 = cy - H - it.by0;
+      const bool colin = bx >= 0 && bx < it.bw;
+#pragma unroll
+      for (int n = 0; n < K; ++n) {
+        const int by = by0 + n;
+        if (colin && by >= 0 && by < it.bh) {
+          const int q = by * it.bw + bx;
+          box_deposit(boxh + q, boxl + q, acc[n], sc, sc_hi);
+        } else if (a.err && acc[n] != 0.f) {  // outside the box: legitimate only off the detector
+          const int X = it.bx0 + bx, Y = it.by0 + by;
+          if (X >= 0 && X < S.W && Y >= 0 && Y < S.H) atomicAdd(a.err, 1);
+        }
+        acc[n] = 0.f;
+      }
+    };
+    for (int b = 0; b < it.nk; ++b) {
+      const int4 st = active ? gst[b] : make_int4(kOffFrame, kOffFrame, 0, 0);
+      const bool valid = st.x != kOffFrame && st.y != kOffFrame;
+      if (valid && (st.x != cx || st.y != cy)) {
+        if (cx != kOffFrame) flush();
+        cx = st.x;
+        cy = st.y;
+      }
+      const float2 uk = tabU[b];
+      const float w = valid ? fmaf(wj.x, uk.x, fmaf(wj.x, uk.y, wj.y * uk.x)) : 0.f;
       const float fx = __int_as_float(st.z), fy = __int_as_float(st.w);
 
-      // twice the column's x-integral (same edge formulas as the separable profile)
-      float whL, wlL, whR, wlR;
-      edge_arg((float)(m - H) - 0.5f, fx, e0.x, e0.y, whL, wlL);
-      edge_arg((float)(m - H) + 0.5f, fx, e0.x, e0.y, whR, wlR);
-      const float EL = tail2(whL, wlL), ER = tail2(whR, wlR);
-      const float FL = fabsf(whL) < kErfMaxArg ? erf_small(whL) : 1.f - EL;
-      const float FR = fabsf(whR) < kErfMaxArg ? erf_small(whR) : 1.f - ER;
+      // twice the column's x-integral (the separable profile's edge formulas), edges m, m + 1
+      float2 wxh, wxl;
+      edge_arg2(f2((float)(m - H) - 0.5f, (float)(m - H) + 0.5f), fx, e0.x, e0.y, wxh, wxl);
+      const float2 EX = tail2x2(wxh, wxl);
+      const float2 FE = erf_small2(wxh);
+      const float EL = EX.x, ER = EX.y;
+      const float FL = fabsf(wxh.x) < kErfMaxArg ? FE.x : 1.f - EL;
+      const float FR = fabsf(wxh.y) < kErfMaxArg ? FE.y : 1.f - ER;
       const float tx = m < H - 1 ? ER - EL : (m == H - 1 ? FL - FR : (m == H ? FL + FR : (m == H + 1 ? FR - FL : EL - ER)));
 
       // column centre offset tb = (m - H) - fx as a double-float (|m - H| >= 1 > |fx| or m == H)
@@ -270,49 +287,56 @@ __global__ void __launch_bounds__(kEThreads, 6) k_render_ellip(const MixedArgs a
         fh = t;
       }
       const float gch = e0.z, gcl = e0.w;
-      const float wq = sw.x * tx;
-      const int bx = st.x - H + m - it.bx0;
-      const bool colin = valid && bx >= 0 && bx < it.bw;
-      const int by0 = st.y - H - it.by0;
+      const float wq = w * tx;
+      // the K + 1 row edges in pairs (n, n + 1); pixel n spans edges n and n + 1
       float Ep = 0.f, Fp = 0.f, hp = 0.f, whp = 0.f;
 #pragma unroll
-      for (int n = 0; n <= K; ++n) {
-        // row edge n at (n - H - 1/2) - f from the conditional centre, in log2 units
-        float dh, de;
-        two_sum((float)(n - H) - 0.5f, -fh, dh, de);
-        const float dl = de - fl;
-        const float wh = dh * gch;
-        const float wl = fmaf(dh, gch, -wh) + fmaf(dh, gcl, dl * gch);
-        float dens;
-        const float E = tail2_dens(wh, wl, dens);
-        // erf only near the conditional centre; the branch is skipped when no lane of the
-        // warp has an edge there
-        const bool near = fabsf(wh) < kErfMaxArg;
-        float F = 1.f - E;
-        if (__any_sync(0xffffffffu, near)) F = near ? erf_small(wh) : F;
-        const float V = wh * kSqrt2Ln2;
-        const float Gv = fmaf(fmaf(fmaf(fmaf(fmaf(g5, V, g4), V, g3), V, g2), V, g1), V, g0);
-        const float h = dens * Gv;
-        if (n > 0) {
-          const bool same = (wh < 0.f) == (whp < 0.f);
-          const bool small = fminf(fabsf(wh), fabsf(whp)) < kErfMaxArg;
-          const float ty = same ? (small ? fabsf(Fp - F) : fabsf(Ep - E)) : (Fp + F);
-          const int by = by0 + n - 1;
-          if (colin && by >= 0 && by < it.bh) {
-            const int q = by * it.bw + bx;
-            box_deposit(boxh + q, boxl + q, wq * (ty + (h - hp)), sc, sc_hi);
-          } else if (a.err && valid) {  // outside the box: legitimate only off the detector
-            const int X = it.bx0 + bx, Y = it.by0 + by;
-            if (X >= 0 && X < S.W && Y >= 0 && Y < S.H) atomicAdd(a.err, 1);
-          }
+      for (int n = 0; n <= K; n += 2) {
+        // row edges at (n - H - 1/2) - f from the conditional centre, in log2 units (TwoSum:
+        // |f| may exceed 1/2)
+        const float2 eg = f2((float)(n - H) - 0.5f, (float)(n - H) + 0.5f);
+        const float2 dh = __fadd2_rn(eg, f2(-fh, -fh));
+        const float2 bb2 = __fadd2_rn(dh, neg2(eg));
+        const float2 de = __fadd2_rn(__fadd2_rn(eg, neg2(__fadd2_rn(dh, neg2(bb2)))), __fadd2_rn(f2(-fh, -fh), neg2(bb2)));
+        const float2 dl = __fadd2_rn(de, f2(-fl, -fl));
+        const float2 gg = f2(gch, gch);
+        const float2 wh = __fmul2_rn(dh, gg);
+        const float2 wl = __fadd2_rn(__ffma2_rn(dh, gg, neg2(wh)), __ffma2_rn(dh, f2(gcl, gcl), __fmul2_rn(dl, gg)));
+        float2 dens;
+        const float2 E = tail2x2_dens(wh, wl, dens);
+        // erf only near the conditional centre; skipped when no lane of the warp has an edge there
+        const bool near0 = fabsf(wh.x) < kErfMaxArg, near1 = fabsf(wh.y) < kErfMaxArg;
+        float2 F = f2(1.f - E.x, 1.f - E.y);
+        if (__any_sync(0xffffffffu, near0 || near1)) {
+          const float2 fe = erf_small2(wh);
+          F = f2(near0 ? fe.x : F.x, near1 ? fe.y : F.y);
         }
-        Ep = E;
-        Fp = F;
-        hp = h;
-        whp = wh;
+        const float2 V = __fmul2_rn(wh, f2(kSqrt2Ln2, kSqrt2Ln2));
+        float2 Gv = __ffma2_rn(f2(g5, g5), V, f2(g4, g4));
+        Gv = __ffma2_rn(Gv, V, f2(g3, g3));
+        Gv = __ffma2_rn(Gv, V, f2(g2, g2));
+        Gv = __ffma2_rn(Gv, V, f2(g1, g1));
+        Gv = __ffma2_rn(Gv, V, f2(g0, g0));
+        const float2 h = __fmul2_rn(dens, Gv);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int ne = n + e;
+          const float Ee = e ? E.y : E.x, Fe = e ? F.y : F.x, he = e ? h.y : h.x, we = e ? wh.y : wh.x;
+          if (ne > 0 && ne <= K) {
+            const bool same = (we < 0.f) == (whp < 0.f);
+            const bool small = fminf(fabsf(we), fabsf(whp)) < kErfMaxArg;
+            const float ty = same ? (small ? fabsf(Fp - Fe) : fabsf(Ep - Ee)) : (Fp + Fe);
+            acc[ne - 1] = fmaf(wq, ty + (he - hp), acc[ne - 1]);
+          }
+          Ep = Ee;
+          Fp = Fe;
+          hp = he;
+          whp = we;
+        }
       }
     }
-    __syncwarp();  // the staging is reused by the next batch
+    if (cx != kOffFrame) flush();
+    __syncwarp();  // the staging is reused by the next round
   }
   __syncthreads();
   float2* out = a.store + it.store_off;
@@ -320,7 +344,9 @@ __global__ void __launch_bounds__(kEThreads, 6) k_render_ellip(const MixedArgs a
   for (int p = tid; p < area; p += kEThreads) out[p] = fixed_to_pair(boxh[p], boxl[p], inv);
 }
 
-size_t ellip_smem_bytes(int area, int nk_max, int nd) { return EllipLayout(32, nk_max, nd, area).total; }
+size_t ellip_smem_bytes(int area, int nk_max, int nd, int k_min) {
+  return EllipLayout(32, nk_max, nd, area, k_min).total;
+}
 
 template <int K>
 static cudaError_t launch_ellip_one(const MixedArgs& a, int n_items, size_t smem, cudaStream_t st) {

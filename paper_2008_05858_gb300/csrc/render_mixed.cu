@@ -25,7 +25,7 @@ namespace e2e {
 // ------------------------------------------------------------------------------ plan
 
 // One thread per (slice, wavelength sample j, block of 16 slit points): map the stamps
-// exactly as the render will, and record (a) per (32-sample block, 16-point block) of each
+// exactly as the render will (map_stamp_df), and record (a) per (32-sample block, 16-point block) of each
 // slice the bounding box of the stamps' windows, (b) per slice the largest spread of window
 // origins over any aligned run of B = 1, 2, 4, 8, 16 consecutive slit points.  Stamps that
 // map off every detector (kOffFrame) are ignored.
@@ -45,23 +45,18 @@ __global__ void k_plan(const DevSlice* __restrict__ slices, int n_slices, const 
     const int j = (int)(local / nkb), kb = (int)(local - (int64_t)j * nkb);
     const double lt = norm_sample_r(j, S.n_lambda, 1.0 / (double)S.n_lambda);
     const double inv_ns = 1.0 / (double)S.n_slit;
-    double px[9], py[9];
-#pragma unroll
-    for (int b = 0; b <= 8; ++b) {
-      px[b] = b <= S.degree ? poly_lt_for_b(S.cx, S.degree, b, lt) : 0.0;
-      py[b] = b <= S.degree ? poly_lt_for_b(S.cy, S.degree, b, lt) : 0.0;
-    }
+    float4 P[9];  // degree <= 8
+    for (int b = 0; b <= S.degree; ++b)
+      P[b] = split_xy(poly_lt_for_b(S.cx, S.degree, b, lt), poly_lt_for_b(S.cy, S.degree, b, lt));
     int xmn = 1 << 30, xmx = -(1 << 30), ymn = 1 << 30, ymx = -(1 << 30);
     int rxmn[5], rxmx[5], rymn[5], rymx[5], spx[5], spy[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) { rxmn[q] = rymn[q] = 1 << 30; rxmx[q] = rymx[q] = -(1 << 30); spx[q] = spy[q] = 0; }
     const int k0 = kb * 16, k1 = min(k0 + 16, S.n_slit);
     for (int k = k0; k < k1; ++k) {
-      const double s = norm_sample_r(k, S.n_slit, inv_ns);
       int ci, ri;
       float fx, fy;
-      split_coord(horner_s(px, S.degree, s), ci, fx);
-      split_coord(horner_s(py, S.degree, s), ri, fy);
+      map_stamp_df(P, S.degree, split_df(norm_sample_r(k, S.n_slit, inv_ns)), ci, fx, ri, fy);
       const bool on = ci != kOffFrame && ri != kOffFrame;
       if (on) {
         xmn = min(xmn, ci); xmx = max(xmx, ci); ymn = min(ymn, ri); ymx = max(ymx, ri);

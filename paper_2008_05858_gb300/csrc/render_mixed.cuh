@@ -24,8 +24,8 @@ struct MixedLayout {
   size_t tabP, tabS, tabW, tabU, tabG, stage, boxh, boxl, total;
   __host__ __device__ MixedLayout(int J, int NK, int nd, int B, int area) {
     size_t o = 0;
-    tabP = o; o += (size_t)J * 2 * nd * 8;   // P_b(lt) of x and y per sample
-    tabS = o; o += (size_t)NK * 8;            // s of each slit point
+    tabP = o; o += (size_t)J * nd * 16;      // P_b(lt) of x and y per sample, split_xy pairs
+    tabS = o; o += (size_t)NK * 8;            // s of each slit point, (hi, lo) floats
     tabW = o; o += (size_t)J * 8;             // flux x bin width / 4 per sample, (hi, lo) floats
     tabU = o; o += (size_t)NK * 8;            // slit weights, (hi, lo) floats
     o = (o + 15) & ~(size_t)15;
@@ -72,8 +72,8 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
   const int area = it.bw * it.bh;
   const int nd = S.degree + 1;
   const MixedLayout L(32 * a.JB, a.nk_max, a.max_deg + 1, a.B, area);
-  double* tabP = reinterpret_cast<double*>(smem + L.tabP);
-  double* tabS = reinterpret_cast<double*>(smem + L.tabS);
+  float4* tabP = reinterpret_cast<float4*>(smem + L.tabP);
+  float2* tabS = reinterpret_cast<float2*>(smem + L.tabS);
   float2* tabW = reinterpret_cast<float2*>(smem + L.tabW);
   float2* tabU = reinterpret_cast<float2*>(smem + L.tabU);
   float4* tabG = reinterpret_cast<float4*>(smem + L.tabG);
@@ -93,17 +93,15 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
   double usum = 0.0;
   for (int kk = tid; kk < it.nk; kk += kThreads) {
     const double uk = u[it.k0 + kk];
-    tabS[kk] = norm_sample_r(it.k0 + kk, S.n_slit, inv_ns);
+    tabS[kk] = split_df(norm_sample_r(it.k0 + kk, S.n_slit, inv_ns));
     tabU[kk] = split_df(uk);
     usum += fabs(uk);
   }
   double wsum = 0.0;
   for (int jj = tid; jj < it.nj; jj += kThreads) {
     const double lt = norm_sample_r(it.j0 + jj, S.n_lambda, inv_nl);
-    for (int b = 0; b < nd; ++b) {
-      tabP[(jj * 2 + 0) * nd + b] = poly_lt_for_b(S.cx, S.degree, b, lt);
-      tabP[(jj * 2 + 1) * nd + b] = poly_lt_for_b(S.cy, S.degree, b, lt);
-    }
+    for (int b = 0; b < nd; ++b)
+      tabP[jj * nd + b] = split_xy(poly_lt_for_b(S.cx, S.degree, b, lt), poly_lt_for_b(S.cy, S.degree, b, lt));
     // edge arguments are carried in log2 units: w = (edge - centre) sqrt(log2 e) / (sqrt2 sigma)
     const double sgx = fma(fma(S.sx[2], lt, S.sx[1]), lt, S.sx[0]);
     const double sgy = fma(fma(S.sy[2], lt, S.sy[1]), lt, S.sy[0]);
@@ -151,22 +149,13 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
     const bool jvalid = jj < it.nj;      // uniform over the pair
     const int kk0 = (task / njh) * a.B;  // first slit point of the run, relative to the item
     const int nb = min(a.B, it.nk - kk0);
-    // map the run's stamps (FP64), half each, into the staging area
+    // map the run's stamps (double-float), half each, into the staging area
     {
-      double px[9], py[9];
-#pragma unroll
-      for (int b = 0; b <= 8; ++b) {
-        px[b] = (jvalid && b < nd) ? tabP[(jj * 2 + 0) * nd + b] : 0.0;
-        py[b] = (jvalid && b < nd) ? tabP[(jj * 2 + 1) * nd + b] : 0.0;
-      }
+      const float4* Pj = tabP + (jvalid ? jj : 0) * nd;
       for (int b = par; b < nb; b += 2) {
         int ci = kOffFrame, ri = kOffFrame;
         float fx = 0.f, fy = 0.f;
-        if (jvalid) {
-          const double s = tabS[kk0 + b];
-          split_coord(horner_s(px, S.degree, s), ci, fx);
-          split_coord(horner_s(py, S.degree, s), ri, fy);
-        }
+        if (jvalid) map_stamp_df(Pj, S.degree, tabS[kk0 + b], ci, fx, ri, fy);
         mystage[b * kPairs] = make_int4(ci, ri, __float_as_int(fx), __float_as_int(fy));
       }
     }
