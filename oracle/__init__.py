@@ -64,6 +64,9 @@ class OracleSlice(C.Structure):
         ("flux", C.POINTER(C.c_double)),
         ("blaze_order", C.c_double),
         ("blaze_lambda", C.c_double),
+        ("n_aper", C.c_int),
+        ("ax", C.c_double * 3),
+        ("ay", C.c_double * 3),
         ("n_field", C.c_int),
         ("field_lt", C.POINTER(C.c_double)),
         ("map_size", C.c_int),
@@ -158,6 +161,8 @@ class _Marshalled:
             fl = np.ascontiguousarray(flux_of(s), dtype=np.float64)
             assert fl.shape == (s.n_lambda,), "flux length must equal n_lambda"
             assert cx.shape == ((s.degree + 1) * (s.degree + 2) // 2,)
+            rows = max(1, int(getattr(s, "n_aper", 0)))
+            assert u.shape == (s.n_slit * rows,), "slit weights: n_slit per aperture row"
             self.keep += [cx, cy, u, fl]
             o = self.arr[i]
             o.detector, o.degree, o.K, o.n_lambda, o.n_slit = s.detector, s.degree, s.K, s.n_lambda, s.n_slit
@@ -169,6 +174,10 @@ class _Marshalled:
             o.theta = float(s.theta)
             o.blaze_order = float(getattr(s, "blaze_order", 0.0))
             o.blaze_lambda = float(getattr(s, "blaze_lambda", 0.0))
+            o.n_aper = int(getattr(s, "n_aper", 0))
+            for p in range(3):
+                o.ax[p] = float(getattr(s, "aper_x", np.zeros(3))[p])
+                o.ay[p] = float(getattr(s, "aper_y", np.zeros(3))[p])
             psf_map = getattr(s, "psf_map", None)
             if psf_map is not None:
                 lt = np.ascontiguousarray(psf_map.field_lt, dtype=np.float64)

@@ -158,22 +158,28 @@ double oracle_blaze(const oracle_slice* s, double lam) {
   return sc * sc;
 }
 
+int oracle_points(const oracle_slice* s) { return s->n_slit * (s->n_aper > 1 ? s->n_aper : 1); }
+
 /* Sample j of n_lambda sits at the centre of the j-th equal bin of [lambda_lo, lambda_hi]
  * (the wavelength grid of Sec. 2); the polynomial variable is that wavelength normalised
  * to [-1, 1].  Slit point k of n_slit sits at the centre of the k-th equal bin of [-1, 1].
  * The weight is flux density x bin width x slit weight (Sec. 2.1: normalised profile times
- * the photons in the sample's wavelength range). */
-void oracle_map(const oracle_slice* s, int j, int k, double* x_c, double* y_c, double* sig_x,
+ * the photons in the sample's wavelength range).  For a 2-D fiber, point kk is slit point
+ * k = kk % n_slit of aperture row l = kk / n_slit, at t_l = -1 + (2l + 1)/n_aper, and its
+ * image moves by t_l (ax(lt), ay(lt)). */
+void oracle_map(const oracle_slice* s, int j, int kk, double* x_c, double* y_c, double* sig_x,
                 double* sig_y, double* weight) {
+  const int k = kk % s->n_slit, l = kk / s->n_slit;
   double dl = (s->lambda_hi - s->lambda_lo) / s->n_lambda;
   double lam = s->lambda_lo + (j + 0.5) * dl;
   double lt = 2.0 * (lam - s->lambda_lo) / (s->lambda_hi - s->lambda_lo) - 1.0;
   double sk = -1.0 + (2.0 * k + 1.0) / s->n_slit;
-  *x_c = poly2(s->cx, s->degree, lt, sk);
-  *y_c = poly2(s->cy, s->degree, lt, sk);
+  double tl = s->n_aper > 1 ? -1.0 + (2.0 * l + 1.0) / s->n_aper : 0.0;
+  *x_c = poly2(s->cx, s->degree, lt, sk) + tl * quad(s->ax, lt);
+  *y_c = poly2(s->cy, s->degree, lt, sk) + tl * quad(s->ay, lt);
   *sig_x = quad(s->sx, lt);
   *sig_y = quad(s->sy, lt);
-  *weight = s->flux[j] * dl * s->u[k] * oracle_blaze(s, lam);
+  *weight = s->flux[j] * dl * s->u[kk] * oracle_blaze(s, lam);
 }
 
 /* Window rule: the K x K window is centred on the pixel containing the mapped point;
@@ -339,7 +345,7 @@ void oracle_stamp(const oracle_slice* s, int psf, int j, int k, double* out, int
 int oracle_window_ties(const oracle_slice* s, double margin, int max_out, int* out) {
   int n = 0;
   for (int j = 0; j < s->n_lambda; ++j)
-    for (int k = 0; k < s->n_slit; ++k) {
+    for (int k = 0; k < oracle_points(s); ++k) {
       double c[2], sx, sy, w;
       oracle_map(s, j, k, &c[0], &c[1], &sx, &sy, &w);
       for (int a = 0; a < 2; ++a) {
@@ -378,7 +384,7 @@ static int n_coeffs(int d) { return (d + 1) * (d + 2) / 2; }
 
 static int valid_slice(const oracle_slice* s, int n_det) {
   if (s->detector < 0 || s->detector >= n_det) return 0;
-  if (s->K < 1 || s->K % 2 == 0 || s->n_lambda < 0 || s->n_slit < 0 || s->degree < 0) return 0;
+  if (s->K < 1 || s->K % 2 == 0 || s->n_lambda < 0 || s->n_slit < 0 || s->degree < 0 || s->n_aper < 0) return 0;
   if (!(s->lambda_hi > s->lambda_lo)) return 0;
   return 1;
 }
@@ -388,7 +394,7 @@ static void render_slice(const oracle_slice* s, int psf, int H, int W, band_t* b
   int K = s->K;
   int xmin = W, xmax = -1, ymin = H, ymax = -1;
   for (int j = 0; j < s->n_lambda; ++j)
-    for (int k = 0; k < s->n_slit; ++k) {
+    for (int k = 0; k < oracle_points(s); ++k) {
       double xc, yc, sx, sy, w;
       oracle_map(s, j, k, &xc, &yc, &sx, &sy, &w);
       int i0 = window_origin(xc, K), r0 = window_origin(yc, K);
@@ -412,7 +418,7 @@ static void render_slice(const oracle_slice* s, int psf, int H, int W, band_t* b
   double* st = (double*)malloc(sizeof(double) * K * K);
   const double dl = (s->lambda_hi - s->lambda_lo) / s->n_lambda;
   for (int j = 0; j < s->n_lambda; ++j)
-    for (int k = 0; k < s->n_slit; ++k) {
+    for (int k = 0; k < oracle_points(s); ++k) {
       int i0, r0;
       if (psf == ORACLE_PSF_TABLE) {
         double xc, yc, sx, sy, w;
@@ -482,7 +488,7 @@ static void slice_grad(const oracle_slice* s, int H, int W, const double* R, dou
   for (int c = 0; c < nc; ++c) gcx[c] = gcy[c] = 0.0;
   for (int p = 0; p < 3; ++p) gsx[p] = gsy[p] = 0.0;
   for (int j = 0; j < s->n_lambda; ++j)
-    for (int k = 0; k < s->n_slit; ++k) {
+    for (int k = 0; k < oracle_points(s); ++k) {
       double xc, yc, sx, sy, w;
       oracle_map(s, j, k, &xc, &yc, &sx, &sy, &w);
       int i0 = window_origin(xc, K), r0 = window_origin(yc, K);
@@ -513,7 +519,7 @@ static void slice_grad(const oracle_slice* s, int H, int W, const double* R, dou
       double dl = (s->lambda_hi - s->lambda_lo) / s->n_lambda;
       double lam = s->lambda_lo + (j + 0.5) * dl;
       double lt = 2.0 * (lam - s->lambda_lo) / (s->lambda_hi - s->lambda_lo) - 1.0;
-      double sk = -1.0 + (2.0 * k + 1.0) / s->n_slit;
+      double sk = -1.0 + (2.0 * (k % s->n_slit) + 1.0) / s->n_slit;  /* the point's slit coordinate */
       for (int a = 0; a <= s->degree; ++a)
         for (int b = 0; a + b <= s->degree; ++b) {
           double mono = pow(lt, a) * pow(sk, b);

@@ -36,11 +36,18 @@ typedef struct {
   double sx[3];     /* PSF width polynomial (quadratic in lt), pixels */
   double sy[3];
   double theta;     /* rotation of the elliptical PSF axes, radians */
-  const double* u;  /* n_slit slit weights */
+  const double* u;  /* slit weights: n_slit of them, or n_slit per aperture row (row-major) */
   const double* flux; /* n_lambda flux samples (photons / Angstrom) at the bin centres */
   double blaze_order;  /* blaze B(lambda) = sinc^2(m (1 - lambda_b / lambda)) weights every
                           sample (0 = none); lambda_b = blaze_lambda */
   double blaze_lambda;
+  /* Two-dimensional fiber sub-aperture (Sec. 2.2: each image is the fiber's spatial profile
+   * convolved with the PSF; n_aper <= 1: a one-dimensional pseudo-slit in s).  With n_aper > 1
+   * the sub-aperture points are (s_k, t_l), t_l = -1 + (2l + 1)/n_aper at the row centres, with
+   * weights u[l n_slit + k], and the point's image moves by t_l (ax(lt), ay(lt)) px, ax and ay
+   * quadratics in lt (the fiber image's half-extent along its second axis). */
+  int n_aper;
+  double ax[3], ay[3];
   /* ORACLE_PSF_TABLE: tabulated PSF maps at n_field wavelengths field_lt[f] (increasing, in
    * [-1, 1]); map f is map_size^2 samples maps[f][v][u] of the PSF density at offsets
    * ((u - c)/q, (v - c)/q) px from the PSF centre, c = (map_size - 1)/2, q = map_oversample;
@@ -72,7 +79,11 @@ void oracle_epsf_window(const oracle_slice* s, int f, double phx, double phy, do
 /* Blaze weight of the slice at wavelength lam (1 when it has none). */
 double oracle_blaze(const oracle_slice* s, double lam);
 
-/* Mapped position and PSF widths of stamp (j, k) of one order-slice. */
+/* Sub-aperture points of an order-slice: n_slit, or n_slit x n_aper for a 2-D fiber; a
+ * point index kk stands for slit point kk % n_slit of aperture row kk / n_slit. */
+int oracle_points(const oracle_slice* s);
+
+/* Mapped position and PSF widths of stamp (j, kk) of one order-slice (kk a point index). */
 void oracle_map(const oracle_slice* s, int j, int k, double* x_c, double* y_c, double* sig_x,
                 double* sig_y, double* weight);
 

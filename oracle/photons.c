@@ -23,9 +23,15 @@
  * Every random number is keyed by the seed and indexed by (bin, slice, photon, stream), so
  * the frame does not depend on the order of evaluation.  Unlike the stamps, the PSF here is
  * not truncated to a window.
+ *
+ * A two-dimensional fiber (n_aper > 1) counts as n_aper order-slices, one per aperture row l,
+ * numbered in model order (slice i's rows follow the rows of the slices before it): row l has
+ * the slit weights u[l n_slit + k] and every one of its photons sits at t_l = -1 + (2l + 1) /
+ * n_aper, its image moved by t_l (ax(lt), ay(lt)).
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include "oracle.h"
@@ -55,17 +61,29 @@ int oracle_render_photons(int n_det, const int* H, const int* W, int n_slices, c
     if (s[i].detector < 0 || s[i].detector >= n_det || s[i].n_lambda < 1 || s[i].n_slit < 1) return -1;
   (void)n_coeffs;
   uint64_t tot = 0;
-  /* slices in parallel; integer counts, so the result does not depend on the threads */
+  int n_rows = 0;  /* (slice, aperture row) pairs: the photon streams' slice index */
+  for (int i = 0; i < n_slices; ++i) n_rows += s[i].n_aper > 1 ? s[i].n_aper : 1;
+  int* row_slice = (int*)malloc(sizeof(int) * (n_rows > 0 ? n_rows : 1));
+  int* row_l = (int*)malloc(sizeof(int) * (n_rows > 0 ? n_rows : 1));
+  for (int i = 0, r = 0; i < n_slices; ++i)
+    for (int l = 0; l < (s[i].n_aper > 1 ? s[i].n_aper : 1); ++l, ++r) {
+      row_slice[r] = i;
+      row_l[r] = l;
+    }
+  /* rows in parallel; integer counts, so the result does not depend on the threads */
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : tot)
 #endif
-  for (int i = 0; i < n_slices; ++i) {
-    const oracle_slice* S = &s[i];
+  for (int i = 0; i < n_rows; ++i) {
+    const oracle_slice* S = &s[row_slice[i]];
+    const int l = row_l[i];
+    const double* u = S->u + (size_t)l * S->n_slit;
+    const double tl = S->n_aper > 1 ? -1.0 + (2.0 * l + 1.0) / S->n_aper : 0.0;
     const int h = H[S->detector], w = W[S->detector];
     uint32_t* frame = counts[S->detector];
     const double dl = (S->lambda_hi - S->lambda_lo) / S->n_lambda;
     double U = 0.0;
-    for (int k = 0; k < S->n_slit; ++k) U += S->u[k];
+    for (int k = 0; k < S->n_slit; ++k) U += u[k];
     const double c = cos(S->theta), sn = sin(S->theta);
     for (int j = 0; j < S->n_lambda; ++j) {
       const double lam_j = S->lambda_lo + (j + 0.5) * dl;  /* bin centre: the blaze weight */
@@ -79,14 +97,15 @@ int oracle_render_photons(int n_det, const int* H, const int* W, int n_slices, c
         const double v = oracle_uniform53(wa[0], wa[1]), t = oracle_uniform53(wa[2], wa[3]);
         const double cu = oracle_uniform53(wb[0], wb[1]) * U;
         int k = 0;
-        double acc = S->u[0];
+        double acc = u[0];
         while (cu > acc && k < S->n_slit - 1) {
           ++k;
-          acc += S->u[k];
+          acc += u[k];
         }
         const double lt = (2.0 * ((double)j + v) - S->n_lambda) / S->n_lambda;
         const double sk = (2.0 * ((double)k + t) - S->n_slit) / S->n_slit;
-        const double xc = poly(S->cx, S->degree, lt, sk), yc = poly(S->cy, S->degree, lt, sk);
+        const double xc = poly(S->cx, S->degree, lt, sk) + tl * (S->ax[0] + S->ax[1] * lt + S->ax[2] * lt * lt);
+        const double yc = poly(S->cy, S->degree, lt, sk) + tl * (S->ay[0] + S->ay[1] * lt + S->ay[2] * lt * lt);
         const double sa = S->sx[0] + S->sx[1] * lt + S->sx[2] * lt * lt;
         const double sb = S->sy[0] + S->sy[1] * lt + S->sy[2] * lt * lt;
         double z1, z2;
@@ -113,6 +132,8 @@ int oracle_render_photons(int n_det, const int* H, const int* W, int n_slices, c
       }
     }
   }
+  free(row_slice);
+  free(row_l);
   if (total) *total = tot;
   return 0;
 }

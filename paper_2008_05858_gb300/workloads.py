@@ -81,6 +81,12 @@ class OrderSlice:
     blaze_order: float = 0.0   # echelle order of the blaze function (0: no blaze)
     blaze_lambda: float = 0.0  # its blaze wavelength (Angstrom)
     psf_map: "PsfMap | None" = None  # tabulated PSF (models with psf = PSF_TABLE)
+    # two-dimensional fiber sub-aperture: n_aper rows t_l at the bin centres of [-1, 1]
+    # (0 or 1: a one-dimensional pseudo-slit), slit_weights then n_slit per row (row-major), and
+    # the image of row l moved by t_l (aper_x(lt), aper_y(lt)) px, quadratics in lt
+    n_aper: int = 0
+    aper_x: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(3))
+    aper_y: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(3))
 
     def copy(self) -> "OrderSlice":
         return dataclasses.replace(
@@ -91,7 +97,14 @@ class OrderSlice:
             sigma_x=self.sigma_x.copy(),
             sigma_y=self.sigma_y.copy(),
             slit_weights=self.slit_weights.copy(),
+            aper_x=np.array(self.aper_x, dtype=np.float64),
+            aper_y=np.array(self.aper_y, dtype=np.float64),
         )
+
+    @property
+    def n_points(self) -> int:
+        """Sub-aperture points: n_slit, or n_slit x n_aper for a 2-D fiber."""
+        return self.n_slit * (self.n_aper if self.n_aper > 1 else 1)
 
 
 @dataclass
@@ -133,6 +146,26 @@ def psf_maps(s: "OrderSlice", *, n_field: int = 5, oversample: float = 10.0, hal
     return PsfMap(lt, maps, oversample)
 
 
+def with_round_fiber(model: "OpticalModel", n_aper: int = 8, n_slit: int = 8, extent_x: float = 3.6,
+                     tilt_y: float = 0.3) -> "OpticalModel":
+    """The model with every slice's fiber a round two-dimensional sub-aperture: an n_slit x n_aper
+    grid of points at the bin centres of [-1, 1]^2 weighted by the unit disk (each slice keeping
+    its total slit weight), the second axis imaged along the dispersion with half-extent
+    extent_x px (slowly varying with wavelength) and a small cross-dispersion tilt tilt_y px."""
+    m = model.copy()
+    s_ = (2 * np.arange(n_slit) + 1 - n_slit) / n_slit
+    t_ = (2 * np.arange(n_aper) + 1 - n_aper) / n_aper
+    disk = ((t_[:, None] ** 2 + s_[None, :] ** 2) <= 1.0).astype(np.float64)
+    for s in m.slices:
+        tot = float(np.sum(s.slit_weights))
+        s.n_slit = n_slit
+        s.n_aper = n_aper
+        s.slit_weights = (disk / disk.sum() * tot).ravel()
+        s.aper_x = np.array([extent_x, 0.04 * extent_x, 0.0])
+        s.aper_y = np.array([tilt_y, 0.0, 0.0])
+    return m
+
+
 def with_psf_maps(model: "OpticalModel", **kw) -> "OpticalModel":
     """The model with every slice's PSF replaced by synthetic tabulated maps (psf_maps)."""
     m = model.copy()
@@ -155,11 +188,11 @@ class OpticalModel:
 
     @property
     def n_stamps(self) -> int:
-        return int(sum(s.n_lambda * s.n_slit for s in self.slices))
+        return int(sum(s.n_lambda * s.n_points for s in self.slices))
 
     @property
     def n_deposits(self) -> int:
-        return int(sum(s.n_lambda * s.n_slit * s.K * s.K for s in self.slices))
+        return int(sum(s.n_lambda * s.n_points * s.K * s.K for s in self.slices))
 
     @property
     def fibers(self) -> List[int]:
