@@ -100,7 +100,7 @@ typedef struct {
                           every wavelength sample (about |theta| <= 20 deg for widths in
                           [1.2, 2.0] px): the renderers expand the conditional profile of
                           y given x in eps * tau over one pixel column */
-  const double* slit_weights; /* n_slit weights u_k (finite, >= 0) */
+  const double* slit_weights; /* n_slit weights u_k (finite), per aperture row with n_aper > 1 */
   double blaze_order;  /* echelle blaze of the order (the paper computes each order's blaze
                           profile analytically, Sec. 4.2): every sample's weight is multiplied by
                           B(lambda) = sinc^2(nu), nu = blaze_order * (1 - blaze_lambda / lambda),
@@ -123,6 +123,19 @@ typedef struct {
   double map_oversample;    /* q: samples per pixel, an integer 1..32;
                                n_field x (q + 1)^2 must stay <= 65535 */
   const double* maps;       /* n_field * M * M densities, finite, >= 0, each map's sum > 0 */
+  /* Two-dimensional fiber sub-aperture (Sec. 2.2: each fiber image is the fiber's spatial
+   * profile convolved with the PSF).  n_aper <= 1: a one-dimensional pseudo-slit in s, and
+   * slit_weights holds n_slit values.  n_aper > 1: aperture rows t_l = -1 + (2l + 1)/n_aper;
+   * slit_weights holds n_slit values per row, row-major (u[l n_slit + k]), and the image of
+   * point (s_k, t_l) is the pseudo-slit's at s_k moved by t_l (aper_x(lt), aper_y(lt)) px,
+   * aper_x and aper_y quadratics c0 + c1 lt + c2 lt^2.  The library renders such a slice as
+   * n_aper one-dimensional slices, one per row, whose lt^q s^0 coefficients are moved by
+   * t_l aper_q (their degree raised to 2 where aper has a quadratic term): the stamp numbering
+   * of e2e_window_origins and the photon renderer's streams count those rows as slices, in
+   * model order.  The aperture itself (aper_x, aper_y) is not differentiated by the adjoint. */
+  int32_t n_aper;           /* 0..64 */
+  double aper_x[3];
+  double aper_y[3];
 } e2e_order_slice;
 
 typedef struct {

@@ -64,6 +64,7 @@ class e2e_order_slice(C.Structure):
         ("slit_weights", C.POINTER(C.c_double)), ("blaze_order", C.c_double), ("blaze_lambda", C.c_double),
         ("n_field", C.c_int32), ("field_lt", C.POINTER(C.c_double)), ("map_size", C.c_int32),
         ("map_oversample", C.c_double), ("maps", C.POINTER(C.c_double)),
+        ("n_aper", C.c_int32), ("aper_x", C.c_double * 3), ("aper_y", C.c_double * 3),
     ]
 
 
@@ -242,6 +243,10 @@ class _ModelDesc:
             o.theta = float(s.theta)
             o.blaze_order = float(getattr(s, "blaze_order", 0.0))
             o.blaze_lambda = float(getattr(s, "blaze_lambda", 0.0))
+            o.n_aper = int(getattr(s, "n_aper", 0))
+            for p in range(3):
+                o.aper_x[p] = float(getattr(s, "aper_x", np.zeros(3))[p])
+                o.aper_y[p] = float(getattr(s, "aper_y", np.zeros(3))[p])
             pm = getattr(s, "psf_map", None)
             if pm is not None:
                 lt = np.ascontiguousarray(pm.field_lt, dtype=np.float64)

@@ -122,6 +122,14 @@ struct Model {
   int64_t n_stamps = 0;  // stamps of all slices (the length of a window-origin list)
   std::vector<int> Ks;    // distinct K values
   Plan plan;
+  // 2-D fiber sub-apertures: the caller's ("parent") slices and the one-dimensional slices,
+  // one per aperture row, the library renders in their place (sub-slice q of parent
+  // parent_of[q], row t_of[q]); identity when no slice has n_aper > 1
+  bool expanded = false;
+  std::vector<int> parent_of, first_sub, parent_nc, parent_coef_off;
+  std::vector<double> t_of, apx, apy;  // apx/apy: 3 per parent
+  int parent_coef_total = 0;
+  int* d_fold = nullptr;  // first_sub | sub coef_off | parent coef_off | parent nc (adjoint folding)
 };
 
 struct Spectrum {
@@ -280,7 +288,10 @@ int validate_slice(const e2e_order_slice& s, int n_det, int psf, int idx) {
   if (!finite_all(s.cx, nc) || !finite_all(s.cy, nc)) return bad("non-finite mapping coefficient");
   if (!finite_all(s.sigma_x, 3) || !finite_all(s.sigma_y, 3)) return bad("non-finite PSF width coefficient");
   if (quad_min(s.sigma_x) <= 0 || quad_min(s.sigma_y) <= 0) return bad("PSF width must stay > 0 on [-1, 1]");
-  if (!finite_all(s.slit_weights, s.n_slit)) return bad("non-finite slit weight");
+  if (s.n_aper < 0 || s.n_aper > 64) return bad("n_aper must be 0..64");
+  if (!finite_all(s.aper_x, 3) || !finite_all(s.aper_y, 3)) return bad("non-finite aperture displacement");
+  if (!finite_all(s.slit_weights, (int64_t)s.n_slit * (s.n_aper > 1 ? s.n_aper : 1)))
+    return bad("non-finite slit weight");
   if (!std::isfinite(s.blaze_order) || (s.blaze_order != 0.0 && !(s.blaze_lambda > 0.0 && std::isfinite(s.blaze_lambda))))
     return bad("blaze: finite order and a positive, finite blaze wavelength required");
   if (psf == E2E_PSF_TABLE) {
@@ -348,6 +359,7 @@ void free_model(Model* m) {
   cudaFree(m->d_T64);
   cudaFree(m->d_T32);
   cudaFree(m->d_dims);
+  cudaFree(m->d_fold);
   free_plan(m->plan);
 }
 
@@ -1104,22 +1116,101 @@ void e2e_destroy(e2e_ctx* ctx) {
   delete ctx;
 }
 
-int e2e_load_model(e2e_ctx* ctx, const e2e_model_desc* desc, uint64_t* model_id) {
-  NvtxRange nvtx_("e2e load model");
-  if (!ctx || !desc || !model_id) return fail(E2E_EINVAL, "null argument");
-  if (desc->n_detectors < 1 || !desc->height || !desc->width) return fail(E2E_EINVAL, "need >= 1 detector");
-  if (desc->n_slices < 0 || (desc->n_slices > 0 && !desc->slices)) return fail(E2E_EINVAL, "bad slice list");
-  if (desc->psf != E2E_PSF_SEPARABLE && desc->psf != E2E_PSF_ELLIPTICAL && desc->psf != E2E_PSF_TABLE)
-    return fail(E2E_EINVAL, "bad psf kind");
-  for (int d = 0; d < desc->n_detectors; ++d)
-    if (desc->height[d] < 1 || desc->width[d] < 1 || desc->height[d] > 16000 || desc->width[d] > 16000)
-      return fail(E2E_EINVAL, "detector size must be 1..16000 px");
+// The one-dimensional slices that render a model's 2-D fibers: parent slice p with n_aper > 1
+// becomes one slice per aperture row l, its coefficients of lt^q s^0 moved by t_l aper_q
+// (degree raised to 2 where the aperture has a quadratic term, to 1 for a linear one) and its
+// slit weights the row's.  cx, cy: parent coefficient arrays (caller layout) or nullptr for
+// the descriptors' own.  Descriptors point into `store`.
+void expand_fibers(const e2e_model_desc* desc, const double* cx_in, const double* cy_in,
+                   std::vector<e2e_order_slice>& out, std::vector<std::vector<double>>& store, Model* m) {
+  out.clear();
+  store.clear();
+  m->parent_of.clear();
+  m->first_sub.assign(1, 0);
+  m->parent_nc.clear();
+  m->parent_coef_off.clear();
+  m->t_of.clear();
+  m->apx.clear();
+  m->apy.clear();
+  m->expanded = false;
+  int off = 0;
   for (int i = 0; i < desc->n_slices; ++i) {
-    int rc = validate_slice(desc->slices[i], desc->n_detectors, desc->psf, i);
+    const e2e_order_slice& s = desc->slices[i];
+    const int nc = n_coeffs(s.degree);
+    m->parent_nc.push_back(nc);
+    m->parent_coef_off.push_back(off);
+    const double* pcx = cx_in ? cx_in + off : s.cx;
+    const double* pcy = cy_in ? cy_in + off : s.cy;
+    off += nc;
+    for (int q = 0; q < 3; ++q) {
+      m->apx.push_back(s.aper_x[q]);
+      m->apy.push_back(s.aper_y[q]);
+    }
+    const int rows = s.n_aper > 1 ? s.n_aper : 1;
+    if (rows > 1) m->expanded = true;
+    int deg = s.degree;
+    if (rows > 1) {
+      if (s.aper_x[2] != 0.0 || s.aper_y[2] != 0.0) deg = std::max(deg, 2);
+      else if (s.aper_x[1] != 0.0 || s.aper_y[1] != 0.0) deg = std::max(deg, 1);
+    }
+    for (int l = 0; l < rows; ++l) {
+      const double t = rows > 1 ? -1.0 + (2.0 * l + 1.0) / rows : 0.0;
+      const int ncs = n_coeffs(deg);
+      std::vector<double> ccx(ncs, 0.0), ccy(ncs, 0.0), uu(s.slit_weights + (size_t)l * s.n_slit,
+                                                        s.slit_weights + (size_t)(l + 1) * s.n_slit);
+      for (int c = 0; c < nc; ++c) {  // a coefficient's index depends on its (a, b) only
+        ccx[c] = pcx[c];
+        ccy[c] = pcy[c];
+      }
+      if (rows > 1)
+        for (int q = 0; q <= std::min(deg, 2); ++q) {
+          ccx[coeff_index(q, 0)] += t * s.aper_x[q];
+          ccy[coeff_index(q, 0)] += t * s.aper_y[q];
+        }
+      e2e_order_slice e = s;
+      e.degree = deg;
+      e.n_aper = 0;
+      store.push_back(std::move(ccx));
+      e.cx = store.back().data();
+      store.push_back(std::move(ccy));
+      e.cy = store.back().data();
+      store.push_back(std::move(uu));
+      e.slit_weights = store.back().data();
+      out.push_back(e);
+      m->parent_of.push_back(i);
+      m->t_of.push_back(t);
+    }
+    m->first_sub.push_back((int)out.size());
+  }
+  m->parent_coef_total = off;
+  // store's vectors were moved in before their data() was taken, and a later push_back moves
+  // the vector objects but not their heap buffers: the pointers stay valid
+}
+
+int e2e_load_model(e2e_ctx* ctx, const e2e_model_desc* desc_in, uint64_t* model_id) {
+  NvtxRange nvtx_("e2e load model");
+  if (!ctx || !desc_in || !model_id) return fail(E2E_EINVAL, "null argument");
+  if (desc_in->n_detectors < 1 || !desc_in->height || !desc_in->width) return fail(E2E_EINVAL, "need >= 1 detector");
+  if (desc_in->n_slices < 0 || (desc_in->n_slices > 0 && !desc_in->slices)) return fail(E2E_EINVAL, "bad slice list");
+  if (desc_in->psf != E2E_PSF_SEPARABLE && desc_in->psf != E2E_PSF_ELLIPTICAL && desc_in->psf != E2E_PSF_TABLE)
+    return fail(E2E_EINVAL, "bad psf kind");
+  for (int d = 0; d < desc_in->n_detectors; ++d)
+    if (desc_in->height[d] < 1 || desc_in->width[d] < 1 || desc_in->height[d] > 16000 || desc_in->width[d] > 16000)
+      return fail(E2E_EINVAL, "detector size must be 1..16000 px");
+  for (int i = 0; i < desc_in->n_slices; ++i) {
+    int rc = validate_slice(desc_in->slices[i], desc_in->n_detectors, desc_in->psf, i);
     if (rc != E2E_OK) return rc;
   }
   DeviceGuard g(ctx->device);
   auto m = std::make_unique<Model>();
+  // 2-D fibers: render the one-dimensional slice of each aperture row
+  std::vector<e2e_order_slice> ex;
+  std::vector<std::vector<double>> ex_store;
+  expand_fibers(desc_in, nullptr, nullptr, ex, ex_store, m.get());
+  e2e_model_desc dexp = *desc_in;
+  dexp.n_slices = (int32_t)ex.size();
+  dexp.slices = ex.data();
+  const e2e_model_desc* desc = &dexp;
   m->n_det = desc->n_detectors;
   m->psf = desc->psf;
   m->H.assign(desc->height, desc->height + m->n_det);
@@ -1211,6 +1302,13 @@ int e2e_load_model(e2e_ctx* ctx, const e2e_model_desc* desc, uint64_t* model_id)
   m->n_bins = bin_off.back();
   m->bin_off = bin_off;
   int rc = upload(&m->d_slices, ds.data(), ds.size());
+  if (rc == E2E_OK && m->expanded) {  // the adjoint's gradient folding: sub-slices -> parents
+    std::vector<int> fold(m->first_sub);
+    for (const DevSlice& v : ds) fold.push_back(v.coef_off);
+    fold.insert(fold.end(), m->parent_coef_off.begin(), m->parent_coef_off.end());
+    fold.insert(fold.end(), m->parent_nc.begin(), m->parent_nc.end());
+    rc = upload(&m->d_fold, fold.data(), fold.size());
+  }
   if (rc == E2E_OK) rc = upload(&m->d_u, u_all.data(), u_all.size());
   if (rc == E2E_OK) rc = upload(&m->d_ucum, ucum.data(), ucum.size());
   if (rc == E2E_OK) rc = upload(&m->d_usum, usum.data(), usum.size());
@@ -1610,12 +1708,26 @@ int e2e_render_adjoint(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const ui
   if (rc != E2E_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t ns = m->slices.size();
+  Scratch sc{{}, st};
+  // 2-D fibers: gradients of the aperture rows' slices in scratch, folded into the caller's
+  // (parent) layout at the end
+  double *ucx = g_cx, *ucy = g_cy, *usx = g_sx, *usy = g_sy;
+  if (m->expanded) {
+    const int np = (int)m->parent_nc.size();
+    E2E_CK(cudaMemsetAsync(ucx, 0, sizeof(double) * m->parent_coef_total, st));
+    E2E_CK(cudaMemsetAsync(ucy, 0, sizeof(double) * m->parent_coef_total, st));
+    E2E_CK(cudaMemsetAsync(usx, 0, sizeof(double) * 3 * np, st));
+    E2E_CK(cudaMemsetAsync(usy, 0, sizeof(double) * 3 * np, st));
+    E2E_CK(sc.get((void**)&g_cx, sizeof(double) * std::max(1, m->coef_total)));
+    E2E_CK(sc.get((void**)&g_cy, sizeof(double) * std::max(1, m->coef_total)));
+    E2E_CK(sc.get((void**)&g_sx, sizeof(double) * 3 * std::max<size_t>(1, ns)));
+    E2E_CK(sc.get((void**)&g_sy, sizeof(double) * 3 * std::max<size_t>(1, ns)));
+  }
   E2E_CK(cudaMemsetAsync(g_cx, 0, sizeof(double) * m->coef_total, st));
   E2E_CK(cudaMemsetAsync(g_cy, 0, sizeof(double) * m->coef_total, st));
   E2E_CK(cudaMemsetAsync(g_sx, 0, sizeof(double) * 3 * ns, st));
   E2E_CK(cudaMemsetAsync(g_sy, 0, sizeof(double) * 3 * ns, st));
   if (ns == 0 || P.items.empty()) return E2E_OK;
-  Scratch sc{{}, st};
   rc = blaze_scratch(m, table, sc, st);
   if (rc != E2E_OK) return rc;
   const double** d_table = nullptr;
@@ -1639,16 +1751,51 @@ int e2e_render_adjoint(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const ui
                           dtype == E2E_F32 ? 0 : 1, P.B, P.nk_max, parts, g_cx, g_cy, g_sx, g_sy, smem, st,
                           reinterpret_cast<const int2*>(frozen_windows)));
   }
+  if (m->expanded)
+    E2E_CK(launch_fold_gradients((int)m->parent_nc.size(), (int)ns, m->d_fold, g_cx, g_cy, g_sx, g_sy, ucx, ucy, usx,
+                                 usy, st));
   return E2E_OK;
 }
 
-int e2e_update_model(e2e_ctx* ctx, uint64_t model_id, const double* cx, const double* cy, const double* sx,
-                     const double* sy) {
-  if (!ctx || !cx || !cy || !sx || !sy) return fail(E2E_EINVAL, "null argument");
+int e2e_update_model(e2e_ctx* ctx, uint64_t model_id, const double* cx_in, const double* cy_in, const double* sx_in,
+                     const double* sy_in) {
+  if (!ctx || !cx_in || !cy_in || !sx_in || !sy_in) return fail(E2E_EINVAL, "null argument");
   DeviceGuard g(ctx->device);
   std::lock_guard<std::mutex> lk(ctx->mu);
   Model* m = find_model(ctx, model_id);
   if (!m) return fail(E2E_ENOTFOUND, "unknown model id");
+  // 2-D fibers: the caller's coefficients are the parents'; each aperture row's slice takes
+  // them plus its displacement (as at load), and the parents' widths
+  std::vector<double> ecx, ecy, esx, esy;
+  const double *cx = cx_in, *cy = cy_in, *sx = sx_in, *sy = sy_in;
+  if (m->expanded) {
+    ecx.assign(m->coef_total, 0.0);
+    ecy.assign(m->coef_total, 0.0);
+    esx.assign(3 * m->slices.size(), 0.0);
+    esy.assign(3 * m->slices.size(), 0.0);
+    for (size_t q = 0; q < m->slices.size(); ++q) {
+      const int p = m->parent_of[q], off = m->dev[q].coef_off, po = m->parent_coef_off[p];
+      const int ncs = n_coeffs(m->slices[q].d.degree);
+      for (int c = 0; c < std::min(ncs, m->parent_nc[p]); ++c) {
+        ecx[off + c] = cx_in[po + c];
+        ecy[off + c] = cy_in[po + c];
+      }
+      const double t = m->t_of[q];
+      if (t != 0.0)
+        for (int a = 0; a <= std::min(m->slices[q].d.degree, 2); ++a) {
+          ecx[off + coeff_index(a, 0)] += t * m->apx[3 * p + a];
+          ecy[off + coeff_index(a, 0)] += t * m->apy[3 * p + a];
+        }
+      for (int k = 0; k < 3; ++k) {
+        esx[3 * q + k] = sx_in[3 * p + k];
+        esy[3 * q + k] = sy_in[3 * p + k];
+      }
+    }
+    cx = ecx.data();
+    cy = ecy.data();
+    sx = esx.data();
+    sy = esy.data();
+  }
   // validate on copies first so a rejected update leaves the model untouched
   std::vector<SliceHost> ns = m->slices;
   std::vector<DevSlice> dv = m->dev;

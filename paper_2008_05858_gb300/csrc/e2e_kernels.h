@@ -95,6 +95,9 @@ cudaError_t launch_photons(const DevSlice* slices, int n_slices, const double* u
                            cudaStream_t st);
 
 size_t adjoint_smem_bytes(int max_area, int max_deg, int nk_max, int nj_max);
+cudaError_t launch_fold_gradients(int n_parent, int n_sub, const int* fold, const double* gcx_e, const double* gcy_e,
+                                  const double* gsx_e, const double* gsy_e, double* gcx, double* gcy, double* gsx,
+                                  double* gsy, cudaStream_t st);
 int adjoint_parts(int max_tasks);  // CTAs per item sharing its warp tasks
 cudaError_t launch_adjoint(int K, const DevSlice* slices, const double* const* flux_tab, const double* u_all,
                            const Item* items, int n_items, const void* const* dldi, const int64_t* pitch, int dtype,

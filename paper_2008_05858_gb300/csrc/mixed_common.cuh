@@ -121,6 +121,34 @@ __device__ __forceinline__ void map_xy_df(const float4* P, int d, float2 s, floa
   lo = ql;
 }
 
+// map_xy_df for coefficients held in registers (P[0..d], d <= 8): the loop unrolled over
+// b = 8..0 with every index static, doing exactly map_xy_df's operations.
+__device__ __forceinline__ void map_xy_df_regs(const float4 (&P)[9], int d, float2 s, float2& hi, float2& lo) {
+  float2 qh = make_float2(0.f, 0.f), ql = qh;
+  const float2 sh = make_float2(s.x, s.x), sl = make_float2(s.y, s.y);
+#pragma unroll
+  for (int b = 8; b >= 0; --b) {
+    if (b == d) {
+      qh = make_float2(P[b].x, P[b].y);
+      ql = make_float2(P[b].z, P[b].w);
+    } else if (b < d) {
+      const float2 ph = __fmul2_rn(qh, sh);
+      float2 pe = __ffma2_rn(qh, sh, neg2(ph));
+      pe = __ffma2_rn(qh, sl, pe);
+      pe = __ffma2_rn(ql, sh, pe);
+      const float2 bh = make_float2(P[b].x, P[b].y), bl = make_float2(P[b].z, P[b].w);
+      const float2 t = __fadd2_rn(ph, bh);
+      const float2 bb = __fadd2_rn(t, neg2(ph));
+      const float2 e = __fadd2_rn(__fadd2_rn(ph, neg2(__fadd2_rn(t, neg2(bb)))), __fadd2_rn(bh, neg2(bb)));
+      const float2 e2 = __fadd2_rn(e, __fadd2_rn(pe, bl));
+      qh = __fadd2_rn(t, e2);
+      ql = __fadd2_rn(e2, neg2(__fadd2_rn(qh, neg2(t))));
+    }
+  }
+  hi = qh;
+  lo = ql;
+}
+
 // Window-centre pixels and FP32 offsets of a stamp (map_xy_df, then split_coord_df).
 __device__ __forceinline__ void map_stamp_df(const float4* P, int d, float2 s, int& ci, float& fx, int& ri,
                                              float& fy) {

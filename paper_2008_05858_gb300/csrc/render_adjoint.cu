@@ -143,8 +143,6 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
   double* red = reinterpret_cast<double*>(smem + o_red);                // [warps][ncoef]
   double* tabS = red + kAdjWarps * ncoef;                               // s of the item's slit points
   float2* tabU = reinterpret_cast<float2*>(tabS + a.nk_max);           // their weights, (hi, lo)
-  // P_b(lt) of the item's samples as split_xy pairs, on a 16-byte boundary
-  float4* tabP = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(tabU + a.nk_max) + 15) & ~(uintptr_t)15);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   {
     const int64_t P = a.pitch[S.det];
@@ -160,13 +158,6 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
     for (int kk = tid; kk < it.nk; kk += kAdjThreads) {
       tabS[kk] = (double)(2 * (it.k0 + kk) + 1 - S.n_slit) * inv_ns;
       tabU[kk] = split_pair(u[it.k0 + kk]);
-    }
-    // the mapping's per-sample coefficients, as the planner forms them
-    const double inv_nl0 = 1.0 / (double)S.n_lambda;
-    for (int jj = tid; jj < it.nj; jj += kAdjThreads) {
-      const double lt0 = (double)(2 * (it.j0 + jj) + 1 - S.n_lambda) * inv_nl0;
-      for (int b = 0; b <= d; ++b)
-        tabP[jj * (d + 1) + b] = split_xy(poly_lt_for_b(S.cx, d, b, lt0), poly_lt_for_b(S.cy, d, b, lt0));
     }
   }
   __syncthreads();
@@ -185,7 +176,10 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
     double lt = 0.0;
     if (jvalid) {
       lt = (double)(2 * j + 1 - S.n_lambda) * inv_nl;
-      const float4* P = tabP + jj * (d + 1);  // P_b(lt) of x and y (the planner's mapping)
+      float4 P[9];  // P_b(lt) of x and y as split_xy pairs (the planner's mapping), degree <= 8
+#pragma unroll
+      for (int b = 0; b <= 8; ++b)
+        P[b] = b <= d ? split_xy(poly_lt_for_b(S.cx, d, b, lt), poly_lt_for_b(S.cy, d, b, lt)) : make_float4(0.f, 0.f, 0.f, 0.f);
       const double sgx = fma(fma(S.sx[2], lt, S.sx[1]), lt, S.sx[0]);
       const double sgy = fma(fma(S.sy[2], lt, S.sy[1]), lt, S.sy[0]);
       const float2 gx = split_pair(kq / sgx), gy = split_pair(kq / sgy);
@@ -197,7 +191,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
         int ci, ri;
         float fx, fy;
         float2 mh, ml;
-        map_xy_df(P, d, split_df(sd), mh, ml);
+        map_xy_df_regs(P, d, split_df(sd), mh, ml);
         split_coord_df(mh.x, ml.x, ci, fx);
         split_coord_df(mh.y, ml.y, ri, fy);
         if (ci == kOffFrame || ri == kOffFrame) continue;
@@ -330,11 +324,49 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
   }
 }
 
+// 2-D fibers: the gradients of a parent slice are the sums over its aperture rows' slices
+// (each row's mapping is the parent's plus a displacement independent of the coefficients);
+// one CTA per parent, rows summed in order.  fold = first_sub[n_parent + 1] | sub coef_off[n_sub] |
+// parent coef_off[n_parent] | parent n_coef[n_parent].
+__global__ void k_fold_gradients(int n_parent, int n_sub, const int* __restrict__ fold,
+                                 const double* __restrict__ gcx_e, const double* __restrict__ gcy_e,
+                                 const double* __restrict__ gsx_e, const double* __restrict__ gsy_e, double* gcx,
+                                 double* gcy, double* gsx, double* gsy) {
+  const int p = blockIdx.x;
+  if (p >= n_parent) return;
+  const int* first = fold;
+  const int* sub_off = fold + n_parent + 1;
+  const int* par_off = sub_off + n_sub;
+  const int* par_nc = par_off + n_parent;
+  const int q0 = first[p], q1 = first[p + 1], nc = par_nc[p];
+  for (int e = threadIdx.x; e < 2 * nc + 6; e += blockDim.x) {
+    double v = 0.0;
+    if (e < 2 * nc) {
+      const double* g = e < nc ? gcx_e : gcy_e;
+      const int c = e < nc ? e : e - nc;
+      for (int q = q0; q < q1; ++q) v += g[sub_off[q] + c];
+      (e < nc ? gcx : gcy)[par_off[p] + c] = v;
+    } else {
+      const int k = e - 2 * nc;
+      const double* g = k < 3 ? gsx_e : gsy_e;
+      for (int q = q0; q < q1; ++q) v += g[3 * q + k % 3];
+      (k < 3 ? gsx : gsy)[3 * p + k % 3] = v;
+    }
+  }
+}
+
+cudaError_t launch_fold_gradients(int n_parent, int n_sub, const int* fold, const double* gcx_e, const double* gcy_e,
+                                  const double* gsx_e, const double* gsy_e, double* gcx, double* gcy, double* gsx,
+                                  double* gsy, cudaStream_t st) {
+  if (n_parent == 0) return cudaSuccess;
+  k_fold_gradients<<<n_parent, 64, 0, st>>>(n_parent, n_sub, fold, gcx_e, gcy_e, gsx_e, gsy_e, gcx, gcy, gsx, gsy);
+  return cudaGetLastError();
+}
+
 size_t adjoint_smem_bytes(int max_area, int max_deg, int nk_max, int nj_max) {
+  (void)nj_max;
   const int nc = (max_deg + 1) * (max_deg + 2) / 2;
-  // dL/dI box, warp partials, s and u of the slit points, then (16-byte aligned) the tables
-  return (((size_t)max_area * 4 + 15) & ~(size_t)15) + (size_t)kAdjWarps * (2 * nc + 6) * 8 + (size_t)nk_max * 16 +
-         16 + (size_t)nj_max * (max_deg + 1) * 16;
+  return (((size_t)max_area * 4 + 15) & ~(size_t)15) + (size_t)kAdjWarps * (2 * nc + 6) * 8 + (size_t)nk_max * 16;
 }
 
 int adjoint_parts(int max_tasks) { return std::max(1, std::min(4, (max_tasks + kAdjWarps - 1) / kAdjWarps)); }

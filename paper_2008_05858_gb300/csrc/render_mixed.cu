@@ -46,8 +46,10 @@ __global__ void k_plan(const DevSlice* __restrict__ slices, int n_slices, const 
     const double lt = norm_sample_r(j, S.n_lambda, 1.0 / (double)S.n_lambda);
     const double inv_ns = 1.0 / (double)S.n_slit;
     float4 P[9];  // degree <= 8
-    for (int b = 0; b <= S.degree; ++b)
-      P[b] = split_xy(poly_lt_for_b(S.cx, S.degree, b, lt), poly_lt_for_b(S.cy, S.degree, b, lt));
+#pragma unroll
+    for (int b = 0; b <= 8; ++b)
+      P[b] = b <= S.degree ? split_xy(poly_lt_for_b(S.cx, S.degree, b, lt), poly_lt_for_b(S.cy, S.degree, b, lt))
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
     int xmn = 1 << 30, xmx = -(1 << 30), ymn = 1 << 30, ymx = -(1 << 30);
     int rxmn[5], rxmx[5], rymn[5], rymx[5], spx[5], spy[5];
 #pragma unroll
@@ -56,7 +58,10 @@ __global__ void k_plan(const DevSlice* __restrict__ slices, int n_slices, const 
     for (int k = k0; k < k1; ++k) {
       int ci, ri;
       float fx, fy;
-      map_stamp_df(P, S.degree, split_df(norm_sample_r(k, S.n_slit, inv_ns)), ci, fx, ri, fy);
+      float2 mh, ml;
+      map_xy_df_regs(P, S.degree, split_df(norm_sample_r(k, S.n_slit, inv_ns)), mh, ml);
+      split_coord_df(mh.x, ml.x, ci, fx);
+      split_coord_df(mh.y, ml.y, ri, fy);
       const bool on = ci != kOffFrame && ri != kOffFrame;
       if (on) {
         xmn = min(xmn, ci); xmx = max(xmx, ci); ymn = min(ymn, ri); ymx = max(ymx, ri);
