@@ -130,6 +130,7 @@ struct Model {
   std::vector<double> t_of, apx, apy;  // apx/apy: 3 per parent
   int parent_coef_total = 0;
   int* d_fold = nullptr;  // first_sub | sub coef_off | parent coef_off | parent nc (adjoint folding)
+  float4* d_stab = nullptr;  // per-sample tables of every slice (DevSlice::samples)
 };
 
 struct Spectrum {
@@ -360,6 +361,7 @@ void free_model(Model* m) {
   cudaFree(m->d_T32);
   cudaFree(m->d_dims);
   cudaFree(m->d_fold);
+  cudaFree(m->d_stab);
   free_plan(m->plan);
 }
 
@@ -533,12 +535,34 @@ int plan_bands_and_tiles(Model* m) {
   return E2E_OK;
 }
 
+// Per-sample tables (mapping coefficients in s and PSF constants at each wavelength sample)
+// of every slice, rebuilt on the device whenever the model's coefficients change.
+int build_sample_tables(Model* m) {
+  const int ns = (int)m->slices.size();
+  int64_t total = 0;
+  int max_lambda = 0;
+  std::vector<int64_t> off(ns);
+  for (int i = 0; i < ns; ++i) {
+    off[i] = total;
+    total += (int64_t)m->dev[i].n_lambda * (m->dev[i].degree + 3);
+    max_lambda = std::max(max_lambda, m->dev[i].n_lambda);
+  }
+  if (!m->d_stab) E2E_CK(cudaMalloc((void**)&m->d_stab, (size_t)total * sizeof(float4)));
+  for (int i = 0; i < ns; ++i) m->dev[i].samples = m->d_stab + off[i];
+  E2E_CK(cudaMemcpy(m->d_slices, m->dev.data(), ns * sizeof(DevSlice), cudaMemcpyHostToDevice));
+  const int psf = m->psf == E2E_PSF_ELLIPTICAL ? 1 : m->psf == E2E_PSF_TABLE ? 2 : 0;
+  E2E_CK(launch_sample_tables(m->d_slices, ns, max_lambda, psf, m->d_ts, m->d_field, 0));
+  E2E_CK(cudaDeviceSynchronize());
+  return E2E_OK;
+}
+
 int plan_model(Model* m) {
   NvtxRange nvtx_("e2e plan");
   Plan& P = m->plan;
   const int ns = (int)m->slices.size();
   const bool ellip = m->psf != E2E_PSF_SEPARABLE;  // item shape of the non-separable kernels
   if (ns == 0) return plan_bands_and_tiles(m);
+  if (int rc0 = build_sample_tables(m); rc0 != E2E_OK) return rc0;
   // ---- device pass: exact window origins of every stamp
   std::vector<int64_t> task_off(ns + 1, 0), bb_off(ns + 1, 0);
   std::vector<int> n_jb(ns), n_k16(ns);

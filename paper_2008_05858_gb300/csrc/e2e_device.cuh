@@ -28,6 +28,10 @@ struct DevSlice {
   int64_t stamp_off;             // first global stamp index of this slice (FP64 path)
   int32_t coef_off;              // offset of this slice's cx / cy in the concatenated gradients
   int32_t index;                 // position of the slice in the model
+  // per-sample table, built once per model (k_sample_tables): for wavelength sample j, the
+  // degree + 3 float4 at samples + j (degree + 3): the s-polynomial's coefficients P_b(lt_j)
+  // as split_xy pairs (b = 0..degree), then two float4 of PSF constants (see sample_tables.cu)
+  const float4* samples;
 };
 
 // A mixed-path work item: a block of wavelength samples x a block of slit points of one

@@ -77,6 +77,10 @@ cudaError_t launch_render_fp64_table(int K, int n_slices, int64_t max_stamps, co
                                      const TableSlice* ts, const double* T64, const double* field_lt,
                                      const double* const* flux_tab, const double* u_all, double* const* acc,
                                      const int64_t* pitch, cudaStream_t st);
+// per-sample mapping coefficients and PSF constants of every slice (DevSlice::samples);
+// psf 0 separable, 1 elliptical, 2 tabulated (ts and field_lt used only then)
+cudaError_t launch_sample_tables(const DevSlice* slices, int n_slices, int max_lambda, int psf, const TableSlice* ts,
+                                 const double* field_lt, cudaStream_t st);
 cudaError_t launch_flag_nonfinite(const double* p, int64_t n, int* flag, cudaStream_t st);
 cudaError_t launch_blaze(const DevSlice* slices, int n_slices, const double* const* flux_in, const int64_t* bin_off,
                          int64_t n_bins, double* out, cudaStream_t st);

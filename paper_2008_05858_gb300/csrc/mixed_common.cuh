@@ -158,6 +158,41 @@ __device__ __forceinline__ void map_stamp_df(const float4* P, int d, float2 s, i
   split_coord_df(hi.y, lo.y, ri, fy);
 }
 
+// Covariance of the rotated PSF at lt and the conditional parameters derived from it.
+struct EllipParams {
+  double vx, gx, beta, sc, eps;
+};
+
+__device__ __forceinline__ EllipParams ellip_params(const DevSlice& S, double lt) {
+  const double sa = fma(fma(S.sx[2], lt, S.sx[1]), lt, S.sx[0]);
+  const double sb = fma(fma(S.sy[2], lt, S.sy[1]), lt, S.sy[0]);
+  const double a2 = sa * sa, b2 = sb * sb, c = S.cos_t, s = S.sin_t;
+  EllipParams p;
+  p.vx = a2 * c * c + b2 * s * s;
+  const double vy = a2 * s * s + b2 * c * c;
+  const double cxy = (a2 - b2) * s * c;
+  p.gx = sqrt(p.vx);
+  p.beta = cxy / p.vx;
+  p.sc = sqrt(vy - p.beta * cxy);
+  p.eps = p.beta / p.sc;
+  return p;
+}
+
+// Field node pair and weight of normalised wavelength lt (the end node beyond the ends).
+__device__ __forceinline__ void field_weight(const double* lt_nodes, int F, double lt, int& f0, int& f1, double& wf) {
+  f0 = 0;
+  f1 = 0;
+  wf = 0.0;
+  if (lt <= lt_nodes[0]) return;
+  if (lt >= lt_nodes[F - 1]) {
+    f0 = f1 = F - 1;
+    return;
+  }
+  while (f0 + 1 < F && lt_nodes[f0 + 1] <= lt) ++f0;
+  f1 = f0 + 1;
+  wf = (lt - lt_nodes[f0]) / (lt_nodes[f1] - lt_nodes[f0]);
+}
+
 // box_deposit's fixed-point words of two values at once: the same operations on each
 // component (packed FP32x2 for the multiplies and the FMA), so the same words.
 __device__ __forceinline__ void fixed_split2(float2 val, float sc, float sc_hi, int2& hi, uint2& lo) {

@@ -168,21 +168,6 @@ __device__ __forceinline__ void phase_cell(const TableSlice& t, double ph, int& 
   tau = (r - lo) * (hi - lo < 1.0 ? 2.0 : 1.0) - 0.5;  // cells are 1 or 1/2 wide
 }
 
-// Field node pair and weight of normalised wavelength lt (the end node beyond the ends).
-__device__ __forceinline__ void field_weight(const double* lt_nodes, int F, double lt, int& f0, int& f1, double& wf) {
-  f0 = 0;
-  f1 = 0;
-  wf = 0.0;
-  if (lt <= lt_nodes[0]) return;
-  if (lt >= lt_nodes[F - 1]) {
-    f0 = f1 = F - 1;
-    return;
-  }
-  while (f0 + 1 < F && lt_nodes[f0 + 1] <= lt) ++f0;
-  f1 = f0 + 1;
-  wf = (lt - lt_nodes[f0]) / (lt_nodes[f1] - lt_nodes[f0]);
-}
-
 // ------------------------------------------------------------------ mixed precision
 
 // The biquadratic C[p][r] tau_y^p tau_x^r (rows p * 3 + r) by Horner in tau_x, then tau_y.
@@ -255,7 +240,7 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
   }
   const double* flux = a.flux_tab[S.flux_slot];
   const double* u = a.u_all + S.u_off;
-  const double inv_nl = 1.0 / (double)S.n_lambda, inv_ns = 1.0 / (double)S.n_slit;
+  const double inv_ns = 1.0 / (double)S.n_slit;
   double usum = 0.0;
   for (int kk = tid; kk < it.nk; kk += kTThreads) {
     const double uk = u[it.k0 + kk];
@@ -263,15 +248,17 @@ __global__ void __launch_bounds__(kTThreads) k_render_table(const TableArgs ta) 
     tabU[kk] = split_df(uk);
     usum += fabs(uk);
   }
+  {  // mapping coefficients and field nodes of the item's samples (per-model tables)
+    const int w = nd + 2;
+    const float4* rows = S.samples + (int64_t)it.j0 * w;
+    for (int e = tid; e < it.nj * w; e += kTThreads) {
+      const int jj = e / w, b = e - jj * w;
+      if (b < nd) tabP[jj * nd + b] = rows[e];
+      else if (b == nd) tabF[jj] = reinterpret_cast<const int4*>(rows)[e];
+    }
+  }
   double wsum = 0.0;
   for (int jj = tid; jj < it.nj; jj += kTThreads) {
-    const double lt = norm_sample_r(it.j0 + jj, S.n_lambda, inv_nl);
-    for (int b = 0; b < nd; ++b)
-      tabP[jj * nd + b] = split_xy(poly_lt_for_b(S.cx, S.degree, b, lt), poly_lt_for_b(S.cy, S.degree, b, lt));
-    int f0, f1;
-    double wf;
-    field_weight(ta.field_lt + TS.field_off, TS.n_field, lt, f0, f1, wf);
-    tabF[jj] = make_int4(f0, f1, __float_as_int((float)wf), 0);
     const double wj = flux[it.j0 + jj] * S.dlam;
     tabW[jj] = split_df(wj);
     wsum += fabs(wj);

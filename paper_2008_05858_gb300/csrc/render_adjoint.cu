@@ -163,7 +163,6 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
   __syncthreads();
   const double* flux = a.flux_tab[S.flux_slot];
   const double inv_nl = 1.0 / (double)S.n_lambda;
-  const double kq = kSqrtLog2eD * 0.70710678118654752440;
   for (int task = blockIdx.y * kAdjWarps + warp; task < ntask; task += gridDim.y * kAdjWarps) {
     const int jj = (task % njb) * 32 + lane;
     const bool jvalid = jj < it.nj;
@@ -176,13 +175,16 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
     double lt = 0.0;
     if (jvalid) {
       lt = (double)(2 * j + 1 - S.n_lambda) * inv_nl;
-      float4 P[9];  // P_b(lt) of x and y as split_xy pairs (the planner's mapping), degree <= 8
+      // P_b(lt) of x and y as split_xy pairs (the planner's mapping), degree <= 8, and the
+      // edge-argument scales, from the per-model sample tables
+      const float4* row = S.samples + (int64_t)j * (d + 3);
+      float4 P[9];
 #pragma unroll
-      for (int b = 0; b <= 8; ++b)
-        P[b] = b <= d ? split_xy(poly_lt_for_b(S.cx, d, b, lt), poly_lt_for_b(S.cy, d, b, lt)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int b = 0; b <= 8; ++b) P[b] = b <= d ? row[b] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 g = row[d + 1];
+      const float2 gx = make_float2(g.x, g.y), gy = make_float2(g.z, g.w);
       const double sgx = fma(fma(S.sx[2], lt, S.sx[1]), lt, S.sx[0]);
       const double sgy = fma(fma(S.sy[2], lt, S.sy[1]), lt, S.sy[0]);
-      const float2 gx = split_pair(kq / sgx), gy = split_pair(kq / sgy);
       const float isx = (float)(1.0 / sgx), isy = (float)(1.0 / sgy);
       const float2 wj = split_pair(flux[j] * S.dlam);
       for (int b = 0; b < nb; ++b) {

@@ -39,27 +39,6 @@ constexpr int kEThreads = 128;
 constexpr int kEWarps = kEThreads / 32;
 constexpr float kSqrt2Ln2 = 1.17741002f;         // V = w sqrt(2 ln 2) for w in log2 units
 constexpr float kTwoOverSqrt2Pi = 0.797884561f;  // 2 phi(V) / exp(-V^2 / 2)
-constexpr double kLog2e = 1.44269504088896340736;
-
-// Covariance of the rotated PSF at lt and the conditional parameters derived from it.
-struct EllipParams {
-  double vx, gx, beta, sc, eps;
-};
-
-__device__ __forceinline__ EllipParams ellip_params(const DevSlice& S, double lt) {
-  const double sa = fma(fma(S.sx[2], lt, S.sx[1]), lt, S.sx[0]);
-  const double sb = fma(fma(S.sy[2], lt, S.sy[1]), lt, S.sy[0]);
-  const double a2 = sa * sa, b2 = sb * sb, c = S.cos_t, s = S.sin_t;
-  EllipParams p;
-  p.vx = a2 * c * c + b2 * s * s;
-  const double vy = a2 * s * s + b2 * c * c;
-  const double cxy = (a2 - b2) * s * c;
-  p.gx = sqrt(p.vx);
-  p.beta = cxy / p.vx;
-  p.sc = sqrt(vy - p.beta * cxy);
-  p.eps = p.beta / p.sc;
-  return p;
-}
 
 // ------------------------------------------------------------------------------ mixed
 
@@ -118,7 +97,7 @@ __global__ void __launch_bounds__(kEThreads, 6) k_render_ellip(const MixedArgs a
   }
   const double* flux = a.flux_tab[S.flux_slot];
   const double* u = a.u_all + S.u_off;
-  const double inv_nl = 1.0 / (double)S.n_lambda, inv_ns = 1.0 / (double)S.n_slit;
+  const double inv_ns = 1.0 / (double)S.n_slit;
   double usum = 0.0;
   for (int kk = tid; kk < it.nk; kk += kEThreads) {
     const double uk = u[it.k0 + kk];
@@ -126,16 +105,17 @@ __global__ void __launch_bounds__(kEThreads, 6) k_render_ellip(const MixedArgs a
     tabU[kk] = split_df(uk);
     usum += fabs(uk);
   }
+  {  // mapping coefficients and PSF constants of the item's samples (per-model tables)
+    const int w = nd + 2;
+    const float4* rows = S.samples + (int64_t)it.j0 * w;
+    for (int e = tid; e < it.nj * w; e += kEThreads) {
+      const int jj = e / w, b = e - jj * w;
+      if (b < nd) tabP[jj * nd + b] = rows[e];
+      else tabE[2 * jj + (b - nd)] = rows[e];
+    }
+  }
   double wsum = 0.0;
   for (int jj = tid; jj < it.nj; jj += kEThreads) {
-    const double lt = norm_sample_r(it.j0 + jj, S.n_lambda, inv_nl);
-    for (int b = 0; b < nd; ++b)
-      tabP[jj * nd + b] = split_xy(poly_lt_for_b(S.cx, S.degree, b, lt), poly_lt_for_b(S.cy, S.degree, b, lt));
-    const EllipParams p = ellip_params(S, lt);
-    const double kq = kSqrtLog2eD * 0.70710678118654752440;  // edge arguments in log2 units
-    const float2 gx = split_df(kq / p.gx), gc = split_df(kq / p.sc), be = split_df(p.beta);
-    tabE[2 * jj + 0] = make_float4(gx.x, gx.y, gc.x, gc.y);
-    tabE[2 * jj + 1] = make_float4(be.x, be.y, (float)p.eps, (float)(-kLog2e / p.vx));
     const double wj = flux[it.j0 + jj] * S.dlam;
     tabW[jj] = split_df(wj * 0.25);  // the column and row integrals below are both doubled
     wsum += fabs(wj);

@@ -43,13 +43,11 @@ __global__ void k_plan(const DevSlice* __restrict__ slices, int n_slices, const 
     const int nkb = (S.n_slit + 15) / 16;
     const int64_t local = t - task_off[lo];
     const int j = (int)(local / nkb), kb = (int)(local - (int64_t)j * nkb);
-    const double lt = norm_sample_r(j, S.n_lambda, 1.0 / (double)S.n_lambda);
     const double inv_ns = 1.0 / (double)S.n_slit;
+    const float4* row = S.samples + (int64_t)j * (S.degree + 3);  // per-model sample tables
     float4 P[9];  // degree <= 8
 #pragma unroll
-    for (int b = 0; b <= 8; ++b)
-      P[b] = b <= S.degree ? split_xy(poly_lt_for_b(S.cx, S.degree, b, lt), poly_lt_for_b(S.cy, S.degree, b, lt))
-                           : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int b = 0; b <= 8; ++b) P[b] = b <= S.degree ? row[b] : make_float4(0.f, 0.f, 0.f, 0.f);
     int xmn = 1 << 30, xmx = -(1 << 30), ymn = 1 << 30, ymx = -(1 << 30);
     int rxmn[5], rxmx[5], rymn[5], rymx[5], spx[5], spy[5];
 #pragma unroll

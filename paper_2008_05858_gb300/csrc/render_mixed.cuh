@@ -38,7 +38,6 @@ struct MixedLayout {
 };
 
 
-// Two CTAs per SM (128 registers) when a lane's accumulator tile is small enough, else one.
 #ifndef E2E_MID_TILE_BLOCKS
 #define E2E_MID_TILE_BLOCKS 4
 #endif
@@ -89,7 +88,7 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
   }
   const double* flux = a.flux_tab[S.flux_slot];
   const double* u = a.u_all + S.u_off;
-  const double inv_nl = 1.0 / (double)S.n_lambda, inv_ns = 1.0 / (double)S.n_slit;
+  const double inv_ns = 1.0 / (double)S.n_slit;
   double usum = 0.0;
   for (int kk = tid; kk < it.nk; kk += kThreads) {
     const double uk = u[it.k0 + kk];
@@ -97,17 +96,17 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
     tabU[kk] = split_df(uk);
     usum += fabs(uk);
   }
+  {  // mapping coefficients and PSF constants of the item's samples (per-model tables)
+    const int w = nd + 2;
+    const float4* rows = S.samples + (int64_t)it.j0 * w;
+    for (int e = tid; e < it.nj * w; e += kThreads) {
+      const int jj = e / w, b = e - jj * w;
+      if (b < nd) tabP[jj * nd + b] = rows[e];
+      else if (b == nd) tabG[jj] = rows[e];
+    }
+  }
   double wsum = 0.0;
   for (int jj = tid; jj < it.nj; jj += kThreads) {
-    const double lt = norm_sample_r(it.j0 + jj, S.n_lambda, inv_nl);
-    for (int b = 0; b < nd; ++b)
-      tabP[jj * nd + b] = split_xy(poly_lt_for_b(S.cx, S.degree, b, lt), poly_lt_for_b(S.cy, S.degree, b, lt));
-    // edge arguments are carried in log2 units: w = (edge - centre) sqrt(log2 e) / (sqrt2 sigma)
-    const double sgx = fma(fma(S.sx[2], lt, S.sx[1]), lt, S.sx[0]);
-    const double sgy = fma(fma(S.sy[2], lt, S.sy[1]), lt, S.sy[0]);
-    const double kq = kSqrtLog2eD * 0.70710678118654752440;
-    const float2 gx = split_df(kq / sgx), gy = split_df(kq / sgy);
-    tabG[jj] = make_float4(gx.x, gx.y, gy.x, gy.y);
     const double wj = flux[it.j0 + jj] * S.dlam;
     tabW[jj] = split_df(wj * 0.25);  // 0.25: the profiles below are 2x the pixel integrals
     wsum += fabs(wj);
