@@ -5,8 +5,8 @@ The kernels integrate the x-marginal density of the rotated Gaussian over one pi
 come from numpy.polynomial.legendre.leggauss (Golub-Welsch), mapped from [-1, 1] to
 [-1/2, 1/2] (nodes / 2, weights / 2).
 
-  * 6 points for the FP32 kernel: only the three positive nodes are emitted (the rule is
-    symmetric); their powers tau^k, k = 1..6, are emitted too.
+  * 5 points for the FP32 kernel: the centre weight and the two positive nodes (the rule is
+    symmetric), with the nodes' powers tau^k, k = 1..6.
   * 12 points for the FP64 kernel, as __constant__ arrays.
 
 Run:  python gen_quad_coeffs.py   (needs numpy; only at build-authoring time).
@@ -27,13 +27,14 @@ def main():
     out.append("#pragma once")
     out.append("")
     out.append("namespace e2e {")
-    x6, w6 = rule(6)
-    pos = [(t, wt) for t, wt in zip(x6, w6) if t > 0]
+    x5, w5 = rule(5)
+    out.append(f"constexpr float kGl5WC = {w5[np.argmin(np.abs(x5))]:.9e}f;  // node tau = 0")
+    pos = [(t, wt) for t, wt in zip(x5, w5) if t > 1e-12]
     pos.sort()
     for i, (t, wt) in enumerate(pos):
-        out.append(f"constexpr float kGl6W{i} = {wt:.9e}f;")
+        out.append(f"constexpr float kGl5W{i} = {wt:.9e}f;")
         for k in range(1, 7):
-            out.append(f"constexpr float kGl6T{i}P{k} = {t ** k:.9e}f;")
+            out.append(f"constexpr float kGl5T{i}P{k} = {t ** k:.9e}f;")
     x12, w12 = rule(12)
     out.append("constexpr int kGl12 = 12;")
     out.append("__constant__ double kGl12T[12] = {" + ", ".join(f"{v:.17e}" for v in x12) + "};")

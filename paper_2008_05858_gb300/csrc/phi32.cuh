@@ -126,15 +126,17 @@ __device__ __forceinline__ float2 tail2x2(float2 wh, float2 wl) {
   return __fmul2_rn(__fmul2_rn(ex, P), f2(rcp_approx(Q.x), rcp_approx(Q.y)));
 }
 
-// tail2x2 that also returns 2^(-w^2) of each argument (tail2_dens on two arguments).
-__device__ __forceinline__ float2 tail2x2_dens(float2 wh, float2 wl, float2& dens) {
+// tail2x2 that also returns 2^(-w^2) of each argument, for an argument held as a pair
+// (wh, wl) whose low part may exceed ulp(wh) (|wl| <= ~1e-6 |wh|, so wl^2 stays negligible):
+// the exponent is formed from the pair, the rational from wn = fl(wh + wl).
+__device__ __forceinline__ float2 tail2x2_dens_n(float2 wh, float2 wl, float2 wn, float2& dens) {
   const float2 p = __fmul2_rn(wh, wh);
   float2 e = __ffma2_rn(wh, wh, f2(-p.x, -p.y));
   e = __ffma2_rn(__fadd2_rn(wh, wh), wl, e);
   const float2 ex = __fmul2_rn(f2(ex2_approx(-p.x), ex2_approx(-p.y)),
                                __ffma2_rn(e, f2(-0.693147181f, -0.693147181f), f2(1.f, 1.f)));
   dens = ex;
-  const float2 x = f2(fminf(fabsf(wh.x), 40.f), fminf(fabsf(wh.y), 40.f));
+  const float2 x = f2(fminf(fabsf(wn.x), 40.f), fminf(fabsf(wn.y), 40.f));
   float2 P = f2(kTailP4, kTailP4);
   P = __ffma2_rn(P, x, f2(kTailP3, kTailP3));
   P = __ffma2_rn(P, x, f2(kTailP2, kTailP2));
@@ -147,6 +149,11 @@ __device__ __forceinline__ float2 tail2x2_dens(float2 wh, float2 wl, float2& den
   Q = __ffma2_rn(Q, x, f2(kTailQ1, kTailQ1));
   Q = __ffma2_rn(Q, x, f2(kTailQ0, kTailQ0));
   return __fmul2_rn(__fmul2_rn(ex, P), f2(rcp_approx(Q.x), rcp_approx(Q.y)));
+}
+
+// tail2x2 that also returns 2^(-w^2) of each argument (tail2_dens on two arguments).
+__device__ __forceinline__ float2 tail2x2_dens(float2 wh, float2 wl, float2& dens) {
+  return tail2x2_dens_n(wh, wl, wh, dens);
 }
 
 // erf_small of w.x and w.y.

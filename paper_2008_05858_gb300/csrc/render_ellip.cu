@@ -23,7 +23,8 @@
 // where mu0[m] is the column's x-integral and mom_k[m] the k-th moment of tau under phi_x
 // restricted to the column, normalised by its mass (Gauss-Legendre on the column).  With
 // |eps tau| <= |eps| / 2 and |eps| <= 0.2 (checked when the model is loaded), the series cut
-// after k = 6 is below 1e-9 of the pixel value (FP32 kernel); the FP64 kernel keeps k <= 9.
+// after k = 6, with 5-point Gauss-Legendre moments, stays below 3e-9 of the pixel value (FP32
+// kernel); the FP64 kernel keeps k <= 9 with 12-point moments.
 // The column's own Phi differences carry the full accuracy: they are formed exactly like the
 // separable PSF's pixel integrals (tails subtracted on one side of the conditional mean, erf
 // across it), only with a per-column centre.
@@ -37,13 +38,21 @@ namespace e2e {
 
 constexpr int kEThreads = 128;
 constexpr int kEWarps = kEThreads / 32;
-constexpr float kSqrt2Ln2 = 1.17741002f;         // V = w sqrt(2 ln 2) for w in log2 units
-constexpr float kTwoOverSqrt2Pi = 0.797884561f;  // 2 phi(V) / exp(-V^2 / 2)
+// 2 phi(V) / exp(-V^2 / 2) = 2 / sqrt(2 pi), times sqrt(2 ln 2)^k (V = w sqrt(2 ln 2) for w in
+// log2 units): the Hermite sum's coefficients as a polynomial in w
+constexpr double kTwoOverSqrt2PiD = 0.79788456080286535588, kSqrt2Ln2D = 1.17741002251547469101;
+constexpr float kHerm0 = (float)kTwoOverSqrt2PiD;
+constexpr float kHerm1 = (float)(kTwoOverSqrt2PiD * kSqrt2Ln2D);
+constexpr float kHerm2 = (float)(kTwoOverSqrt2PiD * kSqrt2Ln2D * kSqrt2Ln2D);
+constexpr float kHerm3 = (float)(kTwoOverSqrt2PiD * kSqrt2Ln2D * kSqrt2Ln2D * kSqrt2Ln2D);
+constexpr float kHerm4 = (float)(kTwoOverSqrt2PiD * kSqrt2Ln2D * kSqrt2Ln2D * kSqrt2Ln2D * kSqrt2Ln2D);
+constexpr float kHerm5 = (float)(kTwoOverSqrt2PiD * kSqrt2Ln2D * kSqrt2Ln2D * kSqrt2Ln2D * kSqrt2Ln2D * kSqrt2Ln2D);
 
 // ------------------------------------------------------------------------------ mixed
 
-// Shared-memory layout of one CTA (bytes), identical on host and device.  Lane groups of K
-// lanes (one per window column) stage the 16 stamps of a run each: 32 / K groups per warp.
+// Shared-memory layout of one CTA (bytes), identical on host and device.  Lane groups of K + 1
+// lanes (lane l owning x-edge l, and window column l for l < K) stage the 16 stamps of a run
+// each: 32 / (K + 1) groups per warp.
 struct EllipLayout {
   size_t tabP, tabS, tabW, tabU, tabE, stage, boxh, boxl, total;
   __host__ __device__ EllipLayout(int J, int NK, int nd, int area, int K) {
@@ -54,7 +63,7 @@ struct EllipLayout {
     tabU = o; o += (size_t)NK * 8;              // slit weights, (hi, lo)
     o = (o + 15) & ~(size_t)15;
     tabE = o; o += (size_t)J * 32;              // two float4 of PSF constants per sample
-    stage = o; o += (size_t)kEWarps * (32 / K) * 16 * 16;  // mapped stamps of the groups' runs
+    stage = o; o += (size_t)kEWarps * (32 / (K + 1)) * 16 * 16;  // mapped stamps of the groups' runs
     boxh = o; o += (size_t)area * 4;
     boxl = o; o += (size_t)area * 4;
     total = o;
@@ -62,18 +71,27 @@ struct EllipLayout {
 };
 
 // One CTA per work item (<= 32 wavelength samples x <= 16 slit points, at most 512 stamps,
-// so no box pixel gets more than 512 fixed-point deposits).  A warp holds 32 / K groups of K
-// lanes, lane m of a group owning window column m.  A group takes one wavelength sample and
+// so no box pixel gets more than 512 fixed-point deposits).  A warp holds 32 / (K + 1) groups
+// of K + 1 lanes: lane l evaluates x-edge l of the window, and lane l < K owns window column l
+// (its right edge comes from lane l + 1 by a shuffle).  A group takes one wavelength sample and
 // walks the run of its slit points in order: the run's stamps are mapped into the group's
-// staging, then for each stamp every lane evaluates its column (the two x-edges, the moments
-// of tau, the K + 1 row edges of the conditional profile, in packed pairs) and adds the K
-// pixels to its registers.  Consecutive slit points mostly share their window origin, so the
-// lanes deposit their columns into the item's box (exact fixed point, shared-memory integer
+// staging, then for each stamp every column lane evaluates its column (the x-integral, the
+// moments of tau, the K + 1 row edges of the conditional profile in packed pairs) and adds
+// the K pixels to its registers.  Consecutive slit points mostly share their window origin, so
+// the lanes deposit their columns into the item's box (exact fixed point, shared-memory integer
 // atomics) only when the origin moves and at the end of the run.
+//
+// Row edges: the conditional centre f = f_y + beta tb (a double-float, |f| can exceed 1/2) is
+// split once per column into fc, f rounded to 19 fractional bits, and the rest ff
+// (|ff| <= 2^-20).  Each edge offset e - fc (e a half-integer) is then exact in FP32 for
+// |e - fc| < 32, and the argument w = (e - f) g_c is the exact product (e - fc) g_ch with its FMA
+// error, plus (e - fc) g_cl - ff g_ch: six FP32 operations per edge instead of a TwoSum and a
+// double-float product.
 template <int K>
 __global__ void __launch_bounds__(kEThreads, 6) k_render_ellip(const MixedArgs a) {
   constexpr int H = K / 2;
-  constexpr int NG = 32 / K;  // lane groups per warp
+  constexpr int GL = K + 1;   // lanes per group
+  constexpr int NG = 32 / GL;  // lane groups per warp
   extern __shared__ __align__(16) unsigned char smem[];
   const Item it = a.items[blockIdx.x];
   const DevSlice& S = a.slices[it.slice];
@@ -142,8 +160,9 @@ __global__ void __launch_bounds__(kEThreads, 6) k_render_ellip(const MixedArgs a
   const int Psh = total > 0.0 ? max(-100, min(100, 52 - ex)) : 0;
   const float sc = ldexpf(1.f, Psh), sc_hi = ldexpf(1.f, Psh - 22);
 
-  const int g = lane / K, m = lane - g * K;  // group and window column (g == NG: spare lane)
+  const int g = lane / GL, l = lane - g * GL;  // group and x-edge (g == NG: spare lane)
   const bool in_group = g < NG;
+  const bool col = in_group && l < K;  // owns window column l
   int4* gst = stage + (warp * NG + (in_group ? g : 0)) * 16;
   float acc[K];
   // the groups of a warp take samples kEWarps apart, so their columns rarely share a box pixel
@@ -151,9 +170,9 @@ __global__ void __launch_bounds__(kEThreads, 6) k_render_ellip(const MixedArgs a
   for (int round = 0; round < n_rounds && total > 0.0; ++round) {
     const int jj = warp + kEWarps * (g + NG * round);
     const bool active = in_group && jj < it.nj;  // uniform over the group
-    // map the run's stamps (double-float, as the planner), lane m taking b = m, m + K, ...
+    // map the run's stamps (double-float, as the planner), lane l taking b = l, l + K + 1, ...
     if (active)
-      for (int b = m; b < it.nk; b += K) {
+      for (int b = l; b < it.nk; b += GL) {
         int ci, ri;
         float fx, fy;
         map_stamp_df(tabP + jj * nd, S.degree, tabS[b], ci, fx, ri, fy);
@@ -171,8 +190,8 @@ __global__ void __launch_bounds__(kEThreads, 6) k_render_ellip(const MixedArgs a
 #pragma unroll
     for (int n = 0; n < K; ++n) acc[n] = 0.f;
     auto flush = [&]() {
-      const int bx = cx - H + m - it.bx0, by0 = cy - H - it.by0;
-      const bool colin = bx >= 0 && bx < it.bw;
+      const int bx = cx - H + l - it.bx0, by0 = cy - H - it.by0;
+      const bool colin = col && bx >= 0 && bx < it.bw;
 #pragma unroll
       for (int n = 0; n < K; ++n) {
         const int by = by0 + n;
@@ -195,50 +214,49 @@ __global__ void __launch_bounds__(kEThreads, 6) k_render_ellip(const MixedArgs a
         cy = st.y;
       }
       const float2 uk = tabU[b];
-      const float w = valid ? fmaf(wj.x, uk.x, fmaf(wj.x, uk.y, wj.y * uk.x)) : 0.f;
+      const float w = valid && col ? fmaf(wj.x, uk.x, fmaf(wj.x, uk.y, wj.y * uk.x)) : 0.f;
       const float fx = __int_as_float(st.z), fy = __int_as_float(st.w);
 
-      // twice the column's x-integral (the separable profile's edge formulas), edges m, m + 1
-      float2 wxh, wxl;
-      edge_arg2(f2((float)(m - H) - 0.5f, (float)(m - H) + 0.5f), fx, e0.x, e0.y, wxh, wxl);
-      const float2 EX = tail2x2(wxh, wxl);
-      const float2 FE = erf_small2(wxh);
-      const float EL = EX.x, ER = EX.y;
-      const float FL = fabsf(wxh.x) < kErfMaxArg ? FE.x : 1.f - EL;
-      const float FR = fabsf(wxh.y) < kErfMaxArg ? FE.y : 1.f - ER;
-      const float tx = m < H - 1 ? ER - EL : (m == H - 1 ? FL - FR : (m == H ? FL + FR : (m == H + 1 ? FR - FL : EL - ER)));
+      // twice the column's x-integral from x-edges l (this lane) and l + 1 (the next lane), by
+      // the separable profile's edge formulas
+      float tx;
+      {
+        float wxh, wxl;
+        edge_arg((float)(l - H) - 0.5f, fx, e0.x, e0.y, wxh, wxl);
+        const float EX = tail2(wxh, wxl);
+        float FX = 1.f - EX;
+        if (fabsf(wxh) < kErfMaxArg) FX = erf_small(wxh);
+        const float ER = __shfl_down_sync(0xffffffffu, EX, 1), FR = __shfl_down_sync(0xffffffffu, FX, 1);
+        const float EL = EX, FL = FX;
+        tx = l < H - 1 ? ER - EL : (l == H - 1 ? FL - FR : (l == H ? FL + FR : (l == H + 1 ? FR - FL : EL - ER)));
+      }
 
-      // column centre offset tb = (m - H) - fx as a double-float (|m - H| >= 1 > |fx| or m == H)
-      const float th = (float)(m - H) - fx;
-      const float tl = ((float)(m - H) - th) - fx;
+      // column centre offset tb = (l - H) - fx as a double-float (|l - H| >= 1 > |fx| or l == H)
+      const float th = (float)(l - H) - fx;
+      const float tl = ((float)(l - H) - th) - fx;
 
       // moments of tau on the column under phi_x(tb + tau) / phi_x(tb) = 2^(al (tb tau + tau^2 / 2)),
-      // 6-point Gauss-Legendre, nodes in symmetric pairs
+      // 5-point Gauss-Legendre: the centre node (factor 1) and two symmetric pairs
       const float al = e1.w;
-      float s0, s1, s2, s3, s4, s5, s6;
+      float s0 = kGl5WC, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f, s5 = 0.f, s6 = 0.f;
       {
         const float q2 = 0.5f * al;
         const float c0 = al * th;
-#define E2E_GL_PAIR(I, INIT)                                                       \
-  {                                                                                \
-    const float cc = q2 * kGl6T##I##P2, cl = c0 * kGl6T##I##P1;                    \
-    const float ep = ex2_approx(cc + cl), em = ex2_approx(cc - cl);                \
-    const float sp = kGl6W##I * (ep + em), dm = kGl6W##I * (ep - em);              \
-    if (INIT) {                                                                    \
-      s0 = sp; s2 = sp * kGl6T##I##P2; s4 = sp * kGl6T##I##P4; s6 = sp * kGl6T##I##P6; \
-      s1 = dm * kGl6T##I##P1; s3 = dm * kGl6T##I##P3; s5 = dm * kGl6T##I##P5;      \
-    } else {                                                                       \
-      s0 += sp; s2 = fmaf(sp, kGl6T##I##P2, s2); s4 = fmaf(sp, kGl6T##I##P4, s4);  \
-      s6 = fmaf(sp, kGl6T##I##P6, s6); s1 = fmaf(dm, kGl6T##I##P1, s1);            \
-      s3 = fmaf(dm, kGl6T##I##P3, s3); s5 = fmaf(dm, kGl6T##I##P5, s5);            \
-    }                                                                              \
+#define E2E_GL_PAIR(I)                                                          \
+  {                                                                             \
+    const float cc = q2 * kGl5T##I##P2, cl = c0 * kGl5T##I##P1;                 \
+    const float ep = ex2_approx(cc + cl), em = ex2_approx(cc - cl);             \
+    const float sp = kGl5W##I * (ep + em), dm = kGl5W##I * (ep - em);           \
+    s0 += sp; s2 = fmaf(sp, kGl5T##I##P2, s2); s4 = fmaf(sp, kGl5T##I##P4, s4); \
+    s6 = fmaf(sp, kGl5T##I##P6, s6); s1 = fmaf(dm, kGl5T##I##P1, s1);           \
+    s3 = fmaf(dm, kGl5T##I##P3, s3); s5 = fmaf(dm, kGl5T##I##P5, s5);           \
   }
-        E2E_GL_PAIR(0, true)
-        E2E_GL_PAIR(1, false)
-        E2E_GL_PAIR(2, false)
+        E2E_GL_PAIR(0)
+        E2E_GL_PAIR(1)
 #undef E2E_GL_PAIR
       }
-      // G(V) = sum_k a_k He_(k-1)(V) as a quintic in V, scaled by 2 / sqrt(2 pi)
+      // G(V) = sum_k a_k He_(k-1)(V) as a quintic, scaled by 2 / sqrt(2 pi) and written as a
+      // polynomial in w = V / sqrt(2 ln 2) (the row edges' argument in log2 units)
       float g0, g1, g2, g3, g4, g5;
       {
         const float r = rcp_approx(s0), ep1 = e1.z;
@@ -246,12 +264,12 @@ __global__ void __launch_bounds__(kEThreads, 6) k_render_ellip(const MixedArgs a
         const float a1 = -p1 * (s1 * r), a2 = -p2 * (s2 * r) * 0.5f, a3 = -p3 * (s3 * r) * (1.f / 6.f);
         const float a4 = -p4 * (s4 * r) * (1.f / 24.f), a5 = -p5 * (s5 * r) * (1.f / 120.f);
         const float a6 = -p6 * (s6 * r) * (1.f / 720.f);
-        g0 = kTwoOverSqrt2Pi * (a1 - a3 + 3.f * a5);
-        g1 = kTwoOverSqrt2Pi * (a2 - 3.f * a4 + 15.f * a6);
-        g2 = kTwoOverSqrt2Pi * (a3 - 6.f * a5);
-        g3 = kTwoOverSqrt2Pi * (a4 - 10.f * a6);
-        g4 = kTwoOverSqrt2Pi * a5;
-        g5 = kTwoOverSqrt2Pi * a6;
+        g0 = kHerm0 * (a1 - a3 + 3.f * a5);
+        g1 = kHerm1 * (a2 - 3.f * a4 + 15.f * a6);
+        g2 = kHerm2 * (a3 - 6.f * a5);
+        g3 = kHerm3 * (a4 - 10.f * a6);
+        g4 = kHerm4 * a5;
+        g5 = kHerm5 * a6;
       }
       // conditional centre of the column relative to the window centre: f = fy + beta tb (double-float)
       float fh, fl;
@@ -267,46 +285,48 @@ __global__ void __launch_bounds__(kEThreads, 6) k_render_ellip(const MixedArgs a
         fh = t;
       }
       const float gch = e0.z, gcl = e0.w;
+      // f = fc + ff, fc on a 2^-19 grid (exact split), ff g_ch in FP32
+      const float fc = rintf(fh * 524288.f) * (1.f / 524288.f);
+      const float ffg = ((fh - fc) + fl) * gch;
       const float wq = w * tx;
       // the K + 1 row edges in pairs (n, n + 1); pixel n spans edges n and n + 1
       float Ep = 0.f, Fp = 0.f, hp = 0.f, whp = 0.f;
 #pragma unroll
       for (int n = 0; n <= K; n += 2) {
-        // row edges at (n - H - 1/2) - f from the conditional centre, in log2 units (TwoSum:
-        // |f| may exceed 1/2)
-        const float2 eg = f2((float)(n - H) - 0.5f, (float)(n - H) + 0.5f);
-        const float2 dh = __fadd2_rn(eg, f2(-fh, -fh));
-        const float2 bb2 = __fadd2_rn(dh, neg2(eg));
-        const float2 de = __fadd2_rn(__fadd2_rn(eg, neg2(__fadd2_rn(dh, neg2(bb2)))), __fadd2_rn(f2(-fh, -fh), neg2(bb2)));
-        const float2 dl = __fadd2_rn(de, f2(-fl, -fl));
+        // w = (e - f) g_c for the half-integers e = n - H -+ 1/2: e - fc exact, its product with
+        // g_ch exact as a pair, the small terms added to the low part; wn = fl(w)
+        const float2 dc = __fadd2_rn(f2((float)(n - H) - 0.5f, (float)(n - H) + 0.5f), f2(-fc, -fc));
         const float2 gg = f2(gch, gch);
-        const float2 wh = __fmul2_rn(dh, gg);
-        const float2 wl = __fadd2_rn(__ffma2_rn(dh, gg, neg2(wh)), __ffma2_rn(dh, f2(gcl, gcl), __fmul2_rn(dl, gg)));
+        const float2 wh = __fmul2_rn(dc, gg);
+        const float2 wl = __fadd2_rn(__ffma2_rn(dc, gg, neg2(wh)), __ffma2_rn(dc, f2(gcl, gcl), f2(-ffg, -ffg)));
+        const float2 wn = __fadd2_rn(wh, wl);
         float2 dens;
-        const float2 E = tail2x2_dens(wh, wl, dens);
+        const float2 E = tail2x2_dens_n(wh, wl, wn, dens);
         // erf only near the conditional centre; skipped when no lane of the warp has an edge there
-        const bool near0 = fabsf(wh.x) < kErfMaxArg, near1 = fabsf(wh.y) < kErfMaxArg;
+        const bool near0 = fabsf(wn.x) < kErfMaxArg, near1 = fabsf(wn.y) < kErfMaxArg;
         float2 F = f2(1.f - E.x, 1.f - E.y);
         if (__any_sync(0xffffffffu, near0 || near1)) {
-          const float2 fe = erf_small2(wh);
+          const float2 fe = erf_small2(wn);
           F = f2(near0 ? fe.x : F.x, near1 ? fe.y : F.y);
         }
-        const float2 V = __fmul2_rn(wh, f2(kSqrt2Ln2, kSqrt2Ln2));
-        float2 Gv = __ffma2_rn(f2(g5, g5), V, f2(g4, g4));
-        Gv = __ffma2_rn(Gv, V, f2(g3, g3));
-        Gv = __ffma2_rn(Gv, V, f2(g2, g2));
-        Gv = __ffma2_rn(Gv, V, f2(g1, g1));
-        Gv = __ffma2_rn(Gv, V, f2(g0, g0));
+        float2 Gv = __ffma2_rn(f2(g5, g5), wn, f2(g4, g4));
+        Gv = __ffma2_rn(Gv, wn, f2(g3, g3));
+        Gv = __ffma2_rn(Gv, wn, f2(g2, g2));
+        Gv = __ffma2_rn(Gv, wn, f2(g1, g1));
+        Gv = __ffma2_rn(Gv, wn, f2(g0, g0));
         const float2 h = __fmul2_rn(dens, Gv);
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           const int ne = n + e;
-          const float Ee = e ? E.y : E.x, Fe = e ? F.y : F.x, he = e ? h.y : h.x, we = e ? wh.y : wh.x;
+          const float Ee = e ? E.y : E.x, Fe = e ? F.y : F.x, he = e ? h.y : h.x, we = e ? wn.y : wn.x;
           if (ne > 0 && ne <= K) {
+            // tails subtracted on one side of the conditional centre (erf near it), erf summed
+            // across it
             const bool same = (we < 0.f) == (whp < 0.f);
             const bool small = fminf(fabsf(we), fabsf(whp)) < kErfMaxArg;
-            const float ty = same ? (small ? fabsf(Fp - Fe) : fabsf(Ep - Ee)) : (Fp + Fe);
-            acc[ne - 1] = fmaf(wq, ty + (he - hp), acc[ne - 1]);
+            const float pa = same && !small ? Ep : Fp;
+            const float pb = same ? (small ? Fe : Ee) : -Fe;
+            acc[ne - 1] = fmaf(wq, fabsf(pa - pb) + (he - hp), acc[ne - 1]);
           }
           Ep = Ee;
           Fp = Fe;
