@@ -88,7 +88,7 @@ struct EllipLayout {
 // error, plus (e - fc) g_cl - ff g_ch: six FP32 operations per edge instead of a TwoSum and a
 // double-float product.
 template <int K>
-__global__ void __launch_bounds__(kEThreads, 6) k_render_ellip(const MixedArgs a) {
+__global__ void __launch_bounds__(kEThreads, 5) k_render_ellip(const MixedArgs a) {
   constexpr int H = K / 2;
   constexpr int GL = K + 1;   // lanes per group
   constexpr int NG = 32 / GL;  // lane groups per warp
