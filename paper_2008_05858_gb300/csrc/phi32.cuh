@@ -129,12 +129,18 @@ __device__ __forceinline__ float2 tail2x2(float2 wh, float2 wl) {
 // tail2x2 that also returns 2^(-w^2) of each argument, for an argument held as a pair
 // (wh, wl) whose low part may exceed ulp(wh) (|wl| <= ~1e-6 |wh|, so wl^2 stays negligible):
 // the exponent is formed from the pair, the rational from wn = fl(wh + wl).
-__device__ __forceinline__ float2 tail2x2_dens_n(float2 wh, float2 wl, float2 wn, float2& dens) {
+// 2^(-w^2) of two arguments held as pairs (wh, wl), |wl| <= ~1e-6 |wh|: the exponent's square
+// formed exactly from the pair, 2^(-p) on the SFU, 2^(-e) ~= 1 - e ln2.
+__device__ __forceinline__ float2 dens2x2(float2 wh, float2 wl) {
   const float2 p = __fmul2_rn(wh, wh);
   float2 e = __ffma2_rn(wh, wh, f2(-p.x, -p.y));
   e = __ffma2_rn(__fadd2_rn(wh, wh), wl, e);
-  const float2 ex = __fmul2_rn(f2(ex2_approx(-p.x), ex2_approx(-p.y)),
-                               __ffma2_rn(e, f2(-0.693147181f, -0.693147181f), f2(1.f, 1.f)));
+  return __fmul2_rn(f2(ex2_approx(-p.x), ex2_approx(-p.y)),
+                    __ffma2_rn(e, f2(-0.693147181f, -0.693147181f), f2(1.f, 1.f)));
+}
+
+__device__ __forceinline__ float2 tail2x2_dens_n(float2 wh, float2 wl, float2 wn, float2& dens) {
+  const float2 ex = dens2x2(wh, wl);
   dens = ex;
   const float2 x = f2(fminf(fabsf(wn.x), 40.f), fminf(fabsf(wn.y), 40.f));
   float2 P = f2(kTailP4, kTailP4);

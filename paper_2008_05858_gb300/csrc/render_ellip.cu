@@ -300,10 +300,14 @@ __global__ void __launch_bounds__(kEThreads, 5) k_render_ellip(const MixedArgs a
         const float2 wh = __fmul2_rn(dc, gg);
         const float2 wl = __fadd2_rn(__ffma2_rn(dc, gg, neg2(wh)), __ffma2_rn(dc, f2(gcl, gcl), f2(-ffg, -ffg)));
         const float2 wn = __fadd2_rn(wh, wl);
-        float2 dens;
-        const float2 E = tail2x2_dens_n(wh, wl, wn, dens);
-        // erf only near the conditional centre; skipped when no lane of the warp has an edge there
+        // tails only off the conditional centre (a near edge's tail is never read), erf only near
+        // it; each skipped when no lane of the warp needs it
         const bool near0 = fabsf(wn.x) < kErfMaxArg, near1 = fabsf(wn.y) < kErfMaxArg;
+        float2 dens, E = f2(0.f, 0.f);
+        if (__any_sync(0xffffffffu, !(near0 && near1)))
+          E = tail2x2_dens_n(wh, wl, wn, dens);
+        else
+          dens = dens2x2(wh, wl);
         float2 F = f2(1.f - E.x, 1.f - E.y);
         if (__any_sync(0xffffffffu, near0 || near1)) {
           const float2 fe = erf_small2(wn);
