@@ -38,24 +38,18 @@ namespace e2e {
 
 constexpr int kEThreads = 128;
 constexpr int kEWarps = kEThreads / 32;
-// 2 phi(V) / exp(-V^2 / 2) = 2 / sqrt(2 pi), times sqrt(2 ln 2)^k (V = w sqrt(2 ln 2) for w in
-// log2 units): the Hermite sum's coefficients as a polynomial in w
-constexpr double kTwoOverSqrt2PiD = 0.79788456080286535588, kSqrt2Ln2D = 1.17741002251547469101;
-constexpr float kHerm0 = (float)kTwoOverSqrt2PiD;
-constexpr float kHerm1 = (float)(kTwoOverSqrt2PiD * kSqrt2Ln2D);
-constexpr float kHerm2 = (float)(kTwoOverSqrt2PiD * kSqrt2Ln2D * kSqrt2Ln2D);
-constexpr float kHerm3 = (float)(kTwoOverSqrt2PiD * kSqrt2Ln2D * kSqrt2Ln2D * kSqrt2Ln2D);
-constexpr float kHerm4 = (float)(kTwoOverSqrt2PiD * kSqrt2Ln2D * kSqrt2Ln2D * kSqrt2Ln2D * kSqrt2Ln2D);
-constexpr float kHerm5 = (float)(kTwoOverSqrt2PiD * kSqrt2Ln2D * kSqrt2Ln2D * kSqrt2Ln2D * kSqrt2Ln2D * kSqrt2Ln2D);
+constexpr float kSqrt2Ln2 = 1.17741002f;         // V = w sqrt(2 ln 2) for w in log2 units
+constexpr float kTwoOverSqrt2Pi = 0.797884561f;  // 2 phi(V) / exp(-V^2 / 2)
 
 // ------------------------------------------------------------------------------ mixed
 
-// Shared-memory layout of one CTA (bytes), identical on host and device.  Lane groups of K + 1
-// lanes (lane l owning x-edge l, and window column l for l < K) stage the 16 stamps of a run
-// each: 32 / (K + 1) groups per warp.
+// Shared-memory layout of one CTA (bytes), identical on host and device.  Lane groups of
+// (K + 1) / 2 lanes (lane j owning window columns 2j and 2j + 1) stage the 16 stamps of a run
+// each and keep their sample's series constants: 32 / ((K + 1) / 2) groups per warp.
 struct EllipLayout {
-  size_t tabP, tabS, tabW, tabU, tabE, stage, boxh, boxl, total;
+  size_t tabP, tabS, tabW, tabU, tabE, stage, cser, boxh, boxl, total;
   __host__ __device__ EllipLayout(int J, int NK, int nd, int area, int K) {
+    const int ng = kEWarps * (32 / ((K + 1) / 2));  // lane groups per CTA
     size_t o = 0;
     tabP = o; o += (size_t)J * nd * 16;        // P_b(lt) of x and y per sample, split_xy pairs
     tabS = o; o += (size_t)NK * 8;              // s of each slit point, (hi, lo) floats
@@ -63,35 +57,44 @@ struct EllipLayout {
     tabU = o; o += (size_t)NK * 8;              // slit weights, (hi, lo)
     o = (o + 15) & ~(size_t)15;
     tabE = o; o += (size_t)J * 32;              // two float4 of PSF constants per sample
-    stage = o; o += (size_t)kEWarps * (32 / (K + 1)) * 16 * 16;  // mapped stamps of the groups' runs
+    stage = o; o += (size_t)ng * 16 * 16;       // mapped stamps of the groups' runs
+    cser = o; o += (size_t)ng * kGlKmax * 8;    // the groups' series constants c_k (left, right)
     boxh = o; o += (size_t)area * 4;
     boxl = o; o += (size_t)area * 4;
     total = o;
   }
 };
 
+// Twice the x-integral of window column m from its edges' tails E and erf values F (left
+// edge L, right edge R), by the separable profile's formulas.
+template <int H>
+__device__ __forceinline__ float column_x(int m, float EL, float FL, float ER, float FR) {
+  return m < H - 1 ? ER - EL : (m == H - 1 ? FL - FR : (m == H ? FL + FR : (m == H + 1 ? FR - FL : EL - ER)));
+}
+
 // One CTA per work item (<= 32 wavelength samples x <= 16 slit points, at most 512 stamps,
-// so no box pixel gets more than 512 fixed-point deposits).  A warp holds 32 / (K + 1) groups
-// of K + 1 lanes: lane l evaluates x-edge l of the window, and lane l < K owns window column l
-// (its right edge comes from lane l + 1 by a shuffle).  A group takes one wavelength sample and
+// so no box pixel gets more than 512 fixed-point deposits).  A warp holds 32 / ((K + 1) / 2)
+// groups of (K + 1) / 2 lanes; lane j of a group owns the window's column pair (2j, 2j + 1)
+// (the last pair of an odd K has no right column).  A group takes one wavelength sample and
 // walks the run of its slit points in order: the run's stamps are mapped into the group's
-// staging, then for each stamp every column lane evaluates its column (the x-integral, the
-// moments of tau, the K + 1 row edges of the conditional profile in packed pairs) and adds
-// the K pixels to its registers.  Consecutive slit points mostly share their window origin, so
-// the lanes deposit their columns into the item's box (exact fixed point, shared-memory integer
-// atomics) only when the origin moves and at the end of the run.
+// staging, then for each stamp every lane evaluates its column pair: x-edges 2j and 2j + 1
+// (edge 2j + 2 from the next lane by a shuffle), the moments of each column about the pair's
+// centre, and the K + 1 row edges of the pair's conditional profile, shared by both columns,
+// in packed pairs; each column's series term is a degree-7 polynomial per edge.  The lane adds
+// the 2K pixels to its registers; consecutive slit points mostly share their window origin, so
+// the lanes deposit their columns into the item's box (exact fixed point, shared-memory
+// integer atomics) only when the origin moves and at the end of the run.
 //
-// Row edges: the conditional centre f = f_y + beta tb (a double-float, |f| can exceed 1/2) is
-// split once per column into fc, f rounded to 19 fractional bits, and the rest ff
-// (|ff| <= 2^-20).  Each edge offset e - fc (e a half-integer) is then exact in FP32 for
-// |e - fc| < 32, and the argument w = (e - f) g_c is the exact product (e - fc) g_ch with its FMA
-// error, plus (e - fc) g_cl - ff g_ch: six FP32 operations per edge instead of a TwoSum and a
-// double-float product.
+// Row edges: the pair's conditional centre f = f_y + beta t_p (t_p the pair's centre offset; a
+// double-float, |f| can exceed 1/2) is split once into fc, f rounded to 19 fractional bits,
+// and the rest ff (|ff| <= 2^-20).  Each edge offset e - fc (e a half-integer) is then exact
+// in FP32 for |e - fc| < 32, and the argument w = (e - f) g_c is the exact product
+// (e - fc) g_ch with its FMA error, plus (e - fc) g_cl - ff g_ch: six FP32 operations per edge.
 template <int K>
 __global__ void __launch_bounds__(kEThreads, 5) k_render_ellip(const MixedArgs a) {
   constexpr int H = K / 2;
-  constexpr int GL = K + 1;   // lanes per group
-  constexpr int NG = 32 / GL;  // lane groups per warp
+  constexpr int GL = (K + 1) / 2;  // lanes per group: column pairs of the window
+  constexpr int NG = 32 / GL;      // lane groups per warp
   extern __shared__ __align__(16) unsigned char smem[];
   const Item it = a.items[blockIdx.x];
   const DevSlice& S = a.slices[it.slice];
@@ -104,6 +107,7 @@ __global__ void __launch_bounds__(kEThreads, 5) k_render_ellip(const MixedArgs a
   float2* tabU = reinterpret_cast<float2*>(smem + L.tabU);
   float4* tabE = reinterpret_cast<float4*>(smem + L.tabE);
   int4* stage = reinterpret_cast<int4*>(smem + L.stage);
+  float2* cser = reinterpret_cast<float2*>(smem + L.cser);
   int* boxh = reinterpret_cast<int*>(smem + L.boxh);
   unsigned* boxl = reinterpret_cast<unsigned*>(smem + L.boxl);
   __shared__ double s_w[kEWarps], s_u[kEWarps];
@@ -160,24 +164,36 @@ __global__ void __launch_bounds__(kEThreads, 5) k_render_ellip(const MixedArgs a
   const int Psh = total > 0.0 ? max(-100, min(100, 52 - ex)) : 0;
   const float sc = ldexpf(1.f, Psh), sc_hi = ldexpf(1.f, Psh - 22);
 
-  const int g = lane / GL, l = lane - g * GL;  // group and x-edge (g == NG: spare lane)
+  const int g = lane / GL, j = lane - g * GL;  // group and column pair (g == NG: spare lane)
   const bool in_group = g < NG;
-  const bool col = in_group && l < K;  // owns window column l
-  int4* gst = stage + (warp * NG + (in_group ? g : 0)) * 16;
-  float acc[K];
+  const int m0 = 2 * j;                        // the pair's left column
+  const bool has_r = in_group && m0 + 1 < K;   // the pair has a right column
+  const int gidx = warp * NG + (in_group ? g : 0);
+  int4* gst = stage + gidx * 16;
+  float2* gcs = cser + gidx * kGlKmax;
+  float2 acc[K];  // window row n of the left (.x) and right (.y) column
   // the groups of a warp take samples kEWarps apart, so their columns rarely share a box pixel
   const int n_rounds = (it.nj + kEWarps * NG - 1) / (kEWarps * NG);
   for (int round = 0; round < n_rounds && total > 0.0; ++round) {
     const int jj = warp + kEWarps * (g + NG * round);
     const bool active = in_group && jj < it.nj;  // uniform over the group
-    // map the run's stamps (double-float, as the planner), lane l taking b = l, l + K + 1, ...
-    if (active)
-      for (int b = l; b < it.nk; b += GL) {
+    if (active) {
+      // map the run's stamps (double-float, as the planner), lane j taking b = j, j + GL, ...
+      for (int b = j; b < it.nk; b += GL) {
         int ci, ri;
         float fx, fy;
         map_stamp_df(tabP + jj * nd, S.degree, tabS[b], ci, fx, ri, fy);
         gst[b] = make_int4(ci, ri, __float_as_int(fx), __float_as_int(fy));
       }
+      // the sample's series constants c_k = -(2 / sqrt(2 pi)) eps_c^k / k! of the left
+      // (eps_c = -eps, moments mirrored) and right (eps_c = eps) column, k = 1..kGlKmax
+      const float eps = tabE[2 * jj + 1].z;
+      for (int k = j + 1; k <= kGlKmax; k += GL) {
+        float p = kTwoOverSqrt2Pi;
+        for (int i = 1; i <= k; ++i) p *= eps / (float)i;
+        gcs[k - 1] = f2((k & 1) ? p : -p, -p);
+      }
+    }
     __syncwarp();
     float4 e0 = make_float4(0.f, 0.f, 0.f, 0.f), e1 = e0;
     float2 wj = make_float2(0.f, 0.f);
@@ -188,21 +204,26 @@ __global__ void __launch_bounds__(kEThreads, 5) k_render_ellip(const MixedArgs a
     }
     int cx = kOffFrame, cy = kOffFrame;  // origin of the stamps held in acc (uniform over the group)
 #pragma unroll
-    for (int n = 0; n < K; ++n) acc[n] = 0.f;
+    for (int n = 0; n < K; ++n) acc[n] = f2(0.f, 0.f);
     auto flush = [&]() {
-      const int bx = cx - H + l - it.bx0, by0 = cy - H - it.by0;
-      const bool colin = col && bx >= 0 && bx < it.bw;
+      const int bx = cx - H + m0 - it.bx0, by0 = cy - H - it.by0;
+      const bool inl = in_group && bx >= 0 && bx < it.bw, inr = has_r && bx + 1 >= 0 && bx + 1 < it.bw;
 #pragma unroll
       for (int n = 0; n < K; ++n) {
         const int by = by0 + n;
-        if (colin && by >= 0 && by < it.bh) {
-          const int q = by * it.bw + bx;
-          box_deposit(boxh + q, boxl + q, acc[n], sc, sc_hi);
-        } else if (a.err && acc[n] != 0.f) {  // outside the box: legitimate only off the detector
-          const int X = it.bx0 + bx, Y = it.by0 + by;
-          if (X >= 0 && X < S.W && Y >= 0 && Y < S.H) atomicAdd(a.err, 1);
+        const bool rowin = by >= 0 && by < it.bh;
+        const int q = by * it.bw + bx;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float v = h ? acc[n].y : acc[n].x;
+          if ((h ? inr : inl) && rowin) {
+            box_deposit(boxh + q + h, boxl + q + h, v, sc, sc_hi);
+          } else if (a.err && v != 0.f) {  // outside the box: legitimate only off the detector
+            const int X = it.bx0 + bx + h, Y = it.by0 + by;
+            if (X >= 0 && X < S.W && Y >= 0 && Y < S.H) atomicAdd(a.err, 1);
+          }
         }
-        acc[n] = 0.f;
+        acc[n] = f2(0.f, 0.f);
       }
     };
     for (int b = 0; b < it.nk; ++b) {
@@ -214,64 +235,76 @@ __global__ void __launch_bounds__(kEThreads, 5) k_render_ellip(const MixedArgs a
         cy = st.y;
       }
       const float2 uk = tabU[b];
-      const float w = valid && col ? fmaf(wj.x, uk.x, fmaf(wj.x, uk.y, wj.y * uk.x)) : 0.f;
+      const float w = valid && in_group ? fmaf(wj.x, uk.x, fmaf(wj.x, uk.y, wj.y * uk.x)) : 0.f;
       const float fx = __int_as_float(st.z), fy = __int_as_float(st.w);
 
-      // twice the column's x-integral from x-edges l (this lane) and l + 1 (the next lane), by
-      // the separable profile's edge formulas
-      float tx;
+      // twice the x-integrals of columns 2j and 2j + 1 from x-edges 2j, 2j + 1 (this lane,
+      // packed) and 2j + 2 (the next lane), times the stamp's weight
+      float2 wq;
       {
-        float wxh, wxl;
-        edge_arg((float)(l - H) - 0.5f, fx, e0.x, e0.y, wxh, wxl);
-        const float EX = tail2(wxh, wxl);
-        float FX = 1.f - EX;
-        if (fabsf(wxh) < kErfMaxArg) FX = erf_small(wxh);
-        const float ER = __shfl_down_sync(0xffffffffu, EX, 1), FR = __shfl_down_sync(0xffffffffu, FX, 1);
-        const float EL = EX, FL = FX;
-        tx = l < H - 1 ? ER - EL : (l == H - 1 ? FL - FR : (l == H ? FL + FR : (l == H + 1 ? FR - FL : EL - ER)));
+        float2 wxh, wxl;
+        edge_arg2(f2((float)(m0 - H) - 0.5f, (float)(m0 - H) + 0.5f), fx, e0.x, e0.y, wxh, wxl);
+        const float2 EX = tail2x2(wxh, wxl);
+        float2 FX = f2(1.f - EX.x, 1.f - EX.y);
+        const bool n0 = fabsf(wxh.x) < kErfMaxArg, n1 = fabsf(wxh.y) < kErfMaxArg;
+        if (n0 || n1) {
+          const float2 fe = erf_small2(wxh);
+          FX = f2(n0 ? fe.x : FX.x, n1 ? fe.y : FX.y);
+        }
+        const float E2 = __shfl_down_sync(0xffffffffu, EX.x, 1), F2 = __shfl_down_sync(0xffffffffu, FX.x, 1);
+        wq = f2(w * column_x<H>(m0, EX.x, FX.x, EX.y, FX.y),
+                has_r ? w * column_x<H>(m0 + 1, EX.y, FX.y, E2, F2) : 0.f);
       }
 
-      // column centre offset tb = (l - H) - fx as a double-float (|l - H| >= 1 > |fx| or l == H)
-      const float th = (float)(l - H) - fx;
-      const float tl = ((float)(l - H) - th) - fx;
+      // the pair's centre offset tp = (2j - H + 1/2) - fx as a double-float (Fast2Sum:
+      // |2j - H + 1/2| >= 1/2 >= |fx|)
+      const float ep = (float)(m0 - H) + 0.5f;
+      const float th = ep - fx;
+      const float tl = (ep - th) - fx;
 
-      // moments of tau on the column under phi_x(tb + tau) / phi_x(tb) = 2^(al (tb tau + tau^2 / 2)),
-      // 5-point Gauss-Legendre: the centre node (factor 1) and two symmetric pairs
-      const float al = e1.w;
-      float s0 = kGl5WC, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f, s5 = 0.f, s6 = 0.f;
-      {
-        const float q2 = 0.5f * al;
-        const float c0 = al * th;
-#define E2E_GL_PAIR(I)                                                          \
-  {                                                                             \
-    const float cc = q2 * kGl5T##I##P2, cl = c0 * kGl5T##I##P1;                 \
-    const float ep = ex2_approx(cc + cl), em = ex2_approx(cc - cl);             \
-    const float sp = kGl5W##I * (ep + em), dm = kGl5W##I * (ep - em);           \
-    s0 += sp; s2 = fmaf(sp, kGl5T##I##P2, s2); s4 = fmaf(sp, kGl5T##I##P4, s4); \
-    s6 = fmaf(sp, kGl5T##I##P6, s6); s1 = fmaf(dm, kGl5T##I##P1, s1);           \
-    s3 = fmaf(dm, kGl5T##I##P3, s3); s5 = fmaf(dm, kGl5T##I##P5, s5);           \
+      // moments of u = tau -+ 1/2 (the offset from the pair's centre) on the left / right
+      // column under phi_x(tc + tau) / phi_x(tc) = 2^(al (tc tau + tau^2 / 2)), tc = tp -+ 1/2
+      // the column's centre, 5-point Gauss-Legendre; the left column's odd moments come out
+      // mirrored (s_k (-1)^k), which its series constants absorb
+      const float al = e1.w, q2 = 0.5f * al;
+      const float2 c0 = f2(al * (th - 0.5f), al * (th + 0.5f));
+      float2 s[kGlKmax + 1];
+#pragma unroll
+      for (int k = 0; k <= kGlKmax; ++k) s[k] = f2(kGlC[k], kGlC[k]);
+#define E2E_GL_NODE(T, TSQ, A, B)                                                               \
+  {                                                                                             \
+    const float2 cl = __fmul2_rn(c0, f2(T, T));                                                 \
+    const float2 cc = f2(q2 * TSQ, q2 * TSQ);                                                   \
+    const float2 xp = __fadd2_rn(cc, cl), xm = __fadd2_rn(cc, neg2(cl));                        \
+    const float2 ep2 = f2(ex2_approx(xp.x), ex2_approx(xp.y)), em2 = f2(ex2_approx(xm.x), ex2_approx(xm.y)); \
+    const float2 pa = f2(em2.x, ep2.y), pb = f2(ep2.x, em2.y);                                 \
+    _Pragma("unroll") for (int k = 0; k <= kGlKmax; ++k) {                                     \
+      s[k] = __ffma2_rn(pa, f2(A[k], A[k]), s[k]);                                              \
+      s[k] = __ffma2_rn(pb, f2(B[k], B[k]), s[k]);                                              \
+    }                                                                                           \
   }
-        E2E_GL_PAIR(0)
-        E2E_GL_PAIR(1)
-#undef E2E_GL_PAIR
-      }
-      // G(V) = sum_k a_k He_(k-1)(V) as a quintic, scaled by 2 / sqrt(2 pi) and written as a
-      // polynomial in w = V / sqrt(2 ln 2) (the row edges' argument in log2 units)
-      float g0, g1, g2, g3, g4, g5;
+      E2E_GL_NODE(kGlT0, kGlT0Sq, kGlA0, kGlB0)
+      E2E_GL_NODE(kGlT1, kGlT1Sq, kGlA1, kGlB1)
+#undef E2E_GL_NODE
+      // a_k = c_k s_k / s_0, and G(V) = sum_k a_k He_(k-1)(V) as a polynomial in V
+      float2 gc0, gc1, gc2, gc3, gc4, gc5, gc6, gc7;
       {
-        const float r = rcp_approx(s0), ep1 = e1.z;
-        const float p1 = ep1, p2 = p1 * ep1, p3 = p2 * ep1, p4 = p3 * ep1, p5 = p4 * ep1, p6 = p5 * ep1;
-        const float a1 = -p1 * (s1 * r), a2 = -p2 * (s2 * r) * 0.5f, a3 = -p3 * (s3 * r) * (1.f / 6.f);
-        const float a4 = -p4 * (s4 * r) * (1.f / 24.f), a5 = -p5 * (s5 * r) * (1.f / 120.f);
-        const float a6 = -p6 * (s6 * r) * (1.f / 720.f);
-        g0 = kHerm0 * (a1 - a3 + 3.f * a5);
-        g1 = kHerm1 * (a2 - 3.f * a4 + 15.f * a6);
-        g2 = kHerm2 * (a3 - 6.f * a5);
-        g3 = kHerm3 * (a4 - 10.f * a6);
-        g4 = kHerm4 * a5;
-        g5 = kHerm5 * a6;
+        const float2 r = f2(rcp_approx(s[0].x), rcp_approx(s[0].y));
+        float2 av[kGlKmax + 1];
+#pragma unroll
+        for (int k = 1; k <= kGlKmax; ++k) av[k] = __fmul2_rn(__fmul2_rn(s[k], r), gcs[k - 1]);
+        const float2 c3 = f2(3.f, 3.f), c6 = f2(-6.f, -6.f), c10 = f2(-10.f, -10.f), c15 = f2(15.f, 15.f);
+        const float2 m15 = f2(-15.f, -15.f), m21 = f2(-21.f, -21.f), c45 = f2(45.f, 45.f);
+        gc0 = __ffma2_rn(av[7], m15, __ffma2_rn(av[5], c3, __fadd2_rn(av[1], neg2(av[3]))));
+        gc1 = __ffma2_rn(av[8], f2(-105.f, -105.f), __ffma2_rn(av[6], c15, __ffma2_rn(av[4], f2(-3.f, -3.f), av[2])));
+        gc2 = __ffma2_rn(av[7], c45, __ffma2_rn(av[5], c6, av[3]));
+        gc3 = __ffma2_rn(av[8], f2(105.f, 105.f), __ffma2_rn(av[6], c10, av[4]));
+        gc4 = __ffma2_rn(av[7], m15, av[5]);
+        gc5 = __ffma2_rn(av[8], m21, av[6]);
+        gc6 = av[7];
+        gc7 = av[8];
       }
-      // conditional centre of the column relative to the window centre: f = fy + beta tb (double-float)
+      // conditional centre of the pair relative to the window centre: f = fy + beta tp (double-float)
       float fh, fl;
       {
         const float bh = e1.x, bl = e1.y;
@@ -280,17 +313,14 @@ __global__ void __launch_bounds__(kEThreads, 5) k_render_ellip(const MixedArgs a
         float se;
         two_sum(fy, ph, fh, se);
         fl = se + pl;
-        const float t = fh + fl;
-        fl = fl - (t - fh);
-        fh = t;
       }
       const float gch = e0.z, gcl = e0.w;
       // f = fc + ff, fc on a 2^-19 grid (exact split), ff g_ch in FP32
       const float fc = rintf(fh * 524288.f) * (1.f / 524288.f);
       const float ffg = ((fh - fc) + fl) * gch;
-      const float wq = w * tx;
-      // the K + 1 row edges in pairs (n, n + 1); pixel n spans edges n and n + 1
-      float Ep = 0.f, Fp = 0.f, hp = 0.f, whp = 0.f;
+      // the K + 1 row edges in pairs (n, n + 1), shared by both columns; pixel n spans edges n and n + 1
+      float Ep = 0.f, Fp = 0.f, whp = 0.f;
+      float2 hp = f2(0.f, 0.f);
 #pragma unroll
       for (int n = 0; n <= K; n += 2) {
         // w = (e - f) g_c for the half-integers e = n - H -+ 1/2: e - fc exact, its product with
@@ -313,28 +343,34 @@ __global__ void __launch_bounds__(kEThreads, 5) k_render_ellip(const MixedArgs a
           const float2 fe = erf_small2(wn);
           F = f2(near0 ? fe.x : F.x, near1 ? fe.y : F.y);
         }
-        float2 Gv = __ffma2_rn(f2(g5, g5), wn, f2(g4, g4));
-        Gv = __ffma2_rn(Gv, wn, f2(g3, g3));
-        Gv = __ffma2_rn(Gv, wn, f2(g2, g2));
-        Gv = __ffma2_rn(Gv, wn, f2(g1, g1));
-        Gv = __ffma2_rn(Gv, wn, f2(g0, g0));
-        const float2 h = __fmul2_rn(dens, Gv);
+        const float2 V = __fmul2_rn(wn, f2(kSqrt2Ln2, kSqrt2Ln2));
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           const int ne = n + e;
-          const float Ee = e ? E.y : E.x, Fe = e ? F.y : F.x, he = e ? h.y : h.x, we = e ? wn.y : wn.x;
+          const float Ee = e ? E.y : E.x, Fe = e ? F.y : F.x, we = e ? wn.y : wn.x;
+          const float2 Vb = e ? f2(V.y, V.y) : f2(V.x, V.x);
+          float2 G = __ffma2_rn(gc7, Vb, gc6);
+          G = __ffma2_rn(G, Vb, gc5);
+          G = __ffma2_rn(G, Vb, gc4);
+          G = __ffma2_rn(G, Vb, gc3);
+          G = __ffma2_rn(G, Vb, gc2);
+          G = __ffma2_rn(G, Vb, gc1);
+          G = __ffma2_rn(G, Vb, gc0);
+          const float de = e ? dens.y : dens.x;
+          const float2 h = __fmul2_rn(f2(de, de), G);
           if (ne > 0 && ne <= K) {
             // tails subtracted on one side of the conditional centre (erf near it), erf summed
-            // across it
+            // across it; the pair's two columns share this and differ in the series term
             const bool same = (we < 0.f) == (whp < 0.f);
             const bool small = fminf(fabsf(we), fabsf(whp)) < kErfMaxArg;
             const float pa = same && !small ? Ep : Fp;
             const float pb = same ? (small ? Fe : Ee) : -Fe;
-            acc[ne - 1] = fmaf(wq, fabsf(pa - pb) + (he - hp), acc[ne - 1]);
+            const float t = fabsf(pa - pb);
+            acc[ne - 1] = __ffma2_rn(wq, __fadd2_rn(f2(t, t), __fadd2_rn(h, neg2(hp))), acc[ne - 1]);
           }
           Ep = Ee;
           Fp = Fe;
-          hp = he;
+          hp = h;
           whp = we;
         }
       }
