@@ -21,13 +21,16 @@
 //   G_m(V)  = sum_{k >= 1} a_k He_(k-1)(V),   a_k = -eps^k mom_k[m] / k!,
 //
 // where mu0[m] is the column's x-integral and mom_k[m] the k-th moment of tau under phi_x
-// restricted to the column, normalised by its mass (Gauss-Legendre on the column).  With
-// |eps tau| <= |eps| / 2 and |eps| <= 0.2 (checked when the model is loaded), the series cut
-// after k = 6, with 5-point Gauss-Legendre moments, stays below 3e-9 of the pixel value (FP32
-// kernel); the FP64 kernel keeps k <= 9 with 12-point moments.
-// The column's own Phi differences carry the full accuracy: they are formed exactly like the
-// separable PSF's pixel integrals (tails subtracted on one side of the conditional mean, erf
-// across it), only with a per-column centre.
+// restricted to the column, normalised by its mass (Gauss-Legendre on the column).  The same
+// holds with the edges V_n taken at any reference abscissa tb' near the column and tau
+// replaced by the offset u = tb + tau - tb' from it.  The FP32 kernel takes tb' at the centre of
+// a pair of columns (u = tau -+ 1/2, |u| <= 1), so the pair's two columns share their K + 1
+// row edges and differ only in their moments; with |eps| <= 0.2 (checked when the model is
+// loaded) the series cut after k = 8, with 5-point Gauss-Legendre moments, stays below 1e-8 of
+// the pixel value.  The FP64 kernel takes each column's own centre (|u| <= 1/2), k <= 9 and
+// 12-point moments.  The Phi differences carry the full accuracy: they are formed exactly like
+// the separable PSF's pixel integrals (tails subtracted on one side of the conditional mean,
+// erf across it), only with a per-pair (FP32) or per-column (FP64) centre.
 #include "e2e_device.cuh"
 #include "e2e_kernels.h"
 #include "mixed_common.cuh"
