@@ -16,7 +16,7 @@ import os
 
 import numpy as np
 
-KMAX = 8  # highest moment of the FP32 kernel's series
+KMAX = 7  # highest moment of the FP32 kernel's series
 
 
 def rule(q):

@@ -26,7 +26,7 @@
 // replaced by the offset u = tb + tau - tb' from it.  The FP32 kernel takes tb' at the centre of
 // a pair of columns (u = tau -+ 1/2, |u| <= 1), so the pair's two columns share their K + 1
 // row edges and differ only in their moments; with |eps| <= 0.2 (checked when the model is
-// loaded) the series cut after k = 8, with 5-point Gauss-Legendre moments, stays below 1e-8 of
+// loaded) the series cut after k = 7, with 5-point Gauss-Legendre moments, stays below 2e-8 of
 // the pixel value.  The FP64 kernel takes each column's own centre (|u| <= 1/2), k <= 9 and
 // 12-point moments.  The Phi differences carry the full accuracy: they are formed exactly like
 // the separable PSF's pixel integrals (tails subtracted on one side of the conditional mean,
@@ -83,7 +83,7 @@ __device__ __forceinline__ float column_x(int m, float EL, float FL, float ER, f
 // staging, then for each stamp every lane evaluates its column pair: x-edges 2j and 2j + 1
 // (edge 2j + 2 from the next lane by a shuffle), the moments of each column about the pair's
 // centre, and the K + 1 row edges of the pair's conditional profile, shared by both columns,
-// in packed pairs; each column's series term is a degree-7 polynomial per edge.  The lane adds
+// in packed pairs; each column's series term is a degree-6 polynomial per edge.  The lane adds
 // the 2K pixels to its registers; consecutive slit points mostly share their window origin, so
 // the lanes deposit their columns into the item's box (exact fixed point, shared-memory
 // integer atomics) only when the origin moves and at the end of the run.
@@ -290,22 +290,21 @@ __global__ void __launch_bounds__(kEThreads, 5) k_render_ellip(const MixedArgs a
       E2E_GL_NODE(kGlT1, kGlT1Sq, kGlA1, kGlB1)
 #undef E2E_GL_NODE
       // a_k = c_k s_k / s_0, and G(V) = sum_k a_k He_(k-1)(V) as a polynomial in V
-      float2 gc0, gc1, gc2, gc3, gc4, gc5, gc6, gc7;
+      float2 gc0, gc1, gc2, gc3, gc4, gc5, gc6;
       {
         const float2 r = f2(rcp_approx(s[0].x), rcp_approx(s[0].y));
         float2 av[kGlKmax + 1];
 #pragma unroll
         for (int k = 1; k <= kGlKmax; ++k) av[k] = __fmul2_rn(__fmul2_rn(s[k], r), gcs[k - 1]);
         const float2 c3 = f2(3.f, 3.f), c6 = f2(-6.f, -6.f), c10 = f2(-10.f, -10.f), c15 = f2(15.f, 15.f);
-        const float2 m15 = f2(-15.f, -15.f), m21 = f2(-21.f, -21.f), c45 = f2(45.f, 45.f);
+        const float2 m15 = f2(-15.f, -15.f), c45 = f2(45.f, 45.f);
         gc0 = __ffma2_rn(av[7], m15, __ffma2_rn(av[5], c3, __fadd2_rn(av[1], neg2(av[3]))));
-        gc1 = __ffma2_rn(av[8], f2(-105.f, -105.f), __ffma2_rn(av[6], c15, __ffma2_rn(av[4], f2(-3.f, -3.f), av[2])));
+        gc1 = __ffma2_rn(av[6], c15, __ffma2_rn(av[4], f2(-3.f, -3.f), av[2]));
         gc2 = __ffma2_rn(av[7], c45, __ffma2_rn(av[5], c6, av[3]));
-        gc3 = __ffma2_rn(av[8], f2(105.f, 105.f), __ffma2_rn(av[6], c10, av[4]));
+        gc3 = __ffma2_rn(av[6], c10, av[4]);
         gc4 = __ffma2_rn(av[7], m15, av[5]);
-        gc5 = __ffma2_rn(av[8], m21, av[6]);
+        gc5 = av[6];
         gc6 = av[7];
-        gc7 = av[8];
       }
       // conditional centre of the pair relative to the window centre: f = fy + beta tp (double-float)
       float fh, fl;
@@ -352,8 +351,7 @@ __global__ void __launch_bounds__(kEThreads, 5) k_render_ellip(const MixedArgs a
           const int ne = n + e;
           const float Ee = e ? E.y : E.x, Fe = e ? F.y : F.x, we = e ? wn.y : wn.x;
           const float2 Vb = e ? f2(V.y, V.y) : f2(V.x, V.x);
-          float2 G = __ffma2_rn(gc7, Vb, gc6);
-          G = __ffma2_rn(G, Vb, gc5);
+          float2 G = __ffma2_rn(gc6, Vb, gc5);
           G = __ffma2_rn(G, Vb, gc4);
           G = __ffma2_rn(G, Vb, gc3);
           G = __ffma2_rn(G, Vb, gc2);
