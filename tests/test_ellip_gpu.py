@@ -64,6 +64,9 @@ CASES = [
     dict(seed=106, K=3, degree=1, n_lambda=64, n_slit=5),
     dict(seed=107, K=1, degree=0, n_lambda=31, n_slit=2),
     dict(seed=108, K=11, theta_deg=19.0, sig=(2.0, 1.2)),  # eps = 0.17, near the accepted limit 0.2
+    dict(seed=109, K=5, degree=2, n_lambda=90, n_slit=11),
+    # a wide, strongly correlated PSF: eps = 0.18, correlation 0.48, x-marginal width 2.9 px
+    dict(seed=110, K=13, theta_deg=12.0, sig=(3.0, 1.0)),
 ]
 
 
