@@ -602,7 +602,7 @@ def pipe_rates(B, dev, reps=3):
 
 def photon_run(B, r, mid, sids, w, stream, flush, stamp_ms, reps=3):
     """The photon Monte-Carlo renderer on the full-detector model, its spectra scaled to
-    1e7 / 1e8 / 1e9 expected photons: photons/s, and the photon count at which it costs what
+    1e7 ... 1e11 expected photons: photons/s, and the photon count at which it costs what
     one stamp render of the frame costs."""
     import torch
 
@@ -612,14 +612,15 @@ def photon_run(B, r, mid, sids, w, stream, flush, stamp_ms, reps=3):
               for s in w.model.slices)
     out = r.render_photons(mid, sids, seed=7, stream=stream, want_total=False)[0]
     rows = []
-    for target in (1e7, 1e8, 1e9):
+    for target in (1e7, 1e8, 1e9, 1e10, 1e11):
         k = target / tot
+        n_rep = reps if target < 1e11 else 1
         ids = []
         for f, sp in w.spectra.items():
             ids.append(r.load_spectrum(Bd_spec(sp, k)))
         _, n = r.render_photons(mid, ids, seed=7, out=out, stream=stream)
         ms = []
-        for _ in range(reps):
+        for _ in range(n_rep):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -631,9 +632,15 @@ def photon_run(B, r, mid, sids, w, stream, flush, stamp_ms, reps=3):
             Bd.e2e_unload_spectrum(r.ctx, i)
         t = statistics.median(ms)
         rows.append({"photons": n, "ms": t, "photons_per_s": n / (t * 1e-3)})
-    rate = rows[-1]["photons_per_s"]
+    # photon count at which a photon render costs one stamp render: log-log interpolation
+    # between the two runs around the stamp render's time
+    eq = None
+    for r0, r1 in zip(rows, rows[1:]):
+        if r0["ms"] <= stamp_ms <= r1["ms"]:
+            f = (np.log(stamp_ms) - np.log(r0["ms"])) / (np.log(r1["ms"]) - np.log(r0["ms"]))
+            eq = float(np.exp(np.log(r0["photons"]) + f * (np.log(r1["photons"]) - np.log(r0["photons"]))))
     return {"runs": rows, "stamp_render_ms": stamp_ms,
-            "photons_at_equal_cost": rate * stamp_ms * 1e-3,
+            "photons_at_equal_cost": eq,
             "note": "photon Monte-Carlo (Sec. 2.2 alternative): FP32 mapping from per-bin FP64 anchors and FP32 Box-Muller, each pixel decision bounded, FP64 redo when too close; bit-exact counts"}
 
 
