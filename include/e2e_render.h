@@ -166,7 +166,11 @@ const char* e2e_last_error(void);
 /* Load an optical model (the spectral-format database of Sec. 2.1, which the paper
  * computes once and reuses across simulations): validates it (degree, K odd, widths > 0 on
  * [-1, 1], finite coefficients, |eps| <= 0.2 for the elliptical PSF), copies it to the
- * device and plans the tiled render (synchronous; uses the context's device).
+ * device and plans the tiled render (synchronous; uses the context's device).  Resident per
+ * model: the slices, the plan (items, merge tiles and their lists), and per wavelength sample
+ * of every slice (degree + 3) x 16 bytes of precomputed mapping coefficients and PSF constants
+ * (261 MB for a 9216^2 frame of 340 slices x 6000 samples at degree 5); the tabulated PSF adds
+ * its coefficient tables.
  * Errors: E2E_EINVAL, E2E_ENOMEM, E2E_ECUDA. */
 int e2e_load_model(e2e_ctx* ctx, const e2e_model_desc* desc, uint64_t* model_id);
 int e2e_unload_model(e2e_ctx* ctx, uint64_t model_id);
