@@ -187,7 +187,10 @@ int e2e_unload_spectrum(e2e_ctx* ctx, uint64_t spec_id);
 
 /* Render every detector of `model` lit by the spectra `spec_ids` (one per fiber used by
  * the model; each order-slice takes the row of its fiber's spectrum for its order, whose
- * length must equal its n_lambda).
+ * length must equal its n_lambda).  The frame is the image model of Sec. 2.2: for every
+ * order-slice, wavelength sample and slit (sub-aperture) point, the PSF integrated over each
+ * pixel of the K x K window around the point's mapped position (spectral format of Sec.
+ * 2.1), weighted by the sampled flux times the bin width times the point's weight, summed.
  *   dst[d]: device pointer to detector d's frame, row-major, dtype E2E_F32 or E2E_F64,
  *           pitch_elems[d] elements between rows (pitch_elems may be NULL = width).
  *           Every pixel of the frame is written.
@@ -197,12 +200,13 @@ int e2e_unload_spectrum(e2e_ctx* ctx, uint64_t spec_id);
 int e2e_render(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids, int32_t precision,
                int32_t dtype, void* const* dst, const int64_t* pitch_elems, void* stream);
 
-/* As e2e_render, into frames the library allocates (stream-ordered, from the device's
+/* As e2e_render (the Sec. 2.2 frame), into frames the library allocates (stream-ordered, from the device's
  * memory pool, on `stream`) and owns until e2e_release_frame. */
 int e2e_render_alloc(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uint64_t* spec_ids,
                      int32_t precision, int32_t dtype, void* stream, uint64_t* frame_id);
 
-/* Copy detector `detector` of a library-owned frame (height*width elements of its dtype,
+/* Copy detector `detector` of a library-owned frame (the Sec. 2.2 frame of e2e_render_alloc;
+ * height*width elements of its dtype,
  * row-major) to dst (device or host memory, `bytes` must equal the frame's size).
  * Stream-ordered on `stream`, after the frame's render wherever that was enqueued; a host
  * destination is complete when the stream is.
@@ -212,7 +216,7 @@ int e2e_fetch_frame(e2e_ctx* ctx, uint64_t frame_id, int32_t detector, void* dst
                     size_t bytes, void* stream);
 int e2e_release_frame(e2e_ctx* ctx, uint64_t frame_id);
 
-/* Render every detector of `model` (as e2e_render) into HOST memory, overlapping the
+/* Render every detector of `model` (the Sec. 2.2 frame, as e2e_render) into HOST memory, overlapping the
  * device-to-host copy with the render: the mixed-precision frame is rendered in up to 16
  * bands of rows (whole merge tiles, the same fraction of every detector), and each band is
  * copied to host_dst[d] as soon as its pixels are final, while later bands still render.
