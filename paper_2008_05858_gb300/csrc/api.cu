@@ -896,16 +896,23 @@ int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, in
     int* count = nullptr;
     E2E_CK(sc.get((void**)&count, (size_t)P.n_tiles * sizeof(int)));
     if (count) E2E_CK(cudaMemsetAsync(count, 0, (size_t)P.n_tiles * sizeof(int), st));
-    {
+    const MergeArgs mg{P.d_items, P.d_tiles, P.d_lists, P.d_tile_of, P.d_grid_off, m->d_dims, count, d_dst, d_pitch,
+                       dtype == E2E_F32 ? 0 : 1, nullptr, 0};
+    bool zeros = false;  // the zero tiles ride as extra CTAs at the end of the first non-empty launch
+    for (auto& g : P.groups) {
+      MergeArgs mgg = mg;
+      if (!zeros && g.count > 0) {
+        mgg.zero_tiles = P.d_zero_tiles;
+        mgg.n_zero = P.n_zero_tiles;
+        zeros = true;
+      }
+      KernelTimer kt(ctx, st, "render_mixed");
+      E2E_CK(launch_items(ctx, m, g.K, g.first, g.count, d_table, store, st, &mgg));
+    }
+    if (!zeros) {  // no item at all: every tile is a zero tile
       KernelTimer kt(ctx, st, "merge_zero");
       E2E_CK(launch_merge(P.d_zero_tiles, P.n_zero_tiles, P.d_lists, P.d_items, store, d_dst, dtype, d_pitch,
                           m->d_dims, st));
-    }
-    const MergeArgs mg{P.d_items, P.d_tiles, P.d_lists, P.d_tile_of, P.d_grid_off, m->d_dims, count, d_dst, d_pitch,
-                       dtype == E2E_F32 ? 0 : 1};
-    for (auto& g : P.groups) {
-      KernelTimer kt(ctx, st, "render_mixed");
-      E2E_CK(launch_items(ctx, m, g.K, g.first, g.count, d_table, store, st, &mg));
     }
   } else {
     for (auto& g : P.groups) {

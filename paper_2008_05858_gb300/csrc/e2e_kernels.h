@@ -25,6 +25,8 @@ struct MergeArgs {
   void* const* dst;         // frames
   const int64_t* pitch;     // their pitches (elements)
   int dtype;                // 0 = FP32 frame, 1 = FP64 frame
+  const Tile* zero_tiles;   // tiles no item overlaps: written as zeros by the launch's last
+  int n_zero;               // n_zero CTAs (0 = none in this launch)
 };
 
 cudaError_t launch_render_fp64(int K, int n_slices, int64_t max_stamps, const DevSlice* slices,

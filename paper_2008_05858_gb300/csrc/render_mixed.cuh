@@ -66,6 +66,17 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
   constexpr int R = K + D;              // pixels of that profile
   constexpr int RYH = (RY + 1) / 2;     // tile rows accumulated per lane of a pair
   extern __shared__ __align__(16) unsigned char smem[];
+  if (mg.n_zero && (int)blockIdx.x >= (int)gridDim.x - mg.n_zero) {  // a tile no item overlaps: zeros
+    const Tile t = mg.zero_tiles[blockIdx.x - (gridDim.x - mg.n_zero)];
+    const int th = mg.dims[2 * t.det], tw = mg.dims[2 * t.det + 1];
+    if (mg.dtype == 0)
+      merge_tile<kThreads, false, float>(t, mg.lists, mg.items, a.store, reinterpret_cast<float* const*>(mg.dst)[t.det],
+                                         mg.pitch[t.det], th, tw, threadIdx.x);
+    else
+      merge_tile<kThreads, false, double>(t, mg.lists, mg.items, a.store, reinterpret_cast<double* const*>(mg.dst)[t.det],
+                                          mg.pitch[t.det], th, tw, threadIdx.x);
+    return;
+  }
   const Item it = a.items[blockIdx.x];
   const DevSlice& S = a.slices[it.slice];
   const int area = it.bw * it.bh;
@@ -349,7 +360,7 @@ static cudaError_t launch_one(const MixedArgs& a, const MergeArgs& mg, int n_ite
   auto kern = k_render_mixed<K, DX, DY, CHECK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<n_items, kThreads, smem, st>>>(FusedArgs{a, mg});
+  kern<<<n_items + mg.n_zero, kThreads, smem, st>>>(FusedArgs{a, mg});
   return cudaGetLastError();
 }
 
