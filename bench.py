@@ -482,8 +482,9 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "frame": "9216x9216 f32", "orders": 85, "fibers": 2, "slices": 2,
                    "n_lambda": 6000, "n_slit": 64, "degree": 5, "K": K, "stamps_per_frame": stamps,
-                   "precision": ("mixed (FP64 mapping; FP32 stamps from double-float edge arguments; FP32 run sums "
-                                 "of <= 16 stamps; exact 52-bit fixed-point item boxes; TwoSum merge of FP32 pairs)"),
+                   "precision": ("mixed (FP64 per-sample mapping coefficients, double-float FP32 mapping in s; "
+                                 "FP32 stamps from double-float edge arguments; FP32 run sums of <= 16 stamps; "
+                                 "exact 52-bit fixed-point item boxes; TwoSum merge of FP32 pairs)"),
                    "l2": "flushed between steps (256 MiB memset outside the timed events)",
                    "parallelism": f"row bands of one frame x{world}" if band else f"independent frame per GPU x{world}",
                    "plan": plan},

@@ -52,7 +52,9 @@ extern "C" {
 
 /* ------------------------------------------------------------------ enums */
 enum { E2E_PSF_SEPARABLE = 0, E2E_PSF_ELLIPTICAL = 1, E2E_PSF_TABLE = 2 };
-/* E2E_PREC_MIXED: FP64 mapping; FP32 PSF stamps from double-float edge arguments; FP32 sums
+/* E2E_PREC_MIXED: the mapping's per-sample coefficients in FP64, its polynomial in the slit
+ *                 coordinate in double-float FP32 (within ~1e-10 px of FP64); FP32 PSF stamps
+ *                 from double-float edge arguments; FP32 sums
  *                 over runs of <= 16 stamps in registers; each item's box summed exactly in
  *                 52-bit fixed point (shared-memory integer atomics) and stored as an FP32
  *                 (hi, lo) pair; boxes merged into the frame with TwoSum compensation (the
