@@ -376,19 +376,19 @@ int upload(T** dptr, const T* src, size_t n) {
 
 // ------------------------------------------------------------------ planning
 
-// Relative cost per stamp of a tile variant of the lane-pair kernel: each lane evaluates
-// the K+1 edges of one axis of the stamp's window (~30 FP32 operations and 2 SFU operations
-// per edge), shifts it into the tile (two selects per pixel), accumulates half of the
-// (K+DX) x (K+DY) tile, and once per run of B stamps maps the run, clears and flushes its
-// half (~30 operations per tile pixel: calibrated on the full-detector frame, K = 11, where
-// runs of 16 / 8 / 4 stamps took 7.41 / 9.30 / 10.18 ms); tiles above 84 accumulators per
-// lane halve the occupancy.
+// Relative cost per stamp of a tile variant of the separable kernel: a lane evaluates the
+// K+1 edges of one axis of a stamp's window (~30 FP32 operations and 2 SFU operations per
+// edge) and shifts it into the tile (two selects per pixel); the quad of lanes that owns the
+// run accumulates the (K+DX) x (K+DY) tile, a quarter of its rows per lane, and once per run
+// of B stamps maps the run, clears and flushes the tile (~30 operations per tile pixel:
+// calibrated on the full-detector frame, K = 11, where runs of 16 / 8 / 4 stamps took 7.41 /
+// 9.30 / 10.18 ms); tiles above 84 accumulators per lane halve the occupancy.
 double variant_cost(int K, int DX, int DY, int B) {
   const int D = std::max(DX, DY);
   const double edges = 2.0 * (K + 1);
   const double tile = (double)(K + DX) * (K + DY);
   double c = edges * 30.0 + 2.0 * (K + D) + tile + tile * 30.0 / B;
-  if ((K + DX) * ((K + DY + 1) / 2) > 84) c *= 1.6;
+  if ((K + DX) * ((K + DY + 3) / 4) > 84) c *= 1.6;
   return c;
 }
 

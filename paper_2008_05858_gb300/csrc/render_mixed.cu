@@ -1,10 +1,11 @@
 // Mixed-precision tiled renderer (separable Gaussian PSF), its planner and the tile merge kernel.
 //
 // Work item = one order-slice x a block of wavelength samples x a block of slit points.
-// Inside the item, each lane owns a *run* of B consecutive slit points of one wavelength
+// Inside the item, a quad of lanes owns a *run* of B consecutive slit points of one wavelength
 // sample: the run's stamps land within a (K+DX) x (K+DY) pixel tile (the plan checks this for
-// every run of the model), so the lane accumulates their outer products w * A_x (x) A_y in
-// FP32 registers and flushes the tile once per run into the item's box in shared memory.
+// every run of the model), so the quad accumulates their outer products w * A_x (x) A_y in
+// FP32 registers (a quarter of the tile's rows per lane) and flushes the tile once per run
+// into the item's box in shared memory.
 // The box holds 52-bit fixed-point sums (two 32-bit words per pixel, scaled by a power of
 // two above the item's total flux) updated with integer atomics: the accumulation is exact
 // and independent of the order of the flushes.  At the end the box is written to a scratch
@@ -15,9 +16,11 @@
 // the frame does not depend on scheduling.
 //
 // Precision (the paper's fidelity target, Sec. 2.2, is a photocenter shift below ~1e-5 px):
-// mapping in FP64, the centre split exactly into an integer pixel and an FP32 offset, PSF
+// per-sample mapping coefficients in FP64 (per-model tables), the polynomial in s in
+// double-float FP32, the centre split exactly into an integer pixel and an FP32 offset, PSF
 // pixel integrals in FP32 with double-float edge arguments (phi32.cuh), FP32 sums over one
-// run (<= B stamps) in registers, exact fixed-point sums per item, FP64 across items.
+// run (<= B stamps) in registers, exact fixed-point sums per item, compensated (TwoSum) sums
+// of FP32 pairs across items.
 #include "render_mixed.cuh"
 
 namespace e2e {

@@ -14,14 +14,17 @@ namespace e2e {
 #endif
 constexpr int kThreads = E2E_MIXED_THREADS;  // threads per render CTA
 constexpr int kWarps = kThreads / 32;
-constexpr int kPairs = kThreads / 2;
+constexpr int kQuads = kThreads / 4;  // runs in flight per CTA (a quad of lanes per run)
+// floats per profile row of the quads' exchange area: 16 used, padded to 80 bytes so that
+// the 16-byte chunks written by the lanes of a warp fall in distinct banks
+constexpr int kXchStride = 20;
 
 // ------------------------------------------------------------------------------ render
 
 
 // Shared-memory layout of one CTA (offsets in bytes), identical on host and device.
 struct MixedLayout {
-  size_t tabP, tabS, tabW, tabU, tabG, stage, boxh, boxl, total;
+  size_t tabP, tabS, tabW, tabU, tabG, stage, xch, boxh, boxl, total;
   __host__ __device__ MixedLayout(int J, int NK, int nd, int B, int area) {
     size_t o = 0;
     tabP = o; o += (size_t)J * nd * 16;      // P_b(lt) of x and y per sample, split_xy pairs
@@ -30,7 +33,8 @@ struct MixedLayout {
     tabU = o; o += (size_t)NK * 8;            // slit weights, (hi, lo) floats
     o = (o + 15) & ~(size_t)15;
     tabG = o; o += (size_t)J * 16;            // 1/(sqrt2 sigma) of x and y, (hi, lo) each
-    stage = o; o += (size_t)B * kPairs * 16;  // mapped stamps of the runs in flight
+    stage = o; o += (size_t)B * kQuads * 16;  // mapped stamps of the runs in flight
+    xch = o; o += (size_t)kQuads * 4 * kXchStride * 4;  // the quads' profile exchange
     boxh = o; o += (size_t)area * 4;          // fixed-point box, high words
     boxl = o; o += (size_t)area * 4;          // low words
     total = o;
@@ -41,12 +45,30 @@ struct MixedLayout {
 #ifndef E2E_MID_TILE_BLOCKS
 #define E2E_MID_TILE_BLOCKS 4
 #endif
+#ifndef E2E_SMALL_TILE_BLOCKS
+#define E2E_SMALL_TILE_BLOCKS 4
+#endif
 // CTAs per SM the register budget is set for (128-thread CTAs): 4 (128 registers) for lane
 // tiles up to 72 accumulators, E2E_MID_TILE_BLOCKS up to 84, else 2.
 template <int K, int DX, int DY>
 constexpr int mixed_min_blocks() {
-  return ((K + DX) * ((K + DY + 1) / 2) <= 72 ? 4 : ((K + DX) * ((K + DY + 1) / 2) <= 84 ? E2E_MID_TILE_BLOCKS : 2)) *
+  return ((K + DX) * ((K + DY + 3) / 4) <= 72 ? E2E_SMALL_TILE_BLOCKS : ((K + DX) * ((K + DY + 3) / 4) <= 84 ? E2E_MID_TILE_BLOCKS : 2)) *
          128 / kThreads;
+}
+
+// N consecutive floats from shared memory at p (p 4N-byte aligned when N is 2 or 4).
+template <int N>
+__device__ __forceinline__ void load_rows(const float* p, float (&v)[N]) {
+  if constexpr (N == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else if constexpr (N == 2) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x; v[1] = t.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = p[i];
+  }
 }
 
 // The separable kernel's arguments: the render's, then the fused tile merge's.
@@ -64,7 +86,10 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
   constexpr int RX = K + DX, RY = K + DY, H = K / 2;
   constexpr int D = DX > DY ? DX : DY;  // slack of the profile a lane evaluates
   constexpr int R = K + D;              // pixels of that profile
-  constexpr int RYH = (RY + 1) / 2;     // tile rows accumulated per lane of a pair
+  constexpr int RY4 = (RY + 3) / 4;     // tile rows accumulated per lane of a quad
+  constexpr int RC = (R + 3) / 4;       // 16-byte chunks of a profile in the exchange
+  constexpr int RXC = (RX + 3) / 4;     // chunks of an x profile the tile reads
+  static_assert(4 * RC <= kXchStride, "profile row exceeds the exchange stride");
   extern __shared__ __align__(16) unsigned char smem[];
   if (mg.n_zero && (int)blockIdx.x >= (int)gridDim.x - mg.n_zero) {  // a tile no item overlaps: zeros
     const Tile t = mg.zero_tiles[blockIdx.x - (gridDim.x - mg.n_zero)];
@@ -88,6 +113,7 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
   float2* tabU = reinterpret_cast<float2*>(smem + L.tabU);
   float4* tabG = reinterpret_cast<float4*>(smem + L.tabG);
   int4* stage = reinterpret_cast<int4*>(smem + L.stage);
+  float* xch = reinterpret_cast<float*>(smem + L.xch);
   int* boxh = reinterpret_cast<int*>(smem + L.boxh);
   unsigned* boxl = reinterpret_cast<unsigned*>(smem + L.boxl);
   __shared__ double s_w[kWarps], s_u[kWarps];
@@ -146,57 +172,62 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
   const int Psh = total > 0.0 ? max(-100, min(100, 52 - ex)) : 0;
   const float sc = ldexpf(1.f, Psh), sc_hi = ldexpf(1.f, Psh - 22);
 
-  // A lane pair owns one run: lane 0 evaluates the x profile, lane 1 the y profile (same
-  // code, different inputs), they swap profiles by shuffle, and each accumulates half of
-  // the tile's rows.
-  const int q = lane >> 1, par = lane & 1;
+  // A quad of lanes owns one run and takes its stamps two at a time: lanes 0 and 1 evaluate
+  // the x and y profiles of the even stamp, lanes 2 and 3 those of the odd one (same code,
+  // different inputs).  The four profiles go through shared memory, and each lane of the quad
+  // accumulates its quarter of the tile's rows from both stamps, in stamp order.
+  const int quad = lane >> 2, qi = lane & 3, slot = qi >> 1, axis = qi & 1;
   const int nrc = (it.nk + a.B - 1) / a.B;
-  const int njh = (it.nj + 15) / 16;
-  const int ntask = njh * nrc;
-  int4* mystage = stage + warp * 16 + q;
+  const int njq = (it.nj + 7) / 8;
+  const int ntask = njq * nrc;
+  int4* mystage = stage + warp * 8 + quad;
+  float* qrow = xch + (warp * 8 + quad) * 4 * kXchStride;  // rows: x, y of the even stamp, x, y of the odd
+  float* myrow = qrow + (slot * 2 + axis) * kXchStride;
   for (int task = warp; task < ntask && total > 0.0; task += kWarps) {
-    const int jj = (task % njh) * 16 + q;
-    const bool jvalid = jj < it.nj;      // uniform over the pair
-    const int kk0 = (task / njh) * a.B;  // first slit point of the run, relative to the item
+    const int jj = (task % njq) * 8 + quad;
+    const bool jvalid = jj < it.nj;      // uniform over the quad
+    const int kk0 = (task / njq) * a.B;  // first slit point of the run, relative to the item
     const int nb = min(a.B, it.nk - kk0);
-    // map the run's stamps (double-float), half each, into the staging area
+    // map the run's stamps (double-float), a quarter each, into the staging area
     {
       const float4* Pj = tabP + (jvalid ? jj : 0) * nd;
-      for (int b = par; b < nb; b += 2) {
+      for (int b = qi; b < nb; b += 4) {
         int ci = kOffFrame, ri = kOffFrame;
         float fx = 0.f, fy = 0.f;
         if (jvalid) map_stamp_df(Pj, S.degree, tabS[kk0 + b], ci, fx, ri, fy);
-        mystage[b * kPairs] = make_int4(ci, ri, __float_as_int(fx), __float_as_int(fy));
+        mystage[b * kQuads] = make_int4(ci, ri, __float_as_int(fx), __float_as_int(fy));
       }
     }
     __syncwarp();
     int xmn = 1 << 30, ymn = 1 << 30;
     for (int b = 0; b < nb; ++b) {
-      const int4 st = mystage[b * kPairs];
+      const int4 st = mystage[b * kQuads];
       if (st.x != kOffFrame && st.y != kOffFrame) {
         xmn = min(xmn, st.x);
         ymn = min(ymn, st.y);
       }
     }
     const float4 g4 = jvalid ? tabG[jj] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float gh = par ? g4.z : g4.x, gl = par ? g4.w : g4.y;
+    const float gh = axis ? g4.z : g4.x, gl = axis ? g4.w : g4.y;
     const float2 wj = jvalid ? tabW[jj] : make_float2(0.f, 0.f);
-    float acc[RYH][RX];
+    float acc[RY4][RX];
 #pragma unroll
-    for (int r = 0; r < RYH; ++r)
+    for (int r = 0; r < RY4; ++r)
 #pragma unroll
       for (int c = 0; c < RX; ++c) acc[r][c] = 0.f;
-    for (int b = 0; b < nb; ++b) {
-      const int4 st = mystage[b * kPairs];
+    const int nstep = (nb + 1) >> 1;
+    for (int step = 0; step < nstep; ++step) {
+      const int b = 2 * step + slot;
+      const int4 st = b < nb ? mystage[b * kQuads] : make_int4(kOffFrame, kOffFrame, 0, 0);
       const bool on = st.x != kOffFrame && st.y != kOffFrame;
-      const int o = on ? (par ? st.y - ymn : st.x - xmn) : 0;  // window offset in the tile, 0..D
+      const int o = on ? (axis ? st.y - ymn : st.x - xmn) : 0;  // window offset in the tile, 0..D
       if constexpr (CHECK) {
-        if (o > (par ? DY : DX)) atomicAdd(a.err, 1);  // the run outgrew the planned tile
+        if (o > (axis ? DY : DX)) atomicAdd(a.err, 1);  // the run outgrew the planned tile
       }
-      const float f = __int_as_float(par ? st.w : st.z);
-      const float2 uk = tabU[kk0 + b];
+      const float f = on ? __int_as_float(axis ? st.w : st.z) : 0.f;
+      const float2 uk = tabU[kk0 + min(b, nb - 1)];
       const float w = on ? fmaf(wj.x, uk.x, fmaf(wj.x, uk.y, wj.y * uk.x)) : 0.f;
-      const float mult = par ? (on ? 1.f : 0.f) : w;  // the weight rides on the x profile
+      const float mult = axis ? (on ? 1.f : 0.f) : w;  // the weight rides on the x profile
       // Profile of the stamp's own K-pixel window, window pixel m spanning edges m and m+1
       // at offsets (m - H -+ 1/2) - f from the stamp centre: tails E = erfc(|w|) at the edges
       // off the centre pixel, and erf F = erf(|w|) at the four edges around the centre pixel H.
@@ -263,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
       win[K - 1] *= mult;
       // place the window at its offset o (0..D) in the tile, prof[c] = win[c - o], as a shift
       // by o & 1 and then by o & 2: two selects per tile pixel
-      float prof[R];
+      float prof[4 * RC];
       if constexpr (D == 0) {
 #pragma unroll
         for (int c = 0; c < R; ++c) prof[c] = win[c];
@@ -281,36 +312,49 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
           }
         }
       }
-      float ax[RX], ay[RYH];
 #pragma unroll
-      for (int c = 0; c < R; ++c) {
-        const float other = __shfl_xor_sync(0xffffffffu, prof[c], 1);
-        if (c < RX) ax[c] = par ? other : prof[c];
-        if (c < RYH) ay[c] = par ? 0.f : other;  // lane 0: rows 0..RYH-1 of lane 1's y profile
+      for (int c = R; c < 4 * RC; ++c) prof[c] = 0.f;
+      // exchange: each lane publishes its profile, then reads the two x profiles whole and
+      // its own rows of the two y profiles
+#pragma unroll
+      for (int q4 = 0; q4 < RC; ++q4)
+        reinterpret_cast<float4*>(myrow)[q4] = make_float4(prof[4 * q4], prof[4 * q4 + 1], prof[4 * q4 + 2], prof[4 * q4 + 3]);
+      __syncwarp();
+      float xa[4 * RXC], xb[4 * RXC], ya[RY4], yb[RY4];
+#pragma unroll
+      for (int q4 = 0; q4 < RXC; ++q4) {
+        const float4 va = reinterpret_cast<const float4*>(qrow)[q4];
+        const float4 vb = reinterpret_cast<const float4*>(qrow + 2 * kXchStride)[q4];
+        xa[4 * q4] = va.x; xa[4 * q4 + 1] = va.y; xa[4 * q4 + 2] = va.z; xa[4 * q4 + 3] = va.w;
+        xb[4 * q4] = vb.x; xb[4 * q4 + 1] = vb.y; xb[4 * q4 + 2] = vb.z; xb[4 * q4 + 3] = vb.w;
       }
+      load_rows<RY4>(qrow + kXchStride + qi * RY4, ya);
+      load_rows<RY4>(qrow + 3 * kXchStride + qi * RY4, yb);
+      __syncwarp();  // the exchange rows are rewritten by the next step
 #pragma unroll
-      for (int i = 0; i < RYH; ++i)
-        if (RYH + i < RY) ay[i] = par ? prof[RYH + i] : ay[i];  // lane 1: its own rows RYH..RY-1
-#pragma unroll
-      for (int r = 0; r < RYH; ++r) {
-        const float2 yy = f2(ay[r], ay[r]);
+      for (int r = 0; r < RY4; ++r) {
+        const float2 yya = f2(ya[r], ya[r]), yyb = f2(yb[r], yb[r]);
 #pragma unroll
         for (int c = 0; c + 1 < RX; c += 2) {
-          const float2 v = __ffma2_rn(yy, f2(ax[c], ax[c + 1]), f2(acc[r][c], acc[r][c + 1]));
+          float2 v = __ffma2_rn(yya, f2(xa[c], xa[c + 1]), f2(acc[r][c], acc[r][c + 1]));
+          v = __ffma2_rn(yyb, f2(xb[c], xb[c + 1]), v);
           acc[r][c] = v.x;
           acc[r][c + 1] = v.y;
         }
-        if constexpr (RX % 2 == 1) acc[r][RX - 1] = fmaf(ay[r], ax[RX - 1], acc[r][RX - 1]);
+        if constexpr (RX % 2 == 1) {
+          acc[r][RX - 1] = fmaf(ya[r], xa[RX - 1], acc[r][RX - 1]);
+          acc[r][RX - 1] = fmaf(yb[r], xb[RX - 1], acc[r][RX - 1]);
+        }
       }
     }
     __syncwarp();  // the staging is reused by the next task
     // flush this lane's rows of the run tile as exact fixed-point increments
-    if (xmn != (1 << 30)) {
-      const int gx0 = xmn - H - it.bx0, gy0 = ymn - H - it.by0 + par * RYH;
-      const int nrow = min(RYH, RY - par * RYH);
+    const int nrow = min(RY4, RY - qi * RY4);
+    if (xmn != (1 << 30) && nrow > 0) {
+      const int gx0 = xmn - H - it.bx0, gy0 = ymn - H - it.by0 + qi * RY4;
       const bool inside = gx0 >= 0 && gx0 + RX <= it.bw && gy0 >= 0 && gy0 + nrow <= it.bh;
 #pragma unroll
-      for (int r = 0; r < RYH; ++r) {
+      for (int r = 0; r < RY4; ++r) {
         const int gy = gy0 + r;
         if constexpr (CHECK) {  // outside the box is legitimate only off the detector
           if (r < nrow && !inside && (gy < 0 || gy >= it.bh)) {
