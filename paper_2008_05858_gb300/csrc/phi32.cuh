@@ -126,6 +126,29 @@ __device__ __forceinline__ float2 tail2x2(float2 wh, float2 wl) {
   return __fmul2_rn(__fmul2_rn(ex, P), f2(rcp_approx(Q.x), rcp_approx(Q.y)));
 }
 
+// tail2x2 of arguments whose low parts come doubled (wl2 = 2 wl, exactly): the same
+// operations with the doubling of wh folded into the argument.
+__device__ __forceinline__ float2 tail2x2_w2(float2 wh, float2 wl2) {
+  const float2 p = __fmul2_rn(wh, wh);
+  float2 e = __ffma2_rn(wh, wh, f2(-p.x, -p.y));
+  e = __ffma2_rn(wh, wl2, e);
+  const float2 ex = __fmul2_rn(f2(ex2_approx(-p.x), ex2_approx(-p.y)),
+                               __ffma2_rn(e, f2(-0.693147181f, -0.693147181f), f2(1.f, 1.f)));
+  const float2 x = f2(fminf(fabsf(wh.x), 40.f), fminf(fabsf(wh.y), 40.f));
+  float2 P = f2(kTailP4, kTailP4);
+  P = __ffma2_rn(P, x, f2(kTailP3, kTailP3));
+  P = __ffma2_rn(P, x, f2(kTailP2, kTailP2));
+  P = __ffma2_rn(P, x, f2(kTailP1, kTailP1));
+  P = __ffma2_rn(P, x, f2(kTailP0, kTailP0));
+  float2 Q = f2(kTailQ5, kTailQ5);
+  Q = __ffma2_rn(Q, x, f2(kTailQ4, kTailQ4));
+  Q = __ffma2_rn(Q, x, f2(kTailQ3, kTailQ3));
+  Q = __ffma2_rn(Q, x, f2(kTailQ2, kTailQ2));
+  Q = __ffma2_rn(Q, x, f2(kTailQ1, kTailQ1));
+  Q = __ffma2_rn(Q, x, f2(kTailQ0, kTailQ0));
+  return __fmul2_rn(__fmul2_rn(ex, P), f2(rcp_approx(Q.x), rcp_approx(Q.y)));
+}
+
 // tail2x2 that also returns 2^(-w^2) of each argument, for an argument held as a pair
 // (wh, wl) whose low part may exceed ulp(wh) (|wl| <= ~1e-6 |wh|, so wl^2 stays negligible):
 // the exponent is formed from the pair, the rational from wn = fl(wh + wl).
@@ -182,6 +205,30 @@ __device__ __forceinline__ void edge_arg2(float2 e, float f, float gh, float gl,
   const float2 dl = __fadd2_rn(__fadd2_rn(e, f2(-dh.x, -dh.y)), f2(-ff.x, -ff.y));
   wh = __fmul2_rn(dh, g);
   wl = __fadd2_rn(__ffma2_rn(dh, g, f2(-wh.x, -wh.y)), __ffma2_rn(dh, f2(gl, gl), __fmul2_rn(dl, g)));
+}
+
+// Offset split for edge arguments: f = fh + fl with fh on the 2^-20 grid (a magic-number
+// rounding: f + 12 lies in [8, 16), where the FP32 spacing is 2^-20), so that e - fh is exact
+// for every half-integer |e| <= 15/2 (|e - fh| <= 8 needs at most 23 bits) and fl = f - fh is
+// exact too (|fl| <= 2^-21).
+__device__ __forceinline__ void split_offset(float f, float& fh, float& fl) {
+  fh = __fsub_rn(__fadd_rn(f, 12.f), 12.f);
+  fl = __fsub_rn(f, fh);
+}
+
+// Edge arguments of the half-integers e.x and e.y, w = (e - f) g as (wh, 2 wl), from the split
+// offset: e - f = dh - fl with dh = e - fh exact.  wh = fl(dh gh + c1), c1 = -fl gh per stamp,
+// is w rounded once (within ~1.3 ulp, as edge_arg2's); its residual dh gh - wh is of the size
+// of c1 plus half an ulp of wh, so the FMA forms it to ~2^-45 g; the low part adds c1 back
+// and dh gl (gl2 = 2 gl and c2 = 2 c1 per stamp; fl gl, below 2^-45 g, is dropped).  w to
+// ~2^-45 g absolute, in five packed operations instead of edge_arg2's eight.
+__device__ __forceinline__ void edge_arg2_split(float2 e, float fh, float gh, float2 gl2, float c1, float2 c2,
+                                                float2& wh, float2& wl2) {
+  const float2 g = f2(gh, gh);
+  const float2 dh = __fadd2_rn(e, f2(-fh, -fh));
+  wh = __ffma2_rn(dh, g, f2(c1, c1));
+  const float2 err = __ffma2_rn(dh, g, f2(-wh.x, -wh.y));
+  wl2 = __ffma2_rn(err, f2(2.f, 2.f), __ffma2_rn(dh, gl2, c2));
 }
 
 }  // namespace e2e

@@ -188,7 +188,9 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
     const bool jvalid = jj < it.nj;      // uniform over the quad
     const int kk0 = (task / njq) * a.B;  // first slit point of the run, relative to the item
     const int nb = min(a.B, it.nk - kk0);
-    // map the run's stamps (double-float), a quarter each, into the staging area
+    // map the run's stamps (double-float), a quarter each, into the staging area; the tile
+    // origin is the least window centre of the run's on-frame stamps (reduced over the quad)
+    int xmn = 1 << 30, ymn = 1 << 30;
     {
       const float4* Pj = tabP + (jvalid ? jj : 0) * nd;
       for (int b = qi; b < nb; b += 4) {
@@ -196,19 +198,21 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
         float fx = 0.f, fy = 0.f;
         if (jvalid) map_stamp_df(Pj, S.degree, tabS[kk0 + b], ci, fx, ri, fy);
         mystage[b * kQuads] = make_int4(ci, ri, __float_as_int(fx), __float_as_int(fy));
+        if (ci != kOffFrame && ri != kOffFrame) {
+          xmn = min(xmn, ci);
+          ymn = min(ymn, ri);
+        }
       }
+    }
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+      xmn = min(xmn, __shfl_xor_sync(0xffffffffu, xmn, o));
+      ymn = min(ymn, __shfl_xor_sync(0xffffffffu, ymn, o));
     }
     __syncwarp();
-    int xmn = 1 << 30, ymn = 1 << 30;
-    for (int b = 0; b < nb; ++b) {
-      const int4 st = mystage[b * kQuads];
-      if (st.x != kOffFrame && st.y != kOffFrame) {
-        xmn = min(xmn, st.x);
-        ymn = min(ymn, st.y);
-      }
-    }
     const float4 g4 = jvalid ? tabG[jj] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float gh = axis ? g4.z : g4.x, gl = axis ? g4.w : g4.y;
+    const float2 gl2 = f2(2.f * gl, 2.f * gl);
     const float2 wj = jvalid ? tabW[jj] : make_float2(0.f, 0.f);
     float acc[RY4][RX];
 #pragma unroll
@@ -238,25 +242,29 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
       // when some lane of the warp needs them.  Edges are taken in pairs (packed arithmetic).
       float E[K + 1], F[K + 1], Wd[K + 1];
       constexpr int NT = K - 1;  // edges 0..H-1 and H+2..K
+      float fh, fl;
+      split_offset(f, fh, fl);
+      const float c1 = -fl * gh;
+      const float2 c2 = f2(2.f * c1, 2.f * c1);
 #pragma unroll
       for (int i = 0; i < NT; i += 2) {
         const int m0 = i < H ? i : i + 2, m1 = i + 1 < H ? i + 1 : i + 3;
-        float2 wh, wl;
-        edge_arg2(f2((float)(m0 - H) - 0.5f, (float)(m1 - H) - 0.5f), f, gh, gl, wh, wl);
-        const float2 t = tail2x2(wh, wl);
+        float2 wh, wl2;
+        edge_arg2_split(f2((float)(m0 - H) - 0.5f, (float)(m1 - H) - 0.5f), fh, gh, gl2, c1, c2, wh, wl2);
+        const float2 t = tail2x2_w2(wh, wl2);
         E[m0] = t.x;
         E[m1] = t.y;
         Wd[m0] = wh.x;
         Wd[m1] = wh.y;
       }
       {
-        float2 wc, wlc;  // edges H and H+1
-        edge_arg2(f2(-0.5f, 0.5f), f, gh, gl, wc, wlc);
+        float2 wc, wlc2;  // edges H and H+1
+        edge_arg2_split(f2(-0.5f, 0.5f), fh, gh, gl2, c1, c2, wc, wlc2);
         Wd[H] = wc.x;
         Wd[H + 1] = wc.y;
         const bool far = fabsf(wc.x) >= kErfMaxArg || fabsf(wc.y) >= kErfMaxArg;
         if (__any_sync(0xffffffffu, far)) {
-          const float2 t = tail2x2(wc, wlc);
+          const float2 t = tail2x2_w2(wc, wlc2);
           E[H] = t.x;
           E[H + 1] = t.y;
         } else {
