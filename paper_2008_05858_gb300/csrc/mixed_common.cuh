@@ -149,6 +149,44 @@ __device__ __forceinline__ void map_xy_df_regs(const float4 (&P)[9], int d, floa
   lo = ql;
 }
 
+// map_xy_df for N slit coordinates at once: one coefficient load per step for all N, the N
+// Horner chains interleaved for instruction-level parallelism; per coordinate exactly
+// map_xy_df's operations, so the same bits.
+template <int N>
+__device__ __forceinline__ void map_xy_df_n(const float4* P, int d, const float2 (&s)[N], float2 (&hi)[N],
+                                            float2 (&lo)[N]) {
+  float4 c = P[d];
+  float2 qh[N], ql[N];
+#pragma unroll
+  for (int n = 0; n < N; ++n) {
+    qh[n] = make_float2(c.x, c.y);
+    ql[n] = make_float2(c.z, c.w);
+  }
+  for (int b = d - 1; b >= 0; --b) {
+    c = P[b];
+    const float2 bh = make_float2(c.x, c.y), bl = make_float2(c.z, c.w);
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      const float2 sh = make_float2(s[n].x, s[n].x), sl = make_float2(s[n].y, s[n].y);
+      const float2 ph = __fmul2_rn(qh[n], sh);
+      float2 pe = __ffma2_rn(qh[n], sh, neg2(ph));
+      pe = __ffma2_rn(qh[n], sl, pe);
+      pe = __ffma2_rn(ql[n], sh, pe);
+      const float2 t = __fadd2_rn(ph, bh);
+      const float2 bb = __fadd2_rn(t, neg2(ph));
+      const float2 e = __fadd2_rn(__fadd2_rn(ph, neg2(__fadd2_rn(t, neg2(bb)))), __fadd2_rn(bh, neg2(bb)));
+      const float2 e2 = __fadd2_rn(e, __fadd2_rn(pe, bl));
+      qh[n] = __fadd2_rn(t, e2);
+      ql[n] = __fadd2_rn(e2, neg2(__fadd2_rn(qh[n], neg2(t))));
+    }
+  }
+#pragma unroll
+  for (int n = 0; n < N; ++n) {
+    hi[n] = qh[n];
+    lo[n] = ql[n];
+  }
+}
+
 // Window-centre pixels and FP32 offsets of a stamp (map_xy_df, then split_coord_df).
 __device__ __forceinline__ void map_stamp_df(const float4* P, int d, float2 s, int& ci, float& fx, int& ri,
                                              float& fy) {

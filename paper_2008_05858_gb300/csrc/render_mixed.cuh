@@ -190,17 +190,29 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
     const int nb = min(a.B, it.nk - kk0);
     // map the run's stamps (double-float), a quarter each, into the staging area; the tile
     // origin is the least window centre of the run's on-frame stamps (reduced over the quad)
+    // (a lane's stamps -- at most four: runs hold at most 16 -- mapped together)
     int xmn = 1 << 30, ymn = 1 << 30;
     {
       const float4* Pj = tabP + (jvalid ? jj : 0) * nd;
-      for (int b = qi; b < nb; b += 4) {
-        int ci = kOffFrame, ri = kOffFrame;
-        float fx = 0.f, fy = 0.f;
-        if (jvalid) map_stamp_df(Pj, S.degree, tabS[kk0 + b], ci, fx, ri, fy);
-        mystage[b * kQuads] = make_int4(ci, ri, __float_as_int(fx), __float_as_int(fy));
-        if (ci != kOffFrame && ri != kOffFrame) {
-          xmn = min(xmn, ci);
-          ymn = min(ymn, ri);
+      float2 sv[4], mh[4], ml[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sv[u] = tabS[kk0 + min(qi + 4 * u, nb - 1)];
+      map_xy_df_n<4>(Pj, S.degree, sv, mh, ml);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int b = qi + 4 * u;
+        if (b < nb) {
+          int ci = kOffFrame, ri = kOffFrame;
+          float fx = 0.f, fy = 0.f;
+          if (jvalid) {
+            split_coord_df(mh[u].x, ml[u].x, ci, fx);
+            split_coord_df(mh[u].y, ml[u].y, ri, fy);
+          }
+          mystage[b * kQuads] = make_int4(ci, ri, __float_as_int(fx), __float_as_int(fy));
+          if (ci != kOffFrame && ri != kOffFrame) {
+            xmn = min(xmn, ci);
+            ymn = min(ymn, ri);
+          }
         }
       }
     }
