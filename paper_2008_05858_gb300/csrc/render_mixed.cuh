@@ -312,33 +312,15 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
         win[m + 1] = p2.y;
       }
       win[K - 1] *= mult;
-      // place the window at its offset o (0..D) in the tile, prof[c] = win[c - o], as a shift
-      // by o & 1 and then by o & 2: two selects per tile pixel
-      float prof[4 * RC];
-      if constexpr (D == 0) {
+      // exchange: each lane publishes its window at its offset o (0..D) in a zeroed row, then
+      // reads the two x profiles whole and its own rows of the two y profiles
+      {
+        const int oc = min(o, D);
 #pragma unroll
-        for (int c = 0; c < R; ++c) prof[c] = win[c];
-      } else {
-        const bool s1 = (o & 1) != 0, s2 = (o & 2) != 0;
-        float t[K + 1];  // win shifted by o & 1
+        for (int q4 = 0; q4 < RC; ++q4) reinterpret_cast<float4*>(myrow)[q4] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int c = 0; c <= K; ++c) t[c] = s1 ? (c >= 1 ? win[c - 1] : 0.f) : (c < K ? win[c] : 0.f);
-#pragma unroll
-        for (int c = 0; c < R; ++c) {
-          if constexpr (D == 1) {
-            prof[c] = t[c];  // R = K + 1
-          } else {
-            prof[c] = s2 ? (c >= 2 && c - 2 <= K ? t[c - 2] : 0.f) : (c <= K ? t[c] : 0.f);
-          }
-        }
+        for (int m = 0; m < K; ++m) myrow[oc + m] = win[m];
       }
-#pragma unroll
-      for (int c = R; c < 4 * RC; ++c) prof[c] = 0.f;
-      // exchange: each lane publishes its profile, then reads the two x profiles whole and
-      // its own rows of the two y profiles
-#pragma unroll
-      for (int q4 = 0; q4 < RC; ++q4)
-        reinterpret_cast<float4*>(myrow)[q4] = make_float4(prof[4 * q4], prof[4 * q4 + 1], prof[4 * q4 + 2], prof[4 * q4 + 3]);
       __syncwarp();
       float xa[4 * RXC], xb[4 * RXC], ya[RY4], yb[RY4];
 #pragma unroll
