@@ -283,10 +283,20 @@ def cut_sample_oracle(B, dev, w: W.Workload, model, n_slices: int, n_slit: int, 
     return base, acc
 
 
+def headline_config(w: W.Workload, K: int, stamps: int, world: int, band: bool) -> dict:
+    """`config` of the headline line, shared by both arms: the workload the metric is quoted on
+    and how its steps are run."""
+    return {"workload": w.name, "frame": "9216x9216 f32", "orders": 85, "fibers": 2, "slices": 2,
+            "n_lambda": 6000, "n_slit": 64, "degree": 5, "K": K, "stamps_per_frame": stamps,
+            "l2": "flushed between steps (256 MiB memset outside the timed events)",
+            "parallelism": f"row bands of one frame x{world}" if band else f"independent frame per GPU x{world}"}
+
+
 def run_reference(args):
-    """The reference arm: the FP64 oracle on the host cores.  One step renders a bounded sample
-    of the headline workload -- its first order-slices in full, one per host core (up to 16) --
-    and the line reports that sample's own time per step and stamps/s."""
+    """The reference arm: the FP64 oracle on the host cores, on the headline's workload and
+    config.  One step renders a bounded sample of that workload -- its first order-slices in
+    full, one per host core (up to 16) -- and the line reports that sample's own time per step
+    and stamps/s, the sample named in `sample` and `cpu_baseline`."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
@@ -312,8 +322,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{w.name}: sample of {n} order-slices", "stamps_per_step": stamps,
-                   "frame": "9216x9216 f64 (the sample's traces)", "parallelism": f"{cores} host cores (OpenMP)"},
+        "config": headline_config(w, w.model.slices[0].K, w.model.n_stamps, world, args.shard == "band" and world > 1),
+        "sample": sample, "stamps_per_step": stamps,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -480,14 +490,11 @@ def run_gpu(args):
         "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "strong" if band else "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name, "frame": "9216x9216 f32", "orders": 85, "fibers": 2, "slices": 2,
-                   "n_lambda": 6000, "n_slit": 64, "degree": 5, "K": K, "stamps_per_frame": stamps,
-                   "precision": ("mixed (FP64 per-sample mapping coefficients, double-float FP32 mapping in s; "
-                                 "FP32 stamps from double-float edge arguments; FP32 run sums of <= 16 stamps; "
-                                 "exact 52-bit fixed-point item boxes; TwoSum merge of FP32 pairs)"),
-                   "l2": "flushed between steps (256 MiB memset outside the timed events)",
-                   "parallelism": f"row bands of one frame x{world}" if band else f"independent frame per GPU x{world}",
-                   "plan": plan},
+        "config": headline_config(w, K, stamps, world, band),
+        "precision": ("mixed (FP64 per-sample mapping coefficients, double-float FP32 mapping in s; "
+                      "FP32 stamps from double-float edge arguments; FP32 run sums of <= 16 stamps; "
+                      "exact 52-bit fixed-point item boxes; TwoSum merge of FP32 pairs)"),
+        "plan": plan,
         "roofline": roof, "roofline_other_pipe": other,
         "fp64_renderer": {"value": fp64_value, "unit": UNIT, "ms_per_step": statistics.median(fp64_ms),
                           "speedup_mixed_over_fp64": statistics.median(fp64_ms) / ms_per_step},
