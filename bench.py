@@ -952,7 +952,8 @@ def _load_spectrum_ptr(B, ctx, fiber, orders, lens, flux_tensor):
     return sid.value
 
 
-KERNEL_SOURCES = ["paper_2008_05858_gb300/csrc/render_mixed.cu", "paper_2008_05858_gb300/csrc/render_mixed.cuh",
+KERNEL_SOURCES = ["paper_2008_05858_gb300/csrc/render_mixed.cu", "paper_2008_05858_gb300/csrc/render_mixed_far.cu",
+                  "paper_2008_05858_gb300/csrc/render_mixed.cuh",
                   "paper_2008_05858_gb300/csrc/phi32.cuh",
                   "paper_2008_05858_gb300/csrc/mixed_common.cuh", "paper_2008_05858_gb300/csrc/merge_tile.cuh",
                   "paper_2008_05858_gb300/csrc/e2e_device.cuh", "paper_2008_05858_gb300/csrc/tail_coeffs.h"]

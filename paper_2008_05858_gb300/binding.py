@@ -140,6 +140,7 @@ _SIGS = {
     "e2e_kernel_times": ([C.c_void_p, C.POINTER(C.c_char_p), C.POINTER(C.c_float), C.c_int32,
                           C.POINTER(C.c_int32)], C.c_int),
     "e2e_eval_tail": ([C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
+    "e2e_eval_tail_far": ([C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
     "e2e_fma_probe": ([C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_int64), C.c_void_p], C.c_int),
     "e2e_render_static": ([C.c_void_p, C.c_uint64, C.c_int32, C.POINTER(C.c_uint64), C.c_int32,
                            C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.c_void_p], C.c_int),
@@ -479,6 +480,15 @@ def e2e_eval_tail(u_dev_ptr: int, n: int, out_dev_ptr: int, stream=None) -> None
                                       C.c_void_p(_stream_handle(stream)))
     if rc != E2E_OK:
         raise E2EError(rc, "e2e_eval_tail failed")
+
+
+def e2e_eval_tail_far(u_dev_ptr: int, n: int, out_dev_ptr: int, stream=None) -> None:
+    """out[i] = the renderer's far-edge FP32 erfc(|u[i]|) for |u[i]| >= 0.667 (device pointers
+    to n doubles / n floats)."""
+    rc = load_library().e2e_eval_tail_far(C.c_void_p(u_dev_ptr), n, C.c_void_p(out_dev_ptr),
+                                          C.c_void_p(_stream_handle(stream)))
+    if rc != E2E_OK:
+        raise E2EError(rc, "e2e_eval_tail_far failed")
 
 
 def e2e_fma_probe(fp64: bool, blocks: int, iters: int, sink_dev_ptr: int, stream=None) -> int:

@@ -24,6 +24,7 @@
 #include "../../include/e2e_render.h"
 #include "e2e_device.cuh"
 #include "e2e_kernels.h"
+#include "tail_coeffs.h"
 
 using namespace e2e;
 
@@ -64,6 +65,7 @@ struct SliceHost {
 struct Plan {
   bool ok = false;
   int B = 1, DX = 0, DY = 0, JB = 1, NB = 8, max_area = 0, max_deg = 0, nk_max = 1;
+  int far_tails = 0;  // separable kernel: every far edge's argument within the far-edge fit
   std::vector<Item> items;  // host copy
   int64_t store_elems = 0;
   size_t smem = 0;
@@ -267,6 +269,12 @@ double quad_min(const double* c) {
     if (t > -1 && t < 1) m = std::min(m, c[0] + c[1] * t + c[2] * t * t);
   }
   return m;
+}
+
+// Maximum of c0 + c1 t + c2 t^2 over t in [-1, 1].
+double quad_max(const double* c) {
+  const double n[3] = {-c[0], -c[1], -c[2]};
+  return -quad_min(n);
 }
 
 constexpr double kMaxEllipEps = 0.2;
@@ -623,6 +631,16 @@ int plan_model(Model* m) {
     }
   }
   P.B = bB;
+  // Edges two or more pixels from a stamp's centre sit at |e - f| >= 2 px, i.e. at arguments
+  // w >= 2 sqrt(log2 e) / (sqrt 2 sigma) in log2 units: when the model's widest PSF keeps that
+  // at or above the far-edge fit's lower end, the separable kernel takes the cheaper rational
+  // there (a margin of 1e-3 on the width covers the FP32 rounding of the per-sample constants).
+  {
+    double smax = 0.0;
+    for (auto& s : m->slices) smax = std::max(smax, std::max(quad_max(s.d.sigma_x), quad_max(s.d.sigma_y)));
+    const double limit = 2.0 * kSqrtLog2eD / (std::sqrt(2.0) * (double)kTailFarMinArg);
+    P.far_tails = !ellip && smax <= limit * (1.0 - 1e-3) ? 1 : 0;
+  }
   P.DX = bDX;
   P.DY = bDY;
   P.max_deg = 0;
@@ -807,7 +825,7 @@ cudaError_t launch_items(e2e_ctx* ctx, Model* m, int K, int first, int count, co
     return launch_render_ellip(K, m->d_slices, d_table, m->d_u, P.d_items + first, count, store, P.nk_max,
                                P.max_deg, P.smem, st, ctx->d_err);
   return launch_render_mixed(K, P.DX, P.DY, m->d_slices, d_table, m->d_u, P.d_items + first, count, store, P.B,
-                             P.JB, P.nk_max, P.max_deg, P.smem, st, ctx->d_err, mg);
+                             P.JB, P.nk_max, P.max_deg, P.far_tails, P.smem, st, ctx->d_err, mg);
 }
 
 int render_impl(e2e_ctx* ctx, Model* m, int n_spec, const uint64_t* spec_ids, int precision, int dtype,
@@ -1700,7 +1718,7 @@ int e2e_render_static(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uin
   for (auto& grp : P.groups) {
     KernelTimer kt(ctx, st, "render_mixed");
     E2E_CK(launch_render_mixed(grp.K, P.DX, P.DY, m->d_slices, d_table, m->d_u, P.d_items + grp.first, grp.count,
-                               store, P.B, P.JB, P.nk_max, P.max_deg, P.smem, st, ctx->d_err));
+                               store, P.B, P.JB, P.nk_max, P.max_deg, P.far_tails, P.smem, st, ctx->d_err));
   }
   {
     KernelTimer kt(ctx, st, "merge");

@@ -1,5 +1,6 @@
-// Diagnostic entry points: evaluate the renderer's FP32 Gaussian-tail function on given
-// arguments, so tests can check it against CUDA's FP64 erfc; and a fused multiply-add probe
+// Diagnostic entry points: evaluate the renderer's FP32 Gaussian-tail functions (the general
+// one and the far-edge one) on given arguments, so tests can check them against CUDA's FP64
+// erfc; and a fused multiply-add probe
 // that measures the FP32 and FP64 FMA rates the roofline of the ALU-bound kernels is quoted
 // against.
 #include "../../include/e2e_render.h"
@@ -7,13 +8,26 @@
 
 namespace {
 
+template <bool FAR>
 __global__ void k_eval_tail(const double* __restrict__ u, int64_t n, float* __restrict__ out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double v = u[i] * e2e::kSqrtLog2eD;  // the kernels' argument is in log2 units
     const float h = (float)v;
     const float l = (float)(v - (double)h);
-    out[i] = e2e::tail2(h, l);
+    out[i] = FAR ? e2e::tail2_far(h, l) : e2e::tail2(h, l);
   }
+}
+
+int eval_tail(bool far, const double* u_dev, int64_t n, float* out_dev, void* stream) {
+  if (n < 0 || (n > 0 && (!u_dev || !out_dev))) return E2E_EINVAL;
+  if (n == 0) return E2E_OK;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (far)
+    k_eval_tail<true><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(u_dev, n, out_dev);
+  else
+    k_eval_tail<false><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(u_dev, n, out_dev);
+  return cudaGetLastError() == cudaSuccess ? E2E_OK : E2E_ECUDA;
 }
 
 // Each thread runs kChains independent FMA chains of `iters` steps (no chain waits on another,
@@ -50,10 +64,9 @@ extern "C" int e2e_fma_probe(int32_t fp64, int32_t blocks, int32_t iters, void* 
 }
 
 extern "C" int e2e_eval_tail(const double* u_dev, int64_t n, float* out_dev, void* stream) {
-  if (n < 0 || (n > 0 && (!u_dev || !out_dev))) return E2E_EINVAL;
-  if (n == 0) return E2E_OK;
-  int64_t blocks = (n + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  k_eval_tail<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(u_dev, n, out_dev);
-  return cudaGetLastError() == cudaSuccess ? E2E_OK : E2E_ECUDA;
+  return eval_tail(false, u_dev, n, out_dev, stream);
+}
+
+extern "C" int e2e_eval_tail_far(const double* u_dev, int64_t n, float* out_dev, void* stream) {
+  return eval_tail(true, u_dev, n, out_dev, stream);
 }

@@ -43,8 +43,8 @@ bool mixed_variant_supported(int K, int DX, int DY);
 size_t mixed_smem_bytes(int area, int JB, int nk_max, int B, int nd);
 cudaError_t launch_render_mixed(int K, int DX, int DY, const DevSlice* slices, const double* const* flux_tab,
                                 const double* u_all, const Item* items, int n_items, float2* store, int B, int JB,
-                                int nk_max, int max_deg, size_t smem, cudaStream_t st, int* err = nullptr,
-                                const MergeArgs* mg = nullptr);
+                                int nk_max, int max_deg, int far_tails, size_t smem, cudaStream_t st,
+                                int* err = nullptr, const MergeArgs* mg = nullptr);
 cudaError_t launch_merge(const Tile* tiles, int n_tiles, const int32_t* lists, const Item* items, const float2* store,
                          void* const* dst, int dtype, const int64_t* pitch, const int* dims, cudaStream_t st);
 

@@ -20,6 +20,7 @@ struct MixedArgs {
   int nk_max;   // largest number of slit points in an item
   int max_deg;  // largest degree among the launched slices
   int* err;     // debug checks: counts deposits the plan did not foresee (nullptr = off)
+  int far_tails;  // separable kernel: the far-edge rational on edges >= 2 px from the centre
 };
 
 __device__ __forceinline__ float2 split_df(double v) {

@@ -51,6 +51,27 @@ __device__ __forceinline__ float tail2(float wh, float wl) {
   return (ex * P) * rcp_approx(Q);
 }
 
+// tail2 with the far-edge rational PF3/QF4 of tail_coeffs.h, for |w| >= kTailFarMinArg (fit
+// error 1.4e-8 there): the edges two or more pixels from a stamp's centre, when the model's
+// widest PSF keeps their arguments in that range.
+__device__ __forceinline__ float tail2_far(float wh, float wl) {
+  const float p = wh * wh;
+  float e = fmaf(wh, wh, -p);
+  e = fmaf(wh + wh, wl, e);
+  const float ex = ex2_approx(-p) * fmaf(e, -0.693147181f, 1.f);
+  const float x = fminf(fabsf(wh), 40.f);
+  float P = kTailFarP3;
+  P = fmaf(P, x, kTailFarP2);
+  P = fmaf(P, x, kTailFarP1);
+  P = fmaf(P, x, kTailFarP0);
+  float Q = kTailFarQ4;
+  Q = fmaf(Q, x, kTailFarQ3);
+  Q = fmaf(Q, x, kTailFarQ2);
+  Q = fmaf(Q, x, kTailFarQ1);
+  Q = fmaf(Q, x, kTailFarQ0);
+  return (ex * P) * rcp_approx(Q);
+}
+
 // As tail2, also returning 2^(-w^2) = exp(-a^2) (the Gaussian density up to a constant).
 __device__ __forceinline__ float tail2_dens(float wh, float wl, float& dens) {
   const float p = wh * wh;
@@ -205,6 +226,27 @@ __device__ __forceinline__ void edge_arg2(float2 e, float f, float gh, float gl,
   const float2 dl = __fadd2_rn(__fadd2_rn(e, f2(-dh.x, -dh.y)), f2(-ff.x, -ff.y));
   wh = __fmul2_rn(dh, g);
   wl = __fadd2_rn(__ffma2_rn(dh, g, f2(-wh.x, -wh.y)), __ffma2_rn(dh, f2(gl, gl), __fmul2_rn(dl, g)));
+}
+
+// tail2x2_w2 with the far-edge rational (tail2_far on two arguments, per component the same
+// operations as tail2_far).
+__device__ __forceinline__ float2 tail2x2_w2_far(float2 wh, float2 wl2) {
+  const float2 p = __fmul2_rn(wh, wh);
+  float2 e = __ffma2_rn(wh, wh, f2(-p.x, -p.y));
+  e = __ffma2_rn(wh, wl2, e);
+  const float2 ex = __fmul2_rn(f2(ex2_approx(-p.x), ex2_approx(-p.y)),
+                               __ffma2_rn(e, f2(-0.693147181f, -0.693147181f), f2(1.f, 1.f)));
+  const float2 x = f2(fminf(fabsf(wh.x), 40.f), fminf(fabsf(wh.y), 40.f));
+  float2 P = f2(kTailFarP3, kTailFarP3);
+  P = __ffma2_rn(P, x, f2(kTailFarP2, kTailFarP2));
+  P = __ffma2_rn(P, x, f2(kTailFarP1, kTailFarP1));
+  P = __ffma2_rn(P, x, f2(kTailFarP0, kTailFarP0));
+  float2 Q = f2(kTailFarQ4, kTailFarQ4);
+  Q = __ffma2_rn(Q, x, f2(kTailFarQ3, kTailFarQ3));
+  Q = __ffma2_rn(Q, x, f2(kTailFarQ2, kTailFarQ2));
+  Q = __ffma2_rn(Q, x, f2(kTailFarQ1, kTailFarQ1));
+  Q = __ffma2_rn(Q, x, f2(kTailFarQ0, kTailFarQ0));
+  return __fmul2_rn(__fmul2_rn(ex, P), f2(rcp_approx(Q.x), rcp_approx(Q.y)));
 }
 
 // Offset split for edge arguments: f = fh + fl with fh on the 2^-20 grid (a magic-number

@@ -140,13 +140,15 @@ bool mixed_variant_supported(int K, int DX, int DY) {
 
 cudaError_t launch_render_mixed(int K, int DX, int DY, const DevSlice* slices, const double* const* flux_tab,
                                 const double* u_all, const Item* items, int n_items, float2* store, int B, int JB,
-                                int nk_max, int max_deg, size_t smem, cudaStream_t st, int* err, const MergeArgs* mg) {
+                                int nk_max, int max_deg, int far_tails, size_t smem, cudaStream_t st, int* err,
+                                const MergeArgs* mg) {
   if (n_items == 0) return cudaSuccess;
-  MixedArgs a{slices, flux_tab, u_all, items, store, B, JB, nk_max, max_deg, err};
+  MixedArgs a{slices, flux_tab, u_all, items, store, B, JB, nk_max, max_deg, err, far_tails};
   const MergeArgs g = mg ? *mg : MergeArgs{};
+  if (far_tails && K >= 7) return launch_render_mixed_far(K, DX, DY, err != nullptr, a, g, n_items, smem, st);
   if (err) return launch_render_mixed_checked(K, DX, DY, a, g, n_items, smem, st);
 #define E2E_V(KK, X, Y) \
-  if (K == KK && DX == X && DY == Y) return launch_one<KK, X, Y, false>(a, g, n_items, smem, st);
+  if (K == KK && DX == X && DY == Y) return launch_one<KK, X, Y, false, false>(a, g, n_items, smem, st);
   E2E_MIXED_VARIANTS(E2E_V)
 #undef E2E_V
   return cudaErrorInvalidValue;

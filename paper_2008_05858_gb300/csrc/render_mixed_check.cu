@@ -8,7 +8,7 @@ namespace e2e {
 cudaError_t launch_render_mixed_checked(int K, int DX, int DY, const MixedArgs& a, const MergeArgs& mg, int n_items,
                                         size_t smem, cudaStream_t st) {
 #define E2E_V(KK, X, Y) \
-  if (K == KK && DX == X && DY == Y) return launch_one<KK, X, Y, true>(a, mg, n_items, smem, st);
+  if (K == KK && DX == X && DY == Y) return launch_one<KK, X, Y, true, false>(a, mg, n_items, smem, st);
   E2E_MIXED_VARIANTS(E2E_V)
 #undef E2E_V
   return cudaErrorInvalidValue;

@@ -498,7 +498,8 @@ def config5(seed: Optional[int] = None) -> Workload:
 def small_config(seed: int = 7, *, width: int = 300, height: int = 160, orders: int = 2, fibers: int = 2,
                  slices: int = 2, n_lambda: int = 333, n_slit: int = 13, degree: int = 5, K: int = 11,
                  psf: int = PSF_SEPARABLE, out_dtype: str = "f32", precision: str = "mixed",
-                 n_detectors: int = 1, trace_pitch: float = 16.0) -> Workload:
+                 n_detectors: int = 1, trace_pitch: float = 16.0,
+                 sigma_range: Tuple[float, float] = (1.2, 2.0)) -> Workload:
     """A small seeded model the oracle renders in well under a second.
 
     Sizes are deliberately ragged (sample and slit counts that are not multiples of the
@@ -508,7 +509,7 @@ def small_config(seed: int = 7, *, width: int = 300, height: int = 160, orders: 
     model = echelle_model(
         rng, n_detectors=n_detectors, height=height, width=width, orders_per_detector=orders, fibers=fibers,
         slices=slices, degree=degree, K=K, n_lambda=n_lambda, n_slit=n_slit, first_order=110,
-        sigma_range=(1.2, 2.0), psf=psf, trace_pitch=trace_pitch,
+        sigma_range=sigma_range, psf=psf, trace_pitch=trace_pitch,
     )
     sp = {f: science_spectra(rng, model, f, n_lines=40) for f in range(fibers)}
     return Workload(f"small-{seed}", model, sp, out_dtype, precision, "test model")

@@ -61,6 +61,10 @@ SMALL = [
     dict(seed=14, K=15, degree=5, n_lambda=60, n_slit=7, width=400, height=200),
     dict(seed=15, K=11, degree=5, n_lambda=2000, n_slit=128, orders=1, fibers=1, slices=1, width=512, height=64),
     dict(seed=16, K=15, degree=8, n_lambda=150, n_slit=20),  # the largest window and degree accepted
+    # PSFs up to 3 px wide: the far edges' arguments fall below the far-edge fit, so the plan
+    # keeps the general rational there (every case above takes the far-edge one)
+    dict(seed=17, K=15, degree=4, n_lambda=120, n_slit=9, sigma_range=(2.2, 3.0)),
+    dict(seed=18, K=5, degree=3, n_lambda=200, n_slit=6, sigma_range=(1.8, 2.6)),
 ]
 
 

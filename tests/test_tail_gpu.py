@@ -27,6 +27,26 @@ def test_tail_relative_error_is_a_few_ulp():
     assert rms < 1.2e-7, rms
 
 
+def test_far_tail_relative_error_is_a_few_ulp():
+    # the cheaper rational of the edges two or more pixels from a stamp's centre, on the range
+    # the planner admits it for (arguments >= 0.8 in log2 units, |u| >= 0.667)
+    from paper_2008_05858_gb300 import binding as B
+
+    g = torch.Generator(device="cuda").manual_seed(6)
+    lo = 0.8 / 1.2011224087864498
+    u = torch.cat([torch.linspace(lo, 6.5, 2_000_001, dtype=torch.float64, device="cuda"),
+                   lo + torch.rand(4_000_000, dtype=torch.float64, device="cuda", generator=g) * (6.5 - lo)])
+    u = torch.cat([u, -u])
+    out = torch.empty(u.shape, dtype=torch.float32, device="cuda")
+    B.e2e_eval_tail_far(u.data_ptr(), u.numel(), out.data_ptr())
+    torch.cuda.synchronize()
+    ref = torch.special.erfc(u.abs())
+    rel = ((out.double() - ref).abs() / ref).max().item()
+    assert rel < 6e-7, rel
+    rms = (((out.double() - ref) / ref) ** 2).mean().sqrt().item()
+    assert rms < 1.2e-7, rms
+
+
 def test_tail_is_finite_and_monotone_far_out():
     u = torch.linspace(0.0, 60.0, 100_001, dtype=torch.float64, device="cuda")
     got = tail(u)
