@@ -23,6 +23,15 @@ struct MixedArgs {
   int far_tails;  // separable kernel: the far-edge rational on edges >= 2 px from the centre
 };
 
+// 16-byte asynchronous copy from global to shared memory (cp.async, bypassing L1); both
+// addresses 16-byte aligned.  Completed by cp_async_wait_all in the issuing thread.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ float2 split_df(double v) {
   const float h = (float)v;
   return make_float2(h, (float)(v - (double)h));

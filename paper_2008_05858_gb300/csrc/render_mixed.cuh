@@ -121,32 +121,36 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
   __shared__ double s_w[kWarps], s_u[kWarps];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int p = tid; p < area; p += kThreads) {
-    boxh[p] = 0;
-    boxl[p] = 0u;
-  }
-  const double* flux = a.flux_tab[S.flux_slot];
-  const double* u = a.u_all + S.u_off;
-  const double inv_ns = 1.0 / (double)S.n_slit;
-  double usum = 0.0;
-  for (int kk = tid; kk < it.nk; kk += kThreads) {
-    const double uk = u[it.k0 + kk];
-    tabS[kk] = split_df(norm_sample_r(it.k0 + kk, S.n_slit, inv_ns));
-    tabU[kk] = split_df(uk);
-    usum += fabs(uk);
-  }
-  {  // mapping coefficients and PSF constants of the item's samples (per-model tables)
+  {  // mapping coefficients and PSF constants of the item's samples (per-model tables), copied
+     // to shared memory asynchronously while the box is cleared and the weights are built
     const int w = nd + 2;
     const float4* rows = S.samples + (int64_t)it.j0 * w;
     for (int e = tid; e < it.nj * w; e += kThreads) {
       const int jj = e / w, b = e - jj * w;
-      if (b < nd) tabP[jj * nd + b] = rows[e];
-      else if (b == nd) tabG[jj] = rows[e];
+      if (b < nd) cp_async16(tabP + jj * nd + b, rows + e);
+      else if (b == nd) cp_async16(tabG + jj, rows + e);
     }
+  }
+  const double* flux = a.flux_tab[S.flux_slot];
+  const double* u = a.u_all + S.u_off;
+  // this thread's first slit weight and flux, loaded before the box is cleared
+  const double u_first = tid < it.nk ? u[it.k0 + tid] : 0.0;
+  const double f_first = tid < it.nj ? flux[it.j0 + tid] : 0.0;
+  for (int p = tid; p < area; p += kThreads) {
+    boxh[p] = 0;
+    boxl[p] = 0u;
+  }
+  const double inv_ns = 1.0 / (double)S.n_slit;
+  double usum = 0.0;
+  for (int kk = tid; kk < it.nk; kk += kThreads) {
+    const double uk = kk == tid ? u_first : u[it.k0 + kk];
+    tabS[kk] = split_df(norm_sample_r(it.k0 + kk, S.n_slit, inv_ns));
+    tabU[kk] = split_df(uk);
+    usum += fabs(uk);
   }
   double wsum = 0.0;
   for (int jj = tid; jj < it.nj; jj += kThreads) {
-    const double wj = flux[it.j0 + jj] * S.dlam;
+    const double wj = (jj == tid ? f_first : flux[it.j0 + jj]) * S.dlam;
     tabW[jj] = split_df(wj * 0.25);  // 0.25: the profiles below are 2x the pixel integrals
     wsum += fabs(wj);
   }
@@ -160,6 +164,7 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
     s_w[warp] = wsum;
     s_u[warp] = usum;
   }
+  cp_async_wait_all();  // this thread's table copies; the barrier then publishes all of them
   __syncthreads();
   double wtot = 0.0, utot = 0.0;
 #pragma unroll

@@ -445,3 +445,27 @@ def test_config2_full_frame_sampled_windows(renderer):
         assert np.abs(ref).max() > 0
         rep = compare(got[y0:y0 + size, x0:x0 + size], ref)
         assert rep.ok, f"window at ({x0}, {y0}): {rep}"
+
+
+def test_width_updates_across_the_far_edge_threshold(renderer):
+    # the plan's far-edge choice follows the model's widest PSF through coefficient updates:
+    # widths of 1.3-1.9 px (far-edge rational on), scaled by 1.6 (up to ~3 px: general rational)
+    # and back, each state checked against the oracle's render of the updated model
+    w = W.small_config(seed=19, K=11, degree=4, n_lambda=150, n_slit=12, sigma_range=(1.3, 1.9))
+    mid = renderer.load_model(w.model)
+    sids = renderer.load_spectra(w)
+    cx, cy, sx, sy = renderer.params(mid)
+    try:
+        for scale in (1.0, 1.6, 1.0):
+            renderer.update(mid, cx, cy, sx * scale, sy * scale)
+            got = renderer.render(mid, sids, "mixed", "f32")
+            torch.cuda.synchronize()
+            m = renderer.models[mid]
+            ref = oracle.render(m, w.flux_for)
+            ties = tie_boxes(m, w.flux_for)
+            for d, g in enumerate(got):
+                rep = compare(g.double().cpu().numpy(), ref[d], ties=ties[d])
+                print(f"scale {scale} detector {d}: {rep}")
+                assert rep.ok, str(rep)
+    finally:
+        renderer.unload_model(mid)
