@@ -464,10 +464,10 @@ int e2e_render_static(e2e_ctx* ctx, uint64_t model_id, int32_t n_spec, const uin
 int e2e_eval_tail(const double* u_dev, int64_t n, float* out_dev, void* stream);
 
 /* Diagnostic: as e2e_eval_tail, with the cheaper rational the separable kernel uses on the
- * edges two or more pixels from a stamp's centre when the model's widest PSF keeps those
- * edges' arguments at or above 0.8 in log2 units (|u| >= 0.8 / sqrt(log2 e) ~= 0.667, the
- * range the rational is fitted on; outside it the result is unspecified).  Same arguments,
- * layout and errors as e2e_eval_tail. */
+ * edges one or more pixels from a stamp's centre when the model's widest PSF (at most ~2.12 px)
+ * keeps those edges' arguments at or above 0.4 in log2 units (|u| >= 0.4 / sqrt(log2 e) ~=
+ * 0.333, the range the rational is fitted on; outside it the result is unspecified).  Same
+ * arguments, layout and errors as e2e_eval_tail. */
 int e2e_eval_tail_far(const double* u_dev, int64_t n, float* out_dev, void* stream);
 
 /* Diagnostic (no counterpart in the paper): the fused multiply-add probe behind the roofline

@@ -483,8 +483,8 @@ def e2e_eval_tail(u_dev_ptr: int, n: int, out_dev_ptr: int, stream=None) -> None
 
 
 def e2e_eval_tail_far(u_dev_ptr: int, n: int, out_dev_ptr: int, stream=None) -> None:
-    """out[i] = the renderer's far-edge FP32 erfc(|u[i]|) for |u[i]| >= 0.667 (device pointers
-    to n doubles / n floats)."""
+    """out[i] = the renderer's cheaper FP32 erfc(|u[i]|) of narrow PSFs' tail edges, for
+    |u[i]| >= 0.333 (device pointers to n doubles / n floats)."""
     rc = load_library().e2e_eval_tail_far(C.c_void_p(u_dev_ptr), n, C.c_void_p(out_dev_ptr),
                                           C.c_void_p(_stream_handle(stream)))
     if rc != E2E_OK:

@@ -65,7 +65,7 @@ struct SliceHost {
 struct Plan {
   bool ok = false;
   int B = 1, DX = 0, DY = 0, JB = 1, NB = 8, max_area = 0, max_deg = 0, nk_max = 1;
-  int far_tails = 0;  // separable kernel: every far edge's argument within the far-edge fit
+  int far_tails = 0;  // separable kernel: every tail edge's argument within the cheaper rational's fit
   std::vector<Item> items;  // host copy
   int64_t store_elems = 0;
   size_t smem = 0;
@@ -631,14 +631,15 @@ int plan_model(Model* m) {
     }
   }
   P.B = bB;
-  // Edges two or more pixels from a stamp's centre sit at |e - f| >= 2 px, i.e. at arguments
-  // w >= 2 sqrt(log2 e) / (sqrt 2 sigma) in log2 units: when the model's widest PSF keeps that
-  // at or above the far-edge fit's lower end, the separable kernel takes the cheaper rational
-  // there (a margin of 1e-3 on the width covers the FP32 rounding of the per-sample constants).
+  // The tail edges (off the centre pixel) sit at |e - f| >= 1 px from a stamp's centre, i.e. at
+  // arguments w >= sqrt(log2 e) / (sqrt 2 sigma) in log2 units: when the model's widest PSF
+  // keeps that at or above the cheaper rational's lower end (sigma <= 2.12 px), the separable
+  // kernel takes that rational on them (a margin of 1e-3 on the width covers the FP32 rounding
+  // of the per-sample constants).
   {
     double smax = 0.0;
     for (auto& s : m->slices) smax = std::max(smax, std::max(quad_max(s.d.sigma_x), quad_max(s.d.sigma_y)));
-    const double limit = 2.0 * kSqrtLog2eD / (std::sqrt(2.0) * (double)kTailFarMinArg);
+    const double limit = kSqrtLog2eD / (std::sqrt(2.0) * (double)kTailFarMinArg);
     P.far_tails = !ellip && smax <= limit * (1.0 - 1e-3) ? 1 : 0;
   }
   P.DX = bDX;

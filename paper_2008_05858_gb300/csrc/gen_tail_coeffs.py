@@ -52,9 +52,9 @@ def fit(m=M, n=N, amax=A * KAPPA, iters=120, npts=6000, amin=0.0):
 
 ERF_W, ERF_TERMS = 1.0, 6
 
-# Far edges (two or more pixels from the stamp centre) of a model whose widest PSF keeps their
+# Tail edges (one or more pixels from the stamp centre) of a model whose widest PSF keeps their
 # arguments at or above FAR_W: a cheaper (3, 4) rational on [FAR_W, 6.5 sqrt(log2 e)].
-FAR_M, FAR_N, FAR_W = 3, 4, 0.8
+FAR_M, FAR_N, FAR_W = 3, 4, 0.4
 
 
 def fit_erf(wmax=ERF_W, nt=ERF_TERMS, iters=80, npts=4000):
@@ -89,11 +89,12 @@ def main():
         *["constexpr float kTailP%d = %.9ef;" % (i, c) for i, c in enumerate(p)],
         *["constexpr float kTailQ%d = %.9ef;" % (i, c) for i, c in enumerate(q)],
         "constexpr float kTailMaxArg = %.4ff;  // largest w the fit covers" % (A * KAPPA),
-        "// far edges: erfcx(w / sqrt(log2 e)) ~= PF(w)/QF(w) on w in [%.2f, %.1f sqrt(log2 e)], degrees (%d, %d),"
+        "// tail edges of narrow PSFs: erfcx(w / sqrt(log2 e)) ~= PF(w)/QF(w) on w in [%.2f, %.1f sqrt(log2 e)],"
+        " degrees (%d, %d),"
         " max relative fit error %.2e" % (FAR_W, A, FAR_M, FAR_N, ef),
         *["constexpr float kTailFarP%d = %.9ef;" % (i, c) for i, c in enumerate(pf)],
         *["constexpr float kTailFarQ%d = %.9ef;" % (i, c) for i, c in enumerate(qf)],
-        "constexpr float kTailFarMinArg = %.2ff;  // smallest w the far fit covers" % FAR_W,
+        "constexpr float kTailFarMinArg = %.2ff;  // smallest w that fit covers" % FAR_W,
         "constexpr float kSqrtLog2e = %.9ff;" % KAPPA,
         "constexpr double kSqrtLog2eD = %.17g;" % KAPPA,
         "// erf(w / sqrt(log2 e)) ~= w * S(w^2) for |w| <= %.2f, %d terms, max relative fit error %.2e"
@@ -105,7 +106,7 @@ def main():
     ]
     with open(os.path.join(here, "tail_coeffs.h"), "w") as fh:
         fh.write("\n".join(lines))
-    print("erfcx rational: max relative fit error %.3e; far-edge rational: %.3e; erf polynomial: %.3e"
+    print("erfcx rational: max relative fit error %.3e; tail-edge rational: %.3e; erf polynomial: %.3e"
           % (e, ef, ee))
 
 

@@ -20,7 +20,7 @@ struct MixedArgs {
   int nk_max;   // largest number of slit points in an item
   int max_deg;  // largest degree among the launched slices
   int* err;     // debug checks: counts deposits the plan did not foresee (nullptr = off)
-  int far_tails;  // separable kernel: the far-edge rational on edges >= 2 px from the centre
+  int far_tails;  // separable kernel: the cheaper rational on the tail edges (>= 1 px from the centre)
 };
 
 // 16-byte asynchronous copy from global to shared memory (cp.async, bypassing L1); both

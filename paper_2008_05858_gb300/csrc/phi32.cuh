@@ -51,9 +51,9 @@ __device__ __forceinline__ float tail2(float wh, float wl) {
   return (ex * P) * rcp_approx(Q);
 }
 
-// tail2 with the far-edge rational PF3/QF4 of tail_coeffs.h, for |w| >= kTailFarMinArg (fit
-// error 1.4e-8 there): the edges two or more pixels from a stamp's centre, when the model's
-// widest PSF keeps their arguments in that range.
+// tail2 with the cheaper rational PF3/QF4 of tail_coeffs.h, for |w| >= kTailFarMinArg (fit
+// error 4.9e-8 there): the tail edges (one or more pixels from a stamp's centre), when the
+// model's widest PSF keeps their arguments in that range.
 __device__ __forceinline__ float tail2_far(float wh, float wl) {
   const float p = wh * wh;
   float e = fmaf(wh, wh, -p);
@@ -228,7 +228,7 @@ __device__ __forceinline__ void edge_arg2(float2 e, float f, float gh, float gl,
   wl = __fadd2_rn(__ffma2_rn(dh, g, f2(-wh.x, -wh.y)), __ffma2_rn(dh, f2(gl, gl), __fmul2_rn(dl, g)));
 }
 
-// tail2x2_w2 with the far-edge rational (tail2_far on two arguments, per component the same
+// tail2x2_w2 with the cheaper rational (tail2_far on two arguments, per component the same
 // operations as tail2_far).
 __device__ __forceinline__ float2 tail2x2_w2_far(float2 wh, float2 wl2) {
   const float2 p = __fmul2_rn(wh, wh);

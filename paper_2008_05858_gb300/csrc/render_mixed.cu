@@ -145,7 +145,7 @@ cudaError_t launch_render_mixed(int K, int DX, int DY, const DevSlice* slices, c
   if (n_items == 0) return cudaSuccess;
   MixedArgs a{slices, flux_tab, u_all, items, store, B, JB, nk_max, max_deg, err, far_tails};
   const MergeArgs g = mg ? *mg : MergeArgs{};
-  if (far_tails && K >= 7) return launch_render_mixed_far(K, DX, DY, err != nullptr, a, g, n_items, smem, st);
+  if (far_tails && K >= 3) return launch_render_mixed_far(K, DX, DY, err != nullptr, a, g, n_items, smem, st);
   if (err) return launch_render_mixed_checked(K, DX, DY, a, g, n_items, smem, st);
 #define E2E_V(KK, X, Y) \
   if (K == KK && DX == X && DY == Y) return launch_one<KK, X, Y, false, false>(a, g, n_items, smem, st);

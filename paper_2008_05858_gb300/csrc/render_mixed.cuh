@@ -78,9 +78,10 @@ struct FusedArgs {
 };
 
 // CHECK: debug build of the same kernel, counting into a.err every deposit the plan did not
-// foresee (the non-checking instantiation carries none of that code).  FAR: the far-edge
-// rational on the edges two or more pixels from a stamp's centre (the plan's far_tails; only
-// windows of K >= 7 have such edge pairs, smaller ones take FAR = false).
+// foresee (the non-checking instantiation carries none of that code).  FAR: the cheaper tail
+// rational on every tail edge (the edges one or more pixels from a stamp's centre) when the
+// model's widest PSF keeps their arguments within its fit (the plan's far_tails; K = 1 has no
+// tail edges and takes FAR = false).
 template <int K, int DX, int DY, bool CHECK, bool FAR>
 __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_render_mixed(const FusedArgs fa) {
   const MixedArgs& a = fa.a;
@@ -270,11 +271,10 @@ __global__ void __launch_bounds__(kThreads, mixed_min_blocks<K, DX, DY>()) k_ren
         const int m0 = i < H ? i : i + 2, m1 = i + 1 < H ? i + 1 : i + 3;
         float2 wh, wl2;
         edge_arg2_split(f2((float)(m0 - H) - 0.5f, (float)(m1 - H) - 0.5f), fh, gh, gl2, c1, c2, wh, wl2);
-        // both edges two or more pixels from the centre (|e - f| >= 2): the far-edge rational
-        // when the plan found every such argument within its fit
-        const bool farp = (m0 <= H - 2 || m0 >= H + 3) && (m1 <= H - 2 || m1 >= H + 3);
+        // edges one or more pixels from the centre (|e - f| >= 1): the cheaper rational when the
+        // plan found every such argument within its fit
         float2 t;
-        if (FAR && farp)
+        if (FAR)
           t = tail2x2_w2_far(wh, wl2);
         else
           t = tail2x2_w2(wh, wl2);
@@ -424,8 +424,8 @@ static cudaError_t launch_one(const MixedArgs& a, const MergeArgs& mg, int n_ite
   return cudaGetLastError();
 }
 
-// Debug-check instantiations (render_mixed_check.cu) and the far-edge ones of windows K >= 7
-// (render_mixed_far.cu: production, render_mixed_check_far.cu: debug checks), each a
+// Debug-check instantiations (render_mixed_check.cu) and the cheaper-tail ones of windows
+// K >= 3 (render_mixed_far.cu: production, render_mixed_check_far.cu: debug checks), each a
 // translation unit of its own so that the instantiations compile in parallel.
 cudaError_t launch_render_mixed_checked(int K, int DX, int DY, const MixedArgs& a, const MergeArgs& mg, int n_items,
                                         size_t smem, cudaStream_t st);
@@ -442,12 +442,12 @@ cudaError_t launch_render_mixed_far_checked(int K, int DX, int DY, const MixedAr
   V(1, 1, 3) V(3, 1, 3) V(5, 1, 3) V(7, 1, 3) V(9, 1, 3) V(11, 1, 3)                                    \
   V(1, 2, 2) V(3, 2, 2) V(5, 2, 2) V(7, 2, 2) V(9, 2, 2)
 
-// The variants with far edge pairs (K >= 7), instantiated a second time with FAR = true.
+// The variants with tail edges (K >= 3), instantiated a second time with FAR = true.
 #define E2E_MIXED_FAR_VARIANTS(V)                                                                       \
-  V(7, 0, 0) V(9, 0, 0) V(11, 0, 0) V(13, 0, 0) V(15, 0, 0)                                             \
-  V(7, 1, 1) V(9, 1, 1) V(11, 1, 1) V(13, 1, 1)                                                         \
-  V(7, 1, 2) V(9, 1, 2) V(11, 1, 2) V(13, 1, 2)                                                         \
-  V(7, 1, 3) V(9, 1, 3) V(11, 1, 3)                                                                     \
-  V(7, 2, 2) V(9, 2, 2)
+  V(3, 0, 0) V(5, 0, 0) V(7, 0, 0) V(9, 0, 0) V(11, 0, 0) V(13, 0, 0) V(15, 0, 0)                       \
+  V(3, 1, 1) V(5, 1, 1) V(7, 1, 1) V(9, 1, 1) V(11, 1, 1) V(13, 1, 1)                                   \
+  V(3, 1, 2) V(5, 1, 2) V(7, 1, 2) V(9, 1, 2) V(11, 1, 2) V(13, 1, 2)                                   \
+  V(3, 1, 3) V(5, 1, 3) V(7, 1, 3) V(9, 1, 3) V(11, 1, 3)                                               \
+  V(3, 2, 2) V(5, 2, 2) V(7, 2, 2) V(9, 2, 2)
 
 }  // namespace e2e

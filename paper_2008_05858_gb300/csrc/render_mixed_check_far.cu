@@ -1,4 +1,4 @@
-// Debug-check instantiations of the far-edge separable render kernel (render_mixed_far.cu):
+// Debug-check instantiations of the cheaper-tail separable render kernel (render_mixed_far.cu):
 // the same kernel, also counting every deposit the plan did not foresee.
 #include "render_mixed.cuh"
 

@@ -1,7 +1,7 @@
-// Far-edge instantiations of the separable-PSF mixed render kernel: the windows with edge
-// pairs two or more pixels from the stamp's centre (K >= 7), for models whose widest PSF keeps
-// those edges' arguments within the far-edge rational's fit (the plan's far_tails).  A
-// separate translation unit so that the library's sets of instantiations compile in parallel.
+// Cheaper-tail instantiations of the separable-PSF mixed render kernel: the windows with tail
+// edges (K >= 3), for models whose widest PSF keeps those edges' arguments within the cheaper
+// rational's fit (the plan's far_tails).  A separate translation unit so that the library's
+// sets of instantiations compile in parallel.
 #include "render_mixed.cuh"
 
 namespace e2e {

@@ -14,17 +14,17 @@ constexpr float kTailQ3 = 7.188032186e-01f;
 constexpr float kTailQ4 = 1.780958689e-01f;
 constexpr float kTailQ5 = 2.032556214e-02f;
 constexpr float kTailMaxArg = 7.8073f;  // largest w the fit covers
-// far edges: erfcx(w / sqrt(log2 e)) ~= PF(w)/QF(w) on w in [0.80, 6.5 sqrt(log2 e)], degrees (3, 4), max relative fit error 1.36e-08
-constexpr float kTailFarP0 = 9.998039818e-01f;
-constexpr float kTailFarP1 = 9.024380298e-01f;
-constexpr float kTailFarP2 = 3.693471869e-01f;
-constexpr float kTailFarP3 = 6.936352788e-02f;
+// tail edges of narrow PSFs: erfcx(w / sqrt(log2 e)) ~= PF(w)/QF(w) on w in [0.40, 6.5 sqrt(log2 e)], degrees (3, 4), max relative fit error 4.91e-08
+constexpr float kTailFarP0 = 9.999673184e-01f;
+constexpr float kTailFarP1 = 8.650136613e-01f;
+constexpr float kTailFarP2 = 3.418012716e-01f;
+constexpr float kTailFarP3 = 5.964265918e-02f;
 constexpr float kTailFarQ0 = 1.000000000e+00f;
-constexpr float kTailFarQ1 = 1.840645697e+00f;
-constexpr float kTailFarQ2 = 1.408933934e+00f;
-constexpr float kTailFarQ3 = 5.447929490e-01f;
-constexpr float kTailFarQ4 = 1.023646609e-01f;
-constexpr float kTailFarMinArg = 0.80f;  // smallest w the far fit covers
+constexpr float kTailFarQ1 = 1.804167850e+00f;
+constexpr float kTailFarQ2 = 1.344621157e+00f;
+constexpr float kTailFarQ3 = 5.040287026e-01f;
+constexpr float kTailFarQ4 = 8.802431055e-02f;
+constexpr float kTailFarMinArg = 0.40f;  // smallest w that fit covers
 constexpr float kSqrtLog2e = 1.201122409f;
 constexpr double kSqrtLog2eD = 1.2011224087864498;
 // erf(w / sqrt(log2 e)) ~= w * S(w^2) for |w| <= 1.00, 6 terms, max relative fit error 4.78e-09

@@ -42,13 +42,13 @@ def test_general_erfcx_rational():
     assert rel < 2e-8, rel  # fit 2.0e-9, plus the FP32 rounding of the coefficients
 
 
-def test_far_edge_erfcx_rational():
+def test_tail_edge_erfcx_rational():
     w = np.linspace(C["kTailFarMinArg"], C["kTailMaxArg"], 200001)
     r = _poly("kTailFarP", 3, w) / _poly("kTailFarQ", 4, w)
     rel = np.abs(r / special.erfcx(w / KAPPA) - 1).max()
-    assert rel < 5e-8, rel  # fit 1.4e-8, plus the FP32 rounding of the coefficients
-    # below its range the far-edge rational is not meant to be used: it is visibly worse there
-    w0 = np.linspace(0.0, 0.4, 1001)
+    assert rel < 8e-8, rel  # fit 4.9e-8, plus the FP32 rounding of the coefficients
+    # below its range the cheaper rational is not meant to be used: it is visibly worse there
+    w0 = np.linspace(0.0, 0.1, 1001)
     r0 = _poly("kTailFarP", 3, w0) / _poly("kTailFarQ", 4, w0)
     assert np.abs(r0 / special.erfcx(w0 / KAPPA) - 1).max() > 10 * rel
 

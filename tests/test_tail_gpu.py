@@ -28,12 +28,12 @@ def test_tail_relative_error_is_a_few_ulp():
 
 
 def test_far_tail_relative_error_is_a_few_ulp():
-    # the cheaper rational of the edges two or more pixels from a stamp's centre, on the range
-    # the planner admits it for (arguments >= 0.8 in log2 units, |u| >= 0.667)
+    # the cheaper rational of the tail edges (one or more pixels from a stamp's centre), on the
+    # range the planner admits it for (arguments >= 0.4 in log2 units, |u| >= 0.333)
     from paper_2008_05858_gb300 import binding as B
 
     g = torch.Generator(device="cuda").manual_seed(6)
-    lo = 0.8 / 1.2011224087864498
+    lo = 0.4 / 1.2011224087864498
     u = torch.cat([torch.linspace(lo, 6.5, 2_000_001, dtype=torch.float64, device="cuda"),
                    lo + torch.rand(4_000_000, dtype=torch.float64, device="cuda", generator=g) * (6.5 - lo)])
     u = torch.cat([u, -u])
