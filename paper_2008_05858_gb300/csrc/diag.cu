@@ -1,8 +1,7 @@
 // Diagnostic entry points: evaluate the renderer's FP32 Gaussian-tail functions (the general
-// one and the far-edge one) on given arguments, so tests can check them against CUDA's FP64
-// erfc; and a fused multiply-add probe
-// that measures the FP32 and FP64 FMA rates the roofline of the ALU-bound kernels is quoted
-// against.
+// one and the cheaper one of narrow PSFs' tail edges) on given arguments, so tests can check
+// them against CUDA's FP64 erfc; and a fused multiply-add probe that measures the FP32 and
+// FP64 FMA rates the roofline of the ALU-bound kernels is quoted against.
 #include "../../include/e2e_render.h"
 #include "phi32.cuh"
 

@@ -61,8 +61,8 @@ SMALL = [
     dict(seed=14, K=15, degree=5, n_lambda=60, n_slit=7, width=400, height=200),
     dict(seed=15, K=11, degree=5, n_lambda=2000, n_slit=128, orders=1, fibers=1, slices=1, width=512, height=64),
     dict(seed=16, K=15, degree=8, n_lambda=150, n_slit=20),  # the largest window and degree accepted
-    # PSFs up to 3 px wide: the far edges' arguments fall below the far-edge fit, so the plan
-    # keeps the general rational there (every case above takes the far-edge one)
+    # PSFs up to 3 px wide: the tail edges' arguments fall below the cheaper rational's fit, so
+    # the plan keeps the general rational there (every case above with K >= 3 takes the cheaper one)
     dict(seed=17, K=15, degree=4, n_lambda=120, n_slit=9, sigma_range=(2.2, 3.0)),
     dict(seed=18, K=5, degree=3, n_lambda=200, n_slit=6, sigma_range=(1.8, 2.6)),
 ]
@@ -448,8 +448,8 @@ def test_config2_full_frame_sampled_windows(renderer):
 
 
 def test_width_updates_across_the_far_edge_threshold(renderer):
-    # the plan's far-edge choice follows the model's widest PSF through coefficient updates:
-    # widths of 1.3-1.9 px (far-edge rational on), scaled by 1.6 (up to ~3 px: general rational)
+    # the plan's choice of tail rational follows the model's widest PSF through coefficient
+    # updates: widths of 1.3-1.9 px (cheaper rational), scaled by 1.6 (up to ~3 px: general one)
     # and back, each state checked against the oracle's render of the updated model
     w = W.small_config(seed=19, K=11, degree=4, n_lambda=150, n_slit=12, sigma_range=(1.3, 1.9))
     mid = renderer.load_model(w.model)
