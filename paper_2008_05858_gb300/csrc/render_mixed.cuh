@@ -48,8 +48,9 @@ struct MixedLayout {
 #ifndef E2E_SMALL_TILE_BLOCKS
 #define E2E_SMALL_TILE_BLOCKS 4
 #endif
-// CTAs per SM the register budget is set for (128-thread CTAs): 4 (128 registers) for lane
-// tiles up to 72 accumulators, E2E_MID_TILE_BLOCKS up to 84, else 2.
+// CTAs per SM the register budget is set for (128-thread CTAs): E2E_SMALL_TILE_BLOCKS (4:
+// 128 registers) for lane tiles up to 72 accumulators -- every quad tile, at most 16 x 4; five
+// CTAs (96 registers) fit without spills but ran slower -- E2E_MID_TILE_BLOCKS up to 84, else 2.
 template <int K, int DX, int DY>
 constexpr int mixed_min_blocks() {
   return ((K + DX) * ((K + DY + 3) / 4) <= 72 ? E2E_SMALL_TILE_BLOCKS : ((K + DX) * ((K + DY + 3) / 4) <= 84 ? E2E_MID_TILE_BLOCKS : 2)) *
