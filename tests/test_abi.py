@@ -53,3 +53,17 @@ def test_create_without_a_gpu_fails_loudly():
 
 def test_build_targets_sm_103a_only():
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_cheaper_tail_instantiations_cover_every_tail_variant():
+    # the render dispatches to the FAR = true instantiation for every tile variant with tail
+    # edges (K >= 3) when the plan sets far_tails; the two variant lists must agree on those
+    src = open(os.path.join(ROOT, "paper_2008_05858_gb300", "csrc", "render_mixed.cuh")).read()
+
+    def variants(name):
+        i = src.index(f"#define {name}(V)")
+        j = src.index("\n\n", i)
+        return set((int(k), int(x), int(y)) for k, x, y in re.findall(r"V\((\d+), (\d+), (\d+)\)", src[i:j]))
+
+    base, far = variants("E2E_MIXED_VARIANTS"), variants("E2E_MIXED_FAR_VARIANTS")
+    assert far == {v for v in base if v[0] >= 3}
